@@ -1,0 +1,424 @@
+"""Pins of the CPU oracle against facts fixed outside it.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, libm, closed forms from the paper's equations, exhaustive
+enumeration on tiny instances, the exact Boltzmann distribution, or invariants
+the method guarantees.  No GPU is needed.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+TWO32 = 1 << 32
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_known_answers():
+    """Random123's published Philox4x32-10 vectors (SC'11 generator)."""
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        vals = [int(x, 16) for x in row]
+        ctr, key, want = vals[0:4], vals[4:6], vals[6:10]
+        got = oracle.philox4x32_10(ctr, key)
+        assert [int(x) for x in got] == want
+
+
+# ------------------------------------------------------------------ det_exp
+def test_det_exp_within_one_ulp_of_libm():
+    rng = np.random.default_rng(7)
+    xs = np.concatenate([rng.uniform(-700, 700, 20000), rng.uniform(-1, 1, 5000),
+                         rng.uniform(-40, 0, 5000)])
+    worst = 0.0
+    for x in xs:
+        a, b = oracle.det_exp(x), math.exp(x)
+        worst = max(worst, abs(a - b) / math.ulp(b))
+    assert worst <= 1.0
+
+
+def test_det_exp_special_values_and_monotone():
+    assert oracle.det_exp(0.0) == 1.0
+    assert oracle.det_exp(-708.0) == 0.0
+    assert math.isinf(oracle.det_exp(710.0))
+    grid = np.linspace(-30, 30, 60001)
+    vals = np.array([oracle.det_exp(x) for x in grid])
+    assert np.all(np.diff(vals) >= 0)
+
+
+def test_round_nonneg():
+    for x, want in [(0.0, 0), (0.49999999999999994, 0), (0.5, 1), (1.5, 2), (2.5, 3),
+                    (4294967295.5, 4294967296), (4294967296.0, 4294967296), (7.25, 7)]:
+        assert oracle.round_nonneg(x) == want
+
+
+# ------------------------------------------------------------------ thresholds
+@pytest.mark.parametrize("beta", [0.01, 0.1, 0.7, 3.0])
+def test_heatbath_threshold_is_eq4(beta):
+    """T(h)/2^32 = (1 + tanh(beta h))/2, the Eq. 4 probability of s=+1."""
+    for h in range(-60, 61):
+        T = oracle.thr_heatbath(beta, h)
+        exact = TWO32 * (1.0 + math.tanh(beta * h)) / 2.0
+        assert abs(T - exact) <= 1.0 + 1e-6 * exact
+        assert 0 <= T <= TWO32
+    assert oracle.thr_heatbath(beta, 0) == TWO32 // 2
+
+
+@pytest.mark.parametrize("beta", [0.05, 0.5, 2.0])
+def test_metropolis_threshold(beta):
+    for dE in range(-20, 41):
+        T = oracle.thr_metropolis(beta, dE)
+        if dE <= 0:
+            assert T == TWO32
+        else:
+            assert abs(T - TWO32 * math.exp(-beta * dE)) <= 1.0 + 1e-9 * TWO32
+
+
+@pytest.mark.parametrize("beta", [0.1, 0.9, 2.5])
+def test_cascaded_sampler_reproduces_softmax(beta):
+    """Suppl. S3: P(0)=T1, P(1)=(1-T1)T2, P(2)=(1-T1)(1-T2) equal the Eq. 8 softmax."""
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        syn = rng.integers(-12, 1, size=3)
+        z = np.exp(beta * syn.astype(np.float64))
+        soft = z / z.sum()
+        t1 = oracle.thr_potts_b1(beta, syn[1] - syn[0], syn[2] - syn[0]) / TWO32
+        t2 = oracle.thr_potts_b2(beta, syn[2] - syn[1]) / TWO32
+        got = np.array([t1, (1 - t1) * t2, (1 - t1) * (1 - t2)])
+        assert np.allclose(got, soft, atol=4.0 / TWO32, rtol=0)
+
+
+# ------------------------------------------------------------------ permutation
+def test_permutation_is_uniform_and_shared_order():
+    n = 7
+    counts = np.zeros((n, n))
+    for t in range(600):
+        for sw in range(5):
+            p = oracle.permutation(n, 11, t, sw)
+            assert sorted(p.tolist()) == list(range(n))
+            counts[p, np.arange(n)] += 1
+    from scipy.stats import chisquare
+    assert chisquare(counts.ravel()).pvalue > 1e-4
+    assert not np.array_equal(oracle.permutation(50, 1, 0, 0), oracle.permutation(50, 1, 0, 1))
+    assert np.array_equal(oracle.permutation(50, 1, 3, 2), oracle.permutation(50, 1, 3, 2))
+
+
+# ------------------------------------------------------------------ resampling
+def _tau(E, delta, escale=1.0):
+    E = np.asarray(E, dtype=np.float64)
+    x = -delta * escale * E          # Eq. 1 weight exp(-(beta_{i+1}-beta_i) E_j)
+    w = np.exp(x - x.max())
+    return len(E) * w / w.sum()
+
+
+def test_resample_conserves_population_and_rounds_tau():
+    rng = np.random.default_rng(5)
+    for trial in range(200):
+        R = int(rng.integers(1, 300))
+        E = rng.integers(-2000, 2000, size=R)
+        delta = float(rng.choice([0.02, -0.02, 0.3, 0.0005]))
+        par, cnt = oracle.resample(E, delta, 1.0, 9, trial)
+        assert cnt.sum() == R
+        assert np.all(np.diff(par) >= 0)
+        assert np.array_equal(np.bincount(par, minlength=R), cnt)
+        tau = _tau(E, delta)
+        assert np.all(cnt >= np.floor(tau - 1e-6)) and np.all(cnt <= np.ceil(tau + 1e-6))
+
+
+def test_resample_zero_delta_is_identity():
+    E = np.array([5, -3, 100, 7, 7, 0], dtype=np.int64)
+    par, cnt = oracle.resample(E, 0.0, 1.0, 1, 4)
+    assert par.tolist() == list(range(6)) and cnt.tolist() == [1] * 6
+
+
+def test_resample_expected_copies_equal_tau():
+    """Eq. 1-2 read as expected copy numbers summing to R."""
+    E = np.array([0, 1, 2, 3, 5, 8, 13, 21], dtype=np.int64)
+    delta = 0.15
+    tot = np.zeros(8)
+    T = 4000
+    for t in range(T):
+        _, cnt = oracle.resample(E, delta, 1.0, 21, t)
+        tot += cnt
+    assert np.allclose(tot / T, _tau(E, delta), atol=0.03)
+
+
+# ------------------------------------------------------------------ energies
+def _dense_J(inst):
+    J = np.zeros((inst.n, inst.n), dtype=np.int64)
+    for i in range(inst.n):
+        for e in range(inst.row_ptr[i], inst.row_ptr[i + 1]):
+            J[i, inst.col[e]] = -inst.w[e]
+    return J
+
+
+def test_energy_and_cut_identity():
+    inst = W.erdos_renyi(40, 0.2, signed=True, seed=2)
+    J = _dense_J(inst)
+    Jcsr = -inst.w
+    Wsum = int(np.triu(-J).sum())
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        s = rng.choice([-1, 1], size=inst.n).astype(np.int8)
+        E = oracle.energy_ising(inst.row_ptr, inst.col, Jcsr, s)
+        assert E == int(-0.5 * s.astype(np.int64) @ J @ s.astype(np.int64))
+        cut = int(sum((-J[i, j]) for i in range(inst.n) for j in range(i + 1, inst.n)
+                      if J[i, j] != 0 and s[i] != s[j]))
+        assert cut == (Wsum - E) // 2 and (Wsum - E) % 2 == 0
+        lab = rng.integers(0, 3, size=inst.n).astype(np.int8)
+        Ep = oracle.energy_potts(inst.row_ptr, inst.col, Jcsr, lab)
+        same = (lab[:, None] == lab[None, :]).astype(np.int64)
+        assert Ep == int(-np.triu(J * (2 * same - 1), 1).sum())
+        cut3 = int(sum((-J[i, j]) for i in range(inst.n) for j in range(i + 1, inst.n)
+                       if J[i, j] != 0 and lab[i] != lab[j]))
+        assert cut3 == (Wsum - Ep) // 2
+
+
+@pytest.mark.parametrize("kind,rule", [(0, 0), (0, 1), (1, 0)])
+def test_incremental_fields_match_recompute(kind, rule):
+    inst = W.gnm(60, 150, signed=True, seed=4)
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, kind=kind, rule=rule, R=12, sweeps=3,
+                           steps=8, beta0=0.2, beta1=2.0)
+    J = _dense_J(inst)
+    for _ in range(8):
+        run.step(1)
+        s = run.spins().astype(np.int64)
+        f = run.fields()
+        E = run.energy()
+        if kind == 0:
+            assert np.array_equal(f, s @ J.T)
+            assert np.array_equal(E, (-0.5 * np.einsum("ri,ij,rj->r", s, J, s)).astype(np.int64))
+        else:
+            onehot = np.stack([(s == c).astype(np.int64) for c in range(3)], axis=-1)
+            assert np.array_equal(f, np.einsum("ij,rjc->ric", J, onehot))
+            for r in range(12):
+                assert E[r] == oracle.energy_potts(inst.row_ptr, inst.col, -inst.w, s[r].astype(np.int8))
+
+
+# ------------------------------------------------------------------ brute force optimum
+def _brute_maxcut(inst):
+    n = inst.n
+    states = ((np.arange(1 << n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.int8)
+    cut = np.zeros(1 << n, dtype=np.int64)
+    for i in range(n):
+        for e in range(inst.row_ptr[i], inst.row_ptr[i + 1]):
+            j = inst.col[e]
+            if i < j:
+                cut += inst.w[e] * (states[:, i] != states[:, j])
+    return int(cut.max())
+
+
+def _brute_max3cut(inst):
+    n = inst.n
+    states = np.array(list(itertools.product(range(3), repeat=n)), dtype=np.int8)
+    cut = np.zeros(states.shape[0], dtype=np.int64)
+    for i in range(n):
+        for e in range(inst.row_ptr[i], inst.row_ptr[i + 1]):
+            j = inst.col[e]
+            if i < j:
+                cut += inst.w[e] * (states[:, i] != states[:, j])
+    return int(cut.max())
+
+
+@pytest.mark.parametrize("seed,signed", [(0, False), (1, True), (2, True)])
+def test_pamc_finds_brute_force_maxcut(seed, signed):
+    inst = W.erdos_renyi(16, 0.4, signed=signed, seed=seed)
+    opt = _brute_maxcut(inst)
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=64, sweeps=2, steps=40, beta0=0.1,
+                           beta1=3.0, seed=seed)
+    run.step(40)
+    m, best = run.best()
+    assert m == opt
+    cut = sum(inst.w[e] for i in range(inst.n) for e in range(inst.row_ptr[i], inst.row_ptr[i + 1])
+              if i < inst.col[e] and best[i] != best[inst.col[e]])
+    assert cut == m and best[0] == 1
+
+
+def test_potts_finds_brute_force_max3cut():
+    inst = W.erdos_renyi(9, 0.6, signed=False, seed=5)
+    opt = _brute_max3cut(inst)
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, kind=1, R=64, sweeps=2, steps=40,
+                           beta0=0.1, beta1=3.0, seed=3)
+    run.step(40)
+    m, best = run.best()
+    assert m == opt
+    assert best[0] == 0
+
+
+def test_target_cut_stops_early():
+    inst = W.erdos_renyi(16, 0.4, signed=False, seed=0)
+    opt = _brute_maxcut(inst)
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=64, sweeps=2, steps=400, beta0=0.1,
+                           beta1=3.0, target_cut=opt)
+    ran = run.step(400)
+    assert ran < 400 and run.ctl()["done"] == 1 and run.best()[0] == opt
+
+
+# ------------------------------------------------------------------ Boltzmann sampling
+def _chi2_pvalue(obs, p):
+    from scipy.stats import chi2
+    exp = p * obs.sum()
+    keep = exp > 5
+    stat = float((((obs - exp) ** 2) / np.where(exp > 0, exp, 1))[keep].sum())
+    return chi2.sf(stat, keep.sum() - 1)
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_fixed_beta_sweeps_sample_boltzmann_ising(rule):
+    """Eq. 4 (heat-bath) and Metropolis leave exp(-beta H) invariant."""
+    inst = W.erdos_renyi(6, 0.7, signed=True, seed=8)
+    beta = 0.45
+    n = inst.n
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, rule=rule, R=512, sweeps=1, steps=60,
+                           beta0=beta, beta1=beta, resample=0, seed=17)
+    obs = np.zeros(1 << n)
+    for step in range(60):
+        run.step(1)
+        if step >= 10 and step % 2 == 0:
+            s = run.spins()
+            code = ((s > 0).astype(np.int64) << np.arange(n)).sum(axis=1)
+            obs += np.bincount(code, minlength=1 << n)
+    states = np.where(((np.arange(1 << n)[:, None] >> np.arange(n)) & 1) == 1, 1, -1).astype(np.int8)
+    E = np.array([oracle.energy_ising(inst.row_ptr, inst.col, -inst.w, s) for s in states], dtype=np.float64)
+    p = np.exp(-beta * E)
+    p /= p.sum()
+    assert _chi2_pvalue(obs, p) > 1e-4
+    # a wrong temperature is rejected by the same statistic
+    q = np.exp(-2 * beta * E)
+    q /= q.sum()
+    assert _chi2_pvalue(obs, q) < 1e-6
+
+
+def test_fixed_beta_sweeps_sample_potts():
+    """Cascaded sampler at Eq. 8's beta samples exp(-(beta/2) E) of Eq. 6."""
+    inst = W.erdos_renyi(5, 0.8, signed=True, seed=6)
+    beta = 0.8
+    n = inst.n
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, kind=1, R=1024, sweeps=1, steps=50,
+                           beta0=beta, beta1=beta, resample=0, seed=23)
+    obs = np.zeros(3 ** n)
+    for step in range(50):
+        run.step(1)
+        if step >= 10 and step % 2 == 0:
+            s = run.spins().astype(np.int64)
+            code = (s * (3 ** np.arange(n))).sum(axis=1)
+            obs += np.bincount(code, minlength=3 ** n)
+    states = np.array(list(itertools.product(range(3), repeat=n)), dtype=np.int8)[:, ::-1]
+    E = np.array([oracle.energy_potts(inst.row_ptr, inst.col, -inst.w, np.ascontiguousarray(s))
+                  for s in states], dtype=np.float64)
+    p = np.exp(-0.5 * beta * E)
+    p /= p.sum()
+    assert _chi2_pvalue(obs, p) > 1e-4
+    q = np.exp(-beta * E)
+    q /= q.sum()
+    assert _chi2_pvalue(obs, q) < 1e-6
+
+
+# ------------------------------------------------------------------ NCM
+def test_ncm_preserves_energy_and_builds_maximal_independent_iso_set():
+    inst = W.torus(12, 12, signed=True, seed=1)
+    J = _dense_J(inst)
+    rng = np.random.default_rng(2)
+    for r in range(30):
+        s = rng.choice([-1, 1], size=inst.n).astype(np.int8)
+        h = (J @ s.astype(np.int64)).astype(np.int32)
+        iso = set(np.nonzero(h == 0)[0].tolist())
+        E0 = oracle.energy_ising(inst.row_ptr, inst.col, -inst.w, s)
+        s1, h1 = s.copy(), h.copy()
+        k = oracle.ncm_replica(inst.row_ptr, inst.col, -inst.w, s1, h1, 4, 99, 3, r)
+        flipped = set(np.nonzero(s1 != s)[0].tolist())
+        assert len(flipped) == k and flipped <= iso
+        assert all(J[a, b] == 0 for a in flipped for b in flipped if a != b)
+        assert all(any(J[a, b] != 0 for b in flipped) for a in iso - flipped)
+        assert oracle.energy_ising(inst.row_ptr, inst.col, -inst.w, s1) == E0
+        assert np.array_equal(h1, (J @ s1.astype(np.int64)).astype(np.int32))
+
+
+def test_ncm_on_dense_flips_at_most_one_site():
+    inst = W.dense_csr(24, seed=3)
+    J = _dense_J(inst)
+    rng = np.random.default_rng(4)
+    for r in range(40):
+        s = rng.choice([-1, 1], size=inst.n).astype(np.int8)
+        h = (J @ s.astype(np.int64)).astype(np.int32)
+        s1 = s.copy()
+        k = oracle.ncm_replica(inst.row_ptr, inst.col, -inst.w, s1, h.copy(), 4, 5, 0, r)
+        assert k == (1 if (h == 0).any() else 0)
+
+
+# ------------------------------------------------------------------ controller
+def _ctl(**kw):
+    return oracle.Controller(stagnation=1, beta0=0.1, beta1=2.1, steps=101, z_rst=0, **kw)
+
+
+def test_controller_keeps_cooling_while_progressing():
+    c = _ctl()
+    beta = 0.1
+    for m in range(60):
+        assert not c.update(m)
+        beta = beta + 0.02
+        st = c.state()
+        assert st["delta"] == pytest.approx(0.02) and st["enable_cm"] == 0
+        assert st["beta"] == beta
+
+
+def test_controller_strong_stagnation_reheats_and_arms_ncm():
+    c = _ctl()
+    beta = 0.1
+    for i in range(39):
+        c.update(7)
+        beta = beta + 0.02
+    assert c.state()["enable_cm"] == 0 and c.state()["beta"] == beta
+    c.update(7)                      # 40th entry: both windows hold one value
+    st = c.state()
+    assert st["enable_cm"] == 1
+    assert st["beta"] == 0.8 * beta + 0.02
+    assert st["delta"] == pytest.approx(0.02)
+
+
+def test_controller_mild_stagnation_reverses_beta():
+    c = _ctl()
+    seq = list(range(1, 16)) + [15] * 25      # 40 entries: last 25 one value, last 40 fifteen
+    beta = 0.1
+    for m in seq[:-1]:
+        c.update(m)
+        beta = beta + 0.02
+    c.update(seq[-1])
+    st = c.state()
+    assert st["enable_cm"] == 0
+    assert st["delta"] == pytest.approx(-0.02)
+    assert st["beta"] == pytest.approx(beta - 0.02)
+
+
+def test_controller_restart_resets_schedule():
+    c = oracle.Controller(stagnation=1, beta0=0.1, beta1=2.1, steps=101, z_rst=5)
+    flags = [c.update(m) for m in range(5)]
+    assert flags == [False, False, False, False, True]
+    st = c.state()
+    assert st["z"] == 1 and st["cycle"] == 1 and st["beta"] == 0.1 and st["hist_len"] == 0
+
+
+# ------------------------------------------------------------------ SA baseline
+def test_without_resampling_replicas_are_independent_chains():
+    inst = W.gnm(30, 60, signed=True, seed=1)
+    a = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=4, sweeps=2, steps=6, resample=0)
+    b = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=9, sweeps=2, steps=6, resample=0)
+    a.step(6)
+    b.step(6)
+    assert np.array_equal(a.spins(), b.spins()[:4])
+
+
+def test_augmented_run_invokes_ncm_and_preserves_energy():
+    inst = W.torus(16, 16, signed=True, seed=2)
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=32, sweeps=2, steps=150, beta0=0.5,
+                           beta1=6.0, stagnation=1, z_rst=120, cooldown_tau=5)
+    run.step(150)
+    st = run.ctl()
+    assert st["ncm_flipped"] > 0 and st["ncm_dE_max"] == 0 and st["cycle"] == 1
