@@ -1,0 +1,152 @@
+/*
+ * pamc.h -- C ABI of the GB300 (sm_103a) augmented Population Annealing Monte
+ * Carlo library (libpamc.so).
+ *
+ * Method: Khan, Redding, Shukla, "Leveraging Population Dynamics to Steer
+ * Efficient Search in Large-Scale Combinatorial Optimization".  The library
+ * runs Algorithm 1 (augmented PAMC) on one GPU:
+ *   - population resampling by Boltzmann weights, Eq. 1-2 (systematic
+ *     resampling over an integer prefix scan of fixed-point weights);
+ *   - S single-spin sweeps per temperature step in a random order shared by
+ *     all replicas, Eq. 3-4 (heat-bath) or Metropolis, and the Max-3-Cut
+ *     three-state Potts update of Eq. 6-7 with the cascaded sampler of
+ *     Suppl. S3;
+ *   - the best cut M* (cut = (W - E)/2), the stagnation-driven adaptive
+ *     temperature control and restart of Algorithm 1 / Sec. II.C, and the
+ *     energy-preserving non-local cluster moves (NCM) of Sec. II.C.
+ * Every result is bit-identical to the plain CPU restatement of the same
+ * steps for the same seed: random numbers come from counter-keyed
+ * Philox4x32-10, thresholds and resampling weights from a deterministic
+ * binary64 exp, and all energies, fields and cuts are exact integers.
+ *
+ * Conventions:
+ *   - Max-Cut weights w (symmetric, zero diagonal); Ising couplings J = -w,
+ *     energy H(s) = -sum_{i<j} J_ij s_i s_j, W = sum_{i<j} w_ij.
+ *   - Spins are int8 +1/-1 (Ising) or labels 0,1,2 (Potts), replica-major:
+ *     element [r*n + i].
+ *
+ * Errors: every call returns a pamc_status; nothing aborts, traps or prints.
+ * A failed call leaves the handle usable unless it returns PAMC_ERR_CUDA.
+ * pamc_last_error() gives a one-line message for the last failure on a
+ * handle.  Device-side waits are bounded; a wait that runs out reports
+ * PAMC_ERR_TIMEOUT.
+ *
+ * Threading: a handle is used by one host thread at a time.  All device work
+ * of a handle is ordered on the stream given at creation.
+ */
+#ifndef PAMC_H
+#define PAMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pamc_handle_s *pamc_handle;
+
+typedef enum {
+    PAMC_OK = 0,
+    PAMC_ERR_ARG = 1,      /* null pointer, bad size or bad parameter */
+    PAMC_ERR_ASYM = 2,     /* coupling matrix not symmetric */
+    PAMC_ERR_DIAG = 3,     /* nonzero diagonal / self loop */
+    PAMC_ERR_RANGE = 4,    /* a value outside what the kernels represent */
+    PAMC_ERR_OOM = 5,      /* device allocation failed */
+    PAMC_ERR_CUDA = 6,     /* CUDA runtime error (message in pamc_last_error) */
+    PAMC_ERR_TIMEOUT = 7,  /* a bounded device wait gave up */
+    PAMC_ERR_STATE = 8     /* call out of order (e.g. pamc_step before pamc_init) */
+} pamc_status;
+
+/* Parameters of one run (the inputs of Algorithm 1). */
+typedef struct {
+    int32_t kind;           /* 0 Max-Cut (Ising), 1 Max-3-Cut (three-state Potts) */
+    int32_t rule;           /* Ising: 0 heat-bath (Eq. 4), 1 Metropolis */
+    int32_t R;              /* population size */
+    int32_t sweeps;         /* S, sweeps per temperature step */
+    int32_t steps;          /* iterations; dbeta = (beta1-beta0)/(steps-1) */
+    double beta0, beta1;    /* linear schedule; beta <- beta + Delta each step */
+    int32_t stagnation;     /* 0 conventional PAMC, 1 adaptive control + NCM */
+    int32_t z_rst;          /* restart every z_rst iterations; <= 0 never */
+    int32_t cooldown_tau;   /* NCM cooldown tau */
+    int32_t n_top;          /* NCM applied to the n_top lowest-energy replicas */
+    int32_t mis_trials;     /* randomised greedy MIS constructions per NCM */
+    int32_t win_short, win_long;                       /* 25, 40 in the paper */
+    int32_t max_distinct_short, max_distinct_long;     /* 3, 5 in the paper */
+    double reheat_factor;   /* 0.8 in the paper */
+    int64_t target_cut;     /* MC*: stop once M* >= target; < 0 none */
+    uint64_t seed;          /* Philox key */
+    int32_t restart_reinit; /* 1: a restart re-randomises the population */
+    int32_t resample;       /* 1 PAMC; 0 independent chains (SA baseline) */
+} pamc_params;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Must be
+ * set before any handle is created; NULL restores cudaMalloc/cudaFree. */
+typedef void *(*pamc_alloc_fn)(size_t bytes, int device, void *stream, void *ctx);
+typedef void (*pamc_free_fn)(void *ptr, int device, void *stream, void *ctx);
+pamc_status pamc_set_allocator(pamc_alloc_fn alloc, pamc_free_fn free_fn, void *ctx);
+
+/* Create a handle for a sparse Max-Cut instance given as symmetric CSR on the
+ * HOST (row_ptr[n+1], col[nnz], w[nnz]; Algorithm 1's coupling-matrix input).
+ * The arrays are validated and copied; the caller keeps ownership.
+ * Limits: 1 <= n < 2^24, |w| <= 127, max_i sum_j |w_ij| <= 127 (the field
+ * range held by the sweep kernels), else PAMC_ERR_RANGE.  Asymmetric input
+ * gives PAMC_ERR_ASYM, a self loop PAMC_ERR_DIAG.  stream is a cudaStream_t
+ * (NULL = legacy default stream) on device cuda_device. */
+pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            const int32_t *w, int cuda_device, void *stream, pamc_handle *out);
+
+/* Create a handle for a dense Max-Cut instance: w is n*n int8 row-major,
+ * symmetric with zero diagonal, either in host memory (w_on_device = 0) or
+ * in device memory of cuda_device (w_on_device = 1; only read during the
+ * call).  Entries must lie in {-1, 0, +1}, else PAMC_ERR_RANGE. */
+pamc_status pamc_create_dense(int32_t n, const int8_t *w, int w_on_device, int cuda_device,
+                              void *stream, pamc_handle *out);
+
+/* Set the run parameters, allocate the population and draw the random
+ * initial population (Algorithm 1, Initialization).  Asynchronous. */
+pamc_status pamc_init(pamc_handle h, const pamc_params *p);
+
+/* Enqueue nsteps iterations of Algorithm 1 (asynchronous; iterations after
+ * the target cut is reached do nothing). */
+pamc_status pamc_step(pamc_handle h, int32_t nsteps);
+
+/* Wait for the handle's stream and report device-side errors. */
+pamc_status pamc_sync(pamc_handle h);
+
+/* pamc_init + pamc_step(p->steps) + pamc_sync. */
+pamc_status pamc_run(pamc_handle h, const pamc_params *p);
+
+/* Best cut M* so far and its configuration (HOST buffer of n int8, may be
+ * NULL).  Ising spins are returned with spin 0 = +1; Potts labels renamed in
+ * order of first appearance.  Synchronises the stream. */
+pamc_status pamc_best(pamc_handle h, int64_t *cut, int8_t *spins);
+
+/* Current population and the last step's resampling, into HOST buffers
+ * (any may be NULL): spins[R*n], E[R] (energies), parents[R] (old replica
+ * index of each new slot), counts[R] (copies of each old replica).
+ * Synchronises the stream. */
+pamc_status pamc_state(pamc_handle h, int8_t *spins, int64_t *E, int32_t *parents,
+                       int32_t *counts);
+
+/* Controller state: iv[10] = t, z, cycle, cooldown, enable_cm, done,
+ * NCM applied in the last iteration, history length, spins flipped by NCM so
+ * far, largest |dE| across an NCM; dv[2] = beta, Delta.  Synchronises. */
+pamc_status pamc_control_state(pamc_handle h, int64_t *iv, double *dv);
+
+/* Number of this library's kernels launched on the handle so far. */
+int64_t pamc_launch_count(pamc_handle h);
+
+/* W = sum_{i<j} w_ij of the instance (cut = (W - E)/2). */
+int64_t pamc_weight_sum(pamc_handle h);
+
+/* Copy the last error message of h (or of the last failed create when h is
+ * NULL) into buf. */
+pamc_status pamc_last_error(pamc_handle h, char *buf, size_t len);
+
+void pamc_destroy(pamc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

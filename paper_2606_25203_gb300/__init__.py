@@ -1,0 +1,288 @@
+"""GB300 (sm_103a) augmented Population Annealing Monte Carlo.
+
+Thin Python binding of the C ABI in ``include/pamc.h`` (libpamc.so): argument
+marshalling only, every step of a run executes in the library's CUDA kernels.
+The functions carry the C names (``pamc_create_csr``, ``pamc_init``,
+``pamc_step``, ``pamc_run``, ``pamc_best``, ...).  PyTorch provides the device
+memory (its caching allocator is registered with the library) and the stream.
+
+There is no CPU fallback: importing the package without the built library or
+a CUDA device raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "PamcError", "Params", "load", "pamc_create_csr", "pamc_create_dense", "pamc_init",
+    "pamc_step", "pamc_sync", "pamc_run", "pamc_best", "pamc_state", "pamc_control_state",
+    "pamc_launch_count", "pamc_weight_sum", "pamc_last_error", "pamc_destroy", "Solver",
+]
+
+STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
+          4: "PAMC_ERR_RANGE", 5: "PAMC_ERR_OOM", 6: "PAMC_ERR_CUDA", 7: "PAMC_ERR_TIMEOUT",
+          8: "PAMC_ERR_STATE"}
+
+
+class PamcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``pamc_params``."""
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("rule", ctypes.c_int32), ("R", ctypes.c_int32),
+        ("sweeps", ctypes.c_int32), ("steps", ctypes.c_int32),
+        ("beta0", ctypes.c_double), ("beta1", ctypes.c_double),
+        ("stagnation", ctypes.c_int32), ("z_rst", ctypes.c_int32),
+        ("cooldown_tau", ctypes.c_int32), ("n_top", ctypes.c_int32), ("mis_trials", ctypes.c_int32),
+        ("win_short", ctypes.c_int32), ("win_long", ctypes.c_int32),
+        ("max_distinct_short", ctypes.c_int32), ("max_distinct_long", ctypes.c_int32),
+        ("reheat_factor", ctypes.c_double), ("target_cut", ctypes.c_int64),
+        ("seed", ctypes.c_uint64), ("restart_reinit", ctypes.c_int32), ("resample", ctypes.c_int32),
+    ]
+
+
+DEFAULTS = dict(kind=0, rule=0, R=16, sweeps=1, steps=10, beta0=0.1, beta1=3.0, stagnation=0,
+                z_rst=0, cooldown_tau=10, n_top=0, mis_trials=4, win_short=25, win_long=40,
+                max_distinct_short=3, max_distinct_long=5, reheat_factor=0.8, target_cut=-1,
+                seed=0, restart_reinit=1, resample=1)
+
+_lib = None
+_alloc_cbs = None
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p,
+                             ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def _register_torch_allocator(L):
+    """Route the library's device allocations through torch's caching allocator."""
+    global _alloc_cbs
+    import torch
+
+    def _alloc(nbytes, device, stream, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0))
+        except Exception:   # allocation failure is reported as NULL (PAMC_ERR_OOM)
+            return None
+
+    def _free(ptr, device, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _alloc_cbs = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    rc = L.pamc_set_allocator(_alloc_cbs[0], _alloc_cbs[1], None)
+    if rc != 0:
+        raise PamcError(rc, "pamc_set_allocator failed")
+
+
+def load(build_if_missing: bool = True, torch_allocator: bool = True):
+    """Load libpamc.so (building it with nvcc if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"libpamc.so is not built ({path}); run __graft_entry__.build()")
+        path = _build.build()
+    L = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.pamc_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, P]
+    L.pamc_create_csr.argtypes = [i32, P, P, P, ctypes.c_int, P, ctypes.POINTER(P)]
+    L.pamc_create_dense.argtypes = [i32, P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)]
+    L.pamc_init.argtypes = [P, ctypes.POINTER(Params)]
+    L.pamc_step.argtypes = [P, i32]
+    L.pamc_sync.argtypes = [P]
+    L.pamc_run.argtypes = [P, ctypes.POINTER(Params)]
+    L.pamc_best.argtypes = [P, P, P]
+    L.pamc_state.argtypes = [P, P, P, P, P]
+    L.pamc_control_state.argtypes = [P, P, P]
+    L.pamc_launch_count.argtypes = [P]
+    L.pamc_launch_count.restype = i64
+    L.pamc_weight_sum.argtypes = [P]
+    L.pamc_weight_sum.restype = i64
+    L.pamc_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
+    L.pamc_destroy.argtypes = [P]
+    for nm in ("pamc_set_allocator", "pamc_create_csr", "pamc_create_dense", "pamc_init",
+               "pamc_step", "pamc_sync", "pamc_run", "pamc_best", "pamc_state",
+               "pamc_control_state", "pamc_last_error"):
+        getattr(L, nm).restype = ctypes.c_int
+    if torch_allocator:
+        _register_torch_allocator(L)
+    _lib = L
+    return L
+
+
+def _check(rc: int, h=None):
+    if rc != 0:
+        buf = ctypes.create_string_buffer(256)
+        _lib.pamc_last_error(h, buf, 256)
+        raise PamcError(rc, buf.value.decode(errors="replace"))
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(device: int, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(int(torch.cuda.current_stream(device).cuda_stream))
+
+
+def make_params(**kw) -> Params:
+    p = dict(DEFAULTS)
+    p.update(kw)
+    return Params(**p)
+
+
+# ---------------------------------------------------------------- C-ABI mirror
+def pamc_create_csr(n, row_ptr, col, w, device: int = 0, stream=None):
+    L = load()
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    ww = np.ascontiguousarray(w, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(L.pamc_create_csr(int(n), _ptr(rp), _ptr(cl), _ptr(ww), int(device),
+                             _stream_ptr(device, stream), ctypes.byref(h)))
+    return h
+
+
+def pamc_create_dense(n, w, device: int = 0, stream=None):
+    """w: host numpy int8 (n, n) or a CUDA tensor (pointer passed as device memory)."""
+    L = load()
+    h = ctypes.c_void_p()
+    if isinstance(w, np.ndarray):
+        arr = np.ascontiguousarray(w, dtype=np.int8)
+        _check(L.pamc_create_dense(int(n), _ptr(arr), 0, int(device), _stream_ptr(device, stream),
+                                   ctypes.byref(h)))
+    else:
+        _check(L.pamc_create_dense(int(n), ctypes.c_void_p(int(w.data_ptr())), 1, int(device),
+                                   _stream_ptr(device, stream), ctypes.byref(h)))
+    return h
+
+
+def pamc_init(h, **params):
+    p = make_params(**params)
+    _check(_lib.pamc_init(h, ctypes.byref(p)), h)
+    return p
+
+
+def pamc_step(h, nsteps: int = 1):
+    _check(_lib.pamc_step(h, int(nsteps)), h)
+
+
+def pamc_sync(h):
+    _check(_lib.pamc_sync(h), h)
+
+
+def pamc_run(h, **params):
+    p = make_params(**params)
+    _check(_lib.pamc_run(h, ctypes.byref(p)), h)
+    return p
+
+
+def pamc_best(h, n: int):
+    cut = np.zeros(1, dtype=np.int64)
+    spins = np.zeros(n, dtype=np.int8)
+    _check(_lib.pamc_best(h, _ptr(cut), _ptr(spins)), h)
+    return int(cut[0]), spins
+
+
+def pamc_state(h, R: int, n: int):
+    spins = np.zeros((R, n), dtype=np.int8)
+    E = np.zeros(R, dtype=np.int64)
+    par = np.zeros(R, dtype=np.int32)
+    cnt = np.zeros(R, dtype=np.int32)
+    _check(_lib.pamc_state(h, _ptr(spins), _ptr(E), _ptr(par), _ptr(cnt)), h)
+    return spins, E, par, cnt
+
+
+CTL_KEYS = ("t", "z", "cycle", "cooldown", "enable_cm", "done", "ncm_last", "hist_len",
+            "ncm_flipped", "ncm_dE_max")
+
+
+def pamc_control_state(h) -> dict:
+    iv = np.zeros(10, dtype=np.int64)
+    dv = np.zeros(2, dtype=np.float64)
+    _check(_lib.pamc_control_state(h, _ptr(iv), _ptr(dv)), h)
+    d = {k: int(v) for k, v in zip(CTL_KEYS, iv)}
+    d["beta"], d["delta"] = float(dv[0]), float(dv[1])
+    return d
+
+
+def pamc_launch_count(h) -> int:
+    return int(_lib.pamc_launch_count(h))
+
+
+def pamc_weight_sum(h) -> int:
+    return int(_lib.pamc_weight_sum(h))
+
+
+def pamc_last_error(h=None) -> str:
+    buf = ctypes.create_string_buffer(256)
+    load().pamc_last_error(h, buf, 256)
+    return buf.value.decode(errors="replace")
+
+
+def pamc_destroy(h):
+    if h is not None and h.value:
+        _lib.pamc_destroy(h)
+
+
+class Solver:
+    """Convenience owner of one handle on a CSR Max-Cut instance."""
+
+    def __init__(self, row_ptr, col, w, device: int = 0, stream=None):
+        self.n = len(row_ptr) - 1
+        self.h = pamc_create_csr(self.n, row_ptr, col, w, device, stream)
+        self.R = 0
+
+    def init(self, **params):
+        p = pamc_init(self.h, **params)
+        self.R = p.R
+        return p
+
+    def step(self, k: int = 1):
+        pamc_step(self.h, k)
+
+    def sync(self):
+        pamc_sync(self.h)
+
+    def run(self, **params):
+        p = pamc_run(self.h, **params)
+        self.R = p.R
+        return p
+
+    def best(self):
+        return pamc_best(self.h, self.n)
+
+    def state(self):
+        return pamc_state(self.h, self.R, self.n)
+
+    def control(self):
+        return pamc_control_state(self.h)
+
+    def launches(self) -> int:
+        return pamc_launch_count(self.h)
+
+    def close(self):
+        pamc_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            if self.h is not None:
+                self.close()
+        except Exception:
+            pass

@@ -1,0 +1,480 @@
+// api.cu -- the C ABI of libpamc (declared in include/pamc.h): instance
+// validation and upload, device memory of a run, and the per-iteration launch
+// sequence of Algorithm 1.  Host code only marshals arguments and enqueues
+// kernels; every step of an iteration runs on the GPU, and the controller
+// state stays in device memory so the host never waits inside a run.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "pamc_internal.h"
+
+using namespace pamc;
+
+namespace pamc {
+cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint64_t *tab,
+                          cudaStream_t st);
+cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
+                        int32_t *count, int32_t *ncm_idx, int32_t *targets, cudaStream_t st);
+cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
+                       const int8_t *src, const int64_t *E_src, const int32_t *parent,
+                       const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey, uint8_t *nstat,
+                       DevCtl *ctl, cudaStream_t st);
+cudaError_t launch_control(int32_t n, int64_t W, const pamc_params &p, const int64_t *E,
+                           const int8_t *spins, int8_t *best, DevCtl *ctl, cudaStream_t st);
+size_t prep_smem_bytes(int32_t R);
+}  // namespace pamc
+
+namespace {
+
+pamc_alloc_fn g_alloc = nullptr;
+pamc_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+thread_local char g_create_err[256] = "";
+
+constexpr int kSchedSlots = 16;   // schedules of this many steps are built per launch
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct pamc_handle_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int32_t n = 0, nnz = 0, H = 0;
+    int64_t W = 0;
+    int dense = 0;
+    // instance
+    int32_t *d_rp = nullptr;
+    uint32_t *d_adj = nullptr;
+    // run
+    pamc_params p{};
+    int initialized = 0;
+    int64_t host_t = 0;
+    int64_t sched_end = 0;     // schedules exist for steps < sched_end
+    SweepCfg cfg{1, 1};
+    std::vector<DevBuf> bufs;  // every device allocation of the run
+    std::vector<DevBuf> inst_bufs;
+    int8_t *d_spins[2] = {nullptr, nullptr};
+    int64_t *d_E[2] = {nullptr, nullptr};
+    int32_t *d_parent = nullptr, *d_count = nullptr, *d_ncm_idx = nullptr, *d_targets = nullptr;
+    int8_t *d_ncm_buf = nullptr;
+    uint32_t *d_nkey = nullptr;
+    uint8_t *d_nstat = nullptr;
+    uint64_t *d_tab = nullptr;
+    int32_t *d_order = nullptr, *d_lvl = nullptr, *d_nlev = nullptr, *d_scnt = nullptr;
+    uint32_t *d_skey = nullptr;
+    DevCtl *d_ctl = nullptr;
+    int8_t *d_best = nullptr;
+    int64_t launches = 0;
+    char err[256] = "";
+};
+
+namespace {
+
+pamc_status fail(pamc_handle h, pamc_status s, const char *fmt, ...) {
+    char buf[256];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) snprintf(h->err, sizeof(h->err), "%s", buf);
+    else snprintf(g_create_err, sizeof(g_create_err), "%s", buf);
+    return s;
+}
+
+pamc_status cuda_fail(pamc_handle h, cudaError_t e, const char *what) {
+    return fail(h, PAMC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void *dev_alloc(pamc_handle h, size_t bytes, std::vector<DevBuf> &list) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (g_alloc) {
+        p = g_alloc(bytes, h->device, (void *)h->stream, g_alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) list.push_back({p, bytes});
+    return p;
+}
+
+void dev_free_all(pamc_handle h, std::vector<DevBuf> &list) {
+    if (!list.empty()) cudaStreamSynchronize(h->stream);
+    for (auto &b : list) {
+        if (g_free) g_free(b.p, h->device, (void *)h->stream, g_alloc_ctx);
+        else cudaFree(b.p);
+    }
+    list.clear();
+}
+
+template <typename T>
+bool alloc_n(pamc_handle h, T *&ptr, size_t count, std::vector<DevBuf> &list) {
+    ptr = static_cast<T *>(dev_alloc(h, count * sizeof(T), list));
+    return ptr != nullptr;
+}
+
+// Validated symmetric CSR -> packed adjacency (col | J<<24 with J = -w).
+pamc_status validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
+                         std::vector<uint32_t> &adj, int64_t &W, int32_t &H) {
+    if (n < 1 || n >= (1 << 24) || !rp || (!col && rp && rp[n] > 0) || (!w && rp && rp[n] > 0))
+        return fail(nullptr, PAMC_ERR_ARG, "invalid n or null CSR pointer");
+    if (rp[0] != 0) return fail(nullptr, PAMC_ERR_ARG, "row_ptr[0] must be 0");
+    for (int32_t i = 0; i < n; ++i)
+        if (rp[i + 1] < rp[i]) return fail(nullptr, PAMC_ERR_ARG, "row_ptr not monotone at %d", i);
+    const int32_t nnz = rp[n];
+    std::vector<std::tuple<int32_t, int32_t, int32_t>> fwd, bwd;
+    fwd.reserve(nnz);
+    bwd.reserve(nnz);
+    adj.resize(nnz);
+    W = 0;
+    H = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t habs = 0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t j = col[e];
+            if (j < 0 || j >= n) return fail(nullptr, PAMC_ERR_ARG, "column index out of range");
+            if (j == i) return fail(nullptr, PAMC_ERR_DIAG, "self loop at vertex %d", i);
+            if (w[e] < -127 || w[e] > 127)
+                return fail(nullptr, PAMC_ERR_RANGE, "|w| > 127 at (%d,%d)", i, j);
+            fwd.emplace_back(i, j, w[e]);
+            bwd.emplace_back(j, i, w[e]);
+            habs += w[e] < 0 ? -w[e] : w[e];
+            W += w[e];
+            const int32_t J = -w[e];
+            adj[e] = (uint32_t)j | ((uint32_t)(uint8_t)(int8_t)J << 24);
+        }
+        if (habs > 127)
+            return fail(nullptr, PAMC_ERR_RANGE, "sum_j |w_ij| = %lld > 127 at vertex %d",
+                        (long long)habs, i);
+        H = std::max<int32_t>(H, (int32_t)habs);
+    }
+    std::sort(fwd.begin(), fwd.end());
+    std::sort(bwd.begin(), bwd.end());
+    if (fwd != bwd) return fail(nullptr, PAMC_ERR_ASYM, "coupling matrix is not symmetric");
+    W /= 2;
+    return PAMC_OK;
+}
+
+void release_run(pamc_handle h) {
+    dev_free_all(h, h->bufs);
+    h->initialized = 0;
+    h->d_spins[0] = h->d_spins[1] = nullptr;
+}
+
+SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H) {
+    SweepCfg c{1, 1};
+    const int RPG = kind == 0 ? 4 : 2;
+    const int32_t groups = (R + RPG - 1) / RPG;
+    c.warps_per_group = n >= 16384 ? 8 : n >= 4096 ? 4 : n >= 1024 ? 2 : 1;
+    const size_t per_group = (size_t)((n + 15) & ~15) + RPG * 8;
+    const size_t tabb = (size_t)(kind == 0 ? 2 * H + 1 : 4 * H + 1) * 8;
+    int gpc = 1024 / (32 * c.warps_per_group);
+    while (gpc > 1 && tabb + gpc * per_group > 96 * 1024) --gpc;
+    gpc = std::min(gpc, 15);
+    const int32_t want_ctas = 152 * 2;
+    while (gpc > 1 && (groups + gpc - 1) / gpc < want_ctas) --gpc;
+    c.groups_per_cta = std::max(gpc, 1);
+    return c;
+}
+
+}  // namespace
+
+extern "C" {
+
+pamc_status pamc_set_allocator(pamc_alloc_fn alloc, pamc_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(nullptr, PAMC_ERR_ARG, "allocator and free function must both be set or both NULL");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+    return PAMC_OK;
+}
+
+pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                            const int32_t *w, int cuda_device, void *stream, pamc_handle *out) {
+    if (!out) return fail(nullptr, PAMC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    std::vector<uint32_t> adj;
+    int64_t W = 0;
+    int32_t H = 0;
+    pamc_status s = validate_csr(n, row_ptr, col, w, adj, W, H);
+    if (s != PAMC_OK) return s;
+    cudaError_t e = cudaSetDevice(cuda_device);
+    if (e != cudaSuccess) return fail(nullptr, PAMC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    pamc_handle h = new (std::nothrow) pamc_handle_s();
+    if (!h) return fail(nullptr, PAMC_ERR_OOM, "host allocation failed");
+    h->device = cuda_device;
+    h->stream = (cudaStream_t)stream;
+    h->n = n;
+    h->nnz = row_ptr[n];
+    h->W = W;
+    h->H = H;
+    if (!alloc_n(h, h->d_rp, (size_t)n + 1, h->inst_bufs) ||
+        !alloc_n(h, h->d_adj, (size_t)std::max(h->nnz, 1), h->inst_bufs)) {
+        dev_free_all(h, h->inst_bufs);
+        delete h;
+        return fail(nullptr, PAMC_ERR_OOM, "device allocation of the instance failed");
+    }
+    e = cudaMemcpyAsync(h->d_rp, row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && h->nnz > 0)
+        e = cudaMemcpyAsync(h->d_adj, adj.data(), sizeof(uint32_t) * h->nnz, cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        dev_free_all(h, h->inst_bufs);
+        delete h;
+        return fail(nullptr, PAMC_ERR_CUDA, "instance upload: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return PAMC_OK;
+}
+
+pamc_status pamc_create_dense(int32_t n, const int8_t *w, int w_on_device, int cuda_device,
+                              void *stream, pamc_handle *out) {
+    (void)n; (void)w; (void)w_on_device; (void)cuda_device; (void)stream;
+    if (out) *out = nullptr;
+    return fail(nullptr, PAMC_ERR_ARG, "dense instances are not supported by this build");
+}
+
+pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
+    if (!h || !pp) return fail(h, PAMC_ERR_ARG, "null handle or params");
+    pamc_params p = *pp;
+    if (p.kind != 0 && p.kind != 1) return fail(h, PAMC_ERR_ARG, "kind must be 0 or 1");
+    if (p.rule != 0 && p.rule != 1) return fail(h, PAMC_ERR_ARG, "rule must be 0 or 1");
+    if (p.kind == 1 && p.rule != 0) return fail(h, PAMC_ERR_ARG, "Potts supports the cascaded heat-bath rule only");
+    if (p.R < 1 || p.R > 16384) return fail(h, PAMC_ERR_RANGE, "R must be in [1, 16384]");
+    if (p.sweeps < 0 || p.steps < 1) return fail(h, PAMC_ERR_ARG, "sweeps >= 0 and steps >= 1 required");
+    if (p.win_short < 0 || p.win_long < 0 || p.win_short > kHistMax || p.win_long > kHistMax)
+        return fail(h, PAMC_ERR_RANGE, "stagnation windows must be in [0, %d]", kHistMax);
+    if (p.n_top <= 0) p.n_top = std::max(1, p.R / 16);
+    if (p.mis_trials < 0) return fail(h, PAMC_ERR_ARG, "mis_trials must be >= 0");
+    if (!(p.beta0 == p.beta0) || !(p.beta1 == p.beta1)) return fail(h, PAMC_ERR_ARG, "beta is NaN");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    release_run(h);
+    h->p = p;
+    const int32_t n = h->n, R = p.R, S = std::max(p.sweeps, 1);
+    const int32_t ntop = std::min(p.n_top, R);
+    const size_t tabn = p.kind == 0 ? (size_t)(2 * h->H + 1)
+                                    : (size_t)(4 * h->H + 1) * (4 * h->H + 1) + (4 * h->H + 1);
+    bool ok = alloc_n(h, h->d_spins[0], (size_t)R * n, h->bufs) &&
+              alloc_n(h, h->d_spins[1], (size_t)R * n, h->bufs) &&
+              alloc_n(h, h->d_E[0], R, h->bufs) && alloc_n(h, h->d_E[1], R, h->bufs) &&
+              alloc_n(h, h->d_parent, R, h->bufs) && alloc_n(h, h->d_count, R, h->bufs) &&
+              alloc_n(h, h->d_ncm_idx, R, h->bufs) && alloc_n(h, h->d_targets, R, h->bufs) &&
+              alloc_n(h, h->d_tab, tabn, h->bufs) && alloc_n(h, h->d_ctl, 1, h->bufs) &&
+              alloc_n(h, h->d_best, n, h->bufs) &&
+              alloc_n(h, h->d_order, (size_t)kSchedSlots * S * n, h->bufs) &&
+              alloc_n(h, h->d_lvl, (size_t)kSchedSlots * S * (n + 1), h->bufs) &&
+              alloc_n(h, h->d_nlev, (size_t)kSchedSlots * S, h->bufs) &&
+              alloc_n(h, h->d_skey, (size_t)kSchedSlots * S * n, h->bufs) &&
+              alloc_n(h, h->d_scnt, (size_t)kSchedSlots * S * n, h->bufs);
+    if (ok && p.stagnation && p.kind == 0)
+        ok = alloc_n(h, h->d_ncm_buf, (size_t)ntop * n, h->bufs) &&
+             alloc_n(h, h->d_nkey, (size_t)ntop * n, h->bufs) &&
+             alloc_n(h, h->d_nstat, (size_t)ntop * n, h->bufs);
+    if (!ok) {
+        release_run(h);
+        return fail(h, PAMC_ERR_OOM, "device allocation of the population failed");
+    }
+    DevCtl c;
+    memset(&c, 0, sizeof(c));
+    c.t = 0;
+    c.z = 1;
+    c.beta = p.beta0;
+    c.dbeta = p.steps > 1 ? (p.beta1 - p.beta0) / (double)(p.steps - 1) : 0.0;
+    c.delta = c.dbeta;
+    c.mstar = INT64_MIN;
+    c.best_replica = -1;
+    e = cudaMemcpyAsync(h->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "controller upload");
+    std::vector<int32_t> ident(R), ones(R, 1), minus(R, -1);
+    for (int32_t r = 0; r < R; ++r) ident[r] = r;
+    e = cudaMemcpyAsync(h->d_parent, ident.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_count, ones.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_ncm_idx, minus.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_best, 0, n, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "initial state upload");
+    e = launch_init(p.kind, n, h->d_rp, h->d_adj, R, p.seed, 0, 0, h->d_ctl, h->W, h->d_spins[0],
+                    h->d_E[0], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "initial population");
+    h->launches += 2;
+    // host copies of the host-side vectors must stay alive until the copies ran
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "init");
+    h->cfg = choose_cfg(p.kind, n, R, h->H);
+    h->host_t = 0;
+    h->sched_end = 0;
+    h->initialized = 1;
+    return PAMC_OK;
+}
+
+pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_step before pamc_init");
+    if (nsteps < 0) return fail(h, PAMC_ERR_ARG, "nsteps < 0");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    const pamc_params &p = h->p;
+    const int32_t n = h->n;
+    for (int32_t i = 0; i < nsteps; ++i) {
+        const int64_t t = h->host_t;
+        if (t > INT32_MAX - 2) return fail(h, PAMC_ERR_RANGE, "step counter overflow");
+        if (p.sweeps > 0 && t >= h->sched_end) {
+            launch_schedule(n, h->d_rp, h->d_adj, p.seed, (int32_t)t, kSchedSlots, p.sweeps, 0,
+                            kSchedSlots, h->d_order, h->d_lvl, h->d_nlev, h->d_skey, h->d_scnt,
+                            h->stream);
+            h->sched_end = t + kSchedSlots;
+            h->launches += 1;
+        }
+        int8_t *src = h->d_spins[t & 1], *dst = h->d_spins[(t + 1) & 1];
+        int64_t *Es = h->d_E[t & 1], *Ed = h->d_E[(t + 1) & 1];
+        e = launch_prep(p, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->stream);
+        if (e == cudaSuccess) e = launch_tables(p.kind, p.rule, h->H, h->d_ctl, h->d_tab, h->stream);
+        h->launches += 2;
+        if (e == cudaSuccess && p.stagnation && p.kind == 0) {
+            e = launch_ncm(n, h->d_rp, h->d_adj, p, src, Es, h->d_parent, h->d_targets, h->d_ncm_buf,
+                           h->d_nkey, h->d_nstat, h->d_ctl, h->stream);
+            h->launches += 1;
+        }
+        SchedView sv{h->d_order, h->d_lvl, h->d_nlev};
+        if (e == cudaSuccess)
+            e = launch_sweep(p.kind, p.rule, n, h->d_rp, h->d_adj, h->H, p, (int32_t)t,
+                             (int32_t)(t % kSchedSlots), sv, h->d_tab, src, h->d_parent,
+                             h->d_ncm_buf, h->d_ncm_idx, dst, Ed, h->d_ctl, h->cfg, h->W, h->stream);
+        if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
+        h->launches += 2;
+        if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
+            e = launch_init(p.kind, n, h->d_rp, h->d_adj, p.R, p.seed, (int32_t)(t + 1), 1, h->d_ctl,
+                            h->W, dst, Ed, h->stream);
+            h->launches += 2;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+        h->host_t = t + 1;
+    }
+    return PAMC_OK;
+}
+
+pamc_status pamc_sync(pamc_handle h) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream synchronize");
+    if (h->initialized) {
+        int32_t err = 0;
+        e = cudaMemcpy(&err, (const char *)h->d_ctl + offsetof(DevCtl, err), sizeof(err),
+                       cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "error flag readback");
+        if (err != 0) return fail(h, (pamc_status)err, "device reported error %d", err);
+    }
+    return PAMC_OK;
+}
+
+pamc_status pamc_run(pamc_handle h, const pamc_params *p) {
+    pamc_status s = pamc_init(h, p);
+    if (s != PAMC_OK) return s;
+    s = pamc_step(h, p->steps);
+    if (s != PAMC_OK) return s;
+    return pamc_sync(h);
+}
+
+static pamc_status read_ctl(pamc_handle h, DevCtl &c) {
+    pamc_status s = pamc_sync(h);
+    if (s != PAMC_OK) return s;
+    cudaError_t e = cudaMemcpy(&c, h->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "controller readback");
+    return PAMC_OK;
+}
+
+pamc_status pamc_best(pamc_handle h, int64_t *cut, int8_t *spins) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_best before pamc_init");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    if (cut) *cut = c.mstar;
+    if (spins) {
+        std::vector<int8_t> b(h->n);
+        cudaError_t e = cudaMemcpy(b.data(), h->d_best, h->n, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "best readback");
+        if (h->p.kind == 0) {
+            const int8_t f = b[0] < 0 ? -1 : 1;   // canonical: spin 0 is +1
+            for (int32_t i = 0; i < h->n; ++i) spins[i] = (int8_t)(b[i] * f);
+        } else {
+            int8_t map[4] = {-1, -1, -1, -1}, next = 0;   // labels in order of first use
+            for (int32_t i = 0; i < h->n; ++i) {
+                const int8_t v = b[i] & 3;
+                if (map[v] < 0) map[v] = next++;
+                spins[i] = map[v];
+            }
+        }
+    }
+    return PAMC_OK;
+}
+
+pamc_status pamc_state(pamc_handle h, int8_t *spins, int64_t *E, int32_t *parents, int32_t *counts) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_state before pamc_init");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    const int cur = c.t & 1;
+    const size_t R = (size_t)h->p.R;
+    cudaError_t e = cudaSuccess;
+    if (spins) e = cudaMemcpy(spins, h->d_spins[cur], R * h->n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && E) e = cudaMemcpy(E, h->d_E[cur], R * sizeof(int64_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && parents)
+        e = cudaMemcpy(parents, h->d_parent, R * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && counts)
+        e = cudaMemcpy(counts, h->d_count, R * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "state readback");
+    return PAMC_OK;
+}
+
+pamc_status pamc_control_state(pamc_handle h, int64_t *iv, double *dv) {
+    if (!h || !iv || !dv) return fail(h, PAMC_ERR_ARG, "null argument");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_control_state before pamc_init");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    iv[0] = c.t; iv[1] = c.z; iv[2] = c.cycle; iv[3] = c.cooldown; iv[4] = c.enable_cm;
+    iv[5] = c.done; iv[6] = c.ncm_last; iv[7] = c.hist_len; iv[8] = c.ncm_flipped;
+    iv[9] = c.ncm_dE_max;
+    dv[0] = c.beta; dv[1] = c.delta;
+    return PAMC_OK;
+}
+
+int64_t pamc_launch_count(pamc_handle h) { return h ? h->launches : 0; }
+
+int64_t pamc_weight_sum(pamc_handle h) { return h ? h->W : 0; }
+
+pamc_status pamc_last_error(pamc_handle h, char *buf, size_t len) {
+    if (!buf || len == 0) return PAMC_ERR_ARG;
+    snprintf(buf, len, "%s", h ? h->err : g_create_err);
+    return PAMC_OK;
+}
+
+void pamc_destroy(pamc_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    release_run(h);
+    dev_free_all(h, h->inst_bufs);
+    delete h;
+}
+
+}  // extern "C"

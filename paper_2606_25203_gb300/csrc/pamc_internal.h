@@ -1,0 +1,70 @@
+// pamc_internal.h -- device data layout and kernel entry points of libpamc.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "../../include/pamc.h"
+
+namespace pamc {
+
+constexpr int kHistMax = 64;   // longest stagnation window supported
+
+// Algorithm 1's controller state, resident in device memory so that a whole
+// iteration (resample, NCM, sweeps, M*, control) runs without the host.
+struct DevCtl {
+    int32_t t;            // global iteration index (keys the random streams)
+    int32_t z, cycle, cooldown, enable_cm, done;
+    int32_t ncm_last;     // NCM applied in the last iteration
+    int32_t hist_len;
+    int32_t resampled;    // the current iteration resampled (z > 1)
+    int32_t ncm_active;   // the current iteration applies NCM
+    int32_t restart;      // the last iteration restarted (reinit pending)
+    int32_t err;          // device-side error code (pamc_status), 0 = none
+    int32_t best_replica; // replica holding M* when it was last improved
+    int32_t pad_;
+    double beta, delta, dbeta;
+    int64_t mstar;        // best cut so far (INT64_MIN = none yet)
+    int64_t ncm_flipped, ncm_dE_max;
+    int64_t hist[kHistMax];
+};
+
+// Per-(t, sweep) update schedule: the random order's dependency levels.
+// order[] lists the vertices level by level; lvl_ptr[l]..lvl_ptr[l+1] is
+// level l.  No two vertices of one level are coupled, and every coupled
+// pair is ordered exactly as in the random permutation.
+struct SchedView {
+    const int32_t *order;    // [slots][S][n]
+    const int32_t *lvl_ptr;  // [slots][S][n+1]
+    const int32_t *nlev;     // [slots][S]
+};
+
+// Launch configuration of the sparse sweep kernel.
+struct SweepCfg {
+    int groups_per_cta;   // replica groups in one CTA
+    int warps_per_group;  // warps cooperating on one group's level
+};
+
+void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t seed, int32_t t0,
+                     int32_t nt, int32_t S, int32_t slot0, int32_t slots, int32_t *order,
+                     int32_t *lvl_ptr, int32_t *nlev, uint32_t *skey, int32_t *scnt,
+                     cudaStream_t st);
+
+size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg);
+
+cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const uint32_t *adj,
+                         int32_t H, const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
+                         const uint64_t *tab, const int8_t *src, const int32_t *parent,
+                         const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst,
+                         int64_t *E_dst, const DevCtl *ctl, SweepCfg cfg, int64_t Wsum,
+                         cudaStream_t st);
+
+// Random (re)initialisation of the population with key t, and its energies;
+// when only_if_restart is set the kernels do nothing unless the controller
+// has just restarted the schedule.
+cudaError_t launch_init(int kind, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
+                        uint64_t seed, int32_t t, int only_if_restart, const DevCtl *ctl,
+                        int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st);
+
+}  // namespace pamc

@@ -1,0 +1,449 @@
+// population.cu -- the population step and the controller of Algorithm 1:
+//   k_tables   acceptance thresholds for the current beta (Eq. 4, Metropolis,
+//              Suppl. S3), in binary64 with the deterministic exp;
+//   k_prep     Boltzmann reweighting and resampling (Eq. 1-2) as systematic
+//              resampling over an integer prefix scan of 64-bit fixed-point
+//              weights, and selection of the NCM targets;
+//   k_ncm      the energy-preserving non-local cluster move (Sec. II.C):
+//              randomised greedy maximal independent sets of iso-sites;
+//   k_control  M* / best configuration, the recent-progress history, the
+//              adaptive temperature rule (Sec. II.C) and the restart.
+// All state lives on the device so that an iteration never waits for the host.
+#include "pamc_device.cuh"
+#include "pamc_internal.h"
+
+namespace pamc {
+
+namespace {
+
+// ---------------------------------------------------------------- tables
+__global__ void k_tables(int kind, int rule, int32_t H, const DevCtl *__restrict__ ctl,
+                         uint64_t *__restrict__ tab) {
+    if (ctl->done) return;
+    const double beta = ctl->beta;
+    if (kind == 0) {
+        const int32_t n = 2 * H + 1;
+        for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const int32_t v = i - H;   // h (heat-bath) or s*h (Metropolis, dE = 2 s h)
+            tab[i] = rule == 0 ? thr_heatbath(beta, v) : thr_metropolis(beta, 2 * (int64_t)v);
+        }
+        return;
+    }
+    // Potts: T1 over (a, b) in [-2H, 2H]^2, then T2 over c in [-2H, 2H]
+    extern __shared__ double e_s[];
+    const int32_t W1 = 4 * H + 1;
+    for (int32_t i = threadIdx.x; i < W1; i += blockDim.x)
+        e_s[i] = det_exp(__dmul_rn(beta, (double)(i - 2 * H)));
+    __syncthreads();
+    const int32_t total = W1 * W1 + W1;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        if (i < W1 * W1) {
+            const int32_t ia = i / W1, ib = i % W1;
+            tab[i] = thr_potts_b1_from(e_s[ia], e_s[ib]);
+        } else {
+            const int32_t c = i - W1 * W1;
+            tab[i] = thr_potts_b2(beta, (int64_t)(c - 2 * H));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- block helpers
+template <typename T, typename Op>
+__device__ T block_reduce(T v, Op op, T *sbuf) {
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sbuf[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T a = sbuf[0];
+        for (int i = 1; i < (int)(blockDim.x >> 5); ++i) a = op(a, sbuf[i]);
+        sbuf[0] = a;
+    }
+    __syncthreads();
+    const T r = sbuf[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------- resampling
+constexpr int kPrepThreads = 1024;
+
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau, uint32_t key0,
+       uint32_t key1, const int64_t *__restrict__ E_src, DevCtl *__restrict__ ctl,
+       int32_t *__restrict__ parent, int32_t *__restrict__ count, int32_t *__restrict__ ncm_idx,
+       int32_t *__restrict__ targets) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint64_t *C = reinterpret_cast<uint64_t *>(sm);             // R prefix sums
+    int32_t *cnt = reinterpret_cast<int32_t *>(sm + (size_t)R * 8);
+    __shared__ long long red_ll[32];
+    __shared__ unsigned long long red_u[32];
+    if (ctl->done) return;
+    const int32_t z = ctl->z;
+    const int32_t t = ctl->t;
+    const double delta = ctl->delta;
+    const bool resampled = z > 1 && do_resample;
+    const bool ncm = z > 1 && ctl->enable_cm && ctl->cooldown == 0;
+    __syncthreads();
+
+    for (int32_t m = threadIdx.x; m < R; m += blockDim.x) { cnt[m] = 0; ncm_idx[m] = -1; }
+    __syncthreads();
+    if (resampled) {
+        // shift by the extreme energy: the reference replica has weight 1
+        long long lmin = LLONG_MAX, lmax = LLONG_MIN;
+        for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
+            lmin = min(lmin, (long long)E_src[r]);
+            lmax = max(lmax, (long long)E_src[r]);
+        }
+        const long long emin = block_reduce(lmin, [](long long a, long long b) { return a < b ? a : b; }, red_ll);
+        const long long emax = block_reduce(lmax, [](long long a, long long b) { return a > b ? a : b; }, red_ll);
+        int lg = 0;
+        while ((1ll << lg) < (long long)R) ++lg;
+        const int S = 62 - lg;
+        const double a = __dmul_rn(fabs(delta), kind == 1 ? 0.5 : 1.0);
+        // contiguous chunk per thread for the scan
+        const int32_t per = (R + blockDim.x - 1) / blockDim.x;
+        const int32_t lo = min(R, (int32_t)threadIdx.x * per), hi = min(R, lo + per);
+        unsigned long long local = 0;
+        for (int32_t r = lo; r < hi; ++r) {
+            long long d = 0;
+            if (delta > 0) d = (long long)E_src[r] - emin;
+            else if (delta < 0) d = emax - (long long)E_src[r];
+            const double w = det_exp(-__dmul_rn(a, (double)d));
+            const uint64_t q = (uint64_t)floor(ldexp(w, S));
+            local += q;
+            C[r] = local;   // chunk-local inclusive prefix
+        }
+        // exclusive scan of the chunk totals across the block
+        unsigned long long x = local;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) red_u[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long v = lane < (int)(blockDim.x >> 5) ? red_u[lane] : 0ull;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            red_u[lane] = v;   // inclusive warp totals
+        }
+        __syncthreads();
+        const unsigned long long excl = (x - local) + (wid > 0 ? red_u[wid - 1] : 0ull);
+        for (int32_t r = lo; r < hi; ++r) C[r] += excl;
+        __syncthreads();
+        const uint64_t T = C[R - 1];
+        const u32x4 u = philox(0u, 0u, (uint32_t)t, kTagResample << 24, key0, key1);
+        const uint64_t v = ((uint64_t)u.y << 32) | (uint64_t)u.x;
+        const uint64_t U = __umul64hi(v, T);
+        for (int32_t m = threadIdx.x; m < R; m += blockDim.x) {
+            const unsigned __int128 pos = (unsigned __int128)m * T + U;
+            int32_t lo2 = 0, hi2 = R - 1;   // smallest j with R*C_j > pos
+            while (lo2 < hi2) {
+                const int32_t mid = (lo2 + hi2) >> 1;
+                if ((unsigned __int128)R * C[mid] > pos) hi2 = mid;
+                else lo2 = mid + 1;
+            }
+            parent[m] = lo2;
+            atomicAdd(&cnt[lo2], 1);
+        }
+    } else {
+        for (int32_t m = threadIdx.x; m < R; m += blockDim.x) { parent[m] = m; cnt[m] = 1; }
+    }
+    __syncthreads();
+    for (int32_t m = threadIdx.x; m < R; m += blockDim.x) count[m] = cnt[m];
+
+    if (ncm && kind == 0) {
+        // targets: the n_top slots with the lowest (energy, slot index)
+        const int32_t ntop = min(n_top, R);
+        for (int32_t m = threadIdx.x; m < R; m += blockDim.x)
+            reinterpret_cast<int64_t *>(C)[m] = E_src[parent[m]];
+        __syncthreads();
+        const int64_t *Ep = reinterpret_cast<const int64_t *>(C);
+        for (int32_t m = threadIdx.x; m < R; m += blockDim.x) {
+            const int64_t em = Ep[m];
+            int32_t rank = 0;
+            for (int32_t j = 0; j < R; ++j) {
+                const int64_t ej = Ep[j];
+                rank += (ej < em || (ej == em && j < m)) ? 1 : 0;
+            }
+            if (rank < ntop) { targets[rank] = m; ncm_idx[m] = rank; }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->resampled = resampled ? 1 : 0;
+        ctl->ncm_active = ncm ? 1 : 0;
+        ctl->ncm_last = ncm ? 1 : 0;
+        if (ncm) { ctl->enable_cm = 0; ctl->cooldown = tau; }
+    }
+}
+
+// ---------------------------------------------------------------- NCM
+constexpr int kNcmThreads = 512;
+
+__device__ __forceinline__ bool nbefore(uint32_t ka, int32_t a, uint32_t kb, int32_t b) {
+    return ka < kb || (ka == kb && a < b);
+}
+
+// One randomised greedy MIS over the iso-sites (stat 0 = candidate,
+// 3 = not a candidate).  Decided in rounds: a candidate is taken (1) once
+// every coupled candidate earlier in the trial's random order is rejected,
+// and rejected (2) once one of them is taken -- the same set the sequential
+// greedy scan in that order builds.  Returns the size of the set.
+__device__ int32_t mis_trial(int32_t n, const int32_t *rp, const uint32_t *adj, uint8_t *stat,
+                             uint32_t *key, int32_t a, int32_t t, int32_t m, uint32_t key0,
+                             uint32_t key1, DevCtl *ctl, int *s_flag, int *s_red) {
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        if (stat[k] != 3) {
+            stat[k] = 0;
+            key[k] = philox((uint32_t)k, (uint32_t)a, (uint32_t)t, (kTagNcm << 24) | (uint32_t)m, key0, key1).x;
+        }
+    }
+    __syncthreads();
+    for (int32_t round = 0; round <= n + 1; ++round) {
+        if (threadIdx.x == 0) *s_flag = 0;
+        __syncthreads();
+        for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+            if (stat[k] != 0) continue;
+            const uint32_t kk = key[k];
+            bool any_in = false, all_out = true;
+            for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+                const uint32_t w = adj[e];
+                if ((w >> 24) == 0) continue;   // zero coupling
+                const int32_t j = (int32_t)(w & 0xFFFFFFu);
+                const uint8_t sj = *(volatile uint8_t *)&stat[j];
+                if (sj == 3 || !nbefore(key[j], j, kk, k)) continue;
+                if (sj == 1) any_in = true;
+                else if (sj == 0) all_out = false;
+            }
+            if (any_in) stat[k] = 2;
+            else if (all_out) stat[k] = 1;
+            else *s_flag = 1;
+        }
+        __syncthreads();
+        const int more = *s_flag;
+        __syncthreads();
+        if (!more) break;
+        if (round == n + 1 && threadIdx.x == 0) atomicExch(&ctl->err, (int)PAMC_ERR_TIMEOUT);
+    }
+    int32_t c = 0;
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) c += stat[k] == 1 ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (threadIdx.x == 0) *s_red = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicAdd(s_red, c);
+    __syncthreads();
+    const int32_t tot = *s_red;
+    __syncthreads();
+    return tot;
+}
+
+__global__ void __launch_bounds__(kNcmThreads)
+k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj, int32_t R,
+      int32_t kind, int32_t n_top, int32_t trials, uint32_t key0, uint32_t key1,
+      const int8_t *__restrict__ src, const int64_t *__restrict__ E_src,
+      const int32_t *__restrict__ parent, const int32_t *__restrict__ targets,
+      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, uint8_t *__restrict__ nstat,
+      DevCtl *__restrict__ ctl) {
+    __shared__ int s_flag, s_red;
+    __shared__ long long s_e[32];
+    if (ctl->done || !ctl->ncm_active || kind != 0) return;
+    const int32_t q = blockIdx.x;
+    if (q >= min(n_top, R)) return;
+    const int32_t t = ctl->t;
+    const int32_t m = targets[q];
+    const int8_t *row = src + (size_t)parent[m] * n;
+    int8_t *sp = ncm_buf + (size_t)q * n;
+    uint32_t *key = nkey + (size_t)q * n;
+    uint8_t *stat = nstat + (size_t)q * n;
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) sp[k] = row[k];
+    __syncthreads();
+    // iso-sites: h_k = 0, so flipping k alone leaves the energy unchanged
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        int32_t h = 0;
+        for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+            const uint32_t w = adj[e];
+            h += ((int32_t)w >> 24) * sp[w & 0xFFFFFFu];
+        }
+        stat[k] = h == 0 ? 0 : 3;
+    }
+    __syncthreads();
+    int32_t best = -1, besta = 0;
+    for (int32_t a = 0; a < trials; ++a) {
+        const int32_t sz = mis_trial(n, rp, adj, stat, key, a, t, m, key0, key1, ctl, &s_flag, &s_red);
+        if (sz > best) { best = sz; besta = a; }   // ties keep the earliest trial
+    }
+    if (trials <= 0) best = 0;
+    if (best > 0) {
+        mis_trial(n, rp, adj, stat, key, besta, t, m, key0, key1, ctl, &s_flag, &s_red);
+        for (int32_t k = threadIdx.x; k < n; k += blockDim.x)
+            if (stat[k] == 1) sp[k] = (int8_t)-sp[k];
+    }
+    __syncthreads();
+    // energy check: the move must not change E = -1/2 sum_k s_k h_k
+    long long acc = 0;
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        long long h = 0;
+        for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+            const uint32_t w = adj[e];
+            h += (long long)((int32_t)w >> 24) * sp[w & 0xFFFFFFu];
+        }
+        acc += (long long)sp[k] * h;
+    }
+    const long long tot = block_reduce(acc, [](long long x, long long y) { return x + y; }, s_e);
+    if (threadIdx.x == 0) {
+        long long d = -(tot / 2) - (long long)E_src[parent[m]];
+        if (d < 0) d = -d;
+        atomicMax((unsigned long long *)&ctl->ncm_dE_max, (unsigned long long)d);
+        atomicAdd((unsigned long long *)&ctl->ncm_flipped, (unsigned long long)(best > 0 ? best : 0));
+    }
+}
+
+// ---------------------------------------------------------------- controller
+constexpr int kCtlThreads = 1024;
+
+__device__ int32_t distinct_last(const int64_t *h, int32_t len, int32_t w) {
+    if (w > len) w = len;
+    int32_t d = 0;
+    for (int32_t i = len - w; i < len; ++i) {
+        bool seen = false;
+        for (int32_t q = len - w; q < i; ++q)
+            if (h[q] == h[i]) { seen = true; break; }
+        if (!seen) ++d;
+    }
+    return d;
+}
+
+__global__ void __launch_bounds__(kCtlThreads)
+k_control(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst, int32_t win_short,
+          int32_t win_long, int32_t max_ds, int32_t max_dl, double reheat, double beta0,
+          int64_t target, const int64_t *__restrict__ E, const int8_t *__restrict__ spins,
+          int8_t *__restrict__ best, DevCtl *__restrict__ ctl) {
+    __shared__ long long s_e[32];
+    __shared__ int s_i[32];
+    __shared__ int s_improved, s_rb;
+    if (ctl->done) return;
+    // argmin of (E, index): the replica with the largest cut, lowest index on ties
+    long long be = LLONG_MAX;
+    int bi = 0x7fffffff;
+    for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
+        const long long e = E[r];
+        if (e < be || (e == be && r < bi)) { be = e; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long e2 = __shfl_down_sync(0xffffffffu, be, o);
+        const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+        if (e2 < be || (e2 == be && i2 < bi)) { be = e2; bi = i2; }
+    }
+    if ((threadIdx.x & 31) == 0) { s_e[threadIdx.x >> 5] = be; s_i[threadIdx.x >> 5] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (s_e[w] < be || (s_e[w] == be && s_i[w] < bi)) { be = s_e[w]; bi = s_i[w]; }
+        const long long cut = (W - be) / 2;
+        s_improved = cut > ctl->mstar;
+        s_rb = bi;
+        if (s_improved) { ctl->mstar = cut; ctl->best_replica = bi; }
+    }
+    __syncthreads();
+    if (s_improved) {
+        const int8_t *row = spins + (size_t)s_rb * n;
+        for (int32_t k = threadIdx.x; k < n; k += blockDim.x) best[k] = row[k];
+    }
+    if (threadIdx.x != 0) return;
+    DevCtl &c = *ctl;
+    int32_t hl = win_long > win_short ? win_long : win_short;
+    if (hl > kHistMax) hl = kHistMax;
+    if (hl > 0) {
+        if (c.hist_len == hl) {
+            for (int32_t i = 0; i + 1 < hl; ++i) c.hist[i] = c.hist[i + 1];
+            c.hist_len = hl - 1;
+        }
+        c.hist[c.hist_len++] = c.mstar;
+    }
+    if (stagnation && c.cooldown == 0 && hl > 0 && c.hist_len >= hl) {
+        const int32_t ds = distinct_last(c.hist, c.hist_len, win_short);
+        const int32_t dl = distinct_last(c.hist, c.hist_len, win_long);
+        if (ds <= max_ds && dl <= max_dl) {
+            c.beta = __dmul_rn(reheat, c.beta);
+            c.delta = c.dbeta;
+            c.enable_cm = 1;
+        } else if (ds <= max_ds) {
+            if (c.beta > beta0) c.delta = -c.dbeta;
+        } else {
+            c.delta = c.dbeta;
+        }
+    }
+    c.restart = 0;
+    if (z_rst > 0 && c.z >= z_rst) {
+        c.cycle += 1;
+        c.z = 1;
+        c.beta = beta0;
+        c.delta = c.dbeta;
+        c.enable_cm = 0;
+        c.cooldown = 0;
+        c.hist_len = 0;
+        c.restart = 1;
+    } else {
+        c.z += 1;
+        c.beta = __dadd_rn(c.beta, c.delta);
+        if (c.cooldown > 0) c.cooldown -= 1;
+    }
+    c.t += 1;
+    if (target >= 0 && c.mstar >= target) c.done = 1;
+}
+
+}  // namespace
+
+cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint64_t *tab,
+                          cudaStream_t st) {
+    if (kind == 0) {
+        k_tables<<<1, 256, 0, st>>>(kind, rule, H, ctl, tab);
+    } else {
+        const int32_t W1 = 4 * H + 1;
+        int grid = (W1 * W1 + W1 + 255) / 256;
+        if (grid > 304) grid = 304;
+        k_tables<<<grid, 256, (size_t)W1 * sizeof(double), st>>>(kind, rule, H, ctl, tab);
+    }
+    return cudaGetLastError();
+}
+
+size_t prep_smem_bytes(int32_t R) { return (size_t)R * 8 + (size_t)R * 4; }
+
+cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
+                        int32_t *count, int32_t *ncm_idx, int32_t *targets, cudaStream_t st) {
+    const size_t smem = prep_smem_bytes(p.R);
+    cudaError_t err = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_prep<<<1, kPrepThreads, smem, st>>>(p.R, p.kind, p.resample, p.n_top, p.cooldown_tau,
+                                          (uint32_t)p.seed, (uint32_t)(p.seed >> 32), E_src, ctl,
+                                          parent, count, ncm_idx, targets);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
+                       const int8_t *src, const int64_t *E_src, const int32_t *parent,
+                       const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey, uint8_t *nstat,
+                       DevCtl *ctl, cudaStream_t st) {
+    const int32_t ntop = p.n_top < p.R ? p.n_top : p.R;
+    if (ntop <= 0 || p.kind != 0 || !p.stagnation) return cudaSuccess;
+    k_ncm<<<ntop, kNcmThreads, 0, st>>>(n, rp, adj, p.R, p.kind, p.n_top, p.mis_trials,
+                                        (uint32_t)p.seed, (uint32_t)(p.seed >> 32), src, E_src,
+                                        parent, targets, ncm_buf, nkey, nstat, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_control(int32_t n, int64_t W, const pamc_params &p, const int64_t *E,
+                           const int8_t *spins, int8_t *best, DevCtl *ctl, cudaStream_t st) {
+    k_control<<<1, kCtlThreads, 0, st>>>(n, W, p.R, p.stagnation, p.z_rst, p.win_short, p.win_long,
+                                         p.max_distinct_short, p.max_distinct_long, p.reheat_factor,
+                                         p.beta0, p.target_cut, E, spins, best, ctl);
+    return cudaGetLastError();
+}
+
+}  // namespace pamc

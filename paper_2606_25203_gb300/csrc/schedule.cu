@@ -1,0 +1,97 @@
+// schedule.cu -- the shared random sweep order of Sec. II.A ("all spins were
+// sequentially updated once in a randomized order"), turned into dependency
+// levels for a parallel sweep with exactly sequential semantics.
+//
+// The order of (t, sweep) sorts the vertices by the 32-bit key
+// Philox(k, sweep, t, PERM<<24)[0], ties by index.  Only the relative order of
+// coupled vertices matters for a sequential single-spin sweep: the decision at
+// vertex k reads the fields of k, which only its neighbours change.  So vertex
+// k is placed at level 1 + max(level of neighbours that come before k), and
+// all vertices of one level (pairwise uncoupled) can be updated at once,
+// level after level, giving bit-identical results to the sequential order.
+// Levels are produced by Kahn's algorithm, frontier by frontier; no sort is
+// needed.  One CTA builds one (t, sweep) schedule; a launch builds the
+// schedules of several steps at once.
+#include "pamc_device.cuh"
+#include "pamc_internal.h"
+
+namespace pamc {
+
+namespace {
+
+__device__ __forceinline__ bool before(uint32_t ka, int32_t a, uint32_t kb, int32_t b) {
+    return ka < kb || (ka == kb && a < b);
+}
+
+constexpr int kSchedThreads = 512;
+
+__global__ void __launch_bounds__(kSchedThreads)
+k_schedule(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
+           uint32_t key0, uint32_t key1, int32_t t0, int32_t S, int32_t slots,
+           int32_t *__restrict__ order, int32_t *__restrict__ lvl_ptr, int32_t *__restrict__ nlev,
+           uint32_t *__restrict__ skey, int32_t *__restrict__ scnt) {
+    const int b = blockIdx.x;
+    const int ti = b / S, sw = b % S;
+    const int32_t t = t0 + ti;
+    const int slot = t % slots;
+    const size_t base = (size_t)slot * S + sw;
+    int32_t *ord = order + base * (size_t)n;
+    int32_t *lp = lvl_ptr + base * (size_t)(n + 1);
+    uint32_t *key = skey + (size_t)b * n;
+    int32_t *cnt = scnt + (size_t)b * n;
+    __shared__ int32_t s_tail;
+    __shared__ int32_t s_end;
+
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x)
+        key[k] = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, kTagPerm << 24, key0, key1).x;
+    if (threadIdx.x == 0) s_tail = 0;
+    __syncthreads();
+
+    // number of coupled predecessors; sources form level 0
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const uint32_t kk = key[k];
+        int32_t c = 0;
+        for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+            const int32_t j = (int32_t)(adj[e] & 0xFFFFFFu);
+            c += before(key[j], j, kk, k) ? 1 : 0;
+        }
+        cnt[k] = c;
+        if (c == 0) ord[atomicAdd(&s_tail, 1)] = k;
+    }
+    __syncthreads();
+    int32_t beg = 0, end = s_tail;
+    int32_t L = 0;
+    if (threadIdx.x == 0) lp[0] = 0;
+    while (beg < end) {
+        if (threadIdx.x == 0) lp[L + 1] = end;
+        for (int32_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+            const int32_t k = ord[i];
+            const uint32_t kk = key[k];
+            for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+                const int32_t j = (int32_t)(adj[e] & 0xFFFFFFu);
+                if (before(kk, k, key[j], j) && atomicSub(&cnt[j], 1) == 1)
+                    ord[atomicAdd(&s_tail, 1)] = j;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_end = s_tail;
+        __syncthreads();
+        beg = end;
+        end = s_end;
+        ++L;
+    }
+    if (threadIdx.x == 0) nlev[base] = L;
+}
+
+}  // namespace
+
+void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t seed, int32_t t0,
+                     int32_t nt, int32_t S, int32_t /*slot0*/, int32_t slots, int32_t *order,
+                     int32_t *lvl_ptr, int32_t *nlev, uint32_t *skey, int32_t *scnt,
+                     cudaStream_t st) {
+    if (nt <= 0 || S <= 0) return;
+    k_schedule<<<nt * S, kSchedThreads, 0, st>>>(n, rp, adj, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                                  t0, S, slots, order, lvl_ptr, nlev, skey, scnt);
+}
+
+}  // namespace pamc

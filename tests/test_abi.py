@@ -1,0 +1,80 @@
+"""The C-ABI library loads and exports every entry point include/pamc.h
+declares, and rejects malformed instances on the host before any CUDA call
+(no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2606_25203_gb300 as pg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(pamc_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return pg.load(torch_allocator=False)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 14
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def _create(lib, rp, col, w):
+    h = ctypes.c_void_p()
+    rp = np.ascontiguousarray(rp, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    rc = lib.pamc_create_csr(len(rp) - 1, rp.ctypes.data_as(ctypes.c_void_p),
+                             col.ctypes.data_as(ctypes.c_void_p), w.ctypes.data_as(ctypes.c_void_p),
+                             0, None, ctypes.byref(h))
+    return rc, h
+
+
+def test_host_validation_errors(lib):
+    # asymmetric weight
+    assert _create(lib, [0, 1, 2], [1, 0], [1, 2])[0] == 2
+    # missing reverse edge
+    assert _create(lib, [0, 1, 1], [1], [1])[0] == 2
+    # self loop
+    assert _create(lib, [0, 1], [0], [1])[0] == 3
+    # weight out of range
+    assert _create(lib, [0, 1, 2], [1, 0], [200, 200])[0] == 4
+    # field range: a vertex with 130 unit edges
+    n = 131
+    ei = np.zeros(130, dtype=np.int64)
+    ej = np.arange(1, 131)
+    import workloads as W
+    star = W.csr_from_edges(n, ei, ej, np.ones(130, dtype=np.int64), "star")
+    assert _create(lib, star.row_ptr, star.col, star.w)[0] == 4
+    # bad row_ptr
+    assert _create(lib, [1, 1], [], [])[0] == 1
+    assert _create(lib, [0, 2, 1], [1, 0], [1, 1])[0] == 1
+    # column out of range
+    assert _create(lib, [0, 1, 2], [5, 0], [1, 1])[0] == 1
+    buf = ctypes.create_string_buffer(256)
+    lib.pamc_last_error(None, buf, 256)
+    assert b"column" in buf.value
+
+
+def test_null_arguments(lib):
+    assert lib.pamc_create_csr(4, None, None, None, 0, None, None) == 1
+    assert lib.pamc_init(None, None) == 1
+    assert lib.pamc_step(None, 1) == 1
+    assert lib.pamc_launch_count(None) == 0

@@ -1,0 +1,168 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every comparison is exact: spins, energies, parents, copy counts, the best cut
+and configuration, and the controller state (t, z, cycle, cooldown, flags,
+beta and Delta bit for bit) after every iteration.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CTL_EXACT = ("t", "z", "cycle", "cooldown", "enable_cm", "done", "ncm_last", "hist_len",
+             "ncm_flipped", "ncm_dE_max")
+
+
+@pytest.fixture(scope="module")
+def pg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_25203_gb300 as pg
+    pg.load()
+    return pg
+
+
+def compare_run(pg, inst, steps, check_every=1, **params):
+    ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, steps=steps, **params)
+    s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+    s.init(steps=steps, **params)
+    assert pg.pamc_weight_sum(s.h) == ref.weight_sum()
+    done = 0
+    while done < steps:
+        k = min(check_every, steps - done)
+        s.step(k)
+        ref.step(k)
+        done += k
+        spins, E, par, cnt = s.state()
+        where = f"after {done} steps"
+        np.testing.assert_array_equal(spins, ref.spins(), err_msg=f"spins {where}")
+        np.testing.assert_array_equal(E, ref.energy(), err_msg=f"energies {where}")
+        rp, rc = ref.parents()
+        np.testing.assert_array_equal(par, rp, err_msg=f"parents {where}")
+        np.testing.assert_array_equal(cnt, rc, err_msg=f"counts {where}")
+        gc, oc = s.control(), ref.ctl()
+        for key in CTL_EXACT:
+            assert gc[key] == oc[key], f"{key} {where}: {gc[key]} != {oc[key]}"
+        assert gc["beta"] == oc["beta"] and gc["delta"] == oc["delta"], where
+        m, b = s.best()
+        rm, rb = ref.best()
+        assert m == rm, f"M* {where}"
+        np.testing.assert_array_equal(b, rb, err_msg=f"best spins {where}")
+    launches = s.launches()
+    s.close()
+    return ref, launches
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_conventional_pamc_er(pg, rule):
+    inst = W.erdos_renyi(150, 0.08, signed=False, seed=3)
+    compare_run(pg, inst, 12, R=20, sweeps=3, beta0=0.1, beta1=3.0, rule=rule, seed=7)
+
+
+def test_signed_sparse_ragged_population(pg):
+    # R not a multiple of the replica group, n not a multiple of 16
+    inst = W.gnm(333, 900, signed=True, seed=2)
+    compare_run(pg, inst, 10, R=13, sweeps=2, beta0=0.2, beta1=2.5, seed=11)
+
+
+def test_potts_max3cut(pg):
+    inst = W.gnm(300, 1800, signed=False, seed=4)
+    compare_run(pg, inst, 12, kind=1, R=10, sweeps=2, beta0=0.1, beta1=3.0, seed=5)
+
+
+def test_potts_signed(pg):
+    inst = W.erdos_renyi(120, 0.1, signed=True, seed=9)
+    compare_run(pg, inst, 8, kind=1, R=7, sweeps=3, beta0=0.3, beta1=2.0, seed=2)
+
+
+def test_augmented_pamc_with_ncm_and_restart(pg):
+    inst = W.torus(16, 16, signed=True, seed=2)
+    ref, _ = compare_run(pg, inst, 150, R=32, sweeps=2, beta0=0.5, beta1=6.0, stagnation=1,
+                         z_rst=120, cooldown_tau=5, seed=3)
+    st = ref.ctl()
+    assert st["ncm_flipped"] > 0 and st["cycle"] == 1
+
+
+def test_augmented_potts_controller(pg):
+    inst = W.gnm(200, 1000, signed=False, seed=8)
+    compare_run(pg, inst, 90, kind=1, R=16, sweeps=1, beta0=0.5, beta1=5.0, stagnation=1,
+                z_rst=70, cooldown_tau=4, seed=4)
+
+
+def test_independent_chains_baseline(pg):
+    inst = W.gnm(400, 1100, signed=True, seed=6)
+    compare_run(pg, inst, 6, R=9, sweeps=2, resample=0, seed=1)
+
+
+def test_target_cut_terminates(pg):
+    inst = W.erdos_renyi(16, 0.4, signed=False, seed=0)
+    ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=64, sweeps=2, steps=40, beta0=0.1,
+                           beta1=3.0)
+    ref.step(40)
+    target = ref.best()[0]
+    _, _ = compare_run(pg, inst, 60, R=64, sweeps=2, beta0=0.1, beta1=3.0, target_cut=target)
+
+
+def test_degenerate_sizes(pg):
+    # a single vertex with no edges, and a single replica
+    one = W.csr_from_edges(1, np.zeros(0), np.zeros(0), np.zeros(0), "one")
+    compare_run(pg, one, 3, R=3, sweeps=2)
+    inst = W.gnm(50, 80, signed=True, seed=3)
+    compare_run(pg, inst, 5, R=1, sweeps=1)
+    # zero sweeps: resampling and control only
+    compare_run(pg, inst, 5, R=8, sweeps=0)
+
+
+def test_config_er800_full(pg):
+    """ER N=800 p=0.06 unit weights, R=128, 50 steps x 5 sweeps, beta 0.1->3.0."""
+    inst = W.c1_er800()
+    compare_run(pg, inst, 50, check_every=5, R=128, sweeps=5, beta0=0.1, beta1=3.0, seed=0)
+
+
+def test_torus141_multi_level_tiles(pg):
+    """Torus 141x141 at reduced R and steps: many levels, many warps per group."""
+    inst = W.c2a_torus141()
+    compare_run(pg, inst, 3, R=12, sweeps=3, beta0=0.1, beta1=4.0, seed=0)
+
+
+def test_sparse7000_augmented_reduced(pg):
+    inst = W.c2b_sparse7000()
+    compare_run(pg, inst, 4, R=16, sweeps=4, beta0=0.1, beta1=4.0, stagnation=1, z_rst=400,
+                seed=0)
+
+
+def test_potts2000_reduced(pg):
+    inst = W.c3_sparse2000()
+    compare_run(pg, inst, 5, kind=1, R=12, sweeps=4, beta0=0.1, beta1=3.0, seed=0)
+
+
+@pytest.mark.parametrize("name", ["torus", "sparse7000"])
+def test_full_size_population_sampled(pg, name):
+    """R=4096 at the benchmark's launch configuration.  Replicas are
+    independent until the first resampling, so the oracle can reproduce a
+    sample of them one by one; the rest is checked by properties that hold
+    at any size (population conserved, energies equal the definition)."""
+    inst = W.c2a_torus141() if name == "torus" else W.c2b_sparse7000()
+    R = 4096
+    s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+    s.init(R=R, sweeps=10, steps=500, beta0=0.1, beta1=4.0, stagnation=1, z_rst=400, seed=0)
+    s.step(1)
+    spins, E, par, cnt = s.state()
+    ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=8, sweeps=10, steps=500, beta0=0.1,
+                           beta1=4.0, stagnation=1, z_rst=400, seed=0)
+    ref.step(1)
+    np.testing.assert_array_equal(spins[:8], ref.spins())
+    np.testing.assert_array_equal(E[:8], ref.energy())
+    s.step(2)
+    spins, E, par, cnt = s.state()
+    assert cnt.sum() == R and np.all(np.diff(par) >= 0)
+    rng = np.random.default_rng(0)
+    for r in rng.choice(R, size=16, replace=False):
+        assert E[r] == oracle.energy_ising(inst.row_ptr, inst.col, -inst.w, spins[r])
+    m, b = s.best()
+    assert m == (pg.pamc_weight_sum(s.h) - oracle.energy_ising(inst.row_ptr, inst.col, -inst.w, b)) // 2
+    s.close()
