@@ -100,8 +100,16 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+ONLY = None
+
+
 def instances():
-    return [W.c2a_torus141(), W.c2b_sparse7000()]
+    insts = [W.c2a_torus141(), W.c2b_sparse7000()]
+    if ONLY == "torus":
+        return insts[:1]
+    if ONLY == "sparse":
+        return insts[1:]
+    return insts
 
 
 def attempts_per_step(insts):
@@ -216,6 +224,14 @@ def run_ours(args):
     att = attempts_per_step(insts) * args.steps * world
     value = att / (ms / 1e3)
 
+    if args.lean:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "attempts/s",
+                              "ms_per_step": ms / args.steps, "gpu_launches": launches,
+                              "config": {"only": ONLY}}))
+        for s in solvers:
+            s.close()
+        return None
     # dominant kernel alone: sweeps of one step on the torus (events around
     # the step minus the other kernels is not separable, so time a sweep-only
     # step with stagnation off on a fresh handle, same launch configuration)
@@ -323,7 +339,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--only", choices=["torus", "sparse"], default=None,
+                    help="run one of the two instances (profiling)")
+    ap.add_argument("--lean", action="store_true",
+                    help="timed steps only: no e2e, kernel split or CPU baseline (profiling)")
     args = ap.parse_args()
+    global ONLY
+    ONLY = args.only
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         if rank != 0:
