@@ -146,6 +146,46 @@ pamc_status pamc_last_error(pamc_handle h, char *buf, size_t len);
 
 void pamc_destroy(pamc_handle h);
 
+/* Size limits of pamc_sweeps_noalloc and the bytes of device memory its
+ * file-scope scratch array takes on every GPU that loads the library. */
+#define PAMC_NOALLOC_MAX_N 32768
+#define PAMC_NOALLOC_MAX_NNZ 262144
+#define PAMC_NOALLOC_MAX_SWEEPS 8
+#define PAMC_NOALLOC_MAX_R 16384
+#define PAMC_NOALLOC_SCRATCH_BYTES 5377280
+
+/* S sweeps (heat-bath rule = 0 or Metropolis rule = 1) of an Ising
+ * population at a fixed beta, with no device or host allocation -- for
+ * callers that cannot call cudaMalloc (code that may only use the buffers it
+ * is handed: a plug-in inside a framework that owns all device memory, or a
+ * loop where allocation is forbidden).  The paper has no counterpart; the
+ * result is bit-identical to S sweeps of pamc_step on the same population at
+ * step index t without resampling (same Philox keys, same sweep orders).
+ * Inputs and outputs are DEVICE pointers owned by the caller: the CSR of the
+ * Max-Cut weights (row_ptr[n+1], col[nnz], w[nnz]; symmetric, no diagonal,
+ * |w| <= 127), H >= max_i sum_j |w_ij| (<= 127), spins_in and spins_out
+ * (R*n int8, +1/-1, replica-major; may be the same buffer) and E_out (R
+ * energies H(s) = -sum_{i<j} J_ij s_i s_j of the result).  err (optional)
+ * receives a one-line message.
+ * Limits: n <= PAMC_NOALLOC_MAX_N, nnz <= PAMC_NOALLOC_MAX_NNZ,
+ * sweeps <= PAMC_NOALLOC_MAX_SWEEPS, R <= PAMC_NOALLOC_MAX_R; larger sizes
+ * return PAMC_ERR_RANGE before any device work.  An invalid instance returns
+ * PAMC_ERR_ARG / ASYM / DIAG / RANGE after a validation kernel, before any
+ * kernel indexes through it.
+ * Scratch: one static device array of PAMC_NOALLOC_SCRATCH_BYTES per GPU,
+ * held from library load until process exit, shared by every call on that
+ * GPU and keeping the last call's contents (the call resets what must start
+ * fresh).  Calls whose device work overlaps on one GPU (different streams or
+ * threads) race on it: serialise them.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  The call is
+ * synchronous: it waits for its stream before returning. */
+pamc_status pamc_sweeps_noalloc(int32_t n, int32_t nnz, const int32_t *row_ptr, const int32_t *col,
+                                const int32_t *w, int32_t H, int32_t rule, int32_t R,
+                                int32_t sweeps, double beta, uint64_t seed, int32_t t,
+                                const int8_t *spins_in, int8_t *spins_out, int64_t *E_out,
+                                void *stream, char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

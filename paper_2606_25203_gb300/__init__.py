@@ -22,6 +22,7 @@ __all__ = [
     "PamcError", "Params", "load", "pamc_create_csr", "pamc_create_dense", "pamc_init",
     "pamc_step", "pamc_sync", "pamc_run", "pamc_best", "pamc_state", "pamc_control_state",
     "pamc_launch_count", "pamc_weight_sum", "pamc_last_error", "pamc_destroy", "Solver",
+    "pamc_sweeps_noalloc",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -111,7 +112,10 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_weight_sum.restype = i64
     L.pamc_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     L.pamc_destroy.argtypes = [P]
-    for nm in ("pamc_set_allocator", "pamc_create_csr", "pamc_create_dense", "pamc_init",
+    L.pamc_sweeps_noalloc.argtypes = [i32, i32, P, P, P, i32, i32, i32, i32, ctypes.c_double,
+                                      ctypes.c_uint64, i32, P, P, P, P, ctypes.c_char_p,
+                                      ctypes.c_size_t]
+    for nm in ("pamc_sweeps_noalloc", "pamc_set_allocator", "pamc_create_csr", "pamc_create_dense", "pamc_init",
                "pamc_step", "pamc_sync", "pamc_run", "pamc_best", "pamc_state",
                "pamc_control_state", "pamc_last_error"):
         getattr(L, nm).restype = ctypes.c_int
@@ -238,6 +242,30 @@ def pamc_last_error(h=None) -> str:
 def pamc_destroy(h):
     if h is not None and h.value:
         _lib.pamc_destroy(h)
+
+
+def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed, t, spins_in,
+                        spins_out, E_out, stream=None):
+    """S sweeps at a fixed beta on a caller-owned device population without any
+    allocation by the library.  Every array argument is a CUDA tensor (or a raw
+    device address as int); see include/pamc.h for the contract."""
+    L = load()
+
+    def addr(x):
+        if x is None:
+            return None
+        return ctypes.c_void_p(int(x) if isinstance(x, int) else int(x.data_ptr()))
+
+    dev = 0
+    if hasattr(spins_in, "device"):
+        dev = spins_in.device.index or 0
+    buf = ctypes.create_string_buffer(256)
+    rc = L.pamc_sweeps_noalloc(int(n), int(nnz), addr(row_ptr), addr(col), addr(w), int(H),
+                               int(rule), int(R), int(sweeps), float(beta), int(seed), int(t),
+                               addr(spins_in), addr(spins_out), addr(E_out),
+                               _stream_ptr(dev, stream), buf, 256)
+    if rc != 0:
+        raise PamcError(rc, buf.value.decode(errors="replace"))
 
 
 class Solver:
