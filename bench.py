@@ -154,10 +154,10 @@ def run_reference(args):
 
 
 def cpu_baseline_sample():
-    """Oracle timed on the host: first iteration of both instances, R=64."""
+    """Oracle timed on the host: first iteration of both instances, R=1024."""
     import oracle
     insts = instances()
-    Rs = 64
+    Rs = 1024
     params = dict(PARAMS, R=Rs)
     t0 = time.perf_counter()
     att = 0

@@ -9,6 +9,8 @@
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -53,6 +55,8 @@ struct pamc_handle_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     int32_t n = 0, nnz = 0, H = 0;
+    int32_t maxdeg = 0;        // largest number of nonzero couplings of a vertex
+    int32_t ell_w = 0;         // ELL width of the schedules (0: CSR reads)
     int64_t W = 0;
     int dense = 0;
     // instance
@@ -75,6 +79,8 @@ struct pamc_handle_s {
     uint64_t *d_tab = nullptr;
     int32_t *d_order = nullptr, *d_lvl = nullptr, *d_nlev = nullptr, *d_scnt = nullptr;
     uint32_t *d_skey = nullptr;
+    uint32_t *d_ell = nullptr;
+    int2 *d_pos = nullptr;
     DevCtl *d_ctl = nullptr;
     int8_t *d_best = nullptr;
     int64_t launches = 0;
@@ -128,7 +134,7 @@ bool alloc_n(pamc_handle h, T *&ptr, size_t count, std::vector<DevBuf> &list) {
 
 // Validated symmetric CSR -> packed adjacency (col | J<<24 with J = -w).
 pamc_status validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *w,
-                         std::vector<uint32_t> &adj, int64_t &W, int32_t &H) {
+                         std::vector<uint32_t> &adj, int64_t &W, int32_t &H, int32_t &maxdeg) {
     if (n < 1 || n >= (1 << 24) || !rp || (!col && rp && rp[n] > 0) || (!w && rp && rp[n] > 0))
         return fail(nullptr, PAMC_ERR_ARG, "invalid n or null CSR pointer");
     if (rp[0] != 0) return fail(nullptr, PAMC_ERR_ARG, "row_ptr[0] must be 0");
@@ -141,8 +147,10 @@ pamc_status validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const
     adj.resize(nnz);
     W = 0;
     H = 0;
+    maxdeg = 0;
     for (int32_t i = 0; i < n; ++i) {
         int64_t habs = 0;
+        int32_t deg = 0;
         for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
             const int32_t j = col[e];
             if (j < 0 || j >= n) return fail(nullptr, PAMC_ERR_ARG, "column index out of range");
@@ -152,6 +160,7 @@ pamc_status validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const
             fwd.emplace_back(i, j, w[e]);
             bwd.emplace_back(j, i, w[e]);
             habs += w[e] < 0 ? -w[e] : w[e];
+            deg += w[e] != 0 ? 1 : 0;
             W += w[e];
             const int32_t J = -w[e];
             adj[e] = (uint32_t)j | ((uint32_t)(uint8_t)(int8_t)J << 24);
@@ -160,6 +169,7 @@ pamc_status validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const
             return fail(nullptr, PAMC_ERR_RANGE, "sum_j |w_ij| = %lld > 127 at vertex %d",
                         (long long)habs, i);
         H = std::max<int32_t>(H, (int32_t)habs);
+        maxdeg = std::max(maxdeg, deg);
     }
     std::sort(fwd.begin(), fwd.end());
     std::sort(bwd.begin(), bwd.end());
@@ -174,20 +184,45 @@ void release_run(pamc_handle h) {
     h->d_spins[0] = h->d_spins[1] = nullptr;
 }
 
-SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H) {
-    SweepCfg c{1, 1};
+// Launch shape of the sweep kernel: groups per CTA and warps per group.
+// Scores every shape by the fraction of group slots used over whole waves,
+// the lane efficiency of a level (average level size over the lanes of a
+// group), and resident warps per SM.  PAMC_SWEEP_CFG="gpc,wpg" overrides.
+SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level, int sms) {
     const int RPG = kind == 0 ? 4 : 2;
     const int32_t groups = (R + RPG - 1) / RPG;
-    c.warps_per_group = n >= 16384 ? 8 : n >= 4096 ? 4 : n >= 1024 ? 2 : 1;
-    const size_t per_group = (size_t)((n + 15) & ~15) + RPG * 8;
-    const size_t tabb = (size_t)(kind == 0 ? 2 * H + 1 : 4 * H + 1) * 8;
-    int gpc = 1024 / (32 * c.warps_per_group);
-    while (gpc > 1 && tabb + gpc * per_group > 96 * 1024) --gpc;
-    gpc = std::min(gpc, 15);
-    const int32_t want_ctas = 152 * 2;
-    while (gpc > 1 && (groups + gpc - 1) / gpc < want_ctas) --gpc;
-    c.groups_per_cta = std::max(gpc, 1);
-    return c;
+    if (const char *env = getenv("PAMC_SWEEP_CFG")) {
+        int a = 0, b = 0;
+        if (sscanf(env, "%d,%d", &a, &b) == 2 && a >= 1 && a <= 15 && b >= 1 && a * b * 32 <= 1024) {
+            SweepCfg c{a, b};
+            if (sweep_smem_bytes(kind, n, H, c) <= 227 * 1024) return c;
+        }
+    }
+    SweepCfg best{1, 1};
+    double best_score = -1.0;
+    for (int wpg = 1; wpg <= 16; wpg *= 2) {
+        const int tpg = wpg * 32;
+        const double iters = std::ceil(std::max(avg_level, 1.0) / tpg);
+        const double lane_eff = std::max(avg_level, 1.0) / (iters * tpg);
+        for (int gpc = 1; gpc <= 15 && gpc * tpg <= 1024; ++gpc) {
+            const SweepCfg c{gpc, wpg};
+            const size_t smem = sweep_smem_bytes(kind, n, H, c);
+            if (smem > 227 * 1024) break;
+            const int threads = gpc * tpg;
+            const int bps = std::min({2048 / threads, (int)(233472 / (smem + 1024)),
+                                      65536 / (64 * threads)});
+            if (bps < 1) continue;
+            const int64_t ctas = (groups + gpc - 1) / gpc;
+            const int64_t slots = (int64_t)sms * bps;
+            const int64_t waves = (ctas + slots - 1) / slots;
+            const double util = (double)groups / ((double)waves * slots * gpc);
+            const double warps = (double)std::min<int64_t>(ctas, slots) / sms * gpc * wpg;
+            const double occ = std::min(1.0, warps / 32.0);
+            const double score = util * lane_eff * (0.5 + 0.5 * occ);
+            if (score > best_score + 1e-9) { best_score = score; best = c; }
+        }
+    }
+    return best;
 }
 
 }  // namespace
@@ -209,8 +244,8 @@ pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *co
     *out = nullptr;
     std::vector<uint32_t> adj;
     int64_t W = 0;
-    int32_t H = 0;
-    pamc_status s = validate_csr(n, row_ptr, col, w, adj, W, H);
+    int32_t H = 0, maxdeg = 0;
+    pamc_status s = validate_csr(n, row_ptr, col, w, adj, W, H, maxdeg);
     if (s != PAMC_OK) return s;
     cudaError_t e = cudaSetDevice(cuda_device);
     if (e != cudaSuccess) return fail(nullptr, PAMC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -222,6 +257,10 @@ pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *co
     h->nnz = row_ptr[n];
     h->W = W;
     h->H = H;
+    h->maxdeg = maxdeg;
+    // position-indexed ELL when its padding stays within 4x the couplings
+    const int64_t ell_entries = (int64_t)((n + 31) / 32) * 32 * ((maxdeg + 3) & ~3);
+    h->ell_w = (maxdeg > 0 && ell_entries <= 4 * (int64_t)h->nnz + 4096) ? ((maxdeg + 3) & ~3) : 0;
     if (!alloc_n(h, h->d_rp, (size_t)n + 1, h->inst_bufs) ||
         !alloc_n(h, h->d_adj, (size_t)std::max(h->nnz, 1), h->inst_bufs)) {
         dev_free_all(h, h->inst_bufs);
@@ -282,6 +321,13 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
               alloc_n(h, h->d_nlev, (size_t)kSchedSlots * S, h->bufs) &&
               alloc_n(h, h->d_skey, (size_t)kSchedSlots * S * n, h->bufs) &&
               alloc_n(h, h->d_scnt, (size_t)kSchedSlots * S * n, h->bufs);
+    if (ok && h->ell_w > 0) {
+        ok = alloc_n(h, h->d_ell, (size_t)kSchedSlots * S * ((n + 31) / 32) * 32 * h->ell_w, h->bufs) &&
+             alloc_n(h, h->d_pos, (size_t)kSchedSlots * S * n, h->bufs);
+    } else {
+        h->d_ell = nullptr;
+        h->d_pos = nullptr;
+    }
     if (ok && p.stagnation && p.kind == 0)
         ok = alloc_n(h, h->d_ncm_buf, (size_t)ntop * n, h->bufs) &&
              alloc_n(h, h->d_nkey, (size_t)ntop * n, h->bufs) &&
@@ -317,9 +363,25 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     // host copies of the host-side vectors must stay alive until the copies ran
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "init");
-    h->cfg = choose_cfg(p.kind, n, R, h->H);
-    h->host_t = 0;
+    // schedules of the first steps; their depth sets the sweep launch shape
+    double avg_level = n;
     h->sched_end = 0;
+    if (p.sweeps > 0) {
+        launch_schedule(n, h->d_rp, h->d_adj, p.seed, 0, kSchedSlots, p.sweeps, 0, kSchedSlots,
+                        h->d_order, h->d_lvl, h->d_nlev, h->d_skey, h->d_scnt, h->stream, h->d_ell,
+                        h->ell_w, h->d_pos);
+        h->launches += 1;
+        h->sched_end = kSchedSlots;
+        int32_t depth = 0;
+        e = cudaMemcpyAsync(&depth, h->d_nlev, sizeof(depth), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "schedule depth readback");
+        avg_level = (double)n / std::max(depth, 1);
+    }
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    h->cfg = choose_cfg(p.kind, n, R, h->H, avg_level, sms);
+    h->host_t = 0;
     h->initialized = 1;
     return PAMC_OK;
 }
@@ -338,7 +400,7 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
         if (p.sweeps > 0 && t >= h->sched_end) {
             launch_schedule(n, h->d_rp, h->d_adj, p.seed, (int32_t)t, kSchedSlots, p.sweeps, 0,
                             kSchedSlots, h->d_order, h->d_lvl, h->d_nlev, h->d_skey, h->d_scnt,
-                            h->stream);
+                            h->stream, h->d_ell, h->ell_w, h->d_pos);
             h->sched_end = t + kSchedSlots;
             h->launches += 1;
         }
@@ -352,7 +414,7 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
                            h->d_nkey, h->d_nstat, h->d_ctl, h->stream);
             h->launches += 1;
         }
-        SchedView sv{h->d_order, h->d_lvl, h->d_nlev};
+        SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w};
         if (e == cudaSuccess)
             e = launch_sweep(p.kind, p.rule, n, h->d_rp, h->d_adj, h->H, p, (int32_t)t,
                              (int32_t)(t % kSchedSlots), sv, h->d_tab, src, h->d_parent,

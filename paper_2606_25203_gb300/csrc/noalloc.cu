@@ -210,7 +210,7 @@ extern "C" pamc_status pamc_sweeps_noalloc(int32_t n, int32_t nnz, const int32_t
     e = launch_tables(0, rule, H, ctl, tab, s);
     SweepCfg cfg{1, n >= 16384 ? 8 : n >= 4096 ? 4 : n >= 1024 ? 2 : 1};
     if (e == cudaSuccess)
-        e = launch_sweep(0, rule, n, row_ptr, adj, H, p, t, 0, SchedView{order, lvl, nlev}, tab,
+        e = launch_sweep(0, rule, n, row_ptr, adj, H, p, t, 0, SchedView{order, lvl, nlev, nullptr, nullptr, 0}, tab,
                          spins_in, parent, nullptr, ncm_idx, spins_out, E_out, ctl, cfg, 0, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&derr, &ctl->err, sizeof(derr), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

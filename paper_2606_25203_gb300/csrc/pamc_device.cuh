@@ -34,6 +34,37 @@ __device__ __forceinline__ u32x4 philox(uint32_t c0, uint32_t c1, uint32_t c2, u
     return {c0, c1, c2, c3};
 }
 
+// The ten round keys of a seed, passed to kernels by value so that the rounds
+// read them as constants instead of recomputing the key schedule per call.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+inline __host__ __device__ PhiloxKeys make_philox_keys(uint64_t seed) {
+    PhiloxKeys K;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        K.k0[i] = a;
+        K.k1[i] = b;
+        a += 0x9E3779B9u;
+        b += 0xBB67AE85u;
+    }
+    return K;
+}
+
+__device__ __forceinline__ u32x4 philox_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const PhiloxKeys &K) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[i];
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[i];
+        c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
+    }
+    return {c0, c1, c2, c3};
+}
+
 // ---------------------------------------------------------------------------
 // Deterministic exp: x = k ln2 + r (Cody & Waite, with ln2 split into a
 // 32-significant-bit head and a tail), e^r by the degree-13 Taylor series in

@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "../../include/pamc.h"
+#include "pamc_device.cuh"
 
 namespace pamc {
 
@@ -35,9 +36,12 @@ struct DevCtl {
 // level l.  No two vertices of one level are coupled, and every coupled
 // pair is ordered exactly as in the random permutation.
 struct SchedView {
-    const int32_t *order;    // [slots][S][n]
+    const int32_t *order;    // [slots][S][n]: k | deg_k << 24
     const int32_t *lvl_ptr;  // [slots][S][n+1]
     const int32_t *nlev;     // [slots][S]
+    const uint32_t *ell;     // [slots][S][ceil(n/32)*32*W] or nullptr (CSR reads)
+    const int2 *pos;         // [slots][S][n]: {k | deg << 24, sum_j J_kj} (with ell)
+    int32_t W;               // ELL width (a multiple of 4, zero-padded)
 };
 
 // Launch configuration of the sparse sweep kernel.
@@ -46,10 +50,23 @@ struct SweepCfg {
     int warps_per_group;  // warps cooperating on one group's level
 };
 
+// Builds the (t, sweep) schedules of nt steps starting at t0 into ring slots
+// t % slots.  order[i] = k | deg_k << 24.  With ell != nullptr the nonzero
+// couplings of position i are also written position-indexed (ELL of width W,
+// W >= the largest degree).
 void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t seed, int32_t t0,
                      int32_t nt, int32_t S, int32_t slot0, int32_t slots, int32_t *order,
                      int32_t *lvl_ptr, int32_t *nlev, uint32_t *skey, int32_t *scnt,
-                     cudaStream_t st);
+                     cudaStream_t st, uint32_t *ell = nullptr, int32_t W = 0,
+                     int2 *pos = nullptr);
+
+size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
+cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uint32_t *adj,
+                               int32_t H, const pamc_params &p, int32_t t, int32_t slot,
+                               SchedView sv, const uint64_t *tab, const int8_t *src,
+                               const int32_t *parent, const int8_t *ncm_buf,
+                               const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
+                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st);
 
 size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg);
 

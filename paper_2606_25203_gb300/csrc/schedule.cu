@@ -29,7 +29,8 @@ __global__ void __launch_bounds__(kSchedThreads)
 k_schedule(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
            uint32_t key0, uint32_t key1, int32_t t0, int32_t S, int32_t slots,
            int32_t *__restrict__ order, int32_t *__restrict__ lvl_ptr, int32_t *__restrict__ nlev,
-           uint32_t *__restrict__ skey, int32_t *__restrict__ scnt) {
+           uint32_t *__restrict__ skey, int32_t *__restrict__ scnt, uint32_t *__restrict__ ell,
+           int32_t W, int2 *__restrict__ pos) {
     const int b = blockIdx.x;
     const int ti = b / S, sw = b % S;
     const int32_t t = t0 + ti;
@@ -81,6 +82,32 @@ k_schedule(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict
         ++L;
     }
     if (threadIdx.x == 0) nlev[base] = L;
+    __syncthreads();
+    // Position-indexed neighbour lists: order[i] becomes k | deg << 24 (deg =
+    // nonzero couplings).  With an ELL buffer (width W, a multiple of 4) the
+    // couplings of position i go to ell[(i/32)*32*W + s*32 + i%32], s < deg,
+    // and the slots deg..W-1 hold 0 (vertex 0, coupling 0), so that a warp's
+    // lanes read consecutive words, the first four slots can be read before
+    // deg is known, and pos[i] = {k | deg << 24, sum_j J_kj}.
+    uint32_t *es = ell ? ell + base * (size_t)(((n + 31) >> 5) << 5) * W : nullptr;
+    int2 *ps = pos ? pos + base * (size_t)n : nullptr;
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int32_t k = ord[i];
+        int32_t d = 0, jsum = 0;
+        uint32_t *ep = es ? es + (size_t)(i >> 5) * 32 * W + (i & 31) : nullptr;
+        for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+            const uint32_t a = adj[e];
+            const int32_t J = (int32_t)a >> 24;
+            if (J == 0) continue;
+            if (ep) ep[(size_t)d * 32] = a;
+            ++d;
+            jsum += J;
+        }
+        if (ep)
+            for (int32_t s2 = d; s2 < W; ++s2) ep[(size_t)s2 * 32] = 0u;
+        ord[i] = k | (d << 24);
+        if (ps) ps[i] = make_int2(k | (d << 24), jsum);
+    }
 }
 
 }  // namespace
@@ -88,10 +115,11 @@ k_schedule(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict
 void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t seed, int32_t t0,
                      int32_t nt, int32_t S, int32_t /*slot0*/, int32_t slots, int32_t *order,
                      int32_t *lvl_ptr, int32_t *nlev, uint32_t *skey, int32_t *scnt,
-                     cudaStream_t st) {
+                     cudaStream_t st, uint32_t *ell, int32_t W, int2 *pos) {
     if (nt <= 0 || S <= 0) return;
     k_schedule<<<nt * S, kSchedThreads, 0, st>>>(n, rp, adj, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                                  t0, S, slots, order, lvl_ptr, nlev, skey, scnt);
+                                                  t0, S, slots, order, lvl_ptr, nlev, skey, scnt,
+                                                  ell, W, pos);
 }
 
 }  // namespace pamc

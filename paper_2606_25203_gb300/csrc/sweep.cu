@@ -48,12 +48,13 @@ __device__ __forceinline__ const int8_t *src_row(int32_t r, int32_t n, const int
     return src + (size_t)parent[r] * n;
 }
 
-template <int KIND>
+template <int KIND, bool ELLP>
 __global__ void __launch_bounds__(1024)
 k_sweep(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
         int32_t H, int32_t R, int32_t S, int32_t rule, uint32_t key0, uint32_t key1, int32_t t,
         int32_t slot, const int32_t *__restrict__ sorder, const int32_t *__restrict__ slvl,
-        const int32_t *__restrict__ snlev, const uint64_t *__restrict__ tab,
+        const int32_t *__restrict__ snlev, const uint32_t *__restrict__ sell, int32_t W,
+        const uint64_t *__restrict__ tab,
         const int8_t *__restrict__ src, const int32_t *__restrict__ parent,
         const int8_t *__restrict__ ncm_buf, const int32_t *__restrict__ ncm_idx,
         int8_t *__restrict__ dst, int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl,
@@ -101,16 +102,32 @@ k_sweep(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t
     const int W1 = 4 * H + 1;
 
     if (active) {
+        const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
         for (int32_t sw = 0; sw < S; ++sw) {
             const size_t sb = (size_t)slot * S + sw;
             const int32_t *ord = sorder + sb * (size_t)n;
             const int32_t *lp = slvl + sb * (size_t)(n + 1);
+            const uint32_t *es = ELLP ? sell + sb * ell_stride : nullptr;
             const int32_t L = snlev[sb];
             for (int32_t lev = 0; lev < L; ++lev) {
                 const int32_t beg = lp[lev], end = lp[lev + 1];
                 for (int32_t i = beg + li; i < end; i += tpg) {
-                    const int32_t k = ord[i];
-                    const int32_t e0 = rp[k], e1 = rp[k + 1];
+                    const uint32_t a0 = (uint32_t)ord[i];
+                    const int32_t k = (int32_t)(a0 & 0xFFFFFFu);
+                    // neighbour words: position-indexed ELL (coalesced, no
+                    // dependence on k) or the CSR row of k
+                    const uint32_t *ep;
+                    int32_t cnt, stride;
+                    if (ELLP) {
+                        ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+                        cnt = (int32_t)(a0 >> 24);
+                        stride = 32;
+                    } else {
+                        const int32_t e0 = rp[k];
+                        ep = adj + e0;
+                        cnt = rp[k + 1] - e0;
+                        stride = 1;
+                    }
                     const u32x4 u = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t,
                                            (kTagFlip << 24) | (uint32_t)g, key0, key1);
                     const uint32_t oldb = sp[k];
@@ -118,8 +135,9 @@ k_sweep(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t
                     if (KIND == 0) {
                         uint32_t accP = 0, accN = 0;
                         int32_t jsum = 0;
-                        for (int32_t e = e0; e < e1; ++e) {
-                            const uint32_t a = adj[e];
+#pragma unroll 4
+                        for (int32_t s2 = 0; s2 < cnt; ++s2) {
+                            const uint32_t a = ep[(size_t)s2 * stride];
                             const int32_t j = (int32_t)(a & 0xFFFFFFu);
                             const int32_t J = (int32_t)a >> 24;
                             const uint32_t x = ((uint32_t)sp[j] * 0x00204081u) & 0x01010101u;
@@ -145,8 +163,9 @@ k_sweep(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t
                         }
                     } else {
                         uint32_t P0 = 0, N0 = 0, P1 = 0, N1 = 0;
-                        for (int32_t e = e0; e < e1; ++e) {
-                            const uint32_t a = adj[e];
+#pragma unroll 4
+                        for (int32_t s2 = 0; s2 < cnt; ++s2) {
+                            const uint32_t a = ep[(size_t)s2 * stride];
                             const int32_t j = (int32_t)(a & 0xFFFFFFu);
                             const int32_t J = (int32_t)a >> 24;
                             const uint32_t nb = sp[j];
@@ -302,6 +321,7 @@ __global__ void k_energy(int kind, int32_t n, const int32_t *__restrict__ rp,
 }  // namespace
 
 size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg) {
+    if (kind == 0) return sweep_ising_smem_bytes(n, H, cfg);
     const int RPG = kind == 0 ? 4 : 2;
     const int tabn = kind == 0 ? (2 * H + 1) : (4 * H + 1);
     const int32_t n_pad = (n + 15) & ~15;
@@ -314,6 +334,9 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
                          const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst,
                          int64_t *E_dst, const DevCtl *ctl, SweepCfg cfg, int64_t Wsum,
                          cudaStream_t st) {
+    if (kind == 0)
+        return launch_sweep_ising(rule, n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_buf,
+                                  ncm_idx, dst, E_dst, ctl, cfg, st);
     const int RPG = kind == 0 ? 4 : 2;
     const int32_t groups = (p.R + RPG - 1) / RPG;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
@@ -322,21 +345,20 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
     const int grid = (groups + gpc - 1) / gpc;
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
     cudaError_t err;
-    if (kind == 0) {
-        err = cudaFuncSetAttribute(k_sweep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        k_sweep<0><<<grid, gpc * tpg, smem, st>>>(n, n_pad, rp, adj, H, p.R, p.sweeps, rule, k0, k1, t,
-                                                   slot, sv.order, sv.lvl_ptr, sv.nlev, tab, src,
-                                                   parent, ncm_buf, ncm_idx, dst, E_dst, ctl, Wsum,
-                                                   gpc, tpg);
-    } else {
-        err = cudaFuncSetAttribute(k_sweep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        k_sweep<1><<<grid, gpc * tpg, smem, st>>>(n, n_pad, rp, adj, H, p.R, p.sweeps, rule, k0, k1, t,
-                                                   slot, sv.order, sv.lvl_ptr, sv.nlev, tab, src,
-                                                   parent, ncm_buf, ncm_idx, dst, E_dst, ctl, Wsum,
-                                                   gpc, tpg);
-    }
+#define PAMC_LAUNCH_SWEEP(KD, EL)                                                                \
+    do {                                                                                         \
+        err = cudaFuncSetAttribute(k_sweep<KD, EL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                   (int)smem);                                                   \
+        if (err != cudaSuccess) return err;                                                      \
+        k_sweep<KD, EL><<<grid, gpc * tpg, smem, st>>>(                                          \
+            n, n_pad, rp, adj, H, p.R, p.sweeps, rule, k0, k1, t, slot, sv.order, sv.lvl_ptr,    \
+            sv.nlev, sv.ell, sv.W, tab, src, parent, ncm_buf, ncm_idx, dst, E_dst, ctl, Wsum,    \
+            gpc, tpg);                                                                           \
+    } while (0)
+    const bool ell = sv.ell != nullptr;
+    if (ell) PAMC_LAUNCH_SWEEP(1, true);
+    else PAMC_LAUNCH_SWEEP(1, false);
+#undef PAMC_LAUNCH_SWEEP
     return cudaGetLastError();
 }
 

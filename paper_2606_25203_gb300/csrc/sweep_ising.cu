@@ -1,0 +1,249 @@
+// sweep_ising.cu -- S single-spin sweeps of the Ising population per
+// temperature step (Eq. 3-4: heat-bath s_k = +1 iff u < T(h_k); Metropolis
+// flip iff u < T_M(2 s_k h_k)), the hot loop of Algorithm 1.
+//
+// Layout.  A replica group (the 4 replicas that share one Philox4x32-10 call
+// per vertex visit) keeps its spins in shared memory as one 32-bit word per
+// vertex with one BYTE per replica (0 or 1).  A neighbour's contribution to
+// the four fields is then a single word added to (or subtracted from) a
+// biased accumulator A (one multiply-add: A += word_j * J_kj) whose byte q
+// holds 128 + sum_j J_kj [s_j = +1], so that
+//     h_q + H = 2 * byte_q(A) + c0,   c0 = H - 256 - sum_j J_kj
+// indexes the threshold table directly.  Bytes never carry or borrow because
+// sum_j |J_kj| <= 127.  A neighbour costs one global load (position-indexed
+// ELL, batches of four in flight), one shared load and one multiply-add.
+//
+// Order.  Vertices of one level of the (t, sweep) schedule are pairwise
+// uncoupled; levels run in order with a named barrier per replica group, which
+// reproduces the sequential sweep exactly.
+#include "pamc_device.cuh"
+#include "pamc_internal.h"
+
+namespace pamc {
+
+namespace {
+
+__device__ __forceinline__ void group_barrier(int id, int nthreads, int groups) {
+    if (groups == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+    }
+}
+
+template <bool ELLP, int RULE>
+__global__ void __launch_bounds__(1024)
+k_sweep_ising(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
+              const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, PhiloxKeys K,
+              int32_t t, int32_t slot, const int32_t *__restrict__ sorder,
+              const int32_t *__restrict__ slvl, const int32_t *__restrict__ snlev,
+              const uint32_t *__restrict__ sell, const int2 *__restrict__ spos, int32_t W,
+              const uint64_t *__restrict__ tab, const int8_t *__restrict__ src,
+              const int32_t *__restrict__ parent, const int8_t *__restrict__ ncm_buf,
+              const int32_t *__restrict__ ncm_idx, int8_t *__restrict__ dst,
+              int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int gpc, int tpg) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    if (ctl->done) return;
+    const int tabn = 2 * H + 1;
+    uint64_t *tab_s = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *spins_all = reinterpret_cast<uint32_t *>(smem + (((size_t)tabn * 8 + 15) & ~(size_t)15));
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(spins_all + (size_t)gpc * n_pad);
+    for (int i = threadIdx.x; i < tabn; i += blockDim.x) tab_s[i] = tab[i];
+    for (int i = threadIdx.x; i < gpc * 4; i += blockDim.x) red[i] = 0ull;
+
+    const int gl = threadIdx.x / tpg, li = threadIdx.x % tpg;
+    const int32_t g = blockIdx.x * gpc + gl;
+    const int32_t r0 = g * 4;
+    const bool active = r0 < R;
+    uint32_t *sp = spins_all + (size_t)gl * n_pad;
+
+    if (active) {
+        // slot r reads the NCM output if the cluster move rewrote it, else
+        // its resampling parent (the replica copy of the population step)
+        const int8_t *rows[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int32_t r = r0 + q;
+            if (r < R) {
+                const int32_t m = ncm_idx[r];
+                rows[q] = m >= 0 ? ncm_buf + (size_t)m * n : src + (size_t)parent[r] * n;
+            } else {
+                rows[q] = nullptr;
+            }
+        }
+        for (int32_t k = li; k < n; k += tpg) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (rows[q] != nullptr) w |= (uint32_t)(rows[q][k] > 0) << (8 * q);
+            sp[k] = w;
+        }
+    }
+    __syncthreads();
+
+    if (active) {
+        const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
+        const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)g;
+        for (int32_t sw = 0; sw < S; ++sw) {
+            const size_t sb = (size_t)slot * S + sw;
+            const int32_t *ord = sorder + sb * (size_t)n;
+            const int32_t *lp = slvl + sb * (size_t)(n + 1);
+            const uint32_t *es = ELLP ? sell + sb * ell_stride : nullptr;
+            const int2 *pos = ELLP ? spos + sb * (size_t)n : nullptr;
+            const int32_t L = snlev[sb];
+            for (int32_t lev = 0; lev < L; ++lev) {
+                const int32_t beg = lp[lev], end = lp[lev + 1];
+                int32_t i = beg + li;
+                // ELL path: the record and the first four neighbour words of
+                // the next position are loaded one iteration ahead
+                int2 pr = make_int2(0, 0);
+                uint32_t e4[4] = {0u, 0u, 0u, 0u};
+                if (ELLP && i < end) {
+                    pr = pos[i];
+                    const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) e4[q] = ep[q * 32];
+                }
+                while (i < end) {
+                    const int32_t inext = i + tpg;
+                    int2 prn = make_int2(0, 0);
+                    uint32_t e4n[4] = {0u, 0u, 0u, 0u};
+                    if (ELLP && inext < end) {
+                        prn = pos[inext];
+                        const uint32_t *epn = es + (size_t)(inext >> 5) * 32 * W + (inext & 31);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) e4n[q] = epn[q * 32];
+                    }
+                    // A: byte q = 128 + sum_j J_kj [s_j = +1] of replica q
+                    uint32_t A = 0x80808080u;
+                    int32_t k, jsum;
+                    if (ELLP) {
+                        const uint32_t a0 = (uint32_t)pr.x;
+                        k = (int32_t)(a0 & 0xFFFFFFu);
+                        const int32_t deg = (int32_t)(a0 >> 24);
+                        jsum = pr.y;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)   // padding slots: coupling 0
+                            A += sp[e4[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e4[q] >> 24);
+                        if (deg > 4) {
+                            const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+                            for (int32_t b0 = 4; b0 < deg; b0 += 4) {
+                                uint32_t ev[4];
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) ev[q] = ep[(b0 + q) * 32];
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    A += sp[ev[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ev[q] >> 24);
+                            }
+                        }
+                    } else {
+                        k = ord[i] & 0xFFFFFF;
+                        jsum = 0;
+                        for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+                            const uint32_t a = adj[e];
+                            const int32_t J = (int32_t)a >> 24;
+                            A += sp[a & 0xFFFFFFu] * (uint32_t)J;
+                            jsum += J;
+                        }
+                    }
+                    const int32_t c0 = H - 256 - jsum;
+                    const u32x4 u = philox_rk((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3, K);
+                    const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+                    const uint32_t old = sp[k];
+                    uint32_t nw = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int32_t idx = 2 * (int32_t)((A >> (8 * q)) & 0xFFu) + c0;   // h + H
+                        if (RULE == 0) {
+                            nw |= ((uint64_t)uw[q] < tab_s[idx] ? 1u : 0u) << (8 * q);
+                        } else {
+                            const uint32_t s = (old >> (8 * q)) & 1u;
+                            const int32_t ix = s ? idx : 2 * H - idx;              // s*h + H
+                            nw |= (((uint64_t)uw[q] < tab_s[ix]) ? (s ^ 1u) : s) << (8 * q);
+                        }
+                    }
+                    if (nw != old) sp[k] = nw;
+                    i = inext;
+                    pr = prn;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) e4[q] = e4n[q];
+                }
+                group_barrier(1 + gl, tpg, gpc);
+            }
+        }
+
+        // energy from the definition E = -1/2 sum_k s_k h_k, and the write-back
+        long long acc[4] = {0, 0, 0, 0};
+        for (int32_t k = li; k < n; k += tpg) {
+            const uint32_t w = sp[k];
+            uint32_t accP = 0, accN = 0;
+            int32_t jsum = 0;
+            for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+                const uint32_t a = adj[e];
+                const int32_t J = (int32_t)a >> 24;
+                const uint32_t x = sp[a & 0xFFFFFFu];
+                if (J > 0) accP += x * (uint32_t)J;
+                else accN += x * (uint32_t)(-J);
+                jsum += J;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t h = 2 * ((int32_t)((accP >> (8 * q)) & 0xFFu) -
+                                       (int32_t)((accN >> (8 * q)) & 0xFFu)) - jsum;
+                const int32_t s = ((w >> (8 * q)) & 1u) ? 1 : -1;
+                acc[q] += (long long)(s * h);
+                if (r0 + q < R) dst[(size_t)(r0 + q) * n + k] = (int8_t)s;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            long long v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&red[gl * 4 + q], (unsigned long long)v);
+        }
+    }
+    __syncthreads();
+    if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 4 + li] / 2);
+}
+
+}  // namespace
+
+size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg) {
+    const int32_t n_pad = (n + 3) & ~3;
+    return (((size_t)(2 * H + 1) * 8 + 15) & ~(size_t)15) + (size_t)cfg.groups_per_cta * n_pad * 4 +
+           (size_t)cfg.groups_per_cta * 4 * 8;
+}
+
+cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uint32_t *adj,
+                               int32_t H, const pamc_params &p, int32_t t, int32_t slot,
+                               SchedView sv, const uint64_t *tab, const int8_t *src,
+                               const int32_t *parent, const int8_t *ncm_buf,
+                               const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
+                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st) {
+    const int32_t groups = (p.R + 3) / 4;
+    const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
+    const int32_t n_pad = (n + 3) & ~3;
+    const size_t smem = sweep_ising_smem_bytes(n, H, cfg);
+    const int grid = (groups + gpc - 1) / gpc;
+    const PhiloxKeys K = make_philox_keys(p.seed);
+    const bool ell = sv.ell != nullptr;
+    cudaError_t err = cudaSuccess;
+#define PAMC_LAUNCH(EL, RU)                                                                   \
+    do {                                                                                          \
+        err = cudaFuncSetAttribute(k_sweep_ising<EL, RU>,                                     \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        if (err != cudaSuccess) return err;                                                       \
+        k_sweep_ising<EL, RU><<<grid, gpc * tpg, smem, st>>>(                                 \
+            n, n_pad, rp, adj, H, p.R, p.sweeps, K, t, slot, sv.order, sv.lvl_ptr, sv.nlev,       \
+            sv.ell, sv.pos, sv.W, tab, src, parent, ncm_buf, ncm_idx, dst, E_dst, ctl, gpc, tpg); \
+    } while (0)
+    if (ell) {
+        if (rule == 0) PAMC_LAUNCH(true, 0); else PAMC_LAUNCH(true, 1);
+    } else {
+        if (rule == 0) PAMC_LAUNCH(false, 0); else PAMC_LAUNCH(false, 1);
+    }
+#undef PAMC_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace pamc
