@@ -83,6 +83,15 @@ struct pamc_handle_s {
     int2 *d_pos = nullptr;
     DevCtl *d_ctl = nullptr;
     int8_t *d_best = nullptr;
+    // dense instances
+    int8_t *d_J = nullptr;               // n x n couplings (J = -w)
+    int32_t *d_H = nullptr;              // [R][n] fields
+    int32_t *d_perm = nullptr, *d_sidx = nullptr, *d_G = nullptr, *d_ident = nullptr, *d_nonc = nullptr;
+    uint32_t *d_pkey = nullptr;
+    int8_t *d_T = nullptr;
+    unsigned long long *d_flip = nullptr, *d_snew = nullptr;
+    void *d_bar = nullptr;
+    int32_t dense_Hc = 0, dense_grid = 0, dense_nupd = 0, dense_rows = 0;
     int64_t launches = 0;
     char err[256] = "";
 };
@@ -225,6 +234,125 @@ SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level,
     return best;
 }
 
+// ---------------------------------------------------------------- dense runs
+pamc_status init_dense(pamc_handle h, pamc_params p) {
+    if (p.kind != 0) return fail(h, PAMC_ERR_ARG, "dense instances run the Ising (Max-Cut) kind only");
+    if (p.R > 64) return fail(h, PAMC_ERR_RANGE, "dense instances support R <= 64");
+    if (p.stagnation && (h->n & 1))
+        return fail(h, PAMC_ERR_ARG, "cluster moves on dense instances need even n (no iso-sites then)");
+    if (p.sweeps > 64) return fail(h, PAMC_ERR_RANGE, "dense instances support at most 64 sweeps per step");
+    int coop = 0, sms = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (!coop) return fail(h, PAMC_ERR_CUDA, "device lacks cooperative launch");
+    const int32_t n = h->n, R = p.R, S = std::max(p.sweeps, 1);
+    const int chain = (R + 3) / 4;
+    const int grid = sms;
+    const int nupd = grid - chain;
+    if (nupd < 1) return fail(h, PAMC_ERR_RANGE, "too few SMs for the dense sweep");
+    const int32_t rows = (n + nupd - 1) / nupd;
+    const size_t smem = dense_sweep_smem(n, R, rows);
+    if (rows > dense_sweep_threads() || smem > 227 * 1024)
+        return fail(h, PAMC_ERR_RANGE, "dense instance too large for the on-chip field slices");
+    release_run(h);
+    h->p = p;
+    h->dense_grid = grid;
+    h->dense_nupd = nupd;
+    h->dense_rows = rows;
+    h->dense_Hc = std::min<int32_t>(n, 32767);
+    const int B = dense_block_positions();
+    const size_t tabn = (size_t)2 * h->dense_Hc + 1;
+    bool ok = alloc_n(h, h->d_spins[0], (size_t)R * n, h->bufs) &&
+              alloc_n(h, h->d_spins[1], (size_t)R * n, h->bufs) &&
+              alloc_n(h, h->d_E[0], 64, h->bufs) && alloc_n(h, h->d_E[1], 64, h->bufs) &&
+              alloc_n(h, h->d_parent, R, h->bufs) && alloc_n(h, h->d_count, R, h->bufs) &&
+              alloc_n(h, h->d_ncm_idx, R, h->bufs) && alloc_n(h, h->d_targets, R, h->bufs) &&
+              alloc_n(h, h->d_tab, tabn, h->bufs) && alloc_n(h, h->d_ctl, 1, h->bufs) &&
+              alloc_n(h, h->d_best, n, h->bufs) && alloc_n(h, h->d_H, (size_t)R * n, h->bufs) &&
+              alloc_n(h, h->d_perm, (size_t)S * n, h->bufs) && alloc_n(h, h->d_pkey, (size_t)S * n, h->bufs) &&
+              alloc_n(h, h->d_sidx, (size_t)S * n, h->bufs) && alloc_n(h, h->d_G, (size_t)B * 64, h->bufs) &&
+              alloc_n(h, h->d_T, (size_t)B * B, h->bufs) && alloc_n(h, h->d_flip, (size_t)2 * B, h->bufs) &&
+              alloc_n(h, h->d_snew, (size_t)2 * B, h->bufs) &&
+              (h->d_bar = dev_alloc(h, 64, h->bufs)) != nullptr &&
+              alloc_n(h, h->d_ident, R, h->bufs) && alloc_n(h, h->d_nonc, R, h->bufs);
+    if (!ok) {
+        release_run(h);
+        return fail(h, PAMC_ERR_OOM, "device allocation of the dense population failed");
+    }
+    DevCtl c;
+    memset(&c, 0, sizeof(c));
+    c.z = 1;
+    c.beta = p.beta0;
+    c.dbeta = p.steps > 1 ? (p.beta1 - p.beta0) / (double)(p.steps - 1) : 0.0;
+    c.delta = c.dbeta;
+    c.mstar = INT64_MIN;
+    c.best_replica = -1;
+    std::vector<int32_t> ident(R), ones(R, 1), minus(R, -1);
+    for (int32_t r = 0; r < R; ++r) ident[r] = r;
+    cudaError_t e = cudaMemcpyAsync(h->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_parent, ident.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ident, ident.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_count, ones.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ncm_idx, minus.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_nonc, minus.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_best, 0, n, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_E[0], 0, 64 * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_E[1], 0, 64 * 8, h->stream);
+    // initial population, its fields (tensor-core recompute) and energies
+    if (e == cudaSuccess) e = launch_init_spins(0, n, R, p.seed, 0, 0, h->d_ctl, h->d_spins[0], h->stream);
+    if (e == cudaSuccess)
+        e = launch_dense_recompute(n, R, h->d_J, h->d_spins[0], h->d_ident, nullptr, h->d_nonc, h->d_H,
+                                   h->d_ctl, h->stream, -1);
+    if (e == cudaSuccess)
+        e = launch_dense_energy(n, R, h->d_H, h->d_spins[0], h->d_E[0], h->d_ctl, h->stream, -1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dense init");
+    h->launches += 3;
+    h->host_t = 0;
+    h->initialized = 1;
+    return PAMC_OK;
+}
+
+pamc_status step_dense(pamc_handle h, int32_t nsteps) {
+    const pamc_params &p = h->p;
+    const int32_t n = h->n, R = p.R;
+    pamc_params pp = p;
+    pp.n_top = 0;   // no cluster-move targets: dense moves are provably empty for even n
+    for (int32_t i = 0; i < nsteps; ++i) {
+        const int64_t t = h->host_t;
+        if (t > INT32_MAX - 2) return fail(h, PAMC_ERR_RANGE, "step counter overflow");
+        int8_t *src = h->d_spins[t & 1], *dst = h->d_spins[(t + 1) & 1];
+        int64_t *Es = h->d_E[t & 1], *Ed = h->d_E[(t + 1) & 1];
+        cudaError_t e = launch_dense_perm(n, p.seed, (int32_t)t, p.sweeps, h->d_perm, h->d_pkey, h->d_sidx,
+                                          h->d_ctl, h->stream);
+        if (e == cudaSuccess)
+            e = launch_prep(pp, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->stream);
+        if (e == cudaSuccess) e = launch_dense_tables(p.rule, h->dense_Hc, n, h->d_ctl, h->d_tab, h->stream);
+        if (e == cudaSuccess)
+            e = launch_dense_recompute(n, R, h->d_J, src, h->d_parent, nullptr, h->d_ncm_idx, h->d_H, h->d_ctl,
+                                       h->stream, -1);
+        if (e == cudaSuccess)
+            e = launch_dense_sweep(n, R, p.sweeps, p.rule, h->dense_Hc, (int32_t)t, p.seed, h->dense_nupd,
+                                   h->dense_rows, h->dense_grid, h->d_J, h->d_perm, h->d_tab, src,
+                                   h->d_parent, nullptr, h->d_ncm_idx, h->d_H, dst, Ed, h->d_G, h->d_T,
+                                   h->d_flip, h->d_snew, h->d_bar, h->d_ctl, h->stream);
+        if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
+        h->launches += 7;
+        if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
+            const int32_t tk = (int32_t)(t + 1);
+            e = launch_init_spins(0, n, R, p.seed, tk, 1, h->d_ctl, dst, h->stream);
+            if (e == cudaSuccess)
+                e = launch_dense_recompute(n, R, h->d_J, dst, h->d_ident, nullptr, h->d_nonc, h->d_H,
+                                           h->d_ctl, h->stream, tk);
+            if (e == cudaSuccess) e = launch_dense_energy(n, R, h->d_H, dst, Ed, h->d_ctl, h->stream, tk);
+            h->launches += 3;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "dense kernel launch");
+        h->host_t = t + 1;
+    }
+    return PAMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -283,9 +411,52 @@ pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *co
 
 pamc_status pamc_create_dense(int32_t n, const int8_t *w, int w_on_device, int cuda_device,
                               void *stream, pamc_handle *out) {
-    (void)n; (void)w; (void)w_on_device; (void)cuda_device; (void)stream;
-    if (out) *out = nullptr;
-    return fail(nullptr, PAMC_ERR_ARG, "dense instances are not supported by this build");
+    if (!out) return fail(nullptr, PAMC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 2 || !w) return fail(nullptr, PAMC_ERR_ARG, "n >= 2 and a weight matrix are required");
+    if ((int64_t)n > (int64_t)1 << 20) return fail(nullptr, PAMC_ERR_RANGE, "n > 2^20");
+    cudaError_t e = cudaSetDevice(cuda_device);
+    if (e != cudaSuccess) return fail(nullptr, PAMC_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    pamc_handle h = new (std::nothrow) pamc_handle_s();
+    if (!h) return fail(nullptr, PAMC_ERR_OOM, "host allocation failed");
+    h->device = cuda_device;
+    h->stream = (cudaStream_t)stream;
+    h->n = n;
+    h->dense = 1;
+    h->nnz = 0;
+    h->H = 0;
+    const size_t total = (size_t)n * n;
+    unsigned long long *d_sum = nullptr;
+    int *d_err = nullptr;
+    if (!alloc_n(h, h->d_J, total, h->inst_bufs) || !alloc_n(h, d_sum, 1, h->inst_bufs) ||
+        !alloc_n(h, d_err, 1, h->inst_bufs)) {
+        dev_free_all(h, h->inst_bufs);
+        delete h;
+        return fail(nullptr, PAMC_ERR_OOM, "device allocation of the dense instance failed");
+    }
+    e = cudaMemcpyAsync(h->d_J, w, total, w_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_sum, 0, sizeof(*d_sum), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(*d_err), h->stream);
+    if (e == cudaSuccess) e = launch_dense_negate_sum(total, h->d_J, d_sum, h->stream);
+    if (e == cudaSuccess) e = launch_dense_validate(n, h->d_J, d_err, h->stream);
+    unsigned long long wsum = 0;
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&wsum, d_sum, sizeof(wsum), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d_err, sizeof(err), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->launches += 2;
+    if (e != cudaSuccess || err != 0) {
+        dev_free_all(h, h->inst_bufs);
+        delete h;
+        if (e != cudaSuccess) return fail(nullptr, PAMC_ERR_CUDA, "dense upload: %s", cudaGetErrorString(e));
+        return fail(nullptr, (pamc_status)err, "dense matrix rejected: %s",
+                    err == PAMC_ERR_ASYM ? "not symmetric" : err == PAMC_ERR_DIAG ? "nonzero diagonal"
+                                                                            : "entries must be +-1 off the diagonal");
+    }
+    h->W = (int64_t)wsum / 2;   // sum over ordered pairs counts each edge twice
+    *out = h;
+    return PAMC_OK;
 }
 
 pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
@@ -303,6 +474,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     if (!(p.beta0 == p.beta0) || !(p.beta1 == p.beta1)) return fail(h, PAMC_ERR_ARG, "beta is NaN");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (h->dense) return init_dense(h, p);
     release_run(h);
     h->p = p;
     const int32_t n = h->n, R = p.R, S = std::max(p.sweeps, 1);
@@ -392,6 +564,7 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
     if (nsteps < 0) return fail(h, PAMC_ERR_ARG, "nsteps < 0");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (h->dense) return step_dense(h, nsteps);
     const pamc_params &p = h->p;
     const int32_t n = h->n;
     for (int32_t i = 0; i < nsteps; ++i) {

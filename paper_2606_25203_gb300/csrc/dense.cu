@@ -1,0 +1,705 @@
+// dense.cu -- the fully connected instance: J is an N x N int8 matrix in HBM
+// (symmetric, +-1 off the diagonal, 0 on it).  Per temperature step:
+//   k_dense_perm       the shared random order of each sweep (Sec. II.A):
+//                      vertices sorted by (Philox key, index) -- bucket by the
+//                      top key bits, then sort each bucket;
+//   k_dense_tables     heat-bath T(h) (Eq. 4) or Metropolis T_M(2x) over the
+//                      field range that does not saturate;
+//   k_dense_recompute  H = J * S for the resampled population with int8
+//                      tensor-core MMA (exact int32 accumulation): the full
+//                      field recompute of every step;
+//   k_dense_sweep      S sequential sweeps (cooperative, persistent): most
+//                      CTAs own a slice of H rows in shared memory and apply
+//                      each block's flips (streaming each flipped row of J
+//                      once for all replicas), a few CTAs run the per-replica
+//                      decision chains of each block of B positions.
+#include <cooperative_groups.h>
+
+#include "pamc_device.cuh"
+#include "pamc_internal.h"
+
+namespace pamc {
+
+namespace {
+
+// ------------------------------------------------------------------ order
+constexpr int kPermThreads = 1024;
+constexpr int kPermBucketBits = 11;   // 2048 buckets
+
+// One CTA per sweep: keys -> bucket by the top bits (counting sort, order
+// within a bucket arbitrary) -> each bucket sorted by (key, index) by one
+// thread.  The result is the unique order by (key, index).
+__global__ void __launch_bounds__(kPermThreads)
+k_dense_perm(int32_t n, uint32_t key0, uint32_t key1, int32_t t, int32_t S,
+             int32_t *__restrict__ perm, uint32_t *__restrict__ skey, int32_t *__restrict__ sidx,
+             const DevCtl *__restrict__ ctl) {
+    constexpr int NB = 1 << kPermBucketBits;
+    __shared__ int32_t cnt[NB];
+    __shared__ int32_t off[NB];
+    if (ctl->done) return;
+    const int32_t sw = blockIdx.x;
+    int32_t *out = perm + (size_t)sw * n;
+    uint32_t *kk = skey + (size_t)sw * n;
+    int32_t *ii = sidx + (size_t)sw * n;
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const uint32_t key = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, kTagPerm << 24, key0, key1).x;
+        atomicAdd(&cnt[key >> (32 - kPermBucketBits)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t a = 0;
+        for (int b = 0; b < NB; ++b) { off[b] = a; a += cnt[b]; }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) cnt[b] = off[b];
+    __syncthreads();
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const uint32_t key = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, kTagPerm << 24, key0, key1).x;
+        const int32_t p = atomicAdd(&cnt[key >> (32 - kPermBucketBits)], 1);
+        kk[p] = key;
+        ii[p] = k;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+        const int32_t lo = off[b], hi = cnt[b];
+        for (int32_t x = lo + 1; x < hi; ++x) {   // insertion sort by (key, index)
+            const uint32_t ck = kk[x];
+            const int32_t ci = ii[x];
+            int32_t y = x - 1;
+            while (y >= lo && (kk[y] > ck || (kk[y] == ck && ii[y] > ci))) {
+                kk[y + 1] = kk[y];
+                ii[y + 1] = ii[y];
+                --y;
+            }
+            kk[y + 1] = ck;
+            ii[y + 1] = ci;
+        }
+        for (int32_t x = lo; x < hi; ++x) out[x] = ii[x];
+    }
+}
+
+// ------------------------------------------------------------------ tables
+// Heat-bath: tab[i] = T(i - Hc), i in [0, 2Hc]; Metropolis: tab[x] = T_M(2x),
+// x in [0, Hc].  When Hc < n the table must reach saturation at its ends
+// (T(Hc) = 2^32, T(-Hc) = 0; T_M(2Hc) = 0), else PAMC_ERR_RANGE.
+__global__ void k_dense_tables(int rule, int32_t Hc, int32_t n, DevCtl *__restrict__ ctl,
+                               uint64_t *__restrict__ tab) {
+    if (ctl->done) return;
+    const double beta = ctl->beta;
+    const int32_t cntv = rule == 0 ? 2 * Hc + 1 : Hc + 1;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cntv; i += gridDim.x * blockDim.x) {
+        uint64_t v;
+        if (rule == 0) v = thr_heatbath(beta, (int64_t)(i - Hc));
+        else v = thr_metropolis(beta, 2 * (int64_t)i);
+        tab[i] = v;
+        if (Hc < n) {
+            if (rule == 0 && i == 0 && v != 0) atomicCAS(&ctl->err, 0, (int)PAMC_ERR_RANGE);
+            if (rule == 0 && i == 2 * Hc && v != (1ull << 32)) atomicCAS(&ctl->err, 0, (int)PAMC_ERR_RANGE);
+            if (rule == 1 && i == Hc && v != 0) atomicCAS(&ctl->err, 0, (int)PAMC_ERR_RANGE);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ recompute
+// H[r][j] = sum_k J[j][k] S[r][k] with mma.m16n8k32 s8 x s8 -> s32 (exact).
+// A = J (row-major, K contiguous), B = S^T (column-major: each replica's
+// spin row is K-contiguous).  One CTA per row slice of kRcRows rows and all
+// (<= 64) replicas; K streamed through shared memory with cp.async.
+constexpr int kRcWarps = 21;                  // 2 m16 tiles per warp
+constexpr int kRcRows = kRcWarps * 32;        // 672 rows per CTA
+constexpr int kRcK = 128;                     // K bytes per stage
+constexpr int kRcAStride = kRcK + 16;         // padded row stride (bank spread)
+constexpr int kRcStageBytes = kRcRows * kRcAStride + 64 * kRcAStride;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    const int sz = pred ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+__global__ void __launch_bounds__(kRcWarps * 32)
+k_dense_recompute(int32_t n, int32_t R, const int8_t *__restrict__ J, const int8_t *__restrict__ src,
+                  const int32_t *__restrict__ parent, const int8_t *__restrict__ ncm_buf,
+                  const int32_t *__restrict__ ncm_idx, int32_t *__restrict__ H,
+                  const DevCtl *__restrict__ ctl, int restart_t) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    // restart_t >= 0: only in the iteration whose controller restarted
+    if (restart_t >= 0 ? !(ctl->restart && ctl->t == restart_t) : ctl->done != 0) return;
+    const int32_t row0 = blockIdx.x * kRcRows;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tig = lane & 3;
+    // replica rows of the resampled population
+    __shared__ const int8_t *rowp[64];
+    if (threadIdx.x < 64) {
+        const int r = threadIdx.x;
+        const int8_t *p = nullptr;
+        if (r < R) {
+            const int32_t q = ncm_idx[r];
+            p = q >= 0 ? ncm_buf + (size_t)q * n : src + (size_t)parent[r] * n;
+        }
+        rowp[r] = p;
+    }
+    __syncthreads();
+    int32_t acc[2][8][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0;
+
+    const int32_t nk = (n + kRcK - 1) / kRcK;
+    auto load_stage = [&](int32_t kc, int stage) {
+        uint8_t *As = sm + (size_t)stage * kRcStageBytes;
+        uint8_t *Bs = As + (size_t)kRcRows * kRcAStride;
+        const int32_t k0 = kc * kRcK;
+        // A: kRcRows rows x kRcK bytes in 16-byte pieces; each piece is either
+        // copied asynchronously (aligned, in range) or written synchronously
+        for (int x = threadIdx.x; x < kRcRows * (kRcK / 16); x += blockDim.x) {
+            const int rr = x / (kRcK / 16), cc = (x % (kRcK / 16)) * 16;
+            const int32_t row = row0 + rr, col = k0 + cc;
+            uint8_t *d = As + rr * kRcAStride + cc;
+            if ((n & 15) == 0 && row < n && col + 16 <= n) {
+                cp_async16(d, J + (size_t)row * n + col, true);
+            } else {
+                for (int q = 0; q < 16; ++q)
+                    d[q] = (row < n && col + q < n) ? (uint8_t)J[(size_t)row * n + col + q] : 0;
+            }
+        }
+        for (int x = threadIdx.x; x < 64 * (kRcK / 16); x += blockDim.x) {
+            const int rr = x / (kRcK / 16), cc = (x % (kRcK / 16)) * 16;
+            const int32_t col = k0 + cc;
+            const int8_t *p = rowp[rr];
+            uint8_t *d = Bs + rr * kRcAStride + cc;
+            if (p != nullptr && col + 16 <= n && (((uintptr_t)(p + col)) & 15) == 0) {
+                cp_async16(d, p + col, true);
+            } else {
+                for (int q = 0; q < 16; ++q)
+                    d[q] = (p != nullptr && col + q < n) ? (uint8_t)p[col + q] : 0;
+            }
+        }
+        cp_async_commit();
+    };
+    load_stage(0, 0);
+    for (int32_t kc = 0; kc < nk; ++kc) {
+        if (kc + 1 < nk) {
+            load_stage(kc + 1, (kc + 1) & 1);
+            cp_async_wait_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const uint8_t *As = sm + (size_t)(kc & 1) * kRcStageBytes;
+        const uint8_t *Bs = As + (size_t)kRcRows * kRcAStride;
+#pragma unroll
+        for (int ks = 0; ks < kRcK; ks += 32) {
+            uint32_t a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+                const uint8_t *ar = As + (size_t)(warp * 32 + mt * 16 + g) * kRcAStride + ks + tig * 4;
+                a[mt][0] = *reinterpret_cast<const uint32_t *>(ar);
+                a[mt][1] = *reinterpret_cast<const uint32_t *>(ar + 8 * kRcAStride);
+                a[mt][2] = *reinterpret_cast<const uint32_t *>(ar + 16);
+                a[mt][3] = *reinterpret_cast<const uint32_t *>(ar + 8 * kRcAStride + 16);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const uint8_t *br = Bs + (size_t)(nt * 8 + g) * kRcAStride + ks + tig * 4;
+                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(br);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(br + 16);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "{%8,%9}, {%0,%1,%2,%3};\n"
+                        : "+r"(acc[mt][nt][0]), "+r"(acc[mt][nt][1]), "+r"(acc[mt][nt][2]),
+                          "+r"(acc[mt][nt][3])
+                        : "r"(a[mt][0]), "r"(a[mt][1]), "r"(a[mt][2]), "r"(a[mt][3]), "r"(b0), "r"(b1));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // C fragment: rows g / g+8, columns (replicas) 2*tig, 2*tig+1
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int32_t row = row0 + warp * 32 + mt * 16 + g + (c >= 2 ? 8 : 0);
+                const int r = nt * 8 + tig * 2 + (c & 1);
+                if (row < n && r < R) H[(size_t)r * n + row] = acc[mt][nt][c];
+            }
+}
+
+// ------------------------------------------------------------------ sweep
+constexpr int kSwThreads = 768;
+constexpr int kB = 256;              // positions per block
+constexpr int kC = kB / 32;          // positions per lane in a chain warp
+constexpr long long kSpinLimit = 1ll << 24;
+
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+};
+
+// Grid-wide barrier for a cooperative launch; every wait is bounded and a
+// wait that runs out sets PAMC_ERR_TIMEOUT and makes the kernel return.
+__device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &gen,
+                             DevCtl *ctl, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long it = 0;
+            while (*(volatile unsigned int *)&bar->gen == gen) {
+                if (++it > kSpinLimit) { atomicCAS(&ctl->err, 0, (int)PAMC_ERR_TIMEOUT); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        if (*(volatile int *)&ctl->err != 0) ok = 0;
+        gen += 1;
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+struct DenseSweepArgs {
+    int32_t n, R, S, rule, Hc;
+    int32_t n_upd;            // CTAs that own H rows (the others run chains)
+    int32_t rows_per;         // rows per update CTA
+    int32_t t;
+    PhiloxKeys K;
+    const int8_t *J;
+    const int32_t *perm;      // [S][n]
+    const uint64_t *tab;
+    const int8_t *src;        // previous population (resampling parents)
+    const int32_t *parent;
+    const int8_t *ncm_buf;
+    const int32_t *ncm_idx;
+    const int32_t *Hin;       // [R][n] recomputed fields
+    int8_t *dst;              // [R][n]
+    int64_t *E;               // [R]
+    int32_t *G;               // [kB][64] published fields of the current block
+    int8_t *T;                // [kB][32][kC] tile J[P][P]
+    unsigned long long *flip; // [2][kB] replica bit masks of flips
+    unsigned long long *snew; // [2][kB] replica bit masks of the new spin (+1)
+    GridBar *bar;
+    DevCtl *ctl;
+};
+
+__global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ int s_ok;
+    if (a.ctl->done) return;
+    const int32_t n = a.n, R = a.R;
+    const unsigned int nblocks = gridDim.x;
+    unsigned int gen = 0;
+    const bool upd = (int)blockIdx.x < a.n_upd;
+    const int32_t nb = (n + kB - 1) / kB;              // blocks per sweep
+    const int32_t total = nb * a.S;                    // blocks of the step
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // ---------------- per-role shared memory
+    // update CTA: Hs[R][rows] int32, spin bits sb[R][(rows+31)/32]
+    // chain CTA : tile[kB*kB] int8, bits[4][(n+31)/32], thr[4][kB], Gs[4][kB]
+    const int32_t ua = upd ? blockIdx.x * a.rows_per : 0;
+    const int32_t ub = upd ? min(n, ua + a.rows_per) : 0;
+    const int32_t rows = ub - ua;
+    const int32_t rw = (a.rows_per + 31) / 32;
+    int32_t *Hs = reinterpret_cast<int32_t *>(sm);
+    uint32_t *ubits = reinterpret_cast<uint32_t *>(sm + (size_t)R * a.rows_per * 4);
+    const int cg = blockIdx.x - a.n_upd;               // chain group (4 replicas)
+    const int32_t nw = (n + 31) / 32;
+    int8_t *tile = reinterpret_cast<int8_t *>(sm);
+    uint32_t *cbits = reinterpret_cast<uint32_t *>(sm + (size_t)kB * kB);
+    int32_t *thr = reinterpret_cast<int32_t *>(cbits + (size_t)4 * nw);
+    int32_t *Gs = thr + 4 * kB;
+
+    if (upd) {
+        for (int32_t x = threadIdx.x; x < R * rows; x += blockDim.x) {
+            const int r = x / rows, j = x % rows;
+            Hs[r * a.rows_per + j] = a.Hin[(size_t)r * n + ua + j];
+        }
+        for (int32_t x = threadIdx.x; x < R * rw; x += blockDim.x) {
+            const int r = x / rw, w = x % rw;
+            const int32_t qn = a.ncm_idx[r];
+            const int8_t *row = qn >= 0 ? a.ncm_buf + (size_t)qn * n : a.src + (size_t)a.parent[r] * n;
+            uint32_t bits = 0;
+            for (int b = 0; b < 32; ++b) {
+                const int32_t j = w * 32 + b;
+                if (j < rows && row[ua + j] > 0) bits |= 1u << b;
+            }
+            ubits[r * rw + w] = bits;
+        }
+    } else {
+        for (int32_t x = threadIdx.x; x < 4 * nw; x += blockDim.x) {
+            const int q = x / nw, w = x % nw;
+            const int r = cg * 4 + q;
+            uint32_t bits = 0;
+            if (r < R) {
+                const int32_t qn = a.ncm_idx[r];
+                const int8_t *row = qn >= 0 ? a.ncm_buf + (size_t)qn * n : a.src + (size_t)a.parent[r] * n;
+                for (int b = 0; b < 32; ++b) {
+                    const int32_t k = w * 32 + b;
+                    if (k < n && row[k] > 0) bits |= 1u << b;
+                }
+            }
+            cbits[x] = bits;
+        }
+        if (blockIdx.x == a.n_upd && threadIdx.x < kB) {   // both mask buffers start empty
+            a.flip[threadIdx.x] = 0ull; a.flip[kB + threadIdx.x] = 0ull;
+            a.snew[threadIdx.x] = 0ull; a.snew[kB + threadIdx.x] = 0ull;
+        }
+        if (blockIdx.x == a.n_upd && threadIdx.x < 64) a.E[threadIdx.x < R ? threadIdx.x : 0] = 0;
+    }
+    if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) return;
+
+    for (int32_t q = 0; q <= total; ++q) {
+        // ================= phase A: apply block q-1, publish block q
+        if (upd) {
+            if (q > 0) {
+                const int32_t qp = q - 1;
+                const int32_t swp = qp / nb, bp = qp % nb;
+                const int32_t *P = a.perm + (size_t)swp * n + (size_t)bp * kB;
+                const int32_t cntp = min(kB, n - bp * kB);
+                const unsigned long long *fm = a.flip + (qp & 1) * kB;
+                const unsigned long long *sn = a.snew + (qp & 1) * kB;
+                const int32_t j = threadIdx.x;
+                for (int32_t m = 0; m < cntp; ++m) {
+                    const unsigned long long f = fm[m];
+                    if (f == 0ull) continue;
+                    const int32_t p = P[m];
+                    const unsigned long long s = sn[m];
+                    if (j < rows) {
+                        const int32_t jv = (int32_t)a.J[(size_t)p * n + ua + j];
+                        unsigned long long ff = f;
+                        while (ff) {
+                            const int r = __ffsll((long long)ff) - 1;
+                            ff &= ff - 1;
+                            const int32_t d = ((s >> r) & 1ull) ? 2 : -2;
+                            Hs[r * a.rows_per + j] += d * jv;
+                        }
+                    }
+                    if (p >= ua && p < ub && threadIdx.x == 0) {
+                        const int32_t lj = p - ua;
+                        unsigned long long ff = f;
+                        while (ff) {
+                            const int r = __ffsll((long long)ff) - 1;
+                            ff &= ff - 1;
+                            ubits[r * rw + (lj >> 5)] ^= 1u << (lj & 31);
+                        }
+                    }
+                }
+            }
+            if (q < total) {
+                const int32_t sw = q / nb, b = q % nb;
+                const int32_t *P = a.perm + (size_t)sw * n + (size_t)b * kB;
+                const int32_t cnt = min(kB, n - b * kB);
+                __syncthreads();
+                // publish the fields of this block's positions that this CTA owns
+                for (int32_t x = threadIdx.x; x < cnt * R; x += blockDim.x) {
+                    const int32_t m = x / R, r = x % R;
+                    const int32_t p = P[m];
+                    if (p >= ua && p < ub) a.G[m * 64 + r] = Hs[r * a.rows_per + (p - ua)];
+                }
+                // gather part of the tile J[P][P] (layout [m][lane][slot])
+                const int32_t per = (kB * kB + a.n_upd - 1) / a.n_upd;
+                const int32_t e0 = blockIdx.x * per, e1 = min(kB * kB, e0 + per);
+                for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+                    const int32_t m = e / kB, m2 = e % kB;
+                    int8_t v = 0;
+                    if (m < cnt && m2 < cnt) v = a.J[(size_t)P[m] * n + P[m2]];
+                    a.T[(size_t)m * kB + (m2 & 31) * kC + (m2 >> 5)] = v;
+                }
+            }
+        } else if (q < total) {
+            // chain CTA: thresholds of block q for its 4 replicas; clear the
+            // mask buffer that block q will fill
+            const int32_t sw = q / nb, b = q % nb;
+            const int32_t *P = a.perm + (size_t)sw * n + (size_t)b * kB;
+            const int32_t cnt = min(kB, n - b * kB);
+            if (blockIdx.x == a.n_upd && threadIdx.x < kB) {
+                a.flip[(q & 1) * kB + threadIdx.x] = 0ull;
+                a.snew[(q & 1) * kB + threadIdx.x] = 0ull;
+            }
+            for (int32_t m = threadIdx.x; m < cnt; m += blockDim.x) {
+                const u32x4 u = philox_rk((uint32_t)P[m], (uint32_t)sw, (uint32_t)a.t,
+                                          (kTagFlip << 24) | (uint32_t)cg, a.K);
+                const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    int32_t res;
+                    if (a.rule == 0) {
+                        // smallest h with T(h) > u  (s = +1 iff h >= res)
+                        int32_t lo = 0, hi = 2 * a.Hc + 1;
+                        while (lo < hi) {
+                            const int32_t mid = (lo + hi) >> 1;
+                            if (a.tab[mid] > (uint64_t)uw[qq]) hi = mid; else lo = mid + 1;
+                        }
+                        res = lo - a.Hc;
+                    } else {
+                        // largest x with T_M(2x) > u  (flip iff s*h <= res)
+                        int32_t lo = 0, hi = a.Hc;
+                        while (lo < hi) {
+                            const int32_t mid = (lo + hi + 1) >> 1;
+                            if (a.tab[mid] > (uint64_t)uw[qq]) lo = mid; else hi = mid - 1;
+                        }
+                        res = (lo == a.Hc && a.Hc >= n) ? n + 1 : lo;
+                    }
+                    thr[qq * kB + m] = res;
+                }
+            }
+        }
+        if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) return;
+        if (q == total) break;
+
+        // ================= phase B: decision chains of block q
+        if (!upd) {
+            const int32_t sw = q / nb, b = q % nb;
+            const int32_t *P = a.perm + (size_t)sw * n + (size_t)b * kB;
+            const int32_t cnt = min(kB, n - b * kB);
+            for (int32_t x = threadIdx.x; x < kB * kB / 16; x += blockDim.x)
+                reinterpret_cast<int4 *>(tile)[x] = reinterpret_cast<const int4 *>(a.T)[x];
+            for (int32_t x = threadIdx.x; x < 4 * cnt; x += blockDim.x) {
+                const int qq = x / cnt, m = x % cnt;
+                const int r = cg * 4 + qq;
+                Gs[qq * kB + m] = r < R ? a.G[m * 64 + r] : 0;
+            }
+            __syncthreads();
+            if (warp < 4 && cg * 4 + warp < R) {
+                const int qq = warp;
+                const int r = cg * 4 + qq;
+                uint32_t *bits = cbits + (size_t)qq * nw;
+                int32_t f[kC];
+#pragma unroll
+                for (int s2 = 0; s2 < kC; ++s2) {
+                    const int32_t m = s2 * 32 + lane;
+                    f[s2] = m < cnt ? Gs[qq * kB + m] : 0;
+                }
+#pragma unroll
+                for (int s2 = 0; s2 < kC; ++s2) {
+                    for (int o = 0; o < 32; ++o) {
+                        const int32_t m = s2 * 32 + o;
+                        if (m >= cnt) break;
+                        const int32_t hm = __shfl_sync(0xffffffffu, f[s2], o);
+                        const int32_t k = P[m];
+                        const uint32_t sold = (bits[k >> 5] >> (k & 31)) & 1u;
+                        const int32_t th = thr[qq * kB + m];
+                        uint32_t snv;
+                        if (a.rule == 0) {
+                            snv = hm >= th ? 1u : 0u;
+                        } else {
+                            const int32_t x = sold ? hm : -hm;
+                            snv = x <= th ? (sold ^ 1u) : sold;
+                        }
+                        if (snv != sold) {
+                            const int32_t d = snv ? 2 : -2;
+                            const int2 tv = *reinterpret_cast<const int2 *>(tile + (size_t)m * kB + lane * kC);
+#pragma unroll
+                            for (int s3 = 0; s3 < kC; ++s3) {
+                                const uint32_t word = s3 < 4 ? (uint32_t)tv.x : (uint32_t)tv.y;
+                                const int32_t jv = (int32_t)(int8_t)((word >> (8 * (s3 & 3))) & 0xFFu);
+                                f[s3] += d * jv;
+                            }
+                            if (lane == 0) {
+                                bits[k >> 5] ^= 1u << (k & 31);
+                                atomicOr(&a.flip[(q & 1) * kB + m], 1ull << r);
+                                if (snv) atomicOr(&a.snew[(q & 1) * kB + m], 1ull << r);
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
+            }
+        }
+        if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) return;
+    }
+
+    // ---------------- energies E_r = -1/2 sum_j s_j h_j, spins back to HBM
+    if (upd) {
+        for (int r = 0; r < R; ++r) {
+            long long accv = 0;
+            for (int32_t j = threadIdx.x; j < rows; j += blockDim.x) {
+                const int32_t s = ((ubits[r * rw + (j >> 5)] >> (j & 31)) & 1u) ? 1 : -1;
+                accv += (long long)s * Hs[r * a.rows_per + j];
+            }
+            for (int o = 16; o > 0; o >>= 1) accv += __shfl_down_sync(0xffffffffu, accv, o);
+            if (lane == 0 && accv != 0) atomicAdd((unsigned long long *)&a.E[r], (unsigned long long)accv);
+        }
+    } else {
+        for (int32_t x = threadIdx.x; x < 4 * n; x += blockDim.x) {
+            const int qq = x / n;
+            const int32_t k = x % n;
+            const int r = cg * 4 + qq;
+            if (r < R) a.dst[(size_t)r * n + k] = ((cbits[qq * nw + (k >> 5)] >> (k & 31)) & 1u) ? 1 : -1;
+        }
+    }
+}
+
+// E_r = -1/2 sum_j s_j h_j from recomputed fields (one CTA per replica)
+__global__ void k_dense_energy_from_H(int32_t n, const int32_t *__restrict__ H,
+                                      const int8_t *__restrict__ spins, int64_t *__restrict__ E,
+                                      const DevCtl *__restrict__ ctl, int restart_t) {
+    __shared__ long long red[32];
+    if (restart_t >= 0 ? !(ctl->restart && ctl->t == restart_t) : ctl->done != 0) return;
+    const int r = blockIdx.x;
+    long long acc = 0;
+    for (int32_t j = threadIdx.x; j < n; j += blockDim.x)
+        acc += (long long)spins[(size_t)r * n + j] * H[(size_t)r * n + j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        E[r] = -(tot / 2);
+    }
+}
+
+// Max-Cut weights -> couplings in place (J = -w), and W = sum_{i<j} w_ij.
+__global__ void k_dense_negate_sum(size_t total, int8_t *__restrict__ J,
+                                   unsigned long long *__restrict__ wsum) {
+    long long acc = 0;
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total;
+         x += (size_t)gridDim.x * blockDim.x) {
+        const int8_t v = J[x];
+        acc += v;
+        J[x] = (int8_t)(-v);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0) atomicAdd(wsum, (unsigned long long)acc);
+}
+
+// the accumulated sum_j s_j h_j becomes E = -sum/2
+__global__ void k_dense_energy_finish(int32_t R, int64_t *E, const DevCtl *ctl) {
+    if (ctl->done) return;
+    const int r = threadIdx.x;
+    if (r < R) E[r] = -(E[r] / 2);
+}
+
+// Validation of a device-resident copy: entries in {-1, 0, +1}, zero diagonal,
+// +-1 off the diagonal, symmetric.  32x32 tiles compared with their transpose.
+__global__ void k_dense_validate(int32_t n, const int8_t *__restrict__ J, int *__restrict__ err) {
+    __shared__ int8_t tl[32][33];
+    const int32_t bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+    if (bj < bi) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int yy = ty; yy < 32; yy += blockDim.x / 32) {
+        const int32_t i = bj + yy, j = bi + tx;
+        tl[yy][tx] = (i < n && j < n) ? J[(size_t)i * n + j] : 0;
+    }
+    __syncthreads();
+    for (int yy = ty; yy < 32; yy += blockDim.x / 32) {
+        const int32_t i = bi + yy, j = bj + tx;
+        if (i < n && j < n) {
+            const int8_t v = J[(size_t)i * n + j];
+            if (i == j) { if (v != 0) atomicCAS(err, 0, (int)PAMC_ERR_DIAG); }
+            else if (v != 1 && v != -1) atomicCAS(err, 0, (int)PAMC_ERR_RANGE);
+            else if (v != tl[tx][yy]) atomicCAS(err, 0, (int)PAMC_ERR_ASYM);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_dense_validate(int32_t n, const int8_t *J, int *err, cudaStream_t st) {
+    const int nt = (n + 31) / 32;
+    k_dense_validate<<<dim3(nt, nt), 256, 0, st>>>(n, J, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_perm(int32_t n, uint64_t seed, int32_t t, int32_t S, int32_t *perm,
+                              uint32_t *skey, int32_t *sidx, const DevCtl *ctl, cudaStream_t st) {
+    if (S <= 0) return cudaSuccess;
+    k_dense_perm<<<S, kPermThreads, 0, st>>>(n, (uint32_t)seed, (uint32_t)(seed >> 32), t, S, perm,
+                                            skey, sidx, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_tables(int rule, int32_t Hc, int32_t n, DevCtl *ctl, uint64_t *tab,
+                                cudaStream_t st) {
+    const int32_t cntv = rule == 0 ? 2 * Hc + 1 : Hc + 1;
+    int grid = (cntv + 255) / 256;
+    if (grid > 304) grid = 304;
+    k_dense_tables<<<grid, 256, 0, st>>>(rule, Hc, n, ctl, tab);
+    return cudaGetLastError();
+}
+
+size_t dense_recompute_smem() { return 2 * (size_t)kRcStageBytes; }
+
+cudaError_t launch_dense_recompute(int32_t n, int32_t R, const int8_t *J, const int8_t *src,
+                                   const int32_t *parent, const int8_t *ncm_buf,
+                                   const int32_t *ncm_idx, int32_t *H, const DevCtl *ctl,
+                                   cudaStream_t st, int restart_t) {
+    const size_t smem = dense_recompute_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_dense_recompute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (n + kRcRows - 1) / kRcRows;
+    k_dense_recompute<<<grid, kRcWarps * 32, smem, st>>>(n, R, J, src, parent, ncm_buf, ncm_idx, H, ctl,
+                                                           restart_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_energy(int32_t n, int32_t R, const int32_t *H, const int8_t *spins, int64_t *E,
+                                const DevCtl *ctl, cudaStream_t st, int restart_t) {
+    k_dense_energy_from_H<<<R, 512, 0, st>>>(n, H, spins, E, ctl, restart_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_negate_sum(size_t total, int8_t *J, unsigned long long *wsum, cudaStream_t st) {
+    k_dense_negate_sum<<<152 * 8, 256, 0, st>>>(total, J, wsum);
+    return cudaGetLastError();
+}
+
+int dense_block_positions() { return kB; }
+
+// Shared memory of the sweep kernel for a given split.
+size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per) {
+    const size_t upd = (size_t)R * rows_per * 4 + (size_t)R * ((rows_per + 31) / 32) * 4;
+    const size_t chn = (size_t)kB * kB + (size_t)4 * ((n + 31) / 32) * 4 + (size_t)8 * kB * 4;
+    return upd > chn ? upd : chn;
+}
+
+cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, int32_t Hc, int32_t t,
+                               uint64_t seed, int32_t n_upd, int32_t rows_per, int32_t grid,
+                               const int8_t *J, const int32_t *perm, const uint64_t *tab,
+                               const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
+                               const int32_t *ncm_idx, const int32_t *Hin, int8_t *dst, int64_t *E,
+                               int32_t *G, int8_t *T, unsigned long long *flip,
+                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st) {
+    DenseSweepArgs a;
+    a.n = n; a.R = R; a.S = S; a.rule = rule; a.Hc = Hc; a.n_upd = n_upd; a.rows_per = rows_per;
+    a.t = t; a.K = make_philox_keys(seed); a.J = J; a.perm = perm; a.tab = tab; a.src = src;
+    a.parent = parent; a.ncm_buf = ncm_buf; a.ncm_idx = ncm_idx; a.Hin = Hin; a.dst = dst; a.E = E;
+    a.G = G; a.T = T; a.flip = flip; a.snew = snew; a.bar = reinterpret_cast<GridBar *>(bar); a.ctl = ctl;
+    const size_t smem = dense_sweep_smem(n, R, rows_per);
+    cudaError_t e = cudaFuncSetAttribute(k_dense_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(bar, 0, sizeof(GridBar), st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&a};
+    e = cudaLaunchCooperativeKernel((const void *)k_dense_sweep, dim3(grid), dim3(kSwThreads), args,
+                                    smem, st);
+    if (e != cudaSuccess) return e;
+    k_dense_energy_finish<<<1, 64, 0, st>>>(R, E, ctl);
+    return cudaGetLastError();
+}
+
+int dense_sweep_threads() { return kSwThreads; }
+
+}  // namespace pamc

@@ -84,4 +84,31 @@ cudaError_t launch_init(int kind, int32_t n, const int32_t *rp, const uint32_t *
                         uint64_t seed, int32_t t, int only_if_restart, const DevCtl *ctl,
                         int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st);
 
+// ---- dense instances (dense.cu)
+cudaError_t launch_dense_validate(int32_t n, const int8_t *J, int *err, cudaStream_t st);
+cudaError_t launch_dense_negate_sum(size_t total, int8_t *J, unsigned long long *wsum, cudaStream_t st);
+cudaError_t launch_dense_perm(int32_t n, uint64_t seed, int32_t t, int32_t S, int32_t *perm,
+                              uint32_t *skey, int32_t *sidx, const DevCtl *ctl, cudaStream_t st);
+cudaError_t launch_dense_tables(int rule, int32_t Hc, int32_t n, DevCtl *ctl, uint64_t *tab,
+                                cudaStream_t st);
+size_t dense_recompute_smem();
+cudaError_t launch_dense_recompute(int32_t n, int32_t R, const int8_t *J, const int8_t *src,
+                                   const int32_t *parent, const int8_t *ncm_buf,
+                                   const int32_t *ncm_idx, int32_t *H, const DevCtl *ctl,
+                                   cudaStream_t st, int restart_t);
+cudaError_t launch_dense_energy(int32_t n, int32_t R, const int32_t *H, const int8_t *spins, int64_t *E,
+                                const DevCtl *ctl, cudaStream_t st, int restart_t);
+cudaError_t launch_init_spins(int kind, int32_t n, int32_t R, uint64_t seed, int32_t t,
+                              int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st);
+int dense_block_positions();
+int dense_sweep_threads();
+size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per);
+cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, int32_t Hc, int32_t t,
+                               uint64_t seed, int32_t n_upd, int32_t rows_per, int32_t grid,
+                               const int8_t *J, const int32_t *perm, const uint64_t *tab,
+                               const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
+                               const int32_t *ncm_idx, const int32_t *Hin, int8_t *dst, int64_t *E,
+                               int32_t *G, int8_t *T, unsigned long long *flip,
+                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st);
+
 }  // namespace pamc

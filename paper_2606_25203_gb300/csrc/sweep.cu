@@ -266,7 +266,9 @@ k_sweep(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t
 __global__ void k_init_spins(int kind, int32_t n, int32_t R, uint32_t key0, uint32_t key1,
                              int32_t t, int only_if_restart, const DevCtl *__restrict__ ctl,
                              int8_t *__restrict__ spins) {
-    if (only_if_restart && !(ctl->restart && !ctl->done)) return;
+    // a restart re-draws the population in the iteration that restarted
+    // (the controller has then advanced t to the key t)
+    if (only_if_restart && !(ctl->restart && ctl->t == t)) return;
     const int32_t groups = (R + 3) / 4;
     const size_t total = (size_t)groups * n;
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total;
@@ -289,9 +291,9 @@ __global__ void k_init_spins(int kind, int32_t n, int32_t R, uint32_t key0, uint
 // Energy of every replica from the definition (one CTA per replica).
 __global__ void k_energy(int kind, int32_t n, const int32_t *__restrict__ rp,
                          const uint32_t *__restrict__ adj, int32_t R, int only_if_restart,
-                         const DevCtl *__restrict__ ctl, int64_t Wsum,
+                         const DevCtl *__restrict__ ctl, int64_t Wsum, int32_t t,
                          const int8_t *__restrict__ spins, int64_t *__restrict__ E) {
-    if (only_if_restart && !(ctl->restart && !ctl->done)) return;
+    if (only_if_restart && !(ctl->restart && ctl->t == t)) return;
     __shared__ long long red[32];
     const int32_t r = blockIdx.x;
     const int8_t *s = spins + (size_t)r * n;
@@ -371,7 +373,18 @@ cudaError_t launch_init(int kind, int32_t n, const int32_t *rp, const uint32_t *
     if (grid < 1) grid = 1;
     k_init_spins<<<grid, 256, 0, st>>>(kind, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
                                         only_if_restart, ctl, spins);
-    k_energy<<<R, 256, 0, st>>>(kind, n, rp, adj, R, only_if_restart, ctl, Wsum, spins, E);
+    k_energy<<<R, 256, 0, st>>>(kind, n, rp, adj, R, only_if_restart, ctl, Wsum, t, spins, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_spins(int kind, int32_t n, int32_t R, uint64_t seed, int32_t t,
+                              int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st) {
+    const size_t total = (size_t)((R + 3) / 4) * n;
+    int grid = (int)((total + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    k_init_spins<<<grid, 256, 0, st>>>(kind, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
+                                        only_if_restart, ctl, spins);
     return cudaGetLastError();
 }
 
