@@ -88,7 +88,7 @@ struct pamc_handle_s {
     int32_t *d_H = nullptr;              // [R][n] fields
     int32_t *d_perm = nullptr, *d_sidx = nullptr, *d_G = nullptr, *d_ident = nullptr, *d_nonc = nullptr;
     uint32_t *d_pkey = nullptr;
-    int8_t *d_T = nullptr;
+    int8_t *d_T = nullptr, *d_T2 = nullptr;
     unsigned long long *d_flip = nullptr, *d_snew = nullptr;
     void *d_bar = nullptr;
     int32_t dense_Hc = 0, dense_grid = 0, dense_nupd = 0, dense_rows = 0;
@@ -270,9 +270,9 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
               alloc_n(h, h->d_tab, tabn, h->bufs) && alloc_n(h, h->d_ctl, 1, h->bufs) &&
               alloc_n(h, h->d_best, n, h->bufs) && alloc_n(h, h->d_H, (size_t)R * n, h->bufs) &&
               alloc_n(h, h->d_perm, (size_t)S * n, h->bufs) && alloc_n(h, h->d_pkey, (size_t)S * n, h->bufs) &&
-              alloc_n(h, h->d_sidx, (size_t)S * n, h->bufs) && alloc_n(h, h->d_G, (size_t)B * 64, h->bufs) &&
-              alloc_n(h, h->d_T, (size_t)B * B, h->bufs) && alloc_n(h, h->d_flip, (size_t)2 * B, h->bufs) &&
-              alloc_n(h, h->d_snew, (size_t)2 * B, h->bufs) &&
+              alloc_n(h, h->d_sidx, (size_t)S * n, h->bufs) && alloc_n(h, h->d_G, (size_t)2 * B * 64, h->bufs) &&
+              alloc_n(h, h->d_T, (size_t)2 * B * B, h->bufs) && alloc_n(h, h->d_T2, (size_t)2 * B * B, h->bufs) &&
+              alloc_n(h, h->d_flip, (size_t)3 * B, h->bufs) && alloc_n(h, h->d_snew, (size_t)3 * B, h->bufs) &&
               (h->d_bar = dev_alloc(h, 64, h->bufs)) != nullptr &&
               alloc_n(h, h->d_ident, R, h->bufs) && alloc_n(h, h->d_nonc, R, h->bufs);
     if (!ok) {
@@ -335,7 +335,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
             e = launch_dense_sweep(n, R, p.sweeps, p.rule, h->dense_Hc, (int32_t)t, p.seed, h->dense_nupd,
                                    h->dense_rows, h->dense_grid, h->d_J, h->d_perm, h->d_tab, src,
                                    h->d_parent, nullptr, h->d_ncm_idx, h->d_H, dst, Ed, h->d_G, h->d_T,
-                                   h->d_flip, h->d_snew, h->d_bar, h->d_ctl, h->stream);
+                                   h->d_T2, h->d_flip, h->d_snew, h->d_bar, h->d_ctl, h->stream);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 7;
         if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
@@ -440,6 +440,7 @@ pamc_status pamc_create_dense(int32_t n, const int8_t *w, int w_on_device, int c
     if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(*d_err), h->stream);
     if (e == cudaSuccess) e = launch_dense_negate_sum(total, h->d_J, d_sum, h->stream);
     if (e == cudaSuccess) e = launch_dense_validate(n, h->d_J, d_err, h->stream);
+    if (e == cudaSuccess) e = launch_dense_to_e4m3(total, h->d_J, h->stream);   // stored as e4m3 bytes
     unsigned long long wsum = 0;
     int err = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&wsum, d_sum, sizeof(wsum), cudaMemcpyDeviceToHost, h->stream);

@@ -103,27 +103,75 @@ __global__ void k_dense_tables(int rule, int32_t Hc, int32_t n, DevCtl *__restri
 }
 
 // ------------------------------------------------------------------ recompute
-// H[r][j] = sum_k J[j][k] S[r][k] with mma.m16n8k32 s8 x s8 -> s32 (exact).
-// A = J (row-major, K contiguous), B = S^T (column-major: each replica's
-// spin row is K-contiguous).  One CTA per row slice of kRcRows rows and all
+// H[r][j] = sum_k J[j][k] S[r][k] with mma.m16n8k32 e4m3 x e4m3 -> f32.  J is
+// stored in HBM as e4m3 bytes (+-1 and 0 are exact), the spins are converted
+// to e4m3 while staged.  Every product is +-1 or 0 and every partial sum an
+// integer of magnitude < 2^24, so the f32 result is the exact integer field
+// (checked at |h| = n-1 by the adversarial recompute test).
+// A = J (row-major, K contiguous), B = S^T (column-major: each replica's spin
+// row is K-contiguous).  One CTA per row slice of kRcRows rows and all
 // (<= 64) replicas; K streamed through shared memory with cp.async.
 constexpr int kRcWarps = 21;                  // 2 m16 tiles per warp
 constexpr int kRcRows = kRcWarps * 32;        // 672 rows per CTA
-constexpr int kRcK = 128;                     // K bytes per stage
+constexpr int kRcK = 64;                      // K bytes per stage
+constexpr int kRcStages = 3;                  // stages in flight
 constexpr int kRcAStride = kRcK + 16;         // padded row stride (bank spread)
 constexpr int kRcStageBytes = kRcRows * kRcAStride + 64 * kRcAStride;
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pred) {
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-    const int sz = pred ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-__global__ void __launch_bounds__(kRcWarps * 32)
-k_dense_recompute(int32_t n, int32_t R, const int8_t *__restrict__ J, const int8_t *__restrict__ src,
+// +-1 int8 spins -> e4m3 (+1.0 = 0x38, -1.0 = 0xB8), four at a time
+__device__ __forceinline__ uint32_t spins_to_e4m3(uint32_t x) { return (x & 0x80808080u) | 0x38383838u; }
+
+// e4m3 coupling byte (0x38, 0xB8 or 0) -> +1, -1, 0
+__device__ __forceinline__ int32_t e4m3_pm1(uint32_t b) {
+    return ((int32_t)(int8_t)(uint8_t)b >> 7) | (int32_t)(b != 0u);
+}
+
+// stage kc of J rows and e4m3 spins into shared stage buffer `stage`
+__device__ __forceinline__ void rc_load_stage(uint8_t *sm, const uint8_t *__restrict__ J,
+                                              const int8_t *const *rowp, int32_t n, int32_t row0,
+                                              int32_t kc, int stage) {
+        uint8_t *As = sm + (size_t)stage * kRcStageBytes;
+        uint8_t *Bs = As + (size_t)kRcRows * kRcAStride;
+        const int32_t k0 = kc * kRcK;
+        // each 16-byte piece is either copied asynchronously (aligned, in
+        // range) or written synchronously -- never both
+        for (int x = threadIdx.x; x < kRcRows * (kRcK / 16); x += blockDim.x) {
+            const int rr = x / (kRcK / 16), cc = (x % (kRcK / 16)) * 16;
+            const int32_t row = row0 + rr, col = k0 + cc;
+            uint8_t *d = As + rr * kRcAStride + cc;
+            if ((n & 15) == 0 && row < n && col + 16 <= n) {
+                cp_async16(d, J + (size_t)row * n + col);
+            } else {
+                for (int q = 0; q < 16; ++q)
+                    d[q] = (row < n && col + q < n) ? J[(size_t)row * n + col + q] : (uint8_t)0;
+            }
+        }
+        for (int x = threadIdx.x; x < 64 * (kRcK / 16); x += blockDim.x) {
+            const int rr = x / (kRcK / 16), cc = (x % (kRcK / 16)) * 16;
+            const int32_t col = k0 + cc;
+            const int8_t *p = rowp[rr];
+            uint8_t *d = Bs + rr * kRcAStride + cc;
+            // raw +-1 spins, converted to e4m3 when the fragments are read;
+            // padding is harmless (J is zero there or the replica is unused)
+            if (p != nullptr && col + 16 <= n && (((uintptr_t)(p + col)) & 15) == 0) {
+                cp_async16(d, p + col);
+            } else {
+                for (int q = 0; q < 16; ++q) d[q] = (p != nullptr && col + q < n) ? (uint8_t)p[col + q] : (uint8_t)1;
+            }
+        }
+        cp_async_commit();
+    }
+
+__global__ void __launch_bounds__(kRcWarps * 32, 1)
+k_dense_recompute(int32_t n, int32_t R, const uint8_t *__restrict__ J, const int8_t *__restrict__ src,
                   const int32_t *__restrict__ parent, const int8_t *__restrict__ ncm_buf,
                   const int32_t *__restrict__ ncm_idx, int32_t *__restrict__ H,
                   const DevCtl *__restrict__ ctl, int restart_t) {
@@ -133,7 +181,6 @@ k_dense_recompute(int32_t n, int32_t R, const int8_t *__restrict__ J, const int8
     const int32_t row0 = blockIdx.x * kRcRows;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tig = lane & 3;
-    // replica rows of the resampled population
     __shared__ const int8_t *rowp[64];
     if (threadIdx.x < 64) {
         const int r = threadIdx.x;
@@ -145,56 +192,28 @@ k_dense_recompute(int32_t n, int32_t R, const int8_t *__restrict__ J, const int8
         rowp[r] = p;
     }
     __syncthreads();
-    int32_t acc[2][8][4];
+    float acc[2][8][4];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0;
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
 
     const int32_t nk = (n + kRcK - 1) / kRcK;
-    auto load_stage = [&](int32_t kc, int stage) {
-        uint8_t *As = sm + (size_t)stage * kRcStageBytes;
-        uint8_t *Bs = As + (size_t)kRcRows * kRcAStride;
-        const int32_t k0 = kc * kRcK;
-        // A: kRcRows rows x kRcK bytes in 16-byte pieces; each piece is either
-        // copied asynchronously (aligned, in range) or written synchronously
-        for (int x = threadIdx.x; x < kRcRows * (kRcK / 16); x += blockDim.x) {
-            const int rr = x / (kRcK / 16), cc = (x % (kRcK / 16)) * 16;
-            const int32_t row = row0 + rr, col = k0 + cc;
-            uint8_t *d = As + rr * kRcAStride + cc;
-            if ((n & 15) == 0 && row < n && col + 16 <= n) {
-                cp_async16(d, J + (size_t)row * n + col, true);
-            } else {
-                for (int q = 0; q < 16; ++q)
-                    d[q] = (row < n && col + q < n) ? (uint8_t)J[(size_t)row * n + col + q] : 0;
-            }
-        }
-        for (int x = threadIdx.x; x < 64 * (kRcK / 16); x += blockDim.x) {
-            const int rr = x / (kRcK / 16), cc = (x % (kRcK / 16)) * 16;
-            const int32_t col = k0 + cc;
-            const int8_t *p = rowp[rr];
-            uint8_t *d = Bs + rr * kRcAStride + cc;
-            if (p != nullptr && col + 16 <= n && (((uintptr_t)(p + col)) & 15) == 0) {
-                cp_async16(d, p + col, true);
-            } else {
-                for (int q = 0; q < 16; ++q)
-                    d[q] = (p != nullptr && col + q < n) ? (uint8_t)p[col + q] : 0;
-            }
-        }
-        cp_async_commit();
-    };
-    load_stage(0, 0);
+    for (int st = 0; st < kRcStages - 1; ++st) {
+        if (st < nk) rc_load_stage(sm, J, rowp, n, row0, st, st);
+        else cp_async_commit();
+    }
     for (int32_t kc = 0; kc < nk; ++kc) {
-        if (kc + 1 < nk) {
-            load_stage(kc + 1, (kc + 1) & 1);
-            cp_async_wait_one();
-        } else {
-            cp_async_wait_all();
-        }
+        // keep kRcStages-1 stages in flight
+        if (kc + kRcStages - 1 < nk)
+            rc_load_stage(sm, J, rowp, n, row0, kc + kRcStages - 1, (kc + kRcStages - 1) % kRcStages);
+        else
+            cp_async_commit();
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kRcStages - 1));
         __syncthreads();
-        const uint8_t *As = sm + (size_t)(kc & 1) * kRcStageBytes;
+        const uint8_t *As = sm + (size_t)(kc % kRcStages) * kRcStageBytes;
         const uint8_t *Bs = As + (size_t)kRcRows * kRcAStride;
 #pragma unroll
         for (int ks = 0; ks < kRcK; ks += 32) {
@@ -210,21 +229,22 @@ k_dense_recompute(int32_t n, int32_t R, const int8_t *__restrict__ J, const int8
 #pragma unroll
             for (int nt = 0; nt < 8; ++nt) {
                 const uint8_t *br = Bs + (size_t)(nt * 8 + g) * kRcAStride + ks + tig * 4;
-                const uint32_t b0 = *reinterpret_cast<const uint32_t *>(br);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t *>(br + 16);
+                const uint32_t b0 = spins_to_e4m3(*reinterpret_cast<const uint32_t *>(br));
+                const uint32_t b1 = spins_to_e4m3(*reinterpret_cast<const uint32_t *>(br + 16));
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt) {
                     asm volatile(
-                        "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
                         "{%8,%9}, {%0,%1,%2,%3};\n"
-                        : "+r"(acc[mt][nt][0]), "+r"(acc[mt][nt][1]), "+r"(acc[mt][nt][2]),
-                          "+r"(acc[mt][nt][3])
+                        : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]),
+                          "+f"(acc[mt][nt][3])
                         : "r"(a[mt][0]), "r"(a[mt][1]), "r"(a[mt][2]), "r"(a[mt][3]), "r"(b0), "r"(b1));
                 }
             }
         }
         __syncthreads();
     }
+    cp_async_wait_all();
     // C fragment: rows g / g+8, columns (replicas) 2*tig, 2*tig+1
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
@@ -234,7 +254,7 @@ k_dense_recompute(int32_t n, int32_t R, const int8_t *__restrict__ J, const int8
             for (int c = 0; c < 4; ++c) {
                 const int32_t row = row0 + warp * 32 + mt * 16 + g + (c >= 2 ? 8 : 0);
                 const int r = nt * 8 + tig * 2 + (c & 1);
-                if (row < n && r < R) H[(size_t)r * n + row] = acc[mt][nt][c];
+                if (row < n && r < R) H[(size_t)r * n + row] = __float2int_rn(acc[mt][nt][c]);
             }
 }
 
@@ -242,15 +262,22 @@ k_dense_recompute(int32_t n, int32_t R, const int8_t *__restrict__ J, const int8
 constexpr int kSwThreads = 768;
 constexpr int kB = 256;              // positions per block
 constexpr int kC = kB / 32;          // positions per lane in a chain warp
-constexpr long long kSpinLimit = 1ll << 24;
+constexpr int kWin = 4096;           // threshold entries kept in shared memory
+constexpr long long kBarCycles = 4000000000ll;   // ~2 s: a barrier wait gives up after this
 
 struct GridBar {
     unsigned int count;
     unsigned int gen;
 };
 
-// Grid-wide barrier for a cooperative launch; every wait is bounded and a
-// wait that runs out sets PAMC_ERR_TIMEOUT and makes the kernel return.
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperative launch.  The wait is bounded by the
+// clock: after kBarCycles it sets PAMC_ERR_TIMEOUT and the kernel returns.
 __device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &gen,
                              DevCtl *ctl, int *s_ok) {
     __syncthreads();
@@ -263,13 +290,19 @@ __device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &g
             __threadfence();
             atomicAdd(&bar->gen, 1u);
         } else {
-            long long it = 0;
-            while (*(volatile unsigned int *)&bar->gen == gen) {
-                if (++it > kSpinLimit) { atomicCAS(&ctl->err, 0, (int)PAMC_ERR_TIMEOUT); ok = 0; break; }
-                __nanosleep(64);
+            const long long start = clock64();
+            int spins = 0;
+            while (ld_acquire_u32(&bar->gen) == gen) {
+                if (++spins > 64) {
+                    __nanosleep(32);
+                    if (clock64() - start > kBarCycles) {
+                        atomicCAS(&ctl->err, 0, (int)PAMC_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
             }
         }
-        if (*(volatile int *)&ctl->err != 0) ok = 0;
         gen += 1;
         __threadfence();
         *s_ok = ok;
@@ -284,27 +317,39 @@ struct DenseSweepArgs {
     int32_t rows_per;         // rows per update CTA
     int32_t t;
     PhiloxKeys K;
-    const int8_t *J;
+    const uint8_t *J;         // e4m3 couplings
     const int32_t *perm;      // [S][n]
     const uint64_t *tab;
     const int8_t *src;        // previous population (resampling parents)
     const int32_t *parent;
     const int8_t *ncm_buf;
     const int32_t *ncm_idx;
-    const int32_t *Hin;       // [R][n] recomputed fields
+    int32_t *H;               // [R][n] in: recomputed fields; out: fields after the sweeps
     int8_t *dst;              // [R][n]
     int64_t *E;               // [R]
-    int32_t *G;               // [kB][64] published fields of the current block
-    int8_t *T;                // [kB][32][kC] tile J[P][P]
-    unsigned long long *flip; // [2][kB] replica bit masks of flips
-    unsigned long long *snew; // [2][kB] replica bit masks of the new spin (+1)
+    int32_t *G;               // [2][kB][64] published fields of a block
+    int8_t *T;                // [2][kB][32][kC] tile J[P_q][P_q]
+    int8_t *T2;               // [2][kB][32][kC] tile J[P_{q-1}][P_q]
+    unsigned long long *flip; // [3][kB] replica bit masks of flips
+    unsigned long long *snew; // [3][kB] replica bit masks of the new spin (+1)
     GridBar *bar;
     DevCtl *ctl;
 };
 
+__device__ __forceinline__ const int8_t *pop_row(const DenseSweepArgs &a, int r) {
+    const int32_t qn = a.ncm_idx[r];
+    return qn >= 0 ? a.ncm_buf + (size_t)qn * a.n : a.src + (size_t)a.parent[r] * a.n;
+}
+
+// The S sweeps of one step.  Block q (kB consecutive positions of a sweep's
+// order) is decided by the chain CTAs in phase q while the update CTAs apply
+// block q-1 to their rows; the fields a chain starts from were published in
+// phase q-1 (all blocks up to q-2 applied) and the chain adds block q-1's
+// flips itself from the tile J[P_{q-1}][P_q].  One grid barrier per block.
 __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a) {
     extern __shared__ __align__(16) uint8_t sm[];
-    __shared__ int s_ok;
+    __shared__ int s_ok, s_nl;
+    __shared__ int32_t s_wlo, s_wn;
     if (a.ctl->done) return;
     const int32_t n = a.n, R = a.R;
     const unsigned int nblocks = gridDim.x;
@@ -313,215 +358,338 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     const int32_t nb = (n + kB - 1) / kB;              // blocks per sweep
     const int32_t total = nb * a.S;                    // blocks of the step
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    auto block_pos = [&](int32_t q) { return a.perm + (size_t)(q / nb) * n + (size_t)(q % nb) * kB; };
+    auto block_cnt = [&](int32_t q) { return min(kB, n - (q % nb) * kB); };
 
-    // ---------------- per-role shared memory
-    // update CTA: Hs[R][rows] int32, spin bits sb[R][(rows+31)/32]
-    // chain CTA : tile[kB*kB] int8, bits[4][(n+31)/32], thr[4][kB], Gs[4][kB]
+    // ---------------- update CTA shared memory
     const int32_t ua = upd ? blockIdx.x * a.rows_per : 0;
     const int32_t ub = upd ? min(n, ua + a.rows_per) : 0;
     const int32_t rows = ub - ua;
     const int32_t rw = (a.rows_per + 31) / 32;
     int32_t *Hs = reinterpret_cast<int32_t *>(sm);
     uint32_t *ubits = reinterpret_cast<uint32_t *>(sm + (size_t)R * a.rows_per * 4);
+    unsigned long long *fprev = reinterpret_cast<unsigned long long *>(
+        sm + (((size_t)R * a.rows_per * 4 + (size_t)R * rw * 4 + 15) & ~(size_t)15));
+    unsigned long long *sprev = fprev + kB;
+    int32_t *Pprev = reinterpret_cast<int32_t *>(sprev + kB);
+    int32_t *Pcur = Pprev + kB;
+    int32_t *Pnext = Pcur + kB;
+    int32_t *flist = Pnext + kB;
+    // ---------------- chain CTA shared memory
     const int cg = blockIdx.x - a.n_upd;               // chain group (4 replicas)
     const int32_t nw = (n + 31) / 32;
-    int8_t *tile = reinterpret_cast<int8_t *>(sm);
-    uint32_t *cbits = reinterpret_cast<uint32_t *>(sm + (size_t)kB * kB);
-    int32_t *thr = reinterpret_cast<int32_t *>(cbits + (size_t)4 * nw);
-    int32_t *Gs = thr + 4 * kB;
+    int8_t *tile = reinterpret_cast<int8_t *>(sm);                 // J[P_q][P_q]
+    int8_t *tile2 = tile + (size_t)kB * kB;                        // J[P_{q-1}][P_q]
+    uint32_t *cbits = reinterpret_cast<uint32_t *>(tile2 + (size_t)kB * kB);
+    uint64_t *win = reinterpret_cast<uint64_t *>(cbits + (((size_t)4 * nw + 3) & ~(size_t)3));
+    int32_t *Gs = reinterpret_cast<int32_t *>(win + kWin);
+    int32_t *thr = Gs + 4 * kB;
+    int32_t *Pc = thr + 4 * kB;
+    unsigned long long *cfm = reinterpret_cast<unsigned long long *>(Pc + kB);
+    unsigned long long *csn = cfm + kB;
 
+    // update CTAs: publish the fields of block qn's positions they own, and
+    // gather their share of the tiles J[P_qn][P_qn] and J[P_{qn-1}][P_qn]
+    auto publish = [&](int32_t qn) {
+        const int32_t *P = block_pos(qn);
+        const int32_t cnt = block_cnt(qn);
+        if ((int)threadIdx.x < cnt) Pnext[threadIdx.x] = P[threadIdx.x];
+        if (qn > 0 && (int)threadIdx.x < block_cnt(qn - 1)) Pcur[threadIdx.x] = block_pos(qn - 1)[threadIdx.x];
+        __syncthreads();
+        int32_t *Gq = a.G + (size_t)(qn & 1) * kB * 64;
+        for (int32_t x = threadIdx.x; x < cnt * R; x += blockDim.x) {
+            const int32_t m = x / R, r = x % R;
+            const int32_t p = Pnext[m];
+            if (p >= ua && p < ub) Gq[m * 64 + r] = Hs[r * a.rows_per + (p - ua)];
+        }
+        const int32_t per = (2 * kB * kB + a.n_upd - 1) / a.n_upd;
+        const int32_t e0 = blockIdx.x * per, e1 = min(2 * kB * kB, e0 + per);
+        const int32_t cntp = qn > 0 ? block_cnt(qn - 1) : 0;
+        int8_t *Tq = a.T + (size_t)(qn & 1) * kB * kB;
+        int8_t *T2q = a.T2 + (size_t)(qn & 1) * kB * kB;
+        for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int32_t which = e / (kB * kB), ee = e % (kB * kB);
+            const int32_t m = ee / kB, m2 = ee % kB;
+            int8_t v = 0;
+            if (which == 0) {
+                if (m < cnt && m2 < cnt) v = (int8_t)e4m3_pm1(a.J[(size_t)Pnext[m] * n + Pnext[m2]]);
+                Tq[(size_t)m * kB + (m2 & 31) * kC + (m2 >> 5)] = v;
+            } else {
+                if (m < cntp && m2 < cnt) v = (int8_t)e4m3_pm1(a.J[(size_t)Pcur[m] * n + Pnext[m2]]);
+                T2q[(size_t)m * kB + (m2 & 31) * kC + (m2 >> 5)] = v;
+            }
+        }
+    };
+
+    // ---------------- prologue
     if (upd) {
         for (int32_t x = threadIdx.x; x < R * rows; x += blockDim.x) {
             const int r = x / rows, j = x % rows;
-            Hs[r * a.rows_per + j] = a.Hin[(size_t)r * n + ua + j];
+            Hs[r * a.rows_per + j] = a.H[(size_t)r * n + ua + j];
         }
         for (int32_t x = threadIdx.x; x < R * rw; x += blockDim.x) {
             const int r = x / rw, w = x % rw;
-            const int32_t qn = a.ncm_idx[r];
-            const int8_t *row = qn >= 0 ? a.ncm_buf + (size_t)qn * n : a.src + (size_t)a.parent[r] * n;
+            const int8_t *row = pop_row(a, r) + ua;
             uint32_t bits = 0;
             for (int b = 0; b < 32; ++b) {
                 const int32_t j = w * 32 + b;
-                if (j < rows && row[ua + j] > 0) bits |= 1u << b;
+                if (j < rows && row[j] > 0) bits |= 1u << b;
             }
             ubits[r * rw + w] = bits;
         }
+        __syncthreads();
+        if (total > 0) publish(0);
     } else {
         for (int32_t x = threadIdx.x; x < 4 * nw; x += blockDim.x) {
-            const int q = x / nw, w = x % nw;
-            const int r = cg * 4 + q;
+            const int qq = x / nw, w = x % nw;
+            const int r = cg * 4 + qq;
             uint32_t bits = 0;
             if (r < R) {
-                const int32_t qn = a.ncm_idx[r];
-                const int8_t *row = qn >= 0 ? a.ncm_buf + (size_t)qn * n : a.src + (size_t)a.parent[r] * n;
-                for (int b = 0; b < 32; ++b) {
-                    const int32_t k = w * 32 + b;
-                    if (k < n && row[k] > 0) bits |= 1u << b;
+                const int8_t *row = pop_row(a, r);
+                const int32_t k0 = w * 32;
+                if (k0 + 32 <= n && (((uintptr_t)(row + k0)) & 15) == 0) {
+                    const uint4 v0 = *reinterpret_cast<const uint4 *>(row + k0);
+                    const uint4 v1 = *reinterpret_cast<const uint4 *>(row + k0 + 16);
+                    const uint32_t wv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            bits |= (((wv[i] >> (8 * b)) & 0x80u) ? 0u : 1u) << (4 * i + b);
+                } else {
+                    for (int b = 0; b < 32; ++b) {
+                        const int32_t k = k0 + b;
+                        if (k < n && row[k] > 0) bits |= 1u << b;
+                    }
                 }
             }
             cbits[x] = bits;
         }
-        if (blockIdx.x == a.n_upd && threadIdx.x < kB) {   // both mask buffers start empty
-            a.flip[threadIdx.x] = 0ull; a.flip[kB + threadIdx.x] = 0ull;
-            a.snew[threadIdx.x] = 0ull; a.snew[kB + threadIdx.x] = 0ull;
+        if (blockIdx.x == a.n_upd && threadIdx.x < kB) {
+            for (int z = 0; z < 3; ++z) { a.flip[z * kB + threadIdx.x] = 0ull; a.snew[z * kB + threadIdx.x] = 0ull; }
         }
-        if (blockIdx.x == a.n_upd && threadIdx.x < 64) a.E[threadIdx.x < R ? threadIdx.x : 0] = 0;
+        if (blockIdx.x == a.n_upd && (int)threadIdx.x < R) a.E[threadIdx.x] = 0;
+        // the part of the threshold table where it is neither 0 nor 2^32
+        // (heat-bath) or above 0 (Metropolis)
+        if (threadIdx.x == 0) {
+            int32_t lo, hi;
+            if (a.rule == 0) {
+                int32_t l = 0, h2 = 2 * a.Hc + 1;
+                while (l < h2) { const int32_t md = (l + h2) >> 1; if (a.tab[md] > 0ull) h2 = md; else l = md + 1; }
+                lo = l;
+                l = lo; h2 = 2 * a.Hc + 1;
+                while (l < h2) { const int32_t md = (l + h2) >> 1; if (a.tab[md] == (1ull << 32)) h2 = md; else l = md + 1; }
+                hi = min(l, 2 * a.Hc);
+            } else {
+                int32_t l = 0, h2 = a.Hc + 1;
+                while (l < h2) { const int32_t md = (l + h2) >> 1; if (a.tab[md] == 0ull) h2 = md; else l = md + 1; }
+                lo = 0;
+                hi = min(l, a.Hc);
+            }
+            s_wlo = lo;
+            s_wn = hi - lo + 1;
+        }
+        __syncthreads();
+        if (s_wn <= kWin)
+            for (int32_t i = threadIdx.x; i < s_wn; i += blockDim.x) win[i] = a.tab[s_wlo + i];
     }
     if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) return;
 
     for (int32_t q = 0; q <= total; ++q) {
-        // ================= phase A: apply block q-1, publish block q
         if (upd) {
+            // ---- apply block q-1 to the owned rows
             if (q > 0) {
                 const int32_t qp = q - 1;
-                const int32_t swp = qp / nb, bp = qp % nb;
-                const int32_t *P = a.perm + (size_t)swp * n + (size_t)bp * kB;
-                const int32_t cntp = min(kB, n - bp * kB);
-                const unsigned long long *fm = a.flip + (qp & 1) * kB;
-                const unsigned long long *sn = a.snew + (qp & 1) * kB;
-                const int32_t j = threadIdx.x;
-                for (int32_t m = 0; m < cntp; ++m) {
-                    const unsigned long long f = fm[m];
-                    if (f == 0ull) continue;
-                    const int32_t p = P[m];
-                    const unsigned long long s = sn[m];
-                    if (j < rows) {
-                        const int32_t jv = (int32_t)a.J[(size_t)p * n + ua + j];
-                        unsigned long long ff = f;
-                        while (ff) {
-                            const int r = __ffsll((long long)ff) - 1;
-                            ff &= ff - 1;
-                            const int32_t d = ((s >> r) & 1ull) ? 2 : -2;
-                            Hs[r * a.rows_per + j] += d * jv;
-                        }
-                    }
-                    if (p >= ua && p < ub && threadIdx.x == 0) {
-                        const int32_t lj = p - ua;
-                        unsigned long long ff = f;
-                        while (ff) {
-                            const int r = __ffsll((long long)ff) - 1;
-                            ff &= ff - 1;
-                            ubits[r * rw + (lj >> 5)] ^= 1u << (lj & 31);
-                        }
-                    }
-                }
-            }
-            if (q < total) {
-                const int32_t sw = q / nb, b = q % nb;
-                const int32_t *P = a.perm + (size_t)sw * n + (size_t)b * kB;
-                const int32_t cnt = min(kB, n - b * kB);
+                const int32_t *P = block_pos(qp);
+                const int32_t cntp = block_cnt(qp);
+                if (threadIdx.x == 0) s_nl = 0;
                 __syncthreads();
-                // publish the fields of this block's positions that this CTA owns
-                for (int32_t x = threadIdx.x; x < cnt * R; x += blockDim.x) {
-                    const int32_t m = x / R, r = x % R;
+                if ((int)threadIdx.x < cntp) {
+                    const int32_t m = threadIdx.x;
+                    const unsigned long long f = a.flip[(qp % 3) * kB + m];
                     const int32_t p = P[m];
-                    if (p >= ua && p < ub) a.G[m * 64 + r] = Hs[r * a.rows_per + (p - ua)];
+                    fprev[m] = f;
+                    sprev[m] = a.snew[(qp % 3) * kB + m];
+                    Pprev[m] = p;
+                    if (f != 0ull) {
+                        flist[atomicAdd(&s_nl, 1)] = m;
+                        if (p >= ua && p < ub) {
+                            const int32_t lj = p - ua;
+                            unsigned long long ff = f;
+                            while (ff) {
+                                const int r = __ffsll((long long)ff) - 1;
+                                ff &= ff - 1;
+                                atomicXor(&ubits[r * rw + (lj >> 5)], 1u << (lj & 31));
+                            }
+                        }
+                    }
                 }
-                // gather part of the tile J[P][P] (layout [m][lane][slot])
-                const int32_t per = (kB * kB + a.n_upd - 1) / a.n_upd;
-                const int32_t e0 = blockIdx.x * per, e1 = min(kB * kB, e0 + per);
-                for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-                    const int32_t m = e / kB, m2 = e % kB;
-                    int8_t v = 0;
-                    if (m < cnt && m2 < cnt) v = a.J[(size_t)P[m] * n + P[m2]];
-                    a.T[(size_t)m * kB + (m2 & 31) * kC + (m2 >> 5)] = v;
+                __syncthreads();
+                const int32_t nl = s_nl;
+                const int32_t j = threadIdx.x;
+                const uint8_t *Jc = a.J + ua + j;
+                for (int32_t base = 0; base < nl; base += 16) {
+                    int32_t jv[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        jv[u] = (base + u < nl && j < rows) ? e4m3_pm1(Jc[(size_t)Pprev[flist[base + u]] * n]) : 0;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        if (base + u >= nl) break;
+                        const int32_t m = flist[base + u];
+                        unsigned long long ff = fprev[m];
+                        const unsigned long long sv = sprev[m];
+                        if (j < rows) {
+                            while (ff) {
+                                const int r = __ffsll((long long)ff) - 1;
+                                ff &= ff - 1;
+                                Hs[r * a.rows_per + j] += (((sv >> r) & 1ull) ? 2 : -2) * jv[u];
+                            }
+                        }
+                    }
                 }
+                __syncthreads();
             }
+            // ---- publish block q+1
+            if (q + 1 < total) publish(q + 1);
         } else if (q < total) {
-            // chain CTA: thresholds of block q for its 4 replicas; clear the
-            // mask buffer that block q will fill
-            const int32_t sw = q / nb, b = q % nb;
-            const int32_t *P = a.perm + (size_t)sw * n + (size_t)b * kB;
-            const int32_t cnt = min(kB, n - b * kB);
-            if (blockIdx.x == a.n_upd && threadIdx.x < kB) {
-                a.flip[(q & 1) * kB + threadIdx.x] = 0ull;
-                a.snew[(q & 1) * kB + threadIdx.x] = 0ull;
+            const int32_t *P = block_pos(q);
+            const int32_t cnt = block_cnt(q);
+            const int32_t sw = q / nb;
+            const int32_t cntp = q > 0 ? block_cnt(q - 1) : 0;
+            if (blockIdx.x == a.n_upd && threadIdx.x < kB) {   // buffer of block q+1 starts empty
+                a.flip[((q + 1) % 3) * kB + threadIdx.x] = 0ull;
+                a.snew[((q + 1) % 3) * kB + threadIdx.x] = 0ull;
             }
+            // the two tiles stream in while the thresholds are computed
+            {
+                const int8_t *Tq = a.T + (size_t)(q & 1) * kB * kB;
+                const int8_t *T2q = a.T2 + (size_t)(q & 1) * kB * kB;
+                for (int32_t x = threadIdx.x; x < kB * kB / 16; x += blockDim.x) {
+                    cp_async16(tile + (size_t)x * 16, Tq + (size_t)x * 16);
+                    if (q > 0) cp_async16(tile2 + (size_t)x * 16, T2q + (size_t)x * 16);
+                }
+                cp_async_commit();
+            }
+            // thresholds of block q for the group's 4 replicas (Eq. 4 /
+            // Metropolis inverted to field values)
             for (int32_t m = threadIdx.x; m < cnt; m += blockDim.x) {
-                const u32x4 u = philox_rk((uint32_t)P[m], (uint32_t)sw, (uint32_t)a.t,
+                const int32_t k = P[m];
+                Pc[m] = k;
+                const u32x4 u = philox_rk((uint32_t)k, (uint32_t)sw, (uint32_t)a.t,
                                           (kTagFlip << 24) | (uint32_t)cg, a.K);
                 const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+                const bool inwin = s_wn <= kWin;
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
                     int32_t res;
+                    const uint64_t uq = (uint64_t)uw[qq];
                     if (a.rule == 0) {
-                        // smallest h with T(h) > u  (s = +1 iff h >= res)
-                        int32_t lo = 0, hi = 2 * a.Hc + 1;
+                        // smallest h with T(h) > u: s = +1 iff h >= res
+                        int32_t lo = 0, hi = inwin ? s_wn - 1 : 2 * a.Hc + 1;
                         while (lo < hi) {
                             const int32_t mid = (lo + hi) >> 1;
-                            if (a.tab[mid] > (uint64_t)uw[qq]) hi = mid; else lo = mid + 1;
+                            const uint64_t tv = inwin ? win[mid] : a.tab[mid];
+                            if (tv > uq) hi = mid; else lo = mid + 1;
                         }
-                        res = lo - a.Hc;
+                        res = (inwin ? lo + s_wlo : lo) - a.Hc;
                     } else {
-                        // largest x with T_M(2x) > u  (flip iff s*h <= res)
-                        int32_t lo = 0, hi = a.Hc;
+                        // largest x with T_M(2x) > u: flip iff s*h <= res
+                        int32_t lo = 0, hi = inwin ? s_wn - 1 : a.Hc;
                         while (lo < hi) {
                             const int32_t mid = (lo + hi + 1) >> 1;
-                            if (a.tab[mid] > (uint64_t)uw[qq]) lo = mid; else hi = mid - 1;
+                            const uint64_t tv = inwin ? win[mid] : a.tab[mid];
+                            if (tv > uq) lo = mid; else hi = mid - 1;
                         }
                         res = (lo == a.Hc && a.Hc >= n) ? n + 1 : lo;
                     }
                     thr[qq * kB + m] = res;
                 }
             }
-        }
-        if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) return;
-        if (q == total) break;
-
-        // ================= phase B: decision chains of block q
-        if (!upd) {
-            const int32_t sw = q / nb, b = q % nb;
-            const int32_t *P = a.perm + (size_t)sw * n + (size_t)b * kB;
-            const int32_t cnt = min(kB, n - b * kB);
-            for (int32_t x = threadIdx.x; x < kB * kB / 16; x += blockDim.x)
-                reinterpret_cast<int4 *>(tile)[x] = reinterpret_cast<const int4 *>(a.T)[x];
+            const int32_t *Gq = a.G + (size_t)(q & 1) * kB * 64;
             for (int32_t x = threadIdx.x; x < 4 * cnt; x += blockDim.x) {
                 const int qq = x / cnt, m = x % cnt;
                 const int r = cg * 4 + qq;
-                Gs[qq * kB + m] = r < R ? a.G[m * 64 + r] : 0;
+                Gs[qq * kB + m] = r < R ? Gq[m * 64 + r] : 0;
             }
+            if (q > 0 && (int)threadIdx.x < cntp) {
+                cfm[threadIdx.x] = a.flip[((q - 1) % 3) * kB + threadIdx.x];
+                csn[threadIdx.x] = a.snew[((q - 1) % 3) * kB + threadIdx.x];
+            }
+            cp_async_wait_all();
             __syncthreads();
             if (warp < 4 && cg * 4 + warp < R) {
                 const int qq = warp;
                 const int r = cg * 4 + qq;
                 uint32_t *bits = cbits + (size_t)qq * nw;
-                int32_t f[kC];
+                int32_t f[kC], th[kC];
+                uint32_t smask[kC];
 #pragma unroll
                 for (int s2 = 0; s2 < kC; ++s2) {
                     const int32_t m = s2 * 32 + lane;
-                    f[s2] = m < cnt ? Gs[qq * kB + m] : 0;
+                    const bool ok = m < cnt;
+                    f[s2] = ok ? Gs[qq * kB + m] : 0;
+                    th[s2] = ok ? thr[qq * kB + m] : 0;
+                    const int32_t k = ok ? Pc[m] : 0;
+                    smask[s2] = __ballot_sync(0xffffffffu, ok && ((bits[k >> 5] >> (k & 31)) & 1u));
                 }
+                // block q-1's flips, which the published fields do not include yet
+                if (q > 0) {
 #pragma unroll
-                for (int s2 = 0; s2 < kC; ++s2) {
-                    for (int o = 0; o < 32; ++o) {
-                        const int32_t m = s2 * 32 + o;
-                        if (m >= cnt) break;
-                        const int32_t hm = __shfl_sync(0xffffffffu, f[s2], o);
-                        const int32_t k = P[m];
-                        const uint32_t sold = (bits[k >> 5] >> (k & 31)) & 1u;
-                        const int32_t th = thr[qq * kB + m];
-                        uint32_t snv;
-                        if (a.rule == 0) {
-                            snv = hm >= th ? 1u : 0u;
-                        } else {
-                            const int32_t x = sold ? hm : -hm;
-                            snv = x <= th ? (sold ^ 1u) : sold;
-                        }
-                        if (snv != sold) {
-                            const int32_t d = snv ? 2 : -2;
-                            const int2 tv = *reinterpret_cast<const int2 *>(tile + (size_t)m * kB + lane * kC);
+                    for (int s2 = 0; s2 < kC; ++s2) {
+                        const int32_t mp = s2 * 32 + lane;
+                        unsigned int bal =
+                            __ballot_sync(0xffffffffu, mp < cntp && ((cfm[mp] >> r) & 1ull));
+                        while (bal) {
+                            const int o = __ffs(bal) - 1;
+                            bal &= bal - 1;
+                            const int32_t m = s2 * 32 + o;
+                            const int32_t d = ((csn[m] >> r) & 1ull) ? 2 : -2;
+                            const int2 tv = *reinterpret_cast<const int2 *>(tile2 + (size_t)m * kB + lane * kC);
 #pragma unroll
                             for (int s3 = 0; s3 < kC; ++s3) {
                                 const uint32_t word = s3 < 4 ? (uint32_t)tv.x : (uint32_t)tv.y;
-                                const int32_t jv = (int32_t)(int8_t)((word >> (8 * (s3 & 3))) & 0xFFu);
-                                f[s3] += d * jv;
+                                f[s3] += d * (int32_t)(int8_t)((word >> (8 * (s3 & 3))) & 0xFFu);
                             }
-                            if (lane == 0) {
-                                bits[k >> 5] ^= 1u << (k & 31);
-                                atomicOr(&a.flip[(q & 1) * kB + m], 1ull << r);
-                                if (snv) atomicOr(&a.snew[(q & 1) * kB + m], 1ull << r);
-                            }
-                            __syncwarp();
+                        }
+                    }
+                }
+                // the sequential decisions of block q, 32 positions at a time:
+                // every lane evaluates its own position with the current
+                // fields; positions before the first lane that flips keep their
+                // spins, that flip is applied to all fields, and evaluation
+                // resumes after it -- the same result as one position at a time
+#pragma unroll
+                for (int s2 = 0; s2 < kC; ++s2) {
+                    const int32_t mb = s2 * 32;
+                    if (mb >= cnt) break;
+                    const uint32_t sold = (smask[s2] >> lane) & 1u;
+                    unsigned int open = cnt - mb >= 32 ? 0xffffffffu : ((1u << (cnt - mb)) - 1u);
+                    while (open) {
+                        uint32_t snv;
+                        if (a.rule == 0) {
+                            snv = f[s2] >= th[s2] ? 1u : 0u;
+                        } else {
+                            const int32_t x = sold ? f[s2] : -f[s2];
+                            snv = x <= th[s2] ? (sold ^ 1u) : sold;
+                        }
+                        const unsigned int fb = __ballot_sync(0xffffffffu, snv != sold) & open;
+                        if (fb == 0u) break;
+                        const int o = __ffs(fb) - 1;
+                        open &= ~((2u << o) - 1u);        // positions up to o are decided
+                        const int32_t m = mb + o;
+                        const int32_t d = ((smask[s2] >> o) & 1u) ? -2 : 2;   // the spin turns over
+                        const int2 tv = *reinterpret_cast<const int2 *>(tile + (size_t)m * kB + lane * kC);
+#pragma unroll
+                        for (int s3 = 0; s3 < kC; ++s3) {
+                            const uint32_t word = s3 < 4 ? (uint32_t)tv.x : (uint32_t)tv.y;
+                            f[s3] += d * (int32_t)(int8_t)((word >> (8 * (s3 & 3))) & 0xFFu);
+                        }
+                        if (lane == 0) {
+                            const int32_t k = Pc[m];
+                            bits[k >> 5] ^= 1u << (k & 31);
+                            atomicOr(&a.flip[(q % 3) * kB + m], 1ull << r);
+                            if (d > 0) atomicOr(&a.snew[(q % 3) * kB + m], 1ull << r);
                         }
                     }
                 }
@@ -530,8 +698,12 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) return;
     }
 
-    // ---------------- energies E_r = -1/2 sum_j s_j h_j, spins back to HBM
+    // ---------------- energies E_r = -1/2 sum_j s_j h_j, fields and spins back to HBM
     if (upd) {
+        for (int32_t x = threadIdx.x; x < R * rows; x += blockDim.x) {
+            const int r = x / rows, j = x % rows;
+            a.H[(size_t)r * n + ua + j] = Hs[r * a.rows_per + j];
+        }
         for (int r = 0; r < R; ++r) {
             long long accv = 0;
             for (int32_t j = threadIdx.x; j < rows; j += blockDim.x) {
@@ -592,6 +764,15 @@ __global__ void k_dense_energy_finish(int32_t R, int64_t *E, const DevCtl *ctl) 
     if (r < R) E[r] = -(E[r] / 2);
 }
 
+// int8 couplings (validated +-1 / 0) -> e4m3 bytes in place
+__global__ void k_dense_to_e4m3(size_t total, uint8_t *__restrict__ J) {
+    for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total;
+         x += (size_t)gridDim.x * blockDim.x) {
+        const int8_t v = (int8_t)J[x];
+        J[x] = v == 0 ? (uint8_t)0 : (v > 0 ? (uint8_t)0x38 : (uint8_t)0xB8);
+    }
+}
+
 // Validation of a device-resident copy: entries in {-1, 0, +1}, zero diagonal,
 // +-1 off the diagonal, symmetric.  32x32 tiles compared with their transpose.
 __global__ void k_dense_validate(int32_t n, const int8_t *__restrict__ J, int *__restrict__ err) {
@@ -640,7 +821,7 @@ cudaError_t launch_dense_tables(int rule, int32_t Hc, int32_t n, DevCtl *ctl, ui
     return cudaGetLastError();
 }
 
-size_t dense_recompute_smem() { return 2 * (size_t)kRcStageBytes; }
+size_t dense_recompute_smem() { return (size_t)kRcStages * kRcStageBytes; }
 
 cudaError_t launch_dense_recompute(int32_t n, int32_t R, const int8_t *J, const int8_t *src,
                                    const int32_t *parent, const int8_t *ncm_buf,
@@ -650,14 +831,19 @@ cudaError_t launch_dense_recompute(int32_t n, int32_t R, const int8_t *J, const 
     cudaError_t e = cudaFuncSetAttribute(k_dense_recompute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int grid = (n + kRcRows - 1) / kRcRows;
-    k_dense_recompute<<<grid, kRcWarps * 32, smem, st>>>(n, R, J, src, parent, ncm_buf, ncm_idx, H, ctl,
-                                                           restart_t);
+    k_dense_recompute<<<grid, kRcWarps * 32, smem, st>>>(n, R, reinterpret_cast<const uint8_t *>(J), src,
+                                                           parent, ncm_buf, ncm_idx, H, ctl, restart_t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dense_energy(int32_t n, int32_t R, const int32_t *H, const int8_t *spins, int64_t *E,
                                 const DevCtl *ctl, cudaStream_t st, int restart_t) {
     k_dense_energy_from_H<<<R, 512, 0, st>>>(n, H, spins, E, ctl, restart_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_to_e4m3(size_t total, int8_t *J, cudaStream_t st) {
+    k_dense_to_e4m3<<<152 * 8, 256, 0, st>>>(total, reinterpret_cast<uint8_t *>(J));
     return cudaGetLastError();
 }
 
@@ -670,8 +856,11 @@ int dense_block_positions() { return kB; }
 
 // Shared memory of the sweep kernel for a given split.
 size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per) {
-    const size_t upd = (size_t)R * rows_per * 4 + (size_t)R * ((rows_per + 31) / 32) * 4;
-    const size_t chn = (size_t)kB * kB + (size_t)4 * ((n + 31) / 32) * 4 + (size_t)8 * kB * 4;
+    const size_t upd = (((size_t)R * rows_per * 4 + (size_t)R * ((rows_per + 31) / 32) * 4 + 15) & ~(size_t)15) +
+                       (size_t)kB * (8 + 8 + 4 + 4 + 4 + 4);
+    const size_t nw = (size_t)((n + 31) / 32);
+    const size_t chn = 2 * (size_t)kB * kB + ((4 * nw + 3) & ~(size_t)3) * 4 + (size_t)kWin * 8 +
+                       (size_t)kB * (4 * 4 + 4 * 4 + 4 + 8 + 8);
     return upd > chn ? upd : chn;
 }
 
@@ -679,14 +868,15 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
                                uint64_t seed, int32_t n_upd, int32_t rows_per, int32_t grid,
                                const int8_t *J, const int32_t *perm, const uint64_t *tab,
                                const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
-                               const int32_t *ncm_idx, const int32_t *Hin, int8_t *dst, int64_t *E,
-                               int32_t *G, int8_t *T, unsigned long long *flip,
+                               const int32_t *ncm_idx, int32_t *H, int8_t *dst, int64_t *E,
+                               int32_t *G, int8_t *T, int8_t *T2, unsigned long long *flip,
                                unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st) {
     DenseSweepArgs a;
     a.n = n; a.R = R; a.S = S; a.rule = rule; a.Hc = Hc; a.n_upd = n_upd; a.rows_per = rows_per;
-    a.t = t; a.K = make_philox_keys(seed); a.J = J; a.perm = perm; a.tab = tab; a.src = src;
-    a.parent = parent; a.ncm_buf = ncm_buf; a.ncm_idx = ncm_idx; a.Hin = Hin; a.dst = dst; a.E = E;
-    a.G = G; a.T = T; a.flip = flip; a.snew = snew; a.bar = reinterpret_cast<GridBar *>(bar); a.ctl = ctl;
+    a.t = t; a.K = make_philox_keys(seed); a.J = reinterpret_cast<const uint8_t *>(J); a.perm = perm;
+    a.tab = tab; a.src = src; a.parent = parent; a.ncm_buf = ncm_buf; a.ncm_idx = ncm_idx; a.H = H;
+    a.dst = dst; a.E = E; a.G = G; a.T = T; a.T2 = T2; a.flip = flip; a.snew = snew;
+    a.bar = reinterpret_cast<GridBar *>(bar); a.ctl = ctl;
     const size_t smem = dense_sweep_smem(n, R, rows_per);
     cudaError_t e = cudaFuncSetAttribute(k_dense_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
