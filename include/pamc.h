@@ -146,6 +146,52 @@ pamc_status pamc_last_error(pamc_handle h, char *buf, size_t len);
 
 void pamc_destroy(pamc_handle h);
 
+/* ---- Batches: many independent instances advanced together ----
+ * Not in the paper: a serving extension.  A batch advances every member by
+ * one iteration of Algorithm 1 per step (resampling, tables, sweeps,
+ * controller) with one launch per kernel type, the sweep launched once per
+ * size class of n with its own shape, so uneven instances share the GPU.
+ * Each launch reads the member's step index from the member's device-side
+ * controller, so one step's launches are captured into a CUDA graph once per
+ * change of membership and replayed.  A member computes exactly what
+ * pamc_step computes for it alone (same random streams, orders, tables and
+ * controller): its spins, energies, parents, counts and best cut are
+ * identical in and out of the batch.
+ * Members: initialised sparse Max-Cut (kind 0) handles with stagnation = 0
+ * and no restart re-initialisation (z_rst = 0 or restart_reinit = 0);
+ * others are refused with PAMC_ERR_ARG.  A member must stay alive and must
+ * not be stepped or re-initialised on its own while it is in the batch.  The batch runs on its
+ * own stream (the one given, or one it creates when stream is NULL); read a
+ * member's results (pamc_best, pamc_state) after pamc_batch_retire returned
+ * it or after pamc_batch_sync. */
+typedef struct pamc_batch_s *pamc_batch;
+
+/* Device bytes of a sparse handle running with p: the instance (CSR) plus
+ * what pamc_init allocates (two spin buffers, energies, parents, counts, the
+ * schedule ring of 16 steps, the threshold table, NCM buffers, the
+ * controller).  For admission by HBM footprint; 0 for a null argument or a
+ * dense handle. */
+size_t pamc_footprint(pamc_handle h, const pamc_params *p);
+/* stream: a cudaStream_t, or NULL for a new non-blocking stream. */
+pamc_status pamc_batch_create(int cuda_device, void *stream, pamc_batch *out);
+/* Add an initialised handle (tops up its schedule ring and waits for its
+ * stream).  Takes effect at the next pamc_batch_step. */
+pamc_status pamc_batch_add(pamc_batch b, pamc_handle h);
+/* Enqueue nsteps batch steps (asynchronous).  Members that completed
+ * p->steps iterations do nothing. */
+pamc_status pamc_batch_step(pamc_batch b, int32_t nsteps);
+/* Remove up to max_out members that completed their iterations and write
+ * them to out, after waiting for the batch stream; returns how many, or -1
+ * on error (null batch, out NULL with max_out > 0, CUDA error). */
+int32_t pamc_batch_retire(pamc_batch b, pamc_handle *out, int32_t max_out);
+int32_t pamc_batch_size(pamc_batch b);      /* members, finished or not */
+int32_t pamc_batch_active(pamc_batch b);    /* members with steps left */
+int64_t pamc_batch_launch_count(pamc_batch b);  /* kernel launches enqueued */
+int64_t pamc_batch_graph_builds(pamc_batch b);  /* CUDA graphs captured */
+pamc_status pamc_batch_sync(pamc_batch b);
+pamc_status pamc_batch_last_error(pamc_batch b, char *buf, size_t len);
+void pamc_batch_destroy(pamc_batch b);
+
 /* Size limits of pamc_sweeps_noalloc and the bytes of device memory its
  * file-scope scratch array takes on every GPU that loads the library. */
 #define PAMC_NOALLOC_MAX_N 32768

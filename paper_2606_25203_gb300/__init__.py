@@ -22,12 +22,15 @@ __all__ = [
     "PamcError", "Params", "load", "pamc_create_csr", "pamc_create_dense", "pamc_init",
     "pamc_step", "pamc_sync", "pamc_run", "pamc_best", "pamc_state", "pamc_control_state",
     "pamc_launch_count", "pamc_weight_sum", "pamc_last_error", "pamc_destroy", "Solver",
-    "pamc_sweeps_noalloc",
+    "pamc_sweeps_noalloc", "pamc_footprint", "pamc_batch_create", "pamc_batch_add", "pamc_batch_step",
+    "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
+    "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
           4: "PAMC_ERR_RANGE", 5: "PAMC_ERR_OOM", 6: "PAMC_ERR_CUDA", 7: "PAMC_ERR_TIMEOUT",
           8: "PAMC_ERR_STATE"}
+STATUS_CODES = {v: k for k, v in STATUS.items()}
 
 
 class PamcError(RuntimeError):
@@ -115,6 +118,26 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_sweeps_noalloc.argtypes = [i32, i32, P, P, P, i32, i32, i32, i32, ctypes.c_double,
                                       ctypes.c_uint64, i32, P, P, P, P, ctypes.c_char_p,
                                       ctypes.c_size_t]
+    L.pamc_footprint.argtypes = [P, ctypes.POINTER(Params)]
+    L.pamc_footprint.restype = ctypes.c_size_t
+    L.pamc_batch_create.argtypes = [ctypes.c_int, P, ctypes.POINTER(P)]
+    L.pamc_batch_add.argtypes = [P, P]
+    L.pamc_batch_step.argtypes = [P, i32]
+    L.pamc_batch_retire.argtypes = [P, P, i32]
+    L.pamc_batch_retire.restype = i32
+    for nm in ("pamc_batch_size", "pamc_batch_active"):
+        getattr(L, nm).argtypes = [P]
+        getattr(L, nm).restype = i32
+    for nm in ("pamc_batch_launch_count", "pamc_batch_graph_builds"):
+        getattr(L, nm).argtypes = [P]
+        getattr(L, nm).restype = i64
+    L.pamc_batch_sync.argtypes = [P]
+    L.pamc_batch_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
+    L.pamc_batch_destroy.argtypes = [P]
+    L.pamc_batch_destroy.restype = None
+    for nm in ("pamc_batch_create", "pamc_batch_add", "pamc_batch_step", "pamc_batch_sync",
+               "pamc_batch_last_error"):
+        getattr(L, nm).restype = ctypes.c_int
     for nm in ("pamc_sweeps_noalloc", "pamc_set_allocator", "pamc_create_csr", "pamc_create_dense", "pamc_init",
                "pamc_step", "pamc_sync", "pamc_run", "pamc_best", "pamc_state",
                "pamc_control_state", "pamc_last_error"):
@@ -266,6 +289,67 @@ def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed,
                                _stream_ptr(dev, stream), buf, 256)
     if rc != 0:
         raise PamcError(rc, buf.value.decode(errors="replace"))
+
+
+def pamc_footprint(h, **params) -> int:
+    return int(_lib.pamc_footprint(h, ctypes.byref(make_params(**params))))
+
+
+def _bcheck(rc: int, b=None):
+    if rc != 0:
+        buf = ctypes.create_string_buffer(256)
+        _lib.pamc_batch_last_error(b, buf, 256)
+        raise PamcError(rc, buf.value.decode(errors="replace"))
+
+
+def pamc_batch_create(device: int = 0, stream=None):
+    """stream None: the batch creates its own non-blocking stream."""
+    L = load()
+    b = ctypes.c_void_p()
+    st = ctypes.c_void_p(int(stream)) if stream is not None else None
+    _bcheck(L.pamc_batch_create(int(device), st, ctypes.byref(b)))
+    return b
+
+
+def pamc_batch_add(b, h):
+    _bcheck(_lib.pamc_batch_add(b, h), b)
+
+
+def pamc_batch_step(b, nsteps: int = 1):
+    _bcheck(_lib.pamc_batch_step(b, int(nsteps)), b)
+
+
+def pamc_batch_retire(b, max_out: int = 4096) -> list:
+    out = (ctypes.c_void_p * max(int(max_out), 1))()
+    k = _lib.pamc_batch_retire(b, out, int(max_out))
+    if k < 0:
+        _bcheck(int(STATUS_CODES["PAMC_ERR_CUDA"]), b)
+    return [ctypes.c_void_p(out[i]) for i in range(k)]
+
+
+def pamc_batch_size(b) -> int:
+    return int(_lib.pamc_batch_size(b))
+
+
+def pamc_batch_active(b) -> int:
+    return int(_lib.pamc_batch_active(b))
+
+
+def pamc_batch_launch_count(b) -> int:
+    return int(_lib.pamc_batch_launch_count(b))
+
+
+def pamc_batch_graph_builds(b) -> int:
+    return int(_lib.pamc_batch_graph_builds(b))
+
+
+def pamc_batch_sync(b):
+    _bcheck(_lib.pamc_batch_sync(b), b)
+
+
+def pamc_batch_destroy(b):
+    if b is not None and b.value:
+        _lib.pamc_batch_destroy(b)
 
 
 class Solver:

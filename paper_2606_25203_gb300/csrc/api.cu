@@ -714,3 +714,340 @@ void pamc_destroy(pamc_handle h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batches
+// A batch advances many sparse Ising instances together.  Every launch reads
+// the member's step index from its device controller (ctl->t), so the
+// launches of one step are the same for every step: they are captured once
+// per membership into a CUDA graph and replayed.  Members that reached their
+// last step are no-ops inside the graph until the next rebuild drops them.
+struct pamc_batch_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<pamc_handle> members;
+    bool dirty = true;
+    DevBuf sw, swi, sd, sdi, prep, tabs, ctl;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t graph_launches = 0;   // kernel launches in one replay
+    int64_t launches = 0;
+    int64_t rebuilds = 0;
+    char err[256] = "";
+};
+
+namespace {
+
+pamc_status bfail(pamc_batch b, pamc_status s, const char *fmt, ...) {
+    char buf[256];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b) snprintf(b->err, sizeof(b->err), "%s", buf);
+    else snprintf(g_create_err, sizeof(g_create_err), "%s", buf);
+    return s;
+}
+
+// Stream-ordered upload of a descriptor array (the stream's earlier work,
+// which may still read the old contents, completes first).
+template <typename T>
+bool upload(pamc_batch b, DevBuf &buf, const std::vector<T> &v) {
+    const size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+    if (buf.bytes < bytes) {
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return false;
+        if (buf.p) cudaFree(buf.p);
+        buf.p = nullptr;
+        buf.bytes = 0;
+        if (cudaMalloc(&buf.p, bytes * 2) != cudaSuccess) { cudaGetLastError(); return false; }
+        buf.bytes = bytes * 2;
+    }
+    if (v.empty()) return true;
+    if (cudaMemcpyAsync(buf.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+        return false;
+    // the host vector is reused by the next rebuild
+    return cudaStreamSynchronize(b->stream) == cudaSuccess;
+}
+
+// Sweep launch shape per size class of n (groups of 4 replicas per CTA,
+// warps per group).  Small instances pack several groups into one CTA.
+constexpr int kClasses = 3;
+int batch_class(int32_t n) { return n <= 2048 ? 0 : n <= 8192 ? 1 : 2; }
+SweepCfg batch_cfg(int cls) {
+    static const SweepCfg c[kClasses] = {{4, 1}, {2, 4}, {1, 8}};
+    const char *env = getenv("PAMC_BATCH_CFG");   // "g0,w0;g1,w1;g2,w2"
+    if (env) {
+        int v[6];
+        if (sscanf(env, "%d,%d;%d,%d;%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 6) {
+            SweepCfg o{v[2 * cls], v[2 * cls + 1]};
+            if (o.groups_per_cta >= 1 && o.warps_per_group >= 1 && o.groups_per_cta * o.warps_per_group <= 32)
+                return o;
+        }
+    }
+    return c[cls];
+}
+
+void drop_graph(pamc_batch b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// Descriptor arrays for the members that still have steps left, then the
+// captured launch sequence of one step.
+pamc_status rebuild(pamc_batch b) {
+    drop_graph(b);
+    std::vector<SchedDesc> sd;
+    std::vector<int2> sdi;
+    std::vector<PrepDesc> prep;
+    std::vector<TabDesc> tabs;
+    std::vector<CtlDesc> ctls;
+    std::vector<SweepDesc> sw;
+    std::vector<int2> swi[2][2][kClasses];   // [ell][rule][class]
+    int32_t nmax[kClasses] = {0, 0, 0}, Rmax = 1;
+    for (pamc_handle h : b->members) {
+        const pamc_params &p = h->p;
+        if (h->host_t >= p.steps) continue;
+        const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
+        const int32_t t_end = p.steps;
+        if (p.sweeps > 0) {
+            SchedDesc d{h->d_rp, h->d_adj, h->d_order, h->d_lvl, h->d_nlev, h->d_scnt, h->d_skey, h->d_ell,
+                        h->d_pos, h->n, 0, p.sweeps, kSchedSlots, h->ell_w, k0, k1, h->d_ctl,
+                        kSchedSlots - 1, t_end};
+            const int idx = (int)sd.size();
+            sd.push_back(d);
+            for (int x = 0; x < p.sweeps; ++x) sdi.push_back(make_int2(idx, x));
+        }
+        PrepDesc pd{nullptr, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, p.R,
+                    p.kind, p.resample, p.n_top, p.cooldown_tau, k0, k1, {h->d_E[0], h->d_E[1]}, t_end};
+        prep.push_back(pd);
+        tabs.push_back(TabDesc{h->d_ctl, h->d_tab, p.rule, h->H, t_end});
+        SweepDesc d;
+        memset(&d, 0, sizeof(d));
+        d.rp = h->d_rp; d.adj = h->d_adj; d.sorder = h->d_order; d.slvl = h->d_lvl; d.snlev = h->d_nlev;
+        d.sell = h->d_ell; d.spos = h->d_pos; d.tab = h->d_tab; d.parent = h->d_parent;
+        d.ncm_buf = nullptr; d.ncm_idx = h->d_ncm_idx; d.ctl = h->d_ctl;
+        d.n = h->n; d.n_pad = (h->n + 3) & ~3; d.H = h->H; d.R = p.R; d.S = p.sweeps;
+        d.W = h->ell_w; d.K = make_philox_keys(p.seed);
+        d.sp[0] = h->d_spins[0]; d.sp[1] = h->d_spins[1]; d.en[0] = h->d_E[0]; d.en[1] = h->d_E[1];
+        d.slots = kSchedSlots; d.t_end = t_end;
+        const int idx = (int)sw.size();
+        sw.push_back(d);
+        const int cls = batch_class(h->n);
+        const SweepCfg cfg = batch_cfg(cls);
+        const int32_t ctas = ((p.R + 3) / 4 + cfg.groups_per_cta - 1) / cfg.groups_per_cta;
+        // with sweeps = 0 the launch still copies the resampled population and its energies
+        auto &items = swi[h->d_ell != nullptr][p.rule][cls];
+        for (int32_t x = 0; x < ctas; ++x) items.push_back(make_int2(idx, x));
+        nmax[cls] = std::max(nmax[cls], h->n);
+        Rmax = std::max(Rmax, p.R);
+        CtlDesc c{nullptr, nullptr, h->d_best, h->d_ctl, h->W, p.target_cut, p.reheat_factor, p.beta0,
+                  h->n, p.R, p.stagnation, p.z_rst, p.win_short, p.win_long, p.max_distinct_short,
+                  p.max_distinct_long, {h->d_E[0], h->d_E[1]}, {h->d_spins[0], h->d_spins[1]}, t_end};
+        ctls.push_back(c);
+    }
+    std::vector<int2> all_items;
+    for (auto &a : swi)
+        for (auto &c : a)
+            for (auto &v : c) all_items.insert(all_items.end(), v.begin(), v.end());
+    const bool ok = upload(b, b->sd, sd) && upload(b, b->sdi, sdi) && upload(b, b->prep, prep) &&
+                    upload(b, b->tabs, tabs) && upload(b, b->sw, sw) && upload(b, b->ctl, ctls) &&
+                    upload(b, b->swi, all_items);
+    if (!ok) return bfail(b, PAMC_ERR_CUDA, "descriptor upload failed");
+    b->dirty = false;
+    b->graph_launches = 0;
+    if (prep.empty()) return PAMC_OK;
+    // one step: population step + tables, sweeps per (ELL, rule, class), controller, next schedule
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    int32_t nl = 0;
+    e = launch_population_batched((const PrepDesc *)b->prep.p, (const TabDesc *)b->tabs.p, (int32_t)prep.size(),
+                                  Rmax, b->stream);
+    nl += 2;
+    size_t off = 0;
+    for (int el = 0; el < 2 && e == cudaSuccess; ++el)
+        for (int ru = 0; ru < 2 && e == cudaSuccess; ++ru)
+            for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+                const auto &items = swi[el][ru][c];
+                if (items.empty()) continue;
+                e = launch_sweep_ising_batched(ru, el != 0, (const SweepDesc *)b->sw.p, (const int2 *)b->swi.p + off,
+                                               (int32_t)items.size(), nmax[c], batch_cfg(c), b->stream);
+                off += items.size();
+                nl += 1;
+            }
+    if (e == cudaSuccess) e = launch_control_batched((const CtlDesc *)b->ctl.p, (int32_t)ctls.size(), b->stream);
+    nl += 1;
+    if (e == cudaSuccess && !sdi.empty()) {
+        launch_schedule_batched((const SchedDesc *)b->sd.p, (const int2 *)b->sdi.p, (int32_t)sdi.size(), b->stream);
+        e = cudaGetLastError();
+        nl += 1;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return bfail(b, PAMC_ERR_CUDA, "capture of the batch step: %s", cudaGetErrorString(e));
+    }
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) {
+        drop_graph(b);
+        return bfail(b, PAMC_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    b->graph_launches = nl;
+    b->rebuilds += 1;
+    return PAMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pamc_footprint(pamc_handle h, const pamc_params *p) {
+    if (!h || !p || h->dense) return 0;
+    const size_t n = (size_t)h->n, R = (size_t)std::max(p->R, 1), S = (size_t)std::max(p->sweeps, 1);
+    const size_t slots = kSchedSlots;
+    size_t b = 2 * R * n + 2 * R * 8 + 4 * R * 4 + n;
+    b += slots * S * (n * 4 + (n + 1) * 4 + 4 + n * 4 + n * 4);
+    if (h->ell_w > 0) b += slots * S * (((n + 31) / 32) * 32 * (size_t)h->ell_w * 4 + n * 8);
+    b += (size_t)(p->kind == 0 ? 2 * h->H + 1 : (4 * h->H + 1) * (4 * h->H + 1) + 4 * h->H + 1) * 8;
+    if (p->stagnation && p->kind == 0) b += 6 * (size_t)std::min(p->n_top > 0 ? p->n_top : std::max(1, p->R / 16), p->R) * n;
+    b += ((size_t)h->n + 1) * 4 + (size_t)std::max(h->nnz, 1) * 4;   // the instance itself
+    return b + sizeof(DevCtl);
+}
+
+pamc_status pamc_batch_create(int cuda_device, void *stream, pamc_batch *out) {
+    if (!out) return bfail(nullptr, PAMC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (cudaSetDevice(cuda_device) != cudaSuccess) return bfail(nullptr, PAMC_ERR_CUDA, "cudaSetDevice failed");
+    pamc_batch b = new (std::nothrow) pamc_batch_s();
+    if (!b) return bfail(nullptr, PAMC_ERR_OOM, "host allocation failed");
+    b->device = cuda_device;
+    b->stream = (cudaStream_t)stream;
+    if (!b->stream) {   // graph capture needs a stream other than the legacy default one
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return bfail(nullptr, PAMC_ERR_CUDA, "stream creation failed");
+        }
+        b->own_stream = true;
+    }
+    *out = b;
+    return PAMC_OK;
+}
+
+pamc_status pamc_batch_add(pamc_batch b, pamc_handle h) {
+    if (!b || !h) return bfail(b, PAMC_ERR_ARG, "null batch or handle");
+    if (!h->initialized) return bfail(b, PAMC_ERR_STATE, "handle not initialised (pamc_init)");
+    if (h->dense || h->p.kind != 0) return bfail(b, PAMC_ERR_ARG, "batches hold sparse Max-Cut (Ising) instances");
+    if (h->p.stagnation || (h->p.z_rst > 0 && h->p.restart_reinit))
+        return bfail(b, PAMC_ERR_ARG, "batched members run without NCM and without restart re-initialisation");
+    if (h->device != b->device) return bfail(b, PAMC_ERR_ARG, "handle on another device");
+    for (pamc_handle m : b->members)
+        if (m == h) return bfail(b, PAMC_ERR_ARG, "handle already in the batch");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "cudaSetDevice failed");
+    // Inside the batch the schedule ring is refilled one step at a time: after
+    // step t it holds steps t+1 .. t+16.  Fill the slots of the steps up to
+    // host_t + 15 that the member's own stepping has not built yet.
+    const pamc_params &p = h->p;
+    const int64_t want = std::min<int64_t>(h->host_t + kSchedSlots, p.steps);
+    if (p.sweeps > 0 && h->sched_end < want) {
+        launch_schedule(h->n, h->d_rp, h->d_adj, p.seed, (int32_t)h->sched_end, (int32_t)(want - h->sched_end),
+                        p.sweeps, 0, kSchedSlots, h->d_order, h->d_lvl, h->d_nlev, h->d_skey, h->d_scnt,
+                        h->stream, h->d_ell, h->ell_w, h->d_pos);
+        h->launches += 1;
+        h->sched_end = want;
+    }
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "member sync: %s", cudaGetErrorString(e));
+    b->members.push_back(h);
+    b->dirty = true;
+    return PAMC_OK;
+}
+
+pamc_status pamc_batch_step(pamc_batch b, int32_t nsteps) {
+    if (!b || nsteps < 0) return bfail(b, PAMC_ERR_ARG, "null batch or nsteps < 0");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "cudaSetDevice failed");
+    for (int32_t it = 0; it < nsteps; ++it) {
+        if (b->dirty) {
+            const pamc_status s = rebuild(b);
+            if (s != PAMC_OK) return s;
+        }
+        if (!b->exec) break;   // nothing left to run
+        const cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+        if (e != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+        b->launches += b->graph_launches;
+        bool finished = false;
+        for (pamc_handle h : b->members) {
+            if (h->host_t >= h->p.steps) continue;
+            h->host_t += 1;
+            h->sched_end = std::min<int64_t>(h->host_t + kSchedSlots, h->p.steps);
+            h->launches += b->graph_launches;
+            finished |= h->host_t >= h->p.steps;
+        }
+        // a member that finished stays a no-op until the graph is rebuilt;
+        // rebuild once every member has finished so the loop ends
+        bool any = false;
+        for (pamc_handle h : b->members) any |= h->host_t < h->p.steps;
+        if (finished && !any) b->dirty = true;
+    }
+    return PAMC_OK;
+}
+
+int32_t pamc_batch_retire(pamc_batch b, pamc_handle *out, int32_t max_out) {
+    if (!b || (max_out > 0 && !out)) return -1;
+    std::vector<pamc_handle> keep, done;
+    for (pamc_handle h : b->members) {
+        if (h->host_t >= h->p.steps && (int32_t)done.size() < max_out) done.push_back(h);
+        else keep.push_back(h);
+    }
+    if (!done.empty()) {
+        if (cudaSetDevice(b->device) != cudaSuccess) return -1;
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return -1;
+        for (size_t i = 0; i < done.size(); ++i) out[i] = done[i];
+        b->members.swap(keep);
+        b->dirty = true;
+    }
+    return (int32_t)done.size();
+}
+
+int32_t pamc_batch_size(pamc_batch b) { return b ? (int32_t)b->members.size() : 0; }
+
+int32_t pamc_batch_active(pamc_batch b) {
+    if (!b) return 0;
+    int32_t a = 0;
+    for (pamc_handle h : b->members) a += h->host_t < h->p.steps;
+    return a;
+}
+
+int64_t pamc_batch_launch_count(pamc_batch b) { return b ? b->launches : 0; }
+
+int64_t pamc_batch_graph_builds(pamc_batch b) { return b ? b->rebuilds : 0; }
+
+pamc_status pamc_batch_sync(pamc_batch b) {
+    if (!b) return PAMC_ERR_ARG;
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "cudaSetDevice failed");
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "batch sync: %s", cudaGetErrorString(e));
+    return PAMC_OK;
+}
+
+pamc_status pamc_batch_last_error(pamc_batch b, char *buf, size_t len) {
+    if (!buf || len == 0) return PAMC_ERR_ARG;
+    snprintf(buf, len, "%s", b ? b->err : g_create_err);
+    return PAMC_OK;
+}
+
+void pamc_batch_destroy(pamc_batch b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (DevBuf *d : {&b->sw, &b->swi, &b->sd, &b->sdi, &b->prep, &b->tabs, &b->ctl})
+        if (d->p) cudaFree(d->p);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

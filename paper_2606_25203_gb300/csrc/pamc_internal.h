@@ -44,6 +44,73 @@ struct SchedView {
     int32_t W;               // ELL width (a multiple of 4, zero-padded)
 };
 
+// Everything the Ising sweep of one instance needs (single or batched launch).
+struct SweepDesc {
+    const int32_t *rp;
+    const uint32_t *adj;
+    const int32_t *sorder, *slvl, *snlev;
+    const uint32_t *sell;
+    const int2 *spos;
+    const uint64_t *tab;
+    const int8_t *src;
+    const int32_t *parent;
+    const int8_t *ncm_buf;
+    const int32_t *ncm_idx;
+    int8_t *dst;
+    int64_t *E_dst;
+    const DevCtl *ctl;
+    int32_t n, n_pad, H, R, S, t, slot, W;
+    PhiloxKeys K;
+    // batched launches: the step index comes from ctl->t, which selects the
+    // double-buffered spins/energies and the schedule slot; steps >= t_end are no-ops
+    int8_t *sp[2];
+    int64_t *en[2];
+    int32_t slots, t_end;
+};
+
+struct SchedDesc {
+    const int32_t *rp;
+    const uint32_t *adj;
+    int32_t *order, *lvl, *nlev, *scnt;
+    uint32_t *skey, *ell;
+    int2 *pos;
+    int32_t n, t0, S, slots, W;
+    uint32_t key0, key1;
+    // batched launches (ctl != nullptr): after step t's controller ran, build
+    // the schedule of step ctl->t + ahead, unless it is >= t_end or ctl->done
+    const DevCtl *ctl;
+    int32_t ahead, t_end;
+};
+
+struct PrepDesc {
+    const int64_t *E_src;
+    DevCtl *ctl;
+    int32_t *parent, *count, *ncm_idx, *targets;
+    int32_t R, kind, do_resample, n_top, tau;
+    uint32_t key0, key1;
+    const int64_t *en[2];   // E_src = en[ctl->t & 1]
+    int32_t t_end;
+};
+
+struct TabDesc {
+    const DevCtl *ctl;
+    uint64_t *tab;
+    int32_t rule, H, t_end;
+};
+
+struct CtlDesc {
+    const int64_t *E;
+    const int8_t *spins;
+    int8_t *best;
+    DevCtl *ctl;
+    int64_t W, target;
+    double reheat, beta0;
+    int32_t n, R, stagnation, z_rst, win_short, win_long, max_ds, max_dl;
+    const int64_t *en[2];   // E = en[(ctl->t + 1) & 1], spins = sp[(ctl->t + 1) & 1]
+    const int8_t *sp[2];
+    int32_t t_end;
+};
+
 // Launch configuration of the sparse sweep kernel.
 struct SweepCfg {
     int groups_per_cta;   // replica groups in one CTA
@@ -61,6 +128,13 @@ void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t
                      int2 *pos = nullptr);
 
 size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
+void launch_schedule_batched(const SchedDesc *descs, const int2 *items, int32_t nitems, cudaStream_t st);
+cudaError_t launch_population_batched(const PrepDesc *prep, const TabDesc *tabs, int32_t ninst,
+                                      int32_t R_max, cudaStream_t st);
+cudaError_t launch_control_batched(const CtlDesc *descs, int32_t ninst, cudaStream_t st);
+size_t prep_smem_bytes(int32_t R);
+cudaError_t launch_sweep_ising_batched(int rule, bool ell, const SweepDesc *descs, const int2 *items,
+                                       int32_t nitems, int32_t n_max, SweepCfg cfg, cudaStream_t st);
 cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uint32_t *adj,
                                int32_t H, const pamc_params &p, int32_t t, int32_t slot,
                                SchedView sv, const uint64_t *tab, const int8_t *src,

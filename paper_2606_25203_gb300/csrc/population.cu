@@ -17,6 +17,23 @@ namespace pamc {
 namespace {
 
 // ---------------------------------------------------------------- tables
+__device__ __forceinline__ void tables_ising_body(int rule, int32_t H, const DevCtl *__restrict__ ctl,
+                                                  uint64_t *__restrict__ tab, int bid, int nb) {
+    if (ctl->done) return;
+    const double beta = ctl->beta;
+    const int32_t n = 2 * H + 1;
+    for (int32_t i = bid * blockDim.x + threadIdx.x; i < n; i += nb * blockDim.x) {
+        const int32_t v = i - H;   // h (heat-bath) or s*h (Metropolis, dE = 2 s h)
+        tab[i] = rule == 0 ? thr_heatbath(beta, v) : thr_metropolis(beta, 2 * (int64_t)v);
+    }
+}
+
+__global__ void k_tables_batched(const TabDesc *__restrict__ descs) {
+    const TabDesc d = descs[blockIdx.x];
+    if (d.ctl->t >= d.t_end) return;
+    tables_ising_body(d.rule, d.H, d.ctl, d.tab, 0, 1);
+}
+
 __global__ void k_tables(int kind, int rule, int32_t H, const DevCtl *__restrict__ ctl,
                          uint64_t *__restrict__ tab) {
     if (ctl->done) return;
@@ -69,11 +86,11 @@ __device__ T block_reduce(T v, Op op, T *sbuf) {
 // ---------------------------------------------------------------- resampling
 constexpr int kPrepThreads = 1024;
 
-__global__ void __launch_bounds__(kPrepThreads)
-k_prep(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau, uint32_t key0,
-       uint32_t key1, const int64_t *__restrict__ E_src, DevCtl *__restrict__ ctl,
-       int32_t *__restrict__ parent, int32_t *__restrict__ count, int32_t *__restrict__ ncm_idx,
-       int32_t *__restrict__ targets) {
+__device__ __forceinline__ void
+prep_body(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau, uint32_t key0,
+          uint32_t key1, const int64_t *__restrict__ E_src, DevCtl *__restrict__ ctl,
+          int32_t *__restrict__ parent, int32_t *__restrict__ count, int32_t *__restrict__ ncm_idx,
+          int32_t *__restrict__ targets) {
     extern __shared__ __align__(16) unsigned char sm[];
     uint64_t *C = reinterpret_cast<uint64_t *>(sm);             // R prefix sums
     int32_t *cnt = reinterpret_cast<int32_t *>(sm + (size_t)R * 8);
@@ -181,6 +198,22 @@ k_prep(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau,
         ctl->ncm_last = ncm ? 1 : 0;
         if (ncm) { ctl->enable_cm = 0; ctl->cooldown = tau; }
     }
+}
+
+__global__ void __launch_bounds__(kPrepThreads)
+k_prep(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau, uint32_t key0,
+       uint32_t key1, const int64_t *__restrict__ E_src, DevCtl *__restrict__ ctl,
+       int32_t *__restrict__ parent, int32_t *__restrict__ count, int32_t *__restrict__ ncm_idx,
+       int32_t *__restrict__ targets) {
+    prep_body(R, kind, do_resample, n_top, tau, key0, key1, E_src, ctl, parent, count, ncm_idx, targets);
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep_batched(const PrepDesc *__restrict__ descs) {
+    const PrepDesc d = descs[blockIdx.x];
+    const int32_t t = d.ctl->t;
+    if (t >= d.t_end) return;
+    prep_body(d.R, d.kind, d.do_resample, d.n_top, d.tau, d.key0, d.key1, d.en[t & 1], d.ctl, d.parent, d.count,
+              d.ncm_idx, d.targets);
 }
 
 // ---------------------------------------------------------------- NCM
@@ -319,11 +352,11 @@ __device__ int32_t distinct_last(const int64_t *h, int32_t len, int32_t w) {
     return d;
 }
 
-__global__ void __launch_bounds__(kCtlThreads)
-k_control(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst, int32_t win_short,
-          int32_t win_long, int32_t max_ds, int32_t max_dl, double reheat, double beta0,
-          int64_t target, const int64_t *__restrict__ E, const int8_t *__restrict__ spins,
-          int8_t *__restrict__ best, DevCtl *__restrict__ ctl) {
+__device__ __forceinline__ void
+control_body(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst, int32_t win_short,
+             int32_t win_long, int32_t max_ds, int32_t max_dl, double reheat, double beta0,
+             int64_t target, const int64_t *__restrict__ E, const int8_t *__restrict__ spins,
+             int8_t *__restrict__ best, DevCtl *__restrict__ ctl) {
     __shared__ long long s_e[32];
     __shared__ int s_i[32];
     __shared__ int s_improved, s_rb;
@@ -398,6 +431,24 @@ k_control(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst, in
     if (target >= 0 && c.mstar >= target) c.done = 1;
 }
 
+__global__ void __launch_bounds__(kCtlThreads)
+k_control(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst, int32_t win_short,
+          int32_t win_long, int32_t max_ds, int32_t max_dl, double reheat, double beta0,
+          int64_t target, const int64_t *__restrict__ E, const int8_t *__restrict__ spins,
+          int8_t *__restrict__ best, DevCtl *__restrict__ ctl) {
+    control_body(n, W, R, stagnation, z_rst, win_short, win_long, max_ds, max_dl, reheat, beta0, target, E,
+                 spins, best, ctl);
+}
+
+__global__ void __launch_bounds__(kCtlThreads) k_control_batched(const CtlDesc *__restrict__ descs) {
+    const CtlDesc d = descs[blockIdx.x];
+    // every thread reads t before control_body's first barrier; thread 0 advances it afterwards
+    const int32_t t = d.ctl->t;
+    if (t >= d.t_end) return;
+    control_body(d.n, d.W, d.R, d.stagnation, d.z_rst, d.win_short, d.win_long, d.max_ds, d.max_dl,
+                 d.reheat, d.beta0, d.target, d.en[(t + 1) & 1], d.sp[(t + 1) & 1], d.best, d.ctl);
+}
+
 }  // namespace
 
 cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint64_t *tab,
@@ -443,6 +494,23 @@ cudaError_t launch_control(int32_t n, int64_t W, const pamc_params &p, const int
     k_control<<<1, kCtlThreads, 0, st>>>(n, W, p.R, p.stagnation, p.z_rst, p.win_short, p.win_long,
                                          p.max_distinct_short, p.max_distinct_long, p.reheat_factor,
                                          p.beta0, p.target_cut, E, spins, best, ctl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_population_batched(const PrepDesc *prep, const TabDesc *tabs, int32_t ninst,
+                                      int32_t R_max, cudaStream_t st) {
+    if (ninst <= 0) return cudaSuccess;
+    const size_t smem = prep_smem_bytes(R_max);
+    cudaError_t err = cudaFuncSetAttribute(k_prep_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    k_prep_batched<<<ninst, kPrepThreads, smem, st>>>(prep);
+    k_tables_batched<<<ninst, 256, 0, st>>>(tabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_control_batched(const CtlDesc *descs, int32_t ninst, cudaStream_t st) {
+    if (ninst <= 0) return cudaSuccess;
+    k_control_batched<<<ninst, kCtlThreads, 0, st>>>(descs);
     return cudaGetLastError();
 }
 

@@ -25,13 +25,12 @@ __device__ __forceinline__ bool before(uint32_t ka, int32_t a, uint32_t kb, int3
 
 constexpr int kSchedThreads = 512;
 
-__global__ void __launch_bounds__(kSchedThreads)
-k_schedule(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
-           uint32_t key0, uint32_t key1, int32_t t0, int32_t S, int32_t slots,
-           int32_t *__restrict__ order, int32_t *__restrict__ lvl_ptr, int32_t *__restrict__ nlev,
-           uint32_t *__restrict__ skey, int32_t *__restrict__ scnt, uint32_t *__restrict__ ell,
-           int32_t W, int2 *__restrict__ pos) {
-    const int b = blockIdx.x;
+__device__ __forceinline__ void
+schedule_body(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
+              uint32_t key0, uint32_t key1, int32_t t0, int32_t S, int32_t slots,
+              int32_t *__restrict__ order, int32_t *__restrict__ lvl_ptr, int32_t *__restrict__ nlev,
+              uint32_t *__restrict__ skey, int32_t *__restrict__ scnt, uint32_t *__restrict__ ell,
+              int32_t W, int2 *__restrict__ pos, int b) {
     const int ti = b / S, sw = b % S;
     const int32_t t = t0 + ti;
     const int slot = t % slots;
@@ -110,6 +109,30 @@ k_schedule(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict
     }
 }
 
+__global__ void __launch_bounds__(kSchedThreads)
+k_schedule(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
+           uint32_t key0, uint32_t key1, int32_t t0, int32_t S, int32_t slots,
+           int32_t *__restrict__ order, int32_t *__restrict__ lvl_ptr, int32_t *__restrict__ nlev,
+           uint32_t *__restrict__ skey, int32_t *__restrict__ scnt, uint32_t *__restrict__ ell,
+           int32_t W, int2 *__restrict__ pos) {
+    schedule_body(n, rp, adj, key0, key1, t0, S, slots, order, lvl_ptr, nlev, skey, scnt, ell, W, pos,
+                  blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kSchedThreads)
+k_schedule_batched(const SchedDesc *__restrict__ descs, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const SchedDesc d = descs[it.x];
+    int32_t t0 = d.t0;
+    if (d.ctl) {
+        if (d.ctl->done) return;
+        t0 = d.ctl->t + d.ahead;
+        if (t0 >= d.t_end) return;
+    }
+    schedule_body(d.n, d.rp, d.adj, d.key0, d.key1, t0, d.S, d.slots, d.order, d.lvl, d.nlev, d.skey,
+                  d.scnt, d.ell, d.W, d.pos, it.y);
+}
+
 }  // namespace
 
 void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t seed, int32_t t0,
@@ -120,6 +143,11 @@ void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t
     k_schedule<<<nt * S, kSchedThreads, 0, st>>>(n, rp, adj, (uint32_t)seed, (uint32_t)(seed >> 32),
                                                   t0, S, slots, order, lvl_ptr, nlev, skey, scnt,
                                                   ell, W, pos);
+}
+
+void launch_schedule_batched(const SchedDesc *descs, const int2 *items, int32_t nitems, cudaStream_t st) {
+    if (nitems <= 0) return;
+    k_schedule_batched<<<nitems, kSchedThreads, 0, st>>>(descs, items);
 }
 
 }  // namespace pamc

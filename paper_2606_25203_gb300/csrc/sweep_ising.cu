@@ -31,17 +31,20 @@ __device__ __forceinline__ void group_barrier(int id, int nthreads, int groups) 
     }
 }
 
+// The sweep of one CTA's replica groups (groups bid*gpc .. bid*gpc+gpc-1 of
+// the instance), shared by the single-instance and the batched kernels.
 template <bool ELLP, int RULE>
-__global__ void __launch_bounds__(1024)
-k_sweep_ising(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
-              const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, PhiloxKeys K,
-              int32_t t, int32_t slot, const int32_t *__restrict__ sorder,
-              const int32_t *__restrict__ slvl, const int32_t *__restrict__ snlev,
-              const uint32_t *__restrict__ sell, const int2 *__restrict__ spos, int32_t W,
-              const uint64_t *__restrict__ tab, const int8_t *__restrict__ src,
-              const int32_t *__restrict__ parent, const int8_t *__restrict__ ncm_buf,
-              const int32_t *__restrict__ ncm_idx, int8_t *__restrict__ dst,
-              int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int gpc, int tpg) {
+__device__ __forceinline__ void
+sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
+                 const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, const PhiloxKeys &K,
+                 int32_t t, int32_t slot, const int32_t *__restrict__ sorder,
+                 const int32_t *__restrict__ slvl, const int32_t *__restrict__ snlev,
+                 const uint32_t *__restrict__ sell, const int2 *__restrict__ spos, int32_t W,
+                 const uint64_t *__restrict__ tab, const int8_t *__restrict__ src,
+                 const int32_t *__restrict__ parent, const int8_t *__restrict__ ncm_buf,
+                 const int32_t *__restrict__ ncm_idx, int8_t *__restrict__ dst,
+                 int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int gpc, int tpg,
+                 int32_t bid) {
     extern __shared__ __align__(16) uint8_t smem[];
     if (ctl->done) return;
     const int tabn = 2 * H + 1;
@@ -52,7 +55,7 @@ k_sweep_ising(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     for (int i = threadIdx.x; i < gpc * 4; i += blockDim.x) red[i] = 0ull;
 
     const int gl = threadIdx.x / tpg, li = threadIdx.x % tpg;
-    const int32_t g = blockIdx.x * gpc + gl;
+    const int32_t g = bid * gpc + gl;
     const int32_t r0 = g * 4;
     const bool active = r0 < R;
     uint32_t *sp = spins_all + (size_t)gl * n_pad;
@@ -206,6 +209,32 @@ k_sweep_ising(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 4 + li] / 2);
 }
 
+template <bool ELLP, int RULE>
+__global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int tpg) {
+    sweep_ising_body<ELLP, RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, d.K, d.t, d.slot, d.sorder, d.slvl,
+                                 d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf, d.ncm_idx,
+                                 d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x);
+}
+
+// Many instances in one launch: CTA b works on instance items[b].x, its
+// local block items[b].y.  Descriptors live in device memory.
+template <bool ELLP, int RULE>
+__global__ void __launch_bounds__(1024)
+k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restrict__ items, int gpc, int tpg) {
+    const int2 it = items[blockIdx.x];
+    SweepDesc d = descs[it.x];
+    const int32_t t = d.ctl->t;
+    if (t >= d.t_end) return;
+    d.t = t;
+    d.slot = t % d.slots;
+    d.src = d.sp[t & 1];
+    d.dst = d.sp[(t + 1) & 1];
+    d.E_dst = d.en[(t + 1) & 1];
+    sweep_ising_body<ELLP, RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, d.K, d.t, d.slot, d.sorder, d.slvl,
+                                 d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf, d.ncm_idx,
+                                 d.dst, d.E_dst, d.ctl, gpc, tpg, it.y);
+}
+
 }  // namespace
 
 size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg) {
@@ -222,20 +251,43 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
                                const DevCtl *ctl, SweepCfg cfg, cudaStream_t st) {
     const int32_t groups = (p.R + 3) / 4;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
-    const int32_t n_pad = (n + 3) & ~3;
+    SweepDesc d;
+    d.rp = rp; d.adj = adj; d.sorder = sv.order; d.slvl = sv.lvl_ptr; d.snlev = sv.nlev; d.sell = sv.ell;
+    d.spos = sv.pos; d.tab = tab; d.src = src; d.parent = parent; d.ncm_buf = ncm_buf; d.ncm_idx = ncm_idx;
+    d.dst = dst; d.E_dst = E_dst; d.ctl = ctl; d.n = n; d.n_pad = (n + 3) & ~3; d.H = H; d.R = p.R;
+    d.S = p.sweeps; d.t = t; d.slot = slot; d.W = sv.W; d.K = make_philox_keys(p.seed);
     const size_t smem = sweep_ising_smem_bytes(n, H, cfg);
     const int grid = (groups + gpc - 1) / gpc;
-    const PhiloxKeys K = make_philox_keys(p.seed);
     const bool ell = sv.ell != nullptr;
     cudaError_t err = cudaSuccess;
-#define PAMC_LAUNCH(EL, RU)                                                                   \
+#define PAMC_LAUNCH(EL, RU)                                                                       \
     do {                                                                                          \
-        err = cudaFuncSetAttribute(k_sweep_ising<EL, RU>,                                     \
+        err = cudaFuncSetAttribute(k_sweep_ising<EL, RU>,                                         \
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
         if (err != cudaSuccess) return err;                                                       \
-        k_sweep_ising<EL, RU><<<grid, gpc * tpg, smem, st>>>(                                 \
-            n, n_pad, rp, adj, H, p.R, p.sweeps, K, t, slot, sv.order, sv.lvl_ptr, sv.nlev,       \
-            sv.ell, sv.pos, sv.W, tab, src, parent, ncm_buf, ncm_idx, dst, E_dst, ctl, gpc, tpg); \
+        k_sweep_ising<EL, RU><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);                        \
+    } while (0)
+    if (ell) {
+        if (rule == 0) PAMC_LAUNCH(true, 0); else PAMC_LAUNCH(true, 1);
+    } else {
+        if (rule == 0) PAMC_LAUNCH(false, 0); else PAMC_LAUNCH(false, 1);
+    }
+#undef PAMC_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_ising_batched(int rule, bool ell, const SweepDesc *descs, const int2 *items,
+                                       int32_t nitems, int32_t n_max, SweepCfg cfg, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
+    const size_t smem = sweep_ising_smem_bytes(n_max, 127, cfg);
+    cudaError_t err = cudaSuccess;
+#define PAMC_LAUNCH(EL, RU)                                                                       \
+    do {                                                                                          \
+        err = cudaFuncSetAttribute(k_sweep_ising_batched<EL, RU>,                                 \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        if (err != cudaSuccess) return err;                                                       \
+        k_sweep_ising_batched<EL, RU><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg);   \
     } while (0)
     if (ell) {
         if (rule == 0) PAMC_LAUNCH(true, 0); else PAMC_LAUNCH(true, 1);

@@ -1,0 +1,229 @@
+"""Batched execution: every member of a batch computes exactly what it computes
+alone (spins, energies, parents, copy counts, controller state and best cut),
+whatever joins or leaves the batch meanwhile, and one member is checked against
+the oracle directly.  The serving loop returns the same cut and configuration
+for each request as the one-instance-at-a-time path."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_25203_gb300 as pg
+    pg.load()
+    return pg
+
+
+def mix():
+    """Instances of every size class (n <= 2048, <= 8192, larger), both weight
+    kinds, CSR and ELL sweeps, ragged R, both update rules."""
+    return [
+        (W.erdos_renyi(300, 0.05, signed=False, seed=1), dict(R=64, sweeps=2, steps=21, rule=0, seed=11)),
+        (W.gnm(1500, 4300, signed=True, seed=2), dict(R=50, sweeps=3, steps=34, rule=1, seed=12)),
+        (W.torus(60, 60, signed=True, seed=3), dict(R=96, sweeps=2, steps=19, rule=0, seed=13)),
+        (W.torus(30, 30, signed=False, seed=6), dict(R=20, sweeps=0, steps=9, rule=0, seed=16)),
+        (W.er_avg_degree(9000, 12, signed=True, seed=4), dict(R=36, sweeps=1, steps=18, rule=0, seed=14)),
+        (W.er_avg_degree(2100, 20, signed=False, seed=5), dict(R=128, sweeps=2, steps=40, rule=1, seed=15,
+                                                            z_rst=13, restart_reinit=0)),
+    ]
+
+
+def snapshot(pg, h, n, R):
+    spins, E, par, cnt = pg.pamc_state(h, R, n)
+    m, b = pg.pamc_best(h, n)
+    return dict(spins=spins, E=E, par=par, cnt=cnt, best=(m, b), ctl=pg.pamc_control_state(h))
+
+
+def assert_same(a, b, where):
+    for k in ("spins", "E", "par", "cnt"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=f"{k} {where}")
+    assert a["best"][0] == b["best"][0], f"M* {where}"
+    np.testing.assert_array_equal(a["best"][1], b["best"][1], err_msg=f"best spins {where}")
+    for k, v in a["ctl"].items():
+        assert v == b["ctl"][k], f"ctl {k} {where}: {v} != {b['ctl'][k]}"
+
+
+def alone(pg, inst, p):
+    h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+    pg.pamc_run(h, **p)
+    s = snapshot(pg, h, inst.n, p["R"])
+    pg.pamc_destroy(h)
+    return s
+
+
+def test_batch_members_equal_alone(pg):
+    cases = mix()
+    ref = [alone(pg, inst, p) for inst, p in cases]
+    b = pg.pamc_batch_create(0)
+    hs = []
+    try:
+        # staggered joins: two members first, the rest after some steps
+        for i, (inst, p) in enumerate(cases):
+            h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+            pg.pamc_init(h, **p)
+            hs.append(h)
+        pg.pamc_batch_add(b, hs[0])
+        pg.pamc_batch_add(b, hs[1])
+        pg.pamc_batch_step(b, 5)
+        for h in hs[2:]:
+            pg.pamc_batch_add(b, h)
+        got = {}
+        while pg.pamc_batch_size(b) > 0:
+            pg.pamc_batch_step(b, 3)
+            for h in pg.pamc_batch_retire(b):
+                i = [x.value for x in hs].index(h.value)
+                inst, p = cases[i]
+                got[i] = snapshot(pg, h, inst.n, p["R"])
+        assert sorted(got) == list(range(len(cases)))
+        for i in range(len(cases)):
+            assert_same(got[i], ref[i], f"member {i} ({cases[i][0].name})")
+        assert pg.pamc_batch_graph_builds(b) >= 2
+    finally:
+        for h in hs:
+            pg.pamc_destroy(h)
+        pg.pamc_batch_destroy(b)
+
+
+def test_batch_member_matches_oracle(pg):
+    inst = W.erdos_renyi(200, 0.06, signed=True, seed=7)
+    p = dict(R=40, sweeps=2, steps=20, rule=0, seed=5, beta0=0.2, beta1=2.5)
+    ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **p)
+    ref.step(p["steps"])
+    other = W.torus(20, 20, signed=True, seed=8)
+    b = pg.pamc_batch_create(0)
+    h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+    h2 = pg.pamc_create_csr(other.n, other.row_ptr, other.col, other.w)
+    try:
+        pg.pamc_init(h, **p)
+        pg.pamc_init(h2, R=64, sweeps=3, steps=50, seed=9)
+        pg.pamc_batch_add(b, h2)
+        pg.pamc_batch_add(b, h)
+        pg.pamc_batch_step(b, p["steps"])
+        pg.pamc_batch_sync(b)
+        spins, E, par, cnt = pg.pamc_state(h, p["R"], inst.n)
+        np.testing.assert_array_equal(spins, ref.spins())
+        np.testing.assert_array_equal(E, ref.energy())
+        rp, rc = ref.parents()
+        np.testing.assert_array_equal(par, rp)
+        np.testing.assert_array_equal(cnt, rc)
+        m, bs = pg.pamc_best(h, inst.n)
+        rm, rb = ref.best()
+        assert m == rm
+        np.testing.assert_array_equal(bs, rb)
+    finally:
+        pg.pamc_destroy(h)
+        pg.pamc_destroy(h2)
+        pg.pamc_batch_destroy(b)
+
+
+def test_join_after_stepping_alone(pg):
+    """A handle stepped on its own for a while (schedule ring partly used) and
+    then moved into a batch ends exactly where a run alone ends."""
+    inst = W.gnm(900, 2600, signed=True, seed=21)
+    p = dict(R=72, sweeps=2, steps=45, rule=0, seed=3)
+    ref = alone(pg, inst, p)
+    for pre in (5, 16, 17):
+        h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+        b = pg.pamc_batch_create(0)
+        try:
+            pg.pamc_init(h, **p)
+            pg.pamc_step(h, pre)
+            pg.pamc_sync(h)
+            pg.pamc_batch_add(b, h)
+            pg.pamc_batch_step(b, p["steps"])
+            assert len(pg.pamc_batch_retire(b)) == 1
+            assert_same(snapshot(pg, h, inst.n, p["R"]), ref, f"joined after {pre} steps")
+        finally:
+            pg.pamc_destroy(h)
+            pg.pamc_batch_destroy(b)
+
+
+def test_finished_member_is_frozen_and_target_stop(pg):
+    """A member past its last step does nothing while the others go on; a
+    member that reaches its target cut stops as it does alone."""
+    a = W.torus(16, 16, signed=True, seed=31)
+    c = W.erdos_renyi(150, 0.08, signed=False, seed=32)
+    pa = dict(R=32, sweeps=2, steps=6, seed=1)
+    pc = dict(R=32, sweeps=2, steps=30, seed=2)
+    ra = alone(pg, a, pa)
+    # target: the cut the run alone reaches after 10 steps
+    h = pg.pamc_create_csr(c.n, c.row_ptr, c.col, c.w)
+    pg.pamc_init(h, **pc)
+    pg.pamc_step(h, 10)
+    target, _ = pg.pamc_best(h, c.n)
+    pg.pamc_destroy(h)
+    pc["target_cut"] = int(target)
+    rc = alone(pg, c, pc)
+    assert rc["ctl"]["done"] == 1
+    b = pg.pamc_batch_create(0)
+    ha = pg.pamc_create_csr(a.n, a.row_ptr, a.col, a.w)
+    hc = pg.pamc_create_csr(c.n, c.row_ptr, c.col, c.w)
+    try:
+        pg.pamc_init(ha, **pa)
+        pg.pamc_init(hc, **pc)
+        pg.pamc_batch_add(b, ha)
+        pg.pamc_batch_add(b, hc)
+        pg.pamc_batch_step(b, 40)   # a finishes after 6 steps and stays in the graph
+        pg.pamc_batch_sync(b)
+        assert pg.pamc_batch_active(b) == 0
+        assert_same(snapshot(pg, ha, a.n, pa["R"]), ra, "finished member")
+        assert_same(snapshot(pg, hc, c.n, pc["R"]), rc, "member stopped at its target")
+        assert len(pg.pamc_batch_retire(b)) == 2
+    finally:
+        pg.pamc_destroy(ha)
+        pg.pamc_destroy(hc)
+        pg.pamc_batch_destroy(b)
+
+
+def test_batch_refusals(pg):
+    inst = W.torus(8, 8, signed=True, seed=1)
+    b = pg.pamc_batch_create(0)
+    h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+    try:
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_add(b, h)                       # not initialised
+        pg.pamc_init(h, R=16, steps=5, stagnation=1)
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_add(b, h)                       # NCM members are refused
+        pg.pamc_init(h, R=16, steps=5, z_rst=3, restart_reinit=1)
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_add(b, h)                       # restart re-initialisation refused
+        pg.pamc_init(h, R=16, steps=5, kind=1)
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_add(b, h)                       # Potts members are refused
+        pg.pamc_init(h, R=16, steps=5)
+        pg.pamc_batch_add(b, h)
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_add(b, h)                       # already a member
+        assert pg.pamc_footprint(h, R=16, steps=5) > 16 * inst.n * 2
+    finally:
+        pg.pamc_batch_destroy(b)
+        pg.pamc_destroy(h)
+
+
+def test_server_equals_sequential(pg):
+    from paper_2606_25203_gb300.serving import Server, serve_sequential
+    reqs = W.serving_stream(10, rate=400.0, seed=3, n_lo=300, n_hi=5000, er_degree=10.0)
+    params = dict(R=64, sweeps=2, steps=24, beta0=0.1, beta1=3.0, seed=17)
+    seq = serve_sequential(reqs, params, keep_spins=True)
+    # a small budget forces admission to wait for retirements
+    srv = Server(hbm_budget=40 << 20, max_active=4, steps_per_tick=3, keep_spins=True)
+    try:
+        st = srv.serve(reqs, params)
+    finally:
+        srv.close()
+    assert len(st.results) == len(reqs)
+    assert st.peak_active <= 4
+    a = {r.rid: r for r in seq.results}
+    for r in st.results:
+        assert r.cut == a[r.rid].cut, f"request {r.rid}"
+        np.testing.assert_array_equal(r.spins, a[r.rid].spins, err_msg=f"request {r.rid}")
+        assert r.finished >= r.admitted >= r.arrival - 1e-9

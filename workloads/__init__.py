@@ -195,3 +195,62 @@ def c2b_sparse7000(seed: int = 0) -> Instance:
 def c3_sparse2000(seed: int = 0) -> Instance:
     """Random sparse N=2,000, average degree 12 (12,000 edges), unit weights."""
     return gnm(2000, 12000, signed=False, seed=seed)
+
+
+def er_avg_degree(n: int, avg_deg: float, signed: bool = False, seed: int = 0) -> Instance:
+    """Erdos-Renyi G(n, m) with m = round(n * avg_deg / 2) distinct uniform edges,
+    drawn vectorised (oversample pairs, keep the first m distinct ones in draw
+    order), so that n = 20,000 takes milliseconds."""
+    m = int(round(n * avg_deg / 2))
+    m = min(m, n * (n - 1) // 2)
+    rng = np.random.default_rng([seed, 4, n, m])
+    codes = np.zeros(0, dtype=np.int64)
+    while True:
+        k = 2 * m + 64
+        a = rng.integers(0, n, size=k)
+        b = rng.integers(0, n, size=k)
+        keep = a != b
+        lo, hi = np.minimum(a[keep], b[keep]), np.maximum(a[keep], b[keep])
+        codes = np.concatenate([codes, lo * n + hi])
+        _, first = np.unique(codes, return_index=True)
+        if first.shape[0] >= m:
+            break
+    sel = codes[np.sort(first)[:m]]
+    ei, ej = sel // n, sel % n
+    return csr_from_edges(n, ei, ej, _weights(rng, m, signed),
+                          f"er_n{n}_d{avg_deg}_{'pm1' if signed else 'unit'}_s{seed}")
+
+
+@dataclass
+class Request:
+    """One solve request of a serving stream: an instance and its arrival time (s)."""
+    rid: int
+    inst: Instance
+    arrival: float
+
+
+def serving_stream(count: int, rate: float, seed: int = 0, n_lo: int = 800, n_hi: int = 20000,
+                   er_degree: float = 20.0) -> list:
+    """Max-Cut requests with Poisson arrivals (exponential gaps, mean 1/rate s),
+    N uniform in [n_lo, n_hi], the graph type cycling through Erdos-Renyi with
+    unit weights, Erdos-Renyi with +-1 weights and a +-1 torus (side
+    round(sqrt(N)), so N becomes side^2).  Erdos-Renyi requests have average
+    degree er_degree (the G22-G31 / G43-G47 density class)."""
+    rng = np.random.default_rng([seed, 5, count])
+    gaps = rng.exponential(1.0 / rate, size=count) if rate > 0 else np.zeros(count)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    sizes = rng.integers(n_lo, n_hi + 1, size=count)
+    kinds = rng.integers(0, 3, size=count)
+    out = []
+    for i in range(count):
+        n = int(sizes[i])
+        s = seed * 100003 + i
+        if kinds[i] == 0:
+            inst = er_avg_degree(n, er_degree, signed=False, seed=s)
+        elif kinds[i] == 1:
+            inst = er_avg_degree(n, er_degree, signed=True, seed=s)
+        else:
+            side = max(3, int(round(np.sqrt(n))))
+            inst = torus(side, side, signed=True, seed=s)
+        out.append(Request(i, inst, float(arrivals[i])))
+    return out
