@@ -774,7 +774,7 @@ bool upload(pamc_batch b, DevBuf &buf, const std::vector<T> &v) {
 constexpr int kClasses = 3;
 int batch_class(int32_t n) { return n <= 2048 ? 0 : n <= 8192 ? 1 : 2; }
 SweepCfg batch_cfg(int cls) {
-    static const SweepCfg c[kClasses] = {{4, 1}, {2, 4}, {1, 8}};
+    static const SweepCfg c[kClasses] = {{8, 1}, {4, 2}, {1, 16}};
     const char *env = getenv("PAMC_BATCH_CFG");   // "g0,w0;g1,w1;g2,w2"
     if (env) {
         int v[6];

@@ -31,12 +31,28 @@ __device__ __forceinline__ void group_barrier(int id, int nthreads, int groups) 
     }
 }
 
+// Philox draws with the round keys precomputed (kernel parameter space) or
+// advanced on the fly from the seed (batched launches, where the key differs
+// per instance and would otherwise sit in local memory).
+struct KeysPre {
+    const PhiloxKeys &K;
+    __device__ __forceinline__ u32x4 operator()(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) const {
+        return philox_rk(c0, c1, c2, c3, K);
+    }
+};
+struct KeysSeed {
+    uint32_t k0, k1;
+    __device__ __forceinline__ u32x4 operator()(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) const {
+        return philox(c0, c1, c2, c3, k0, k1);
+    }
+};
+
 // The sweep of one CTA's replica groups (groups bid*gpc .. bid*gpc+gpc-1 of
 // the instance), shared by the single-instance and the batched kernels.
-template <bool ELLP, int RULE>
+template <bool ELLP, int RULE, class KeyT>
 __device__ __forceinline__ void
 sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
-                 const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, const PhiloxKeys &K,
+                 const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, const KeyT &draw,
                  int32_t t, int32_t slot, const int32_t *__restrict__ sorder,
                  const int32_t *__restrict__ slvl, const int32_t *__restrict__ snlev,
                  const uint32_t *__restrict__ sell, const int2 *__restrict__ spos, int32_t W,
@@ -120,24 +136,53 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                     // A: byte q = 128 + sum_j J_kj [s_j = +1] of replica q
                     uint32_t A = 0x80808080u;
                     int32_t k, jsum;
+                    u32x4 u;
                     if (ELLP) {
                         const uint32_t a0 = (uint32_t)pr.x;
                         k = (int32_t)(a0 & 0xFFFFFFu);
                         const int32_t deg = (int32_t)(a0 >> 24);
                         jsum = pr.y;
+                        // the next neighbour words are requested before the draw is
+                        // computed, so that the Philox rounds overlap their latency
+                        if (W <= 4) {   // every neighbour word is already in registers
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)   // padding slots: coupling 0
+                                A += sp[e4[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e4[q] >> 24);
+                            u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
+                        } else {
+                        const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31) + 4 * 32;
+                        // up to sixteen more neighbour words in flight before the draw
+                        uint32_t ev[8], ew[8];
+                        if (deg > 4) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) ev[q] = (4 + q < W) ? ep[q * 32] : 0u;
+                        }
+                        if (deg > 12) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) ew[q] = (12 + q < W) ? ep[(8 + q) * 32] : 0u;
+                        }
+                        u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
 #pragma unroll
                         for (int q = 0; q < 4; ++q)   // padding slots: coupling 0
                             A += sp[e4[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e4[q] >> 24);
                         if (deg > 4) {
-                            const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
-                            for (int32_t b0 = 4; b0 < deg; b0 += 4) {
-                                uint32_t ev[4];
 #pragma unroll
-                                for (int q = 0; q < 4; ++q) ev[q] = ep[(b0 + q) * 32];
+                            for (int q = 0; q < 8; ++q)
+                                A += sp[ev[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ev[q] >> 24);
+                        }
+                        if (deg > 12) {
 #pragma unroll
-                                for (int q = 0; q < 4; ++q)
-                                    A += sp[ev[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ev[q] >> 24);
-                            }
+                            for (int q = 0; q < 8; ++q)
+                                A += sp[ew[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ew[q] >> 24);
+                        }
+                        for (int32_t b0 = 20; b0 < deg; b0 += 8) {
+                            ep += (b0 == 20 ? 16 : 8) * 32;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) ev[q] = (b0 + q < W) ? ep[q * 32] : 0u;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                A += sp[ev[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ev[q] >> 24);
+                        }
                         }
                     } else {
                         k = ord[i] & 0xFFFFFF;
@@ -149,8 +194,8 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                             jsum += J;
                         }
                     }
+                    if (!ELLP) u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
                     const int32_t c0 = H - 256 - jsum;
-                    const u32x4 u = philox_rk((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3, K);
                     const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
                     const uint32_t old = sp[k];
                     uint32_t nw = 0;
@@ -211,28 +256,26 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
 
 template <bool ELLP, int RULE>
 __global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int tpg) {
-    sweep_ising_body<ELLP, RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, d.K, d.t, d.slot, d.sorder, d.slvl,
-                                 d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf, d.ncm_idx,
-                                 d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x);
+    sweep_ising_body<ELLP, RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t, d.slot, d.sorder,
+                                 d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf,
+                                 d.ncm_idx, d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x);
 }
 
 // Many instances in one launch: CTA b works on instance items[b].x, its
-// local block items[b].y.  Descriptors live in device memory.
+// local block items[b].y.  Descriptors live in device memory and are read
+// field by field (no local copy of the descriptor).
 template <bool ELLP, int RULE>
 __global__ void __launch_bounds__(1024)
 k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restrict__ items, int gpc, int tpg) {
     const int2 it = items[blockIdx.x];
-    SweepDesc d = descs[it.x];
-    const int32_t t = d.ctl->t;
+    const SweepDesc &d = descs[it.x];
+    const DevCtl *ctl = d.ctl;
+    const int32_t t = ctl->t;
     if (t >= d.t_end) return;
-    d.t = t;
-    d.slot = t % d.slots;
-    d.src = d.sp[t & 1];
-    d.dst = d.sp[(t + 1) & 1];
-    d.E_dst = d.en[(t + 1) & 1];
-    sweep_ising_body<ELLP, RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, d.K, d.t, d.slot, d.sorder, d.slvl,
-                                 d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf, d.ncm_idx,
-                                 d.dst, d.E_dst, d.ctl, gpc, tpg, it.y);
+    const KeysSeed draw{d.K.k0[0], d.K.k1[0]};
+    sweep_ising_body<ELLP, RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.sorder,
+                                 d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.ncm_buf,
+                                 d.ncm_idx, d.sp[(t + 1) & 1], d.en[(t + 1) & 1], ctl, gpc, tpg, it.y);
 }
 
 }  // namespace
