@@ -441,6 +441,14 @@ def run_serving(args):
     warm = W.serving_stream(max(3, args.warmup), rate=0.0, seed=2, n_lo=800, n_hi=2000)
     wp = dict(P, steps=4)
     srv = Server(max_active=args.serve_max_active, steps_per_tick=2)
+    # launch shape per size class, tuned on copies of requests from another stream
+    t1 = time.perf_counter()
+    tune_reqs = W.serving_stream(24, rate=0.0, seed=3)
+    samples = []
+    for lo, hi in ((800, 2048), (2049, 8192), (8193, 20000)):
+        samples += [r.inst for r in tune_reqs if lo <= r.inst.n <= hi][:6]
+    shapes = srv.autotune(samples, P)
+    tune_s = time.perf_counter() - t1
     srv.serve(warm, wp)
     serve_sequential(warm, wp)
     torch.cuda.synchronize()
@@ -485,6 +493,9 @@ def run_serving(args):
                 "d2h_bytes_per_step": int(np.mean([r.inst.n + 8 for r in burst]))},
         "clocks": clk.summary(), "gpu_launches": st.launches, "graph_builds": st.graph_builds,
         "peak_active": st.peak_active, "peak_resident_bytes": st.peak_bytes,
+        "batch_shapes": {str(c): {"groups_per_cta": g, "warps_per_group": w, "ms_per_step": ms}
+                         for c, (g, w, ms) in shapes.items()},
+        "autotune_s": tune_s,
         "request_generation_s": gen_s,
     }
     print(json.dumps(line))

@@ -184,6 +184,15 @@ pamc_status pamc_batch_step(pamc_batch b, int32_t nsteps);
  * them to out, after waiting for the batch stream; returns how many, or -1
  * on error (null batch, out NULL with max_out > 0, CUDA error). */
 int32_t pamc_batch_retire(pamc_batch b, pamc_handle *out, int32_t max_out);
+/* Size class of an n-spin member: 0 for n <= 2048, 1 for n <= 8192, 2 above. */
+int pamc_size_class(int32_t n);
+/* Launch shape of the batched sweep for one size class: replica groups (of
+ * four replicas) per CTA and warps per group, groups * warps <= 32.  Where the
+ * class's largest member needs it, fewer groups per CTA are used so that the
+ * spins fit shared memory.  The shape changes speed only, never results.
+ * Takes effect at the next pamc_batch_step.  PAMC_ERR_ARG when out of range. */
+pamc_status pamc_batch_set_shape(pamc_batch b, int size_class, int groups_per_cta, int warps_per_group);
+pamc_status pamc_batch_get_shape(pamc_batch b, int size_class, int *groups_per_cta, int *warps_per_group);
 int32_t pamc_batch_size(pamc_batch b);      /* members, finished or not */
 int32_t pamc_batch_active(pamc_batch b);    /* members with steps left */
 int64_t pamc_batch_launch_count(pamc_batch b);  /* kernel launches enqueued */

@@ -24,7 +24,8 @@ __all__ = [
     "pamc_launch_count", "pamc_weight_sum", "pamc_last_error", "pamc_destroy", "Solver",
     "pamc_sweeps_noalloc", "pamc_footprint", "pamc_batch_create", "pamc_batch_add", "pamc_batch_step",
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
-    "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy",
+    "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
+    "pamc_batch_set_shape", "pamc_batch_get_shape",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -131,6 +132,12 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     for nm in ("pamc_batch_launch_count", "pamc_batch_graph_builds"):
         getattr(L, nm).argtypes = [P]
         getattr(L, nm).restype = i64
+    L.pamc_size_class.argtypes = [i32]
+    L.pamc_size_class.restype = ctypes.c_int
+    L.pamc_batch_set_shape.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.pamc_batch_set_shape.restype = ctypes.c_int
+    L.pamc_batch_get_shape.argtypes = [P, ctypes.c_int, P, P]
+    L.pamc_batch_get_shape.restype = ctypes.c_int
     L.pamc_batch_sync.argtypes = [P]
     L.pamc_batch_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     L.pamc_batch_destroy.argtypes = [P]
@@ -325,6 +332,20 @@ def pamc_batch_retire(b, max_out: int = 4096) -> list:
     if k < 0:
         _bcheck(int(STATUS_CODES["PAMC_ERR_CUDA"]), b)
     return [ctypes.c_void_p(out[i]) for i in range(k)]
+
+
+def pamc_size_class(n: int) -> int:
+    return int(load().pamc_size_class(int(n)))
+
+
+def pamc_batch_set_shape(b, size_class: int, groups_per_cta: int, warps_per_group: int):
+    _bcheck(_lib.pamc_batch_set_shape(b, int(size_class), int(groups_per_cta), int(warps_per_group)), b)
+
+
+def pamc_batch_get_shape(b, size_class: int):
+    g, w = ctypes.c_int(0), ctypes.c_int(0)
+    _bcheck(_lib.pamc_batch_get_shape(b, int(size_class), ctypes.byref(g), ctypes.byref(w)), b)
+    return g.value, w.value
 
 
 def pamc_batch_size(b) -> int:

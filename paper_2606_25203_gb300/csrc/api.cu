@@ -43,6 +43,7 @@ void *g_alloc_ctx = nullptr;
 thread_local char g_create_err[256] = "";
 
 constexpr int kSchedSlots = 16;   // schedules of this many steps are built per launch
+constexpr size_t kSmemMax = 227 * 1024;   // opt-in shared memory per CTA
 
 struct DevBuf {
     void *p = nullptr;
@@ -554,6 +555,10 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     h->cfg = choose_cfg(p.kind, n, R, h->H, avg_level, sms);
+    if (sweep_smem_bytes(p.kind, n, h->H, h->cfg) > kSmemMax) {
+        release_run(h);
+        return fail(h, PAMC_ERR_RANGE, "n = %d: one replica group's spins exceed shared memory", n);
+    }
     h->host_t = 0;
     h->initialized = 1;
     return PAMC_OK;
@@ -733,6 +738,7 @@ struct pamc_batch_s {
     int32_t graph_launches = 0;   // kernel launches in one replay
     int64_t launches = 0;
     int64_t rebuilds = 0;
+    SweepCfg shape[3];            // batched sweep launch shape per size class
     char err[256] = "";
 };
 
@@ -806,6 +812,15 @@ pamc_status rebuild(pamc_batch b) {
     std::vector<SweepDesc> sw;
     std::vector<int2> swi[2][2][kClasses];   // [ell][rule][class]
     int32_t nmax[kClasses] = {0, 0, 0}, Rmax = 1;
+    for (pamc_handle h : b->members)
+        if (h->host_t < h->p.steps) nmax[batch_class(h->n)] = std::max(nmax[batch_class(h->n)], h->n);
+    // the shape of each class, with fewer groups per CTA where the largest member's spins need it
+    SweepCfg eff[kClasses];
+    for (int c = 0; c < kClasses; ++c) {
+        eff[c] = b->shape[c];
+        while (eff[c].groups_per_cta > 1 && sweep_ising_smem_bytes(nmax[c], 127, eff[c]) > kSmemMax)
+            eff[c].groups_per_cta -= 1;
+    }
     for (pamc_handle h : b->members) {
         const pamc_params &p = h->p;
         if (h->host_t >= p.steps) continue;
@@ -835,12 +850,11 @@ pamc_status rebuild(pamc_batch b) {
         const int idx = (int)sw.size();
         sw.push_back(d);
         const int cls = batch_class(h->n);
-        const SweepCfg cfg = batch_cfg(cls);
+        const SweepCfg cfg = eff[cls];
         const int32_t ctas = ((p.R + 3) / 4 + cfg.groups_per_cta - 1) / cfg.groups_per_cta;
         // with sweeps = 0 the launch still copies the resampled population and its energies
         auto &items = swi[h->d_ell != nullptr][p.rule][cls];
         for (int32_t x = 0; x < ctas; ++x) items.push_back(make_int2(idx, x));
-        nmax[cls] = std::max(nmax[cls], h->n);
         Rmax = std::max(Rmax, p.R);
         CtlDesc c{nullptr, nullptr, h->d_best, h->d_ctl, h->W, p.target_cut, p.reheat_factor, p.beta0,
                   h->n, p.R, p.stagnation, p.z_rst, p.win_short, p.win_long, p.max_distinct_short,
@@ -872,7 +886,7 @@ pamc_status rebuild(pamc_batch b) {
                 const auto &items = swi[el][ru][c];
                 if (items.empty()) continue;
                 e = launch_sweep_ising_batched(ru, el != 0, (const SweepDesc *)b->sw.p, (const int2 *)b->swi.p + off,
-                                               (int32_t)items.size(), nmax[c], batch_cfg(c), b->stream);
+                                               (int32_t)items.size(), nmax[c], eff[c], b->stream);
                 off += items.size();
                 nl += 1;
             }
@@ -926,6 +940,7 @@ pamc_status pamc_batch_create(int cuda_device, void *stream, pamc_batch *out) {
     if (!b) return bfail(nullptr, PAMC_ERR_OOM, "host allocation failed");
     b->device = cuda_device;
     b->stream = (cudaStream_t)stream;
+    for (int c = 0; c < kClasses; ++c) b->shape[c] = batch_cfg(c);
     if (!b->stream) {   // graph capture needs a stream other than the legacy default one
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
             delete b;
@@ -1010,6 +1025,26 @@ int32_t pamc_batch_retire(pamc_batch b, pamc_handle *out, int32_t max_out) {
         b->dirty = true;
     }
     return (int32_t)done.size();
+}
+
+int pamc_size_class(int32_t n) { return batch_class(n); }
+
+pamc_status pamc_batch_set_shape(pamc_batch b, int size_class, int groups_per_cta, int warps_per_group) {
+    if (!b) return bfail(b, PAMC_ERR_ARG, "null batch");
+    if (size_class < 0 || size_class >= kClasses) return bfail(b, PAMC_ERR_ARG, "size class must be 0, 1 or 2");
+    if (groups_per_cta < 1 || warps_per_group < 1 || groups_per_cta * warps_per_group > 32)
+        return bfail(b, PAMC_ERR_ARG, "need groups >= 1, warps >= 1 and groups * warps <= 32");
+    b->shape[size_class] = SweepCfg{groups_per_cta, warps_per_group};
+    b->dirty = true;
+    return PAMC_OK;
+}
+
+pamc_status pamc_batch_get_shape(pamc_batch b, int size_class, int *groups_per_cta, int *warps_per_group) {
+    if (!b || !groups_per_cta || !warps_per_group) return bfail(b, PAMC_ERR_ARG, "null argument");
+    if (size_class < 0 || size_class >= kClasses) return bfail(b, PAMC_ERR_ARG, "size class must be 0, 1 or 2");
+    *groups_per_cta = b->shape[size_class].groups_per_cta;
+    *warps_per_group = b->shape[size_class].warps_per_group;
+    return PAMC_OK;
 }
 
 int32_t pamc_batch_size(pamc_batch b) { return b ? (int32_t)b->members.size() : 0; }

@@ -87,6 +87,12 @@ class Server:
         self.admit_stream = torch.cuda.Stream(device)    # instance upload and initialisation
         self.batch = pamc_batch_create(device, self.stream.cuda_stream)
 
+    def autotune(self, samples, params: dict, **kw) -> dict:
+        """Pick the batched sweep's launch shape per size class on copies of
+        ``samples`` (see ``tune.tune_batch_shapes``)."""
+        from .tune import tune_batch_shapes
+        return tune_batch_shapes(self.batch, samples, params, device=self.device, **kw)
+
     def close(self):
         if self.batch is not None:
             pamc_batch_destroy(self.batch)

@@ -1,0 +1,61 @@
+"""Autotuner for the batched sweep's launch shape per size class.
+
+For every size class (``pamc_size_class``: n <= 2048, <= 8192, larger) that the
+sample instances cover, the samples of that class are loaded into a throwaway
+batch and each candidate shape -- replica groups (of four replicas) per CTA and
+warps per group -- is timed with CUDA events over a few batch steps; the
+fastest one is set on the caller's batch.  A shape changes speed only, never
+results, so tuning on copies of representative instances is safe.
+"""
+from __future__ import annotations
+
+from . import (pamc_batch_add, pamc_batch_create, pamc_batch_destroy, pamc_batch_set_shape,
+               pamc_batch_step, pamc_create_csr, pamc_destroy, pamc_init, pamc_size_class)
+
+CANDIDATES = tuple((g, w) for g in (1, 2, 4, 8) for w in (1, 2, 4, 8, 16) if g * w <= 32)
+
+
+def tune_batch_shapes(batch, samples, params: dict, steps: int = 3, rounds: int = 2, device: int = 0,
+                      candidates=CANDIDATES) -> dict:
+    """samples: instances with ``n``, ``row_ptr``, ``col``, ``w`` (numpy CSR).
+    params: run parameters of the served requests (R, sweeps, rule, ...).
+    Returns {size_class: (groups_per_cta, warps_per_group, ms_per_step)}."""
+    import torch
+    by_class = {}
+    for inst in samples:
+        by_class.setdefault(pamc_size_class(inst.n), []).append(inst)
+    p = dict(params)
+    p["steps"] = 1 << 20          # the throwaway runs never finish
+    p.pop("target_cut", None)
+    stream = torch.cuda.Stream(device)
+    chosen = {}
+    for cls, insts in sorted(by_class.items()):
+        hs = []
+        tmp = pamc_batch_create(device, stream.cuda_stream)
+        try:
+            for inst in insts:
+                h = pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w, device, stream.cuda_stream)
+                hs.append(h)
+                pamc_init(h, **p)
+                pamc_batch_add(tmp, h)
+            best = {}
+            for _ in range(rounds):          # candidates interleaved, best of the rounds
+                for g, w in candidates:
+                    pamc_batch_set_shape(tmp, cls, g, w)
+                    pamc_batch_step(tmp, 1)  # capture and warm up
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    pamc_batch_step(tmp, steps)
+                    b.record(stream)
+                    b.synchronize()
+                    ms = a.elapsed_time(b) / steps
+                    best[(g, w)] = min(ms, best.get((g, w), float("inf")))
+            (g, w), ms = min(best.items(), key=lambda kv: kv[1])
+            pamc_batch_set_shape(batch, cls, g, w)
+            chosen[cls] = (g, w, ms)
+        finally:
+            pamc_batch_destroy(tmp)
+            for h in hs:
+                pamc_destroy(h)
+    return chosen

@@ -227,3 +227,47 @@ def test_server_equals_sequential(pg):
         assert r.cut == a[r.rid].cut, f"request {r.rid}"
         np.testing.assert_array_equal(r.spins, a[r.rid].spins, err_msg=f"request {r.rid}")
         assert r.finished >= r.admitted >= r.arrival - 1e-9
+
+
+def test_shapes_change_speed_not_results(pg):
+    """Every launch shape of every size class gives the same members' results,
+    and the autotuner sets one of the candidates."""
+    from paper_2606_25203_gb300.tune import tune_batch_shapes
+    cases = [(W.gnm(1200, 3400, signed=True, seed=41), dict(R=40, sweeps=2, steps=7, seed=1)),
+             (W.er_avg_degree(3000, 16, signed=False, seed=42), dict(R=24, sweeps=2, steps=7, seed=2, rule=1)),
+             (W.torus(95, 95, signed=True, seed=43), dict(R=28, sweeps=1, steps=7, seed=3))]
+    ref = [alone(pg, inst, p) for inst, p in cases]
+    for shape in [(1, 1), (2, 16), (8, 4), (3, 3)]:
+        b = pg.pamc_batch_create(0)
+        hs = []
+        try:
+            for c in range(3):
+                pg.pamc_batch_set_shape(b, c, *shape)
+                assert pg.pamc_batch_get_shape(b, c) == shape
+            for inst, p in cases:
+                h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+                pg.pamc_init(h, **p)
+                pg.pamc_batch_add(b, h)
+                hs.append(h)
+            pg.pamc_batch_step(b, 7)
+            pg.pamc_batch_sync(b)
+            for i, (inst, p) in enumerate(cases):
+                assert_same(snapshot(pg, hs[i], inst.n, p["R"]), ref[i], f"shape {shape} member {i}")
+        finally:
+            pg.pamc_batch_destroy(b)
+            for h in hs:
+                pg.pamc_destroy(h)
+    b = pg.pamc_batch_create(0)
+    try:
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_set_shape(b, 0, 8, 8)      # 64 warps
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_set_shape(b, 3, 1, 1)      # no such class
+        got = tune_batch_shapes(b, [c[0] for c in cases], dict(R=32, sweeps=1), steps=1, rounds=1,
+                                candidates=((1, 4), (2, 2)))
+        assert sorted(got) == [0, 1, 2]
+        for c, (g, w, ms) in got.items():
+            assert (g, w) in ((1, 4), (2, 2)) and ms > 0
+            assert pg.pamc_batch_get_shape(b, c) == (g, w)
+    finally:
+        pg.pamc_batch_destroy(b)
