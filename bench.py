@@ -53,6 +53,31 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+# DRAM bytes per launch from the committed ncu captures (profiles/), valid
+# only while the kernel sources still hash to what was captured.
+PROFILED_TRAFFIC = {
+    # k_sweep_ising, torus 141x141, R=4096, 10 sweeps: one launch
+    "sweep_torus": (64.79e6, {"paper_2606_25203_gb300/csrc/sweep_ising.cu":
+                              "e8cc7d5ac06dfb8f15f73bf8c5e85f3692e90270"}),
+    # k_dense_sweep, 2 sweeps: the n=30,000 capture (1.746 GB) scaled by n^2 to n=100,000
+    "dense_sweep_100k": (1.746e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
+                                                           "bd901a06639e7899a1ba41cbb92cdb0990c36b3a"}),
+}
+
+
+def profiled_traffic(key):
+    import hashlib
+    nbytes, sources = PROFILED_TRAFFIC[key]
+    for path, sha in sources.items():
+        try:
+            with open(os.path.join(ROOT, path), "rb") as f:
+                if hashlib.sha1(f.read()).hexdigest() != sha:
+                    return None
+        except OSError:
+            return None
+    return nbytes
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -172,6 +197,24 @@ def cpu_baseline_sample():
 
 
 # ---------------------------------------------------------------- our arm
+def rank_seed(seed: int, rank: int) -> int:
+    """Replicas only: rank r runs its own copy of the workload with seed + r."""
+    return seed + rank
+
+
+def reduce_over_ranks(dist, ms: float, attempts: float, device="cuda"):
+    """Whole-job figures: the timed region is the max over ranks, the attempts
+    the sum over ranks.  Returns (ms, attempts)."""
+    if dist is None:
+        return ms, attempts
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    a = torch.tensor([attempts], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(a.item())
+
+
 def run_ours(args):
     import torch
     import paper_2606_25203_gb300 as pg
@@ -190,7 +233,7 @@ def run_ours(args):
     solvers = []
     for inst in insts:
         s = pg.Solver(inst.row_ptr, inst.col, inst.w, device=local, stream=stream.cuda_stream)
-        s.init(**dict(PARAMS, seed=PARAMS["seed"] + rank))
+        s.init(**dict(PARAMS, seed=rank_seed(PARAMS["seed"], rank)))
         solvers.append(s)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     for _ in range(args.warmup):
@@ -217,11 +260,7 @@ def run_ours(args):
     ms = sum(a.elapsed_time(b) for a, b in ev)
     for s in solvers:
         s.sync()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    att = attempts_per_step(insts) * args.steps * world
+    ms, att = reduce_over_ranks(dist, ms, attempts_per_step(insts) * args.steps)
     value = att / (ms / 1e3)
 
     if args.lean:
@@ -253,8 +292,8 @@ def run_ours(args):
                        "attempts_per_step": attempts_per_step(insts), "l2": "flushed between steps (512 MB write)",
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                         "frac": achieved / peak_tops, "traffic": None,
-                         "kernel": "k_sweep (torus 141x141, R=4096, 10 sweeps)",
+                         "frac": achieved / peak_tops, "traffic": profiled_traffic("sweep_torus"),
+                         "kernel": "k_sweep_ising (torus 141x141, R=4096, 10 sweeps)",
                          "ops_per_attempt": ops_per_attempt,
                          "peak_source": f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)"},
             "clocks": clk.summary(),
@@ -362,9 +401,12 @@ def run_dense(args):
     del w
     torch.cuda.empty_cache()
     P = dict(DENSE_PARAMS)
+    # warm-up steps on a throwaway run, then the timed steps 0..K-1 of a fresh
+    # run (the cost of a step depends on where it is in the beta schedule)
     pg.pamc_init(h, **P)
-    for _ in range(args.warmup):
-        pg.pamc_step(h, 1)
+    pg.pamc_step(h, args.warmup)
+    pg.pamc_sync(h)
+    pg.pamc_init(h, **P)
     torch.cuda.synchronize()
     l0 = pg.pamc_launch_count(h)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -376,9 +418,12 @@ def run_dense(args):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     pg.pamc_sync(h)
-    ms = sum(a.elapsed_time(b) for a, b in ev)
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(per_step)
     launches = pg.pamc_launch_count(h) - l0
     att = P["R"] * n * P["sweeps"] * args.steps
+    m, _ = pg.pamc_best(h, n)
+    e_best = pg.pamc_weight_sum(h) - 2 * m     # E = W - 2 cut
     # kernel split: a step without sweeps (order, resampling, tables, the
     # tensor-core recompute, control) on the same population
     pg.pamc_init(h, **dict(P, sweeps=0))
@@ -391,7 +436,6 @@ def run_dense(args):
     torch.cuda.synchronize()
     ms_nosweep = a.elapsed_time(b) / 3
     ms_sweep = ms / args.steps - ms_nosweep
-    m, _ = pg.pamc_best(h, n)
     peaks, src = load_peaks()
     hbm = peaks["hbm_gbs"]
     rc_gbs = n * n / (ms_nosweep / 1e3) / 1e9            # J bytes of the recompute
@@ -404,12 +448,17 @@ def run_dense(args):
                                         "l2": "inputs (10 GB) larger than L2"},
         "kernels_ms": {"step": ms / args.steps, "sweeps": ms_sweep, "recompute_and_rest": ms_nosweep},
         "roofline": {"bound": "hbm", "achieved": sw_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": sw_gbs / hbm, "traffic": None,
+                     "frac": sw_gbs / hbm,
+                     "traffic": (profiled_traffic("dense_sweep_100k") * (n / 100000) ** 2
+                                 if profiled_traffic("dense_sweep_100k") else None),
                      "kernel": "k_dense_sweep (bytes = one read of J per sweep)",
                      "peak_source": src},
         "recompute_roofline": {"bound": "hbm", "achieved": rc_gbs, "peak": hbm, "unit": "GB/s",
                                "frac": rc_gbs / hbm},
-        "clocks": clk.summary(), "gpu_launches": launches, "best_cut_after": m,
+        "clocks": clk.summary(), "gpu_launches": launches,
+        "timed_steps": f"steps 0..{args.steps - 1} of a fresh run (beta {P['beta0']} -> {P['beta1']} over {P['steps']})",
+        "ms_step_first_last": [per_step[0], per_step[-1]],
+        "best_cut": m, "best_energy_density": e_best / n ** 1.5,
         "instance_generation_s": gen_s,
     }
     print(json.dumps(line))
@@ -501,6 +550,56 @@ def run_serving(args):
     print(json.dumps(line))
 
 
+def run_batch(args):
+    """A fixed batch of serving requests resident on the device, advanced by
+    pamc_batch_step: device-timed steps (CUDA events on the batch stream), the
+    throughput of the batched kernels without admission or host gaps."""
+    import torch
+    import paper_2606_25203_gb300 as pg
+    pg.load()
+    P = dict(SERVE_PARAMS, steps=1 << 20)
+    reqs = W.serving_stream(args.batch_requests, rate=0.0, seed=1, n_lo=args.batch_n_lo, n_hi=args.batch_n_hi)
+    st = torch.cuda.Stream()
+    b = pg.pamc_batch_create(0, st.cuda_stream)
+    hs = []
+    for r in reqs:
+        h = pg.pamc_create_csr(r.inst.n, r.inst.row_ptr, r.inst.col, r.inst.w, 0, st.cuda_stream)
+        pg.pamc_init(h, **P)
+        pg.pamc_batch_add(b, h)
+        hs.append(h)
+    pg.pamc_batch_step(b, args.warmup)
+    torch.cuda.synchronize()
+    l0 = pg.pamc_batch_launch_count(b)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(st)
+            pg.pamc_batch_step(b, 1)
+            ev[k][1].record(st)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in ev)
+    att = sum(P["R"] * r.inst.n * P["sweeps"] for r in reqs) * args.steps
+    ops = sum(P["R"] * r.inst.n * P["sweeps"] * (18 + 2 * r.inst.nnz / r.inst.n) for r in reqs) * args.steps
+    peaks, src = load_peaks()
+    alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    ach = ops / (ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": att / (ms / 1e3), "unit": "attempts/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batch of {len(reqs)} resident serving requests, N ~ U[{args.batch_n_lo}, "
+                               f"{args.batch_n_hi}], R=512, 10 sweeps/step",
+                   "l2": "populations and schedule rings exceed L2"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "Tops/s", "frac": ach / alu_peak,
+                     "traffic": None, "kernel": "whole batched step (all kernels)"},
+        "clocks": clk.summary(), "gpu_launches": pg.pamc_batch_launch_count(b) - l0,
+    }
+    print(json.dumps(line))
+    pg.pamc_batch_destroy(b)
+    for h in hs:
+        pg.pamc_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -511,7 +610,10 @@ def main():
                     help="run one of the two instances (profiling)")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only: no e2e, kernel split or CPU baseline (profiling)")
-    ap.add_argument("--workload", choices=["sparse", "dense100k", "serving"], default="sparse")
+    ap.add_argument("--workload", choices=["sparse", "dense100k", "serving", "batch"], default="sparse")
+    ap.add_argument("--batch-requests", type=int, default=48)
+    ap.add_argument("--batch-n-lo", type=int, default=800)
+    ap.add_argument("--batch-n-hi", type=int, default=20000)
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-max-active", type=int, default=64)
     ap.add_argument("--dense-n", type=int, default=DENSE_N)
@@ -520,6 +622,9 @@ def main():
     ONLY = args.only
     if args.workload == "dense100k" and args.impl == "ours":
         run_dense(args)
+        return
+    if args.workload == "batch" and args.impl == "ours":
+        run_batch(args)
         return
     if args.workload == "serving" and args.impl == "ours":
         run_serving(args)

@@ -828,7 +828,7 @@ cudaError_t launch_dense_recompute(int32_t n, int32_t R, const int8_t *J, const 
                                    const int32_t *ncm_idx, int32_t *H, const DevCtl *ctl,
                                    cudaStream_t st, int restart_t) {
     const size_t smem = dense_recompute_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_dense_recompute, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(k_dense_recompute, smem);
     if (e != cudaSuccess) return e;
     const int grid = (n + kRcRows - 1) / kRcRows;
     k_dense_recompute<<<grid, kRcWarps * 32, smem, st>>>(n, R, reinterpret_cast<const uint8_t *>(J), src,
@@ -878,7 +878,7 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
     a.dst = dst; a.E = E; a.G = G; a.T = T; a.T2 = T2; a.flip = flip; a.snew = snew;
     a.bar = reinterpret_cast<GridBar *>(bar); a.ctl = ctl;
     const size_t smem = dense_sweep_smem(n, R, rows_per);
-    cudaError_t e = cudaFuncSetAttribute(k_dense_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_dynamic_smem(k_dense_sweep, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(bar, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;

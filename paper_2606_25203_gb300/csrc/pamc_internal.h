@@ -111,6 +111,26 @@ struct CtlDesc {
     int32_t t_end;
 };
 
+// Allows every launch of `func` with up to `bytes` of dynamic shared memory
+// by raising the kernel's limit to the device's opt-in maximum (minus its
+// static shared memory).  The limit is never lowered, so launches enqueued or
+// captured into a graph earlier with a larger size stay valid whatever the
+// order of later launches.
+template <typename F>
+inline cudaError_t allow_dynamic_smem(F *func, size_t bytes) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, func);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int lim = optin - (int)a.sharedSizeBytes;
+    if ((long long)bytes > (long long)lim) return cudaErrorInvalidValue;
+    if (a.maxDynamicSharedSizeBytes >= lim) return cudaSuccess;
+    return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
 // Launch configuration of the sparse sweep kernel.
 struct SweepCfg {
     int groups_per_cta;   // replica groups in one CTA

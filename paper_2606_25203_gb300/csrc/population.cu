@@ -469,7 +469,7 @@ size_t prep_smem_bytes(int32_t R) { return (size_t)R * 8 + (size_t)R * 4; }
 cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
                         int32_t *count, int32_t *ncm_idx, int32_t *targets, cudaStream_t st) {
     const size_t smem = prep_smem_bytes(p.R);
-    cudaError_t err = cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = allow_dynamic_smem(k_prep, smem);
     if (err != cudaSuccess) return err;
     k_prep<<<1, kPrepThreads, smem, st>>>(p.R, p.kind, p.resample, p.n_top, p.cooldown_tau,
                                           (uint32_t)p.seed, (uint32_t)(p.seed >> 32), E_src, ctl,
@@ -501,7 +501,7 @@ cudaError_t launch_population_batched(const PrepDesc *prep, const TabDesc *tabs,
                                       int32_t R_max, cudaStream_t st) {
     if (ninst <= 0) return cudaSuccess;
     const size_t smem = prep_smem_bytes(R_max);
-    cudaError_t err = cudaFuncSetAttribute(k_prep_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = allow_dynamic_smem(k_prep_batched, smem);
     if (err != cudaSuccess) return err;
     k_prep_batched<<<ninst, kPrepThreads, smem, st>>>(prep);
     k_tables_batched<<<ninst, 256, 0, st>>>(tabs);

@@ -349,8 +349,7 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
     cudaError_t err;
 #define PAMC_LAUNCH_SWEEP(KD, EL)                                                                \
     do {                                                                                         \
-        err = cudaFuncSetAttribute(k_sweep<KD, EL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                   (int)smem);                                                   \
+        err = allow_dynamic_smem(k_sweep<KD, EL>, smem);                                         \
         if (err != cudaSuccess) return err;                                                      \
         k_sweep<KD, EL><<<grid, gpc * tpg, smem, st>>>(                                          \
             n, n_pad, rp, adj, H, p.R, p.sweeps, rule, k0, k1, t, slot, sv.order, sv.lvl_ptr,    \

@@ -305,8 +305,7 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
     cudaError_t err = cudaSuccess;
 #define PAMC_LAUNCH(EL, RU)                                                                       \
     do {                                                                                          \
-        err = cudaFuncSetAttribute(k_sweep_ising<EL, RU>,                                         \
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        err = allow_dynamic_smem(k_sweep_ising<EL, RU>, smem);                                    \
         if (err != cudaSuccess) return err;                                                       \
         k_sweep_ising<EL, RU><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);                        \
     } while (0)
@@ -327,8 +326,7 @@ cudaError_t launch_sweep_ising_batched(int rule, bool ell, const SweepDesc *desc
     cudaError_t err = cudaSuccess;
 #define PAMC_LAUNCH(EL, RU)                                                                       \
     do {                                                                                          \
-        err = cudaFuncSetAttribute(k_sweep_ising_batched<EL, RU>,                                 \
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+        err = allow_dynamic_smem(k_sweep_ising_batched<EL, RU>, smem);                            \
         if (err != cudaSuccess) return err;                                                       \
         k_sweep_ising_batched<EL, RU><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg);   \
     } while (0)
