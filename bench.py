@@ -600,6 +600,50 @@ def run_batch(args):
         pg.pamc_destroy(h)
 
 
+def run_diag(args):
+    """Diagnostics on the torus population of the default workload (R=4096):
+    the corrected pairwise Hamming histogram (8.4M pairs) and the lineage,
+    each timed as the whole C-ABI call (scratch, kernels, readback)."""
+    import torch
+    import paper_2606_25203_gb300 as pg
+    pg.load()
+    inst = W.c2a_torus141()
+    h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+    pg.pamc_init(h, **PARAMS)
+    pg.pamc_step(h, 5)
+    pg.pamc_sync(h)
+    for _ in range(args.warmup):
+        pg.pamc_hamming(h, inst.n)
+    ts = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            hist, total = pg.pamc_hamming(h, inst.n)
+            ts.append(time.perf_counter() - t0)
+    t1 = time.perf_counter()
+    fam, nf = pg.pamc_lineage(h, R)
+    t_lin = time.perf_counter() - t1
+    pairs = R * (R - 1) // 2
+    nw = (inst.n + 31) // 32
+    sec = float(np.median(ts))
+    ops = pairs * nw * 3                        # xor, popcount, add per word pair
+    peaks, _ = load_peaks()
+    peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    line = {
+        "metric": "replica pairs/s (Hamming histogram)", "value": pairs / sec, "unit": "pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "torus 141x141, R=4096 after 5 steps of the default run", "pairs": pairs,
+                   "timing": "median host wall clock of the whole pamc_hamming call"},
+        "roofline": {"bound": "alu", "achieved": ops / sec / 1e12, "peak": peak, "unit": "Tops/s",
+                     "frac": ops / sec / 1e12 / peak, "traffic": None, "kernel": "k_hamming"},
+        "mean_normalised_distance": total / (pairs * inst.n), "lineage_ms": t_lin * 1e3,
+        "families_alive": nf, "clocks": clk.summary(), "gpu_launches": 2 * args.steps,
+    }
+    print(json.dumps(line))
+    pg.pamc_destroy(h)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -610,7 +654,8 @@ def main():
                     help="run one of the two instances (profiling)")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only: no e2e, kernel split or CPU baseline (profiling)")
-    ap.add_argument("--workload", choices=["sparse", "dense100k", "serving", "batch"], default="sparse")
+    ap.add_argument("--workload", choices=["sparse", "dense100k", "serving", "batch", "diag"],
+                    default="sparse")
     ap.add_argument("--batch-requests", type=int, default=48)
     ap.add_argument("--batch-n-lo", type=int, default=800)
     ap.add_argument("--batch-n-hi", type=int, default=20000)
@@ -622,6 +667,9 @@ def main():
     ONLY = args.only
     if args.workload == "dense100k" and args.impl == "ours":
         run_dense(args)
+        return
+    if args.workload == "diag" and args.impl == "ours":
+        run_diag(args)
         return
     if args.workload == "batch" and args.impl == "ours":
         run_batch(args)

@@ -144,6 +144,22 @@ int64_t pamc_weight_sum(pamc_handle h);
  * NULL) into buf. */
 pamc_status pamc_last_error(pamc_handle h, char *buf, size_t len);
 
+/* Diversity of the current population (Suppl., Hamming distance of
+ * replicas): for every pair of replicas r < r', d = the number of spins in
+ * which they differ, corrected for the global flip symmetry of Max-Cut as
+ * dc = min(d, n - d).  hist (caller array of n/2 + 1 int64, floor division)
+ * receives hist[k] = the number of pairs with dc = k, *sum the sum of dc over
+ * all R(R-1)/2 pairs, so the mean normalised distance is
+ * sum / (R(R-1)/2 * n).  Synchronises the handle's stream; allocates scratch
+ * of R * ceil(n/32) words.  Ising (kind 0) runs, sparse or dense;
+ * PAMC_ERR_ARG for Potts. */
+pamc_status pamc_hamming(pamc_handle h, int64_t *hist, int64_t *sum);
+/* Lineage of the current population (Sec. III, genealogy of the resampled
+ * population): family[r] (caller array of R int32) = the slot of the initial
+ * population, or of the last re-initialised one after a restart, that slot r
+ * descends from through the resampling parent maps (NCM keeps the family).
+ * *n_families (may be NULL) = the number of distinct families alive. */
+pamc_status pamc_lineage(pamc_handle h, int32_t *family, int32_t *n_families);
 void pamc_destroy(pamc_handle h);
 
 /* ---- Batches: many independent instances advanced together ----

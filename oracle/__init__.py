@@ -182,6 +182,35 @@ def ncm_replica(rp, col, J, s, h, mis_trials, seed, t, r):
                                      int(mis_trials), int(seed), int(t), int(r)))
 
 
+def hamming_counts(spins):
+    """Replica diversity (Suppl., Hamming distance of replicas), written out
+    from its definition: for every pair r < r' of the R x n +-1 population,
+    d = the number of spins in which the two replicas differ, corrected for the
+    global flip symmetry as dc = min(d, n - d).  Returns (hist, total) with
+    hist[k] = the number of pairs with dc = k (k = 0 .. n // 2) and total = the
+    sum of dc over all pairs."""
+    spins = np.asarray(spins)
+    R, n = spins.shape
+    hist = np.zeros(n // 2 + 1, dtype=np.int64)
+    total = 0
+    for r in range(R):
+        for q in range(r + 1, R):
+            d = int(np.count_nonzero(spins[r] != spins[q]))
+            dc = min(d, n - d)
+            hist[dc] += 1
+            total += dc
+    return hist, total
+
+
+def lineage_step(family, parent, reinitialised: bool = False):
+    """Genealogy through one population step: slot m inherits its resampling
+    parent's family; a re-initialised population starts new families."""
+    family = np.asarray(family)
+    if reinitialised:
+        return np.arange(family.shape[0], dtype=family.dtype)
+    return family[np.asarray(parent)]
+
+
 class Controller:
     """Algorithm 1's post-sweep control block on its own (for hand-built M*
     sequences): ``update(mstar)`` returns True when the schedule restarts."""

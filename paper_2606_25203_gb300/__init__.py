@@ -25,7 +25,7 @@ __all__ = [
     "pamc_sweeps_noalloc", "pamc_footprint", "pamc_batch_create", "pamc_batch_add", "pamc_batch_step",
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
-    "pamc_batch_set_shape", "pamc_batch_get_shape",
+    "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_hamming", "pamc_lineage",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -119,6 +119,10 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_sweeps_noalloc.argtypes = [i32, i32, P, P, P, i32, i32, i32, i32, ctypes.c_double,
                                       ctypes.c_uint64, i32, P, P, P, P, ctypes.c_char_p,
                                       ctypes.c_size_t]
+    L.pamc_hamming.argtypes = [P, P, P]
+    L.pamc_hamming.restype = ctypes.c_int
+    L.pamc_lineage.argtypes = [P, P, P]
+    L.pamc_lineage.restype = ctypes.c_int
     L.pamc_footprint.argtypes = [P, ctypes.POINTER(Params)]
     L.pamc_footprint.restype = ctypes.c_size_t
     L.pamc_batch_create.argtypes = [ctypes.c_int, P, ctypes.POINTER(P)]
@@ -296,6 +300,22 @@ def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed,
                                _stream_ptr(dev, stream), buf, 256)
     if rc != 0:
         raise PamcError(rc, buf.value.decode(errors="replace"))
+
+
+def pamc_hamming(h, n: int):
+    """(hist, sum): hist[k] = pairs of replicas at corrected distance k = min(d, n - d)."""
+    hist = np.zeros(n // 2 + 1, dtype=np.int64)
+    total = np.zeros(1, dtype=np.int64)
+    _check(_lib.pamc_hamming(h, _ptr(hist), _ptr(total)), h)
+    return hist, int(total[0])
+
+
+def pamc_lineage(h, R: int):
+    """(family, n_families): family[r] = the initial slot that slot r descends from."""
+    fam = np.zeros(R, dtype=np.int32)
+    k = np.zeros(1, dtype=np.int32)
+    _check(_lib.pamc_lineage(h, _ptr(fam), _ptr(k)), h)
+    return fam, int(k[0])
 
 
 def pamc_footprint(h, **params) -> int:

@@ -25,7 +25,7 @@ namespace pamc {
 cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint64_t *tab,
                           cudaStream_t st);
 cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
-                        int32_t *count, int32_t *ncm_idx, int32_t *targets, cudaStream_t st);
+                        int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, cudaStream_t st);
 cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
                        const int8_t *src, const int64_t *E_src, const int32_t *parent,
                        const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey, uint8_t *nstat,
@@ -74,6 +74,7 @@ struct pamc_handle_s {
     int8_t *d_spins[2] = {nullptr, nullptr};
     int64_t *d_E[2] = {nullptr, nullptr};
     int32_t *d_parent = nullptr, *d_count = nullptr, *d_ncm_idx = nullptr, *d_targets = nullptr;
+    int32_t *d_fam = nullptr;   // [2][R] lineage (family of each slot)
     int8_t *d_ncm_buf = nullptr;
     uint32_t *d_nkey = nullptr;
     uint8_t *d_nstat = nullptr;
@@ -267,6 +268,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
               alloc_n(h, h->d_spins[1], (size_t)R * n, h->bufs) &&
               alloc_n(h, h->d_E[0], 64, h->bufs) && alloc_n(h, h->d_E[1], 64, h->bufs) &&
               alloc_n(h, h->d_parent, R, h->bufs) && alloc_n(h, h->d_count, R, h->bufs) &&
+              alloc_n(h, h->d_fam, 2 * (size_t)R, h->bufs) &&
               alloc_n(h, h->d_ncm_idx, R, h->bufs) && alloc_n(h, h->d_targets, R, h->bufs) &&
               alloc_n(h, h->d_tab, tabn, h->bufs) && alloc_n(h, h->d_ctl, 1, h->bufs) &&
               alloc_n(h, h->d_best, n, h->bufs) && alloc_n(h, h->d_H, (size_t)R * n, h->bufs) &&
@@ -292,6 +294,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
     for (int32_t r = 0; r < R; ++r) ident[r] = r;
     cudaError_t e = cudaMemcpyAsync(h->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_parent, ident.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_fam, ident.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ident, ident.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_count, ones.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ncm_idx, minus.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
@@ -327,7 +330,8 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
         cudaError_t e = launch_dense_perm(n, p.seed, (int32_t)t, p.sweeps, h->d_perm, h->d_pkey, h->d_sidx,
                                           h->d_ctl, h->stream);
         if (e == cudaSuccess)
-            e = launch_prep(pp, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->stream);
+            e = launch_prep(pp, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
+                            h->stream);
         if (e == cudaSuccess) e = launch_dense_tables(p.rule, h->dense_Hc, n, h->d_ctl, h->d_tab, h->stream);
         if (e == cudaSuccess)
             e = launch_dense_recompute(n, R, h->d_J, src, h->d_parent, nullptr, h->d_ncm_idx, h->d_H, h->d_ctl,
@@ -487,6 +491,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
               alloc_n(h, h->d_spins[1], (size_t)R * n, h->bufs) &&
               alloc_n(h, h->d_E[0], R, h->bufs) && alloc_n(h, h->d_E[1], R, h->bufs) &&
               alloc_n(h, h->d_parent, R, h->bufs) && alloc_n(h, h->d_count, R, h->bufs) &&
+              alloc_n(h, h->d_fam, 2 * (size_t)R, h->bufs) &&
               alloc_n(h, h->d_ncm_idx, R, h->bufs) && alloc_n(h, h->d_targets, R, h->bufs) &&
               alloc_n(h, h->d_tab, tabn, h->bufs) && alloc_n(h, h->d_ctl, 1, h->bufs) &&
               alloc_n(h, h->d_best, n, h->bufs) &&
@@ -524,6 +529,8 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     std::vector<int32_t> ident(R), ones(R, 1), minus(R, -1);
     for (int32_t r = 0; r < R; ++r) ident[r] = r;
     e = cudaMemcpyAsync(h->d_parent, ident.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_fam, ident.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_count, ones.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
@@ -585,7 +592,8 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
         }
         int8_t *src = h->d_spins[t & 1], *dst = h->d_spins[(t + 1) & 1];
         int64_t *Es = h->d_E[t & 1], *Ed = h->d_E[(t + 1) & 1];
-        e = launch_prep(p, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->stream);
+        e = launch_prep(p, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
+                        h->stream);
         if (e == cudaSuccess) e = launch_tables(p.kind, p.rule, h->H, h->d_ctl, h->d_tab, h->stream);
         h->launches += 2;
         if (e == cudaSuccess && p.stagnation && p.kind == 0) {
@@ -697,6 +705,55 @@ pamc_status pamc_control_state(pamc_handle h, int64_t *iv, double *dv) {
     iv[5] = c.done; iv[6] = c.ncm_last; iv[7] = c.hist_len; iv[8] = c.ncm_flipped;
     iv[9] = c.ncm_dE_max;
     dv[0] = c.beta; dv[1] = c.delta;
+    return PAMC_OK;
+}
+
+pamc_status pamc_hamming(pamc_handle h, int64_t *hist, int64_t *sum) {
+    if (!h || !hist || !sum) return fail(h, PAMC_ERR_ARG, "null argument");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_hamming before pamc_init");
+    if (h->p.kind != 0) return fail(h, PAMC_ERR_ARG, "Hamming distances are defined for Ising (Max-Cut) runs");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    const int32_t n = h->n, R = h->p.R;
+    const size_t nb = (size_t)n / 2 + 1, nw = ((size_t)n + 31) / 32;
+    std::vector<DevBuf> tmp;
+    uint32_t *bits = nullptr;
+    unsigned long long *dh = nullptr;
+    if (!alloc_n(h, bits, std::max<size_t>((size_t)R * nw, 1), tmp) || !alloc_n(h, dh, nb + 1, tmp)) {
+        dev_free_all(h, tmp);
+        return fail(h, PAMC_ERR_OOM, "device allocation for the Hamming distances failed");
+    }
+    cudaError_t e = launch_hamming(n, R, h->d_spins[c.t & 1], bits, dh, dh + nb, h->stream);
+    std::vector<unsigned long long> out(nb + 1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out.data(), dh, sizeof(unsigned long long) * (nb + 1), cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free_all(h, tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "Hamming distances");
+    for (size_t k = 0; k < nb; ++k) hist[k] = (int64_t)out[k];
+    *sum = (int64_t)out[nb];
+    return PAMC_OK;
+}
+
+pamc_status pamc_lineage(pamc_handle h, int32_t *family, int32_t *n_families) {
+    if (!h || !family) return fail(h, PAMC_ERR_ARG, "null argument");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_lineage before pamc_init");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    const int32_t R = h->p.R;
+    cudaError_t e = cudaMemcpy(family, h->d_fam + (size_t)(c.t & 1) * R, sizeof(int32_t) * R,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lineage readback");
+    if (n_families) {
+        std::vector<char> seen(R, 0);
+        int32_t k = 0;
+        for (int32_t r = 0; r < R; ++r)
+            if (family[r] >= 0 && family[r] < R && !seen[family[r]]) { seen[family[r]] = 1; ++k; }
+        *n_families = k;
+    }
     return PAMC_OK;
 }
 
@@ -835,7 +892,8 @@ pamc_status rebuild(pamc_batch b) {
             for (int x = 0; x < p.sweeps; ++x) sdi.push_back(make_int2(idx, x));
         }
         PrepDesc pd{nullptr, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, p.R,
-                    p.kind, p.resample, p.n_top, p.cooldown_tau, k0, k1, {h->d_E[0], h->d_E[1]}, t_end};
+                    p.kind, p.resample, p.n_top, p.cooldown_tau, k0, k1, {h->d_E[0], h->d_E[1]}, t_end,
+                    h->d_fam, 0};
         prep.push_back(pd);
         tabs.push_back(TabDesc{h->d_ctl, h->d_tab, p.rule, h->H, t_end});
         SweepDesc d;
@@ -923,7 +981,7 @@ size_t pamc_footprint(pamc_handle h, const pamc_params *p) {
     if (!h || !p || h->dense) return 0;
     const size_t n = (size_t)h->n, R = (size_t)std::max(p->R, 1), S = (size_t)std::max(p->sweeps, 1);
     const size_t slots = kSchedSlots;
-    size_t b = 2 * R * n + 2 * R * 8 + 4 * R * 4 + n;
+    size_t b = 2 * R * n + 2 * R * 8 + 4 * R * 4 + 2 * R * 4 + n;
     b += slots * S * (n * 4 + (n + 1) * 4 + 4 + n * 4 + n * 4);
     if (h->ell_w > 0) b += slots * S * (((n + 31) / 32) * 32 * (size_t)h->ell_w * 4 + n * 8);
     b += (size_t)(p->kind == 0 ? 2 * h->H + 1 : (4 * h->H + 1) * (4 * h->H + 1) + 4 * h->H + 1) * 8;

@@ -90,6 +90,8 @@ struct PrepDesc {
     uint32_t key0, key1;
     const int64_t *en[2];   // E_src = en[ctl->t & 1]
     int32_t t_end;
+    int32_t *fam;           // [2][R] lineage, double-buffered by step parity
+    int32_t fam_reset;      // a restart re-initialises the population
 };
 
 struct TabDesc {
@@ -177,6 +179,13 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
 cudaError_t launch_init(int kind, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
                         uint64_t seed, int32_t t, int only_if_restart, const DevCtl *ctl,
                         int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st);
+
+// ---- diagnostics (diag.cu)
+// Pairwise corrected Hamming distances of a +-1 population (R rows of n int8):
+// hist[min(d, n - d)] += 1 and *sum += min(d, n - d) over all pairs r < r'.
+// bits: scratch of R * ceil(n / 32) words.  hist and sum are zeroed first.
+cudaError_t launch_hamming(int32_t n, int32_t R, const int8_t *spins, uint32_t *bits,
+                           unsigned long long *hist, unsigned long long *sum, cudaStream_t st);
 
 // ---- dense instances (dense.cu)
 cudaError_t launch_dense_validate(int32_t n, const int8_t *J, int *err, cudaStream_t st);

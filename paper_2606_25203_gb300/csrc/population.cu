@@ -90,7 +90,7 @@ __device__ __forceinline__ void
 prep_body(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau, uint32_t key0,
           uint32_t key1, const int64_t *__restrict__ E_src, DevCtl *__restrict__ ctl,
           int32_t *__restrict__ parent, int32_t *__restrict__ count, int32_t *__restrict__ ncm_idx,
-          int32_t *__restrict__ targets) {
+          int32_t *__restrict__ targets, int32_t *__restrict__ fam, int32_t fam_reset) {
     extern __shared__ __align__(16) unsigned char sm[];
     uint64_t *C = reinterpret_cast<uint64_t *>(sm);             // R prefix sums
     int32_t *cnt = reinterpret_cast<int32_t *>(sm + (size_t)R * 8);
@@ -102,6 +102,7 @@ prep_body(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t t
     const double delta = ctl->delta;
     const bool resampled = z > 1 && do_resample;
     const bool ncm = z > 1 && ctl->enable_cm && ctl->cooldown == 0;
+    const bool restarted = ctl->restart != 0;
     __syncthreads();
 
     for (int32_t m = threadIdx.x; m < R; m += blockDim.x) { cnt[m] = 0; ncm_idx[m] = -1; }
@@ -173,6 +174,14 @@ prep_body(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t t
     }
     __syncthreads();
     for (int32_t m = threadIdx.x; m < R; m += blockDim.x) count[m] = cnt[m];
+    // lineage: slot m joins its parent's family (double-buffered by step
+    // parity); a re-initialised population starts new families
+    if (fam) {
+        const int32_t *fs = fam + (size_t)(t & 1) * R;
+        int32_t *fd = fam + (size_t)((t + 1) & 1) * R;
+        for (int32_t m = threadIdx.x; m < R; m += blockDim.x)
+            fd[m] = (fam_reset && restarted) ? m : fs[parent[m]];
+    }
 
     if (ncm && kind == 0) {
         // targets: the n_top slots with the lowest (energy, slot index)
@@ -204,8 +213,9 @@ __global__ void __launch_bounds__(kPrepThreads)
 k_prep(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau, uint32_t key0,
        uint32_t key1, const int64_t *__restrict__ E_src, DevCtl *__restrict__ ctl,
        int32_t *__restrict__ parent, int32_t *__restrict__ count, int32_t *__restrict__ ncm_idx,
-       int32_t *__restrict__ targets) {
-    prep_body(R, kind, do_resample, n_top, tau, key0, key1, E_src, ctl, parent, count, ncm_idx, targets);
+       int32_t *__restrict__ targets, int32_t *__restrict__ fam, int32_t fam_reset) {
+    prep_body(R, kind, do_resample, n_top, tau, key0, key1, E_src, ctl, parent, count, ncm_idx, targets, fam,
+              fam_reset);
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep_batched(const PrepDesc *__restrict__ descs) {
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_batched(const PrepDesc *_
     const int32_t t = d.ctl->t;
     if (t >= d.t_end) return;
     prep_body(d.R, d.kind, d.do_resample, d.n_top, d.tau, d.key0, d.key1, d.en[t & 1], d.ctl, d.parent, d.count,
-              d.ncm_idx, d.targets);
+              d.ncm_idx, d.targets, d.fam, d.fam_reset);
 }
 
 // ---------------------------------------------------------------- NCM
@@ -467,13 +477,14 @@ cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint
 size_t prep_smem_bytes(int32_t R) { return (size_t)R * 8 + (size_t)R * 4; }
 
 cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
-                        int32_t *count, int32_t *ncm_idx, int32_t *targets, cudaStream_t st) {
+                        int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, cudaStream_t st) {
     const size_t smem = prep_smem_bytes(p.R);
     cudaError_t err = allow_dynamic_smem(k_prep, smem);
     if (err != cudaSuccess) return err;
     k_prep<<<1, kPrepThreads, smem, st>>>(p.R, p.kind, p.resample, p.n_top, p.cooldown_tau,
                                           (uint32_t)p.seed, (uint32_t)(p.seed >> 32), E_src, ctl,
-                                          parent, count, ncm_idx, targets);
+                                          parent, count, ncm_idx, targets, fam,
+                                          p.z_rst > 0 && p.restart_reinit ? 1 : 0);
     return cudaGetLastError();
 }
 

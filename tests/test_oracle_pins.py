@@ -422,3 +422,51 @@ def test_augmented_run_invokes_ncm_and_preserves_energy():
     run.step(150)
     st = run.ctl()
     assert st["ncm_flipped"] > 0 and st["ncm_dE_max"] == 0 and st["cycle"] == 1
+
+
+# ---------------------------------------------------------------- diagnostics
+def test_hamming_hand_example():
+    """Three replicas of four spins: d(s0,s1)=1, d(s0,s2)=4 -> 0 (complement),
+    d(s1,s2)=3 -> 1; histogram [1, 2, 0], sum 2, mean 2 / (3 pairs * 4)."""
+    s = np.array([[1, 1, 1, 1], [1, -1, 1, 1], [-1, -1, -1, -1]], dtype=np.int8)
+    hist, total = oracle.hamming_counts(s)
+    assert hist.tolist() == [1, 2, 0]
+    assert total == 2
+
+
+def test_hamming_symmetries():
+    rng = np.random.default_rng(5)
+    s = np.where(rng.random((7, 11)) < 0.5, 1, -1).astype(np.int8)
+    hist, total = oracle.hamming_counts(s)
+    assert hist.sum() == 7 * 6 // 2
+    assert total == int((np.arange(hist.size) * hist).sum())
+    # flipping a whole replica or permuting the spins changes nothing
+    s2 = s.copy()
+    s2[3] = -s2[3]
+    perm = rng.permutation(11)
+    for other in (s2, s[:, perm], s[::-1]):
+        h2, t2 = oracle.hamming_counts(other)
+        assert h2.tolist() == hist.tolist() and t2 == total
+
+
+def test_hamming_distribution_of_independent_pairs():
+    """Independent uniform replicas: d ~ Binomial(n, 1/2), so dc = min(d, n-d)
+    has P(k) = 2 C(n,k) / 2^n for k < n/2 and C(n, n/2) / 2^n at k = n/2."""
+    n, trials = 6, 20000
+    rng = np.random.default_rng(9)
+    counts = np.zeros(n // 2 + 1)
+    for _ in range(trials):
+        s = np.where(rng.random((2, n)) < 0.5, 1, -1).astype(np.int8)
+        counts += oracle.hamming_counts(s)[0]
+    p = np.array([2 * math.comb(n, k) for k in range(n // 2)] + [math.comb(n, n // 2)]) / 2 ** n
+    chi2 = float(((counts - trials * p) ** 2 / (trials * p)).sum())
+    assert chi2 < 16.3   # 3 degrees of freedom, p = 0.001
+
+
+def test_lineage_composition():
+    fam = np.arange(6)
+    fam = oracle.lineage_step(fam, [0, 0, 2, 3, 3, 3])
+    assert fam.tolist() == [0, 0, 2, 3, 3, 3]
+    fam = oracle.lineage_step(fam, [1, 1, 1, 4, 5, 5])
+    assert fam.tolist() == [0, 0, 0, 3, 3, 3]
+    assert oracle.lineage_step(fam, [0] * 6, reinitialised=True).tolist() == list(range(6))
