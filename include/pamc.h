@@ -60,8 +60,10 @@ typedef enum {
 
 /* Parameters of one run (the inputs of Algorithm 1). */
 typedef struct {
-    int32_t kind;           /* 0 Max-Cut (Ising), 1 Max-3-Cut (three-state Potts) */
-    int32_t rule;           /* Ising: 0 heat-bath (Eq. 4), 1 Metropolis */
+    int32_t kind;           /* 0 Max-Cut (Ising), 1 Max-K-Cut (K-state Potts) */
+    int32_t rule;           /* Ising: 0 heat-bath (Eq. 4), 1 Metropolis;
+                               Potts: 0 cascaded sampler (Suppl. S3, K = 3),
+                               2 softmax noisy argmax (Sec. III.E, 2 <= K <= 8) */
     int32_t R;              /* population size */
     int32_t sweeps;         /* S, sweeps per temperature step */
     int32_t steps;          /* iterations; dbeta = (beta1-beta0)/(steps-1) */
@@ -78,6 +80,9 @@ typedef struct {
     uint64_t seed;          /* Philox key */
     int32_t restart_reinit; /* 1: a restart re-randomises the population */
     int32_t resample;       /* 1 PAMC; 0 independent chains (SA baseline) */
+    int32_t K;              /* Potts labels; 0 means 3 */
+    double gamma;           /* softmax noisy argmax: sigma <- argmax_c (P_c - gamma U_c),
+                               U_c uniform on [0, 1); finite, >= 0 */
 } pamc_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Must be

@@ -59,6 +59,7 @@ class _Params(ctypes.Structure):
         ("max_distinct_short", ctypes.c_int32), ("max_distinct_long", ctypes.c_int32),
         ("reheat_factor", ctypes.c_double), ("target_cut", ctypes.c_int64),
         ("seed", ctypes.c_uint64), ("restart_reinit", ctypes.c_int32), ("resample", ctypes.c_int32),
+        ("K", ctypes.c_int32), ("gamma", ctypes.c_double),
     ]
 
 
@@ -102,6 +103,8 @@ def lib():
             L.orc_ncm_replica.restype = i32
             L.orc_control.argtypes = [ctypes.POINTER(_Ctl), ctypes.POINTER(_Params), dbl, i64]
             L.orc_control.restype = ctypes.c_int
+            L.orc_softmax_pick.argtypes = [i32, P, dbl, dbl, P]
+            L.orc_softmax_pick.restype = i32
             _lib = L
     return _lib
 
@@ -182,6 +185,13 @@ def ncm_replica(rp, col, J, s, h, mis_trials, seed, t, r):
                                      int(mis_trials), int(seed), int(t), int(r)))
 
 
+def softmax_pick(syn, beta: float, gamma: float, u) -> int:
+    """One softmax noisy-argmax label choice (see pamc_oracle.h)."""
+    syn = np.ascontiguousarray(syn, dtype=np.int32)
+    u = np.ascontiguousarray(u, dtype=np.uint32)
+    return int(lib().orc_softmax_pick(int(syn.shape[0]), _ptr(syn), float(beta), float(gamma), _ptr(u)))
+
+
 def hamming_counts(spins):
     """Replica diversity (Suppl., Hamming distance of replicas), written out
     from its definition: for every pair r < r' of the R x n +-1 population,
@@ -237,7 +247,7 @@ class Controller:
 DEFAULTS = dict(kind=0, rule=0, R=16, sweeps=1, steps=10, beta0=0.1, beta1=3.0, stagnation=0,
                 z_rst=0, cooldown_tau=10, n_top=0, mis_trials=4, win_short=25, win_long=40,
                 max_distinct_short=3, max_distinct_long=5, reheat_factor=0.8, target_cut=-1,
-                seed=0, restart_reinit=1, resample=1)
+                seed=0, restart_reinit=1, resample=1, K=3, gamma=1.0)
 
 
 def make_params(**kw) -> dict:
@@ -283,10 +293,10 @@ class OracleRun:
         return out
 
     def fields(self) -> np.ndarray:
-        f = 3 if self.p["kind"] == 1 else 1
+        f = self.p["K"] if self.p["kind"] == 1 else 1
         out = np.zeros((self.R, self.n * f), dtype=np.int32)
         lib().orc_get_fields(self._h, _ptr(out))
-        return out.reshape(self.R, self.n, f) if f == 3 else out
+        return out.reshape(self.R, self.n, f) if self.p["kind"] == 1 else out
 
     def energy(self) -> np.ndarray:
         out = np.zeros(self.R, dtype=np.int64)

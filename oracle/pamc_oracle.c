@@ -206,7 +206,7 @@ struct orc_state {
     int32_t hist_len;
 };
 
-static int32_t nf(const orc_state *st) { return st->p.kind == 1 ? 3 : 1; }
+static int32_t nf(const orc_state *st) { return st->p.kind == 1 ? st->p.K : 1; }
 
 int64_t orc_energy_ising(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *J,
                          const int8_t *s) {
@@ -241,10 +241,11 @@ static void orc_fields_replica(const orc_state *st, const int8_t *s, int32_t *h)
             h[k] = acc;
         }
     } else {
+        int32_t K = st->p.K;
         for (int32_t k = 0; k < n; ++k) {
-            int32_t a[3] = {0, 0, 0};
+            int32_t *a = h + (size_t)K * k;
+            for (int32_t c = 0; c < K; ++c) a[c] = 0;
             for (int32_t e = st->rp[k]; e < st->rp[k + 1]; ++e) a[s[st->col[e]]] += st->J[e];
-            h[3 * k] = a[0]; h[3 * k + 1] = a[1]; h[3 * k + 2] = a[2];
         }
     }
 }
@@ -271,7 +272,7 @@ static void orc_init_population(orc_state *st, int32_t t) {
             uint32_t x = u[r & 3];
             int8_t v;
             if (st->p.kind == 0) v = (x >> 31) ? 1 : -1;
-            else v = (int8_t)(((uint64_t)x * 3u) >> 32);
+            else v = (int8_t)(((uint64_t)x * (uint64_t)st->p.K) >> 32);
             st->s[(size_t)r * n + i] = v;
         }
         orc_refresh_replica(st, r);
@@ -282,6 +283,9 @@ orc_state *orc_create(int32_t n, const int32_t *rp, const int32_t *col, const in
                       const orc_params *p) {
     if (n <= 0 || !rp || !p || p->R <= 0 || p->sweeps < 0 || p->steps <= 0) return NULL;
     if (p->kind != 0 && p->kind != 1) return NULL;
+    if (p->kind == 1 && !((p->rule == 0 && p->K == 3) || (p->rule == 2 && p->K >= 2 && p->K <= 8)))
+        return NULL;
+    if (p->kind == 1 && p->rule == 2 && !(p->gamma >= 0.0)) return NULL;
     if (rp[0] != 0) return NULL;
     int32_t nnz = rp[n];
     for (int32_t i = 0; i < n; ++i) {
@@ -394,6 +398,58 @@ static void orc_sweep_potts(orc_state *st, int32_t r, const int32_t *perm, int32
                 int32_t j = st->col[e];
                 h[3 * j + old] -= st->J[e];
                 h[3 * j + nw] += st->J[e];
+            }
+        }
+    }
+}
+
+int32_t orc_softmax_pick(int32_t K, const int32_t *syn, double beta, double gamma, const uint32_t *u) {
+    int32_t smax = syn[0];
+    for (int32_t c = 1; c < K; ++c)
+        if (syn[c] > smax) smax = syn[c];
+    float e[8];
+    float S = 0.0f;
+    for (int32_t c = 0; c < K; ++c) {
+        e[c] = (float)orc_det_exp(-(beta * (double)(smax - syn[c])));
+        S = S + e[c];
+    }
+    const float g = (float)gamma;
+    int32_t best = 0;
+    float vbest = 0.0f;
+    for (int32_t c = 0; c < K; ++c) {
+        const float P = e[c] / S;
+        const float U = (float)u[c] * 0x1p-32f;
+        const float v = P - g * U;
+        if (c == 0 || v > vbest) { vbest = v; best = c; }
+    }
+    return best;
+}
+
+/* Potts with K labels and the softmax noisy-argmax update (Sec. III.E):
+ * the draws of replica r at vertex k are words c mod 4 of Philox counters
+ * (k, sweep, t, FLIP<<24 | (r * ceil(K/4) + c/4)), c = 0..K-1. */
+static void orc_sweep_potts_softmax(orc_state *st, int32_t r, const int32_t *perm, int32_t sweep) {
+    int32_t n = st->n, K = st->p.K, nb = (K + 3) / 4;
+    int8_t *s = st->s + (size_t)r * n;
+    int32_t *h = st->h + (size_t)r * n * K;
+    for (int32_t p = 0; p < n; ++p) {
+        int32_t k = perm[p];
+        uint32_t u[8];
+        for (int32_t b = 0; b < nb; ++b) {
+            uint32_t u4[4];
+            orc_draw4(st->p.seed, (uint32_t)k, (uint32_t)sweep, (uint32_t)st->t,
+                      ((uint32_t)ORC_TAG_FLIP << 24) | (uint32_t)(r * nb + b), u4);
+            for (int32_t q = 0; q < 4 && 4 * b + q < K; ++q) u[4 * b + q] = u4[q];
+        }
+        int8_t old = s[k];
+        int8_t nw = (int8_t)orc_softmax_pick(K, h + (size_t)K * k, st->beta, st->p.gamma, u);
+        if (nw != old) {
+            st->E[r] += -2 * ((int64_t)h[(size_t)K * k + nw] - h[(size_t)K * k + old]);
+            s[k] = nw;
+            for (int32_t e = st->rp[k]; e < st->rp[k + 1]; ++e) {
+                int32_t j = st->col[e];
+                h[(size_t)K * j + old] -= st->J[e];
+                h[(size_t)K * j + nw] += st->J[e];
             }
         }
     }
@@ -570,6 +626,7 @@ static void orc_iteration(orc_state *st) {
         orc_permutation(n, st->p.seed, st->t, sw, perm);
         for (int32_t r = 0; r < R; ++r) {
             if (st->p.kind == 0) orc_sweep_ising(st, r, perm, sw);
+            else if (st->p.rule == 2) orc_sweep_potts_softmax(st, r, perm, sw);
             else orc_sweep_potts(st, r, perm, sw);
         }
     }
@@ -624,7 +681,7 @@ void orc_get_best(const orc_state *st, int64_t *mstar, int8_t *spins) {
         int8_t f = st->best[0] < 0 ? -1 : 1;   /* canonical: spin 0 is +1 */
         for (int32_t i = 0; i < n; ++i) spins[i] = (int8_t)(st->best[i] * f);
     } else {
-        int8_t map[3] = {-1, -1, -1};          /* labels renamed in order of first use */
+        int8_t map[8] = {-1, -1, -1, -1, -1, -1, -1, -1};   /* labels renamed in order of first use */
         int8_t next = 0;
         for (int32_t i = 0; i < n; ++i) {
             int8_t c = st->best[i];

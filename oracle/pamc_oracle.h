@@ -73,8 +73,9 @@ int orc_resample(int32_t R, const int64_t *E, double delta, double escale, uint6
 /* ---- Whole Algorithm 1 on a CSR instance ---- */
 
 typedef struct {
-    int32_t kind;            /* 0 Max-Cut / Ising, 1 Max-3-Cut / three-state Potts */
-    int32_t rule;            /* Ising only: 0 heat-bath (Eq. 4), 1 Metropolis */
+    int32_t kind;            /* 0 Max-Cut / Ising, 1 Max-K-Cut / K-state Potts */
+    int32_t rule;            /* Ising: 0 heat-bath (Eq. 4), 1 Metropolis;
+                                Potts: 0 cascaded sampler (K = 3), 2 softmax noisy argmax */
     int32_t R, sweeps, steps;
     double beta0, beta1;     /* linear increment dbeta = (beta1-beta0)/(steps-1) */
     int32_t stagnation;      /* 0 conventional PAMC, 1 Algorithm 1 controller */
@@ -85,7 +86,18 @@ typedef struct {
     uint64_t seed;
     int32_t restart_reinit;
     int32_t resample;        /* 1 PAMC; 0 independent chains (the SA baseline) */
+    int32_t K;               /* Potts labels (3 for the cascaded sampler; 2..8 softmax) */
+    double gamma;            /* softmax noisy argmax: noise amplitude */
 } orc_params;
+
+/* Softmax noisy-argmax label choice (Sec. III.E, first Potts update):
+ * P_k = exp(beta syn_k) / sum_m exp(beta syn_m), new label =
+ * argmax_k (P_k - gamma U_k), U_k = u[k] / 2^32.  Decided in binary32 with
+ * round-to-nearest operations in this order: d_k = max_m syn_m - syn_k,
+ * e_k = (float) det_exp(-(beta * d_k)), S = e_0 + ... + e_{K-1} (left to
+ * right), P_k = e_k / S, U_k = (float) u[k] * 2^-32,
+ * v_k = P_k - (float) gamma * U_k; the first maximal k wins. */
+int32_t orc_softmax_pick(int32_t K, const int32_t *syn, double beta, double gamma, const uint32_t *u);
 
 typedef struct orc_state orc_state;
 

@@ -52,13 +52,14 @@ class Params(ctypes.Structure):
         ("max_distinct_short", ctypes.c_int32), ("max_distinct_long", ctypes.c_int32),
         ("reheat_factor", ctypes.c_double), ("target_cut", ctypes.c_int64),
         ("seed", ctypes.c_uint64), ("restart_reinit", ctypes.c_int32), ("resample", ctypes.c_int32),
+        ("K", ctypes.c_int32), ("gamma", ctypes.c_double),
     ]
 
 
 DEFAULTS = dict(kind=0, rule=0, R=16, sweeps=1, steps=10, beta0=0.1, beta1=3.0, stagnation=0,
                 z_rst=0, cooldown_tau=10, n_top=0, mis_trials=4, win_short=25, win_long=40,
                 max_distinct_short=3, max_distinct_long=5, reheat_factor=0.8, target_cut=-1,
-                seed=0, restart_reinit=1, resample=1)
+                seed=0, restart_reinit=1, resample=1, K=3, gamma=1.0)
 
 _lib = None
 _alloc_cbs = None

@@ -199,8 +199,10 @@ void release_run(pamc_handle h) {
 // Scores every shape by the fraction of group slots used over whole waves,
 // the lane efficiency of a level (average level size over the lanes of a
 // group), and resident warps per SM.  PAMC_SWEEP_CFG="gpc,wpg" overrides.
+int sweep_kind(const pamc_params &p) { return p.kind == 0 ? 0 : (p.rule == 2 ? 2 : 1); }
+
 SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level, int sms) {
-    const int RPG = kind == 0 ? 4 : 2;
+    const int RPG = kind == 1 ? 2 : 4;
     const int32_t groups = (R + RPG - 1) / RPG;
     if (const char *env = getenv("PAMC_SWEEP_CFG")) {
         int a = 0, b = 0;
@@ -303,7 +305,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_E[0], 0, 64 * 8, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_E[1], 0, 64 * 8, h->stream);
     // initial population, its fields (tensor-core recompute) and energies
-    if (e == cudaSuccess) e = launch_init_spins(0, n, R, p.seed, 0, 0, h->d_ctl, h->d_spins[0], h->stream);
+    if (e == cudaSuccess) e = launch_init_spins(0, 0, n, R, p.seed, 0, 0, h->d_ctl, h->d_spins[0], h->stream);
     if (e == cudaSuccess)
         e = launch_dense_recompute(n, R, h->d_J, h->d_spins[0], h->d_ident, nullptr, h->d_nonc, h->d_H,
                                    h->d_ctl, h->stream, -1);
@@ -345,7 +347,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
         h->launches += 7;
         if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
             const int32_t tk = (int32_t)(t + 1);
-            e = launch_init_spins(0, n, R, p.seed, tk, 1, h->d_ctl, dst, h->stream);
+            e = launch_init_spins(0, 0, n, R, p.seed, tk, 1, h->d_ctl, dst, h->stream);
             if (e == cudaSuccess)
                 e = launch_dense_recompute(n, R, h->d_J, dst, h->d_ident, nullptr, h->d_nonc, h->d_H,
                                            h->d_ctl, h->stream, tk);
@@ -468,9 +470,14 @@ pamc_status pamc_create_dense(int32_t n, const int8_t *w, int w_on_device, int c
 pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     if (!h || !pp) return fail(h, PAMC_ERR_ARG, "null handle or params");
     pamc_params p = *pp;
+    if (p.K == 0) p.K = 3;
     if (p.kind != 0 && p.kind != 1) return fail(h, PAMC_ERR_ARG, "kind must be 0 or 1");
-    if (p.rule != 0 && p.rule != 1) return fail(h, PAMC_ERR_ARG, "rule must be 0 or 1");
-    if (p.kind == 1 && p.rule != 0) return fail(h, PAMC_ERR_ARG, "Potts supports the cascaded heat-bath rule only");
+
+    if (p.kind == 0 && p.rule != 0 && p.rule != 1) return fail(h, PAMC_ERR_ARG, "Ising rule must be 0 or 1");
+    if (p.kind == 1 && !((p.rule == 0 && p.K == 3) || (p.rule == 2 && p.K >= 2 && p.K <= 8)))
+        return fail(h, PAMC_ERR_ARG, "Potts: rule 0 (cascaded) needs K = 3, rule 2 (softmax) 2 <= K <= 8");
+    if (p.kind == 1 && p.rule == 2 && !(p.gamma >= 0.0 && p.gamma < 1e30))
+        return fail(h, PAMC_ERR_ARG, "softmax noise amplitude gamma must be finite and >= 0");
     if (p.R < 1 || p.R > 16384) return fail(h, PAMC_ERR_RANGE, "R must be in [1, 16384]");
     if (p.sweeps < 0 || p.steps < 1) return fail(h, PAMC_ERR_ARG, "sweeps >= 0 and steps >= 1 required");
     if (p.win_short < 0 || p.win_long < 0 || p.win_short > kHistMax || p.win_long > kHistMax)
@@ -537,7 +544,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
         e = cudaMemcpyAsync(h->d_ncm_idx, minus.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_best, 0, n, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "initial state upload");
-    e = launch_init(p.kind, n, h->d_rp, h->d_adj, R, p.seed, 0, 0, h->d_ctl, h->W, h->d_spins[0],
+    e = launch_init(p.kind, p.K, n, h->d_rp, h->d_adj, R, p.seed, 0, 0, h->d_ctl, h->W, h->d_spins[0],
                     h->d_E[0], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "initial population");
     h->launches += 2;
@@ -561,8 +568,8 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    h->cfg = choose_cfg(p.kind, n, R, h->H, avg_level, sms);
-    if (sweep_smem_bytes(p.kind, n, h->H, h->cfg) > kSmemMax) {
+    h->cfg = choose_cfg(sweep_kind(p), n, R, h->H, avg_level, sms);
+    if (sweep_smem_bytes(sweep_kind(p), n, h->H, h->cfg) > kSmemMax) {
         release_run(h);
         return fail(h, PAMC_ERR_RANGE, "n = %d: one replica group's spins exceed shared memory", n);
     }
@@ -603,13 +610,13 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
         }
         SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w};
         if (e == cudaSuccess)
-            e = launch_sweep(p.kind, p.rule, n, h->d_rp, h->d_adj, h->H, p, (int32_t)t,
+            e = launch_sweep(sweep_kind(p), p.rule, n, h->d_rp, h->d_adj, h->H, p, (int32_t)t,
                              (int32_t)(t % kSchedSlots), sv, h->d_tab, src, h->d_parent,
                              h->d_ncm_buf, h->d_ncm_idx, dst, Ed, h->d_ctl, h->cfg, h->W, h->stream);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 2;
         if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
-            e = launch_init(p.kind, n, h->d_rp, h->d_adj, p.R, p.seed, (int32_t)(t + 1), 1, h->d_ctl,
+            e = launch_init(p.kind, p.K, n, h->d_rp, h->d_adj, p.R, p.seed, (int32_t)(t + 1), 1, h->d_ctl,
                             h->W, dst, Ed, h->stream);
             h->launches += 2;
         }
@@ -665,9 +672,9 @@ pamc_status pamc_best(pamc_handle h, int64_t *cut, int8_t *spins) {
             const int8_t f = b[0] < 0 ? -1 : 1;   // canonical: spin 0 is +1
             for (int32_t i = 0; i < h->n; ++i) spins[i] = (int8_t)(b[i] * f);
         } else {
-            int8_t map[4] = {-1, -1, -1, -1}, next = 0;   // labels in order of first use
+            int8_t map[8] = {-1, -1, -1, -1, -1, -1, -1, -1}, next = 0;   // labels in order of first use
             for (int32_t i = 0; i < h->n; ++i) {
-                const int8_t v = b[i] & 3;
+                const int8_t v = b[i] & 7;
                 if (map[v] < 0) map[v] = next++;
                 spins[i] = map[v];
             }

@@ -164,7 +164,14 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
                                const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
                                const DevCtl *ctl, SweepCfg cfg, cudaStream_t st);
 
+// Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax.
 size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg);
+size_t sweep_softmax_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
+cudaError_t launch_sweep_softmax(int32_t n, const int32_t *rp, const uint32_t *adj, int32_t H,
+                                 const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
+                                 const uint64_t *tab, const int8_t *src, const int32_t *parent,
+                                 const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst, const DevCtl *ctl,
+                                 SweepCfg cfg, int64_t Wsum, cudaStream_t st);
 
 cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const uint32_t *adj,
                          int32_t H, const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
@@ -176,7 +183,7 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
 // Random (re)initialisation of the population with key t, and its energies;
 // when only_if_restart is set the kernels do nothing unless the controller
 // has just restarted the schedule.
-cudaError_t launch_init(int kind, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
+cudaError_t launch_init(int kind, int32_t K, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
                         uint64_t seed, int32_t t, int only_if_restart, const DevCtl *ctl,
                         int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st);
 
@@ -201,7 +208,7 @@ cudaError_t launch_dense_recompute(int32_t n, int32_t R, const int8_t *J, const 
                                    cudaStream_t st, int restart_t);
 cudaError_t launch_dense_energy(int32_t n, int32_t R, const int32_t *H, const int8_t *spins, int64_t *E,
                                 const DevCtl *ctl, cudaStream_t st, int restart_t);
-cudaError_t launch_init_spins(int kind, int32_t n, int32_t R, uint64_t seed, int32_t t,
+cudaError_t launch_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint64_t seed, int32_t t,
                               int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st);
 int dense_block_positions();
 int dense_sweep_threads();

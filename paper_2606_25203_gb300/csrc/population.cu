@@ -34,6 +34,14 @@ __global__ void k_tables_batched(const TabDesc *__restrict__ descs) {
     tables_ising_body(d.rule, d.H, d.ctl, d.tab, 0, 1);
 }
 
+// Softmax Potts: e(d) = (float) exp(-beta d) for d = max_m syn_m - syn_c in [0, 2H].
+__global__ void k_tables_softmax(int32_t H, const DevCtl *__restrict__ ctl, float *__restrict__ tab) {
+    if (ctl->done) return;
+    const double beta = ctl->beta;
+    for (int32_t d = threadIdx.x; d <= 2 * H; d += blockDim.x)
+        tab[d] = __double2float_rn(det_exp(-__dmul_rn(beta, (double)d)));
+}
+
 __global__ void k_tables(int kind, int rule, int32_t H, const DevCtl *__restrict__ ctl,
                          uint64_t *__restrict__ tab) {
     if (ctl->done) return;
@@ -463,7 +471,9 @@ __global__ void __launch_bounds__(kCtlThreads) k_control_batched(const CtlDesc *
 
 cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint64_t *tab,
                           cudaStream_t st) {
-    if (kind == 0) {
+    if (kind == 1 && rule == 2) {
+        k_tables_softmax<<<1, 256, 0, st>>>(H, ctl, reinterpret_cast<float *>(tab));
+    } else if (kind == 0) {
         k_tables<<<1, 256, 0, st>>>(kind, rule, H, ctl, tab);
     } else {
         const int32_t W1 = 4 * H + 1;

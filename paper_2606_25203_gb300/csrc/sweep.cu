@@ -263,7 +263,7 @@ k_sweep(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t
 
 // Random initial population: Ising s = +1 iff the top bit of the draw is set,
 // Potts sigma = floor(3 u / 2^32); draw = Philox(i, 0, t, INIT<<24 | r/4)[r%4].
-__global__ void k_init_spins(int kind, int32_t n, int32_t R, uint32_t key0, uint32_t key1,
+__global__ void k_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint32_t key0, uint32_t key1,
                              int32_t t, int only_if_restart, const DevCtl *__restrict__ ctl,
                              int8_t *__restrict__ spins) {
     // a restart re-draws the population in the iteration that restarted
@@ -282,7 +282,7 @@ __global__ void k_init_spins(int kind, int32_t n, int32_t R, uint32_t key0, uint
             if (r >= R) break;
             int8_t v;
             if (kind == 0) v = (w[q] >> 31) ? 1 : -1;
-            else v = (int8_t)(((uint64_t)w[q] * 3ull) >> 32);
+            else v = (int8_t)(((uint64_t)w[q] * (uint64_t)K) >> 32);
             spins[(size_t)r * n + i] = v;
         }
     }
@@ -324,6 +324,7 @@ __global__ void k_energy(int kind, int32_t n, const int32_t *__restrict__ rp,
 
 size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg) {
     if (kind == 0) return sweep_ising_smem_bytes(n, H, cfg);
+    if (kind == 2) return sweep_softmax_smem_bytes(n, H, cfg);
     const int RPG = kind == 0 ? 4 : 2;
     const int tabn = kind == 0 ? (2 * H + 1) : (4 * H + 1);
     const int32_t n_pad = (n + 15) & ~15;
@@ -339,6 +340,9 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
     if (kind == 0)
         return launch_sweep_ising(rule, n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_buf,
                                   ncm_idx, dst, E_dst, ctl, cfg, st);
+    if (kind == 2)
+        return launch_sweep_softmax(n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_idx, dst, E_dst, ctl,
+                                    cfg, Wsum, st);
     const int RPG = kind == 0 ? 4 : 2;
     const int32_t groups = (p.R + RPG - 1) / RPG;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
@@ -363,26 +367,26 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_init(int kind, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
+cudaError_t launch_init(int kind, int32_t K, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
                         uint64_t seed, int32_t t, int only_if_restart, const DevCtl *ctl,
                         int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st) {
     const size_t total = (size_t)((R + 3) / 4) * n;
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
-    k_init_spins<<<grid, 256, 0, st>>>(kind, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
+    k_init_spins<<<grid, 256, 0, st>>>(kind, K, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
                                         only_if_restart, ctl, spins);
     k_energy<<<R, 256, 0, st>>>(kind, n, rp, adj, R, only_if_restart, ctl, Wsum, t, spins, E);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_spins(int kind, int32_t n, int32_t R, uint64_t seed, int32_t t,
+cudaError_t launch_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint64_t seed, int32_t t,
                               int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st) {
     const size_t total = (size_t)((R + 3) / 4) * n;
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
-    k_init_spins<<<grid, 256, 0, st>>>(kind, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
+    k_init_spins<<<grid, 256, 0, st>>>(kind, K, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
                                         only_if_restart, ctl, spins);
     return cudaGetLastError();
 }

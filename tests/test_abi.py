@@ -78,3 +78,22 @@ def test_null_arguments(lib):
     assert lib.pamc_init(None, None) == 1
     assert lib.pamc_step(None, 1) == 1
     assert lib.pamc_launch_count(None) == 0
+
+
+def test_params_layout_matches_header(tmp_path):
+    """The Python mirror of pamc_params has the C layout (size and every
+    field offset), checked against a program compiled from include/pamc.h."""
+    fields = [f[0] for f in pg.Params._fields_]
+    prog = ["#include <stddef.h>", "#include <stdio.h>", '#include "pamc.h"', "int main(void) {",
+            '  printf("%zu\\n", sizeof(pamc_params));']
+    prog += [f'  printf("%zu\\n", offsetof(pamc_params, {f}));' for f in fields]
+    prog += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert out[0] == ctypes.sizeof(pg.Params)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(pg.Params, f).offset == off, f

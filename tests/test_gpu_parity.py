@@ -79,6 +79,33 @@ def test_potts_signed(pg):
     compare_run(pg, inst, 8, kind=1, R=7, sweeps=3, beta0=0.3, beta1=2.0, seed=2)
 
 
+@pytest.mark.parametrize("K,gamma", [(3, 1.0), (2, 0.5), (4, 0.0), (5, 2.5), (8, 1.0)])
+def test_potts_softmax_noisy_argmax(pg, K, gamma):
+    # Sec. III.E softmax update, K labels, ragged R
+    inst = W.gnm(260, 1300, signed=K % 2 == 0, seed=K)
+    compare_run(pg, inst, 9, kind=1, rule=2, K=K, gamma=gamma, R=22, sweeps=2, beta0=0.1, beta1=3.0,
+                seed=3 + K)
+
+
+def test_potts_softmax_torus_restart_and_sa(pg):
+    inst = W.torus(18, 18, signed=True, seed=5)
+    compare_run(pg, inst, 30, kind=1, rule=2, K=3, gamma=0.7, R=40, sweeps=2, beta0=0.2, beta1=4.0,
+                z_rst=13, seed=9)
+    compare_run(pg, inst, 5, kind=1, rule=2, K=6, gamma=1.2, R=9, sweeps=3, resample=0, seed=2)
+
+
+def test_potts_rejects_bad_k(pg):
+    inst = W.torus(6, 6, signed=True, seed=1)
+    h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+    try:
+        for bad in (dict(kind=1, rule=0, K=4), dict(kind=1, rule=2, K=9), dict(kind=1, rule=2, K=1),
+                    dict(kind=1, rule=2, K=3, gamma=-1.0), dict(kind=1, rule=1)):
+            with pytest.raises(pg.PamcError):
+                pg.pamc_init(h, R=8, steps=2, **bad)
+    finally:
+        pg.pamc_destroy(h)
+
+
 def test_augmented_pamc_with_ncm_and_restart(pg):
     inst = W.torus(16, 16, signed=True, seed=2)
     ref, _ = compare_run(pg, inst, 150, R=32, sweeps=2, beta0=0.5, beta1=6.0, stagnation=1,

@@ -470,3 +470,71 @@ def test_lineage_composition():
     fam = oracle.lineage_step(fam, [1, 1, 1, 4, 5, 5])
     assert fam.tolist() == [0, 0, 0, 3, 3, 3]
     assert oracle.lineage_step(fam, [0] * 6, reinitialised=True).tolist() == list(range(6))
+
+
+# ---------------------------------------------------------------- softmax Potts
+def test_softmax_pick_gamma_zero_is_argmax():
+    """gamma = 0: the label with the largest probability, i.e. the largest
+    syn (softmax is monotone), the first one on ties."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        K = int(rng.integers(2, 9))
+        syn = rng.integers(-6, 7, size=K)
+        u = rng.integers(0, 2 ** 32, size=K, dtype=np.uint64).astype(np.uint32)
+        assert oracle.softmax_pick(syn, 0.7, 0.0, u) == int(np.argmax(syn))
+
+
+def test_softmax_pick_two_labels_closed_form():
+    """K = 2: label 0 wins iff U1 - U0 >= a = (P1 - P0) / gamma, and U1 - U0 is
+    triangular on [-1, 1]: P(0) = (1 - a)^2 / 2 for a >= 0, 1 - (1 + a)^2 / 2
+    for a < 0."""
+    rng = np.random.default_rng(12)
+    N = 40000
+    for syn, beta, gamma in [((0, 2), 0.4, 1.0), ((3, -1), 0.25, 0.7), ((1, 1), 1.0, 1.0), ((0, 5), 0.3, 2.0)]:
+        p1 = 1.0 / (1.0 + math.exp(beta * (syn[0] - syn[1])))
+        a = (p1 - (1.0 - p1)) / gamma
+        expect = (1 - a) ** 2 / 2 if a >= 0 else 1 - (1 + a) ** 2 / 2
+        u = rng.integers(0, 2 ** 32, size=(N, 2), dtype=np.uint64).astype(np.uint32)
+        zeros = sum(oracle.softmax_pick(syn, beta, gamma, u[i]) == 0 for i in range(N))
+        sd = math.sqrt(expect * (1 - expect) / N)
+        assert abs(zeros / N - expect) < 5 * sd + 1e-4, (syn, beta, gamma, zeros / N, expect)
+
+
+def test_softmax_pick_large_noise_is_uniform():
+    rng = np.random.default_rng(13)
+    K, N = 5, 20000
+    counts = np.zeros(K)
+    syn = np.array([4, -2, 0, 1, 3])
+    for i in range(N):
+        u = rng.integers(0, 2 ** 32, size=K, dtype=np.uint64).astype(np.uint32)
+        counts[oracle.softmax_pick(syn, 0.5, 1e6, u)] += 1
+    chi2 = float(((counts - N / K) ** 2 / (N / K)).sum())
+    assert chi2 < 18.5   # 4 degrees of freedom, p = 0.001
+
+
+@pytest.mark.parametrize("K", [2, 3, 5, 8])
+def test_softmax_potts_run_invariants(K):
+    """A softmax Potts run keeps its incremental syn fields and energies equal
+    to the definitions (Eq. 6-7) and labels in range; cut = (W - E)/2."""
+    inst = W.gnm(60, 170, signed=True, seed=K)
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, kind=1, rule=2, K=K, gamma=0.8, R=12, sweeps=2,
+                           steps=6, seed=4)
+    rp, col = inst.row_ptr, inst.col
+    J = -inst.w
+    for _ in range(6):
+        run.step(1)
+        s = run.spins()
+        assert s.min() >= 0 and s.max() < K
+        F = run.fields()
+        E = run.energy()
+        for r in range(run.R):
+            syn = np.zeros((inst.n, K), dtype=np.int64)
+            for k in range(inst.n):
+                for e in range(rp[k], rp[k + 1]):
+                    syn[k, s[r, col[e]]] += J[e]
+            np.testing.assert_array_equal(F[r], syn)
+            assert E[r] == oracle.energy_potts(rp, col, J.astype(np.int32), s[r])
+    m, best = run.best()
+    assert m == (run.weight_sum() - oracle.energy_potts(rp, col, J.astype(np.int32),
+                                                        best.astype(np.int8))) // 2
+    run.close()
