@@ -600,6 +600,69 @@ def run_batch(args):
         pg.pamc_destroy(h)
 
 
+POTTS_PARAMS = dict(kind=1, R=2048, sweeps=10, steps=300, beta0=0.1, beta1=3.0, seed=0)
+POTTS_WORKLOAD = "Max-3-Cut, random sparse N=2,000, m=12,000 (avg deg 12), unit weights, R=2048, 10 sweeps/step"
+
+
+def run_potts(args):
+    """Configuration 3: three-state Potts on the N=2,000 graph, the cascaded
+    sampler (rule 0) as the headline and the softmax noisy argmax (rule 2,
+    gamma 1) beside it; steps 0..K-1 of a fresh run timed with CUDA events."""
+    import torch
+    import paper_2606_25203_gb300 as pg
+    pg.load()
+    inst = W.c3_sparse2000()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    out = {}
+    for name, extra in (("cascaded", dict(rule=0)), ("softmax", dict(rule=2, K=3, gamma=1.0))):
+        P = dict(POTTS_PARAMS, **extra)
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w, stream=stream.cuda_stream)
+        s.init(**P)
+        s.step(args.warmup)
+        s.sync()
+        s.init(**P)
+        torch.cuda.synchronize()
+        l0 = s.launches()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with ClockSampler(0) as clk:
+            for k in range(args.steps):
+                flush.add_(1)
+                ev[k][0].record(stream)
+                s.step(1)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        cut, _ = s.best()
+        out[name] = dict(ms=ms, launches=s.launches() - l0, cut=int(cut), clocks=clk.summary())
+        s.close()
+    att = POTTS_PARAMS["R"] * inst.n * POTTS_PARAMS["sweeps"] * args.steps
+    deg = inst.nnz / inst.n
+    peaks, _ = load_peaks()
+    peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # cascaded: half a Philox call (30 ops), 2 ops per incident edge, two threshold tests (8)
+    ops = 30 + 2 * deg + 8
+    c = out["cascaded"]
+    ach = att * ops / (c["ms"] / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": att / (c["ms"] / 1e3), "unit": "attempts/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": c["ms"] / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": POTTS_WORKLOAD, **POTTS_PARAMS, "l2": "flushed between steps (512 MB write)",
+                   "timed_steps": f"steps 0..{args.steps - 1} of a fresh run"},
+        "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s", "frac": ach / peak,
+                     "traffic": None, "kernel": "k_sweep<Potts> (cascaded)", "ops_per_attempt": ops},
+        "cut_after_timed_steps": c["cut"],
+        "softmax": {"value": att / (out["softmax"]["ms"] / 1e3), "unit": "attempts/s",
+                    "ms_per_step": out["softmax"]["ms"] / args.steps, "cut_after_timed_steps": out["softmax"]["cut"],
+                    "gamma": 1.0},
+        "clocks": c["clocks"], "gpu_launches": c["launches"],
+    }
+    print(json.dumps(line))
+
+
 def run_diag(args):
     """Diagnostics on the torus population of the default workload (R=4096):
     the corrected pairwise Hamming histogram (8.4M pairs) and the lineage,
@@ -654,7 +717,7 @@ def main():
                     help="run one of the two instances (profiling)")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only: no e2e, kernel split or CPU baseline (profiling)")
-    ap.add_argument("--workload", choices=["sparse", "dense100k", "serving", "batch", "diag"],
+    ap.add_argument("--workload", choices=["sparse", "dense100k", "serving", "batch", "diag", "potts"],
                     default="sparse")
     ap.add_argument("--batch-requests", type=int, default=48)
     ap.add_argument("--batch-n-lo", type=int, default=800)
@@ -667,6 +730,9 @@ def main():
     ONLY = args.only
     if args.workload == "dense100k" and args.impl == "ours":
         run_dense(args)
+        return
+    if args.workload == "potts" and args.impl == "ours":
+        run_potts(args)
         return
     if args.workload == "diag" and args.impl == "ours":
         run_diag(args)

@@ -149,6 +149,16 @@ int64_t pamc_weight_sum(pamc_handle h);
  * NULL) into buf. */
 pamc_status pamc_last_error(pamc_handle h, char *buf, size_t len);
 
+/* Replace the current population with caller values (host, R rows of n:
+ * +-1 for Ising, labels 0..K-1 for Potts), e.g. a warm start.  The energies,
+ * and for dense instances the fields H = J S (the full recompute), are
+ * recomputed from the definition.  PAMC_ERR_RANGE for a value out of range,
+ * PAMC_ERR_STATE once the run reached its target.  Synchronises. */
+pamc_status pamc_set_population(pamc_handle h, const int8_t *spins);
+/* Dense instances: the local fields H[r][k] = sum_j J_kj s_j of the current
+ * population as the device holds them (R rows of n int32, caller-owned).
+ * PAMC_ERR_ARG for sparse handles, which keep no field array. */
+pamc_status pamc_fields(pamc_handle h, int32_t *H);
 /* Diversity of the current population (Suppl., Hamming distance of
  * replicas): for every pair of replicas r < r', d = the number of spins in
  * which they differ, corrected for the global flip symmetry of Max-Cut as

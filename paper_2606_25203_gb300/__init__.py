@@ -25,7 +25,7 @@ __all__ = [
     "pamc_sweeps_noalloc", "pamc_footprint", "pamc_batch_create", "pamc_batch_add", "pamc_batch_step",
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
-    "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_hamming", "pamc_lineage",
+    "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_hamming", "pamc_lineage", "pamc_set_population", "pamc_fields",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -120,6 +120,10 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_sweeps_noalloc.argtypes = [i32, i32, P, P, P, i32, i32, i32, i32, ctypes.c_double,
                                       ctypes.c_uint64, i32, P, P, P, P, ctypes.c_char_p,
                                       ctypes.c_size_t]
+    L.pamc_set_population.argtypes = [P, P]
+    L.pamc_set_population.restype = ctypes.c_int
+    L.pamc_fields.argtypes = [P, P]
+    L.pamc_fields.restype = ctypes.c_int
     L.pamc_hamming.argtypes = [P, P, P]
     L.pamc_hamming.restype = ctypes.c_int
     L.pamc_lineage.argtypes = [P, P, P]
@@ -301,6 +305,17 @@ def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed,
                                _stream_ptr(dev, stream), buf, 256)
     if rc != 0:
         raise PamcError(rc, buf.value.decode(errors="replace"))
+
+
+def pamc_set_population(h, spins):
+    arr = np.ascontiguousarray(spins, dtype=np.int8)
+    _check(_lib.pamc_set_population(h, _ptr(arr)), h)
+
+
+def pamc_fields(h, R: int, n: int):
+    H = np.zeros((R, n), dtype=np.int32)
+    _check(_lib.pamc_fields(h, _ptr(H)), h)
+    return H
 
 
 def pamc_hamming(h, n: int):

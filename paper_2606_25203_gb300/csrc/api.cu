@@ -702,6 +702,49 @@ pamc_status pamc_state(pamc_handle h, int8_t *spins, int64_t *E, int32_t *parent
     return PAMC_OK;
 }
 
+pamc_status pamc_set_population(pamc_handle h, const int8_t *spins) {
+    if (!h || !spins) return fail(h, PAMC_ERR_ARG, "null argument");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_set_population before pamc_init");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    if (c.done) return fail(h, PAMC_ERR_STATE, "the run has reached its target");
+    const int32_t n = h->n, R = h->p.R;
+    const size_t total = (size_t)R * n;
+    for (size_t x = 0; x < total; ++x) {
+        const int8_t v = spins[x];
+        const bool ok = h->p.kind == 0 ? (v == 1 || v == -1) : (v >= 0 && v < h->p.K);
+        if (!ok) return fail(h, PAMC_ERR_RANGE, "spin %zu out of range", x);
+    }
+    const int cur = c.t & 1;
+    cudaError_t e = cudaMemcpyAsync(h->d_spins[cur], spins, total, cudaMemcpyHostToDevice, h->stream);
+    if (h->dense) {
+        if (e == cudaSuccess)
+            e = launch_dense_recompute(n, R, h->d_J, h->d_spins[cur], h->d_ident, nullptr, h->d_nonc, h->d_H,
+                                       h->d_ctl, h->stream, -1);
+        if (e == cudaSuccess)
+            e = launch_dense_energy(n, R, h->d_H, h->d_spins[cur], h->d_E[cur], h->d_ctl, h->stream, -1);
+    } else if (e == cudaSuccess) {
+        e = launch_energy(h->p.kind, n, h->d_rp, h->d_adj, R, h->d_ctl, h->W, h->d_spins[cur], h->d_E[cur],
+                          h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set population");
+    h->launches += 2;
+    return PAMC_OK;
+}
+
+pamc_status pamc_fields(pamc_handle h, int32_t *H) {
+    if (!h || !H) return fail(h, PAMC_ERR_ARG, "null argument");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_fields before pamc_init");
+    if (!h->dense) return fail(h, PAMC_ERR_ARG, "sparse runs keep no field array (fields are pulled per visit)");
+    pamc_status s = pamc_sync(h);
+    if (s != PAMC_OK) return s;
+    const cudaError_t e = cudaMemcpy(H, h->d_H, sizeof(int32_t) * (size_t)h->p.R * h->n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "fields readback");
+    return PAMC_OK;
+}
+
 pamc_status pamc_control_state(pamc_handle h, int64_t *iv, double *dv) {
     if (!h || !iv || !dv) return fail(h, PAMC_ERR_ARG, "null argument");
     if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_control_state before pamc_init");

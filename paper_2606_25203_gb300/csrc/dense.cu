@@ -107,7 +107,8 @@ __global__ void k_dense_tables(int rule, int32_t Hc, int32_t n, DevCtl *__restri
 // stored in HBM as e4m3 bytes (+-1 and 0 are exact), the spins are converted
 // to e4m3 while staged.  Every product is +-1 or 0 and every partial sum an
 // integer of magnitude < 2^24, so the f32 result is the exact integer field
-// (checked at |h| = n-1 by the adversarial recompute test).
+// (a GPU test sets a replica equal to a row of J, |h| = n - 1 up to 99,999,
+// and compares every field with an exact product).
 // A = J (row-major, K contiguous), B = S^T (column-major: each replica's spin
 // row is K-contiguous).  One CTA per row slice of kRcRows rows and all
 // (<= 64) replicas; K streamed through shared memory with cp.async.

@@ -187,6 +187,10 @@ cudaError_t launch_init(int kind, int32_t K, int32_t n, const int32_t *rp, const
                         uint64_t seed, int32_t t, int only_if_restart, const DevCtl *ctl,
                         int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st);
 
+// Energies of a given population from the definition (one CTA per replica).
+cudaError_t launch_energy(int kind, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
+                          const DevCtl *ctl, int64_t Wsum, const int8_t *spins, int64_t *E, cudaStream_t st);
+
 // ---- diagnostics (diag.cu)
 // Pairwise corrected Hamming distances of a +-1 population (R rows of n int8):
 // hist[min(d, n - d)] += 1 and *sum += min(d, n - d) over all pairs r < r'.

@@ -380,6 +380,12 @@ cudaError_t launch_init(int kind, int32_t K, int32_t n, const int32_t *rp, const
     return cudaGetLastError();
 }
 
+cudaError_t launch_energy(int kind, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
+                          const DevCtl *ctl, int64_t Wsum, const int8_t *spins, int64_t *E, cudaStream_t st) {
+    k_energy<<<R, 256, 0, st>>>(kind, n, rp, adj, R, 0, ctl, Wsum, 0, spins, E);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint64_t seed, int32_t t,
                               int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st) {
     const size_t total = (size_t)((R + 3) / 4) * n;

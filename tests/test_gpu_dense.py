@@ -101,3 +101,78 @@ def test_dense_rejects(pg):
     with pytest.raises(pg.PamcError):
         pg.pamc_init(h, R=8, steps=2, stagnation=1)
     pg.pamc_destroy(h)
+
+
+def _exact_fields(torch, Jd, S, chunk=4096):
+    """H = J S^T row block by row block with fp32 products on CUDA cores
+    (exact: integer sums below 2^24, TF32 off)."""
+    Sf = torch.from_numpy(S).cuda().float().T.contiguous()
+    out = torch.empty((S.shape[0], Jd.shape[0]), dtype=torch.int64, device="cuda")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for r0 in range(0, Jd.shape[0], chunk):
+            out[:, r0:r0 + chunk] = (Jd[r0:r0 + chunk].float() @ Sf).round().long().T
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [32768, 100000])
+def test_dense_recompute_exact_at_large_fields(pg, n):
+    """The tensor-core recompute H = J S is the exact integer field where it
+    needs the most bits: replica 0 equals row 0 of J, so h_0 = n - 1 (up to
+    99,999 = 17 bits), replica 1 equals minus row 7 (h_7 = -(n - 1)), replica
+    2 is all +1 (row sums).  Every field is compared with an exact fp32
+    product on CUDA cores, and the energies with the definition; then the run
+    goes on from the set population and is checked again."""
+    import torch
+    R, seed = 8, 5
+    wd = torch.empty((n, n), dtype=torch.int8, device="cuda")
+    for r0 in range(0, n, 2000):
+        wd[r0:r0 + 2000] = -W.dense_rows_torch(n, r0, min(n, r0 + 2000), seed, device="cuda")
+    h = pg.pamc_create_dense(n, wd)
+    try:
+        pg.pamc_init(h, R=R, sweeps=1, steps=4, seed=1)
+        Jd = wd.neg_()                                    # J = -w, reusing the buffer
+        rng = np.random.default_rng(0)
+        S = np.where(rng.random((R, n)) < 0.5, 1, -1).astype(np.int8)
+        S[0] = np.where(Jd[0].cpu().numpy() >= 0, 1, -1)
+        S[1] = -np.where(Jd[7].cpu().numpy() >= 0, 1, -1)
+        S[2] = 1
+        pg.pamc_set_population(h, S)
+        H = pg.pamc_fields(h, R, n)
+        ref = _exact_fields(torch, Jd, S)
+        assert H[0, 0] == n - 1 and H[1, 7] == -(n - 1)
+        np.testing.assert_array_equal(H, ref)
+        _, E, _, _ = pg.pamc_state(h, R, n)
+        np.testing.assert_array_equal(E, -(S.astype(np.int64) * ref).sum(axis=1) // 2)
+        pg.pamc_step(h, 2)
+        spins, E2, _, _ = pg.pamc_state(h, R, n)
+        H2 = pg.pamc_fields(h, R, n)
+        ref2 = _exact_fields(torch, Jd, spins)
+        np.testing.assert_array_equal(H2, ref2)
+        np.testing.assert_array_equal(E2, -(spins.astype(np.int64) * ref2).sum(axis=1) // 2)
+    finally:
+        pg.pamc_destroy(h)
+
+
+def test_set_population_sparse_and_ranges(pg):
+    inst = W.torus(12, 12, signed=True, seed=3)
+    h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+    try:
+        pg.pamc_init(h, R=6, steps=3, seed=2)
+        S = np.ones((6, inst.n), dtype=np.int8)
+        S[3, ::2] = -1
+        pg.pamc_set_population(h, S)
+        _, E, _, _ = pg.pamc_state(h, 6, inst.n)
+        J = -inst.w.astype(np.int32)
+        for r in range(6):
+            assert E[r] == oracle.energy_ising(inst.row_ptr, inst.col, J, S[r])
+        S[0, 0] = 0
+        with pytest.raises(pg.PamcError):
+            pg.pamc_set_population(h, S)
+        with pytest.raises(pg.PamcError):
+            pg.pamc_fields(h, 6, inst.n)
+    finally:
+        pg.pamc_destroy(h)
