@@ -88,6 +88,10 @@ struct pamc_handle_s {
     // dense instances
     int8_t *d_J = nullptr;               // n x n couplings (J = -w)
     int32_t *d_H = nullptr;              // [R][n] fields
+    uint8_t *d_Sb = nullptr;             // [64][n] e4m3 population for the tcgen05 recompute
+    bool dense_tc = false;               // recompute on tcgen05 (n a multiple of 16)
+    alignas(64) unsigned char tm_J[128];  // tensor maps of J and of d_Sb
+    alignas(64) unsigned char tm_S[128];
     int32_t *d_perm = nullptr, *d_sidx = nullptr, *d_G = nullptr, *d_ident = nullptr, *d_nonc = nullptr;
     uint32_t *d_pkey = nullptr;
     int8_t *d_T = nullptr, *d_T2 = nullptr;
@@ -239,6 +243,16 @@ SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level,
 }
 
 // ---------------------------------------------------------------- dense runs
+// H = J S for the population given by (src, parent, ncm_idx)
+cudaError_t dense_recompute(pamc_handle h, const int8_t *src, const int32_t *parent, const int32_t *ncm_idx,
+                            int restart_t) {
+    if (h->dense_tc)
+        return launch_dense_recompute_tc(h->n, h->p.R, h->tm_J, h->tm_S, src, parent, nullptr, ncm_idx, h->d_Sb,
+                                         h->d_H, h->d_ctl, h->stream, restart_t);
+    return launch_dense_recompute(h->n, h->p.R, h->d_J, src, parent, nullptr, ncm_idx, h->d_H, h->d_ctl,
+                                  h->stream, restart_t);
+}
+
 pamc_status init_dense(pamc_handle h, pamc_params p) {
     if (p.kind != 0) return fail(h, PAMC_ERR_ARG, "dense instances run the Ising (Max-Cut) kind only");
     if (p.R > 64) return fail(h, PAMC_ERR_RANGE, "dense instances support R <= 64");
@@ -280,6 +294,14 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
               alloc_n(h, h->d_flip, (size_t)3 * B, h->bufs) && alloc_n(h, h->d_snew, (size_t)3 * B, h->bufs) &&
               (h->d_bar = dev_alloc(h, 64, h->bufs)) != nullptr &&
               alloc_n(h, h->d_ident, R, h->bufs) && alloc_n(h, h->d_nonc, R, h->bufs);
+    const char *rc_env = getenv("PAMC_DENSE_RECOMPUTE");   // "mma": the mma.sync kernel
+    h->dense_tc = dense_tc_supported(n) && !(rc_env && strcmp(rc_env, "mma") == 0);
+    if (ok && h->dense_tc) {
+        ok = alloc_n(h, h->d_Sb, (size_t)64 * n, h->bufs);
+        if (ok && (dense_tc_map(h->tm_J, h->d_J, n, n, 256) != cudaSuccess ||
+                   dense_tc_map(h->tm_S, h->d_Sb, 64, n, 64) != cudaSuccess))
+            h->dense_tc = false;
+    }
     if (!ok) {
         release_run(h);
         return fail(h, PAMC_ERR_OOM, "device allocation of the dense population failed");
@@ -307,8 +329,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
     // initial population, its fields (tensor-core recompute) and energies
     if (e == cudaSuccess) e = launch_init_spins(0, 0, n, R, p.seed, 0, 0, h->d_ctl, h->d_spins[0], h->stream);
     if (e == cudaSuccess)
-        e = launch_dense_recompute(n, R, h->d_J, h->d_spins[0], h->d_ident, nullptr, h->d_nonc, h->d_H,
-                                   h->d_ctl, h->stream, -1);
+        e = dense_recompute(h, h->d_spins[0], h->d_ident, h->d_nonc, -1);
     if (e == cudaSuccess)
         e = launch_dense_energy(n, R, h->d_H, h->d_spins[0], h->d_E[0], h->d_ctl, h->stream, -1);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -336,8 +357,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
                             h->stream);
         if (e == cudaSuccess) e = launch_dense_tables(p.rule, h->dense_Hc, n, h->d_ctl, h->d_tab, h->stream);
         if (e == cudaSuccess)
-            e = launch_dense_recompute(n, R, h->d_J, src, h->d_parent, nullptr, h->d_ncm_idx, h->d_H, h->d_ctl,
-                                       h->stream, -1);
+            e = dense_recompute(h, src, h->d_parent, h->d_ncm_idx, -1);
         if (e == cudaSuccess)
             e = launch_dense_sweep(n, R, p.sweeps, p.rule, h->dense_Hc, (int32_t)t, p.seed, h->dense_nupd,
                                    h->dense_rows, h->dense_grid, h->d_J, h->d_perm, h->d_tab, src,
@@ -349,8 +369,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
             const int32_t tk = (int32_t)(t + 1);
             e = launch_init_spins(0, 0, n, R, p.seed, tk, 1, h->d_ctl, dst, h->stream);
             if (e == cudaSuccess)
-                e = launch_dense_recompute(n, R, h->d_J, dst, h->d_ident, nullptr, h->d_nonc, h->d_H,
-                                           h->d_ctl, h->stream, tk);
+                e = dense_recompute(h, dst, h->d_ident, h->d_nonc, tk);
             if (e == cudaSuccess) e = launch_dense_energy(n, R, h->d_H, dst, Ed, h->d_ctl, h->stream, tk);
             h->launches += 3;
         }
@@ -720,8 +739,7 @@ pamc_status pamc_set_population(pamc_handle h, const int8_t *spins) {
     cudaError_t e = cudaMemcpyAsync(h->d_spins[cur], spins, total, cudaMemcpyHostToDevice, h->stream);
     if (h->dense) {
         if (e == cudaSuccess)
-            e = launch_dense_recompute(n, R, h->d_J, h->d_spins[cur], h->d_ident, nullptr, h->d_nonc, h->d_H,
-                                       h->d_ctl, h->stream, -1);
+            e = dense_recompute(h, h->d_spins[cur], h->d_ident, h->d_nonc, -1);
         if (e == cudaSuccess)
             e = launch_dense_energy(n, R, h->d_H, h->d_spins[cur], h->d_E[cur], h->d_ctl, h->stream, -1);
     } else if (e == cudaSuccess) {

@@ -226,4 +226,14 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
                                unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_dense_to_e4m3(size_t total, int8_t *J, cudaStream_t st);
 
+// ---- dense recompute on tcgen05 (dense_tc.cu), n a multiple of 16
+bool dense_tc_supported(int32_t n);
+size_t dense_tc_smem();
+// map: 128-byte CUtensorMap storage (64-byte aligned)
+cudaError_t dense_tc_map(void *map, const void *base, int32_t rows, int32_t cols, int32_t box_rows);
+cudaError_t launch_dense_recompute_tc(int32_t n, int32_t R, const void *mapJ, const void *mapS,
+                                      const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
+                                      const int32_t *ncm_idx, uint8_t *Sb, int32_t *H, DevCtl *ctl,
+                                      cudaStream_t st, int restart_t);
+
 }  // namespace pamc
