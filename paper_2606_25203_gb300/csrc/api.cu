@@ -90,6 +90,7 @@ struct pamc_handle_s {
     int32_t *d_H = nullptr;              // [R][n] fields
     uint8_t *d_Sb = nullptr;             // [64][n] e4m3 population for the tcgen05 recompute
     bool dense_tc = false;               // recompute on tcgen05 (n a multiple of 16)
+    bool dense_tcu = false;              // field update of the sweep on tcgen05
     alignas(64) unsigned char tm_J[128];  // tensor maps of J and of d_Sb
     alignas(64) unsigned char tm_S[128];
     int32_t *d_perm = nullptr, *d_sidx = nullptr, *d_G = nullptr, *d_ident = nullptr, *d_nonc = nullptr;
@@ -268,8 +269,12 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
     const int grid = sms;
     const int nupd = grid - chain;
     if (nupd < 1) return fail(h, PAMC_ERR_RANGE, "too few SMs for the dense sweep");
-    const int32_t rows = (n + nupd - 1) / nupd;
-    const size_t smem = dense_sweep_smem(n, R, rows);
+    // field update on the tensor cores (fields in tensor memory) when n allows TMA-style rows
+    const char *sw_env = getenv("PAMC_DENSE_UPDATE");   // "cuda": the CUDA-core update
+    const bool tcu = dense_tc_supported(n) && !(sw_env && strcmp(sw_env, "cuda") == 0);
+    int32_t rows = (n + nupd - 1) / nupd;
+    if (tcu) rows = (rows + 31) & ~31;
+    const size_t smem = dense_sweep_smem(n, R, rows, tcu);
     if (rows > dense_sweep_threads() || smem > 227 * 1024)
         return fail(h, PAMC_ERR_RANGE, "dense instance too large for the on-chip field slices");
     release_run(h);
@@ -277,6 +282,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
     h->dense_grid = grid;
     h->dense_nupd = nupd;
     h->dense_rows = rows;
+    h->dense_tcu = tcu;
     h->dense_Hc = std::min<int32_t>(n, 32767);
     const int B = dense_block_positions();
     const size_t tabn = (size_t)2 * h->dense_Hc + 1;
@@ -362,7 +368,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
             e = launch_dense_sweep(n, R, p.sweeps, p.rule, h->dense_Hc, (int32_t)t, p.seed, h->dense_nupd,
                                    h->dense_rows, h->dense_grid, h->d_J, h->d_perm, h->d_tab, src,
                                    h->d_parent, nullptr, h->d_ncm_idx, h->d_H, dst, Ed, h->d_G, h->d_T,
-                                   h->d_T2, h->d_flip, h->d_snew, h->d_bar, h->d_ctl, h->stream);
+                                   h->d_T2, h->d_flip, h->d_snew, h->d_bar, h->d_ctl, h->stream, h->dense_tcu);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 7;
         if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {

@@ -17,6 +17,7 @@
 
 #include "pamc_device.cuh"
 #include "pamc_internal.h"
+#include "tc_sm100.cuh"
 
 namespace pamc {
 
@@ -266,6 +267,30 @@ constexpr int kC = kB / 32;          // positions per lane in a chain warp
 constexpr int kWin = 4096;           // threshold entries kept in shared memory
 constexpr long long kBarCycles = 4000000000ll;   // ~2 s: a barrier wait gives up after this
 
+// tensor-core field update (TCU): the update CTA's fields live in tensor
+// memory, one 128-row tile of 64 replica columns per 128 rows; a block's flips
+// are applied as H += J[flipped, slice]^T D with D = +-2 (the new spin) or 0
+constexpr int kTuTileBytes = 128 * 128;       // one K slice of one A tile
+constexpr int kTuMaxTiles = 6;                // <= 768 rows per update CTA
+constexpr int kTuBSlice = 64 * 128;           // one K slice of B (64 replicas)
+constexpr uint32_t kTuCols = 512;             // tensor memory columns allocated
+constexpr uint32_t kTuIdesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+// A rows of a 32-row block are permuted so that the transposed 32-bit shared
+// stores of a warp hit 32 distinct banks: A row 32b + 8r + g <-> slice row
+// 32b + 4g + r (g < 8, r < 4)
+__device__ __forceinline__ int32_t tu_row_of(int32_t arow) {
+    return (arow & ~31) + ((arow & 7) << 2) + ((arow >> 3) & 3);
+}
+__device__ __forceinline__ int32_t tu_arow_of(int32_t row) {
+    return (row & ~31) + ((row & 3) << 3) + ((row >> 2) & 7);
+}
+// byte offset of (row a of an A tile or replica row of B, k) in a 128-byte-
+// swizzled K-major slice
+__device__ __forceinline__ uint32_t tu_sw_off(int32_t row, int32_t kk) {
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((kk >> 4) ^ row) & 7) << 4) + (kk & 15));
+}
+
 struct GridBar {
     unsigned int count;
     unsigned int gen;
@@ -316,6 +341,7 @@ struct DenseSweepArgs {
     int32_t n, R, S, rule, Hc;
     int32_t n_upd;            // CTAs that own H rows (the others run chains)
     int32_t rows_per;         // rows per update CTA
+    int32_t ntiles;           // tensor-core update: 128-row tiles per update CTA
     int32_t t;
     PhiloxKeys K;
     const uint8_t *J;         // e4m3 couplings
@@ -347,10 +373,14 @@ __device__ __forceinline__ const int8_t *pop_row(const DenseSweepArgs &a, int r)
 // block q-1 to their rows; the fields a chain starts from were published in
 // phase q-1 (all blocks up to q-2 applied) and the chain adds block q-1's
 // flips itself from the tile J[P_{q-1}][P_q].  One grid barrier per block.
+template <bool TCU>
 __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a) {
     extern __shared__ __align__(16) uint8_t sm[];
     __shared__ int s_ok, s_nl;
     __shared__ int32_t s_wlo, s_wn;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int32_t s_nown;
     if (a.ctl->done) return;
     const int32_t n = a.n, R = a.R;
     const unsigned int nblocks = gridDim.x;
@@ -364,18 +394,25 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
 
     // ---------------- update CTA shared memory
     const int32_t ua = upd ? blockIdx.x * a.rows_per : 0;
-    const int32_t ub = upd ? min(n, ua + a.rows_per) : 0;
+    const int32_t ub = upd ? max(ua, min(n, ua + a.rows_per)) : 0;
     const int32_t rows = ub - ua;
     const int32_t rw = (a.rows_per + 31) / 32;
+    // TCU: [A: 2 K slices x ntiles tiles][B: 2 K slices] 1024-aligned, then the rest
+    uint8_t *tu_base = sm + ((1024u - (smem_u32(sm) & 1023u)) & 1023u);
+    uint8_t *tuA = tu_base;
+    uint8_t *tuB = tuA + (size_t)2 * a.ntiles * kTuTileBytes;
+    // 16-byte aligned, as dense_sweep_smem counts it (the 64-bit masks below need it)
+    uint8_t *after = TCU ? tuB + 2 * kTuBSlice : sm + (((size_t)R * a.rows_per * 4 + 15) & ~(size_t)15);
     int32_t *Hs = reinterpret_cast<int32_t *>(sm);
-    uint32_t *ubits = reinterpret_cast<uint32_t *>(sm + (size_t)R * a.rows_per * 4);
+    uint32_t *ubits = reinterpret_cast<uint32_t *>(after);
     unsigned long long *fprev = reinterpret_cast<unsigned long long *>(
-        sm + (((size_t)R * a.rows_per * 4 + (size_t)R * rw * 4 + 15) & ~(size_t)15));
+        after + ((((size_t)R * rw * 4) + 15) & ~(size_t)15));
     unsigned long long *sprev = fprev + kB;
     int32_t *Pprev = reinterpret_cast<int32_t *>(sprev + kB);
     int32_t *Pcur = Pprev + kB;
     int32_t *Pnext = Pcur + kB;
     int32_t *flist = Pnext + kB;
+    int32_t *ownl = flist + kB;                        // TCU: block positions owned by this CTA
     // ---------------- chain CTA shared memory
     const int cg = blockIdx.x - a.n_upd;               // chain group (4 replicas)
     const int32_t nw = (n + 31) / 32;
@@ -391,18 +428,57 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
 
     // update CTAs: publish the fields of block qn's positions they own, and
     // gather their share of the tiles J[P_qn][P_qn] and J[P_{qn-1}][P_qn]
-    auto publish = [&](int32_t qn) {
+    // update CTAs publish, for block qn: the fields of the positions they own
+    // (publish_G) and their share of the tiles J[P_qn][P_qn] and
+    // J[P_{qn-1}][P_qn] (publish_tiles); publish_lists stages the position lists
+    auto publish_lists = [&](int32_t qn) {
         const int32_t *P = block_pos(qn);
         const int32_t cnt = block_cnt(qn);
+        if (threadIdx.x == 0) s_nown = 0;
         if ((int)threadIdx.x < cnt) Pnext[threadIdx.x] = P[threadIdx.x];
         if (qn > 0 && (int)threadIdx.x < block_cnt(qn - 1)) Pcur[threadIdx.x] = block_pos(qn - 1)[threadIdx.x];
         __syncthreads();
-        int32_t *Gq = a.G + (size_t)(qn & 1) * kB * 64;
-        for (int32_t x = threadIdx.x; x < cnt * R; x += blockDim.x) {
-            const int32_t m = x / R, r = x % R;
-            const int32_t p = Pnext[m];
-            if (p >= ua && p < ub) Gq[m * 64 + r] = Hs[r * a.rows_per + (p - ua)];
+        if constexpr (TCU) {
+            if ((int)threadIdx.x < cnt) {
+                const int32_t p = Pnext[threadIdx.x];
+                if (p >= ua && p < ub) ownl[atomicAdd(&s_nown, 1)] = (int32_t)threadIdx.x;
+            }
+            __syncthreads();
         }
+    };
+    auto publish_G = [&](int32_t qn) {
+        const int32_t cnt = block_cnt(qn);
+        int32_t *Gq = a.G + (size_t)(qn & 1) * kB * 64;
+        if constexpr (TCU) {
+            // warp w < 4 reads the owned positions whose tensor-memory lane is in its quarter
+            if (warp < 4) {
+                const int32_t nown = s_nown;
+                for (int32_t o = 0; o < nown; ++o) {
+                    const int32_t m = ownl[o];
+                    const int32_t ar = tu_arow_of(Pnext[m] - ua);
+                    if (((ar & 127) >> 5) != warp) continue;
+                    const uint32_t tbase = s_tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((ar >> 7) * 64);
+#pragma unroll
+                    for (int c0 = 0; c0 < 64; c0 += 16) {
+                        uint32_t v[16];
+                        tc_ld16(tbase + (uint32_t)c0, v);
+                        if (lane == (ar & 31))
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (c0 + j < R) Gq[m * 64 + c0 + j] = __float2int_rn(__uint_as_float(v[j]));
+                    }
+                }
+            }
+        } else {
+            for (int32_t x = threadIdx.x; x < cnt * R; x += blockDim.x) {
+                const int32_t m = x / R, r = x % R;
+                const int32_t p = Pnext[m];
+                if (p >= ua && p < ub) Gq[m * 64 + r] = Hs[r * a.rows_per + (p - ua)];
+            }
+        }
+    };
+    auto publish_tiles = [&](int32_t qn) {
+        const int32_t cnt = block_cnt(qn);
         const int32_t per = (2 * kB * kB + a.n_upd - 1) / a.n_upd;
         const int32_t e0 = blockIdx.x * per, e1 = min(2 * kB * kB, e0 + per);
         const int32_t cntp = qn > 0 ? block_cnt(qn - 1) : 0;
@@ -424,9 +500,39 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
 
     // ---------------- prologue
     if (upd) {
-        for (int32_t x = threadIdx.x; x < R * rows; x += blockDim.x) {
-            const int r = x / rows, j = x % rows;
-            Hs[r * a.rows_per + j] = a.H[(size_t)r * n + ua + j];
+        if constexpr (TCU) {
+            if (warp == 0) tc_alloc(&s_tmem, kTuCols);
+            if (threadIdx.x == 0) {
+                mbar_init(&s_mbar, 1);
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            }
+            // A and B start as zeros (finite operands wherever a K step reads past the flips)
+            for (int32_t x = threadIdx.x; x < (2 * a.ntiles * kTuTileBytes + 2 * kTuBSlice) / 16; x += blockDim.x)
+                reinterpret_cast<uint4 *>(tuA)[x] = make_uint4(0u, 0u, 0u, 0u);
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            // fields into tensor memory: warp w covers lane quarter w % 4 of some (tile, 16 columns)
+            const int quarter = warp & 3;
+            for (int32_t pr = warp >> 2; pr < a.ntiles * 4; pr += (kSwThreads / 32) / 4) {
+                const int tile = pr >> 2, c0 = (pr & 3) * 16;
+                const int32_t ar = tile * 128 + quarter * 32 + lane;
+                const int32_t j = tu_row_of(ar);
+                uint32_t v[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int r = c0 + c;
+                    const int32_t hv = (j < rows && r < R) ? a.H[(size_t)r * n + ua + j] : 0;
+                    v[c] = __float_as_uint((float)hv);
+                }
+                tc_st16(s_tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * 64 + c0), v);
+            }
+            tc_wait_st();
+        } else {
+            for (int32_t x = threadIdx.x; x < R * rows; x += blockDim.x) {
+                const int r = x / rows, j = x % rows;
+                Hs[r * a.rows_per + j] = a.H[(size_t)r * n + ua + j];
+            }
         }
         for (int32_t x = threadIdx.x; x < R * rw; x += blockDim.x) {
             const int r = x / rw, w = x % rw;
@@ -438,8 +544,14 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             }
             ubits[r * rw + w] = bits;
         }
+        if constexpr (TCU) tc_fence_before();
         __syncthreads();
-        if (total > 0) publish(0);
+        if constexpr (TCU) tc_fence_after();
+        if (total > 0) {
+            publish_lists(0);
+            publish_G(0);
+            publish_tiles(0);
+        }
     } else {
         for (int32_t x = threadIdx.x; x < 4 * nw; x += blockDim.x) {
             const int qq = x / nw, w = x % nw;
@@ -494,10 +606,11 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         if (s_wn <= kWin)
             for (int32_t i = threadIdx.x; i < s_wn; i += blockDim.x) win[i] = a.tab[s_wlo + i];
     }
-    if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) return;
-
-    for (int32_t q = 0; q <= total; ++q) {
+    uint32_t mphase = 0;     // TCU: completed phases of s_mbar
+    bool alive = grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok);
+    for (int32_t q = 0; alive && q <= total; ++q) {
         if (upd) {
+            bool issued = false;   // TCU: MMAs of this phase in flight
             // ---- apply block q-1 to the owned rows
             if (q > 0) {
                 const int32_t qp = q - 1;
@@ -527,6 +640,73 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 }
                 __syncthreads();
                 const int32_t nl = s_nl;
+                if constexpr (TCU) {
+                    if (nl > 0) {
+                        // A: the flipped positions' coupling rows over this slice,
+                        // transposed 4x4 bytes at a time into K-major tiles; k = list index
+                        const int32_t n16 = (nl + 15) >> 4, nb32 = (a.ntiles * 128) >> 5;
+                        const int pg = lane >> 3, rg = lane & 7;
+                        for (int32_t task = warp; task < n16 * nb32; task += kSwThreads / 32) {
+                            const int32_t c16 = task / nb32, rb = task % nb32;
+                            const int32_t j0 = rb * 32 + rg * 4;          // slice rows j0 .. j0+3
+                            uint32_t w[4];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const int32_t i = c16 * 16 + pg * 4 + c;
+                                w[c] = 0u;
+                                if (i < nl && j0 < rows)
+                                    w[c] = *reinterpret_cast<const uint32_t *>(a.J + (size_t)Pprev[flist[i]] * n + ua + j0);
+                            }
+                            const uint32_t lo01 = __byte_perm(w[0], w[1], 0x5140), hi01 = __byte_perm(w[0], w[1], 0x7362);
+                            const uint32_t lo23 = __byte_perm(w[2], w[3], 0x5140), hi23 = __byte_perm(w[2], w[3], 0x7362);
+                            const uint32_t o[4] = {__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632),
+                                                   __byte_perm(hi01, hi23, 0x5410), __byte_perm(hi01, hi23, 0x7632)};
+                            const int32_t k = c16 * 16 + pg * 4;
+                            uint8_t *Ak = tuA + (size_t)(k >> 7) * a.ntiles * kTuTileBytes;
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const int32_t ar = rb * 32 + r * 8 + rg;   // = tu_arow_of(j0 + r)
+                                *reinterpret_cast<uint32_t *>(Ak + (size_t)(ar >> 7) * kTuTileBytes +
+                                                              tu_sw_off(ar & 127, k & 127)) = o[r];
+                            }
+                        }
+                        // B = D^T: replica r, k -> +2 (new spin +1) / -2 / 0 as e4m3
+                        const int32_t nk4 = ((nl + 31) >> 5) * 8;        // 4-byte words per replica row
+                        for (int32_t x = threadIdx.x; x < 64 * nk4; x += blockDim.x) {
+                            const int r = x / nk4;
+                            const int32_t k0 = (x % nk4) * 4;
+                            uint32_t wv = 0u;
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const int32_t i = k0 + c;
+                                if (i < nl && r < R) {
+                                    const int32_t m = flist[i];
+                                    if ((fprev[m] >> r) & 1ull)
+                                        wv |= (((sprev[m] >> r) & 1ull) ? 0x40u : 0xC0u) << (8 * c);
+                                }
+                            }
+                            *reinterpret_cast<uint32_t *>(tuB + (size_t)(k0 >> 7) * kTuBSlice + tu_sw_off(r, k0 & 127)) = wv;
+                        }
+                        fence_async_smem();
+                        __syncthreads();
+                        if (threadIdx.x == 0) {
+                            tc_fence_after();
+                            const int32_t ks = (nl + 31) >> 5;
+                            for (int tl = 0; tl < a.ntiles; ++tl)
+                                for (int32_t kq = 0; kq < ks; ++kq) {
+                                    const uint32_t aaddr = smem_u32(tuA + (size_t)(kq >> 2) * a.ntiles * kTuTileBytes +
+                                                                    (size_t)tl * kTuTileBytes);
+                                    const uint32_t baddr = smem_u32(tuB + (size_t)(kq >> 2) * kTuBSlice);
+                                    tc_mma(s_tmem + (uint32_t)(tl * 64), sw128_desc(aaddr) + (uint64_t)(2 * (kq & 3)),
+                                           sw128_desc(baddr) + (uint64_t)(2 * (kq & 3)), kTuIdesc, 1u);
+                                }
+                            tc_commit(&s_mbar);
+                        }
+                        __syncwarp();
+                        issued = true;   // waited for after the independent tile gather below
+                    }
+                    __syncthreads();
+                } else {
                 const int32_t j = threadIdx.x;
                 const uint8_t *Jc = a.J + ua + j;
                 for (int32_t base = 0; base < nl; base += 16) {
@@ -550,9 +730,28 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                     }
                 }
                 __syncthreads();
+                }
             }
-            // ---- publish block q+1
-            if (q + 1 < total) publish(q + 1);
+            // ---- publish block q+1 (TCU: the tiles while the MMAs run, the fields after them)
+            if constexpr (TCU) {
+                if (q + 1 < total) {
+                    publish_lists(q + 1);
+                    publish_tiles(q + 1);
+                }
+                if (issued) {
+                    if (!mbar_wait(&s_mbar, mphase & 1u)) {
+                        atomicCAS(&a.ctl->err, 0, (int)PAMC_ERR_TIMEOUT);
+                        mbar_wait(&s_mbar, mphase & 1u);
+                    }
+                    ++mphase;
+                    tc_fence_after();
+                }
+                if (q + 1 < total) publish_G(q + 1);
+            } else if (q + 1 < total) {
+                publish_lists(q + 1);
+                publish_G(q + 1);
+                publish_tiles(q + 1);
+            }
         } else if (q < total) {
             const int32_t *P = block_pos(q);
             const int32_t cnt = block_cnt(q);
@@ -696,11 +895,41 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 }
             }
         }
-        if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) return;
+        if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) { alive = false; break; }
     }
 
     // ---------------- energies E_r = -1/2 sum_j s_j h_j, fields and spins back to HBM
-    if (upd) {
+    if (upd && TCU) {
+        if (alive) {
+            const int quarter = warp & 3;
+            for (int32_t pr = warp >> 2; pr < a.ntiles * 4; pr += (kSwThreads / 32) / 4) {
+                const int tile = pr >> 2, c0 = (pr & 3) * 16;
+                const int32_t ar = tile * 128 + quarter * 32 + lane;
+                const int32_t j = tu_row_of(ar);
+                uint32_t v[16];
+                tc_ld16(s_tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(tile * 64 + c0), v);
+                const int32_t s01 = j < rows ? 1 : 0;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int r = c0 + c;
+                    const int32_t hv = __float2int_rn(__uint_as_float(v[c]));
+                    long long accv = 0;
+                    if (s01 && r < R) {
+                        a.H[(size_t)r * n + ua + j] = hv;
+                        const int32_t sgn = ((ubits[r * rw + (j >> 5)] >> (j & 31)) & 1u) ? 1 : -1;
+                        accv = (long long)sgn * hv;
+                    }
+                    for (int o = 16; o > 0; o >>= 1) accv += __shfl_down_sync(0xffffffffu, accv, o);
+                    if (lane == 0 && r < R && accv != 0) atomicAdd((unsigned long long *)&a.E[r], (unsigned long long)accv);
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0) tc_dealloc(s_tmem, kTuCols);
+    } else if (!alive) {
+        return;
+    } else if (upd) {
         for (int32_t x = threadIdx.x; x < R * rows; x += blockDim.x) {
             const int r = x / rows, j = x % rows;
             a.H[(size_t)r * n + ua + j] = Hs[r * a.rows_per + j];
@@ -856,9 +1085,12 @@ cudaError_t launch_dense_negate_sum(size_t total, int8_t *J, unsigned long long 
 int dense_block_positions() { return kB; }
 
 // Shared memory of the sweep kernel for a given split.
-size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per) {
-    const size_t upd = (((size_t)R * rows_per * 4 + (size_t)R * ((rows_per + 31) / 32) * 4 + 15) & ~(size_t)15) +
-                       (size_t)kB * (8 + 8 + 4 + 4 + 4 + 4);
+size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu) {
+    const size_t rest = ((((size_t)R * ((rows_per + 31) / 32) * 4) + 15) & ~(size_t)15) +
+                        (size_t)kB * (8 + 8 + 4 + 4 + 4 + 4 + 4);
+    const size_t ntiles = ((size_t)rows_per + 127) / 128;
+    const size_t upd = tcu ? 1024 + 2 * ntiles * kTuTileBytes + 2 * kTuBSlice + rest
+                           : (((size_t)R * rows_per * 4 + 15) & ~(size_t)15) + rest;
     const size_t nw = (size_t)((n + 31) / 32);
     const size_t chn = 2 * (size_t)kB * kB + ((4 * nw + 3) & ~(size_t)3) * 4 + (size_t)kWin * 8 +
                        (size_t)kB * (4 * 4 + 4 * 4 + 4 + 8 + 8);
@@ -871,21 +1103,23 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
                                const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int32_t *H, int8_t *dst, int64_t *E,
                                int32_t *G, int8_t *T, int8_t *T2, unsigned long long *flip,
-                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st) {
+                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st, bool tcu) {
     DenseSweepArgs a;
     a.n = n; a.R = R; a.S = S; a.rule = rule; a.Hc = Hc; a.n_upd = n_upd; a.rows_per = rows_per;
+    a.ntiles = (rows_per + 127) / 128;
     a.t = t; a.K = make_philox_keys(seed); a.J = reinterpret_cast<const uint8_t *>(J); a.perm = perm;
     a.tab = tab; a.src = src; a.parent = parent; a.ncm_buf = ncm_buf; a.ncm_idx = ncm_idx; a.H = H;
     a.dst = dst; a.E = E; a.G = G; a.T = T; a.T2 = T2; a.flip = flip; a.snew = snew;
     a.bar = reinterpret_cast<GridBar *>(bar); a.ctl = ctl;
-    const size_t smem = dense_sweep_smem(n, R, rows_per);
-    cudaError_t e = allow_dynamic_smem(k_dense_sweep, smem);
+    if (tcu && (a.ntiles > kTuMaxTiles || n % 16 != 0 || rows_per % 32 != 0)) return cudaErrorInvalidValue;
+    const size_t smem = dense_sweep_smem(n, R, rows_per, tcu);
+    const void *fn = tcu ? (const void *)k_dense_sweep<true> : (const void *)k_dense_sweep<false>;
+    cudaError_t e = tcu ? allow_dynamic_smem(k_dense_sweep<true>, smem) : allow_dynamic_smem(k_dense_sweep<false>, smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(bar, 0, sizeof(GridBar), st);
     if (e != cudaSuccess) return e;
     void *args[] = {&a};
-    e = cudaLaunchCooperativeKernel((const void *)k_dense_sweep, dim3(grid), dim3(kSwThreads), args,
-                                    smem, st);
+    e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kSwThreads), args, smem, st);
     if (e != cudaSuccess) return e;
     k_dense_energy_finish<<<1, 64, 0, st>>>(R, E, ctl);
     return cudaGetLastError();

@@ -216,14 +216,14 @@ cudaError_t launch_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint64_
                               int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st);
 int dense_block_positions();
 int dense_sweep_threads();
-size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per);
+size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu);
 cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, int32_t Hc, int32_t t,
                                uint64_t seed, int32_t n_upd, int32_t rows_per, int32_t grid,
                                const int8_t *J, const int32_t *perm, const uint64_t *tab,
                                const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int32_t *H, int8_t *dst, int64_t *E,
                                int32_t *G, int8_t *T, int8_t *T2, unsigned long long *flip,
-                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st);
+                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st, bool tcu);
 cudaError_t launch_dense_to_e4m3(size_t total, int8_t *J, cudaStream_t st);
 
 // ---- dense recompute on tcgen05 (dense_tc.cu), n a multiple of 16
