@@ -94,6 +94,7 @@ struct pamc_handle_s {
     alignas(64) unsigned char tm_J[128];  // tensor maps of J and of d_Sb
     alignas(64) unsigned char tm_S[128];
     int32_t *d_perm = nullptr, *d_sidx = nullptr, *d_G = nullptr, *d_ident = nullptr, *d_nonc = nullptr;
+    int32_t *d_boff = nullptr;           // bucket offsets of the order sort
     uint32_t *d_pkey = nullptr;
     int8_t *d_T = nullptr, *d_T2 = nullptr;
     unsigned long long *d_flip = nullptr, *d_snew = nullptr;
@@ -299,7 +300,8 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
               alloc_n(h, h->d_T, (size_t)2 * B * B, h->bufs) && alloc_n(h, h->d_T2, (size_t)2 * B * B, h->bufs) &&
               alloc_n(h, h->d_flip, (size_t)3 * B, h->bufs) && alloc_n(h, h->d_snew, (size_t)3 * B, h->bufs) &&
               (h->d_bar = dev_alloc(h, 64, h->bufs)) != nullptr &&
-              alloc_n(h, h->d_ident, R, h->bufs) && alloc_n(h, h->d_nonc, R, h->bufs);
+              alloc_n(h, h->d_ident, R, h->bufs) && alloc_n(h, h->d_nonc, R, h->bufs) &&
+              alloc_n(h, h->d_boff, dense_perm_offsets(S), h->bufs);
     const char *rc_env = getenv("PAMC_DENSE_RECOMPUTE");   // "mma": the mma.sync kernel
     h->dense_tc = dense_tc_supported(n) && !(rc_env && strcmp(rc_env, "mma") == 0);
     if (ok && h->dense_tc) {
@@ -357,7 +359,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
         int8_t *src = h->d_spins[t & 1], *dst = h->d_spins[(t + 1) & 1];
         int64_t *Es = h->d_E[t & 1], *Ed = h->d_E[(t + 1) & 1];
         cudaError_t e = launch_dense_perm(n, p.seed, (int32_t)t, p.sweeps, h->d_perm, h->d_pkey, h->d_sidx,
-                                          h->d_ctl, h->stream);
+                                          h->d_boff, h->d_ctl, h->stream);
         if (e == cudaSuccess)
             e = launch_prep(pp, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
                             h->stream);

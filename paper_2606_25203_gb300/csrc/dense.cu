@@ -27,21 +27,22 @@ namespace {
 constexpr int kPermThreads = 1024;
 constexpr int kPermBucketBits = 11;   // 2048 buckets
 
-// One CTA per sweep: keys -> bucket by the top bits (counting sort, order
-// within a bucket arbitrary) -> each bucket sorted by (key, index) by one
-// thread.  The result is the unique order by (key, index).
+// The order of each sweep by (Philox key, index) in two launches.  Bucketing
+// (one CTA per sweep): keys, a histogram over the top 11 key bits, a
+// block-wide exclusive scan and a scatter into buckets (order within a bucket
+// arbitrary).  Sorting (32 buckets per CTA): each bucket is ranked in shared
+// memory by (key, index), which is unique, so the result is the exact order.
 __global__ void __launch_bounds__(kPermThreads)
-k_dense_perm(int32_t n, uint32_t key0, uint32_t key1, int32_t t, int32_t S,
-             int32_t *__restrict__ perm, uint32_t *__restrict__ skey, int32_t *__restrict__ sidx,
-             const DevCtl *__restrict__ ctl) {
+k_dense_perm_bucket(int32_t n, uint32_t key0, uint32_t key1, int32_t t, uint32_t *__restrict__ skey,
+                    int32_t *__restrict__ sidx, int32_t *__restrict__ boff, const DevCtl *__restrict__ ctl) {
     constexpr int NB = 1 << kPermBucketBits;
     __shared__ int32_t cnt[NB];
-    __shared__ int32_t off[NB];
+    __shared__ int32_t wsum[kPermThreads / 32];
     if (ctl->done) return;
     const int32_t sw = blockIdx.x;
-    int32_t *out = perm + (size_t)sw * n;
     uint32_t *kk = skey + (size_t)sw * n;
     int32_t *ii = sidx + (size_t)sw * n;
+    int32_t *bo = boff + (size_t)sw * (NB + 1);
     for (int b = threadIdx.x; b < NB; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
@@ -49,12 +50,37 @@ k_dense_perm(int32_t n, uint32_t key0, uint32_t key1, int32_t t, int32_t S,
         atomicAdd(&cnt[key >> (32 - kPermBucketBits)], 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t a = 0;
-        for (int b = 0; b < NB; ++b) { off[b] = a; a += cnt[b]; }
+    // exclusive scan of the NB counts: NB / blockDim consecutive buckets per thread
+    constexpr int per = NB / kPermThreads;
+    int32_t local[per], tot = 0;
+#pragma unroll
+    for (int i = 0; i < per; ++i) { local[i] = cnt[threadIdx.x * per + i]; tot += local[i]; }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t x = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t v = lane < kPermThreads / 32 ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < kPermThreads / 32) wsum[lane] = v;
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < NB; b += blockDim.x) cnt[b] = off[b];
+    int32_t run = (x - tot) + (wid > 0 ? wsum[wid - 1] : 0);
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+        const int b = threadIdx.x * per + i;
+        bo[b] = run;
+        cnt[b] = run;
+        run += local[i];
+    }
+    if (threadIdx.x == 0) bo[NB] = n;
     __syncthreads();
     for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
         const uint32_t key = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, kTagPerm << 24, key0, key1).x;
@@ -62,22 +88,47 @@ k_dense_perm(int32_t n, uint32_t key0, uint32_t key1, int32_t t, int32_t S,
         kk[p] = key;
         ii[p] = k;
     }
+}
+
+constexpr int kSortBuckets = 32;        // buckets per sorting CTA
+constexpr int kSortCap = 6144;          // items staged in shared memory (larger ranges sort in place)
+
+__device__ __forceinline__ bool perm_before(uint32_t ka, int32_t ia, uint32_t kb, int32_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+__global__ void __launch_bounds__(256)
+k_dense_perm_sort(int32_t n, const uint32_t *__restrict__ skey, const int32_t *__restrict__ sidx,
+                  const int32_t *__restrict__ boff, int32_t *__restrict__ perm, const DevCtl *__restrict__ ctl) {
+    constexpr int NB = 1 << kPermBucketBits;
+    __shared__ uint32_t ks[kSortCap];
+    __shared__ int32_t is[kSortCap];
+    if (ctl->done) return;
+    const int32_t sw = blockIdx.y;
+    const uint32_t *kk = skey + (size_t)sw * n;
+    const int32_t *ii = sidx + (size_t)sw * n;
+    const int32_t *bo = boff + (size_t)sw * (NB + 1);
+    int32_t *out = perm + (size_t)sw * n;
+    const int b0 = blockIdx.x * kSortBuckets;
+    const int32_t lo = bo[b0], hi = bo[b0 + kSortBuckets];
+    const bool staged = hi - lo <= kSortCap;
+    if (staged)
+        for (int32_t x = lo + threadIdx.x; x < hi; x += blockDim.x) { ks[x - lo] = kk[x]; is[x - lo] = ii[x]; }
     __syncthreads();
-    for (int b = threadIdx.x; b < NB; b += blockDim.x) {
-        const int32_t lo = off[b], hi = cnt[b];
-        for (int32_t x = lo + 1; x < hi; ++x) {   // insertion sort by (key, index)
-            const uint32_t ck = kk[x];
-            const int32_t ci = ii[x];
-            int32_t y = x - 1;
-            while (y >= lo && (kk[y] > ck || (kk[y] == ck && ii[y] > ci))) {
-                kk[y + 1] = kk[y];
-                ii[y + 1] = ii[y];
-                --y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = b0 + warp; b < b0 + kSortBuckets; b += blockDim.x / 32) {
+        const int32_t blo = bo[b], bhi = bo[b + 1];
+        for (int32_t xi = blo + lane; xi < bhi; xi += 32) {
+            const uint32_t kx = staged ? ks[xi - lo] : kk[xi];
+            const int32_t ix = staged ? is[xi - lo] : ii[xi];
+            int32_t rank = 0;
+            for (int32_t y = blo; y < bhi; ++y) {
+                const uint32_t ky = staged ? ks[y - lo] : kk[y];
+                const int32_t iy = staged ? is[y - lo] : ii[y];
+                rank += perm_before(ky, iy, kx, ix) ? 1 : 0;
             }
-            kk[y + 1] = ck;
-            ii[y + 1] = ci;
+            out[blo + rank] = ix;
         }
-        for (int32_t x = lo; x < hi; ++x) out[x] = ii[x];
     }
 }
 
@@ -1035,12 +1086,16 @@ cudaError_t launch_dense_validate(int32_t n, const int8_t *J, int *err, cudaStre
 }
 
 cudaError_t launch_dense_perm(int32_t n, uint64_t seed, int32_t t, int32_t S, int32_t *perm,
-                              uint32_t *skey, int32_t *sidx, const DevCtl *ctl, cudaStream_t st) {
+                              uint32_t *skey, int32_t *sidx, int32_t *boff, const DevCtl *ctl, cudaStream_t st) {
     if (S <= 0) return cudaSuccess;
-    k_dense_perm<<<S, kPermThreads, 0, st>>>(n, (uint32_t)seed, (uint32_t)(seed >> 32), t, S, perm,
-                                            skey, sidx, ctl);
+    k_dense_perm_bucket<<<S, kPermThreads, 0, st>>>(n, (uint32_t)seed, (uint32_t)(seed >> 32), t, skey, sidx,
+                                                   boff, ctl);
+    k_dense_perm_sort<<<dim3((1 << kPermBucketBits) / kSortBuckets, S), 256, 0, st>>>(n, skey, sidx, boff, perm,
+                                                                                       ctl);
     return cudaGetLastError();
 }
+
+size_t dense_perm_offsets(int32_t S) { return (size_t)S * ((1 << kPermBucketBits) + 1); }
 
 cudaError_t launch_dense_tables(int rule, int32_t Hc, int32_t n, DevCtl *ctl, uint64_t *tab,
                                 cudaStream_t st) {

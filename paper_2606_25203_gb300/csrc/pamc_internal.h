@@ -202,7 +202,8 @@ cudaError_t launch_hamming(int32_t n, int32_t R, const int8_t *spins, uint32_t *
 cudaError_t launch_dense_validate(int32_t n, const int8_t *J, int *err, cudaStream_t st);
 cudaError_t launch_dense_negate_sum(size_t total, int8_t *J, unsigned long long *wsum, cudaStream_t st);
 cudaError_t launch_dense_perm(int32_t n, uint64_t seed, int32_t t, int32_t S, int32_t *perm,
-                              uint32_t *skey, int32_t *sidx, const DevCtl *ctl, cudaStream_t st);
+                              uint32_t *skey, int32_t *sidx, int32_t *boff, const DevCtl *ctl, cudaStream_t st);
+size_t dense_perm_offsets(int32_t S);   // int32 bucket offsets launch_dense_perm needs
 cudaError_t launch_dense_tables(int rule, int32_t Hc, int32_t n, DevCtl *ctl, uint64_t *tab,
                                 cudaStream_t st);
 size_t dense_recompute_smem();
