@@ -353,30 +353,26 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
     return v;
 }
 
-// Grid-wide barrier for a cooperative launch.  The wait is bounded by the
-// clock: after kBarCycles it sets PAMC_ERR_TIMEOUT and the kernel returns.
+// Grid-wide barrier for a cooperative launch: one monotonic arrival counter;
+// phase g completes when it reaches (g + 1) * nblocks.  The wait is bounded by
+// the clock: after kBarCycles it sets PAMC_ERR_TIMEOUT and the kernel returns.
 __device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &gen,
                              DevCtl *ctl, int *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            const long long start = clock64();
-            int spins = 0;
-            while (ld_acquire_u32(&bar->gen) == gen) {
-                if (++spins > 64) {
-                    __nanosleep(32);
-                    if (clock64() - start > kBarCycles) {
-                        atomicCAS(&ctl->err, 0, (int)PAMC_ERR_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+        const unsigned int target = (gen + 1u) * nblocks;
+        const long long start = clock64();
+        int spins = 0;
+        while ((int)(ld_acquire_u32(&bar->count) - target) < 0) {
+            if (++spins > 256) {
+                __nanosleep(20);
+                if (clock64() - start > kBarCycles) {
+                    atomicCAS(&ctl->err, 0, (int)PAMC_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
         }
@@ -460,10 +456,12 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         after + ((((size_t)R * rw * 4) + 15) & ~(size_t)15));
     unsigned long long *sprev = fprev + kB;
     int32_t *Pprev = reinterpret_cast<int32_t *>(sprev + kB);
-    int32_t *Pcur = Pprev + kB;
-    int32_t *Pnext = Pcur + kB;
-    int32_t *flist = Pnext + kB;
+    int32_t *Pring = Pprev + kB;                       // positions of block b in slot b % 3 (TCU)
+    int32_t *Pcur = Pring;
+    int32_t *Pnext = Pring + kB;
+    int32_t *flist = Pring + 3 * kB;
     int32_t *ownl = flist + kB;                        // TCU: block positions owned by this CTA
+    auto ring_slot = [&](int32_t b) { return Pring + (size_t)(b % 3) * kB; };
     // ---------------- chain CTA shared memory
     const int cg = blockIdx.x - a.n_upd;               // chain group (4 replicas)
     const int32_t nw = (n + 31) / 32;
@@ -549,6 +547,47 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         }
     };
 
+    // TCU: this CTA's share of the tiles of a block is loaded one phase ahead
+    // (issued before the grid barrier, two independent loads per thread held
+    // in registers as raw bytes) and stored in the next phase
+    uint32_t tvA = 0u, tvB = 0u;
+    int32_t teA = -1, teB = -1;
+    auto tile_issue = [&](int32_t qn) {
+        teA = teB = -1;
+        if (qn >= total) return;
+        const int32_t cnt = block_cnt(qn), cntc = block_cnt(qn - 1);
+        const int32_t *Pn = ring_slot(qn), *Pc = ring_slot(qn - 1);
+        const int32_t per = (2 * kB * kB + a.n_upd - 1) / a.n_upd;
+        const int32_t e0 = blockIdx.x * per, e1 = min(2 * kB * kB, e0 + per);
+        auto tile_src = [&](int32_t e) -> const uint8_t * {   // nullptr: outside the block
+            const int32_t which = e / (kB * kB), ee = e % (kB * kB);
+            const int32_t m = ee / kB, m2 = ee % kB;
+            if (which == 0) return (m < cnt && m2 < cnt) ? a.J + (size_t)Pn[m] * n + Pn[m2] : nullptr;
+            return (m < cntc && m2 < cnt) ? a.J + (size_t)Pc[m] * n + Pn[m2] : nullptr;
+        };
+        const int32_t ea = e0 + (int32_t)threadIdx.x, eb = ea + (int32_t)blockDim.x;
+        tvA = tvB = 0u;
+        if (ea < e1) { teA = ea; const uint8_t *src = tile_src(ea); if (src) tvA = *src; }
+        if (eb < e1) { teB = eb; const uint8_t *src = tile_src(eb); if (src) tvB = *src; }
+        for (int32_t e = ea + 2 * (int32_t)blockDim.x; e < e1; e += blockDim.x) {   // > 2 per thread: now
+            const uint8_t *src = tile_src(e);
+            const int32_t which = e / (kB * kB), ee = e % (kB * kB);
+            int8_t *Tq = (which == 0 ? a.T : a.T2) + (size_t)(qn & 1) * kB * kB;
+            Tq[(size_t)(ee / kB) * kB + ((ee % kB) & 31) * kC + ((ee % kB) >> 5)] =
+                src ? (int8_t)e4m3_pm1(*src) : (int8_t)0;
+        }
+    };
+    auto tile_flush = [&](int32_t qn) {
+        auto tile_store = [&](int32_t e, uint32_t raw) {
+            const int32_t which = e / (kB * kB), ee = e % (kB * kB);
+            const int32_t m = ee / kB, m2 = ee % kB;
+            int8_t *Tq = (which == 0 ? a.T : a.T2) + (size_t)(qn & 1) * kB * kB;
+            Tq[(size_t)m * kB + (m2 & 31) * kC + (m2 >> 5)] = (int8_t)e4m3_pm1(raw);
+        };
+        if (teA >= 0) tile_store(teA, tvA);
+        if (teB >= 0) tile_store(teB, tvB);
+    };
+
     // ---------------- prologue
     if (upd) {
         if constexpr (TCU) {
@@ -599,9 +638,18 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         __syncthreads();
         if constexpr (TCU) tc_fence_after();
         if (total > 0) {
+            if constexpr (TCU) {
+                Pnext = ring_slot(0);
+                Pcur = ring_slot(2);
+                if (total > 1 && (int)threadIdx.x < block_cnt(1)) ring_slot(1)[threadIdx.x] = block_pos(1)[threadIdx.x];
+            }
             publish_lists(0);
             publish_G(0);
             publish_tiles(0);
+            if constexpr (TCU) {
+                __syncthreads();   // ring slot 1 written
+                tile_issue(1);
+            }
         }
     } else {
         for (int32_t x = threadIdx.x; x < 4 * nw; x += blockDim.x) {
@@ -662,10 +710,16 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     for (int32_t q = 0; alive && q <= total; ++q) {
         if (upd) {
             bool issued = false;   // TCU: MMAs of this phase in flight
+            // TCU: start the independent loads first -- this CTA's share of the
+            // tiles of block q+1 (positions already in the ring) and the
+            // positions of block q+2 -- so their latency overlaps the update
+            int32_t pn2 = -1;
+            if constexpr (TCU)
+                if (q + 2 < total && (int)threadIdx.x < block_cnt(q + 2)) pn2 = block_pos(q + 2)[threadIdx.x];
             // ---- apply block q-1 to the owned rows
             if (q > 0) {
                 const int32_t qp = q - 1;
-                const int32_t *P = block_pos(qp);
+                const int32_t *P = TCU ? ring_slot(qp) : block_pos(qp);
                 const int32_t cntp = block_cnt(qp);
                 if (threadIdx.x == 0) s_nl = 0;
                 __syncthreads();
@@ -785,9 +839,21 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             }
             // ---- publish block q+1 (TCU: the tiles while the MMAs run, the fields after them)
             if constexpr (TCU) {
+                if (q + 1 < total) tile_flush(q + 1);
+                __syncthreads();   // every thread is past its reads of ring slot q-1
+                if (pn2 >= 0) ring_slot(q + 2)[threadIdx.x] = pn2;
                 if (q + 1 < total) {
-                    publish_lists(q + 1);
-                    publish_tiles(q + 1);
+                    // owned positions of block q+1
+                    const int32_t *Pn = ring_slot(q + 1);
+                    const int32_t cnt = block_cnt(q + 1);
+                    if (threadIdx.x == 0) s_nown = 0;
+                    __syncthreads();
+                    if ((int)threadIdx.x < cnt) {
+                        const int32_t p = Pn[threadIdx.x];
+                        if (p >= ua && p < ub) ownl[atomicAdd(&s_nown, 1)] = (int32_t)threadIdx.x;
+                    }
+                    __syncthreads();
+                    Pnext = ring_slot(q + 1);
                 }
                 if (issued) {
                     if (!mbar_wait(&s_mbar, mphase & 1u)) {
@@ -798,6 +864,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                     tc_fence_after();
                 }
                 if (q + 1 < total) publish_G(q + 1);
+                tile_issue(q + 2);   // completes during the barrier; stored next phase
             } else if (q + 1 < total) {
                 publish_lists(q + 1);
                 publish_G(q + 1);
@@ -1142,7 +1209,7 @@ int dense_block_positions() { return kB; }
 // Shared memory of the sweep kernel for a given split.
 size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu) {
     const size_t rest = ((((size_t)R * ((rows_per + 31) / 32) * 4) + 15) & ~(size_t)15) +
-                        (size_t)kB * (8 + 8 + 4 + 4 + 4 + 4 + 4);
+                        (size_t)kB * (8 + 8 + 4 + 12 + 4 + 4);
     const size_t ntiles = ((size_t)rows_per + 127) / 128;
     const size_t upd = tcu ? 1024 + 2 * ntiles * kTuTileBytes + 2 * kTuBSlice + rest
                            : (((size_t)R * rows_per * 4 + 15) & ~(size_t)15) + rest;
