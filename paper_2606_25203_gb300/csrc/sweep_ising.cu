@@ -110,19 +110,26 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
             const uint32_t *es = ELLP ? sell + sb * ell_stride : nullptr;
             const int2 *pos = ELLP ? spos + sb * (size_t)n : nullptr;
             const int32_t L = snlev[sb];
-            for (int32_t lev = 0; lev < L; ++lev) {
-                const int32_t beg = lp[lev], end = lp[lev + 1];
-                int32_t i = beg + li;
-                // ELL path: the record and the first four neighbour words of
-                // the next position are loaded one iteration ahead
-                int2 pr = make_int2(0, 0);
-                uint32_t e4[4] = {0u, 0u, 0u, 0u};
-                if (ELLP && i < end) {
-                    pr = pos[i];
-                    const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+            // ELL path: the record and the first four neighbour words of a
+            // position are loaded one iteration ahead -- for a level's first
+            // position before the previous level's barrier (they do not
+            // depend on spins), so the wait overlaps the barrier
+            int2 pr = make_int2(0, 0);
+            uint32_t e4[4] = {0u, 0u, 0u, 0u};
+            int32_t end = 0;
+            if (ELLP && L > 0) {
+                // unconditional, from a clamped position: whether it is used is
+                // decided once the level's bounds are known
+                const int32_t i0 = min(li, n - 1);
+                pr = pos[i0];
+                const uint32_t *ep = es + (size_t)(i0 >> 5) * 32 * W + (i0 & 31);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) e4[q] = ep[q * 32];
-                }
+                for (int q = 0; q < 4; ++q) e4[q] = ep[q * 32];
+            }
+            for (int32_t lev = 0; lev < L; ++lev) {
+                const int32_t beg = lp[lev];
+                end = lp[lev + 1];
+                int32_t i = beg + li;
                 while (i < end) {
                     const int32_t inext = i + tpg;
                     int2 prn = make_int2(0, 0);
@@ -215,6 +222,13 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                     pr = prn;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) e4[q] = e4n[q];
+                }
+                if (ELLP && lev + 1 < L) {   // the next level's first position (clamped, see above)
+                    const int32_t i2 = min(end + li, n - 1);
+                    pr = pos[i2];
+                    const uint32_t *ep = es + (size_t)(i2 >> 5) * 32 * W + (i2 & 31);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) e4[q] = ep[q * 32];
                 }
                 group_barrier(1 + gl, tpg, gpc);
             }
