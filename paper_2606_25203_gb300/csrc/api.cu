@@ -208,8 +208,7 @@ void release_run(pamc_handle h) {
 int sweep_kind(const pamc_params &p) { return p.kind == 0 ? 0 : (p.rule == 2 ? 2 : 1); }
 
 SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level, int sms) {
-    const int RPG = kind == 1 ? 2 : 4;
-    const int32_t groups = (R + RPG - 1) / RPG;
+    const int32_t groups = (R + 3) / 4;   // every sweep kind groups four replicas
     if (const char *env = getenv("PAMC_SWEEP_CFG")) {
         int a = 0, b = 0;
         if (sscanf(env, "%d,%d", &a, &b) == 2 && a >= 1 && a <= 15 && b >= 1 && a * b * 32 <= 1024) {

@@ -164,9 +164,15 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
                                const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
                                const DevCtl *ctl, SweepCfg cfg, cudaStream_t st);
 
-// Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax.
+// Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax;
+// every kind keeps groups of four replicas.
 size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg);
 size_t sweep_softmax_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
+size_t sweep_potts_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
+cudaError_t launch_sweep_potts(int32_t n, const int32_t *rp, const uint32_t *adj, int32_t H, const pamc_params &p,
+                               int32_t t, int32_t slot, SchedView sv, const uint64_t *tab, const int8_t *src,
+                               const int32_t *parent, int8_t *dst, int64_t *E_dst, const DevCtl *ctl,
+                               SweepCfg cfg, int64_t Wsum, cudaStream_t st);
 cudaError_t launch_sweep_softmax(int32_t n, const int32_t *rp, const uint32_t *adj, int32_t H,
                                  const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
                                  const uint64_t *tab, const int8_t *src, const int32_t *parent,
