@@ -57,8 +57,8 @@ def load_peaks():
 # only while the kernel sources still hash to what was captured.
 PROFILED_TRAFFIC = {
     # k_sweep_ising, torus 141x141, R=4096, 10 sweeps: one launch
-    "sweep_torus": (64.79e6, {"paper_2606_25203_gb300/csrc/sweep_ising.cu":
-                              "e8cc7d5ac06dfb8f15f73bf8c5e85f3692e90270"}),
+    "sweep_torus": (64.93e6, {"paper_2606_25203_gb300/csrc/sweep_ising.cu":
+                              "2ef365775b709862158a5691bf2075cb0d9101f1"}),
     # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.741 GB) scaled by n^2 to n=100,000
     "dense_sweep_100k": (1.741e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
                                                            "61dcf4f94c020340a8522b74c8ccda28d2ea6d99"}),
