@@ -663,6 +663,81 @@ def run_potts(args):
     print(json.dumps(line))
 
 
+C1_PARAMS = dict(R=128, sweeps=5, steps=50, beta0=0.1, beta1=3.0, seed=0)
+# time-to-target runs: the paper's method (stagnation control and NCM on) on the same instance
+TTS_PARAMS = dict(R=128, sweeps=5, steps=500, beta0=0.1, beta1=3.0, stagnation=1, z_rst=400, seed=0)
+
+
+def run_tts(args):
+    """Time-to-target cut (the paper's TTS: T_com ln(1-0.99) / ln(1-P_s)) on the
+    Erdos-Renyi N=800 instance with the augmented controller (stagnation
+    control and NCM on; R=128, 5 sweeps, 500 steps).  The target is the best cut
+    of three long reference runs (R=1024, 1000 steps); then `args.tts_runs`
+    independent runs stop when they reach it.  For every run length k, P_s(k)
+    is the fraction of runs that reached the target within k steps and
+    T_com(k) = k times the device time of a step; the reported TTS is the
+    minimum over k (P_s = 1 counts as a single run)."""
+    import math
+    import torch
+    import paper_2606_25203_gb300 as pg
+    pg.load()
+    inst = W.c1_er800()
+    stream = torch.cuda.current_stream()
+    target = -1
+    for sd in range(3):
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w, stream=stream.cuda_stream)
+        s.run(**dict(TTS_PARAMS, R=1024, steps=1000, seed=1000 + sd))
+        target = max(target, int(s.best()[0]))
+        s.close()
+    # device time of one step of the configuration (no early stop)
+    s = pg.Solver(inst.row_ptr, inst.col, inst.w, stream=stream.cuda_stream)
+    s.init(**TTS_PARAMS)
+    s.step(args.warmup)
+    s.sync()
+    s.init(**TTS_PARAMS)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.step(TTS_PARAMS["steps"])
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_step = a.elapsed_time(b) / TTS_PARAMS["steps"]
+    s.close()
+    reach = []
+    launches = 0
+    t0 = time.perf_counter()
+    for sd in range(args.tts_runs):
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w, stream=stream.cuda_stream)
+        s.run(**dict(TTS_PARAMS, seed=sd, target_cut=target))
+        c = s.control()
+        reach.append(int(c["t"]) if c["done"] else None)
+        launches += s.launches()
+        s.close()
+    wall = time.perf_counter() - t0
+    best = None
+    for k in range(1, TTS_PARAMS["steps"] + 1):
+        ps = sum(1 for r in reach if r is not None and r <= k) / len(reach)
+        if ps <= 0:
+            continue
+        t_com = k * ms_step / 1e3
+        tts = t_com if ps >= 0.99 else t_com * math.log(0.01) / math.log(1.0 - ps)
+        if best is None or tts < best[0]:
+            best = (tts, k, ps, t_com)
+    line = {
+        "metric": "time-to-target cut (99%)", "value": best[0] if best else None, "unit": "s", "n_gpus": 1,
+        "steps": TTS_PARAMS["steps"], "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "Erdos-Renyi N=800, p=0.06, unit weights; augmented PAMC, R=128, beta 0.1 -> 3.0 "
+                               "over 500 steps, 5 sweeps/step, restart every 400", "runs": args.tts_runs,
+                   "target": f"best cut of three reference runs (R=1024, 1000 steps): {target}"},
+        "target_cut": target, "best_steps": best[1] if best else None, "P_s": best[2] if best else 0.0,
+        "T_com_s": best[3] if best else None,
+        "reached": sum(1 for r in reach if r is not None), "runs_wall_s": wall,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line))
+
+
 def run_diag(args):
     """Diagnostics on the torus population of the default workload (R=4096):
     the corrected pairwise Hamming histogram (8.4M pairs) and the lineage,
@@ -717,9 +792,10 @@ def main():
                     help="run one of the two instances (profiling)")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only: no e2e, kernel split or CPU baseline (profiling)")
-    ap.add_argument("--workload", choices=["sparse", "dense100k", "serving", "batch", "diag", "potts"],
+    ap.add_argument("--workload", choices=["sparse", "dense100k", "serving", "batch", "diag", "potts", "tts"],
                     default="sparse")
     ap.add_argument("--batch-requests", type=int, default=48)
+    ap.add_argument("--tts-runs", type=int, default=32)
     ap.add_argument("--batch-n-lo", type=int, default=800)
     ap.add_argument("--batch-n-hi", type=int, default=20000)
     ap.add_argument("--serve-requests", type=int, default=48)
@@ -730,6 +806,9 @@ def main():
     ONLY = args.only
     if args.workload == "dense100k" and args.impl == "ours":
         run_dense(args)
+        return
+    if args.workload == "tts" and args.impl == "ours":
+        run_tts(args)
         return
     if args.workload == "potts" and args.impl == "ours":
         run_potts(args)
