@@ -142,6 +142,14 @@ pamc_status pamc_control_state(pamc_handle h, int64_t *iv, double *dv);
 /* Number of this library's kernels launched on the handle so far. */
 int64_t pamc_launch_count(pamc_handle h);
 
+/* Launch shape the sparse sweep of an initialised run uses: replica groups
+ * (four replicas each) per CTA, warps per group, and lanes that share one
+ * vertex's couplings (1 except for Ising runs on ELL schedules; set by
+ * pamc_init from the schedule's level widths, or by the environment variable
+ * PAMC_SWEEP_CFG="gpc,wpg[,lpv]").  The shape changes speed only, never
+ * results.  PAMC_ERR_STATE before pamc_init or for dense runs. */
+pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_group, int *lanes_per_vertex);
+
 /* W = sum_{i<j} w_ij of the instance (cut = (W - E)/2). */
 int64_t pamc_weight_sum(pamc_handle h);
 

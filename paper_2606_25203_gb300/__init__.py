@@ -21,7 +21,7 @@ from . import build as _build
 __all__ = [
     "PamcError", "Params", "load", "pamc_create_csr", "pamc_create_dense", "pamc_init",
     "pamc_step", "pamc_sync", "pamc_run", "pamc_best", "pamc_state", "pamc_control_state",
-    "pamc_launch_count", "pamc_weight_sum", "pamc_last_error", "pamc_destroy", "Solver",
+    "pamc_launch_count", "pamc_sweep_shape", "pamc_weight_sum", "pamc_last_error", "pamc_destroy", "Solver",
     "pamc_sweeps_noalloc", "pamc_footprint", "pamc_batch_create", "pamc_batch_add", "pamc_batch_step",
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_control_state.argtypes = [P, P, P]
     L.pamc_launch_count.argtypes = [P]
     L.pamc_launch_count.restype = i64
+    L.pamc_sweep_shape.argtypes = [P, P, P, P]
     L.pamc_weight_sum.argtypes = [P]
     L.pamc_weight_sum.restype = i64
     L.pamc_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
@@ -266,6 +267,13 @@ def pamc_control_state(h) -> dict:
 
 def pamc_launch_count(h) -> int:
     return int(_lib.pamc_launch_count(h))
+
+
+def pamc_sweep_shape(h) -> tuple:
+    """(groups per CTA, warps per group, lanes per vertex) of the sparse sweep."""
+    v = np.zeros(3, dtype=np.int32)
+    _check(_lib.pamc_sweep_shape(h, _ptr(v[0:1]), _ptr(v[1:2]), _ptr(v[2:3])), h)
+    return int(v[0]), int(v[1]), int(v[2])
 
 
 def pamc_weight_sum(h) -> int:

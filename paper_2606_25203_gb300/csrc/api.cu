@@ -201,20 +201,52 @@ void release_run(pamc_handle h) {
     h->d_spins[0] = h->d_spins[1] = nullptr;
 }
 
-// Launch shape of the sweep kernel: groups per CTA and warps per group.
-// Scores every shape by the fraction of group slots used over whole waves,
-// the lane efficiency of a level (average level size over the lanes of a
-// group), and resident warps per SM.  PAMC_SWEEP_CFG="gpc,wpg" overrides.
+// Launch shape of the sweep kernel: groups per CTA, warps per group and
+// lanes per vertex.  Ising runs on ELL schedules give each group a CTA of its
+// own, sized for the latency of a level, unless the SMs are shared and the
+// levels are too wide for more than one lane per vertex.  Otherwise every
+// (gpc, wpg) is scored by the fraction of group slots used
+// over whole waves, the lane efficiency of a level (average level size over
+// the lanes of a group), and resident warps per SM; Ising runs on ELL
+// schedules then give the lanes a level leaves idle to the couplings (the
+// largest power of two up to 8 at which an average level still fits the
+// group's lanes in one pass).  PAMC_SWEEP_CFG="gpc,wpg[,lpv]" overrides.
 int sweep_kind(const pamc_params &p) { return p.kind == 0 ? 0 : (p.rule == 2 ? 2 : 1); }
 
-SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level, int sms) {
+SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level, double avg_deg, int sms,
+                    int32_t ell_w) {
     const int32_t groups = (R + 3) / 4;   // every sweep kind groups four replicas
+    const bool lpv_ok = kind == 0 && ell_w > 4;
     if (const char *env = getenv("PAMC_SWEEP_CFG")) {
-        int a = 0, b = 0;
-        if (sscanf(env, "%d,%d", &a, &b) == 2 && a >= 1 && a <= 15 && b >= 1 && a * b * 32 <= 1024) {
-            SweepCfg c{a, b};
+        int a = 0, b = 0, v = 1;
+        const int got = sscanf(env, "%d,%d,%d", &a, &b, &v);
+        if (got >= 2 && a >= 1 && a <= 15 && b >= 1 && a * b * 32 <= 1024 &&
+            v >= 1 && v <= 32 && (v & (v - 1)) == 0) {
+            SweepCfg c{a, b, lpv_ok ? v : 1};
             if (sweep_smem_bytes(kind, n, H, c) <= 227 * 1024) return c;
         }
+    }
+    if (kind == 0 && ell_w > 0) {
+        // Groups sized for the latency of a level: lanes per vertex so that
+        // the eight slots a lane loads ahead cover an average row (half that
+        // where four or more groups share an SM, and two groups to a CTA
+        // there), halved while an average level needs more lanes than a
+        // group's share of the SM (1024 threads over the groups an SM
+        // holds), then warps so that an average level takes one pass.
+        // Where that leaves one lane per vertex on a shared SM, the scoring
+        // below decides.
+        const int64_t per_sm = (groups + sms - 1) / std::max(sms, 1);
+        int lanes = 1024;
+        while (lanes > 32 && (int64_t)lanes * per_sm > 1024) lanes >>= 1;
+        const double lev = std::max(avg_level, 1.0);
+        SweepCfg c{per_sm >= 4 ? 2 : 1, 1, 1};
+        if (lpv_ok)
+            while (c.lanes_per_vertex < 32 && 8.0 * c.lanes_per_vertex < avg_deg) c.lanes_per_vertex *= 2;
+        if (per_sm >= 4 && c.lanes_per_vertex > 1) c.lanes_per_vertex >>= 1;
+        while (c.lanes_per_vertex > 1 && lev * c.lanes_per_vertex > lanes) c.lanes_per_vertex >>= 1;
+        while (c.warps_per_group * 32 < lanes && 32.0 * c.warps_per_group < lev * c.lanes_per_vertex)
+            c.warps_per_group *= 2;
+        if ((per_sm <= 1 || c.lanes_per_vertex > 1) && sweep_smem_bytes(kind, n, H, c) <= 227 * 1024) return c;
     }
     SweepCfg best{1, 1};
     double best_score = -1.0;
@@ -239,6 +271,13 @@ SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level,
             const double score = util * lane_eff * (0.5 + 0.5 * occ);
             if (score > best_score + 1e-9) { best_score = score; best = c; }
         }
+    }
+    if (lpv_ok) {
+        const double lev = std::ceil(std::max(avg_level, 1.0));
+        const int tpg = best.warps_per_group * 32;
+        while (best.lanes_per_vertex < 8 && lev * best.lanes_per_vertex * 2 <= tpg &&
+               4 * best.lanes_per_vertex < ell_w)
+            best.lanes_per_vertex *= 2;
     }
     return best;
 }
@@ -594,7 +633,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    h->cfg = choose_cfg(sweep_kind(p), n, R, h->H, avg_level, sms);
+    h->cfg = choose_cfg(sweep_kind(p), n, R, h->H, avg_level, (double)h->nnz / std::max(n, 1), sms, h->ell_w);
     if (sweep_smem_bytes(sweep_kind(p), n, h->H, h->cfg) > kSmemMax) {
         release_run(h);
         return fail(h, PAMC_ERR_RANGE, "n = %d: one replica group's spins exceed shared memory", n);
@@ -833,6 +872,15 @@ pamc_status pamc_lineage(pamc_handle h, int32_t *family, int32_t *n_families) {
 }
 
 int64_t pamc_launch_count(pamc_handle h) { return h ? h->launches : 0; }
+
+pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_group, int *lanes_per_vertex) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    if (!h->initialized || h->dense) return fail(h, PAMC_ERR_STATE, "no sparse run initialised");
+    if (groups_per_cta) *groups_per_cta = h->cfg.groups_per_cta;
+    if (warps_per_group) *warps_per_group = h->cfg.warps_per_group;
+    if (lanes_per_vertex) *lanes_per_vertex = h->cfg.lanes_per_vertex;
+    return PAMC_OK;
+}
 
 int64_t pamc_weight_sum(pamc_handle h) { return h ? h->W : 0; }
 

@@ -137,6 +137,7 @@ inline cudaError_t allow_dynamic_smem(F *func, size_t bytes) {
 struct SweepCfg {
     int groups_per_cta;   // replica groups in one CTA
     int warps_per_group;  // warps cooperating on one group's level
+    int lanes_per_vertex = 1;  // Ising, ELL: lanes sharing one vertex's couplings (1, 2, 4, .., 32)
 };
 
 // Builds the (t, sweep) schedules of nt steps starting at t0 into ring slots

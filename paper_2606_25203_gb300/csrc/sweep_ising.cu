@@ -47,9 +47,35 @@ struct KeysSeed {
     }
 };
 
+// New four-replica spin word from the byte-lane field accumulator A (byte q =
+// 128 + sum_j J_kj [s_j = +1]), c0 = H - 256 - sum_j J_kj, the draws u and the
+// old word: heat-bath s = +1 iff u < T(h); Metropolis flip iff u < T_M(2 s h).
+template <int RULE>
+__device__ __forceinline__ uint32_t ising_decide(uint32_t A, int32_t c0, const u32x4 &u, uint32_t old,
+                                                 const uint64_t *tab_s, int32_t H) {
+    const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+    uint32_t nw = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int32_t idx = 2 * (int32_t)((A >> (8 * q)) & 0xFFu) + c0;   // h + H
+        if (RULE == 0) {
+            nw |= ((uint64_t)uw[q] < tab_s[idx] ? 1u : 0u) << (8 * q);
+        } else {
+            const uint32_t s = (old >> (8 * q)) & 1u;
+            const int32_t ix = s ? idx : 2 * H - idx;              // s*h + H
+            nw |= (((uint64_t)uw[q] < tab_s[ix]) ? (s ^ 1u) : s) << (8 * q);
+        }
+    }
+    return nw;
+}
+
 // The sweep of one CTA's replica groups (groups bid*gpc .. bid*gpc+gpc-1 of
-// the instance), shared by the single-instance and the batched kernels.
-template <bool ELLP, int RULE, class KeyT>
+// the instance), shared by the single-instance and the batched kernels.  With
+// LPV > 1 (position-indexed ELL only; LPV a power of two up to 32) LPV lanes share a vertex: lane sub takes
+// the coupling slots sub, sub + LPV, ...; the byte-lane partial sums add up
+// exactly under XOR shuffles (plain 32-bit addition), and every lane of the
+// group runs the same iterations so that the shuffles always converge.
+template <bool ELLP, int RULE, int LPV, class KeyT>
 __device__ __forceinline__ void
 sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                  const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, const KeyT &draw,
@@ -110,6 +136,65 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
             const uint32_t *es = ELLP ? sell + sb * ell_stride : nullptr;
             const int2 *pos = ELLP ? spos + sb * (size_t)n : nullptr;
             const int32_t L = snlev[sb];
+            if constexpr (ELLP && LPV > 1) {
+                // lane sub of a vertex takes the slots sub + LPV q; the record
+                // and the first eight slots of a pass are loaded ahead, for a
+                // level's first pass before the previous level's barrier
+                // (from a clamped position: they do not depend on spins)
+                const int32_t vl = li / LPV, sub = li % LPV, vpi = tpg / LPV;
+                int2 pr;
+                uint32_t e8[8];
+                auto fetch = [&](int32_t i) {
+                    pr = pos[i];
+                    const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int32_t sl = sub + q * LPV;   // slots >= deg hold coupling 0
+                        e8[q] = sl < W ? ep[(size_t)sl * 32] : 0u;
+                    }
+                };
+                if (L > 0) fetch(min(vl, n - 1));
+                for (int32_t lev = 0; lev < L; ++lev) {
+                    const int32_t beg = lp[lev], end = lp[lev + 1];
+                    for (int32_t base = beg; base < end; base += vpi) {   // uniform over the group
+                        // idle lanes take a clamped position too: a whole row of
+                        // one vertex, so that its sum indexes the table in range
+                        const bool act = base + vl < end;
+                        const int32_t ic = min(base + vl, n - 1);
+                        if (base != beg) fetch(ic);
+                        const int32_t k = pr.x & 0xFFFFFF;
+                        const int32_t deg = (int32_t)((uint32_t)pr.x >> 24);
+                        const u32x4 u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
+                        uint32_t Ap = 0u;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) Ap += sp[e8[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e8[q] >> 24);
+                        if (8 * LPV < deg) {
+                            const uint32_t *ep = es + (size_t)(ic >> 5) * 32 * W + (ic & 31);
+                            for (int32_t s0 = sub + 8 * LPV; s0 < deg; s0 += 8 * LPV) {
+                                uint32_t ev[8];
+#pragma unroll
+                                for (int q = 0; q < 8; ++q) {
+                                    const int32_t sl = s0 + q * LPV;
+                                    ev[q] = sl < W ? ep[(size_t)sl * 32] : 0u;
+                                }
+#pragma unroll
+                                for (int q = 0; q < 8; ++q)
+                                    Ap += sp[ev[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ev[q] >> 24);
+                            }
+                        }
+#pragma unroll
+                        for (int o = 1; o < LPV; o <<= 1) Ap += __shfl_xor_sync(0xffffffffu, Ap, o);
+                        const uint32_t old = sp[k];
+                        const uint32_t nw = ising_decide<RULE>(0x80808080u + Ap, H - 256 - pr.y, u, old, tab_s, H);
+                        // every lane has read sp[k] before any lane of the group writes it
+                        __syncwarp();
+                        if (act && sub == 0 && nw != old) sp[k] = nw;
+                    }
+                    if (lev + 1 < L) fetch(min(end + vl, n - 1));
+                    group_barrier(1 + gl, tpg, gpc);
+                }
+                continue;
+            }
             // ELL path: the record and the first four neighbour words of a
             // position are loaded one iteration ahead -- for a level's first
             // position before the previous level's barrier (they do not
@@ -202,21 +287,8 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                         }
                     }
                     if (!ELLP) u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
-                    const int32_t c0 = H - 256 - jsum;
-                    const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
                     const uint32_t old = sp[k];
-                    uint32_t nw = 0;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int32_t idx = 2 * (int32_t)((A >> (8 * q)) & 0xFFu) + c0;   // h + H
-                        if (RULE == 0) {
-                            nw |= ((uint64_t)uw[q] < tab_s[idx] ? 1u : 0u) << (8 * q);
-                        } else {
-                            const uint32_t s = (old >> (8 * q)) & 1u;
-                            const int32_t ix = s ? idx : 2 * H - idx;              // s*h + H
-                            nw |= (((uint64_t)uw[q] < tab_s[ix]) ? (s ^ 1u) : s) << (8 * q);
-                        }
-                    }
+                    const uint32_t nw = ising_decide<RULE>(A, H - 256 - jsum, u, old, tab_s, H);
                     if (nw != old) sp[k] = nw;
                     i = inext;
                     pr = prn;
@@ -268,9 +340,9 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 4 + li] / 2);
 }
 
-template <bool ELLP, int RULE>
+template <bool ELLP, int RULE, int LPV>
 __global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int tpg) {
-    sweep_ising_body<ELLP, RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t, d.slot, d.sorder,
+    sweep_ising_body<ELLP, RULE, LPV>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t, d.slot, d.sorder,
                                  d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf,
                                  d.ncm_idx, d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x);
 }
@@ -287,7 +359,7 @@ k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restric
     const int32_t t = ctl->t;
     if (t >= d.t_end) return;
     const KeysSeed draw{d.K.k0[0], d.K.k1[0]};
-    sweep_ising_body<ELLP, RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.sorder,
+    sweep_ising_body<ELLP, RULE, 1>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.sorder,
                                  d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.ncm_buf,
                                  d.ncm_idx, d.sp[(t + 1) & 1], d.en[(t + 1) & 1], ctl, gpc, tpg, it.y);
 }
@@ -317,17 +389,30 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
     const int grid = (groups + gpc - 1) / gpc;
     const bool ell = sv.ell != nullptr;
     cudaError_t err = cudaSuccess;
-#define PAMC_LAUNCH(EL, RU)                                                                       \
+#define PAMC_LAUNCH(EL, RU, LV)                                                                   \
     do {                                                                                          \
-        err = allow_dynamic_smem(k_sweep_ising<EL, RU>, smem);                                    \
+        err = allow_dynamic_smem(k_sweep_ising<EL, RU, LV>, smem);                                \
         if (err != cudaSuccess) return err;                                                       \
-        k_sweep_ising<EL, RU><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);                        \
+        k_sweep_ising<EL, RU, LV><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);                    \
     } while (0)
+#define PAMC_LAUNCH_LPV(RU)                                                                       \
+    do {                                                                                          \
+        switch (lpv) {                                                                            \
+        case 32: PAMC_LAUNCH(true, RU, 32); break;                                                \
+        case 16: PAMC_LAUNCH(true, RU, 16); break;                                                \
+        case 8: PAMC_LAUNCH(true, RU, 8); break;                                                  \
+        case 4: PAMC_LAUNCH(true, RU, 4); break;                                                  \
+        case 2: PAMC_LAUNCH(true, RU, 2); break;                                                  \
+        default: PAMC_LAUNCH(true, RU, 1); break;                                                 \
+        }                                                                                         \
+    } while (0)
+    const int lpv = ell ? cfg.lanes_per_vertex : 1;
     if (ell) {
-        if (rule == 0) PAMC_LAUNCH(true, 0); else PAMC_LAUNCH(true, 1);
+        if (rule == 0) PAMC_LAUNCH_LPV(0); else PAMC_LAUNCH_LPV(1);
     } else {
-        if (rule == 0) PAMC_LAUNCH(false, 0); else PAMC_LAUNCH(false, 1);
+        if (rule == 0) PAMC_LAUNCH(false, 0, 1); else PAMC_LAUNCH(false, 1, 1);
     }
+#undef PAMC_LAUNCH_LPV
 #undef PAMC_LAUNCH
     return cudaGetLastError();
 }

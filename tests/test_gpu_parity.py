@@ -120,6 +120,36 @@ def test_augmented_potts_controller(pg):
                 z_rst=70, cooldown_tau=4, seed=4)
 
 
+@pytest.mark.parametrize("cfg,rule", [("1,1,2", 0), ("1,1,4", 1), ("1,1,8", 0), ("2,2,8", 1), ("3,4,4", 0),
+                                      ("1,2,16", 1), ("2,4,32", 0), ("1,32,32", 1)])
+def test_lanes_per_vertex_shapes(pg, monkeypatch, cfg, rule):
+    """Several lanes per vertex (coupling slots split, partial sums shuffled)
+    give the sequential result: dense ER rows longer than the lanes' share,
+    sparse rows shorter than it, a ragged population, both update rules."""
+    monkeypatch.setenv("PAMC_SWEEP_CFG", cfg)
+    lpv = int(cfg.split(",")[2])
+    for inst, R in ((W.erdos_renyi(300, 0.2, signed=True, seed=4), 13),
+                    (W.gnm(333, 900, signed=True, seed=2), 20)):
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+        s.init(R=R, sweeps=2, steps=3, rule=rule, seed=9)
+        assert pg.pamc_sweep_shape(s.h)[2] == lpv
+        s.close()
+        compare_run(pg, inst, 6, R=R, sweeps=2, beta0=0.3, beta1=3.0, rule=rule, stagnation=1,
+                    z_rst=4, cooldown_tau=1, seed=9)
+
+
+def test_lanes_per_vertex_default_choice(pg, monkeypatch):
+    """Narrow-level dense-row instances get several lanes per vertex; the
+    torus (rows of four) keeps one."""
+    monkeypatch.delenv("PAMC_SWEEP_CFG", raising=False)
+    for inst, want_many in ((W.c1_er800(), True), (W.torus(40, 40, signed=True, seed=1), False)):
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+        s.init(R=128, sweeps=2, steps=3, seed=0)
+        lpv = pg.pamc_sweep_shape(s.h)[2]
+        s.close()
+        assert (lpv > 1) == want_many, (inst.name, lpv)
+
+
 def test_independent_chains_baseline(pg):
     inst = W.gnm(400, 1100, signed=True, seed=6)
     compare_run(pg, inst, 6, R=9, sweeps=2, resample=0, seed=1)
