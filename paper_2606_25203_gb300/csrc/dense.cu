@@ -327,14 +327,14 @@ constexpr int kTuBSlice = 64 * 128;           // one K slice of B (64 replicas)
 constexpr uint32_t kTuCols = 512;             // tensor memory columns allocated
 constexpr uint32_t kTuIdesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-// A rows of a 32-row block are permuted so that the transposed 32-bit shared
-// stores of a warp hit 32 distinct banks: A row 32b + 8r + g <-> slice row
-// 32b + 4g + r (g < 8, r < 4)
+// A rows of a 128-row tile are permuted so that the transposed 32-bit shared
+// stores of a warp hit 32 distinct banks: A row 128b + 8s + g <-> slice row
+// 128b + 16g + s (g < 8, s < 16)
 __device__ __forceinline__ int32_t tu_row_of(int32_t arow) {
-    return (arow & ~31) + ((arow & 7) << 2) + ((arow >> 3) & 3);
+    return (arow & ~127) + ((arow & 7) << 4) + ((arow >> 3) & 15);
 }
 __device__ __forceinline__ int32_t tu_arow_of(int32_t row) {
-    return (row & ~31) + ((row & 3) << 3) + ((row >> 2) & 7);
+    return (row & ~127) + ((row & 15) << 3) + ((row >> 4) & 7);
 }
 // byte offset of (row a of an A tile or replica row of B, k) in a 128-byte-
 // swizzled K-major slice
@@ -361,7 +361,9 @@ __device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &g
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
+        // the release add publishes the CTA's writes (ordered before it by the
+        // CTA barrier); the acquire load of the last arrival makes every
+        // CTA's writes visible to this one
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
         const unsigned int target = (gen + 1u) * nblocks;
         const long long start = clock64();
@@ -377,7 +379,6 @@ __device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &g
             }
         }
         gen += 1;
-        __threadfence();
         *s_ok = ok;
     }
     __syncthreads();
@@ -499,23 +500,26 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         const int32_t cnt = block_cnt(qn);
         int32_t *Gq = a.G + (size_t)(qn & 1) * kB * 64;
         if constexpr (TCU) {
-            // warp w < 4 reads the owned positions whose tensor-memory lane is in its quarter
-            if (warp < 4) {
-                const int32_t nown = s_nown;
-                for (int32_t o = 0; o < nown; ++o) {
-                    const int32_t m = ownl[o];
-                    const int32_t ar = tu_arow_of(Pnext[m] - ua);
-                    if (((ar & 127) >> 5) != warp) continue;
-                    const uint32_t tbase = s_tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((ar >> 7) * 64);
+            // an owned position's fields are four loads of 16 columns from its
+            // tensor-memory lane; the warps of a lane quarter (warp % 4) deal
+            // those loads out among themselves in list order
+            const int quarter = warp & 3, share = warp >> 2;
+            constexpr int kShares = (kSwThreads / 32) / 4;
+            const int32_t nown = s_nown;
+            int dealt = 0;
+            for (int32_t o = 0; o < nown; ++o) {
+                const int32_t m = ownl[o];
+                const int32_t ar = tu_arow_of(Pnext[m] - ua);
+                if (((ar & 127) >> 5) != quarter) continue;
+                const uint32_t tbase = s_tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((ar >> 7) * 64);
+                for (int c0 = 0; c0 < 64; c0 += 16, ++dealt) {
+                    if (dealt % kShares != share) continue;
+                    uint32_t v[16];
+                    tc_ld16(tbase + (uint32_t)c0, v);
+                    if (lane == (ar & 31))
 #pragma unroll
-                    for (int c0 = 0; c0 < 64; c0 += 16) {
-                        uint32_t v[16];
-                        tc_ld16(tbase + (uint32_t)c0, v);
-                        if (lane == (ar & 31))
-#pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (c0 + j < R) Gq[m * 64 + c0 + j] = __float2int_rn(__uint_as_float(v[j]));
-                    }
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < R) Gq[m * 64 + c0 + j] = __float2int_rn(__uint_as_float(v[j]));
                 }
             }
         } else {
@@ -748,31 +752,52 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 if constexpr (TCU) {
                     if (nl > 0) {
                         // A: the flipped positions' coupling rows over this slice,
-                        // transposed 4x4 bytes at a time into K-major tiles; k = list index
-                        const int32_t n16 = (nl + 15) >> 4, nb32 = (a.ntiles * 128) >> 5;
+                        // transposed 4x4 bytes at a time into K-major tiles; k = list
+                        // index.  A warp task is 16 positions x 128 rows: lane (pg, rg)
+                        // loads 16 rows (16 bytes) of 4 positions; two tasks per
+                        // iteration keep eight 16-byte loads of a lane in flight
+                        constexpr int kNW = kSwThreads / 32;
+                        const int32_t ntask = ((nl + 15) >> 4) * a.ntiles;
                         const int pg = lane >> 3, rg = lane & 7;
-                        for (int32_t task = warp; task < n16 * nb32; task += kSwThreads / 32) {
-                            const int32_t c16 = task / nb32, rb = task % nb32;
-                            const int32_t j0 = rb * 32 + rg * 4;          // slice rows j0 .. j0+3
-                            uint32_t w[4];
+                        for (int32_t t0 = warp; t0 < ntask; t0 += 2 * kNW) {
+                            uint4 w[2][4];
 #pragma unroll
-                            for (int c = 0; c < 4; ++c) {
-                                const int32_t i = c16 * 16 + pg * 4 + c;
-                                w[c] = 0u;
-                                if (i < nl && j0 < rows)
-                                    w[c] = *reinterpret_cast<const uint32_t *>(a.J + (size_t)Pprev[flist[i]] * n + ua + j0);
+                            for (int u = 0; u < 2; ++u) {
+                                const int32_t task = t0 + u * kNW;
+                                const int32_t c16 = task / a.ntiles, rb = task % a.ntiles;
+                                const int32_t j0 = rb * 128 + rg * 16;         // slice rows j0 .. j0+15
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    const int32_t i = c16 * 16 + pg * 4 + c;
+                                    w[u][c] = make_uint4(0u, 0u, 0u, 0u);
+                                    if (task < ntask && i < nl && j0 < rows)
+                                        w[u][c] = __ldg(reinterpret_cast<const uint4 *>(
+                                            a.J + (size_t)Pprev[flist[i]] * n + ua + j0));
+                                }
                             }
-                            const uint32_t lo01 = __byte_perm(w[0], w[1], 0x5140), hi01 = __byte_perm(w[0], w[1], 0x7362);
-                            const uint32_t lo23 = __byte_perm(w[2], w[3], 0x5140), hi23 = __byte_perm(w[2], w[3], 0x7362);
-                            const uint32_t o[4] = {__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632),
-                                                   __byte_perm(hi01, hi23, 0x5410), __byte_perm(hi01, hi23, 0x7632)};
-                            const int32_t k = c16 * 16 + pg * 4;
-                            uint8_t *Ak = tuA + (size_t)(k >> 7) * a.ntiles * kTuTileBytes;
 #pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                const int32_t ar = rb * 32 + r * 8 + rg;   // = tu_arow_of(j0 + r)
-                                *reinterpret_cast<uint32_t *>(Ak + (size_t)(ar >> 7) * kTuTileBytes +
-                                                              tu_sw_off(ar & 127, k & 127)) = o[r];
+                            for (int u = 0; u < 2; ++u) {
+                                const int32_t task = t0 + u * kNW;
+                                if (task >= ntask) break;
+                                const int32_t c16 = task / a.ntiles, rb = task % a.ntiles;
+                                const int32_t k = c16 * 16 + pg * 4;
+                                uint8_t *Ak = tuA + (size_t)(k >> 7) * a.ntiles * kTuTileBytes + (size_t)rb * kTuTileBytes;
+#pragma unroll
+                                for (int s4 = 0; s4 < 4; ++s4) {
+                                    const uint32_t x0 = s4 == 0 ? w[u][0].x : s4 == 1 ? w[u][0].y : s4 == 2 ? w[u][0].z : w[u][0].w;
+                                    const uint32_t x1 = s4 == 0 ? w[u][1].x : s4 == 1 ? w[u][1].y : s4 == 2 ? w[u][1].z : w[u][1].w;
+                                    const uint32_t x2 = s4 == 0 ? w[u][2].x : s4 == 1 ? w[u][2].y : s4 == 2 ? w[u][2].z : w[u][2].w;
+                                    const uint32_t x3 = s4 == 0 ? w[u][3].x : s4 == 1 ? w[u][3].y : s4 == 2 ? w[u][3].z : w[u][3].w;
+                                    const uint32_t lo01 = __byte_perm(x0, x1, 0x5140), hi01 = __byte_perm(x0, x1, 0x7362);
+                                    const uint32_t lo23 = __byte_perm(x2, x3, 0x5140), hi23 = __byte_perm(x2, x3, 0x7362);
+                                    const uint32_t o[4] = {__byte_perm(lo01, lo23, 0x5410), __byte_perm(lo01, lo23, 0x7632),
+                                                           __byte_perm(hi01, hi23, 0x5410), __byte_perm(hi01, hi23, 0x7632)};
+#pragma unroll
+                                    for (int r = 0; r < 4; ++r) {
+                                        const int32_t ar = (4 * s4 + r) * 8 + rg;   // = tu_arow_of(j0 + 4 s4 + r) & 127
+                                        *reinterpret_cast<uint32_t *>(Ak + tu_sw_off(ar, k & 127)) = o[r];
+                                    }
+                                }
                             }
                         }
                         // B = D^T: replica r, k -> +2 (new spin +1) / -2 / 0 as e4m3
