@@ -96,7 +96,7 @@ struct pamc_handle_s {
     int32_t *d_perm = nullptr, *d_sidx = nullptr, *d_G = nullptr, *d_ident = nullptr, *d_nonc = nullptr;
     int32_t *d_boff = nullptr;           // bucket offsets of the order sort
     uint32_t *d_pkey = nullptr;
-    int8_t *d_T = nullptr, *d_T2 = nullptr;
+    uint32_t *d_T = nullptr, *d_T2 = nullptr;   // bit tiles of the dense chains
     unsigned long long *d_flip = nullptr, *d_snew = nullptr;
     void *d_bar = nullptr;
     int32_t dense_Hc = 0, dense_grid = 0, dense_nupd = 0, dense_rows = 0;
@@ -335,7 +335,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
               alloc_n(h, h->d_best, n, h->bufs) && alloc_n(h, h->d_H, (size_t)R * n, h->bufs) &&
               alloc_n(h, h->d_perm, (size_t)S * n, h->bufs) && alloc_n(h, h->d_pkey, (size_t)S * n, h->bufs) &&
               alloc_n(h, h->d_sidx, (size_t)S * n, h->bufs) && alloc_n(h, h->d_G, (size_t)2 * B * 64, h->bufs) &&
-              alloc_n(h, h->d_T, (size_t)2 * B * B, h->bufs) && alloc_n(h, h->d_T2, (size_t)2 * B * B, h->bufs) &&
+              alloc_n(h, h->d_T, (size_t)2 * B * (B / 32), h->bufs) && alloc_n(h, h->d_T2, (size_t)2 * B * (B / 32), h->bufs) &&
               alloc_n(h, h->d_flip, (size_t)3 * B, h->bufs) && alloc_n(h, h->d_snew, (size_t)3 * B, h->bufs) &&
               (h->d_bar = dev_alloc(h, 64, h->bufs)) != nullptr &&
               alloc_n(h, h->d_ident, R, h->bufs) && alloc_n(h, h->d_nonc, R, h->bufs) &&

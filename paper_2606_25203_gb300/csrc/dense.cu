@@ -177,7 +177,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 // +-1 int8 spins -> e4m3 (+1.0 = 0x38, -1.0 = 0xB8), four at a time
 __device__ __forceinline__ uint32_t spins_to_e4m3(uint32_t x) { return (x & 0x80808080u) | 0x38383838u; }
@@ -315,6 +314,9 @@ k_dense_recompute(int32_t n, int32_t R, const uint8_t *__restrict__ J, const int
 constexpr int kSwThreads = 768;
 constexpr int kB = 256;              // positions per block
 constexpr int kC = kB / 32;          // positions per lane in a chain warp
+// Chain tiles hold one bit per coupling (+1 set; J is +-1 off the diagonal):
+// row m is kC words, bit l of word c for column position 32 c + l
+constexpr int kTileWords = 2 * kB * kC;   // both tiles of a block
 constexpr int kWin = 4096;           // threshold entries kept in shared memory
 constexpr long long kBarCycles = 4000000000ll;   // ~2 s: a barrier wait gives up after this
 
@@ -354,17 +356,21 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
 }
 
 // Grid-wide barrier for a cooperative launch: one monotonic arrival counter;
-// phase g completes when it reaches (g + 1) * nblocks.  The wait is bounded by
-// the clock: after kBarCycles it sets PAMC_ERR_TIMEOUT and the kernel returns.
-__device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &gen,
-                             DevCtl *ctl, int *s_ok) {
+// phase g completes when it reaches (g + 1) * nblocks.  Split in two so that
+// a CTA can issue independent memory work between its arrival and its wait.
+// The wait is bounded by the clock: after kBarCycles it sets
+// PAMC_ERR_TIMEOUT and the kernel returns.
+__device__ void grid_arrive(GridBar *bar) {
     __syncthreads();
+    // the release add publishes the CTA's writes (ordered before it by the
+    // CTA barrier); the acquire load that sees the last arrival makes every
+    // CTA's writes visible to this one
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+}
+
+__device__ bool grid_wait(GridBar *bar, unsigned int nblocks, unsigned int &gen, DevCtl *ctl, int *s_ok) {
     if (threadIdx.x == 0) {
         int ok = 1;
-        // the release add publishes the CTA's writes (ordered before it by the
-        // CTA barrier); the acquire load of the last arrival makes every
-        // CTA's writes visible to this one
-        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
         const unsigned int target = (gen + 1u) * nblocks;
         const long long start = clock64();
         int spins = 0;
@@ -385,6 +391,11 @@ __device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &g
     return *s_ok != 0;
 }
 
+__device__ bool grid_barrier(GridBar *bar, unsigned int nblocks, unsigned int &gen, DevCtl *ctl, int *s_ok) {
+    grid_arrive(bar);
+    return grid_wait(bar, nblocks, gen, ctl, s_ok);
+}
+
 struct DenseSweepArgs {
     int32_t n, R, S, rule, Hc;
     int32_t n_upd;            // CTAs that own H rows (the others run chains)
@@ -403,8 +414,8 @@ struct DenseSweepArgs {
     int8_t *dst;              // [R][n]
     int64_t *E;               // [R]
     int32_t *G;               // [2][kB][64] published fields of a block
-    int8_t *T;                // [2][kB][32][kC] tile J[P_q][P_q]
-    int8_t *T2;               // [2][kB][32][kC] tile J[P_{q-1}][P_q]
+    uint32_t *T;              // [2][kB][kC] bit tile J[P_q][P_q]
+    uint32_t *T2;             // [2][kB][kC] bit tile J[P_{q-1}][P_q]
     unsigned long long *flip; // [3][kB] replica bit masks of flips
     unsigned long long *snew; // [3][kB] replica bit masks of the new spin (+1)
     GridBar *bar;
@@ -457,24 +468,61 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         after + ((((size_t)R * rw * 4) + 15) & ~(size_t)15));
     unsigned long long *sprev = fprev + kB;
     int32_t *Pprev = reinterpret_cast<int32_t *>(sprev + kB);
-    int32_t *Pring = Pprev + kB;                       // positions of block b in slot b % 3 (TCU)
+    int32_t *Pring = Pprev + kB;                       // positions of block b in slot b % 4 (TCU)
     int32_t *Pcur = Pring;
     int32_t *Pnext = Pring + kB;
-    int32_t *flist = Pring + 3 * kB;
+    int32_t *flist = Pring + 4 * kB;
     int32_t *ownl = flist + kB;                        // TCU: block positions owned by this CTA
-    auto ring_slot = [&](int32_t b) { return Pring + (size_t)(b % 3) * kB; };
+    auto ring_slot = [&](int32_t b) { return Pring + (size_t)(b & 3) * kB; };
     // ---------------- chain CTA shared memory
     const int cg = blockIdx.x - a.n_upd;               // chain group (4 replicas)
     const int32_t nw = (n + 31) / 32;
-    int8_t *tile = reinterpret_cast<int8_t *>(sm);                 // J[P_q][P_q]
-    int8_t *tile2 = tile + (size_t)kB * kB;                        // J[P_{q-1}][P_q]
-    uint32_t *cbits = reinterpret_cast<uint32_t *>(tile2 + (size_t)kB * kB);
+    uint32_t *tile = reinterpret_cast<uint32_t *>(sm);             // J[P_q][P_q]
+    uint32_t *tile2 = tile + (size_t)kB * kC;                      // J[P_{q-1}][P_q]
+    uint32_t *cbits = tile2 + (size_t)kB * kC;
     uint64_t *win = reinterpret_cast<uint64_t *>(cbits + (((size_t)4 * nw + 3) & ~(size_t)3));
     int32_t *Gs = reinterpret_cast<int32_t *>(win + kWin);
-    int32_t *thr = Gs + 4 * kB;
+    int32_t *thr = Gs + 4 * kB;                                     // [4][kB]
     int32_t *Pc = thr + 4 * kB;
     unsigned long long *cfm = reinterpret_cast<unsigned long long *>(Pc + kB);
     unsigned long long *csn = cfm + kB;
+    // thresholds of block qb for the group's 4 replicas (Eq. 4 / Metropolis
+    // inverted to field values), one (position, replica) per thread of
+    // tid0 .. tid0 + nthr - 1
+    auto thresholds = [&](int32_t qb, int32_t tid0, int32_t nthr) {
+        const int32_t *P = block_pos(qb);
+        const int32_t cnt = block_cnt(qb);
+        const int32_t sw = qb / nb;
+        const bool inwin = s_wn <= kWin;
+        for (int32_t x = (int32_t)threadIdx.x - tid0; x < 4 * cnt; x += nthr) {
+            const int32_t m = x >> 2;
+            const int qq = x & 3;
+            const u32x4 u = philox_rk((uint32_t)P[m], (uint32_t)sw, (uint32_t)a.t,
+                                      (kTagFlip << 24) | (uint32_t)cg, a.K);
+            const uint64_t uq = (uint64_t)(qq == 0 ? u.x : qq == 1 ? u.y : qq == 2 ? u.z : u.w);
+            int32_t res;
+            if (a.rule == 0) {
+                // smallest h with T(h) > u: s = +1 iff h >= res
+                int32_t lo = 0, hi = inwin ? s_wn - 1 : 2 * a.Hc + 1;
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi) >> 1;
+                    const uint64_t tv = inwin ? win[mid] : a.tab[mid];
+                    if (tv > uq) hi = mid; else lo = mid + 1;
+                }
+                res = (inwin ? lo + s_wlo : lo) - a.Hc;
+            } else {
+                // largest x with T_M(2x) > u: flip iff s*h <= res
+                int32_t lo = 0, hi = inwin ? s_wn - 1 : a.Hc;
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi + 1) >> 1;
+                    const uint64_t tv = inwin ? win[mid] : a.tab[mid];
+                    if (tv > uq) lo = mid; else hi = mid - 1;
+                }
+                res = (lo == a.Hc && a.Hc >= n) ? n + 1 : lo;
+            }
+            thr[qq * kB + m] = res;
+        }
+    };
 
     // update CTAs: publish the fields of block qn's positions they own, and
     // gather their share of the tiles J[P_qn][P_qn] and J[P_{qn-1}][P_qn]
@@ -532,64 +580,65 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     };
     auto publish_tiles = [&](int32_t qn) {
         const int32_t cnt = block_cnt(qn);
-        const int32_t per = (2 * kB * kB + a.n_upd - 1) / a.n_upd;
-        const int32_t e0 = blockIdx.x * per, e1 = min(2 * kB * kB, e0 + per);
+        const int32_t per = (kTileWords + a.n_upd - 1) / a.n_upd;
+        const int32_t w0 = blockIdx.x * per, w1 = min(kTileWords, w0 + per);
         const int32_t cntp = qn > 0 ? block_cnt(qn - 1) : 0;
-        int8_t *Tq = a.T + (size_t)(qn & 1) * kB * kB;
-        int8_t *T2q = a.T2 + (size_t)(qn & 1) * kB * kB;
-        for (int32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const int32_t which = e / (kB * kB), ee = e % (kB * kB);
-            const int32_t m = ee / kB, m2 = ee % kB;
-            int8_t v = 0;
+        for (int32_t wd = w0 + warp; wd < w1; wd += kSwThreads / 32) {   // warp-uniform
+            const int32_t which = wd / (kB * kC), ee = wd % (kB * kC);
+            const int32_t m = ee / kC, m2 = (ee % kC) * 32 + lane;
+            bool pos = false;
             if (which == 0) {
-                if (m < cnt && m2 < cnt) v = (int8_t)e4m3_pm1(a.J[(size_t)Pnext[m] * n + Pnext[m2]]);
-                Tq[(size_t)m * kB + (m2 & 31) * kC + (m2 >> 5)] = v;
+                if (m < cnt && m2 < cnt) pos = e4m3_pm1(a.J[(size_t)Pnext[m] * n + Pnext[m2]]) > 0;
             } else {
-                if (m < cntp && m2 < cnt) v = (int8_t)e4m3_pm1(a.J[(size_t)Pcur[m] * n + Pnext[m2]]);
-                T2q[(size_t)m * kB + (m2 & 31) * kC + (m2 >> 5)] = v;
+                if (m < cntp && m2 < cnt) pos = e4m3_pm1(a.J[(size_t)Pcur[m] * n + Pnext[m2]]) > 0;
             }
+            const uint32_t word = __ballot_sync(0xffffffffu, pos);
+            if (lane == 0) (which == 0 ? a.T : a.T2)[(size_t)(qn & 1) * kB * kC + ee] = word;
         }
     };
 
-    // TCU: this CTA's share of the tiles of a block is loaded one phase ahead
-    // (issued before the grid barrier, two independent loads per thread held
-    // in registers as raw bytes) and stored in the next phase
+    // TCU: this CTA's share of the tiles of block q+2 is loaded between its
+    // arrival at the grid barrier that ends phase q and its wait (a warp's
+    // first two tile words held in registers as raw coupling bytes, one per
+    // lane; the scattered single-byte loads keep the load pipeline busy for a
+    // while, which costs least there) and packed and stored in phase q+1
     uint32_t tvA = 0u, tvB = 0u;
-    int32_t teA = -1, teB = -1;
+    bool tokA = false, tokB = false;   // the lane's coupling lies inside the block
+    int32_t teA = -1, teB = -1;        // warp-uniform word indices
+    auto tile_src = [&](int32_t qn, int32_t wd) -> const uint8_t * {   // nullptr: outside the block
+        const int32_t cnt = block_cnt(qn), cntc = block_cnt(qn - 1);
+        const int32_t *Pn = ring_slot(qn), *Pc = ring_slot(qn - 1);
+        const int32_t which = wd / (kB * kC), ee = wd % (kB * kC);
+        const int32_t m = ee / kC, m2 = (ee % kC) * 32 + lane;
+        if (which == 0) return (m < cnt && m2 < cnt) ? a.J + (size_t)Pn[m] * n + Pn[m2] : nullptr;
+        return (m < cntc && m2 < cnt) ? a.J + (size_t)Pc[m] * n + Pn[m2] : nullptr;
+    };
+    auto tile_word_store = [&](int32_t qn, int32_t wd, uint32_t raw) {
+        const uint32_t word = __ballot_sync(0xffffffffu, e4m3_pm1(raw) > 0);
+        const int32_t which = wd / (kB * kC), ee = wd % (kB * kC);
+        if (lane == 0) (which == 0 ? a.T : a.T2)[(size_t)(qn & 1) * kB * kC + ee] = word;
+    };
     auto tile_issue = [&](int32_t qn) {
         teA = teB = -1;
         if (qn >= total) return;
-        const int32_t cnt = block_cnt(qn), cntc = block_cnt(qn - 1);
-        const int32_t *Pn = ring_slot(qn), *Pc = ring_slot(qn - 1);
-        const int32_t per = (2 * kB * kB + a.n_upd - 1) / a.n_upd;
-        const int32_t e0 = blockIdx.x * per, e1 = min(2 * kB * kB, e0 + per);
-        auto tile_src = [&](int32_t e) -> const uint8_t * {   // nullptr: outside the block
-            const int32_t which = e / (kB * kB), ee = e % (kB * kB);
-            const int32_t m = ee / kB, m2 = ee % kB;
-            if (which == 0) return (m < cnt && m2 < cnt) ? a.J + (size_t)Pn[m] * n + Pn[m2] : nullptr;
-            return (m < cntc && m2 < cnt) ? a.J + (size_t)Pc[m] * n + Pn[m2] : nullptr;
-        };
-        const int32_t ea = e0 + (int32_t)threadIdx.x, eb = ea + (int32_t)blockDim.x;
-        tvA = tvB = 0u;
-        if (ea < e1) { teA = ea; const uint8_t *src = tile_src(ea); if (src) tvA = *src; }
-        if (eb < e1) { teB = eb; const uint8_t *src = tile_src(eb); if (src) tvB = *src; }
-        for (int32_t e = ea + 2 * (int32_t)blockDim.x; e < e1; e += blockDim.x) {   // > 2 per thread: now
-            const uint8_t *src = tile_src(e);
-            const int32_t which = e / (kB * kB), ee = e % (kB * kB);
-            int8_t *Tq = (which == 0 ? a.T : a.T2) + (size_t)(qn & 1) * kB * kB;
-            Tq[(size_t)(ee / kB) * kB + ((ee % kB) & 31) * kC + ((ee % kB) >> 5)] =
-                src ? (int8_t)e4m3_pm1(*src) : (int8_t)0;
+        // warps 1.. only: warp 0 polls the grid barrier meanwhile
+        if (warp == 0) return;
+        const int32_t per = (kTileWords + a.n_upd - 1) / a.n_upd;
+        const int32_t w0 = blockIdx.x * per, w1 = min(kTileWords, w0 + per);
+        constexpr int kNW = kSwThreads / 32 - 1;
+        const int32_t wa = w0 + warp - 1, wb = wa + kNW;
+        // unconditional loads (from J[0][0] outside the block), so that nothing
+        // waits for them before the next phase
+        if (wa < w1) { teA = wa; const uint8_t *src = tile_src(qn, wa); tokA = src != nullptr; tvA = *(tokA ? src : a.J); }
+        if (wb < w1) { teB = wb; const uint8_t *src = tile_src(qn, wb); tokB = src != nullptr; tvB = *(tokB ? src : a.J); }
+        for (int32_t wd = wa + 2 * kNW; wd < w1; wd += kNW) {   // more than two words per warp: now
+            const uint8_t *src = tile_src(qn, wd);
+            tile_word_store(qn, wd, src ? (uint32_t)*src : 0u);
         }
     };
     auto tile_flush = [&](int32_t qn) {
-        auto tile_store = [&](int32_t e, uint32_t raw) {
-            const int32_t which = e / (kB * kB), ee = e % (kB * kB);
-            const int32_t m = ee / kB, m2 = ee % kB;
-            int8_t *Tq = (which == 0 ? a.T : a.T2) + (size_t)(qn & 1) * kB * kB;
-            Tq[(size_t)m * kB + (m2 & 31) * kC + (m2 >> 5)] = (int8_t)e4m3_pm1(raw);
-        };
-        if (teA >= 0) tile_store(teA, tvA);
-        if (teB >= 0) tile_store(teB, tvB);
+        if (teA >= 0) tile_word_store(qn, teA, tokA ? tvA : 0u);
+        if (teB >= 0) tile_word_store(qn, teB, tokB ? tvB : 0u);
     };
 
     // ---------------- prologue
@@ -644,8 +693,9 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         if (total > 0) {
             if constexpr (TCU) {
                 Pnext = ring_slot(0);
-                Pcur = ring_slot(2);
-                if (total > 1 && (int)threadIdx.x < block_cnt(1)) ring_slot(1)[threadIdx.x] = block_pos(1)[threadIdx.x];
+                Pcur = ring_slot(3);
+                for (int32_t b = 1; b <= 2; ++b)
+                    if (total > b && (int)threadIdx.x < block_cnt(b)) ring_slot(b)[threadIdx.x] = block_pos(b)[threadIdx.x];
             }
             publish_lists(0);
             publish_G(0);
@@ -714,12 +764,21 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     for (int32_t q = 0; alive && q <= total; ++q) {
         if (upd) {
             bool issued = false;   // TCU: MMAs of this phase in flight
-            // TCU: start the independent loads first -- this CTA's share of the
-            // tiles of block q+1 (positions already in the ring) and the
-            // positions of block q+2 -- so their latency overlaps the update
-            int32_t pn2 = -1;
-            if constexpr (TCU)
-                if (q + 2 < total && (int)threadIdx.x < block_cnt(q + 2)) pn2 = block_pos(q + 2)[threadIdx.x];
+            // the independent loads go first: block q-1's flip masks and (TCU)
+            // the positions of block q+3 (unconditional, from a clamped index:
+            // nothing waits for them here)
+            unsigned long long fl_in = 0ull, sn_in = 0ull;
+            if (q > 0 && (int)threadIdx.x < block_cnt(q - 1)) {
+                fl_in = a.flip[((q - 1) % 3) * kB + threadIdx.x];
+                sn_in = a.snew[((q - 1) % 3) * kB + threadIdx.x];
+            }
+            int32_t pn3 = -1;
+            bool pn3_ok = false;
+            if constexpr (TCU) {
+                const int32_t q3 = min(q + 3, total - 1);
+                pn3_ok = q + 3 < total && (int)threadIdx.x < block_cnt(q3);
+                pn3 = block_pos(q3)[min((int32_t)threadIdx.x, block_cnt(q3) - 1)];
+            }
             // ---- apply block q-1 to the owned rows
             if (q > 0) {
                 const int32_t qp = q - 1;
@@ -729,10 +788,10 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 __syncthreads();
                 if ((int)threadIdx.x < cntp) {
                     const int32_t m = threadIdx.x;
-                    const unsigned long long f = a.flip[(qp % 3) * kB + m];
+                    const unsigned long long f = fl_in;
                     const int32_t p = P[m];
                     fprev[m] = f;
-                    sprev[m] = a.snew[(qp % 3) * kB + m];
+                    sprev[m] = sn_in;
                     Pprev[m] = p;
                     if (f != 0ull) {
                         flist[atomicAdd(&s_nl, 1)] = m;
@@ -865,8 +924,8 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             // ---- publish block q+1 (TCU: the tiles while the MMAs run, the fields after them)
             if constexpr (TCU) {
                 if (q + 1 < total) tile_flush(q + 1);
-                __syncthreads();   // every thread is past its reads of ring slot q-1
-                if (pn2 >= 0) ring_slot(q + 2)[threadIdx.x] = pn2;
+                __syncthreads();   // every thread is past its reads of ring slot q-1 (= slot q+3)
+                if (pn3_ok) ring_slot(q + 3)[threadIdx.x] = pn3;
                 if (q + 1 < total) {
                     // owned positions of block q+1
                     const int32_t *Pn = ring_slot(q + 1);
@@ -889,7 +948,6 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                     tc_fence_after();
                 }
                 if (q + 1 < total) publish_G(q + 1);
-                tile_issue(q + 2);   // completes during the barrier; stored next phase
             } else if (q + 1 < total) {
                 publish_lists(q + 1);
                 publish_G(q + 1);
@@ -898,7 +956,6 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         } else if (q < total) {
             const int32_t *P = block_pos(q);
             const int32_t cnt = block_cnt(q);
-            const int32_t sw = q / nb;
             const int32_t cntp = q > 0 ? block_cnt(q - 1) : 0;
             if (blockIdx.x == a.n_upd && threadIdx.x < kB) {   // buffer of block q+1 starts empty
                 a.flip[((q + 1) % 3) * kB + threadIdx.x] = 0ull;
@@ -906,54 +963,27 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             }
             // the two tiles stream in while the thresholds are computed
             {
-                const int8_t *Tq = a.T + (size_t)(q & 1) * kB * kB;
-                const int8_t *T2q = a.T2 + (size_t)(q & 1) * kB * kB;
-                for (int32_t x = threadIdx.x; x < kB * kB / 16; x += blockDim.x) {
-                    cp_async16(tile + (size_t)x * 16, Tq + (size_t)x * 16);
-                    if (q > 0) cp_async16(tile2 + (size_t)x * 16, T2q + (size_t)x * 16);
+                const uint32_t *Tq = a.T + (size_t)(q & 1) * kB * kC;
+                const uint32_t *T2q = a.T2 + (size_t)(q & 1) * kB * kC;
+                for (int32_t x = threadIdx.x; x < kB * kC / 4; x += blockDim.x) {
+                    cp_async16(tile + (size_t)x * 4, Tq + (size_t)x * 4);
+                    if (q > 0) cp_async16(tile2 + (size_t)x * 4, T2q + (size_t)x * 4);
                 }
                 cp_async_commit();
             }
-            // thresholds of block q for the group's 4 replicas (Eq. 4 /
-            // Metropolis inverted to field values)
-            for (int32_t m = threadIdx.x; m < cnt; m += blockDim.x) {
-                const int32_t k = P[m];
-                Pc[m] = k;
-                const u32x4 u = philox_rk((uint32_t)k, (uint32_t)sw, (uint32_t)a.t,
-                                          (kTagFlip << 24) | (uint32_t)cg, a.K);
-                const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
-                const bool inwin = s_wn <= kWin;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    int32_t res;
-                    const uint64_t uq = (uint64_t)uw[qq];
-                    if (a.rule == 0) {
-                        // smallest h with T(h) > u: s = +1 iff h >= res
-                        int32_t lo = 0, hi = inwin ? s_wn - 1 : 2 * a.Hc + 1;
-                        while (lo < hi) {
-                            const int32_t mid = (lo + hi) >> 1;
-                            const uint64_t tv = inwin ? win[mid] : a.tab[mid];
-                            if (tv > uq) hi = mid; else lo = mid + 1;
-                        }
-                        res = (inwin ? lo + s_wlo : lo) - a.Hc;
-                    } else {
-                        // largest x with T_M(2x) > u: flip iff s*h <= res
-                        int32_t lo = 0, hi = inwin ? s_wn - 1 : a.Hc;
-                        while (lo < hi) {
-                            const int32_t mid = (lo + hi + 1) >> 1;
-                            const uint64_t tv = inwin ? win[mid] : a.tab[mid];
-                            if (tv > uq) lo = mid; else hi = mid - 1;
-                        }
-                        res = (lo == a.Hc && a.Hc >= n) ? n + 1 : lo;
-                    }
-                    thr[qq * kB + m] = res;
-                }
-            }
+            if ((int)threadIdx.x < cnt) Pc[threadIdx.x] = P[threadIdx.x];
+            thresholds(q, 0, blockDim.x);
             const int32_t *Gq = a.G + (size_t)(q & 1) * kB * 64;
-            for (int32_t x = threadIdx.x; x < 4 * cnt; x += blockDim.x) {
-                const int qq = x / cnt, m = x % cnt;
-                const int r = cg * 4 + qq;
-                Gs[qq * kB + m] = r < R ? Gq[m * 64 + r] : 0;
+            {
+                // both of a thread's loads in flight before either store
+                static_assert(4 * kB <= 2 * kSwThreads, "two published fields per thread");
+                const int32_t x0 = threadIdx.x, x1 = x0 + blockDim.x;
+                const int r0 = cg * 4 + x0 / max(cnt, 1), r1 = cg * 4 + x1 / max(cnt, 1);
+                const bool ok0 = x0 < 4 * cnt && r0 < R, ok1 = x1 < 4 * cnt && r1 < R;
+                const int32_t g0 = ok0 ? Gq[(x0 % cnt) * 64 + r0] : 0;
+                const int32_t g1 = ok1 ? Gq[(x1 % cnt) * 64 + r1] : 0;
+                if (x0 < 4 * cnt) Gs[(x0 / cnt) * kB + x0 % cnt] = g0;
+                if (x1 < 4 * cnt) Gs[(x1 / cnt) * kB + x1 % cnt] = g1;
             }
             if (q > 0 && (int)threadIdx.x < cntp) {
                 cfm[threadIdx.x] = a.flip[((q - 1) % 3) * kB + threadIdx.x];
@@ -976,8 +1006,12 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                     const int32_t k = ok ? Pc[m] : 0;
                     smask[s2] = __ballot_sync(0xffffffffu, ok && ((bits[k >> 5] >> (k & 31)) & 1u));
                 }
-                // block q-1's flips, which the published fields do not include yet
+                // block q-1's flips, which the published fields do not include yet.
+                // Blocks of one sweep are disjoint; at a seam (block q-1 ends the
+                // previous sweep) the two blocks can share vertices
                 if (q > 0) {
+                    const bool seam = (q % nb) == 0;
+                    const int32_t *Pprv = block_pos(q - 1);
 #pragma unroll
                     for (int s2 = 0; s2 < kC; ++s2) {
                         const int32_t mp = s2 * 32 + lane;
@@ -988,11 +1022,17 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                             bal &= bal - 1;
                             const int32_t m = s2 * 32 + o;
                             const int32_t d = ((csn[m] >> r) & 1ull) ? 2 : -2;
-                            const int2 tv = *reinterpret_cast<const int2 *>(tile2 + (size_t)m * kB + lane * kC);
+                            const uint4 t0 = *reinterpret_cast<const uint4 *>(tile2 + (size_t)m * kC);
+                            const uint4 t1 = *reinterpret_cast<const uint4 *>(tile2 + (size_t)m * kC + 4);
+                            const uint32_t tw[kC] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
-                            for (int s3 = 0; s3 < kC; ++s3) {
-                                const uint32_t word = s3 < 4 ? (uint32_t)tv.x : (uint32_t)tv.y;
-                                f[s3] += d * (int32_t)(int8_t)((word >> (8 * (s3 & 3))) & 0xFFu);
+                            for (int s3 = 0; s3 < kC; ++s3) f[s3] += ((tw[s3] >> lane) & 1u) ? d : -d;
+                            if (seam) {
+                                // J_vv = 0 where the vertex is also in block q: undo the -d of its clear bit
+                                const int32_t v = Pprv[m];
+#pragma unroll
+                                for (int s3 = 0; s3 < kC; ++s3)
+                                    if (s3 * 32 + lane < cnt && Pc[s3 * 32 + lane] == v) f[s3] += d;
                             }
                         }
                     }
@@ -1022,12 +1062,12 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                         open &= ~((2u << o) - 1u);        // positions up to o are decided
                         const int32_t m = mb + o;
                         const int32_t d = ((smask[s2] >> o) & 1u) ? -2 : 2;   // the spin turns over
-                        const int2 tv = *reinterpret_cast<const int2 *>(tile + (size_t)m * kB + lane * kC);
+                        // (the diagonal bit is arbitrary: position m is decided)
+                        const uint4 t0 = *reinterpret_cast<const uint4 *>(tile + (size_t)m * kC);
+                        const uint4 t1 = *reinterpret_cast<const uint4 *>(tile + (size_t)m * kC + 4);
+                        const uint32_t tw[kC] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
-                        for (int s3 = 0; s3 < kC; ++s3) {
-                            const uint32_t word = s3 < 4 ? (uint32_t)tv.x : (uint32_t)tv.y;
-                            f[s3] += d * (int32_t)(int8_t)((word >> (8 * (s3 & 3))) & 0xFFu);
-                        }
+                        for (int s3 = 0; s3 < kC; ++s3) f[s3] += ((tw[s3] >> lane) & 1u) ? d : -d;
                         if (lane == 0) {
                             const int32_t k = Pc[m];
                             bits[k >> 5] ^= 1u << (k & 31);
@@ -1038,7 +1078,9 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 }
             }
         }
-        if (!grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok)) { alive = false; break; }
+        grid_arrive(a.bar);
+        if (upd && TCU) tile_issue(q + 2);
+        if (!grid_wait(a.bar, nblocks, gen, a.ctl, &s_ok)) { alive = false; break; }
     }
 
     // ---------------- energies E_r = -1/2 sum_j s_j h_j, fields and spins back to HBM
@@ -1234,12 +1276,12 @@ int dense_block_positions() { return kB; }
 // Shared memory of the sweep kernel for a given split.
 size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu) {
     const size_t rest = ((((size_t)R * ((rows_per + 31) / 32) * 4) + 15) & ~(size_t)15) +
-                        (size_t)kB * (8 + 8 + 4 + 12 + 4 + 4);
+                        (size_t)kB * (8 + 8 + 4 + 16 + 4 + 4);
     const size_t ntiles = ((size_t)rows_per + 127) / 128;
     const size_t upd = tcu ? 1024 + 2 * ntiles * kTuTileBytes + 2 * kTuBSlice + rest
                            : (((size_t)R * rows_per * 4 + 15) & ~(size_t)15) + rest;
     const size_t nw = (size_t)((n + 31) / 32);
-    const size_t chn = 2 * (size_t)kB * kB + ((4 * nw + 3) & ~(size_t)3) * 4 + (size_t)kWin * 8 +
+    const size_t chn = 2 * (size_t)kB * kC * 4 + ((4 * nw + 3) & ~(size_t)3) * 4 + (size_t)kWin * 8 +
                        (size_t)kB * (4 * 4 + 4 * 4 + 4 + 8 + 8);
     return upd > chn ? upd : chn;
 }
@@ -1249,7 +1291,7 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
                                const int8_t *J, const int32_t *perm, const uint64_t *tab,
                                const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int32_t *H, int8_t *dst, int64_t *E,
-                               int32_t *G, int8_t *T, int8_t *T2, unsigned long long *flip,
+                               int32_t *G, uint32_t *T, uint32_t *T2, unsigned long long *flip,
                                unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st, bool tcu) {
     DenseSweepArgs a;
     a.n = n; a.R = R; a.S = S; a.rule = rule; a.Hc = Hc; a.n_upd = n_upd; a.rows_per = rows_per;

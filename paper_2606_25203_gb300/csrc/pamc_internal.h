@@ -230,7 +230,7 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
                                const int8_t *J, const int32_t *perm, const uint64_t *tab,
                                const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int32_t *H, int8_t *dst, int64_t *E,
-                               int32_t *G, int8_t *T, int8_t *T2, unsigned long long *flip,
+                               int32_t *G, uint32_t *T, uint32_t *T2, unsigned long long *flip,
                                unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st, bool tcu);
 cudaError_t launch_dense_to_e4m3(size_t total, int8_t *J, cudaStream_t st);
 
