@@ -486,42 +486,61 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     int32_t *Pc = thr + 4 * kB;
     unsigned long long *cfm = reinterpret_cast<unsigned long long *>(Pc + kB);
     unsigned long long *csn = cfm + kB;
+    uint32_t *udraw = reinterpret_cast<uint32_t *>(csn + kB);      // [4][kB] draws of a block
     // thresholds of block qb for the group's 4 replicas (Eq. 4 / Metropolis
-    // inverted to field values), one (position, replica) per thread of
-    // tid0 .. tid0 + nthr - 1
-    auto thresholds = [&](int32_t qb, int32_t tid0, int32_t nthr) {
-        const int32_t *P = block_pos(qb);
+    // inverted to field values): one Philox call per position (its four words
+    // are the four replicas' draws), then one (position, replica) item per
+    // thread and a second one for the first 4 kB - blockDim threads, both
+    // binary searches run in step so that their table reads overlap.
+    // Positions are read from Pc; every thread of the CTA calls it.
+    auto thresholds = [&](int32_t qb) {
+        static_assert(4 * kB <= 2 * kSwThreads, "two threshold items per thread");
         const int32_t cnt = block_cnt(qb);
         const int32_t sw = qb / nb;
         const bool inwin = s_wn <= kWin;
-        for (int32_t x = (int32_t)threadIdx.x - tid0; x < 4 * cnt; x += nthr) {
-            const int32_t m = x >> 2;
-            const int qq = x & 3;
-            const u32x4 u = philox_rk((uint32_t)P[m], (uint32_t)sw, (uint32_t)a.t,
+        if ((int)threadIdx.x < cnt) {
+            const u32x4 u = philox_rk((uint32_t)Pc[threadIdx.x], (uint32_t)sw, (uint32_t)a.t,
                                       (kTagFlip << 24) | (uint32_t)cg, a.K);
-            const uint64_t uq = (uint64_t)(qq == 0 ? u.x : qq == 1 ? u.y : qq == 2 ? u.z : u.w);
-            int32_t res;
-            if (a.rule == 0) {
-                // smallest h with T(h) > u: s = +1 iff h >= res
-                int32_t lo = 0, hi = inwin ? s_wn - 1 : 2 * a.Hc + 1;
-                while (lo < hi) {
-                    const int32_t mid = (lo + hi) >> 1;
-                    const uint64_t tv = inwin ? win[mid] : a.tab[mid];
-                    if (tv > uq) hi = mid; else lo = mid + 1;
-                }
-                res = (inwin ? lo + s_wlo : lo) - a.Hc;
-            } else {
-                // largest x with T_M(2x) > u: flip iff s*h <= res
-                int32_t lo = 0, hi = inwin ? s_wn - 1 : a.Hc;
-                while (lo < hi) {
-                    const int32_t mid = (lo + hi + 1) >> 1;
-                    const uint64_t tv = inwin ? win[mid] : a.tab[mid];
-                    if (tv > uq) lo = mid; else hi = mid - 1;
-                }
-                res = (lo == a.Hc && a.Hc >= n) ? n + 1 : lo;
-            }
-            thr[qq * kB + m] = res;
+            udraw[threadIdx.x] = u.x;
+            udraw[kB + threadIdx.x] = u.y;
+            udraw[2 * kB + threadIdx.x] = u.z;
+            udraw[3 * kB + threadIdx.x] = u.w;
         }
+        __syncthreads();
+        const int32_t xa = threadIdx.x, xb = xa + blockDim.x;
+        if (xa >= 4 * cnt) return;
+        const bool vb = xb < 4 * cnt;
+        const int32_t ma = xa >> 2, mb = vb ? (xb >> 2) : ma;
+        const uint64_t uqa = udraw[(xa & 3) * kB + ma], uqb = udraw[(xb & 3) * kB + mb];
+        auto tv = [&](int32_t i) -> uint64_t { return inwin ? win[i] : a.tab[i]; };
+        int32_t ra, rb;
+        if (a.rule == 0) {
+            // smallest h with T(h) > u: s = +1 iff h >= res
+            const int32_t top = inwin ? s_wn - 1 : 2 * a.Hc + 1;
+            int32_t loa = 0, hia = top, lob = 0, hib = vb ? top : 0;
+            while (loa < hia || lob < hib) {
+                const int32_t mida = (loa + hia) >> 1, midb = (lob + hib) >> 1;
+                const uint64_t ta = loa < hia ? tv(mida) : 0ull, tb = lob < hib ? tv(midb) : 0ull;
+                if (loa < hia) { if (ta > uqa) hia = mida; else loa = mida + 1; }
+                if (lob < hib) { if (tb > uqb) hib = midb; else lob = midb + 1; }
+            }
+            ra = (inwin ? loa + s_wlo : loa) - a.Hc;
+            rb = (inwin ? lob + s_wlo : lob) - a.Hc;
+        } else {
+            // largest x with T_M(2x) > u: flip iff s*h <= res
+            const int32_t top = inwin ? s_wn - 1 : a.Hc;
+            int32_t loa = 0, hia = top, lob = 0, hib = vb ? top : 0;
+            while (loa < hia || lob < hib) {
+                const int32_t mida = (loa + hia + 1) >> 1, midb = (lob + hib + 1) >> 1;
+                const uint64_t ta = loa < hia ? tv(mida) : 0ull, tb = lob < hib ? tv(midb) : 0ull;
+                if (loa < hia) { if (ta > uqa) loa = mida; else hia = mida - 1; }
+                if (lob < hib) { if (tb > uqb) lob = midb; else hib = midb - 1; }
+            }
+            ra = (loa == a.Hc && a.Hc >= n) ? n + 1 : loa;
+            rb = (lob == a.Hc && a.Hc >= n) ? n + 1 : lob;
+        }
+        thr[(xa & 3) * kB + ma] = ra;
+        if (vb) thr[(xb & 3) * kB + mb] = rb;
     };
 
     // update CTAs: publish the fields of block qn's positions they own, and
@@ -600,8 +619,9 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     // TCU: this CTA's share of the tiles of block q+2 is loaded between its
     // arrival at the grid barrier that ends phase q and its wait (a warp's
     // first two tile words held in registers as raw coupling bytes, one per
-    // lane; the scattered single-byte loads keep the load pipeline busy for a
-    // while, which costs least there) and packed and stored in phase q+1
+    // lane) and packed and stored in phase q+1.  The entries are single bytes
+    // at scattered places of J: their misses occupy the load pipeline for a
+    // while, which costs least there.
     uint32_t tvA = 0u, tvB = 0u;
     bool tokA = false, tokB = false;   // the lane's coupling lies inside the block
     int32_t teA = -1, teB = -1;        // warp-uniform word indices
@@ -621,7 +641,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     auto tile_issue = [&](int32_t qn) {
         teA = teB = -1;
         if (qn >= total) return;
-        // warps 1.. only: warp 0 polls the grid barrier meanwhile
+        // warps 1..: warp 0 polls the grid barrier meanwhile
         if (warp == 0) return;
         const int32_t per = (kTileWords + a.n_upd - 1) / a.n_upd;
         const int32_t w0 = blockIdx.x * per, w1 = min(kTileWords, w0 + per);
@@ -760,6 +780,8 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             for (int32_t i = threadIdx.x; i < s_wn; i += blockDim.x) win[i] = a.tab[s_wlo + i];
     }
     uint32_t mphase = 0;     // TCU: completed phases of s_mbar
+    // chain CTAs: this thread's position of the next block, loaded a phase ahead
+    int32_t pcn = (!upd && total > 0) ? block_pos(0)[min((int32_t)threadIdx.x, block_cnt(0) - 1)] : 0;
     bool alive = grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok);
     for (int32_t q = 0; alive && q <= total; ++q) {
         if (upd) {
@@ -954,14 +976,24 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 publish_tiles(q + 1);
             }
         } else if (q < total) {
-            const int32_t *P = block_pos(q);
             const int32_t cnt = block_cnt(q);
             const int32_t cntp = q > 0 ? block_cnt(q - 1) : 0;
+            if ((int)threadIdx.x < cnt) Pc[threadIdx.x] = pcn;   // loaded last phase
             if (blockIdx.x == a.n_upd && threadIdx.x < kB) {   // buffer of block q+1 starts empty
                 a.flip[((q + 1) % 3) * kB + threadIdx.x] = 0ull;
                 a.snew[((q + 1) % 3) * kB + threadIdx.x] = 0ull;
             }
-            // the two tiles stream in while the thresholds are computed
+            // the independent loads first: the published fields, block q-1's
+            // flip masks and the two tiles; they complete while the
+            // thresholds are computed
+            // (unconditional loads from clamped indices: nothing waits for
+            // them until they are stored after the thresholds).  A position's
+            // four fields of the group are 16 contiguous bytes.
+            const int32_t *Gq = a.G + (size_t)(q & 1) * kB * 64;
+            const int4 g4 = *reinterpret_cast<const int4 *>(Gq + (size_t)min((int32_t)threadIdx.x, cnt - 1) * 64 + cg * 4);
+            const bool okm = q > 0 && (int)threadIdx.x < cntp;
+            const size_t mi = (size_t)(q > 0 ? (q - 1) % 3 : 0) * kB + min((int32_t)threadIdx.x, kB - 1);
+            const unsigned long long fm = a.flip[mi], sm2 = a.snew[mi];
             {
                 const uint32_t *Tq = a.T + (size_t)(q & 1) * kB * kC;
                 const uint32_t *T2q = a.T2 + (size_t)(q & 1) * kB * kC;
@@ -971,26 +1003,21 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 }
                 cp_async_commit();
             }
-            if ((int)threadIdx.x < cnt) Pc[threadIdx.x] = P[threadIdx.x];
-            thresholds(q, 0, blockDim.x);
-            const int32_t *Gq = a.G + (size_t)(q & 1) * kB * 64;
-            {
-                // both of a thread's loads in flight before either store
-                static_assert(4 * kB <= 2 * kSwThreads, "two published fields per thread");
-                const int32_t x0 = threadIdx.x, x1 = x0 + blockDim.x;
-                const int r0 = cg * 4 + x0 / max(cnt, 1), r1 = cg * 4 + x1 / max(cnt, 1);
-                const bool ok0 = x0 < 4 * cnt && r0 < R, ok1 = x1 < 4 * cnt && r1 < R;
-                const int32_t g0 = ok0 ? Gq[(x0 % cnt) * 64 + r0] : 0;
-                const int32_t g1 = ok1 ? Gq[(x1 % cnt) * 64 + r1] : 0;
-                if (x0 < 4 * cnt) Gs[(x0 / cnt) * kB + x0 % cnt] = g0;
-                if (x1 < 4 * cnt) Gs[(x1 / cnt) * kB + x1 % cnt] = g1;
+            __syncthreads();   // Pc
+            thresholds(q);
+            if ((int)threadIdx.x < cnt) {
+                const int32_t m = threadIdx.x;
+                Gs[m] = cg * 4 < R ? g4.x : 0;
+                Gs[kB + m] = cg * 4 + 1 < R ? g4.y : 0;
+                Gs[2 * kB + m] = cg * 4 + 2 < R ? g4.z : 0;
+                Gs[3 * kB + m] = cg * 4 + 3 < R ? g4.w : 0;
             }
-            if (q > 0 && (int)threadIdx.x < cntp) {
-                cfm[threadIdx.x] = a.flip[((q - 1) % 3) * kB + threadIdx.x];
-                csn[threadIdx.x] = a.snew[((q - 1) % 3) * kB + threadIdx.x];
-            }
+            if (okm) { cfm[threadIdx.x] = fm; csn[threadIdx.x] = sm2; }
             cp_async_wait_all();
             __syncthreads();
+            // positions of block q+1 for the next phase (unconditional, from a
+            // clamped index: nothing waits for them here)
+            if (q + 1 < total) pcn = block_pos(q + 1)[min((int32_t)threadIdx.x, block_cnt(q + 1) - 1)];
             if (warp < 4 && cg * 4 + warp < R) {
                 const int qq = warp;
                 const int r = cg * 4 + qq;
@@ -1282,7 +1309,7 @@ size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu) {
                            : (((size_t)R * rows_per * 4 + 15) & ~(size_t)15) + rest;
     const size_t nw = (size_t)((n + 31) / 32);
     const size_t chn = 2 * (size_t)kB * kC * 4 + ((4 * nw + 3) & ~(size_t)3) * 4 + (size_t)kWin * 8 +
-                       (size_t)kB * (4 * 4 + 4 * 4 + 4 + 8 + 8);
+                       (size_t)kB * (4 * 4 + 4 * 4 + 4 + 8 + 8 + 16);
     return upd > chn ? upd : chn;
 }
 
