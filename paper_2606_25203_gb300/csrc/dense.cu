@@ -316,7 +316,39 @@ constexpr int kB = 256;              // positions per block
 constexpr int kC = kB / 32;          // positions per lane in a chain warp
 // Chain tiles hold one bit per coupling (+1 set; J is +-1 off the diagonal):
 // row m is kC words, bit l of word c for column position 32 c + l
-constexpr int kTileWords = 2 * kB * kC;   // both tiles of a block
+// A chain applies the row of a flipped position m of its own block to the
+// positions after m only (the earlier ones are decided), so of the tile
+// J[P_q][P_q] only the words holding some column > m are produced: row m
+// needs words floor((m + 1) / 32) .. kC - 1.  Rows with the same k =
+// floor((m + 1) / 32) form a segment: rows 0..30 for k = 0, rows 32k-1 ..
+// 32k+30 for k >= 1, each with kC - k words.
+constexpr int tile_words_upper() {
+    int w = 31 * kC;
+    for (int k = 1; k < kC; ++k) w += 32 * (kC - k);
+    return w;
+}
+constexpr int kTileWordsT = tile_words_upper();
+constexpr int kTileWords = kTileWordsT + kB * kC;   // both tiles of a block
+// word wd of a block's production list -> tile (0: J[P_q][P_q], 1:
+// J[P_{q-1}][P_q]) and word index m * kC + c within it
+__device__ __forceinline__ void tile_word(int32_t wd, int &which, int32_t &ee) {
+    if (wd >= kTileWordsT) {
+        which = 1;
+        ee = wd - kTileWordsT;
+        return;
+    }
+    which = 0;
+    int32_t base = 0;
+    int k = 0;
+    for (; k < kC - 1; ++k) {
+        const int32_t words = (k == 0 ? 31 : 32) * (kC - k);
+        if (wd < base + words) break;
+        base += words;
+    }
+    const int32_t local = wd - base;
+    const int32_t m = (k == 0 ? 0 : 32 * k - 1) + local / (kC - k);
+    ee = m * kC + k + local % (kC - k);
+}
 constexpr int kWin = 4096;           // threshold entries kept in shared memory
 constexpr long long kBarCycles = 4000000000ll;   // ~2 s: a barrier wait gives up after this
 
@@ -603,7 +635,9 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         const int32_t w0 = blockIdx.x * per, w1 = min(kTileWords, w0 + per);
         const int32_t cntp = qn > 0 ? block_cnt(qn - 1) : 0;
         for (int32_t wd = w0 + warp; wd < w1; wd += kSwThreads / 32) {   // warp-uniform
-            const int32_t which = wd / (kB * kC), ee = wd % (kB * kC);
+            int which;
+            int32_t ee;
+            tile_word(wd, which, ee);
             const int32_t m = ee / kC, m2 = (ee % kC) * 32 + lane;
             bool pos = false;
             if (which == 0) {
@@ -628,14 +662,18 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     auto tile_src = [&](int32_t qn, int32_t wd) -> const uint8_t * {   // nullptr: outside the block
         const int32_t cnt = block_cnt(qn), cntc = block_cnt(qn - 1);
         const int32_t *Pn = ring_slot(qn), *Pc = ring_slot(qn - 1);
-        const int32_t which = wd / (kB * kC), ee = wd % (kB * kC);
+        int which;
+        int32_t ee;
+        tile_word(wd, which, ee);
         const int32_t m = ee / kC, m2 = (ee % kC) * 32 + lane;
         if (which == 0) return (m < cnt && m2 < cnt) ? a.J + (size_t)Pn[m] * n + Pn[m2] : nullptr;
         return (m < cntc && m2 < cnt) ? a.J + (size_t)Pc[m] * n + Pn[m2] : nullptr;
     };
     auto tile_word_store = [&](int32_t qn, int32_t wd, uint32_t raw) {
         const uint32_t word = __ballot_sync(0xffffffffu, e4m3_pm1(raw) > 0);
-        const int32_t which = wd / (kB * kC), ee = wd % (kB * kC);
+        int which;
+        int32_t ee;
+        tile_word(wd, which, ee);
         if (lane == 0) (which == 0 ? a.T : a.T2)[(size_t)(qn & 1) * kB * kC + ee] = word;
     };
     auto tile_issue = [&](int32_t qn) {
