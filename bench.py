@@ -57,11 +57,11 @@ def load_peaks():
 # only while the kernel sources still hash to what was captured.
 PROFILED_TRAFFIC = {
     # k_sweep_ising, torus 141x141, R=4096, 10 sweeps: one launch
-    "sweep_torus": (64.93e6, {"paper_2606_25203_gb300/csrc/sweep_ising.cu":
-                              "2ef365775b709862158a5691bf2075cb0d9101f1"}),
-    # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.741 GB) scaled by n^2 to n=100,000
-    "dense_sweep_100k": (1.741e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
-                                                           "61dcf4f94c020340a8522b74c8ccda28d2ea6d99"}),
+    "sweep_torus": (64.97e6, {"paper_2606_25203_gb300/csrc/sweep_ising.cu":
+                              "716b4b3f604dc859003e279035917bbf9ef6fa4d"}),
+    # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.688 GB) scaled by n^2 to n=100,000
+    "dense_sweep_100k": (1.688e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
+                                                           "3df158cc1b8b82e8b57def43d3e9a1f26901c7cb"}),
 }
 
 
@@ -663,8 +663,7 @@ def run_potts(args):
     print(json.dumps(line))
 
 
-C1_PARAMS = dict(R=128, sweeps=5, steps=50, beta0=0.1, beta1=3.0, seed=0)
-# time-to-target runs: the paper's method (stagnation control and NCM on) on the same instance
+# time-to-target runs: the paper's method (stagnation control and NCM on) on the Erdos-Renyi N=800 instance
 TTS_PARAMS = dict(R=128, sweeps=5, steps=500, beta0=0.1, beta1=3.0, stagnation=1, z_rst=400, seed=0)
 
 
