@@ -157,6 +157,57 @@ def test_dense_recompute_exact_at_large_fields(pg, n):
         pg.pamc_destroy(h)
 
 
+def test_dense_full_size_sweep_replay(pg):
+    """The sweep at full size, n = 100,000 and R = 64 (the benchmark's
+    instance and population), on sampled outputs the oracle computes one by
+    one: from a seeded population set through the ABI, one step of one sweep
+    at beta0; the first 1,024 positions of the order (four blocks, so the
+    chains, the tiles and the tensor-core field update of earlier blocks all
+    take part) are replayed sequentially on the CPU for every replica from
+    their exact fields, with the oracle's draws, order and thresholds."""
+    import torch
+    n, R, seed, K = 100000, 64, 0, 1024
+    params = dict(R=R, sweeps=1, steps=4, beta0=0.01, beta1=1.0, seed=11)
+    wd = torch.empty((n, n), dtype=torch.int8, device="cuda")
+    for r0 in range(0, n, 2000):
+        wd[r0:r0 + 2000] = -W.dense_rows_torch(n, r0, min(n, r0 + 2000), seed, device="cuda")
+    h = pg.pamc_create_dense(n, wd)
+    del wd
+    torch.cuda.empty_cache()
+    try:
+        pg.pamc_init(h, **params)
+        rng = np.random.default_rng(7)
+        S0 = np.where(rng.random((R, n)) < 0.5, 1, -1).astype(np.int8)
+        pg.pamc_set_population(h, S0)
+        pg.pamc_step(h, 1)
+        S1, _, _, _ = pg.pamc_state(h, R, n)
+    finally:
+        pg.pamc_destroy(h)
+    order = oracle.permutation(n, params["seed"], 0, 0)
+    P = order[:K]
+    JP = W.dense_rows_np(n, P, seed)                                   # couplings of the K rows
+    hcur = (JP.astype(np.float32) @ S0.T.astype(np.float32)).round().astype(np.int64)   # exact: |h| < 2^24
+    JPP = JP[:, P].astype(np.int64)                                    # couplings among the K positions
+    key = (params["seed"] & 0xFFFFFFFF, params["seed"] >> 32)
+    thr = {}
+    s = S0[:, P].astype(np.int64).T.copy()                             # K x R
+    for i in range(K):
+        k = int(P[i])
+        for g in range(R // 4):
+            u = oracle.philox4x32_10((k, 0, 0, (oracle.TAG_FLIP << 24) | g), key)
+            for q in range(4):
+                r = 4 * g + q
+                hv = int(hcur[i, r])
+                if hv not in thr:
+                    thr[hv] = oracle.thr_heatbath(params["beta0"], hv)
+                new = 1 if int(u[q]) < thr[hv] else -1
+                if new != s[i, r]:
+                    hcur[i + 1:, r] += 2 * new * JPP[i + 1:, i]
+                    s[i, r] = new
+    np.testing.assert_array_equal(S1[:, P], s.T.astype(np.int8))
+    assert (s.T != S0[:, P]).mean() > 0.2          # a hot step: the update path is exercised
+
+
 def test_set_population_sparse_and_ranges(pg):
     inst = W.torus(12, 12, signed=True, seed=3)
     h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
