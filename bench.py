@@ -409,6 +409,7 @@ def run_dense(args):
     pg.pamc_init(h, **P)
     torch.cuda.synchronize()
     l0 = pg.pamc_launch_count(h)
+    rows0, pos0 = pg.pamc_dense_rows(h)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     with ClockSampler(0) as clk:
@@ -418,6 +419,7 @@ def run_dense(args):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     pg.pamc_sync(h)
+    rows1, pos1 = pg.pamc_dense_rows(h)
     per_step = [a.elapsed_time(b) for a, b in ev]
     ms = sum(per_step)
     launches = pg.pamc_launch_count(h) - l0
@@ -455,6 +457,11 @@ def run_dense(args):
                      "peak_source": src},
         "recompute_roofline": {"bound": "hbm", "achieved": rc_gbs, "peak": hbm, "unit": "GB/s",
                                "frac": rc_gbs / hbm},
+        # the rows the flips needed: positions that flipped in at least one
+        # replica; their rows are all a sweep's field updates read of J
+        "rows_needed": {"rows": rows1 - rows0, "positions": pos1 - pos0,
+                        "fraction": (rows1 - rows0) / max(pos1 - pos0, 1),
+                        "achieved_gbs": (rows1 - rows0) * n / (ms_sweep * args.steps / 1e3) / 1e9},
         "clocks": clk.summary(), "gpu_launches": launches,
         "timed_steps": f"steps 0..{args.steps - 1} of a fresh run (beta {P['beta0']} -> {P['beta1']} over {P['steps']})",
         "ms_step_first_last": [per_step[0], per_step[-1]],

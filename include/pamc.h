@@ -163,6 +163,13 @@ pamc_status pamc_last_error(pamc_handle h, char *buf, size_t len);
  * recomputed from the definition.  PAMC_ERR_RANGE for a value out of range,
  * PAMC_ERR_STATE once the run reached its target.  Synchronises. */
 pamc_status pamc_set_population(pamc_handle h, const int8_t *spins);
+/* Dense instances: coupling rows the sweeps' field updates gathered (one per
+ * position that flipped in at least one replica; the rows a block's flips
+ * need) and positions visited, both summed since pamc_init.  An update reads
+ * the gathered rows over every field slice, so rows x n bytes is the sweep's
+ * J traffic below the n^2 bytes of one full read per sweep.  PAMC_ERR_ARG for
+ * sparse handles.  Synchronises. */
+pamc_status pamc_dense_rows(pamc_handle h, int64_t *rows_gathered, int64_t *positions_visited);
 /* Dense instances: the local fields H[r][k] = sum_j J_kj s_j of the current
  * population as the device holds them (R rows of n int32, caller-owned).
  * PAMC_ERR_ARG for sparse handles, which keep no field array. */

@@ -21,7 +21,7 @@ from . import build as _build
 __all__ = [
     "PamcError", "Params", "load", "pamc_create_csr", "pamc_create_dense", "pamc_init",
     "pamc_step", "pamc_sync", "pamc_run", "pamc_best", "pamc_state", "pamc_control_state",
-    "pamc_launch_count", "pamc_sweep_shape", "pamc_weight_sum", "pamc_last_error", "pamc_destroy", "Solver",
+    "pamc_launch_count", "pamc_sweep_shape", "pamc_dense_rows", "pamc_weight_sum", "pamc_last_error", "pamc_destroy", "Solver",
     "pamc_sweeps_noalloc", "pamc_footprint", "pamc_batch_create", "pamc_batch_add", "pamc_batch_step",
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_sweeps_noalloc.argtypes = [i32, i32, P, P, P, i32, i32, i32, i32, ctypes.c_double,
                                       ctypes.c_uint64, i32, P, P, P, P, ctypes.c_char_p,
                                       ctypes.c_size_t]
+    L.pamc_dense_rows.argtypes = [P, P, P]
     L.pamc_set_population.argtypes = [P, P]
     L.pamc_set_population.restype = ctypes.c_int
     L.pamc_fields.argtypes = [P, P]
@@ -267,6 +268,13 @@ def pamc_control_state(h) -> dict:
 
 def pamc_launch_count(h) -> int:
     return int(_lib.pamc_launch_count(h))
+
+
+def pamc_dense_rows(h) -> tuple:
+    """(coupling rows gathered by the dense field updates, positions visited) since pamc_init."""
+    v = np.zeros(2, dtype=np.int64)
+    _check(_lib.pamc_dense_rows(h, _ptr(v[0:1]), _ptr(v[1:2])), h)
+    return int(v[0]), int(v[1])
 
 
 def pamc_sweep_shape(h) -> tuple:

@@ -798,6 +798,20 @@ pamc_status pamc_set_population(pamc_handle h, const int8_t *spins) {
     return PAMC_OK;
 }
 
+pamc_status pamc_dense_rows(pamc_handle h, int64_t *rows_gathered, int64_t *positions_visited) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    if (!h->dense) return fail(h, PAMC_ERR_ARG, "pamc_dense_rows: not a dense instance");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_dense_rows before pamc_init");
+    cudaError_t e = cudaSetDevice(h->device);
+    DevCtl c;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&c, h->d_ctl, sizeof(c), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pamc_dense_rows");
+    if (rows_gathered) *rows_gathered = c.dense_rows;
+    if (positions_visited) *positions_visited = c.dense_positions;
+    return PAMC_OK;
+}
+
 pamc_status pamc_fields(pamc_handle h, int32_t *H) {
     if (!h || !H) return fail(h, PAMC_ERR_ARG, "null argument");
     if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_fields before pamc_init");

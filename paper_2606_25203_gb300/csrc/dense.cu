@@ -868,6 +868,10 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 }
                 __syncthreads();
                 const int32_t nl = s_nl;
+                if (blockIdx.x == 0 && threadIdx.x == 0) {   // the only writer
+                    a.ctl->dense_rows += nl;
+                    a.ctl->dense_positions += cntp;
+                }
                 if constexpr (TCU) {
                     if (nl > 0) {
                         // A: the flipped positions' coupling rows over this slice,

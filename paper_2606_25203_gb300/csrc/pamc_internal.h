@@ -29,6 +29,9 @@ struct DevCtl {
     int64_t mstar;        // best cut so far (INT64_MIN = none yet)
     int64_t ncm_flipped, ncm_dE_max;
     int64_t hist[kHistMax];
+    // dense sweeps: coupling rows gathered by the field update (positions
+    // that flipped in some replica) and positions visited, since pamc_init
+    int64_t dense_rows, dense_positions;
 };
 
 // Per-(t, sweep) update schedule: the random order's dependency levels.

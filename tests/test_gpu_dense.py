@@ -157,6 +157,43 @@ def test_dense_recompute_exact_at_large_fields(pg, n):
         pg.pamc_destroy(h)
 
 
+@pytest.mark.parametrize("n", [256, 1000])
+def test_dense_rows_gathered(pg, n):
+    """pamc_dense_rows counts, per sweep position, whether some replica's spin
+    turned over at its visit (the rows the field update needs).  With one
+    sweep per step every vertex is visited once, so the count is the number of
+    vertices whose value after the sweep differs, in some replica, from the
+    resampled population before it (oracle spins and parents); positions are
+    n per step."""
+    w, inst = dense_pair(n, 4)
+    params = dict(R=12, sweeps=1, steps=6, beta0=0.05, beta1=2.0, seed=3)
+    ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **params)
+    h = pg.pamc_create_dense(n, w)
+    try:
+        pg.pamc_init(h, **params)
+        want = 0
+        prev = ref.spins()
+        for _ in range(params["steps"]):
+            pg.pamc_step(h, 1)
+            ref.step(1)
+            par, _ = ref.parents()
+            cur = ref.spins()
+            want += int((cur != prev[par]).any(axis=0).sum())
+            prev = cur
+        rows, positions = pg.pamc_dense_rows(h)
+        assert positions == n * params["steps"]
+        assert rows == want
+    finally:
+        pg.pamc_destroy(h)
+    small = W.torus(6, 6, signed=True, seed=1)
+    hs = pg.pamc_create_csr(small.n, small.row_ptr, small.col, small.w)
+    try:
+        with pytest.raises(pg.PamcError):
+            pg.pamc_dense_rows(hs)
+    finally:
+        pg.pamc_destroy(hs)
+
+
 def test_dense_full_size_sweep_replay(pg):
     """The sweep at full size, n = 100,000 and R = 64 (the benchmark's
     instance and population), on sampled outputs the oracle computes one by
