@@ -329,6 +329,12 @@ constexpr int tile_words_upper() {
 }
 constexpr int kTileWordsT = tile_words_upper();
 constexpr int kTileWords = kTileWordsT + kB * kC;   // both tiles of a block
+// When few positions flip (late in an anneal most blocks have a handful),
+// the tile J[P_{q-1}][P_q] is not produced by the update CTAs: each chain CTA
+// loads the rows of the positions its own replicas flipped in block q-1 at the
+// end of that block's chain.  The update CTAs decide per block from the count
+// of flipped positions two blocks earlier (the same count in every CTA).
+constexpr int kT2Rare = 16;
 // word wd of a block's production list -> tile (0: J[P_q][P_q], 1:
 // J[P_{q-1}][P_q]) and word index m * kC + c within it
 __device__ __forceinline__ void tile_word(int32_t wd, int &which, int32_t &ee) {
@@ -379,6 +385,7 @@ __device__ __forceinline__ uint32_t tu_sw_off(int32_t row, int32_t kk) {
 struct GridBar {
     unsigned int count;
     unsigned int gen;
+    int32_t t2_mode[4];   // block b's tile J[P_{b-1}][P_b] produced by the update CTAs (slot b % 4)
 };
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
@@ -471,7 +478,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     __shared__ int32_t s_wlo, s_wn;
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ uint32_t s_tmem;
-    __shared__ int32_t s_nown;
+    __shared__ int32_t s_nown, s_nu;
     if (a.ctl->done) return;
     const int32_t n = a.n, R = a.R;
     const unsigned int nblocks = gridDim.x;
@@ -519,6 +526,9 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     unsigned long long *cfm = reinterpret_cast<unsigned long long *>(Pc + kB);
     unsigned long long *csn = cfm + kB;
     uint32_t *udraw = reinterpret_cast<uint32_t *>(csn + kB);      // [4][kB] draws of a block
+    uint32_t *gmask = udraw + 4 * kB;      // [kB] the group's replicas that flipped at a position
+    int32_t *Ulist = reinterpret_cast<int32_t *>(gmask + kB);     // [kB] positions some of them flipped
+    int32_t *Pnx = Ulist + kB;                                     // [kB] positions of the next block
     // thresholds of block qb for the group's 4 replicas (Eq. 4 / Metropolis
     // inverted to field values): one Philox call per position (its four words
     // are the four replicas' draws), then one (position, replica) item per
@@ -676,13 +686,13 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         tile_word(wd, which, ee);
         if (lane == 0) (which == 0 ? a.T : a.T2)[(size_t)(qn & 1) * kB * kC + ee] = word;
     };
-    auto tile_issue = [&](int32_t qn) {
+    auto tile_issue = [&](int32_t qn, int32_t words) {
         teA = teB = -1;
         if (qn >= total) return;
         // warps 1..: warp 0 polls the grid barrier meanwhile
         if (warp == 0) return;
-        const int32_t per = (kTileWords + a.n_upd - 1) / a.n_upd;
-        const int32_t w0 = blockIdx.x * per, w1 = min(kTileWords, w0 + per);
+        const int32_t per = (words + a.n_upd - 1) / a.n_upd;
+        const int32_t w0 = blockIdx.x * per, w1 = min(words, w0 + per);
         constexpr int kNW = kSwThreads / 32 - 1;
         const int32_t wa = w0 + warp - 1, wb = wa + kNW;
         // unconditional loads (from J[0][0] outside the block), so that nothing
@@ -697,6 +707,37 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     auto tile_flush = [&](int32_t qn) {
         if (teA >= 0) tile_word_store(qn, teA, tokA ? tvA : 0u);
         if (teB >= 0) tile_word_store(qn, teB, tokB ? tvB : 0u);
+    };
+    // chain CTAs, blocks whose J[P_{q-1}][P_q] is not produced: the rows of
+    // the positions in Ulist (block q-1, Pc) over block q's positions (Pnx),
+    // packed straight into the shared tile.  Word wd is row Ulist[wd / kC],
+    // columns 32 (wd % kC) .. +31.  A warp's first two words are loaded at the
+    // end of block q-1's chain and packed at the start of block q's.
+    auto chain_word_store = [&](int32_t wd, bool ok, uint32_t raw) {
+        const uint32_t word = __ballot_sync(0xffffffffu, ok && e4m3_pm1(raw) > 0);
+        if (lane == 0) tile2[(size_t)Ulist[wd / kC] * kC + wd % kC] = word;
+    };
+    auto chain_src = [&](int32_t wd, int32_t cnt1, bool &ok) -> const uint8_t * {
+        const int32_t m2 = (wd % kC) * 32 + lane;
+        ok = m2 < cnt1;
+        return ok ? a.J + (size_t)Pc[Ulist[wd / kC]] * n + Pnx[m2] : a.J;
+    };
+    auto chain_t2_issue = [&](int32_t nu, int32_t cnt1) {
+        constexpr int kNW = kSwThreads / 32;
+        const int32_t words = nu * kC, wa = warp, wb = warp + kNW;
+        teA = teB = -1;
+        if (wa < words) { teA = wa; tvA = *chain_src(wa, cnt1, tokA); }
+        if (wb < words) { teB = wb; tvB = *chain_src(wb, cnt1, tokB); }
+        for (int32_t wd = wa + 2 * kNW; wd < words; wd += kNW) {   // more than two words per warp: now
+            bool ok;
+            const uint8_t *src = chain_src(wd, cnt1, ok);
+            chain_word_store(wd, ok, *src);
+        }
+    };
+    auto chain_t2_flush = [&]() {
+        if (teA >= 0) chain_word_store(teA, tokA, tvA);
+        if (teB >= 0) chain_word_store(teB, tokB, tvB);
+        teA = teB = -1;
     };
 
     // ---------------- prologue
@@ -760,7 +801,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             publish_tiles(0);
             if constexpr (TCU) {
                 __syncthreads();   // ring slot 1 written
-                tile_issue(1);
+                tile_issue(1, kTileWords);
             }
         }
     } else {
@@ -820,8 +861,10 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     uint32_t mphase = 0;     // TCU: completed phases of s_mbar
     // chain CTAs: this thread's position of the next block, loaded a phase ahead
     int32_t pcn = (!upd && total > 0) ? block_pos(0)[min((int32_t)threadIdx.x, block_cnt(0) - 1)] : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.bar->t2_mode[1] = 1;   // block 1's tile: produced in the prologue
     bool alive = grid_barrier(a.bar, nblocks, gen, a.ctl, &s_ok);
     for (int32_t q = 0; alive && q <= total; ++q) {
+        int32_t nl_q = 0;          // update CTAs: positions of block q-1 that flipped in some replica
         if (upd) {
             bool issued = false;   // TCU: MMAs of this phase in flight
             // the independent loads go first: block q-1's flip masks and (TCU)
@@ -868,6 +911,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 }
                 __syncthreads();
                 const int32_t nl = s_nl;
+                nl_q = nl;
                 if (blockIdx.x == 0 && threadIdx.x == 0) {   // the only writer
                     a.ctl->dense_rows += nl;
                     a.ctl->dense_positions += cntp;
@@ -1039,12 +1083,15 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             {
                 const uint32_t *Tq = a.T + (size_t)(q & 1) * kB * kC;
                 const uint32_t *T2q = a.T2 + (size_t)(q & 1) * kB * kC;
+                const bool t2_global = q > 0 && __ldcg(&a.bar->t2_mode[q & 3]);
                 for (int32_t x = threadIdx.x; x < kB * kC / 4; x += blockDim.x) {
                     cp_async16(tile + (size_t)x * 4, Tq + (size_t)x * 4);
-                    if (q > 0) cp_async16(tile2 + (size_t)x * 4, T2q + (size_t)x * 4);
+                    if (t2_global) cp_async16(tile2 + (size_t)x * 4, T2q + (size_t)x * 4);
                 }
                 cp_async_commit();
             }
+            chain_t2_flush();   // rows loaded at the end of the last chain (no-op otherwise)
+            if ((int)threadIdx.x < kB) gmask[threadIdx.x] = 0u;
             __syncthreads();   // Pc
             thresholds(q);
             if ((int)threadIdx.x < cnt) {
@@ -1140,6 +1187,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                         if (lane == 0) {
                             const int32_t k = Pc[m];
                             bits[k >> 5] ^= 1u << (k & 31);
+                            atomicOr(&gmask[m], 1u << qq);
                             atomicOr(&a.flip[(q % 3) * kB + m], 1ull << r);
                             if (d > 0) atomicOr(&a.snew[(q % 3) * kB + m], 1ull << r);
                         }
@@ -1147,8 +1195,24 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 }
             }
         }
+        // the update CTAs produce block q+2's J[P_{q+1}][P_{q+2}] unless block
+        // q-1 had few flipped positions (always with the CUDA-core update)
+        const bool t2_on = !TCU || q == 0 || nl_q > kT2Rare;
+        if (upd && blockIdx.x == 0 && threadIdx.x == 0 && q + 2 < total) a.bar->t2_mode[(q + 2) & 3] = t2_on;
+        // chain CTAs: block q decided; if block q+1's tile is not produced, load
+        // the rows of the positions this group's replicas flipped in block q
+        if (!upd && q + 1 < total && !__ldcg(&a.bar->t2_mode[(q + 1) & 3])) {
+            __syncthreads();   // the decisions (gmask) are complete
+            const int32_t cnt1 = block_cnt(q + 1);
+            if ((int)threadIdx.x < cnt1) Pnx[threadIdx.x] = pcn;
+            if (threadIdx.x == 0) s_nu = 0;
+            __syncthreads();
+            if ((int)threadIdx.x < block_cnt(q) && gmask[threadIdx.x] != 0u) Ulist[atomicAdd(&s_nu, 1)] = threadIdx.x;
+            __syncthreads();
+            chain_t2_issue(s_nu, cnt1);
+        }
         grid_arrive(a.bar);
-        if (upd && TCU) tile_issue(q + 2);
+        if (upd && TCU) tile_issue(q + 2, t2_on ? kTileWords : kTileWordsT);
         if (!grid_wait(a.bar, nblocks, gen, a.ctl, &s_ok)) { alive = false; break; }
     }
 
@@ -1351,7 +1415,7 @@ size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu) {
                            : (((size_t)R * rows_per * 4 + 15) & ~(size_t)15) + rest;
     const size_t nw = (size_t)((n + 31) / 32);
     const size_t chn = 2 * (size_t)kB * kC * 4 + ((4 * nw + 3) & ~(size_t)3) * 4 + (size_t)kWin * 8 +
-                       (size_t)kB * (4 * 4 + 4 * 4 + 4 + 8 + 8 + 16);
+                       (size_t)kB * (4 * 4 + 4 * 4 + 4 + 8 + 8 + 16 + 12);
     return upd > chn ? upd : chn;
 }
 

@@ -74,6 +74,15 @@ def test_dense_full_population_multi_block(pg):
     compare_dense(pg, 2048, 4, R=64, sweeps=2, beta0=0.01, beta1=1.0, seed=2)
 
 
+@pytest.mark.parametrize("rule", [0, 1])
+def test_dense_cold_rare_flips(pg, rule):
+    """A cold anneal (few positions flip per block after the first steps),
+    so most blocks take the path where the chains load the rows of their own
+    replicas' flips of the previous block instead of a produced tile, and the
+    update CTAs produce only the upper part of the block tile."""
+    compare_dense(pg, 1024, 12, R=16, sweeps=2, beta0=0.5, beta1=3.0, rule=rule, seed=9, check_every=3)
+
+
 def test_dense_restart_and_controller(pg):
     compare_dense(pg, 320, 60, R=16, sweeps=1, beta0=0.01, beta1=0.4, stagnation=1, z_rst=45, seed=5,
                   check_every=3)
