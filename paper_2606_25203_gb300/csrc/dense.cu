@@ -521,8 +521,8 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     uint32_t *cbits = tile2 + (size_t)kB * kC;
     uint64_t *win = reinterpret_cast<uint64_t *>(cbits + (((size_t)4 * nw + 3) & ~(size_t)3));
     int32_t *Gs = reinterpret_cast<int32_t *>(win + kWin);
-    int32_t *thr = Gs + 4 * kB;                                     // [4][kB]
-    int32_t *Pc = thr + 4 * kB;
+    int32_t *thr_all = Gs + 4 * kB;                                 // [2][4][kB]: block b in b & 1
+    int32_t *Pc = thr_all + 8 * kB;
     unsigned long long *cfm = reinterpret_cast<unsigned long long *>(Pc + kB);
     unsigned long long *csn = cfm + kB;
     uint32_t *udraw = reinterpret_cast<uint32_t *>(csn + kB);      // [4][kB] draws of a block
@@ -530,59 +530,62 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     int32_t *Ulist = reinterpret_cast<int32_t *>(gmask + kB);     // [kB] positions some of them flipped
     int32_t *Pnx = Ulist + kB;                                     // [kB] positions of the next block
     // thresholds of block qb for the group's 4 replicas (Eq. 4 / Metropolis
-    // inverted to field values): one Philox call per position (its four words
-    // are the four replicas' draws), then one (position, replica) item per
-    // thread and a second one for the first 4 kB - blockDim threads, both
+    // inverted to field values) into thr_all[qb & 1], by nthr threads from
+    // tid0 (all of the CTA, or a group of warps synchronised by named barrier
+    // bar): one Philox call per position (its four words are the four
+    // replicas' draws), then (position, replica) items two at a time, the two
     // binary searches run in step so that their table reads overlap.
-    // Positions are read from Pc; every thread of the CTA calls it.
-    auto thresholds = [&](int32_t qb) {
-        static_assert(4 * kB <= 2 * kSwThreads, "two threshold items per thread");
+    // Positions come from P.
+    auto thresholds = [&](int32_t qb, const int32_t *P, int32_t tid0, int32_t nthr, int bar) {
         const int32_t cnt = block_cnt(qb);
         const int32_t sw = qb / nb;
         const bool inwin = s_wn <= kWin;
-        if ((int)threadIdx.x < cnt) {
-            const u32x4 u = philox_rk((uint32_t)Pc[threadIdx.x], (uint32_t)sw, (uint32_t)a.t,
-                                      (kTagFlip << 24) | (uint32_t)cg, a.K);
-            udraw[threadIdx.x] = u.x;
-            udraw[kB + threadIdx.x] = u.y;
-            udraw[2 * kB + threadIdx.x] = u.z;
-            udraw[3 * kB + threadIdx.x] = u.w;
+        const int32_t t = (int32_t)threadIdx.x - tid0;
+        int32_t *thr = thr_all + (size_t)(qb & 1) * 4 * kB;
+        for (int32_t m = t; m < cnt; m += nthr) {
+            const u32x4 u = philox_rk((uint32_t)P[m], (uint32_t)sw, (uint32_t)a.t, (kTagFlip << 24) | (uint32_t)cg, a.K);
+            udraw[m] = u.x;
+            udraw[kB + m] = u.y;
+            udraw[2 * kB + m] = u.z;
+            udraw[3 * kB + m] = u.w;
         }
-        __syncthreads();
-        const int32_t xa = threadIdx.x, xb = xa + blockDim.x;
-        if (xa >= 4 * cnt) return;
-        const bool vb = xb < 4 * cnt;
-        const int32_t ma = xa >> 2, mb = vb ? (xb >> 2) : ma;
-        const uint64_t uqa = udraw[(xa & 3) * kB + ma], uqb = udraw[(xb & 3) * kB + mb];
+        if (nthr == (int32_t)blockDim.x) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthr) : "memory");
         auto tv = [&](int32_t i) -> uint64_t { return inwin ? win[i] : a.tab[i]; };
-        int32_t ra, rb;
-        if (a.rule == 0) {
-            // smallest h with T(h) > u: s = +1 iff h >= res
-            const int32_t top = inwin ? s_wn - 1 : 2 * a.Hc + 1;
-            int32_t loa = 0, hia = top, lob = 0, hib = vb ? top : 0;
-            while (loa < hia || lob < hib) {
-                const int32_t mida = (loa + hia) >> 1, midb = (lob + hib) >> 1;
-                const uint64_t ta = loa < hia ? tv(mida) : 0ull, tb = lob < hib ? tv(midb) : 0ull;
-                if (loa < hia) { if (ta > uqa) hia = mida; else loa = mida + 1; }
-                if (lob < hib) { if (tb > uqb) hib = midb; else lob = midb + 1; }
+        for (int32_t xa = t; xa < 4 * cnt; xa += 2 * nthr) {
+            const int32_t xb = xa + nthr;
+            const bool vb = xb < 4 * cnt;
+            const int32_t ma = xa >> 2, mb = vb ? (xb >> 2) : ma;
+            const uint64_t uqa = udraw[(xa & 3) * kB + ma], uqb = udraw[(xb & 3) * kB + mb];
+            int32_t ra, rb;
+            if (a.rule == 0) {
+                // smallest h with T(h) > u: s = +1 iff h >= res
+                const int32_t top = inwin ? s_wn - 1 : 2 * a.Hc + 1;
+                int32_t loa = 0, hia = top, lob = 0, hib = vb ? top : 0;
+                while (loa < hia || lob < hib) {
+                    const int32_t mida = (loa + hia) >> 1, midb = (lob + hib) >> 1;
+                    const uint64_t ta = loa < hia ? tv(mida) : 0ull, tb = lob < hib ? tv(midb) : 0ull;
+                    if (loa < hia) { if (ta > uqa) hia = mida; else loa = mida + 1; }
+                    if (lob < hib) { if (tb > uqb) hib = midb; else lob = midb + 1; }
+                }
+                ra = (inwin ? loa + s_wlo : loa) - a.Hc;
+                rb = (inwin ? lob + s_wlo : lob) - a.Hc;
+            } else {
+                // largest x with T_M(2x) > u: flip iff s*h <= res
+                const int32_t top = inwin ? s_wn - 1 : a.Hc;
+                int32_t loa = 0, hia = top, lob = 0, hib = vb ? top : 0;
+                while (loa < hia || lob < hib) {
+                    const int32_t mida = (loa + hia + 1) >> 1, midb = (lob + hib + 1) >> 1;
+                    const uint64_t ta = loa < hia ? tv(mida) : 0ull, tb = lob < hib ? tv(midb) : 0ull;
+                    if (loa < hia) { if (ta > uqa) loa = mida; else hia = mida - 1; }
+                    if (lob < hib) { if (tb > uqb) lob = midb; else hib = midb - 1; }
+                }
+                ra = (loa == a.Hc && a.Hc >= n) ? n + 1 : loa;
+                rb = (lob == a.Hc && a.Hc >= n) ? n + 1 : lob;
             }
-            ra = (inwin ? loa + s_wlo : loa) - a.Hc;
-            rb = (inwin ? lob + s_wlo : lob) - a.Hc;
-        } else {
-            // largest x with T_M(2x) > u: flip iff s*h <= res
-            const int32_t top = inwin ? s_wn - 1 : a.Hc;
-            int32_t loa = 0, hia = top, lob = 0, hib = vb ? top : 0;
-            while (loa < hia || lob < hib) {
-                const int32_t mida = (loa + hia + 1) >> 1, midb = (lob + hib + 1) >> 1;
-                const uint64_t ta = loa < hia ? tv(mida) : 0ull, tb = lob < hib ? tv(midb) : 0ull;
-                if (loa < hia) { if (ta > uqa) loa = mida; else hia = mida - 1; }
-                if (lob < hib) { if (tb > uqb) lob = midb; else hib = midb - 1; }
-            }
-            ra = (loa == a.Hc && a.Hc >= n) ? n + 1 : loa;
-            rb = (lob == a.Hc && a.Hc >= n) ? n + 1 : lob;
+            thr[(xa & 3) * kB + ma] = ra;
+            if (vb) thr[(xb & 3) * kB + mb] = rb;
         }
-        thr[(xa & 3) * kB + ma] = ra;
-        if (vb) thr[(xb & 3) * kB + mb] = rb;
     };
 
     // update CTAs: publish the fields of block qn's positions they own, and
@@ -1090,10 +1093,12 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 }
                 cp_async_commit();
             }
-            chain_t2_flush();   // rows loaded at the end of the last chain (no-op otherwise)
+            // rows loaded at the end of the last chain (no-op otherwise): after
+            // the loads above are on their way, so the waits overlap
+            chain_t2_flush();
             if ((int)threadIdx.x < kB) gmask[threadIdx.x] = 0u;
             __syncthreads();   // Pc
-            thresholds(q);
+            if (q == 0) thresholds(0, Pc, 0, blockDim.x, 0);   // later blocks: computed during the last chain
             if ((int)threadIdx.x < cnt) {
                 const int32_t m = threadIdx.x;
                 Gs[m] = cg * 4 < R ? g4.x : 0;
@@ -1118,7 +1123,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                     const int32_t m = s2 * 32 + lane;
                     const bool ok = m < cnt;
                     f[s2] = ok ? Gs[qq * kB + m] : 0;
-                    th[s2] = ok ? thr[qq * kB + m] : 0;
+                    th[s2] = ok ? thr_all[(size_t)(q & 1) * 4 * kB + qq * kB + m] : 0;
                     const int32_t k = ok ? Pc[m] : 0;
                     smask[s2] = __ballot_sync(0xffffffffu, ok && ((bits[k >> 5] >> (k & 31)) & 1u));
                 }
@@ -1193,6 +1198,10 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                         }
                     }
                 }
+            } else if (warp >= 4 && warp < 8 && q + 1 < total) {
+                // four of the idle warps: the next block's thresholds (they
+                // depend on the draws only)
+                thresholds(q + 1, block_pos(q + 1), 128, 128, 2);
             }
         }
         // the update CTAs produce block q+2's J[P_{q+1}][P_{q+2}] unless block
@@ -1415,7 +1424,7 @@ size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu) {
                            : (((size_t)R * rows_per * 4 + 15) & ~(size_t)15) + rest;
     const size_t nw = (size_t)((n + 31) / 32);
     const size_t chn = 2 * (size_t)kB * kC * 4 + ((4 * nw + 3) & ~(size_t)3) * 4 + (size_t)kWin * 8 +
-                       (size_t)kB * (4 * 4 + 4 * 4 + 4 + 8 + 8 + 16 + 12);
+                       (size_t)kB * (4 * 4 + 8 * 4 + 4 + 8 + 8 + 16 + 12);
     return upd > chn ? upd : chn;
 }
 
