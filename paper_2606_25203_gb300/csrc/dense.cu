@@ -1113,6 +1113,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             // clamped index: nothing waits for them here)
             if (q + 1 < total) pcn = block_pos(q + 1)[min((int32_t)threadIdx.x, block_cnt(q + 1) - 1)];
             if (warp < 4 && cg * 4 + warp < R) {
+                const bool pf_rows = q + 1 < total && !__ldcg(&a.bar->t2_mode[(q + 1) & 3]);
                 const int qq = warp;
                 const int r = cg * 4 + qq;
                 uint32_t *bits = cbits + (size_t)qq * nw;
@@ -1189,12 +1190,20 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                         const uint32_t tw[kC] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
 #pragma unroll
                         for (int s3 = 0; s3 < kC; ++s3) f[s3] += ((tw[s3] >> lane) & 1u) ? d : -d;
+                        uint32_t before = 1u;
                         if (lane == 0) {
                             const int32_t k = Pc[m];
                             bits[k >> 5] ^= 1u << (k & 31);
-                            atomicOr(&gmask[m], 1u << qq);
+                            before = atomicOr(&gmask[m], 1u << qq);
                             atomicOr(&a.flip[(q % 3) * kB + m], 1ull << r);
                             if (d > 0) atomicOr(&a.snew[(q % 3) * kB + m], 1ull << r);
+                        }
+                        // few flips: the first replica of the group to flip at m pulls
+                        // m's coupling row into L2 for the next phase's field update
+                        if (pf_rows && __shfl_sync(0xffffffffu, before, 0) == 0u) {
+                            const uint8_t *row = a.J + (size_t)Pc[m] * n;
+                            for (int32_t off = lane * 128; off < n; off += 32 * 128)
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
                         }
                     }
                 }
