@@ -61,7 +61,7 @@ PROFILED_TRAFFIC = {
                               "716b4b3f604dc859003e279035917bbf9ef6fa4d"}),
     # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.688 GB) scaled by n^2 to n=100,000
     "dense_sweep_100k": (1.688e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
-                                                           "3df158cc1b8b82e8b57def43d3e9a1f26901c7cb"}),
+                                                           "7b49778bf74b1f9fdbdbf246a7a7cc55ae18b92a"}),
 }
 
 
