@@ -306,27 +306,69 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
             }
         }
 
-        // energy from the definition E = -1/2 sum_k s_k h_k, and the write-back
-        long long acc[4] = {0, 0, 0, 0};
-        for (int32_t k = li; k < n; k += tpg) {
-            const uint32_t w = sp[k];
-            uint32_t accP = 0, accN = 0;
-            int32_t jsum = 0;
-            for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
-                const uint32_t a = adj[e];
-                const int32_t J = (int32_t)a >> 24;
-                const uint32_t x = sp[a & 0xFFFFFFu];
-                if (J > 0) accP += x * (uint32_t)J;
-                else accN += x * (uint32_t)(-J);
-                jsum += J;
-            }
+        // energy from the definition E = -1/2 sum_k s_k h_k (per thread at most
+        // n / 32 vertices of |s h| <= 127 each: int32), and the write-back
+        int32_t acc[4] = {0, 0, 0, 0};
+        if (ELLP && S > 0) {
+            // by position over the last sweep's ELL rows: coalesced loads that do
+            // not depend on spins, the next position's issued one ahead
+            const size_t sb = (size_t)slot * S + (S - 1);
+            const uint32_t *es = sell + sb * ell_stride;
+            const int2 *pos = spos + sb * (size_t)n;
+            int2 pr = make_int2(0, 0);
+            uint32_t e4[4] = {0u, 0u, 0u, 0u};
+            auto fetch = [&](int32_t i) {
+                pr = pos[i];
+                const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int32_t h = 2 * ((int32_t)((accP >> (8 * q)) & 0xFFu) -
-                                       (int32_t)((accN >> (8 * q)) & 0xFFu)) - jsum;
-                const int32_t s = ((w >> (8 * q)) & 1u) ? 1 : -1;
-                acc[q] += (long long)(s * h);
-                if (r0 + q < R) dst[(size_t)(r0 + q) * n + k] = (int8_t)s;
+                for (int q = 0; q < 4; ++q) e4[q] = q < W ? ep[q * 32] : 0u;
+            };
+            if (li < n) fetch(li);
+            for (int32_t i = li; i < n; i += tpg) {
+                const int2 p0 = pr;
+                uint32_t A = 0x80808080u;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) A += sp[e4[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e4[q] >> 24);
+                if (i + tpg < n) fetch(i + tpg);
+                const int32_t deg = (int32_t)((uint32_t)p0.x >> 24);
+                if (deg > 4) {
+                    const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+                    for (int32_t sl = 4; sl < deg; ++sl) {
+                        const uint32_t e = ep[(size_t)sl * 32];
+                        A += sp[e & 0xFFFFFFu] * (uint32_t)((int32_t)e >> 24);
+                    }
+                }
+                const uint32_t w = sp[p0.x & 0xFFFFFF];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int32_t h = 2 * ((int32_t)((A >> (8 * q)) & 0xFFu) - 128) - p0.y;   // p0.y = sum_j J_kj
+                    acc[q] += ((w >> (8 * q)) & 1u) ? h : -h;
+                }
+            }
+            for (int32_t k = li; k < n; k += tpg) {
+                const uint32_t w = sp[k];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (r0 + q < R) dst[(size_t)(r0 + q) * n + k] = ((w >> (8 * q)) & 1u) ? 1 : -1;
+            }
+        } else {
+            for (int32_t k = li; k < n; k += tpg) {
+                const uint32_t w = sp[k];
+                uint32_t A = 0x80808080u;
+                int32_t jsum = 0;
+                for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+                    const uint32_t a = adj[e];
+                    const int32_t J = (int32_t)a >> 24;
+                    A += sp[a & 0xFFFFFFu] * (uint32_t)J;
+                    jsum += J;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int32_t h = 2 * ((int32_t)((A >> (8 * q)) & 0xFFu) - 128) - jsum;
+                    const int32_t sv = ((w >> (8 * q)) & 1u) ? 1 : -1;
+                    acc[q] += sv * h;
+                    if (r0 + q < R) dst[(size_t)(r0 + q) * n + k] = (int8_t)sv;
+                }
             }
         }
 #pragma unroll
