@@ -239,6 +239,11 @@ int pamc_size_class(int32_t n);
  * Takes effect at the next pamc_batch_step.  PAMC_ERR_ARG when out of range. */
 pamc_status pamc_batch_set_shape(pamc_batch b, int size_class, int groups_per_cta, int warps_per_group);
 pamc_status pamc_batch_get_shape(pamc_batch b, int size_class, int *groups_per_cta, int *warps_per_group);
+/* Lanes that share one vertex's couplings in the batched Ising sweep of a size
+ * class (1, 2 or 4; default 1), for members on ELL schedules.  Speed only,
+ * never results.  PAMC_ERR_ARG for another value or class. */
+pamc_status pamc_batch_set_lanes(pamc_batch b, int size_class, int lanes_per_vertex);
+pamc_status pamc_batch_get_lanes(pamc_batch b, int size_class, int *lanes_per_vertex);
 int32_t pamc_batch_size(pamc_batch b);      /* members, finished or not */
 int32_t pamc_batch_active(pamc_batch b);    /* members with steps left */
 int64_t pamc_batch_launch_count(pamc_batch b);  /* kernel launches enqueued */

@@ -25,7 +25,7 @@ __all__ = [
     "pamc_sweeps_noalloc", "pamc_footprint", "pamc_batch_create", "pamc_batch_add", "pamc_batch_step",
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
-    "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_hamming", "pamc_lineage", "pamc_set_population", "pamc_fields",
+    "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_batch_set_lanes", "pamc_batch_get_lanes", "pamc_hamming", "pamc_lineage", "pamc_set_population", "pamc_fields",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -149,6 +149,10 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_batch_set_shape.restype = ctypes.c_int
     L.pamc_batch_get_shape.argtypes = [P, ctypes.c_int, P, P]
     L.pamc_batch_get_shape.restype = ctypes.c_int
+    L.pamc_batch_set_lanes.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    L.pamc_batch_set_lanes.restype = ctypes.c_int
+    L.pamc_batch_get_lanes.argtypes = [P, ctypes.c_int, P]
+    L.pamc_batch_get_lanes.restype = ctypes.c_int
     L.pamc_batch_sync.argtypes = [P]
     L.pamc_batch_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     L.pamc_batch_destroy.argtypes = [P]
@@ -398,6 +402,16 @@ def pamc_batch_get_shape(b, size_class: int):
     g, w = ctypes.c_int(0), ctypes.c_int(0)
     _bcheck(_lib.pamc_batch_get_shape(b, int(size_class), ctypes.byref(g), ctypes.byref(w)), b)
     return g.value, w.value
+
+
+def pamc_batch_set_lanes(b, size_class: int, lanes_per_vertex: int):
+    _bcheck(_lib.pamc_batch_set_lanes(b, int(size_class), int(lanes_per_vertex)), b)
+
+
+def pamc_batch_get_lanes(b, size_class: int) -> int:
+    v = ctypes.c_int(0)
+    _bcheck(_lib.pamc_batch_get_lanes(b, int(size_class), ctypes.byref(v)), b)
+    return v.value
 
 
 def pamc_batch_size(b) -> int:

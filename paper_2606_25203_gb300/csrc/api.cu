@@ -973,13 +973,14 @@ bool upload(pamc_batch b, DevBuf &buf, const std::vector<T> &v) {
 // warps per group).  Small instances pack several groups into one CTA.
 constexpr int kClasses = 3;
 int batch_class(int32_t n) { return n <= 2048 ? 0 : n <= 8192 ? 1 : 2; }
+bool batch_lanes_ok(int l) { return l == 1 || l == 2 || l == 4; }
 SweepCfg batch_cfg(int cls) {
-    static const SweepCfg c[kClasses] = {{8, 1}, {4, 2}, {1, 16}};
+    static const SweepCfg c[kClasses] = {{8, 1, 1}, {4, 2, 1}, {1, 16, 1}};
     const char *env = getenv("PAMC_BATCH_CFG");   // "g0,w0;g1,w1;g2,w2"
     if (env) {
         int v[6];
         if (sscanf(env, "%d,%d;%d,%d;%d,%d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 6) {
-            SweepCfg o{v[2 * cls], v[2 * cls + 1]};
+            SweepCfg o{v[2 * cls], v[2 * cls + 1], 1};
             if (o.groups_per_cta >= 1 && o.warps_per_group >= 1 && o.groups_per_cta * o.warps_per_group <= 32)
                 return o;
         }
@@ -1229,8 +1230,25 @@ pamc_status pamc_batch_set_shape(pamc_batch b, int size_class, int groups_per_ct
     if (size_class < 0 || size_class >= kClasses) return bfail(b, PAMC_ERR_ARG, "size class must be 0, 1 or 2");
     if (groups_per_cta < 1 || warps_per_group < 1 || groups_per_cta * warps_per_group > 32)
         return bfail(b, PAMC_ERR_ARG, "need groups >= 1, warps >= 1 and groups * warps <= 32");
-    b->shape[size_class] = SweepCfg{groups_per_cta, warps_per_group};
+    b->shape[size_class].groups_per_cta = groups_per_cta;
+    b->shape[size_class].warps_per_group = warps_per_group;
     b->dirty = true;
+    return PAMC_OK;
+}
+
+pamc_status pamc_batch_set_lanes(pamc_batch b, int size_class, int lanes_per_vertex) {
+    if (!b) return bfail(b, PAMC_ERR_ARG, "null batch");
+    if (size_class < 0 || size_class >= kClasses) return bfail(b, PAMC_ERR_ARG, "size class must be 0, 1 or 2");
+    if (!batch_lanes_ok(lanes_per_vertex)) return bfail(b, PAMC_ERR_ARG, "lanes per vertex must be 1, 2 or 4");
+    b->shape[size_class].lanes_per_vertex = lanes_per_vertex;
+    b->dirty = true;
+    return PAMC_OK;
+}
+
+pamc_status pamc_batch_get_lanes(pamc_batch b, int size_class, int *lanes_per_vertex) {
+    if (!b || !lanes_per_vertex) return bfail(b, PAMC_ERR_ARG, "null argument");
+    if (size_class < 0 || size_class >= kClasses) return bfail(b, PAMC_ERR_ARG, "size class must be 0, 1 or 2");
+    *lanes_per_vertex = b->shape[size_class].lanes_per_vertex;
     return PAMC_OK;
 }
 

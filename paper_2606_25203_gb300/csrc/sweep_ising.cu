@@ -391,8 +391,9 @@ __global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int 
 
 // Many instances in one launch: CTA b works on instance items[b].x, its
 // local block items[b].y.  Descriptors live in device memory and are read
-// field by field (no local copy of the descriptor).
-template <bool ELLP, int RULE>
+// field by field (no local copy of the descriptor).  LPV > 1: lanes per
+// vertex, as for one instance (ELL schedules only).
+template <bool ELLP, int RULE, int LPV>
 __global__ void __launch_bounds__(1024)
 k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restrict__ items, int gpc, int tpg) {
     const int2 it = items[blockIdx.x];
@@ -401,7 +402,7 @@ k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restric
     const int32_t t = ctl->t;
     if (t >= d.t_end) return;
     const KeysSeed draw{d.K.k0[0], d.K.k1[0]};
-    sweep_ising_body<ELLP, RULE, 1>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.sorder,
+    sweep_ising_body<ELLP, RULE, LPV>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.sorder,
                                  d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.ncm_buf,
                                  d.ncm_idx, d.sp[(t + 1) & 1], d.en[(t + 1) & 1], ctl, gpc, tpg, it.y);
 }
@@ -465,17 +466,26 @@ cudaError_t launch_sweep_ising_batched(int rule, bool ell, const SweepDesc *desc
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
     const size_t smem = sweep_ising_smem_bytes(n_max, 127, cfg);
     cudaError_t err = cudaSuccess;
-#define PAMC_LAUNCH(EL, RU)                                                                       \
+#define PAMC_LAUNCH(EL, RU, LV)                                                                   \
     do {                                                                                          \
-        err = allow_dynamic_smem(k_sweep_ising_batched<EL, RU>, smem);                            \
+        err = allow_dynamic_smem(k_sweep_ising_batched<EL, RU, LV>, smem);                        \
         if (err != cudaSuccess) return err;                                                       \
-        k_sweep_ising_batched<EL, RU><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg);   \
+        k_sweep_ising_batched<EL, RU, LV><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg); \
+    } while (0)
+#define PAMC_LAUNCH_LPV(RU)                                                                       \
+    do {                                                                                          \
+        switch (cfg.lanes_per_vertex) {                                                           \
+        case 4: PAMC_LAUNCH(true, RU, 4); break;                                                  \
+        case 2: PAMC_LAUNCH(true, RU, 2); break;                                                  \
+        default: PAMC_LAUNCH(true, RU, 1); break;                                                 \
+        }                                                                                         \
     } while (0)
     if (ell) {
-        if (rule == 0) PAMC_LAUNCH(true, 0); else PAMC_LAUNCH(true, 1);
+        if (rule == 0) PAMC_LAUNCH_LPV(0); else PAMC_LAUNCH_LPV(1);
     } else {
-        if (rule == 0) PAMC_LAUNCH(false, 0); else PAMC_LAUNCH(false, 1);
+        if (rule == 0) PAMC_LAUNCH(false, 0, 1); else PAMC_LAUNCH(false, 1, 1);
     }
+#undef PAMC_LAUNCH_LPV
 #undef PAMC_LAUNCH
     return cudaGetLastError();
 }

@@ -237,13 +237,16 @@ def test_shapes_change_speed_not_results(pg):
              (W.er_avg_degree(3000, 16, signed=False, seed=42), dict(R=24, sweeps=2, steps=7, seed=2, rule=1)),
              (W.torus(95, 95, signed=True, seed=43), dict(R=28, sweeps=1, steps=7, seed=3))]
     ref = [alone(pg, inst, p) for inst, p in cases]
-    for shape in [(1, 1), (2, 16), (8, 4), (3, 3)]:
+    for shape, lanes in [((1, 1), 1), ((2, 16), 1), ((8, 4), 1), ((3, 3), 1), ((1, 8), 2), ((2, 16), 4),
+                         ((1, 32), 4)]:
         b = pg.pamc_batch_create(0)
         hs = []
         try:
             for c in range(3):
                 pg.pamc_batch_set_shape(b, c, *shape)
+                pg.pamc_batch_set_lanes(b, c, lanes)
                 assert pg.pamc_batch_get_shape(b, c) == shape
+                assert pg.pamc_batch_get_lanes(b, c) == lanes
             for inst, p in cases:
                 h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
                 pg.pamc_init(h, **p)
@@ -252,7 +255,7 @@ def test_shapes_change_speed_not_results(pg):
             pg.pamc_batch_step(b, 7)
             pg.pamc_batch_sync(b)
             for i, (inst, p) in enumerate(cases):
-                assert_same(snapshot(pg, hs[i], inst.n, p["R"]), ref[i], f"shape {shape} member {i}")
+                assert_same(snapshot(pg, hs[i], inst.n, p["R"]), ref[i], f"shape {shape} lanes {lanes} member {i}")
         finally:
             pg.pamc_batch_destroy(b)
             for h in hs:
@@ -263,11 +266,14 @@ def test_shapes_change_speed_not_results(pg):
             pg.pamc_batch_set_shape(b, 0, 8, 8)      # 64 warps
         with pytest.raises(pg.PamcError):
             pg.pamc_batch_set_shape(b, 3, 1, 1)      # no such class
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_set_lanes(b, 0, 3)         # 1, 2 or 4
         got = tune_batch_shapes(b, [c[0] for c in cases], dict(R=32, sweeps=1), steps=1, rounds=1,
-                                candidates=((1, 4), (2, 2)))
+                                candidates=((1, 4), (2, 2), (1, 8, 2)))
         assert sorted(got) == [0, 1, 2]
-        for c, (g, w, ms) in got.items():
-            assert (g, w) in ((1, 4), (2, 2)) and ms > 0
+        for c, (g, w, lv, ms) in got.items():
+            assert (g, w, lv) in ((1, 4, 1), (2, 2, 1), (1, 8, 2)) and ms > 0
             assert pg.pamc_batch_get_shape(b, c) == (g, w)
+            assert pg.pamc_batch_get_lanes(b, c) == lv
     finally:
         pg.pamc_batch_destroy(b)
