@@ -661,7 +661,8 @@ def run_potts(args):
         "config": {"workload": POTTS_WORKLOAD, **POTTS_PARAMS, "l2": "flushed between steps (512 MB write)",
                    "timed_steps": f"steps 0..{args.steps - 1} of a fresh run"},
         "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tops/s", "frac": ach / peak,
-                     "traffic": None, "kernel": "k_sweep<Potts> (cascaded)", "ops_per_attempt": ops},
+                     "traffic": None, "kernel": "whole step, k_sweep_potts (cascaded) dominating",
+                     "ops_per_attempt": ops},
         "cut_after_timed_steps": c["cut"],
         "softmax": {"value": att / (out["softmax"]["ms"] / 1e3), "unit": "attempts/s",
                     "ms_per_step": out["softmax"]["ms"] / args.steps, "cut_after_timed_steps": out["softmax"]["cut"],
