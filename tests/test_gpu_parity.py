@@ -223,3 +223,24 @@ def test_full_size_population_sampled(pg, name):
     m, b = s.best()
     assert m == (pg.pamc_weight_sum(s.h) - oracle.energy_ising(inst.row_ptr, inst.col, -inst.w, b)) // 2
     s.close()
+
+
+@pytest.mark.parametrize("rule", [0, 2])
+def test_potts_full_size_first_step(pg, rule):
+    """Configuration 3 at full size: N=2,000 (avg degree 12), R=2,048, 10
+    sweeps, the benchmark's launch shape.  The first iteration does not
+    resample, so the oracle runs all 2,048 replicas through it and every label
+    and energy is compared; the cascaded sampler and the softmax noisy argmax."""
+    inst = W.c3_sparse2000()
+    params = dict(kind=1, rule=rule, R=2048, sweeps=10, steps=300, beta0=0.1, beta1=3.0, seed=0)
+    if rule == 2:
+        params.update(K=3, gamma=1.0)
+    s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+    s.init(**params)
+    s.step(1)
+    spins, E, _, _ = s.state()
+    ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **params)
+    ref.step(1)
+    np.testing.assert_array_equal(spins, ref.spins())
+    np.testing.assert_array_equal(E, ref.energy())
+    s.close()
