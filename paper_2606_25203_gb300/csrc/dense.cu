@@ -5,14 +5,16 @@
 //                      top key bits, then sort each bucket;
 //   k_dense_tables     heat-bath T(h) (Eq. 4) or Metropolis T_M(2x) over the
 //                      field range that does not saturate;
-//   k_dense_recompute  H = J * S for the resampled population with int8
-//                      tensor-core MMA (exact int32 accumulation): the full
-//                      field recompute of every step;
+//   k_dense_recompute  H = J * S for the resampled population with
+//                      mma.sync on e4m3 couplings (exact integer fields):
+//                      the full recompute of every step when n is not a
+//                      multiple of 16 (dense_tc.cu has the tcgen05 one);
 //   k_dense_sweep      S sequential sweeps (cooperative, persistent): most
-//                      CTAs own a slice of H rows in shared memory and apply
-//                      each block's flips (streaming each flipped row of J
-//                      once for all replicas), a few CTAs run the per-replica
-//                      decision chains of each block of B positions.
+//                      CTAs own a slice of H rows (in tensor memory with the
+//                      tcgen05 update, else in shared memory) and apply each
+//                      block's flips (each flipped row of J read once for all
+//                      replicas), a few CTAs run the per-replica decision
+//                      chains of each block of kB positions.
 #include <cooperative_groups.h>
 
 #include "pamc_device.cuh"
