@@ -177,8 +177,13 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 // +-1 int8 spins -> e4m3 (+1.0 = 0x38, -1.0 = 0xB8), four at a time
 __device__ __forceinline__ uint32_t spins_to_e4m3(uint32_t x) { return (x & 0x80808080u) | 0x38383838u; }
@@ -337,6 +342,10 @@ constexpr int kTileWords = kTileWordsT + kB * kC;   // both tiles of a block
 // end of that block's chain.  The update CTAs decide per block from the count
 // of flipped positions two blocks earlier (the same count in every CTA).
 constexpr int kT2Rare = 16;
+// ... and in those blocks the row of a flip is staged while the chain runs:
+// the first replica of a group to flip a position copies the row's 4-byte
+// pieces that hold the next block's columns into a staging slot
+constexpr int kStgSlots = 32;
 // word wd of a block's production list -> tile (0: J[P_q][P_q], 1:
 // J[P_{q-1}][P_q]) and word index m * kC + c within it
 __device__ __forceinline__ void tile_word(int32_t wd, int &which, int32_t &ee) {
@@ -480,7 +489,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     __shared__ int32_t s_wlo, s_wn;
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ uint32_t s_tmem;
-    __shared__ int32_t s_nown, s_nu;
+    __shared__ int32_t s_nown, s_nu, s_nslot;
     if (a.ctl->done) return;
     const int32_t n = a.n, R = a.R;
     const unsigned int nblocks = gridDim.x;
@@ -531,6 +540,8 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     uint32_t *gmask = udraw + 4 * kB;      // [kB] the group's replicas that flipped at a position
     int32_t *Ulist = reinterpret_cast<int32_t *>(gmask + kB);     // [kB] positions some of them flipped
     int32_t *Pnx = Ulist + kB;                                     // [kB] positions of the next block
+    uint32_t *stg = reinterpret_cast<uint32_t *>(Pnx + kB);       // [kStgSlots][kC][32] staged row pieces
+    int32_t *Uslot = reinterpret_cast<int32_t *>(stg + (size_t)kStgSlots * kC * 32);   // [kStgSlots] their positions
     // thresholds of block qb for the group's 4 replicas (Eq. 4 / Metropolis
     // inverted to field values) into thr_all[qb & 1], by nthr threads from
     // tid0 (all of the CTA, or a group of warps synchronised by named barrier
@@ -839,6 +850,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             for (int z = 0; z < 3; ++z) { a.flip[z * kB + threadIdx.x] = 0ull; a.snew[z * kB + threadIdx.x] = 0ull; }
         }
         if (blockIdx.x == a.n_upd && (int)threadIdx.x < R) a.E[threadIdx.x] = 0;
+        if (threadIdx.x == 0) s_nslot = 0;
         // the part of the threshold table where it is neither 0 nor 2^32
         // (heat-bath) or above 0 (Metropolis)
         if (threadIdx.x == 0) {
@@ -864,6 +876,8 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             for (int32_t i = threadIdx.x; i < s_wn; i += blockDim.x) win[i] = a.tab[s_wlo + i];
     }
     uint32_t mphase = 0;     // TCU: completed phases of s_mbar
+    // chain CTAs stage 4-byte pieces of J (its base must be 4-byte aligned)
+    const bool stage_ok = (reinterpret_cast<uintptr_t>(a.J) & 3) == 0;
     // chain CTAs: this thread's position of the next block, loaded a phase ahead
     int32_t pcn = (!upd && total > 0) ? block_pos(0)[min((int32_t)threadIdx.x, block_cnt(0) - 1)] : 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.bar->t2_mode[1] = 1;   // block 1's tile: produced in the prologue
@@ -1069,7 +1083,11 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         } else if (q < total) {
             const int32_t cnt = block_cnt(q);
             const int32_t cntp = q > 0 ? block_cnt(q - 1) : 0;
+            const int32_t nstg = min(s_nslot, kStgSlots);          // rows staged by the last chain
             if ((int)threadIdx.x < cnt) Pc[threadIdx.x] = pcn;   // loaded last phase
+            // positions of block q+1, for staging rows during this chain
+            const int32_t q1 = min(q + 1, total - 1);
+            const int32_t pnx_v = block_pos(q1)[min((int32_t)threadIdx.x, block_cnt(q1) - 1)];
             if (blockIdx.x == a.n_upd && threadIdx.x < kB) {   // buffer of block q+1 starts empty
                 a.flip[((q + 1) % 3) * kB + threadIdx.x] = 0ull;
                 a.snew[((q + 1) % 3) * kB + threadIdx.x] = 0ull;
@@ -1099,7 +1117,18 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             // the loads above are on their way, so the waits overlap
             chain_t2_flush();
             if ((int)threadIdx.x < kB) gmask[threadIdx.x] = 0u;
-            __syncthreads();   // Pc
+            cp_async_wait_prior();   // this thread's staged pieces (all but the tiles just issued)
+            __syncthreads();   // Pc, staged pieces
+            if (threadIdx.x == 0) s_nslot = 0;
+            // staged rows of the last block's flips -> bit rows of J[P_{q-1}][P_q]
+            for (int32_t task = warp; task < nstg * kC; task += kSwThreads / 32) {   // warp-uniform
+                const int32_t sl = task / kC, wv = task % kC, m2 = wv * 32 + lane;
+                const uint32_t piece = stg[(size_t)task * 32 + lane];
+                const int32_t col = Pc[min(m2, cnt - 1)];
+                const uint32_t raw = (piece >> (8 * (col & 3))) & 0xFFu;
+                const uint32_t word = __ballot_sync(0xffffffffu, m2 < cnt && e4m3_pm1(raw) > 0);
+                if (lane == 0) tile2[(size_t)Uslot[sl] * kC + wv] = word;
+            }
             if (q == 0) thresholds(0, Pc, 0, blockDim.x, 0);   // later blocks: computed during the last chain
             if ((int)threadIdx.x < cnt) {
                 const int32_t m = threadIdx.x;
@@ -1109,13 +1138,15 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 Gs[3 * kB + m] = cg * 4 + 3 < R ? g4.w : 0;
             }
             if (okm) { cfm[threadIdx.x] = fm; csn[threadIdx.x] = sm2; }
+            if ((int)threadIdx.x < kB) Pnx[threadIdx.x] = pnx_v;
             cp_async_wait_all();
             __syncthreads();
             // positions of block q+1 for the next phase (unconditional, from a
             // clamped index: nothing waits for them here)
             if (q + 1 < total) pcn = block_pos(q + 1)[min((int32_t)threadIdx.x, block_cnt(q + 1) - 1)];
             if (warp < 4 && cg * 4 + warp < R) {
-                const bool pf_rows = q + 1 < total && !__ldcg(&a.bar->t2_mode[(q + 1) & 3]);
+                const bool pf_rows = q + 1 < total && !__ldcg(&a.bar->t2_mode[(q + 1) & 3]) && stage_ok;
+                const int32_t cnt1 = block_cnt(q1);
                 const int qq = warp;
                 const int r = cg * 4 + qq;
                 uint32_t *bits = cbits + (size_t)qq * nw;
@@ -1193,36 +1224,57 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
 #pragma unroll
                         for (int s3 = 0; s3 < kC; ++s3) f[s3] += ((tw[s3] >> lane) & 1u) ? d : -d;
                         uint32_t before = 1u;
+                        int32_t slot = kStgSlots;
                         if (lane == 0) {
                             const int32_t k = Pc[m];
                             bits[k >> 5] ^= 1u << (k & 31);
                             before = atomicOr(&gmask[m], 1u << qq);
                             atomicOr(&a.flip[(q % 3) * kB + m], 1ull << r);
                             if (d > 0) atomicOr(&a.snew[(q % 3) * kB + m], 1ull << r);
+                            if (pf_rows && before == 0u) {
+                                slot = atomicAdd(&s_nslot, 1);
+                                if (slot < kStgSlots) Uslot[slot] = m;
+                            }
                         }
                         // few flips: the first replica of the group to flip at m pulls
-                        // m's coupling row into L2 for the next phase's field update
+                        // m's coupling row into L2 for the next phase's field update and
+                        // stages the pieces of it over the next block's positions
                         if (pf_rows && __shfl_sync(0xffffffffu, before, 0) == 0u) {
                             const uint8_t *row = a.J + (size_t)Pc[m] * n;
                             for (int32_t off = lane * 128; off < n; off += 32 * 128)
                                 asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
+                            slot = __shfl_sync(0xffffffffu, slot, 0);
+                            if (slot < kStgSlots) {
+#pragma unroll
+                                for (int wv = 0; wv < kC; ++wv) {
+                                    const int32_t m2 = wv * 32 + lane;
+                                    if (m2 < cnt1)
+                                        cp_async4(stg + ((size_t)slot * kC + wv) * 32 + lane, row + (Pnx[m2] & ~3));
+                                }
+                            }
                         }
                     }
                 }
-            } else if (warp >= 4 && warp < 8 && q + 1 < total) {
-                // four of the idle warps: the next block's thresholds (they
+            } else if (warp >= 4 && warp < 12 && q + 1 < total) {
+                // eight of the idle warps: the next block's thresholds (they
                 // depend on the draws only)
-                thresholds(q + 1, block_pos(q + 1), 128, 128, 2);
+                thresholds(q + 1, block_pos(q + 1), 128, 256, 2);
             }
         }
         // the update CTAs produce block q+2's J[P_{q+1}][P_{q+2}] unless block
         // q-1 had few flipped positions (always with the CUDA-core update)
         const bool t2_on = !TCU || q == 0 || nl_q > kT2Rare;
         if (upd && blockIdx.x == 0 && threadIdx.x == 0 && q + 2 < total) a.bar->t2_mode[(q + 2) & 3] = t2_on;
-        // chain CTAs: block q decided; if block q+1's tile is not produced, load
-        // the rows of the positions this group's replicas flipped in block q
+        // chain CTAs: block q decided; if block q+1's tile is not produced, its
+        // rows were staged during the chain -- unless more positions flipped
+        // than there are slots: then the rows of all of them are loaded here
+        if (!upd && q < total) cp_async_commit();   // the staged pieces
+        bool t2_load = false;
         if (!upd && q + 1 < total && !__ldcg(&a.bar->t2_mode[(q + 1) & 3])) {
-            __syncthreads();   // the decisions (gmask) are complete
+            __syncthreads();   // the decisions (gmask, the staging count) are complete
+            t2_load = !stage_ok || s_nslot > kStgSlots;
+        }
+        if (t2_load) {
             const int32_t cnt1 = block_cnt(q + 1);
             if ((int)threadIdx.x < cnt1) Pnx[threadIdx.x] = pcn;
             if (threadIdx.x == 0) s_nu = 0;
@@ -1435,7 +1487,8 @@ size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu) {
                            : (((size_t)R * rows_per * 4 + 15) & ~(size_t)15) + rest;
     const size_t nw = (size_t)((n + 31) / 32);
     const size_t chn = 2 * (size_t)kB * kC * 4 + ((4 * nw + 3) & ~(size_t)3) * 4 + (size_t)kWin * 8 +
-                       (size_t)kB * (4 * 4 + 8 * 4 + 4 + 8 + 8 + 16 + 12);
+                       (size_t)kB * (4 * 4 + 8 * 4 + 4 + 8 + 8 + 16 + 12) +
+                       (size_t)kStgSlots * (kC * 32 * 4 + 4);
     return upd > chn ? upd : chn;
 }
 
