@@ -878,6 +878,9 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
     uint32_t mphase = 0;     // TCU: completed phases of s_mbar
     // chain CTAs stage 4-byte pieces of J (its base must be 4-byte aligned)
     const bool stage_ok = (reinterpret_cast<uintptr_t>(a.J) & 3) == 0;
+    // chain CTAs: whether the current block's J[P_{q-1}][P_q] was produced,
+    // read one phase ahead (block 1's is, by the prologue)
+    int32_t t2_cur = 1;
     // chain CTAs: this thread's position of the next block, loaded a phase ahead
     int32_t pcn = (!upd && total > 0) ? block_pos(0)[min((int32_t)threadIdx.x, block_cnt(0) - 1)] : 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.bar->t2_mode[1] = 1;   // block 1's tile: produced in the prologue
@@ -1084,6 +1087,8 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             const int32_t cnt = block_cnt(q);
             const int32_t cntp = q > 0 ? block_cnt(q - 1) : 0;
             const int32_t nstg = min(s_nslot, kStgSlots);          // rows staged by the last chain
+            // block q+1's mode (written in phase q-1), consumed after the prep
+            const int32_t t2_next = __ldcg(&a.bar->t2_mode[(q + 1) & 3]);
             if ((int)threadIdx.x < cnt) Pc[threadIdx.x] = pcn;   // loaded last phase
             // positions of block q+1, for staging rows during this chain
             const int32_t q1 = min(q + 1, total - 1);
@@ -1106,7 +1111,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             {
                 const uint32_t *Tq = a.T + (size_t)(q & 1) * kB * kC;
                 const uint32_t *T2q = a.T2 + (size_t)(q & 1) * kB * kC;
-                const bool t2_global = q > 0 && __ldcg(&a.bar->t2_mode[q & 3]);
+                const bool t2_global = q > 0 && t2_cur;
                 for (int32_t x = threadIdx.x; x < kB * kC / 4; x += blockDim.x) {
                     cp_async16(tile + (size_t)x * 4, Tq + (size_t)x * 4);
                     if (t2_global) cp_async16(tile2 + (size_t)x * 4, T2q + (size_t)x * 4);
@@ -1145,7 +1150,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
             // clamped index: nothing waits for them here)
             if (q + 1 < total) pcn = block_pos(q + 1)[min((int32_t)threadIdx.x, block_cnt(q + 1) - 1)];
             if (warp < 4 && cg * 4 + warp < R) {
-                const bool pf_rows = q + 1 < total && !__ldcg(&a.bar->t2_mode[(q + 1) & 3]) && stage_ok;
+                const bool pf_rows = q + 1 < total && !t2_next && stage_ok;
                 const int32_t cnt1 = block_cnt(q1);
                 const int qq = warp;
                 const int r = cg * 4 + qq;
@@ -1260,6 +1265,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
                 // depend on the draws only)
                 thresholds(q + 1, block_pos(q + 1), 128, 256, 2);
             }
+            t2_cur = t2_next;   // block q+1 is the next block
         }
         // the update CTAs produce block q+2's J[P_{q+1}][P_{q+2}] unless block
         // q-1 had few flipped positions (always with the CUDA-core update)
@@ -1270,7 +1276,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         // than there are slots: then the rows of all of them are loaded here
         if (!upd && q < total) cp_async_commit();   // the staged pieces
         bool t2_load = false;
-        if (!upd && q + 1 < total && !__ldcg(&a.bar->t2_mode[(q + 1) & 3])) {
+        if (!upd && q + 1 < total && !t2_cur) {
             __syncthreads();   // the decisions (gmask, the staging count) are complete
             t2_load = !stage_ok || s_nslot > kStgSlots;
         }
