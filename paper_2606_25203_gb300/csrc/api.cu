@@ -1089,7 +1089,10 @@ pamc_status rebuild(pamc_batch b) {
     if (e == cudaSuccess) e = launch_control_batched((const CtlDesc *)b->ctl.p, (int32_t)ctls.size(), b->stream);
     nl += 1;
     if (e == cudaSuccess && !sdi.empty()) {
-        launch_schedule_batched((const SchedDesc *)b->sd.p, (const int2 *)b->sdi.p, (int32_t)sdi.size(), b->stream);
+        int32_t sched_nmax = 1;
+        for (const SchedDesc &d : sd) sched_nmax = std::max(sched_nmax, d.n);
+        launch_schedule_batched((const SchedDesc *)b->sd.p, (const int2 *)b->sdi.p, (int32_t)sdi.size(), sched_nmax,
+                                b->stream);
         e = cudaGetLastError();
         nl += 1;
     }

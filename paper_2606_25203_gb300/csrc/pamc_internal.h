@@ -154,7 +154,8 @@ void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t
                      int2 *pos = nullptr);
 
 size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
-void launch_schedule_batched(const SchedDesc *descs, const int2 *items, int32_t nitems, cudaStream_t st);
+void launch_schedule_batched(const SchedDesc *descs, const int2 *items, int32_t nitems, int32_t n_max,
+                             cudaStream_t st);
 cudaError_t launch_population_batched(const PrepDesc *prep, const TabDesc *tabs, int32_t ninst,
                                       int32_t R_max, cudaStream_t st);
 cudaError_t launch_control_batched(const CtlDesc *descs, int32_t ninst, cudaStream_t st);

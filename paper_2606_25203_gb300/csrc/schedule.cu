@@ -11,7 +11,12 @@
 // level after level, giving bit-identical results to the sequential order.
 // Levels are produced by Kahn's algorithm, frontier by frontier; no sort is
 // needed.  One CTA builds one (t, sweep) schedule; a launch builds the
-// schedules of several steps at once.
+// schedules of several steps at once.  The keys and predecessor counters sit
+// in shared memory when 8n bytes fit (global scratch otherwise), and a
+// frontier narrower than the CTA gives each vertex several lanes, which split
+// its neighbour list.
+#include <algorithm>
+
 #include "pamc_device.cuh"
 #include "pamc_internal.h"
 
@@ -24,21 +29,24 @@ __device__ __forceinline__ bool before(uint32_t ka, int32_t a, uint32_t kb, int3
 }
 
 constexpr int kSchedThreads = 512;
+constexpr size_t kSchedSmemMax = 160 * 1024;   // keys and counters of n <= 20,480 in shared memory
 
 __device__ __forceinline__ void
 schedule_body(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
               uint32_t key0, uint32_t key1, int32_t t0, int32_t S, int32_t slots,
               int32_t *__restrict__ order, int32_t *__restrict__ lvl_ptr, int32_t *__restrict__ nlev,
               uint32_t *__restrict__ skey, int32_t *__restrict__ scnt, uint32_t *__restrict__ ell,
-              int32_t W, int2 *__restrict__ pos, int b) {
+              int32_t W, int2 *__restrict__ pos, int b, size_t smem_bytes) {
+    extern __shared__ uint32_t ssched[];
     const int ti = b / S, sw = b % S;
     const int32_t t = t0 + ti;
     const int slot = t % slots;
     const size_t base = (size_t)slot * S + sw;
     int32_t *ord = order + base * (size_t)n;
     int32_t *lp = lvl_ptr + base * (size_t)(n + 1);
-    uint32_t *key = skey + (size_t)b * n;
-    int32_t *cnt = scnt + (size_t)b * n;
+    const bool in_smem = (size_t)n * 8 <= smem_bytes;
+    uint32_t *key = in_smem ? ssched : skey + (size_t)b * n;
+    int32_t *cnt = in_smem ? reinterpret_cast<int32_t *>(ssched + n) : scnt + (size_t)b * n;
     __shared__ int32_t s_tail;
     __shared__ int32_t s_end;
 
@@ -64,10 +72,15 @@ schedule_body(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restr
     if (threadIdx.x == 0) lp[0] = 0;
     while (beg < end) {
         if (threadIdx.x == 0) lp[L + 1] = end;
-        for (int32_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        // lanes per frontier vertex: the largest power of two up to 32 that
+        // still leaves a lane group for every vertex of the frontier
+        int lpv = 1;
+        while (lpv < 32 && (int32_t)(blockDim.x / (2 * lpv)) >= end - beg) lpv *= 2;
+        const int32_t sub = threadIdx.x % lpv, step = blockDim.x / lpv;
+        for (int32_t i = beg + threadIdx.x / lpv; i < end; i += step) {
             const int32_t k = ord[i];
             const uint32_t kk = key[k];
-            for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+            for (int32_t e = rp[k] + sub; e < rp[k + 1]; e += lpv) {
                 const int32_t j = (int32_t)(adj[e] & 0xFFFFFFu);
                 if (before(kk, k, key[j], j) && atomicSub(&cnt[j], 1) == 1)
                     ord[atomicAdd(&s_tail, 1)] = j;
@@ -114,13 +127,13 @@ k_schedule(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict
            uint32_t key0, uint32_t key1, int32_t t0, int32_t S, int32_t slots,
            int32_t *__restrict__ order, int32_t *__restrict__ lvl_ptr, int32_t *__restrict__ nlev,
            uint32_t *__restrict__ skey, int32_t *__restrict__ scnt, uint32_t *__restrict__ ell,
-           int32_t W, int2 *__restrict__ pos) {
+           int32_t W, int2 *__restrict__ pos, size_t smem_bytes) {
     schedule_body(n, rp, adj, key0, key1, t0, S, slots, order, lvl_ptr, nlev, skey, scnt, ell, W, pos,
-                  blockIdx.x);
+                  blockIdx.x, smem_bytes);
 }
 
 __global__ void __launch_bounds__(kSchedThreads)
-k_schedule_batched(const SchedDesc *__restrict__ descs, const int2 *__restrict__ items) {
+k_schedule_batched(const SchedDesc *__restrict__ descs, const int2 *__restrict__ items, size_t smem_bytes) {
     const int2 it = items[blockIdx.x];
     const SchedDesc d = descs[it.x];
     int32_t t0 = d.t0;
@@ -130,7 +143,7 @@ k_schedule_batched(const SchedDesc *__restrict__ descs, const int2 *__restrict__
         if (t0 >= d.t_end) return;
     }
     schedule_body(d.n, d.rp, d.adj, d.key0, d.key1, t0, d.S, d.slots, d.order, d.lvl, d.nlev, d.skey,
-                  d.scnt, d.ell, d.W, d.pos, it.y);
+                  d.scnt, d.ell, d.W, d.pos, it.y, smem_bytes);
 }
 
 }  // namespace
@@ -140,14 +153,20 @@ void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t
                      int32_t *lvl_ptr, int32_t *nlev, uint32_t *skey, int32_t *scnt,
                      cudaStream_t st, uint32_t *ell, int32_t W, int2 *pos) {
     if (nt <= 0 || S <= 0) return;
-    k_schedule<<<nt * S, kSchedThreads, 0, st>>>(n, rp, adj, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                                  t0, S, slots, order, lvl_ptr, nlev, skey, scnt,
-                                                  ell, W, pos);
+    size_t smem = (size_t)n * 8 <= kSchedSmemMax ? (size_t)n * 8 : 0;
+    if (allow_dynamic_smem(k_schedule, smem) != cudaSuccess) smem = 0;   // the global-scratch path
+    k_schedule<<<nt * S, kSchedThreads, smem, st>>>(n, rp, adj, (uint32_t)seed, (uint32_t)(seed >> 32),
+                                                     t0, S, slots, order, lvl_ptr, nlev, skey, scnt,
+                                                     ell, W, pos, smem);
 }
 
-void launch_schedule_batched(const SchedDesc *descs, const int2 *items, int32_t nitems, cudaStream_t st) {
+void launch_schedule_batched(const SchedDesc *descs, const int2 *items, int32_t nitems, int32_t n_max,
+                             cudaStream_t st) {
     if (nitems <= 0) return;
-    k_schedule_batched<<<nitems, kSchedThreads, 0, st>>>(descs, items);
+    // members whose 8n bytes exceed this use their global scratch
+    size_t smem = std::min((size_t)n_max * 8, kSchedSmemMax);
+    if (allow_dynamic_smem(k_schedule_batched, smem) != cudaSuccess) smem = 0;   // the global-scratch path
+    k_schedule_batched<<<nitems, kSchedThreads, smem, st>>>(descs, items, smem);
 }
 
 }  // namespace pamc
