@@ -61,7 +61,7 @@ PROFILED_TRAFFIC = {
                               "e17e3bcc4115ff182f430c678f68cca954727ae6"}),
     # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.688 GB) scaled by n^2 to n=100,000
     "dense_sweep_100k": (1.688e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
-                                                           "ae2cde87d490480f47b0e3c871a0625737771e63"}),
+                                                           "6a66522d06fdb69ae910862d82054a0150aecbe8"}),
 }
 
 
