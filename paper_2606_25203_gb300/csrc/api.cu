@@ -204,8 +204,9 @@ void release_run(pamc_handle h) {
 // Launch shape of the sweep kernel: groups per CTA, warps per group and
 // lanes per vertex.  Ising runs on ELL schedules give each group a CTA of its
 // own, sized for the latency of a level, unless the SMs are shared and the
-// levels are too wide for more than one lane per vertex.  Otherwise every
-// (gpc, wpg) is scored by the fraction of group slots used
+// levels are too wide for more than one lane per vertex; Potts runs do the
+// same (one lane per vertex) where an average level fits the group's share
+// of the SM in one pass.  Otherwise every (gpc, wpg) is scored by the fraction of group slots used
 // over whole waves, the lane efficiency of a level (average level size over
 // the lanes of a group), and resident warps per SM; Ising runs on ELL
 // schedules then give the lanes a level leaves idle to the couplings (the
@@ -247,6 +248,17 @@ SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level,
         while (c.warps_per_group * 32 < lanes && 32.0 * c.warps_per_group < lev * c.lanes_per_vertex)
             c.warps_per_group *= 2;
         if ((per_sm <= 1 || c.lanes_per_vertex > 1) && sweep_smem_bytes(kind, n, H, c) <= 227 * 1024) return c;
+    }
+    if (kind != 0) {
+        // Potts: one group per CTA with warps for one pass over an average
+        // level, where that fits the group's share of the SM; wide levels or
+        // crowded SMs take the scoring below
+        const int64_t per_sm = (groups + sms - 1) / std::max(sms, 1);
+        int lanes = 1024;
+        while (lanes > 32 && (int64_t)lanes * per_sm > 1024) lanes >>= 1;
+        SweepCfg c{1, 1, 1};
+        while (c.warps_per_group < 32 && 32.0 * c.warps_per_group < std::max(avg_level, 1.0)) c.warps_per_group *= 2;
+        if (32 * c.warps_per_group <= lanes && sweep_smem_bytes(kind, n, H, c) <= 227 * 1024) return c;
     }
     SweepCfg best{1, 1};
     double best_score = -1.0;
