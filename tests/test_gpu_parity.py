@@ -138,6 +138,19 @@ def test_lanes_per_vertex_shapes(pg, monkeypatch, cfg, rule):
                     z_rst=4, cooldown_tau=1, seed=9)
 
 
+@pytest.mark.parametrize("rule", [0, 2])
+def test_potts_launch_shapes_same_results(pg, monkeypatch, rule):
+    """Potts sweeps under several forced launch shapes (groups per CTA,
+    warps per group) give the oracle's labels and energies."""
+    inst = W.gnm(700, 4200, signed=False, seed=12)
+    params = dict(kind=1, rule=rule, R=24, sweeps=2, beta0=0.2, beta1=2.5, seed=6)
+    if rule == 2:
+        params.update(K=3, gamma=1.0)
+    for cfg in ("1,1", "1,4", "3,2", "2,8"):
+        monkeypatch.setenv("PAMC_SWEEP_CFG", cfg)
+        compare_run(pg, inst, 4, **params)
+
+
 def test_lanes_per_vertex_default_choice(pg, monkeypatch):
     """Narrow-level dense-row instances get several lanes per vertex; the
     torus (rows of four) keeps one."""
