@@ -95,6 +95,39 @@ schedule_body(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restr
     }
     if (threadIdx.x == 0) nlev[base] = L;
     __syncthreads();
+    // Within a level the order is free (its vertices are uncoupled), so each
+    // level is grouped by degree (counting sort into eight classes, stable
+    // enough for the purpose): the lanes of a warp then walk rows of similar
+    // length in the sweep.  The counters' array is free now and holds the
+    // sorted copy.
+    {
+        __shared__ int32_t bc[8];
+        int32_t *tmp = cnt;
+        auto dclass = [&](int32_t k) {
+            const int32_t d = rp[k + 1] - rp[k];
+            return d <= 4 ? 0 : d <= 8 ? 1 : d <= 12 ? 2 : d <= 16 ? 3 : d <= 24 ? 4 : d <= 32 ? 5 : d <= 64 ? 6 : 7;
+        };
+        for (int32_t l = 0; l < L; ++l) {
+            const int32_t b0 = lp[l], b1 = lp[l + 1];
+            if (b1 - b0 < 64) continue;   // one or two warps: nothing to gain
+            if (threadIdx.x < 8) bc[threadIdx.x] = 0;
+            __syncthreads();
+            for (int32_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) atomicAdd(&bc[dclass(ord[i])], 1);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int32_t acc = b0;
+                for (int c = 0; c < 8; ++c) { const int32_t v = bc[c]; bc[c] = acc; acc += v; }
+            }
+            __syncthreads();
+            for (int32_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+                const int32_t k = ord[i];
+                tmp[atomicAdd(&bc[dclass(k)], 1)] = k;
+            }
+            __syncthreads();
+            for (int32_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) ord[i] = tmp[i];
+            __syncthreads();
+        }
+    }
     // Position-indexed neighbour lists: order[i] becomes k | deg << 24 (deg =
     // nonzero couplings).  With an ELL buffer (width W, a multiple of 4) the
     // couplings of position i go to ell[(i/32)*32*W + s*32 + i%32], s < deg,
