@@ -5,7 +5,7 @@
  * -ffp-contract=off so that every floating-point operation is exactly the one
  * written; the only fused operation is the explicit fma() of det_exp.
  *
- * Conventions (readings of the paper, listed in the design doc):
+ * Conventions (readings of the paper where it is silent or ambiguous):
  *  - Ising energy H(s) = -sum_{i<j} J_ij s_i s_j (Sec. I; each pair once),
  *    Max-Cut couplings J = -w, so cut = (W - H)/2 with W = sum_{i<j} w_ij.
  *  - Potts energy (Eq. 6) with the same pair convention and J = -w, so the
@@ -115,6 +115,9 @@ uint64_t orc_thr_potts_b2(double beta, int64_t c) {
 /* ------------------------------------------------------------------ */
 /* Randomised sweep order (Sec. II.A, last sentence before Sec. II.B). */
 /* ------------------------------------------------------------------ */
+/* Reading: the paper asks only for a random order.  One order per
+ * (step, sweep), shared by every replica: the indices sorted by a 32-bit
+ * PERM draw, the index breaking ties. */
 typedef struct { uint32_t key; int32_t idx; } orc_keyed;
 
 static int orc_cmp_keyed(const void *a, const void *b) {
@@ -139,6 +142,13 @@ void orc_permutation(int32_t n, uint64_t seed, int32_t t, int32_t sweep, int32_t
 /* ------------------------------------------------------------------ */
 /* Systematic resampling (Eq. 1-2; Fig. 2).                            */
 /* ------------------------------------------------------------------ */
+/* Readings: tau_j are expected copy numbers summing to R (Eq. 1 as printed
+ * normalises them to 1, which contradicts Q = (1/R) sum of Eq. 2); the
+ * population size stays R and the copies are drawn by systematic resampling
+ * over the inclusive prefix of integer weights; the paper gives no energy
+ * shift, so the weights are taken relative to E_min (cooling) or E_max
+ * (reheating), which keeps exp from underflowing and gives the reference
+ * replica weight 1. */
 int orc_resample(int32_t R, const int64_t *E, double delta, double escale, uint64_t seed,
                  int32_t t, int32_t *parent, int32_t *count) {
     if (R <= 0) return -1;
@@ -261,7 +271,9 @@ static void orc_refresh_replica(orc_state *st, int32_t r) {
     st->E[r] = orc_energy_replica(st, st->s + (size_t)r * n);
 }
 
-/* Random initial population (Algorithm 1, Initialization), keyed by step t. */
+/* Random initial population (Algorithm 1, Initialization), keyed by step t.
+ * Reading: a restart that resets the system draws a fresh population with
+ * the key of the step at which it happens. */
 static void orc_init_population(orc_state *st, int32_t t) {
     int32_t n = st->n, R = st->p.R;
     for (int32_t r = 0; r < R; ++r) {
@@ -347,7 +359,9 @@ void orc_destroy(orc_state *st) {
 /* ------------------------------------------------------------------ */
 /* Ising, Eq. 3-4: visit the spins in the sweep's order; heat-bath sets
  * s_k = +1 iff u < T(h_k); Metropolis flips iff u < T_M(2 s_k h_k).  On a
- * change the neighbours' fields move by 2 s_k^new J_jk. */
+ * change the neighbours' fields move by 2 s_k^new J_jk.  Readings: the pair
+ * sum runs over i < j, so Eq. 4 is the exact conditional; the draw u / 2^32
+ * plays r, and u == T (the tie of sgn(0)) gives -1. */
 static void orc_sweep_ising(orc_state *st, int32_t r, const int32_t *perm, int32_t sweep) {
     int32_t n = st->n;
     int8_t *s = st->s + (size_t)r * n;
@@ -458,6 +472,10 @@ static void orc_sweep_potts_softmax(orc_state *st, int32_t r, const int32_t *per
 /* ------------------------------------------------------------------ */
 /* Non-local cluster move (Sec. II.C, NCM bullet)                      */
 /* ------------------------------------------------------------------ */
+/* Readings: the paper fixes neither the number of greedy MIS trials nor the
+ * number of low-energy replicas that take the move; both are parameters.
+ * Trial a orders the iso-sites by an NCM draw keyed (site, a, step, replica);
+ * the largest set wins, ties to the earliest trial. */
 int32_t orc_ncm_replica(int32_t n, const int32_t *rp, const int32_t *col, const int32_t *J,
                         int8_t *s, int32_t *h, int32_t mis_trials, uint64_t seed, int32_t t,
                         int32_t r) {
@@ -529,6 +547,11 @@ static int32_t orc_distinct_last(const int64_t *hist, int32_t len, int32_t w) {
 /* Adaptive temperature control and restart (Algorithm 1, after the    */
 /* sweeps; the stagnation rule of Sec. II.C, second bullet).           */
 /* ------------------------------------------------------------------ */
+/* Readings: where the branches of Algorithm 1 and the text disagree the text
+ * is taken -- progress keeps cooling; a stagnant short window alone reverses
+ * the update only above beta0, and the listing's early exit changes nothing;
+ * control runs once the history holds win_long values; a restart clears the
+ * history and returns to beta0; beta advances by repeated addition. */
 int orc_control(orc_ctl *c, const orc_params *p, double dbeta, int64_t mstar) {
     /* record M* in the recent-progress history (the last win_long values) */
     int32_t hl = p->win_long > p->win_short ? p->win_long : p->win_short;
@@ -577,6 +600,9 @@ int orc_control(orc_ctl *c, const orc_params *p, double dbeta, int64_t mstar) {
 /* ------------------------------------------------------------------ */
 static void orc_iteration(orc_state *st) {
     int32_t n = st->n, R = st->p.R, F = nf(st);
+    /* Reading: the Potts update follows Eq. 8 literally (P ~ e^{beta syn_k}),
+     * which samples e^{-(beta/2) E} with E of Eq. 6, so the reweighting uses
+     * half the energy for Potts. */
     double escale = st->p.kind == 1 ? 0.5 : 1.0;
     st->ncm_last = 0;
     for (int32_t r = 0; r < R; ++r) { st->parent[r] = r; st->count[r] = 1; }

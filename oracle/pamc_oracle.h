@@ -9,8 +9,8 @@
  * load it.  It shares no code, header or table with the CUDA library.
  *
  * Every function follows the paper's text step by step (section / equation /
- * algorithm cited beside it) with plain loops, in the reading documented in
- * the design doc where the paper is silent or ambiguous.
+ * algorithm cited beside it) with plain loops; where the paper is silent or
+ * ambiguous the reading taken is stated beside the function.
  *
  * Parity unpinned (defined only by the reading, no independent pin exists):
  * the exact controller trajectory of Algorithm 1 under stagnation, the NCM
