@@ -7,7 +7,8 @@ with R=4,096 replicas, 10 sweeps per temperature step, beta 0.1 -> 4.0 over
 500 steps, adaptive reheating + NCM on, restart every 400 steps.  One timed
 "step" is one iteration of Algorithm 1 (resample, NCM, 10 sweeps, energies,
 M*, control) on BOTH instances.  attempts per step = R * N * S summed over the
-two instances.
+two instances.  The timed steps are steps 0..K-1 of a fresh run after W
+warm-up steps on a throwaway one; by default K = 500, the whole schedule.
 
 Timing: device time with CUDA events on the library's stream, one event pair
 per step; between timed steps a 512 MB buffer is written to flush L2 (the
@@ -79,50 +80,101 @@ def profiled_traffic(key):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    One nvidia-smi process in loop mode (-lms) runs across the region; each
+    sample carries nvidia-smi's own timestamp, and the summary keeps the
+    samples that fall between the host times at which the region opened and
+    closed.  The process is stopped with SIGINT (its normal end of loop mode),
+    which flushes its output."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    INTERVAL_MS = 20
+    WARM_IN_S = 0.5     # nvidia-smi start-up before the region opens
 
     def __init__(self, index: int = 0):
         self.index = index
-        self.samples = []
-        self._stop = threading.Event()
-        self._t = None
+        self.samples = []          # (unix time or None, [sm, max, power, 4 reasons])
+        self.t0 = self.t1 = None
+        self._proc = None
+        self._started = 0.0
 
-    def _run(self):
-        while not self._stop.is_set():
+    @staticmethod
+    def parse_line(line: str):
+        import datetime
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 8:
+            return None
+        try:
+            ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        return ts, f[1:8]
+
+    def start(self):
+        """Start nvidia-smi ahead of the region (e.g. before the warm-up
+        steps, so that its start-up does not leave the GPU idle)."""
+        if self._proc is None:
             try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+                self._proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                     "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self._started = time.time()
+            except OSError:
+                self._proc = None
+        return self
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        self.start()
+        if self._proc is not None:
+            time.sleep(max(0.0, self.WARM_IN_S - (time.time() - self._started)))
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        import signal
+        self.t1 = time.time()
+        if self._proc is None:
+            return
+        try:
+            time.sleep(2 * self.INTERVAL_MS / 1e3)   # one more sample after the region closes
+            self._proc.send_signal(signal.SIGINT)
+            out, _ = self._proc.communicate(timeout=10)
+        except Exception:
+            self._proc.kill()
+            out, _ = self._proc.communicate()
+        for line in (out or "").splitlines():
+            r = self.parse_line(line)
+            if r is not None:
+                self.samples.append(r)
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
-                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+        inside = [f for ts, f in self.samples
+                  if ts is not None and self.t0 is not None and self.t0 <= ts <= self.t1]
+        window = "timed region"
+        if not inside:
+            # a region shorter than the sampling interval: the samples nearest to it
+            near = sorted((abs(ts - (self.t0 + self.t1) / 2), f) for ts, f in self.samples if ts is not None)
+            inside = [f for _, f in near[:2]] or [f for _, f in self.samples]
+            window = "nearest to the timed region"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(f[0]) for f in inside) if v is not None]
+        mx = [v for v in (num(f[1]) for f in inside) if v is not None]
+        reasons = sorted({self.REASONS[i] for f in inside for i in range(4) if f[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "sm_mhz_min": min(sm) if sm else None, "reasons": reasons, "samples": len(inside),
+                "window": window, "region_s": round(self.t1 - self.t0, 4)}
 
 
 ONLY = None
@@ -236,9 +288,14 @@ def run_ours(args):
         s.init(**dict(PARAMS, seed=rank_seed(PARAMS["seed"], rank)))
         solvers.append(s)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    clk = ClockSampler(local).start()
     for _ in range(args.warmup):
         for s in solvers:
             s.step(1)
+    # the timed steps are steps 0..K-1 of a fresh run: the work of a step
+    # depends on where it is in the schedule (control, NCM, restart)
+    for s in solvers:
+        s.init(**dict(PARAMS, seed=rank_seed(PARAMS["seed"], rank)))
     torch.cuda.synchronize()
     launches0 = sum(s.launches() for s in solvers)
     if dist:
@@ -246,7 +303,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    with ClockSampler(local) as clk:
+    with clk:
         for k in range(args.steps):
             flush.add_(1)
             ev[k][0].record(stream)
@@ -267,7 +324,7 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "attempts/s",
                               "ms_per_step": ms / args.steps, "gpu_launches": launches,
-                              "config": {"only": ONLY}}))
+                              "clocks": clk.summary(), "config": {"only": ONLY}}))
         for s in solvers:
             s.close()
         return None
@@ -290,6 +347,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "R": R, "sweeps_per_step": SWEEPS,
                        "attempts_per_step": attempts_per_step(insts), "l2": "flushed between steps (512 MB write)",
+                       "timed_steps": f"steps 0..{args.steps - 1} of a fresh run ({STEPS_SCHEDULE}-step schedule, "
+                                      f"restart every {PARAMS['z_rst']})",
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                          "frac": achieved / peak_tops, "traffic": profiled_traffic("sweep_torus"),
@@ -793,7 +852,8 @@ def run_diag(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the whole 500-step schedule for the sparse workload, 20 otherwise)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--only", choices=["torus", "sparse"], default=None,
@@ -810,6 +870,8 @@ def main():
     ap.add_argument("--serve-max-active", type=int, default=64)
     ap.add_argument("--dense-n", type=int, default=DENSE_N)
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = STEPS_SCHEDULE if (args.workload == "sparse" and args.impl == "ours") else 20
     global ONLY
     ONLY = args.only
     if args.workload == "dense100k" and args.impl == "ours":

@@ -25,7 +25,8 @@ namespace pamc {
 cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint64_t *tab,
                           cudaStream_t st);
 cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
-                        int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, cudaStream_t st);
+                        int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, uint64_t *qbuf,
+                        cudaStream_t st);
 cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
                        const int8_t *src, const int64_t *E_src, const int32_t *parent,
                        const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey, uint8_t *nstat,
@@ -74,6 +75,7 @@ struct pamc_handle_s {
     int8_t *d_spins[2] = {nullptr, nullptr};
     int64_t *d_E[2] = {nullptr, nullptr};
     int32_t *d_parent = nullptr, *d_count = nullptr, *d_ncm_idx = nullptr, *d_targets = nullptr;
+    uint64_t *d_q = nullptr;   // resampling weights (sparse handles)
     int32_t *d_fam = nullptr;   // [2][R] lineage (family of each slot)
     int8_t *d_ncm_buf = nullptr;
     uint32_t *d_nkey = nullptr;
@@ -412,7 +414,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
                                           h->d_boff, h->d_ctl, h->stream);
         if (e == cudaSuccess)
             e = launch_prep(pp, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
-                            h->stream);
+                            nullptr, h->stream);
         if (e == cudaSuccess) e = launch_dense_tables(p.rule, h->dense_Hc, n, h->d_ctl, h->d_tab, h->stream);
         if (e == cudaSuccess)
             e = dense_recompute(h, src, h->d_parent, h->d_ncm_idx, -1);
@@ -574,6 +576,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     bool ok = alloc_n(h, h->d_spins[0], (size_t)R * n, h->bufs) &&
               alloc_n(h, h->d_spins[1], (size_t)R * n, h->bufs) &&
               alloc_n(h, h->d_E[0], R, h->bufs) && alloc_n(h, h->d_E[1], R, h->bufs) &&
+              alloc_n(h, h->d_q, R, h->bufs) &&
               alloc_n(h, h->d_parent, R, h->bufs) && alloc_n(h, h->d_count, R, h->bufs) &&
               alloc_n(h, h->d_fam, 2 * (size_t)R, h->bufs) &&
               alloc_n(h, h->d_ncm_idx, R, h->bufs) && alloc_n(h, h->d_targets, R, h->bufs) &&
@@ -677,9 +680,9 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
         int8_t *src = h->d_spins[t & 1], *dst = h->d_spins[(t + 1) & 1];
         int64_t *Es = h->d_E[t & 1], *Ed = h->d_E[(t + 1) & 1];
         e = launch_prep(p, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
-                        h->stream);
+                        h->d_q, h->stream);
         if (e == cudaSuccess) e = launch_tables(p.kind, p.rule, h->H, h->d_ctl, h->d_tab, h->stream);
-        h->launches += 2;
+        h->launches += 3;
         if (e == cudaSuccess && p.stagnation && p.kind == 0) {
             e = launch_ncm(n, h->d_rp, h->d_adj, p, src, Es, h->d_parent, h->d_targets, h->d_ncm_buf,
                            h->d_nkey, h->d_nstat, h->d_ctl, h->stream);
@@ -1134,7 +1137,7 @@ size_t pamc_footprint(pamc_handle h, const pamc_params *p) {
     if (!h || !p || h->dense) return 0;
     const size_t n = (size_t)h->n, R = (size_t)std::max(p->R, 1), S = (size_t)std::max(p->sweeps, 1);
     const size_t slots = kSchedSlots;
-    size_t b = 2 * R * n + 2 * R * 8 + 4 * R * 4 + 2 * R * 4 + n;
+    size_t b = 2 * R * n + 3 * R * 8 + 4 * R * 4 + 2 * R * 4 + n;
     b += slots * S * (n * 4 + (n + 1) * 4 + 4 + n * 4 + n * 4);
     if (h->ell_w > 0) b += slots * S * (((n + 31) / 32) * 32 * (size_t)h->ell_w * 4 + n * 8);
     b += (size_t)(p->kind == 0 ? 2 * h->H + 1 : (4 * h->H + 1) * (4 * h->H + 1) + 4 * h->H + 1) * 8;

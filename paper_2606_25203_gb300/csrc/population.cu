@@ -1,6 +1,8 @@
 // population.cu -- the population step and the controller of Algorithm 1:
 //   k_tables   acceptance thresholds for the current beta (Eq. 4, Metropolis,
 //              Suppl. S3), in binary64 with the deterministic exp;
+//   k_weights  the binary64 resampling weights of Eq. 1 as 64-bit fixed-point
+//              integers, spread over many CTAs;
 //   k_prep     Boltzmann reweighting and resampling (Eq. 1-2) as systematic
 //              resampling over an integer prefix scan of 64-bit fixed-point
 //              weights, and selection of the NCM targets;
@@ -93,12 +95,46 @@ __device__ T block_reduce(T v, Op op, T *sbuf) {
 
 // ---------------------------------------------------------------- resampling
 constexpr int kPrepThreads = 1024;
+constexpr int kWeightThreads = 256;
+
+// Integer resampling weights q_r = floor(2^S * w_r), w_r = exp(-|Delta| d_r)
+// (Eq. 1, the one binary64 step), spread over ceil(R / 256) CTAs: binary64
+// arithmetic runs at a small fraction of the integer rate, so R weights in a
+// single CTA would keep one SM busy for tens of microseconds.  Every CTA
+// reduces E_min / E_max over the whole population itself.  Writes nothing
+// when the step does not resample.
+__global__ void __launch_bounds__(kWeightThreads)
+k_weights(int32_t R, int32_t kind, int32_t do_resample, const int64_t *__restrict__ E_src,
+          const DevCtl *__restrict__ ctl, uint64_t *__restrict__ q) {
+    __shared__ long long red_ll[32];
+    if (ctl->done || !(ctl->z > 1 && do_resample)) return;
+    const double delta = ctl->delta;
+    long long lmin = LLONG_MAX, lmax = LLONG_MIN;
+    for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
+        lmin = min(lmin, (long long)E_src[r]);
+        lmax = max(lmax, (long long)E_src[r]);
+    }
+    const long long emin = block_reduce(lmin, [](long long a, long long b) { return a < b ? a : b; }, red_ll);
+    const long long emax = block_reduce(lmax, [](long long a, long long b) { return a > b ? a : b; }, red_ll);
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    int lg = 0;
+    while ((1ll << lg) < (long long)R) ++lg;
+    const int S = 62 - lg;
+    const double a = __dmul_rn(fabs(delta), kind == 1 ? 0.5 : 1.0);
+    long long d = 0;
+    if (delta > 0) d = (long long)E_src[r] - emin;
+    else if (delta < 0) d = emax - (long long)E_src[r];
+    const double w = det_exp(-__dmul_rn(a, (double)d));
+    q[r] = (uint64_t)floor(ldexp(w, S));
+}
 
 __device__ __forceinline__ void
 prep_body(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau, uint32_t key0,
           uint32_t key1, const int64_t *__restrict__ E_src, DevCtl *__restrict__ ctl,
           int32_t *__restrict__ parent, int32_t *__restrict__ count, int32_t *__restrict__ ncm_idx,
-          int32_t *__restrict__ targets, int32_t *__restrict__ fam, int32_t fam_reset) {
+          int32_t *__restrict__ targets, int32_t *__restrict__ fam, int32_t fam_reset,
+          const uint64_t *__restrict__ qpre) {
     extern __shared__ __align__(16) unsigned char sm[];
     uint64_t *C = reinterpret_cast<uint64_t *>(sm);             // R prefix sums
     int32_t *cnt = reinterpret_cast<int32_t *>(sm + (size_t)R * 8);
@@ -117,13 +153,18 @@ prep_body(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t t
     __syncthreads();
     if (resampled) {
         // shift by the extreme energy: the reference replica has weight 1
+        // (the weights come precomputed by k_weights when qpre is given)
         long long lmin = LLONG_MAX, lmax = LLONG_MIN;
-        for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
-            lmin = min(lmin, (long long)E_src[r]);
-            lmax = max(lmax, (long long)E_src[r]);
+        if (!qpre) {
+            for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
+                lmin = min(lmin, (long long)E_src[r]);
+                lmax = max(lmax, (long long)E_src[r]);
+            }
         }
-        const long long emin = block_reduce(lmin, [](long long a, long long b) { return a < b ? a : b; }, red_ll);
-        const long long emax = block_reduce(lmax, [](long long a, long long b) { return a > b ? a : b; }, red_ll);
+        const long long emin =
+            qpre ? 0 : block_reduce(lmin, [](long long a, long long b) { return a < b ? a : b; }, red_ll);
+        const long long emax =
+            qpre ? 0 : block_reduce(lmax, [](long long a, long long b) { return a > b ? a : b; }, red_ll);
         int lg = 0;
         while ((1ll << lg) < (long long)R) ++lg;
         const int S = 62 - lg;
@@ -133,11 +174,16 @@ prep_body(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t t
         const int32_t lo = min(R, (int32_t)threadIdx.x * per), hi = min(R, lo + per);
         unsigned long long local = 0;
         for (int32_t r = lo; r < hi; ++r) {
-            long long d = 0;
-            if (delta > 0) d = (long long)E_src[r] - emin;
-            else if (delta < 0) d = emax - (long long)E_src[r];
-            const double w = det_exp(-__dmul_rn(a, (double)d));
-            const uint64_t q = (uint64_t)floor(ldexp(w, S));
+            uint64_t q;
+            if (qpre) {
+                q = qpre[r];
+            } else {
+                long long d = 0;
+                if (delta > 0) d = (long long)E_src[r] - emin;
+                else if (delta < 0) d = emax - (long long)E_src[r];
+                const double w = det_exp(-__dmul_rn(a, (double)d));
+                q = (uint64_t)floor(ldexp(w, S));
+            }
             local += q;
             C[r] = local;   // chunk-local inclusive prefix
         }
@@ -221,9 +267,10 @@ __global__ void __launch_bounds__(kPrepThreads)
 k_prep(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau, uint32_t key0,
        uint32_t key1, const int64_t *__restrict__ E_src, DevCtl *__restrict__ ctl,
        int32_t *__restrict__ parent, int32_t *__restrict__ count, int32_t *__restrict__ ncm_idx,
-       int32_t *__restrict__ targets, int32_t *__restrict__ fam, int32_t fam_reset) {
+       int32_t *__restrict__ targets, int32_t *__restrict__ fam, int32_t fam_reset,
+       const uint64_t *__restrict__ qpre) {
     prep_body(R, kind, do_resample, n_top, tau, key0, key1, E_src, ctl, parent, count, ncm_idx, targets, fam,
-              fam_reset);
+              fam_reset, qpre);
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep_batched(const PrepDesc *__restrict__ descs) {
@@ -231,7 +278,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_batched(const PrepDesc *_
     const int32_t t = d.ctl->t;
     if (t >= d.t_end) return;
     prep_body(d.R, d.kind, d.do_resample, d.n_top, d.tau, d.key0, d.key1, d.en[t & 1], d.ctl, d.parent, d.count,
-              d.ncm_idx, d.targets, d.fam, d.fam_reset);
+              d.ncm_idx, d.targets, d.fam, d.fam_reset, nullptr);
 }
 
 // ---------------------------------------------------------------- NCM
@@ -358,16 +405,15 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
 // ---------------------------------------------------------------- controller
 constexpr int kCtlThreads = 1024;
 
-__device__ int32_t distinct_last(const int64_t *h, int32_t len, int32_t w) {
+// Entry i of the last w history values counts as distinct when no earlier
+// entry of that window holds the same value; one entry per thread, summed by
+// the barrier count (the history sits in shared memory).
+__device__ __forceinline__ bool distinct_entry(const long long *h, int32_t len, int32_t w, int32_t i) {
     if (w > len) w = len;
-    int32_t d = 0;
-    for (int32_t i = len - w; i < len; ++i) {
-        bool seen = false;
-        for (int32_t q = len - w; q < i; ++q)
-            if (h[q] == h[i]) { seen = true; break; }
-        if (!seen) ++d;
-    }
-    return d;
+    if (i < len - w || i >= len) return false;
+    for (int32_t q = len - w; q < i; ++q)
+        if (h[q] == h[i]) return false;
+    return true;
 }
 
 __device__ __forceinline__ void
@@ -378,6 +424,8 @@ control_body(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst,
     __shared__ long long s_e[32];
     __shared__ int s_i[32];
     __shared__ int s_improved, s_rb;
+    __shared__ long long s_hist[kHistMax];
+    __shared__ int s_len, s_gate;
     if (ctl->done) return;
     // argmin of (E, index): the replica with the largest cut, lowest index on ties
     long long be = LLONG_MAX;
@@ -406,20 +454,36 @@ control_body(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst,
         const int8_t *row = spins + (size_t)s_rb * n;
         for (int32_t k = threadIdx.x; k < n; k += blockDim.x) best[k] = row[k];
     }
-    if (threadIdx.x != 0) return;
     DevCtl &c = *ctl;
-    int32_t hl = win_long > win_short ? win_long : win_short;
-    if (hl > kHistMax) hl = kHistMax;
-    if (hl > 0) {
-        if (c.hist_len == hl) {
-            for (int32_t i = 0; i + 1 < hl; ++i) c.hist[i] = c.hist[i + 1];
-            c.hist_len = hl - 1;
+    // record M* in the recent-progress history (the last max(windows) values),
+    // shifted in shared memory and written back by all threads
+    const int32_t len0 = c.hist_len;
+    for (int32_t i = threadIdx.x; i < len0; i += blockDim.x) s_hist[i] = c.hist[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t hl = win_long > win_short ? win_long : win_short;
+        if (hl > kHistMax) hl = kHistMax;
+        int32_t len = len0;
+        if (hl > 0) {
+            if (len == hl) {
+                for (int32_t i = 0; i + 1 < hl; ++i) s_hist[i] = s_hist[i + 1];
+                len = hl - 1;
+            }
+            s_hist[len++] = c.mstar;
         }
-        c.hist[c.hist_len++] = c.mstar;
+        s_len = len;
+        s_gate = stagnation && c.cooldown == 0 && hl > 0 && len >= hl;
     }
-    if (stagnation && c.cooldown == 0 && hl > 0 && c.hist_len >= hl) {
-        const int32_t ds = distinct_last(c.hist, c.hist_len, win_short);
-        const int32_t dl = distinct_last(c.hist, c.hist_len, win_long);
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < s_len; i += blockDim.x) c.hist[i] = s_hist[i];
+    if (threadIdx.x == 0) c.hist_len = s_len;
+    int32_t ds = 0, dl = 0;
+    if (s_gate) {   // uniform over the block
+        ds = __syncthreads_count(distinct_entry(s_hist, s_len, win_short, (int32_t)threadIdx.x));
+        dl = __syncthreads_count(distinct_entry(s_hist, s_len, win_long, (int32_t)threadIdx.x));
+    }
+    if (threadIdx.x != 0) return;
+    if (s_gate) {
         if (ds <= max_ds && dl <= max_dl) {
             c.beta = __dmul_rn(reheat, c.beta);
             c.delta = c.dbeta;
@@ -487,14 +551,18 @@ cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint
 size_t prep_smem_bytes(int32_t R) { return (size_t)R * 8 + (size_t)R * 4; }
 
 cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
-                        int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, cudaStream_t st) {
+                        int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, uint64_t *qbuf,
+                        cudaStream_t st) {
     const size_t smem = prep_smem_bytes(p.R);
     cudaError_t err = allow_dynamic_smem(k_prep, smem);
     if (err != cudaSuccess) return err;
+    if (qbuf)
+        k_weights<<<(p.R + kWeightThreads - 1) / kWeightThreads, kWeightThreads, 0, st>>>(p.R, p.kind, p.resample,
+                                                                                          E_src, ctl, qbuf);
     k_prep<<<1, kPrepThreads, smem, st>>>(p.R, p.kind, p.resample, p.n_top, p.cooldown_tau,
                                           (uint32_t)p.seed, (uint32_t)(p.seed >> 32), E_src, ctl,
                                           parent, count, ncm_idx, targets, fam,
-                                          p.z_rst > 0 && p.restart_reinit ? 1 : 0);
+                                          p.z_rst > 0 && p.restart_reinit ? 1 : 0, qbuf);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,55 @@
+"""Host-side logic of the benchmark: the clock record kept beside each number."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _line(ts, sm, reasons=("Not Active",) * 4):
+    return ", ".join([ts, str(sm), "2070", "812.40", *reasons])
+
+
+def test_clock_line_parses_timestamp_and_fields():
+    ts, f = bench.ClockSampler.parse_line(_line("2026/12/03 01:52:33.125", 2070))
+    import datetime
+    assert ts == datetime.datetime(2026, 12, 3, 1, 52, 33, 125000).timestamp()
+    assert f[0] == "2070" and f[1] == "2070" and len(f) == 7
+    assert bench.ClockSampler.parse_line("garbage") is None
+
+
+def test_clock_summary_keeps_only_samples_inside_the_region():
+    c = bench.ClockSampler(0)
+    c.t0, c.t1 = 100.0, 101.0
+    act = ("Not Active", "Not Active", "Not Active", "Active")
+    hot = ("Active", "Not Active", "Not Active", "Not Active")
+    c.samples = [
+        (99.5, ["1200", "2070", "500", *hot]),      # before the region: ignored
+        (100.2, ["2070", "2070", "900", *act]),
+        (100.5, ["2055", "2070", "950", *act]),
+        (100.9, ["2040", "2070", "990", "Not Active", "Not Active", "Not Active", "Not Active"]),
+        (101.5, ["900", "2070", "400", *hot]),      # after: ignored
+    ]
+    s = c.summary()
+    assert s["samples"] == 3 and s["window"] == "timed region"
+    assert s["sm_mhz"] == 2055.0 and s["sm_mhz_min"] == 2040.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_short_region_takes_nearest_samples():
+    c = bench.ClockSampler(0)
+    c.t0, c.t1 = 100.00, 100.01
+    c.samples = [(99.0, ["1000", "2070", "1", "Not Active", "Not Active", "Not Active", "Not Active"]),
+                 (100.02, ["2070", "2070", "1", "Not Active", "Not Active", "Not Active", "Not Active"]),
+                 (99.98, ["2060", "2070", "1", "Not Active", "Not Active", "Not Active", "Not Active"])]
+    s = c.summary()
+    assert s["window"] == "nearest to the timed region" and s["samples"] == 2
+    assert s["sm_mhz"] == 2065.0
+
+
+def test_clock_summary_without_samples():
+    c = bench.ClockSampler(0)
+    c.t0, c.t1 = 1.0, 2.0
+    assert c.summary()["reasons"] == ["unsampled"]
