@@ -29,7 +29,7 @@ cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl,
                         cudaStream_t st);
 cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
                        const int8_t *src, const int64_t *E_src, const int32_t *parent,
-                       const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey, uint8_t *nstat,
+                       const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey,
                        DevCtl *ctl, cudaStream_t st);
 cudaError_t launch_control(int32_t n, int64_t W, const pamc_params &p, const int64_t *E,
                            const int8_t *spins, int8_t *best, DevCtl *ctl, cudaStream_t st);
@@ -79,7 +79,6 @@ struct pamc_handle_s {
     int32_t *d_fam = nullptr;   // [2][R] lineage (family of each slot)
     int8_t *d_ncm_buf = nullptr;
     uint32_t *d_nkey = nullptr;
-    uint8_t *d_nstat = nullptr;
     uint64_t *d_tab = nullptr;
     int32_t *d_order = nullptr, *d_lvl = nullptr, *d_nlev = nullptr, *d_scnt = nullptr;
     uint32_t *d_skey = nullptr;
@@ -596,8 +595,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     }
     if (ok && p.stagnation && p.kind == 0)
         ok = alloc_n(h, h->d_ncm_buf, (size_t)ntop * n, h->bufs) &&
-             alloc_n(h, h->d_nkey, (size_t)ntop * n, h->bufs) &&
-             alloc_n(h, h->d_nstat, (size_t)ntop * n, h->bufs);
+             alloc_n(h, h->d_nkey, (size_t)ntop * n, h->bufs);
     if (!ok) {
         release_run(h);
         return fail(h, PAMC_ERR_OOM, "device allocation of the population failed");
@@ -685,7 +683,7 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
         h->launches += 3;
         if (e == cudaSuccess && p.stagnation && p.kind == 0) {
             e = launch_ncm(n, h->d_rp, h->d_adj, p, src, Es, h->d_parent, h->d_targets, h->d_ncm_buf,
-                           h->d_nkey, h->d_nstat, h->d_ctl, h->stream);
+                           h->d_nkey, h->d_ctl, h->stream);
             h->launches += 1;
         }
         SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w};
@@ -1141,7 +1139,7 @@ size_t pamc_footprint(pamc_handle h, const pamc_params *p) {
     b += slots * S * (n * 4 + (n + 1) * 4 + 4 + n * 4 + n * 4);
     if (h->ell_w > 0) b += slots * S * (((n + 31) / 32) * 32 * (size_t)h->ell_w * 4 + n * 8);
     b += (size_t)(p->kind == 0 ? 2 * h->H + 1 : (4 * h->H + 1) * (4 * h->H + 1) + 4 * h->H + 1) * 8;
-    if (p->stagnation && p->kind == 0) b += 6 * (size_t)std::min(p->n_top > 0 ? p->n_top : std::max(1, p->R / 16), p->R) * n;
+    if (p->stagnation && p->kind == 0) b += 5 * (size_t)std::min(p->n_top > 0 ? p->n_top : std::max(1, p->R / 16), p->R) * n;
     b += ((size_t)h->n + 1) * 4 + (size_t)std::max(h->nnz, 1) * 4;   // the instance itself
     return b + sizeof(DevCtl);
 }

@@ -346,8 +346,10 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
       int32_t kind, int32_t n_top, int32_t trials, uint32_t key0, uint32_t key1,
       const int8_t *__restrict__ src, const int64_t *__restrict__ E_src,
       const int32_t *__restrict__ parent, const int32_t *__restrict__ targets,
-      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, uint8_t *__restrict__ nstat,
-      DevCtl *__restrict__ ctl) {
+      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, DevCtl *__restrict__ ctl) {
+    // the per-site decision state of the MIS rounds lives in shared memory
+    // (n bytes): every round reads the states of all neighbours
+    extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_flag, s_red;
     __shared__ long long s_e[32];
     if (ctl->done || !ctl->ncm_active || kind != 0) return;
@@ -358,7 +360,7 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
     const int8_t *row = src + (size_t)parent[m] * n;
     int8_t *sp = ncm_buf + (size_t)q * n;
     uint32_t *key = nkey + (size_t)q * n;
-    uint8_t *stat = nstat + (size_t)q * n;
+    uint8_t *stat = sm;
     for (int32_t k = threadIdx.x; k < n; k += blockDim.x) sp[k] = row[k];
     __syncthreads();
     // iso-sites: h_k = 0, so flipping k alone leaves the energy unchanged
@@ -568,13 +570,16 @@ cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl,
 
 cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
                        const int8_t *src, const int64_t *E_src, const int32_t *parent,
-                       const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey, uint8_t *nstat,
-                       DevCtl *ctl, cudaStream_t st) {
+                       const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey, DevCtl *ctl,
+                       cudaStream_t st) {
     const int32_t ntop = p.n_top < p.R ? p.n_top : p.R;
     if (ntop <= 0 || p.kind != 0 || !p.stagnation) return cudaSuccess;
-    k_ncm<<<ntop, kNcmThreads, 0, st>>>(n, rp, adj, p.R, p.kind, p.n_top, p.mis_trials,
-                                        (uint32_t)p.seed, (uint32_t)(p.seed >> 32), src, E_src,
-                                        parent, targets, ncm_buf, nkey, nstat, ctl);
+    const size_t smem = ((size_t)n + 15) & ~(size_t)15;
+    cudaError_t err = allow_dynamic_smem(k_ncm, smem);
+    if (err != cudaSuccess) return err;
+    k_ncm<<<ntop, kNcmThreads, smem, st>>>(n, rp, adj, p.R, p.kind, p.n_top, p.mis_trials,
+                                           (uint32_t)p.seed, (uint32_t)(p.seed >> 32), src, E_src,
+                                           parent, targets, ncm_buf, nkey, ctl);
     return cudaGetLastError();
 }
 
