@@ -238,20 +238,42 @@ prep_body(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t t
     }
 
     if (ncm && kind == 0) {
-        // targets: the n_top slots with the lowest (energy, slot index)
+        // targets: the n_top slots with the lowest (energy, slot index), by a
+        // block-wide bitonic sort of (energy, slot) pairs over the next power
+        // of two (padding sorts last); the counts above are already stored,
+        // so the whole shared buffer is free for the keys
         const int32_t ntop = min(n_top, R);
-        for (int32_t m = threadIdx.x; m < R; m += blockDim.x)
-            reinterpret_cast<int64_t *>(C)[m] = E_src[parent[m]];
+        int32_t P2 = 1;
+        while (P2 < R) P2 <<= 1;
+        int64_t *Ek = reinterpret_cast<int64_t *>(C);
+        int32_t *Mi = reinterpret_cast<int32_t *>(sm + (size_t)P2 * 8);
         __syncthreads();
-        const int64_t *Ep = reinterpret_cast<const int64_t *>(C);
-        for (int32_t m = threadIdx.x; m < R; m += blockDim.x) {
-            const int64_t em = Ep[m];
-            int32_t rank = 0;
-            for (int32_t j = 0; j < R; ++j) {
-                const int64_t ej = Ep[j];
-                rank += (ej < em || (ej == em && j < m)) ? 1 : 0;
+        for (int32_t m = threadIdx.x; m < P2; m += blockDim.x) {
+            Ek[m] = m < R ? (int64_t)E_src[parent[m]] : INT64_MAX;
+            Mi[m] = m < R ? m : INT32_MAX;
+        }
+        __syncthreads();
+        for (int32_t k = 2; k <= P2; k <<= 1) {
+            for (int32_t j = k >> 1; j > 0; j >>= 1) {
+                for (int32_t i = threadIdx.x; i < P2; i += blockDim.x) {
+                    const int32_t l = i ^ j;
+                    if (l > i) {
+                        const int64_t ei = Ek[i], el = Ek[l];
+                        const int32_t mi = Mi[i], ml = Mi[l];
+                        const bool gt = ei > el || (ei == el && mi > ml);
+                        if (gt == ((i & k) == 0)) {   // ascending where bit k of i is clear
+                            Ek[i] = el; Ek[l] = ei;
+                            Mi[i] = ml; Mi[l] = mi;
+                        }
+                    }
+                }
+                __syncthreads();
             }
-            if (rank < ntop) { targets[rank] = m; ncm_idx[m] = rank; }
+        }
+        for (int32_t q = threadIdx.x; q < ntop; q += blockDim.x) {
+            const int32_t m = Mi[q];
+            targets[q] = m;
+            ncm_idx[m] = q;
         }
     }
     __syncthreads();
@@ -550,7 +572,13 @@ cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint
     return cudaGetLastError();
 }
 
-size_t prep_smem_bytes(int32_t R) { return (size_t)R * 8 + (size_t)R * 4; }
+// R prefix sums (8 bytes) and R counts (4 bytes), sized for the next power of
+// two of R so that the NCM target sort can pad to it
+size_t prep_smem_bytes(int32_t R) {
+    size_t P2 = 1;
+    while (P2 < (size_t)(R > 1 ? R : 1)) P2 <<= 1;
+    return P2 * 8 + P2 * 4;
+}
 
 cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
                         int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, uint64_t *qbuf,
