@@ -363,14 +363,19 @@ __device__ int32_t mis_trial(int32_t n, const int32_t *rp, const uint32_t *adj, 
     return tot;
 }
 
+__host__ __device__ constexpr size_t ncm_stat_bytes(int32_t n) { return ((size_t)n + 15) & ~(size_t)15; }
+constexpr size_t kNcmKeySmemMax = 160 * 1024;   // keys join the states in shared memory up to this total
+
 __global__ void __launch_bounds__(kNcmThreads)
 k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj, int32_t R,
       int32_t kind, int32_t n_top, int32_t trials, uint32_t key0, uint32_t key1,
       const int8_t *__restrict__ src, const int64_t *__restrict__ E_src,
       const int32_t *__restrict__ parent, const int32_t *__restrict__ targets,
-      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, DevCtl *__restrict__ ctl) {
+      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, int32_t key_smem,
+      DevCtl *__restrict__ ctl) {
     // the per-site decision state of the MIS rounds lives in shared memory
-    // (n bytes): every round reads the states of all neighbours
+    // (n bytes), and the trial's order keys too (4n bytes) when key_smem:
+    // every round reads the state and key of every neighbour
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_flag, s_red;
     __shared__ long long s_e[32];
@@ -381,7 +386,7 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
     const int32_t m = targets[q];
     const int8_t *row = src + (size_t)parent[m] * n;
     int8_t *sp = ncm_buf + (size_t)q * n;
-    uint32_t *key = nkey + (size_t)q * n;
+    uint32_t *key = key_smem ? reinterpret_cast<uint32_t *>(sm + ncm_stat_bytes(n)) : nkey + (size_t)q * n;
     uint8_t *stat = sm;
     for (int32_t k = threadIdx.x; k < n; k += blockDim.x) sp[k] = row[k];
     __syncthreads();
@@ -602,12 +607,14 @@ cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const 
                        cudaStream_t st) {
     const int32_t ntop = p.n_top < p.R ? p.n_top : p.R;
     if (ntop <= 0 || p.kind != 0 || !p.stagnation) return cudaSuccess;
-    const size_t smem = ((size_t)n + 15) & ~(size_t)15;
+    const size_t with_keys = ncm_stat_bytes(n) + (size_t)n * 4;
+    const int key_smem = with_keys <= kNcmKeySmemMax ? 1 : 0;
+    const size_t smem = key_smem ? with_keys : ncm_stat_bytes(n);
     cudaError_t err = allow_dynamic_smem(k_ncm, smem);
     if (err != cudaSuccess) return err;
     k_ncm<<<ntop, kNcmThreads, smem, st>>>(n, rp, adj, p.R, p.kind, p.n_top, p.mis_trials,
                                            (uint32_t)p.seed, (uint32_t)(p.seed >> 32), src, E_src,
-                                           parent, targets, ncm_buf, nkey, ctl);
+                                           parent, targets, ncm_buf, nkey, key_smem, ctl);
     return cudaGetLastError();
 }
 
