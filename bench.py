@@ -764,10 +764,11 @@ def run_tts(args):
     s.init(**TTS_PARAMS)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    s.step(TTS_PARAMS["steps"])
-    b.record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        a.record(stream)
+        s.step(TTS_PARAMS["steps"])
+        b.record(stream)
+        torch.cuda.synchronize()
     ms_step = a.elapsed_time(b) / TTS_PARAMS["steps"]
     s.close()
     reach = []
@@ -800,7 +801,7 @@ def run_tts(args):
         "target_cut": target, "best_steps": best[1] if best else None, "P_s": best[2] if best else 0.0,
         "T_com_s": best[3] if best else None,
         "reached": sum(1 for r in reach if r is not None), "runs_wall_s": wall,
-        "gpu_launches": launches,
+        "gpu_launches": launches, "clocks": clk.summary(),
     }
     print(json.dumps(line))
 
