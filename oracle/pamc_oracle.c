@@ -272,8 +272,9 @@ static void orc_refresh_replica(orc_state *st, int32_t r) {
 }
 
 /* Random initial population (Algorithm 1, Initialization), keyed by step t.
- * Reading: a restart that resets the system draws a fresh population with
- * the key of the step at which it happens. */
+ * Reading: a restart that resets the system draws a fresh population keyed
+ * by the index of the step that starts from it (t + 1 for a restart decided
+ * at the end of step t). */
 static void orc_init_population(orc_state *st, int32_t t) {
     int32_t n = st->n, R = st->p.R;
     for (int32_t r = 0; r < R; ++r) {
