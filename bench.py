@@ -61,8 +61,9 @@ PROFILED_TRAFFIC = {
     "sweep_torus": (63.82e6, {"paper_2606_25203_gb300/csrc/sweep_ising.cu":
                               "e17e3bcc4115ff182f430c678f68cca954727ae6"}),
     # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.688 GB) scaled by n^2 to n=100,000
+    # (captured at 6a66522d; the source since differs by one comment line)
     "dense_sweep_100k": (1.688e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
-                                                           "6a66522d06fdb69ae910862d82054a0150aecbe8"}),
+                                                           "6f3fe9f84c0c5abf5a9ed8b7440af1d08f591712"}),
 }
 
 

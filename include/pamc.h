@@ -12,8 +12,8 @@
  *     three-state Potts update of Eq. 6-7 with the cascaded sampler of
  *     Suppl. S3;
  *   - the best cut M* (cut = (W - E)/2), the stagnation-driven adaptive
- *     temperature control and restart of Algorithm 1 / Sec. II.C, and the
- *     energy-preserving non-local cluster moves (NCM) of Sec. II.C.
+ *     temperature control and restart of Algorithm 1 / Sec. III.C, and the
+ *     energy-preserving non-local cluster moves (NCM) of Sec. III.C.
  * Every result is bit-identical to the plain CPU restatement of the same
  * steps for the same seed: random numbers come from counter-keyed
  * Philox4x32-10, thresholds and resampling weights from a deterministic
@@ -63,7 +63,7 @@ typedef struct {
     int32_t kind;           /* 0 Max-Cut (Ising), 1 Max-K-Cut (K-state Potts) */
     int32_t rule;           /* Ising: 0 heat-bath (Eq. 4), 1 Metropolis;
                                Potts: 0 cascaded sampler (Suppl. S3, K = 3),
-                               2 softmax noisy argmax (Sec. III.E, 2 <= K <= 8) */
+                               2 softmax noisy argmax (Sec. III.F, 2 <= K <= 8) */
     int32_t R;              /* population size */
     int32_t sweeps;         /* S, sweeps per temperature step */
     int32_t steps;          /* iterations; dbeta = (beta1-beta0)/(steps-1) */
@@ -184,7 +184,7 @@ pamc_status pamc_fields(pamc_handle h, int32_t *H);
  * of R * ceil(n/32) words.  Ising (kind 0) runs, sparse or dense;
  * PAMC_ERR_ARG for Potts. */
 pamc_status pamc_hamming(pamc_handle h, int64_t *hist, int64_t *sum);
-/* Lineage of the current population (Sec. III, genealogy of the resampled
+/* Lineage of the current population (Sec. III.D, genealogy of the resampled
  * population): family[r] (caller array of R int32) = the slot of the initial
  * population, or of the last re-initialised one after a restart, that slot r
  * descends from through the resampling parent maps (NCM keeps the family).

@@ -113,7 +113,7 @@ uint64_t orc_thr_potts_b2(double beta, int64_t c) {
 }
 
 /* ------------------------------------------------------------------ */
-/* Randomised sweep order (Sec. II.A, last sentence before Sec. II.B). */
+/* Randomised sweep order (Sec. III.A, last sentence before Sec. III.B). */
 /* ------------------------------------------------------------------ */
 /* Reading: the paper asks only for a random order.  One order per
  * (step, sweep), shared by every replica: the indices sorted by a 32-bit
@@ -440,7 +440,7 @@ int32_t orc_softmax_pick(int32_t K, const int32_t *syn, double beta, double gamm
     return best;
 }
 
-/* Potts with K labels and the softmax noisy-argmax update (Sec. III.E):
+/* Potts with K labels and the softmax noisy-argmax update (Sec. III.F):
  * the draws of replica r at vertex k are words c mod 4 of Philox counters
  * (k, sweep, t, FLIP<<24 | (r * ceil(K/4) + c/4)), c = 0..K-1. */
 static void orc_sweep_potts_softmax(orc_state *st, int32_t r, const int32_t *perm, int32_t sweep) {
@@ -471,7 +471,7 @@ static void orc_sweep_potts_softmax(orc_state *st, int32_t r, const int32_t *per
 }
 
 /* ------------------------------------------------------------------ */
-/* Non-local cluster move (Sec. II.C, NCM bullet)                      */
+/* Non-local cluster move (Sec. III.C, NCM bullet)                      */
 /* ------------------------------------------------------------------ */
 /* Readings: the paper fixes neither the number of greedy MIS trials nor the
  * number of low-energy replicas that take the move; both are parameters.
@@ -546,7 +546,7 @@ static int32_t orc_distinct_last(const int64_t *hist, int32_t len, int32_t w) {
 
 /* ------------------------------------------------------------------ */
 /* Adaptive temperature control and restart (Algorithm 1, after the    */
-/* sweeps; the stagnation rule of Sec. II.C, second bullet).           */
+/* sweeps; the stagnation rule of Sec. III.C, second bullet).           */
 /* ------------------------------------------------------------------ */
 /* Readings: where the branches of Algorithm 1 and the text disagree the text
  * is taken -- progress keeps cooling; a stagnant short window alone reverses

@@ -59,7 +59,7 @@ uint64_t orc_thr_potts_b2(double beta, int64_t c);
 
 /* Random permutation of 0..n-1 shared by all replicas for (t, sweep):
  * vertices sorted by the 32-bit key Philox((k, sweep, t, PERM<<24))[0],
- * equal keys by vertex index (Sec. II.A: spins updated once per sweep in a
+ * equal keys by vertex index (Sec. III.A: spins updated once per sweep in a
  * randomised order). */
 void orc_permutation(int32_t n, uint64_t seed, int32_t t, int32_t sweep, int32_t *perm);
 
@@ -90,7 +90,7 @@ typedef struct {
     double gamma;            /* softmax noisy argmax: noise amplitude */
 } orc_params;
 
-/* Softmax noisy-argmax label choice (Sec. III.E, first Potts update):
+/* Softmax noisy-argmax label choice (Sec. III.F, first Potts update):
  * P_k = exp(beta syn_k) / sum_m exp(beta syn_m), new label =
  * argmax_k (P_k - gamma U_k), U_k = u[k] / 2^32.  Decided in binary32 with
  * round-to-nearest operations in this order: d_k = max_m syn_m - syn_k,
@@ -111,7 +111,7 @@ typedef struct {
 } orc_ctl;
 
 /* Everything Algorithm 1 does after the sweeps and the M* update: record M*,
- * apply the adaptive temperature rule (Sec. II.C) when cooldown = 0 and the
+ * apply the adaptive temperature rule (Sec. III.C) when cooldown = 0 and the
  * history is full, then restart (returns 1) or advance z and beta (returns 0). */
 int orc_control(orc_ctl *c, const orc_params *p, double dbeta, int64_t mstar);
 
@@ -145,7 +145,7 @@ int64_t orc_energy_ising(int32_t n, const int32_t *row_ptr, const int32_t *col, 
 int64_t orc_energy_potts(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *J,
                          const int8_t *sigma);
 
-/* Non-local cluster move (Sec. II.C, first bullet) on one replica: spins s,
+/* Non-local cluster move (Sec. III.C, first bullet) on one replica: spins s,
  * fields h (Ising).  Applies mis_trials randomised greedy MIS constructions
  * over the iso-sites and flips the largest.  Returns the number flipped. */
 int32_t orc_ncm_replica(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *J,

@@ -1,6 +1,6 @@
 // dense.cu -- the fully connected instance: J is an N x N int8 matrix in HBM
 // (symmetric, +-1 off the diagonal, 0 on it).  Per temperature step:
-//   k_dense_perm       the shared random order of each sweep (Sec. II.A):
+//   k_dense_perm       the shared random order of each sweep (Sec. III.A):
 //                      vertices sorted by (Philox key, index) -- bucket by the
 //                      top key bits, then sort each bucket;
 //   k_dense_tables     heat-bath T(h) (Eq. 4) or Metropolis T_M(2x) over the

@@ -6,10 +6,10 @@
 //   k_prep     Boltzmann reweighting and resampling (Eq. 1-2) as systematic
 //              resampling over an integer prefix scan of 64-bit fixed-point
 //              weights, and selection of the NCM targets;
-//   k_ncm      the energy-preserving non-local cluster move (Sec. II.C):
+//   k_ncm      the energy-preserving non-local cluster move (Sec. III.C):
 //              randomised greedy maximal independent sets of iso-sites;
 //   k_control  M* / best configuration, the recent-progress history, the
-//              adaptive temperature rule (Sec. II.C) and the restart.
+//              adaptive temperature rule (Sec. III.C) and the restart.
 // All state lives on the device so that an iteration never waits for the host.
 #include "pamc_device.cuh"
 #include "pamc_internal.h"

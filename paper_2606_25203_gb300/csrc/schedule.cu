@@ -1,4 +1,4 @@
-// schedule.cu -- the shared random sweep order of Sec. II.A ("all spins were
+// schedule.cu -- the shared random sweep order of Sec. III.A ("all spins were
 // sequentially updated once in a randomized order"), turned into dependency
 // levels for a parallel sweep with exactly sequential semantics.
 //

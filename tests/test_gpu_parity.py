@@ -81,7 +81,7 @@ def test_potts_signed(pg):
 
 @pytest.mark.parametrize("K,gamma", [(3, 1.0), (2, 0.5), (4, 0.0), (5, 2.5), (8, 1.0)])
 def test_potts_softmax_noisy_argmax(pg, K, gamma):
-    # Sec. III.E softmax update, K labels, ragged R
+    # Sec. III.F softmax update, K labels, ragged R
     inst = W.gnm(260, 1300, signed=K % 2 == 0, seed=K)
     compare_run(pg, inst, 9, kind=1, rule=2, K=K, gamma=gamma, R=22, sweeps=2, beta0=0.1, beta1=3.0,
                 seed=3 + K)

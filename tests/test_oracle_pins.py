@@ -541,3 +541,34 @@ def test_softmax_potts_run_invariants(K):
     assert m == (run.weight_sum() - oracle.energy_potts(rp, col, J.astype(np.int32),
                                                         best.astype(np.int8))) // 2
     run.close()
+
+
+def test_dense_sk_anneal_reaches_parisi_neighbourhood():
+    """A loose physics pin for the fully connected +-1 instance (Sec. III.G):
+    annealed ground-state energies of the Sherrington-Kirkpatrick model
+    approach E / N^{3/2} = -0.7633 (Parisi) as N grows.  Four N=256 instances
+    annealed by conventional PAMC land near it, and a run held hot does not
+    (so a broken sampler or resampler fails the band)."""
+    n = 256
+    dens = []
+    for sd in range(4):
+        inst = W.dense_csr(n, seed=sd)
+        run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=64, sweeps=2, steps=300, beta0=0.01,
+                               beta1=1.0, seed=0)
+        run.step(300)
+        m, best = run.best()
+        e = run.weight_sum() - 2 * m
+        J = -inst.w.astype(np.int64)
+        s = best.astype(np.int64)
+        assert e == -sum(J[q] * s[k] * s[inst.col[q]] for k in range(n)
+                         for q in range(inst.row_ptr[k], inst.row_ptr[k + 1]) if inst.col[q] > k)
+        dens.append(e / n ** 1.5)
+        run.close()
+    assert -0.80 <= float(np.mean(dens)) <= -0.72
+    inst = W.dense_csr(n, seed=0)
+    hot = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=64, sweeps=2, steps=300, beta0=0.001,
+                           beta1=0.002, seed=0)
+    hot.step(300)
+    m, _ = hot.best()
+    assert (hot.weight_sum() - 2 * m) / n ** 1.5 > -0.5
+    hot.close()

@@ -4,8 +4,8 @@ This module is shared by the tests, the benchmark, the CPU oracle and the CUDA
 path.  It holds none of the method's arithmetic: it only builds Max-Cut
 instances (symmetric CSR with integer weights, or a dense symmetric int8
 coupling matrix) and parameter sets.  The recipes stand in for the G-set graphs
-and the fully connected 100k-spin instance the paper uses (Sec. III.D-F), which
-are not available here:
+(Sec. II, Sec. III.E-F) and the fully connected 100k-spin instance (Sec. III.G)
+the paper uses, which are not available here:
 
 * ``erdos_renyi``  -- each pair i<j is an edge with probability p (G1-G10 are
   n=800, p=0.06 random graphs with unit weights).
