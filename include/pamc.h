@@ -63,7 +63,7 @@ typedef struct {
     int32_t kind;           /* 0 Max-Cut (Ising), 1 Max-K-Cut (K-state Potts) */
     int32_t rule;           /* Ising: 0 heat-bath (Eq. 4), 1 Metropolis;
                                Potts: 0 cascaded sampler (Suppl. S3, K = 3),
-                               2 softmax noisy argmax (Sec. III.F, 2 <= K <= 8) */
+                               2 softmax noisy argmax (Sec. III.F, Eq. 8-9, 2 <= K <= 8) */
     int32_t R;              /* population size */
     int32_t sweeps;         /* S, sweeps per temperature step */
     int32_t steps;          /* iterations; dbeta = (beta1-beta0)/(steps-1) */

@@ -440,7 +440,7 @@ int32_t orc_softmax_pick(int32_t K, const int32_t *syn, double beta, double gamm
     return best;
 }
 
-/* Potts with K labels and the softmax noisy-argmax update (Sec. III.F):
+/* Potts with K labels and the softmax noisy-argmax update (Sec. III.F, Eq. 8-9):
  * the draws of replica r at vertex k are words c mod 4 of Philox counters
  * (k, sweep, t, FLIP<<24 | (r * ceil(K/4) + c/4)), c = 0..K-1. */
 static void orc_sweep_potts_softmax(orc_state *st, int32_t r, const int32_t *perm, int32_t sweep) {

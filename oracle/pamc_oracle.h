@@ -90,7 +90,7 @@ typedef struct {
     double gamma;            /* softmax noisy argmax: noise amplitude */
 } orc_params;
 
-/* Softmax noisy-argmax label choice (Sec. III.F, first Potts update):
+/* Softmax noisy-argmax label choice (Sec. III.F, Eq. 8-9, first Potts update):
  * P_k = exp(beta syn_k) / sum_m exp(beta syn_m), new label =
  * argmax_k (P_k - gamma U_k), U_k = u[k] / 2^32.  Decided in binary32 with
  * round-to-nearest operations in this order: d_k = max_m syn_m - syn_k,

@@ -3,7 +3,7 @@
 // temperature step (Algorithm 1, "Run S MCMC updates on every replica at
 // beta") to the kernel of the model: sweep_ising.cu (Ising, Eq. 3-4),
 // sweep_potts.cu (three-state Potts, cascaded sampler of Suppl. S3) and
-// sweep_softmax.cu (K-state Potts, softmax noisy argmax of Sec. III.F).
+// sweep_softmax.cu (K-state Potts, softmax noisy argmax of Sec. III.F, Eq. 8-9).
 //
 // Initial values: replica r's value at vertex i comes from word r mod 4 of
 // Philox(i, 0, t, INIT<<24 | r/4): s = +1 iff the top bit is set (Ising), or

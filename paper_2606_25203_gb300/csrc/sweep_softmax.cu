@@ -1,5 +1,5 @@
 // sweep_softmax.cu -- S sweeps of the K-state Potts population (Max-K-Cut)
-// with the softmax noisy-argmax update of Sec. III.F:
+// with the softmax noisy-argmax update of Sec. III.F (Eq. 8-9):
 //   P_c = exp(beta syn_c) / sum_m exp(beta syn_m),  syn_c(k) = sum_j J_kj [sigma_j = c],
 //   sigma_k <- argmax_c (P_c - gamma U_c),           U_c uniform on [0, 1).
 // The choice is made in binary32 with round-to-nearest operations in a fixed
