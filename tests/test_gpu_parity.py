@@ -114,6 +114,18 @@ def test_augmented_pamc_with_ncm_and_restart(pg):
     assert st["ncm_flipped"] > 0 and st["cycle"] == 1
 
 
+@pytest.mark.parametrize("R,n_top", [(24, 7), (40, 11)])
+def test_augmented_ncm_ragged_population(pg, R, n_top):
+    """Cluster moves on populations that are not a power of two, with more
+    targets than the default: the (energy, slot) sort that picks the targets
+    pads to the next power of two, and the targets' moves, the energies and
+    the controller stay bit for bit the oracle's."""
+    inst = W.torus(16, 16, signed=True, seed=2)
+    ref, _ = compare_run(pg, inst, 150, R=R, sweeps=2, beta0=0.5, beta1=6.0, stagnation=1,
+                         z_rst=120, cooldown_tau=5, n_top=n_top, seed=3)
+    assert ref.ctl()["ncm_flipped"] > 0
+
+
 def test_augmented_potts_controller(pg):
     inst = W.gnm(200, 1000, signed=False, seed=8)
     compare_run(pg, inst, 90, kind=1, R=16, sweeps=1, beta0=0.5, beta1=5.0, stagnation=1,
