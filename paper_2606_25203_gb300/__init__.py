@@ -198,9 +198,15 @@ def make_params(**kw) -> Params:
 # ---------------------------------------------------------------- C-ABI mirror
 def pamc_create_csr(n, row_ptr, col, w, device: int = 0, stream=None):
     L = load()
-    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
-    cl = np.ascontiguousarray(col, dtype=np.int32)
-    ww = np.ascontiguousarray(w, dtype=np.int32)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32).reshape(-1)
+    cl = np.ascontiguousarray(col, dtype=np.int32).reshape(-1)
+    ww = np.ascontiguousarray(w, dtype=np.int32).reshape(-1)
+    # the library reads n + 1 row pointers and row_ptr[n] entries of col and w
+    if int(n) < 0 or rp.shape[0] != int(n) + 1:
+        raise ValueError(f"row_ptr must hold n + 1 = {int(n) + 1} entries, got {rp.shape[0]}")
+    nnz = int(rp[-1])
+    if cl.shape[0] != nnz or ww.shape[0] != nnz:
+        raise ValueError(f"col and w must hold row_ptr[n] = {nnz} entries, got {cl.shape[0]} and {ww.shape[0]}")
     h = ctypes.c_void_p()
     _check(L.pamc_create_csr(int(n), _ptr(rp), _ptr(cl), _ptr(ww), int(device),
                              _stream_ptr(device, stream), ctypes.byref(h)))
@@ -211,11 +217,16 @@ def pamc_create_dense(n, w, device: int = 0, stream=None):
     """w: host numpy int8 (n, n) or a CUDA tensor (pointer passed as device memory)."""
     L = load()
     h = ctypes.c_void_p()
+    if tuple(w.shape) != (int(n), int(n)):
+        raise ValueError(f"w must be n x n = ({int(n)}, {int(n)}), got {tuple(w.shape)}")
     if isinstance(w, np.ndarray):
         arr = np.ascontiguousarray(w, dtype=np.int8)
         _check(L.pamc_create_dense(int(n), _ptr(arr), 0, int(device), _stream_ptr(device, stream),
                                    ctypes.byref(h)))
     else:
+        import torch
+        if w.dtype != torch.int8 or not w.is_cuda or not w.is_contiguous():
+            raise ValueError("a device w must be a contiguous CUDA int8 tensor")
         _check(L.pamc_create_dense(int(n), ctypes.c_void_p(int(w.data_ptr())), 1, int(device),
                                    _stream_ptr(device, stream), ctypes.byref(h)))
     return h

@@ -97,3 +97,15 @@ def test_params_layout_matches_header(tmp_path):
     assert out[0] == ctypes.sizeof(pg.Params)
     for f, off in zip(fields, out[1:]):
         assert getattr(pg.Params, f).offset == off, f
+
+
+def test_binding_checks_array_lengths():
+    """The binding refuses arrays shorter than what the library would read
+    (n + 1 row pointers, row_ptr[n] couplings, an n x n matrix) before any
+    pointer reaches it."""
+    with pytest.raises(ValueError, match="n \\+ 1"):
+        pg.pamc_create_csr(3, [0, 1, 2], [1, 0], [1, 1])
+    with pytest.raises(ValueError, match="row_ptr\\[n\\]"):
+        pg.pamc_create_csr(2, [0, 1, 2], [1], [1, 1])
+    with pytest.raises(ValueError, match="n x n"):
+        pg.pamc_create_dense(3, np.zeros((3, 2), dtype=np.int8))
