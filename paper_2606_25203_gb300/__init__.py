@@ -177,6 +177,22 @@ def _check(rc: int, h=None):
         raise PamcError(rc, buf.value.decode(errors="replace"))
 
 
+# handle address -> [n, R]: the sizes the library reads from or writes into
+# caller buffers, so that a mismatched n or R is refused before a pointer is
+# passed (handles made outside this module are not checked)
+_dims = {}
+
+
+def _dims_check(h, n=None, R=None):
+    d = _dims.get(getattr(h, "value", None))
+    if d is None:
+        return
+    if n is not None and int(n) != d[0]:
+        raise ValueError(f"n = {int(n)} does not match the instance's n = {d[0]}")
+    if R is not None and d[1] is not None and int(R) != d[1]:
+        raise ValueError(f"R = {int(R)} does not match the population's R = {d[1]}")
+
+
 def _ptr(a: np.ndarray):
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.c_void_p)
@@ -210,6 +226,7 @@ def pamc_create_csr(n, row_ptr, col, w, device: int = 0, stream=None):
     h = ctypes.c_void_p()
     _check(L.pamc_create_csr(int(n), _ptr(rp), _ptr(cl), _ptr(ww), int(device),
                              _stream_ptr(device, stream), ctypes.byref(h)))
+    _dims[h.value] = [int(n), None]
     return h
 
 
@@ -229,12 +246,20 @@ def pamc_create_dense(n, w, device: int = 0, stream=None):
             raise ValueError("a device w must be a contiguous CUDA int8 tensor")
         _check(L.pamc_create_dense(int(n), ctypes.c_void_p(int(w.data_ptr())), 1, int(device),
                                    _stream_ptr(device, stream), ctypes.byref(h)))
+    _dims[h.value] = [int(n), None]
     return h
+
+
+def _set_R(h, R):
+    d = _dims.get(getattr(h, "value", None))
+    if d is not None:
+        d[1] = int(R)
 
 
 def pamc_init(h, **params):
     p = make_params(**params)
     _check(_lib.pamc_init(h, ctypes.byref(p)), h)
+    _set_R(h, p.R)
     return p
 
 
@@ -249,10 +274,12 @@ def pamc_sync(h):
 def pamc_run(h, **params):
     p = make_params(**params)
     _check(_lib.pamc_run(h, ctypes.byref(p)), h)
+    _set_R(h, p.R)
     return p
 
 
 def pamc_best(h, n: int):
+    _dims_check(h, n=n)
     cut = np.zeros(1, dtype=np.int64)
     spins = np.zeros(n, dtype=np.int8)
     _check(_lib.pamc_best(h, _ptr(cut), _ptr(spins)), h)
@@ -260,6 +287,7 @@ def pamc_best(h, n: int):
 
 
 def pamc_state(h, R: int, n: int):
+    _dims_check(h, n=n, R=R)
     spins = np.zeros((R, n), dtype=np.int8)
     E = np.zeros(R, dtype=np.int64)
     par = np.zeros(R, dtype=np.int32)
@@ -311,6 +339,7 @@ def pamc_last_error(h=None) -> str:
 
 def pamc_destroy(h):
     if h is not None and h.value:
+        _dims.pop(h.value, None)
         _lib.pamc_destroy(h)
 
 
@@ -340,10 +369,14 @@ def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed,
 
 def pamc_set_population(h, spins):
     arr = np.ascontiguousarray(spins, dtype=np.int8)
+    d = _dims.get(getattr(h, "value", None))
+    if d is not None and d[1] is not None and arr.size != d[0] * d[1]:
+        raise ValueError(f"spins must hold R x n = {d[1]} x {d[0]} values, got {arr.size}")
     _check(_lib.pamc_set_population(h, _ptr(arr)), h)
 
 
 def pamc_fields(h, R: int, n: int):
+    _dims_check(h, n=n, R=R)
     H = np.zeros((R, n), dtype=np.int32)
     _check(_lib.pamc_fields(h, _ptr(H)), h)
     return H
@@ -351,6 +384,7 @@ def pamc_fields(h, R: int, n: int):
 
 def pamc_hamming(h, n: int):
     """(hist, sum): hist[k] = pairs of replicas at corrected distance k = min(d, n - d)."""
+    _dims_check(h, n=n)
     hist = np.zeros(n // 2 + 1, dtype=np.int64)
     total = np.zeros(1, dtype=np.int64)
     _check(_lib.pamc_hamming(h, _ptr(hist), _ptr(total)), h)
@@ -359,6 +393,7 @@ def pamc_hamming(h, n: int):
 
 def pamc_lineage(h, R: int):
     """(family, n_families): family[r] = the initial slot that slot r descends from."""
+    _dims_check(h, R=R)
     fam = np.zeros(R, dtype=np.int32)
     k = np.zeros(1, dtype=np.int32)
     _check(_lib.pamc_lineage(h, _ptr(fam), _ptr(k)), h)

@@ -109,3 +109,26 @@ def test_binding_checks_array_lengths():
         pg.pamc_create_csr(2, [0, 1, 2], [1], [1, 1])
     with pytest.raises(ValueError, match="n x n"):
         pg.pamc_create_dense(3, np.zeros((3, 2), dtype=np.int8))
+
+
+def test_binding_checks_sizes_against_the_handle():
+    """Buffers sized from a caller's n or R that differ from the handle's are
+    refused before the library writes into them (a registered stand-in
+    handle; only the refusals run, so no device call is made)."""
+    h = ctypes.c_void_p(0x1234)
+    pg._dims[h.value] = [10, 4]
+    try:
+        with pytest.raises(ValueError, match="n = 11"):
+            pg.pamc_best(h, 11)
+        with pytest.raises(ValueError, match="R = 5"):
+            pg.pamc_state(h, 5, 10)
+        with pytest.raises(ValueError, match="n = 9"):
+            pg.pamc_fields(h, 4, 9)
+        with pytest.raises(ValueError, match="n = 12"):
+            pg.pamc_hamming(h, 12)
+        with pytest.raises(ValueError, match="R = 3"):
+            pg.pamc_lineage(h, 3)
+        with pytest.raises(ValueError, match="R x n"):
+            pg.pamc_set_population(h, np.ones((4, 9), dtype=np.int8))
+    finally:
+        pg._dims.pop(h.value, None)
