@@ -116,8 +116,12 @@ def test_binding_checks_sizes_against_the_handle():
     refused before the library writes into them (a registered stand-in
     handle; only the refusals run, so no device call is made)."""
     h = ctypes.c_void_p(0x1234)
-    pg._dims[h.value] = [10, 4]
+    pg._dims[h.value] = [10, None]
     try:
+        pg._dims_check(h, n=10, R=7)          # R unknown before init: only n is checked
+        pg._set_R(h, 4)                        # what pamc_init / pamc_run record
+        assert pg._dims[h.value] == [10, 4]
+        pg._dims_check(h, n=10, R=4)
         with pytest.raises(ValueError, match="n = 11"):
             pg.pamc_best(h, 11)
         with pytest.raises(ValueError, match="R = 5"):
