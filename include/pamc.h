@@ -213,9 +213,9 @@ void pamc_destroy(pamc_handle h);
 typedef struct pamc_batch_s *pamc_batch;
 
 /* Device bytes of a sparse handle running with p: the instance (CSR) plus
- * what pamc_init allocates (two spin buffers, energies, parents, counts, the
- * schedule ring of 16 steps, the threshold table, NCM buffers, the
- * controller).  For admission by HBM footprint; 0 for a null argument or a
+ * what pamc_init allocates (two spin buffers, energies, resampling weights,
+ * parents, counts, the schedule ring of 16 steps, the threshold table, NCM
+ * buffers, the controller).  For admission by HBM footprint; 0 for a null argument or a
  * dense handle. */
 size_t pamc_footprint(pamc_handle h, const pamc_params *p);
 /* stream: a cudaStream_t, or NULL for a new non-blocking stream. */
