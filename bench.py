@@ -201,29 +201,31 @@ def run_reference(args):
     # bounded sample: the same instances and schedule, R_s replicas, one step each
     Rs = 32
     params = dict(PARAMS, R=Rs)
-    total_attempts = 0
-    t_all = 0.0
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
-    per_step = []
-    for k in range(args.steps):
+
+    def sample_step():
         att = 0
-        t0 = time.perf_counter()
         for inst in insts:
             run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **params)
             run.step(1)
             att += Rs * inst.n * SWEEPS
             run.close()
-        dt = time.perf_counter() - t0
-        per_step.append(dt)
-        total_attempts += att
-        t_all += dt
+        return att
+
+    for _ in range(args.warmup):     # untimed warm-up steps of the same sample
+        sample_step()
+    total_attempts = 0
+    t_all = 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        total_attempts += sample_step()
+        t_all += time.perf_counter() - t0
     value = total_attempts / t_all
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"R={Rs} per instance"},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "R": R, "sweeps_per_step": SWEEPS,
+                                        "sample": f"R={Rs} per instance, the first iteration of a run"},
         "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": 1, "kind": "oracle",
                          "sample": f"first iteration of both instances with R={Rs} (same seeds)"},
         "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

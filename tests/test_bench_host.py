@@ -53,3 +53,24 @@ def test_clock_summary_without_samples():
     c = bench.ClockSampler(0)
     c.t0, c.t1 = 1.0, 2.0
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_reference_arm_line(tmp_path):
+    """The reference arm (the oracle on the host) prints one JSON line with the
+    contract's keys, on the default workload's name, after its warm-up."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600,
+                         cwd=str(tmp_path))
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "attempts/s"
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == bench.WORKLOAD
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "attempts/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
