@@ -10,9 +10,9 @@ built with ``-ffp-contract=off``); this module only compiles it and marshals
 numpy arrays through ctypes.  See ``pamc_oracle.h`` for the paper passage each
 function follows.
 
-Parity unpinned: the controller trajectory of Algorithm 1 under stagnation, the
-NCM defaults, restart re-initialisation and the Potts beta factor of Eq. 8 are
-defined only by the documented reading.
+Every function is pinned (``tests/test_oracle_pins*.py``); the NCM defaults,
+the reading that a restart re-draws the population and the Potts beta factor
+of Eq. 8 are readings of the paper, stated beside the functions that take them.
 """
 from __future__ import annotations
 
@@ -74,7 +74,10 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
+            # PAMC_ORACLE_LIB: a test-built variant of this library (the
+            # mutation tests build copies of the oracle with a planted mistake
+            # and check that the pins reject them)
+            path = os.environ.get("PAMC_ORACLE_LIB") or build()
             L = ctypes.CDLL(path)
             P = ctypes.c_void_p
             i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double

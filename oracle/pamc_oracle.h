@@ -12,10 +12,15 @@
  * algorithm cited beside it) with plain loops; where the paper is silent or
  * ambiguous the reading taken is stated beside the function.
  *
- * Parity unpinned (defined only by the reading, no independent pin exists):
- * the exact controller trajectory of Algorithm 1 under stagnation, the NCM
- * defaults (number of MIS trials, n top replicas), restart re-initialisation,
- * and the Potts beta factor of Eq. 8.
+ * Every function is pinned by a test against something fixed outside the
+ * oracle (known answers, libm, closed forms, exhaustive enumeration, exact
+ * Boltzmann distributions, invariants, hand-built populations), including
+ * the initial population and its restart re-draw (uniform, independent,
+ * re-keyed) and the choice of cluster-move targets (lowest energy, ties to
+ * the lower slot).  What no pin can fix are the readings where the paper is
+ * silent, stated beside each function: the NCM defaults (MIS trials, n top
+ * replicas, cooldown), that a restart re-draws the population, and the beta
+ * factor of Eq. 8.
  */
 #ifndef PAMC_ORACLE_H
 #define PAMC_ORACLE_H
