@@ -271,21 +271,26 @@ void pamc_batch_destroy(pamc_batch b);
  * Max-Cut weights (row_ptr[n+1], col[nnz], w[nnz]; symmetric, no diagonal,
  * |w| <= 127), H >= max_i sum_j |w_ij| (<= 127), spins_in and spins_out
  * (R*n int8, +1/-1, replica-major; may be the same buffer) and E_out (R
- * energies H(s) = -sum_{i<j} J_ij s_i s_j of the result).  err (optional)
- * receives a one-line message.
+ * energies H(s) = -sum_{i<j} J_ij s_i s_j of the result).  In-place use
+ * (spins_in == spins_out) is supported because the sweep reads each replica
+ * group's rows completely into shared memory, in the CTA that later writes
+ * them, before any write.  err (optional) receives a one-line message.
  * Limits: n <= PAMC_NOALLOC_MAX_N, nnz <= PAMC_NOALLOC_MAX_NNZ,
  * sweeps <= PAMC_NOALLOC_MAX_SWEEPS, R <= PAMC_NOALLOC_MAX_R; larger sizes
  * return PAMC_ERR_RANGE before any device work.  An invalid instance returns
  * PAMC_ERR_ARG / ASYM / DIAG / RANGE after a validation kernel, before any
- * kernel indexes through it.
+ * kernel indexes through it; symmetry is checked as a multiset (a neighbour
+ * listed twice in one row must be listed twice in the other).
  * Scratch: one static device array of PAMC_NOALLOC_SCRATCH_BYTES per GPU,
  * held from library load until process exit, shared by every call on that
  * GPU and keeping the last call's contents (the call resets what must start
  * fresh).  Calls whose device work overlaps on one GPU (different streams or
  * threads) race on it: serialise them.  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  The call is
- * synchronous: it waits for its stream before returning. */
+ * current and keeps it for the process; make that first call before any
+ * stream capture.  A cudaDeviceReset while the library is loaded is not
+ * supported (the kept address would be stale).  Each call waits for its
+ * stream twice: after validating the instance and before returning. */
 pamc_status pamc_sweeps_noalloc(int32_t n, int32_t nnz, const int32_t *row_ptr, const int32_t *col,
                                 const int32_t *w, int32_t H, int32_t rule, int32_t R,
                                 int32_t sweeps, double beta, uint64_t seed, int32_t t,

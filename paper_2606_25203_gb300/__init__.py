@@ -346,25 +346,54 @@ def pamc_destroy(h):
 def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed, t, spins_in,
                         spins_out, E_out, stream=None):
     """S sweeps at a fixed beta on a caller-owned device population without any
-    allocation by the library.  Every array argument is a CUDA tensor (or a raw
-    device address as int); see include/pamc.h for the contract."""
+    allocation by the library.  Every array argument is a CUDA tensor or a raw
+    device address (int); see include/pamc.h for the contract.  Tensors are
+    checked before any pointer is passed: one CUDA device for all of them,
+    contiguous, int32 CSR arrays of n + 1 and nnz entries, int8 spins of at
+    least R * n and int64 energies of at least R; the call runs with that
+    device current."""
     L = load()
+    want = {"row_ptr": (row_ptr, "int32", int(n) + 1), "col": (col, "int32", int(nnz)),
+            "w": (w, "int32", int(nnz)), "spins_in": (spins_in, "int8", int(R) * int(n)),
+            "spins_out": (spins_out, "int8", int(R) * int(n)), "E_out": (E_out, "int64", int(R))}
+    dev = None
+    for name, (x, dt, count) in want.items():
+        if x is None or isinstance(x, int):
+            continue
+        if not getattr(x, "is_cuda", False):
+            raise ValueError(f"{name} must be a CUDA tensor or a device address")
+        if str(x.dtype) != "torch." + dt:
+            raise ValueError(f"{name} must be {dt}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if x.numel() < count:
+            raise ValueError(f"{name} holds {x.numel()} elements, the call reads or writes {count}")
+        d = x.device.index or 0
+        if dev is not None and d != dev:
+            raise ValueError(f"{name} is on cuda:{d}, other arguments on cuda:{dev}")
+        dev = d
 
     def addr(x):
         if x is None:
             return None
         return ctypes.c_void_p(int(x) if isinstance(x, int) else int(x.data_ptr()))
 
-    dev = 0
-    if hasattr(spins_in, "device"):
-        dev = spins_in.device.index or 0
-    buf = ctypes.create_string_buffer(256)
-    rc = L.pamc_sweeps_noalloc(int(n), int(nnz), addr(row_ptr), addr(col), addr(w), int(H),
-                               int(rule), int(R), int(sweeps), float(beta), int(seed), int(t),
-                               addr(spins_in), addr(spins_out), addr(E_out),
-                               _stream_ptr(dev, stream), buf, 256)
-    if rc != 0:
-        raise PamcError(rc, buf.value.decode(errors="replace"))
+    def call():
+        d = dev if dev is not None else 0
+        buf = ctypes.create_string_buffer(256)
+        rc = L.pamc_sweeps_noalloc(int(n), int(nnz), addr(row_ptr), addr(col), addr(w), int(H),
+                                   int(rule), int(R), int(sweeps), float(beta), int(seed), int(t),
+                                   addr(spins_in), addr(spins_out), addr(E_out),
+                                   _stream_ptr(d, stream), buf, 256)
+        if rc != 0:
+            raise PamcError(rc, buf.value.decode(errors="replace"))
+
+    if dev is None:
+        call()
+        return
+    import torch
+    with torch.cuda.device(dev):
+        call()
 
 
 def pamc_set_population(h, spins):

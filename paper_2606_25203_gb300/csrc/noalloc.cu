@@ -76,8 +76,11 @@ __global__ void k_noalloc_reset(DevCtl *ctl, double beta, int32_t *parent, int32
 }
 
 // Validate the caller's device CSR and pack it as (col | (-w) << 24).
-// Each entry needs a reverse entry of equal weight; |w| <= 127; no self loop;
-// every row's sum |w| <= H.  Errors set ctl->err (first error wins).
+// Symmetry as a multiset: (j, w) occurs in row i exactly as often as (i, w)
+// in row j (the schedule counts a vertex's earlier neighbours over its own
+// row and counts them down over theirs, so an unmatched duplicate would leave
+// a vertex unscheduled); |w| <= 127; no self loop; every row's sum |w| <= H.
+// Errors set ctl->err (first error wins).
 __global__ void k_noalloc_pack(int32_t n, int32_t nnz, const int32_t *__restrict__ rp,
                                const int32_t *__restrict__ col, const int32_t *__restrict__ w,
                                int32_t H, uint32_t *__restrict__ adj, DevCtl *ctl) {
@@ -95,10 +98,11 @@ __global__ void k_noalloc_pack(int32_t n, int32_t nnz, const int32_t *__restrict
             if (we < -127 || we > 127) { atomicCAS(&ctl->err, 0, (int)PAMC_ERR_RANGE); break; }
             habs += we < 0 ? -we : we;
             const int32_t jb = rp[j], je = rp[j + 1];
-            bool rev = false;
+            int32_t fwd = 0, bwd = 0;
+            for (int32_t f = b; f < e1; ++f) fwd += (col[f] == j && w[f] == we) ? 1 : 0;
             if (jb >= 0 && je <= nnz && jb <= je)
-                for (int32_t f = jb; f < je && !rev; ++f) rev = col[f] == i && w[f] == we;
-            if (!rev) { atomicCAS(&ctl->err, 0, (int)PAMC_ERR_ASYM); break; }
+                for (int32_t f = jb; f < je; ++f) bwd += (col[f] == i && w[f] == we) ? 1 : 0;
+            if (fwd != bwd) { atomicCAS(&ctl->err, 0, (int)PAMC_ERR_ASYM); break; }
             adj[e] = (uint32_t)j | ((uint32_t)(uint8_t)(int8_t)(-we) << 24);
         }
         if (habs > H) atomicCAS(&ctl->err, 0, (int)PAMC_ERR_RANGE);
@@ -209,6 +213,9 @@ extern "C" pamc_status pamc_sweeps_noalloc(int32_t n, int32_t nnz, const int32_t
         launch_schedule(n, row_ptr, adj, seed, t, 1, sweeps, 0, 1, order, lvl, nlev, skey, scnt, s);
     e = launch_tables(0, rule, H, ctl, tab, s);
     SweepCfg cfg{1, n >= 16384 ? 8 : n >= 4096 ? 4 : n >= 1024 ? 2 : 1};
+    // spins_in may equal spins_out: the sweep's CTA for a replica group reads
+    // the group's rows completely into shared memory before its first write,
+    // and no other CTA touches those rows
     if (e == cudaSuccess)
         e = launch_sweep(0, rule, n, row_ptr, adj, H, p, t, 0, SchedView{order, lvl, nlev, nullptr, nullptr, 0}, tab,
                          spins_in, parent, nullptr, ncm_idx, spins_out, E_out, ctl, cfg, 0, s);
