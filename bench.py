@@ -7,8 +7,15 @@ with R=4,096 replicas, 10 sweeps per temperature step, beta 0.1 -> 4.0 over
 500 steps, adaptive reheating + NCM on, restart every 400 steps.  One timed
 "step" is one iteration of Algorithm 1 (resample, NCM, 10 sweeps, energies,
 M*, control) on BOTH instances.  attempts per step = R * N * S summed over the
-two instances.  The timed steps are steps 0..K-1 of a fresh run after W
-warm-up steps on a throwaway one; by default K = 500, the whole schedule.
+two instances.  With K = 500 (the default) the timed steps are the whole
+schedule of a fresh run.  With fewer, a pre-pass over the schedule (which is
+also the warm-up; the controller's trajectory is fixed by the seed) finds the
+iterations that apply cluster moves or reheat, and the K timed steps of a
+fresh run are the window past step 40 (the stagnation windows are full from
+there) that holds the most of them; the steps before the window run untimed.
+The line also carries a "dense100k" object: the whole 200-step anneal of the
+fully connected N=100,000 instance, device-timed, with its HBM roofline and
+an end-to-end figure from host buffers.
 
 Timing: device time with CUDA events on the library's stream, one event pair
 per step; between timed steps a 512 MB buffer is written to flush L2 (the
@@ -292,14 +299,22 @@ def run_ours(args):
         solvers.append(s)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
     clk = ClockSampler(local).start()
-    for _ in range(args.warmup):
-        for s in solvers:
-            s.step(1)
-    # the timed steps are steps 0..K-1 of a fresh run: the work of a step
-    # depends on where it is in the schedule (control, NCM, restart)
+    run_params = dict(PARAMS, seed=rank_seed(PARAMS["seed"], rank))
+    # the work of a step depends on where it is in the schedule (control,
+    # cluster moves, restart): place the timed window
+    if args.steps >= STEPS_SCHEDULE:
+        for _ in range(args.warmup):
+            for s in solvers:
+                s.step(1)
+        start, events = 0, None
+    else:
+        events = schedule_events(solvers)          # also the warm-up
+        start = choose_window(events, args.steps)
     for s in solvers:
-        s.init(**dict(PARAMS, seed=rank_seed(PARAMS["seed"], rank)))
+        s.init(**run_params)
+        s.step(start)                              # untimed steps before the window
     torch.cuda.synchronize()
+    ctl0 = [s.control() for s in solvers]
     launches0 = sum(s.launches() for s in solvers)
     if dist:
         dist.barrier()
@@ -320,6 +335,8 @@ def run_ours(args):
     ms = sum(a.elapsed_time(b) for a, b in ev)
     for s in solvers:
         s.sync()
+    ctl1 = [s.control() for s in solvers]
+    window = window_summary(events, start, args.steps, ctl0, ctl1)
     ms, att = reduce_over_ranks(dist, ms, attempts_per_step(insts) * args.steps)
     value = att / (ms / 1e3)
 
@@ -340,7 +357,14 @@ def run_ours(args):
     ops_per_attempt = alu_ops_per_attempt(insts[0])
     achieved = sw_att * ops_per_attempt / (sw_ms / 1e3) / 1e12
     peak_tops = 152 * 128 * sm_max * 1e6 / 1e12
-    e2e = e2e_measure(pg, torch, insts, args, local)
+    e2e = e2e_measure(pg, torch, insts, args, local, start)
+    dense = None
+    if world == 1 and not args.no_dense:
+        for s in solvers:
+            s.close()
+        solvers = []
+        torch.cuda.empty_cache()
+        dense = dense_measure(pg, torch, DENSE_N, DENSE_PARAMS["steps"], args.warmup, e2e=True)
     result = None
     if rank == 0:
         cpu = cpu_baseline_sample() if world == 1 else None
@@ -350,8 +374,10 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "R": R, "sweeps_per_step": SWEEPS,
                        "attempts_per_step": attempts_per_step(insts), "l2": "flushed between steps (512 MB write)",
-                       "timed_steps": f"steps 0..{args.steps - 1} of a fresh run ({STEPS_SCHEDULE}-step schedule, "
-                                      f"restart every {PARAMS['z_rst']})",
+                       "timed_steps": f"steps {start}..{start + args.steps - 1} of a fresh run "
+                                      f"({STEPS_SCHEDULE}-step schedule, restart every {PARAMS['z_rst']}"
+                                      + (f"; steps 0..{start - 1} untimed" if start else "") + ")",
+                       "timed_window": window,
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
                          "frac": achieved / peak_tops, "traffic": profiled_traffic("sweep_torus"),
@@ -362,6 +388,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "dense100k": dense,
         }
         print(json.dumps(result))
     for s in solvers:
@@ -369,6 +396,56 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return result
+
+
+def schedule_events(solvers):
+    """One pass over the whole schedule of each run, reading the controller
+    after every iteration: the iterations that applied cluster moves, that
+    reheated (strong stagnation: the cluster move armed), and that restarted.
+    The trajectory is a function of the seed, so a fresh run with the same
+    seed meets the same events at the same steps."""
+    ev = []
+    for s in solvers:
+        ncm, reheat, restart = [], [], []
+        prev = s.control()
+        for t in range(STEPS_SCHEDULE):
+            s.step(1)
+            c = s.control()
+            if c["ncm_last"]:
+                ncm.append(t)
+            if c["enable_cm"] and not prev["enable_cm"]:
+                reheat.append(t)
+            if c["cycle"] > prev["cycle"]:
+                restart.append(t)
+            prev = c
+        ev.append({"ncm": ncm, "reheat": reheat, "restart": restart})
+    return ev
+
+
+def choose_window(events, K, lo=40):
+    """First step of the K-step window at or after lo (the stagnation windows
+    hold 40 values from there) that contains the most cluster-move and reheat
+    iterations of all runs; ties to the earliest."""
+    hi = max(lo, STEPS_SCHEDULE - K)
+    marks = sorted(t for e in events for t in e["ncm"] + e["reheat"])
+    best, best_n = lo, -1
+    for a in range(lo, hi + 1):
+        n = sum(1 for t in marks if a <= t < a + K)
+        if n > best_n:
+            best, best_n = a, n
+    return best
+
+
+def window_summary(events, start, K, ctl0, ctl1):
+    """What the timed window contains: from the pre-pass, the iterations of
+    each run that applied cluster moves, reheated or restarted; from the
+    timed run itself, the spins the cluster moves flipped in the window."""
+    out = {"first": start, "last": start + K - 1,
+           "ncm_spins_flipped": [int(b["ncm_flipped"] - a["ncm_flipped"]) for a, b in zip(ctl0, ctl1)]}
+    if events is not None:
+        for key in ("ncm", "reheat", "restart"):
+            out[key + "_steps"] = [[t for t in e[key] if start <= t < start + K] for e in events]
+    return out
 
 
 def alu_ops_per_attempt(inst):
@@ -406,10 +483,12 @@ def sweep_kernel_time(pg, torch, inst, stream):
     return max(t_full - t_zero, 1e-6), R * inst.n * SWEEPS
 
 
-def e2e_measure(pg, torch, insts, args, device):
+def e2e_measure(pg, torch, insts, args, device, start=0):
     """End to end through the public API with host buffers: instance upload
-    (host CSR -> device), init, K iterations each followed by a read of the
-    best cut and configuration to the host."""
+    (host CSR -> device), init, the untimed steps before the window and the K
+    window iterations, each iteration followed by a read of the best cut and
+    configuration to the host; all of it inside the timed region, and the
+    attempts of every step run counted."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2d = 0
@@ -420,7 +499,8 @@ def e2e_measure(pg, torch, insts, args, device):
         h2d += inst.row_ptr.nbytes + inst.col.nbytes + inst.w.nbytes
         s.init(**PARAMS)
         solvers.append(s)
-    for _ in range(args.steps):
+    nsteps = start + args.steps
+    for _ in range(nsteps):
         for s in solvers:
             s.step(1)
             s.best()
@@ -429,9 +509,9 @@ def e2e_measure(pg, torch, insts, args, device):
     dt = time.perf_counter() - t0
     for s in solvers:
         s.close()
-    att = attempts_per_step(insts) * args.steps
-    return {"value": att / dt, "unit": "attempts/s", "h2d_bytes_per_step": h2d / args.steps,
-            "d2h_bytes_per_step": d2h / args.steps}
+    att = attempts_per_step(insts) * nsteps
+    return {"value": att / dt, "unit": "attempts/s", "h2d_bytes_per_step": h2d / nsteps,
+            "d2h_bytes_per_step": d2h / nsteps, "steps": nsteps}
 
 
 # ---------------------------------------------------------------- dense 100k
@@ -449,16 +529,21 @@ def dense_weights_device(torch, n, seed=0, chunk=2000):
     return w
 
 
-def run_dense(args):
-    import torch
-    import paper_2606_25203_gb300 as pg
-    pg.load()
-    n = args.dense_n
+def dense_measure(pg, torch, n, steps, warmup, e2e=False):
+    """Configuration 4: steps 0..steps-1 of a fresh anneal of the dense
+    instance, device-timed step by step (the instance, 10 GB at n = 100,000,
+    is larger than L2), the kernel split (a step without sweeps), the HBM
+    roofline of the sweep (one read of J per sweep) and of the recompute (one
+    read of J per step), and the rows the flips needed.  With e2e, the same
+    steps again through the public API from a host copy of the weights:
+    upload, validation, init, every step followed by a read of the best cut
+    and configuration, all inside the wall-clock region."""
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     w = dense_weights_device(torch, n)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
+    w_host = w.cpu().numpy() if e2e else None
     h = pg.pamc_create_dense(n, w, stream=stream.cuda_stream)
     del w
     torch.cuda.empty_cache()
@@ -466,16 +551,16 @@ def run_dense(args):
     # warm-up steps on a throwaway run, then the timed steps 0..K-1 of a fresh
     # run (the cost of a step depends on where it is in the beta schedule)
     pg.pamc_init(h, **P)
-    pg.pamc_step(h, args.warmup)
+    pg.pamc_step(h, warmup)
     pg.pamc_sync(h)
     pg.pamc_init(h, **P)
     torch.cuda.synchronize()
     l0 = pg.pamc_launch_count(h)
     rows0, pos0 = pg.pamc_dense_rows(h)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
+          for _ in range(steps)]
     with ClockSampler(0) as clk:
-        for k in range(args.steps):
+        for k in range(steps):
             ev[k][0].record(stream)
             pg.pamc_step(h, 1)
             ev[k][1].record(stream)
@@ -485,7 +570,7 @@ def run_dense(args):
     per_step = [a.elapsed_time(b) for a, b in ev]
     ms = sum(per_step)
     launches = pg.pamc_launch_count(h) - l0
-    att = P["R"] * n * P["sweeps"] * args.steps
+    att = P["R"] * n * P["sweeps"] * steps
     m, _ = pg.pamc_best(h, n)
     e_best = pg.pamc_weight_sum(h) - 2 * m     # E = W - 2 cut
     # kernel split: a step without sweeps (order, resampling, tables, the
@@ -499,18 +584,34 @@ def run_dense(args):
     b.record(stream)
     torch.cuda.synchronize()
     ms_nosweep = a.elapsed_time(b) / 3
-    ms_sweep = ms / args.steps - ms_nosweep
+    ms_sweep = ms / steps - ms_nosweep
+    pg.pamc_destroy(h)
     peaks, src = load_peaks()
     hbm = peaks["hbm_gbs"]
     rc_gbs = n * n / (ms_nosweep / 1e3) / 1e9            # J bytes of the recompute
     sw_gbs = P["sweeps"] * n * n / (ms_sweep / 1e3) / 1e9  # one read of J per sweep
-    line = {
+    e2e_obj = None
+    if e2e:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h = pg.pamc_create_dense(n, w_host, stream=stream.cuda_stream)
+        pg.pamc_init(h, **P)
+        for _ in range(steps):
+            pg.pamc_step(h, 1)
+            pg.pamc_best(h, n)
+        dt = time.perf_counter() - t1
+        pg.pamc_destroy(h)
+        e2e_obj = {"value": att / dt, "unit": "attempts/s", "h2d_bytes_per_step": n * n / steps,
+                   "d2h_bytes_per_step": 8 + n, "steps": steps,
+                   "includes": "upload of the n x n weights from pageable host memory, validation, init"}
+    del w_host
+    return {
         "metric": METRIC, "value": att / (ms / 1e3), "unit": "attempts/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": {"workload": DENSE_WORKLOAD, "n": n, **P,
                                         "l2": "inputs (10 GB) larger than L2"},
-        "kernels_ms": {"step": ms / args.steps, "sweeps": ms_sweep, "recompute_and_rest": ms_nosweep},
+        "kernels_ms": {"step": ms / steps, "sweeps": ms_sweep, "recompute_and_rest": ms_nosweep},
         "roofline": {"bound": "hbm", "achieved": sw_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": sw_gbs / hbm,
                      "traffic": (profiled_traffic("dense_sweep_100k") * (n / 100000) ** 2
@@ -523,15 +624,21 @@ def run_dense(args):
         # replica; their rows are all a sweep's field updates read of J
         "rows_needed": {"rows": rows1 - rows0, "positions": pos1 - pos0,
                         "fraction": (rows1 - rows0) / max(pos1 - pos0, 1),
-                        "achieved_gbs": (rows1 - rows0) * n / (ms_sweep * args.steps / 1e3) / 1e9},
+                        "achieved_gbs": (rows1 - rows0) * n / (ms_sweep * steps / 1e3) / 1e9},
+        "e2e": e2e_obj,
         "clocks": clk.summary(), "gpu_launches": launches,
-        "timed_steps": f"steps 0..{args.steps - 1} of a fresh run (beta {P['beta0']} -> {P['beta1']} over {P['steps']})",
+        "timed_steps": f"steps 0..{steps - 1} of a fresh run (beta {P['beta0']} -> {P['beta1']} over {P['steps']})",
         "ms_step_first_last": [per_step[0], per_step[-1]],
         "best_cut": m, "best_energy_density": e_best / n ** 1.5,
         "instance_generation_s": gen_s,
     }
-    print(json.dumps(line))
-    pg.pamc_destroy(h)
+
+
+def run_dense(args):
+    import torch
+    import paper_2606_25203_gb300 as pg
+    pg.load()
+    print(json.dumps(dense_measure(pg, torch, args.dense_n, args.steps, args.warmup, e2e=args.dense_e2e)))
 
 
 SERVE_PARAMS = dict(R=512, sweeps=10, steps=200, beta0=0.1, beta1=3.0, seed=0)
@@ -873,6 +980,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-max-active", type=int, default=64)
     ap.add_argument("--dense-n", type=int, default=DENSE_N)
+    ap.add_argument("--dense-e2e", action="store_true", help="dense100k: add the end-to-end figure")
+    ap.add_argument("--no-dense", action="store_true",
+                    help="sparse workload: leave out the dense100k object (profiling)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = STEPS_SCHEDULE if (args.workload == "sparse" and args.impl == "ours") else 20

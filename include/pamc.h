@@ -139,6 +139,14 @@ pamc_status pamc_state(pamc_handle h, int8_t *spins, int64_t *E, int32_t *parent
  * far, largest |dE| across an NCM; dv[2] = beta, Delta.  Synchronises. */
 pamc_status pamc_control_state(pamc_handle h, int64_t *iv, double *dv);
 
+/* The rest of Algorithm 1's state, so that a run can be continued or
+ * checked elsewhere from step t: hist (caller array of 64 int64, may be
+ * NULL) receives the recent-progress history of M* that the stagnation
+ * windows read, oldest first, and *hist_len its length; *mstar (may be
+ * NULL) the best cut so far, INT64_MIN before the first iteration.
+ * Synchronises. */
+pamc_status pamc_control_history(pamc_handle h, int64_t *hist, int32_t *hist_len, int64_t *mstar);
+
 /* Number of this library's kernels launched on the handle so far. */
 int64_t pamc_launch_count(pamc_handle h);
 

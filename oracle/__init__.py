@@ -108,6 +108,10 @@ def lib():
             L.orc_control.restype = ctypes.c_int
             L.orc_softmax_pick.argtypes = [i32, P, dbl, dbl, P]
             L.orc_softmax_pick.restype = i32
+            L.orc_set_state.argtypes = [P, i32, ctypes.POINTER(_Ctl), i64, P, P]
+            L.orc_set_sweep_replay.argtypes = [P, P, P]
+            L.orc_get_ncm_targets.argtypes = [P, P, P]
+            L.orc_get_history.argtypes = [P, P]
             _lib = L
     return _lib
 
@@ -334,3 +338,38 @@ class OracleRun:
     def set_spins(self, s: np.ndarray):
         s = np.ascontiguousarray(s, dtype=np.int8).reshape(self.R, self.n)
         lib().orc_set_spins(self._h, _ptr(s))
+
+    def set_state(self, t: int, ctl: dict, hist, mstar: int, best, spins):
+        """Load a state of Algorithm 1 reached elsewhere (see orc_set_state):
+        ctl holds z, cycle, cooldown, enable_cm, beta and delta; hist the M*
+        history, oldest first."""
+        hist = np.asarray(hist, dtype=np.int64).reshape(-1)
+        c = _Ctl(z=int(ctl["z"]), cycle=int(ctl["cycle"]), cooldown=int(ctl["cooldown"]),
+                 enable_cm=int(ctl["enable_cm"]), hist_len=int(hist.shape[0]), beta=float(ctl["beta"]),
+                 delta=float(ctl["delta"]))
+        for i, v in enumerate(hist.tolist()):
+            c.hist[i] = int(v)
+        sp = np.ascontiguousarray(spins, dtype=np.int8).reshape(self.R, self.n)
+        b = None if best is None else _ptr(np.ascontiguousarray(best, dtype=np.int8).reshape(self.n))
+        lib().orc_set_state(self._h, int(t), ctypes.byref(c), int(mstar), b, _ptr(sp))
+
+    def set_sweep_replay(self, mask=None, spins_after=None):
+        """Sweep only the replicas in mask; the others take spins_after (see
+        orc_set_sweep_replay).  No arguments: every replica is swept again."""
+        if mask is None:
+            lib().orc_set_sweep_replay(self._h, None, None)
+            return
+        m = np.ascontiguousarray(np.asarray(mask, dtype=bool).astype(np.uint8).reshape(self.R))
+        sa = np.ascontiguousarray(spins_after, dtype=np.int8).reshape(self.R, self.n)
+        lib().orc_set_sweep_replay(self._h, _ptr(m), _ptr(sa))
+
+    def history(self) -> np.ndarray:
+        out = np.zeros(64, dtype=np.int64)
+        lib().orc_get_history(self._h, _ptr(out))
+        return out[:self.ctl()["hist_len"]]
+
+    def ncm_targets(self) -> np.ndarray:
+        out = np.zeros(self.R, dtype=np.int32)
+        k = np.zeros(1, dtype=np.int32)
+        lib().orc_get_ncm_targets(self._h, _ptr(out), _ptr(k))
+        return out[:int(k[0])]

@@ -214,6 +214,10 @@ struct orc_state {
     int8_t *best;
     int64_t hist[ORC_HIST_MAX];
     int32_t hist_len;
+    int32_t *ncm_targets;      /* slots of the last iteration's cluster move */
+    int32_t n_ncm_targets;
+    uint8_t *rmask;            /* sampled sweeps: sweep replica r iff rmask[r] */
+    int8_t *r_spins;           /* sampled sweeps: the other replicas' results */
 };
 
 static int32_t nf(const orc_state *st) { return st->p.kind == 1 ? st->p.K : 1; }
@@ -338,6 +342,10 @@ orc_state *orc_create(int32_t n, const int32_t *rp, const int32_t *col, const in
     st->parent = (int32_t *)malloc(sizeof(int32_t) * (size_t)R);
     st->count = (int32_t *)malloc(sizeof(int32_t) * (size_t)R);
     st->best = (int8_t *)calloc((size_t)n, 1);
+    st->ncm_targets = (int32_t *)malloc(sizeof(int32_t) * (size_t)R);
+    st->n_ncm_targets = 0;
+    st->rmask = NULL;
+    st->r_spins = NULL;
     st->dbeta = p->steps > 1 ? (p->beta1 - p->beta0) / (double)(p->steps - 1) : 0.0;
     st->t = 0; st->z = 1; st->cycle = 0; st->cooldown = 0; st->enable_cm = 0; st->done = 0;
     st->beta = p->beta0; st->delta = st->dbeta;
@@ -352,7 +360,7 @@ void orc_destroy(orc_state *st) {
     if (!st) return;
     free(st->rp); free(st->col); free(st->J); free(st->s); free(st->s_tmp); free(st->h);
     free(st->h_tmp); free(st->E); free(st->E_tmp); free(st->parent); free(st->count);
-    free(st->best); free(st);
+    free(st->best); free(st->ncm_targets); free(st->rmask); free(st->r_spins); free(st);
 }
 
 /* ------------------------------------------------------------------ */
@@ -606,6 +614,7 @@ static void orc_iteration(orc_state *st) {
      * half the energy for Potts. */
     double escale = st->p.kind == 1 ? 0.5 : 1.0;
     st->ncm_last = 0;
+    st->n_ncm_targets = 0;
     for (int32_t r = 0; r < R; ++r) { st->parent[r] = r; st->count[r] = 1; }
     if (st->z > 1) {
         if (st->p.resample) {
@@ -630,6 +639,7 @@ static void orc_iteration(orc_state *st) {
                 qsort(idx, (size_t)R, sizeof(int32_t), orc_cmp_energy_idx);
                 for (int32_t q = 0; q < ntop; ++q) {
                     int32_t r = idx[q];
+                    st->ncm_targets[st->n_ncm_targets++] = r;
                     int64_t before = st->E[r];
                     st->ncm_flipped += orc_ncm_replica(n, st->rp, st->col, st->J,
                                                        st->s + (size_t)r * n, st->h + (size_t)r * n,
@@ -652,12 +662,20 @@ static void orc_iteration(orc_state *st) {
     for (int32_t sw = 0; sw < st->p.sweeps; ++sw) {
         orc_permutation(n, st->p.seed, st->t, sw, perm);
         for (int32_t r = 0; r < R; ++r) {
+            if (st->rmask && !st->rmask[r]) continue;
             if (st->p.kind == 0) orc_sweep_ising(st, r, perm, sw);
             else if (st->p.rule == 2) orc_sweep_potts_softmax(st, r, perm, sw);
             else orc_sweep_potts(st, r, perm, sw);
         }
     }
     free(perm);
+    /* sampled sweeps: the replicas outside the sample take the results given */
+    if (st->rmask)
+        for (int32_t r = 0; r < R; ++r)
+            if (!st->rmask[r]) {
+                memcpy(st->s + (size_t)r * n, st->r_spins + (size_t)r * n, (size_t)n);
+                orc_refresh_replica(st, r);
+            }
     /* M* <- max(M*, max Cut(P)); cut = (W - E)/2 */
     int32_t rbest = 0;
     for (int32_t r = 1; r < R; ++r)
@@ -727,4 +745,43 @@ int64_t orc_weight_sum(const orc_state *st) { return st->W; }
 void orc_set_spins(orc_state *st, const int8_t *spins) {
     memcpy(st->s, spins, (size_t)st->p.R * st->n);
     for (int32_t r = 0; r < st->p.R; ++r) orc_refresh_replica(st, r);
+}
+
+void orc_set_state(orc_state *st, int32_t t, const orc_ctl *ctl, int64_t mstar, const int8_t *best,
+                   const int8_t *spins) {
+    st->t = t;
+    st->z = ctl->z; st->cycle = ctl->cycle; st->cooldown = ctl->cooldown; st->enable_cm = ctl->enable_cm;
+    st->beta = ctl->beta; st->delta = ctl->delta;
+    st->hist_len = ctl->hist_len;
+    memcpy(st->hist, ctl->hist, sizeof(int64_t) * (size_t)ctl->hist_len);
+    st->mstar = mstar;
+    if (best) memcpy(st->best, best, (size_t)st->n);
+    st->done = 0;
+    st->ncm_last = 0;
+    st->ncm_flipped = 0;
+    st->ncm_dE_max = 0;
+    st->n_ncm_targets = 0;
+    orc_set_spins(st, spins);
+}
+
+void orc_set_sweep_replay(orc_state *st, const uint8_t *mask, const int8_t *spins_after) {
+    free(st->rmask);
+    free(st->r_spins);
+    st->rmask = NULL;
+    st->r_spins = NULL;
+    if (!mask) return;
+    size_t R = (size_t)st->p.R, sn = R * (size_t)st->n;
+    st->rmask = (uint8_t *)malloc(R);
+    st->r_spins = (int8_t *)malloc(sn);
+    memcpy(st->rmask, mask, R);
+    memcpy(st->r_spins, spins_after, sn);
+}
+
+void orc_get_ncm_targets(const orc_state *st, int32_t *targets, int32_t *count) {
+    memcpy(targets, st->ncm_targets, sizeof(int32_t) * (size_t)st->n_ncm_targets);
+    *count = st->n_ncm_targets;
+}
+
+void orc_get_history(const orc_state *st, int64_t *hist) {
+    memcpy(hist, st->hist, sizeof(int64_t) * (size_t)st->hist_len);
 }

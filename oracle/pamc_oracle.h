@@ -144,6 +144,32 @@ int64_t orc_weight_sum(const orc_state *st);
  * the definition; used by tests that start from a hand-built state. */
 void orc_set_spins(orc_state *st, const int8_t *spins);
 
+/* ---- Step replay from a state reached elsewhere (parity at full size) ----
+ * orc_set_state loads a whole state of Algorithm 1 -- step index t, the
+ * controller (z, cycle, cooldown, enable_cm, beta, Delta and the M* history
+ * in ctl), the best cut so far mstar (INT64_MIN for none) and its
+ * configuration best (n values, may be NULL), and the population spins
+ * (R*n) -- and recomputes fields and energies from the definition.  The
+ * NCM counters restart at zero.  The next iterations run from it as from a
+ * state the oracle reached itself. */
+void orc_set_state(orc_state *st, int32_t t, const orc_ctl *ctl, int64_t mstar, const int8_t *best,
+                   const int8_t *spins);
+/* Sampled sweeps: in the following iterations only the replicas with
+ * mask[r] != 0 are swept; every other replica takes its configuration after
+ * the sweeps from spins_after (R*n, results computed elsewhere), with its
+ * fields and energy recomputed from the definition.  Resampling, cluster
+ * moves, M*, the best configuration and the controller then run on the
+ * whole population exactly as in Algorithm 1, so an iteration of a large
+ * population can be checked with the sweeps of a sample only.  mask NULL
+ * switches the mode off. */
+void orc_set_sweep_replay(orc_state *st, const uint8_t *mask, const int8_t *spins_after);
+/* The M* history of the stagnation windows, oldest first (hist_len values
+ * of orc_get_ctl). */
+void orc_get_history(const orc_state *st, int64_t *hist);
+/* The slots that took the cluster move in the last iteration, in the order
+ * chosen (lowest (energy, slot) first); *count = 0 when none did. */
+void orc_get_ncm_targets(const orc_state *st, int32_t *targets, int32_t *count);
+
 /* Energy from the definition (i<j pairs), used by the pins. */
 int64_t orc_energy_ising(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *J,
                          const int8_t *s);

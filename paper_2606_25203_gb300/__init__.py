@@ -26,6 +26,7 @@ __all__ = [
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
     "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_batch_set_lanes", "pamc_batch_get_lanes", "pamc_hamming", "pamc_lineage", "pamc_set_population", "pamc_fields",
+    "pamc_control_history",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -60,6 +61,9 @@ DEFAULTS = dict(kind=0, rule=0, R=16, sweeps=1, steps=10, beta0=0.1, beta1=3.0, 
                 z_rst=0, cooldown_tau=10, n_top=0, mis_trials=4, win_short=25, win_long=40,
                 max_distinct_short=3, max_distinct_long=5, reheat_factor=0.8, target_cut=-1,
                 seed=0, restart_reinit=1, resample=1, K=3, gamma=1.0)
+
+# limits of pamc_sweeps_noalloc (PAMC_NOALLOC_MAX_* in include/pamc.h)
+NOALLOC_MAX_N, NOALLOC_MAX_NNZ, NOALLOC_MAX_SWEEPS, NOALLOC_MAX_R = 32768, 262144, 8, 16384
 
 _lib = None
 _alloc_cbs = None
@@ -122,6 +126,8 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
                                       ctypes.c_uint64, i32, P, P, P, P, ctypes.c_char_p,
                                       ctypes.c_size_t]
     L.pamc_dense_rows.argtypes = [P, P, P]
+    L.pamc_control_history.argtypes = [P, P, P, P]
+    L.pamc_control_history.restype = ctypes.c_int
     L.pamc_set_population.argtypes = [P, P]
     L.pamc_set_population.restype = ctypes.c_int
     L.pamc_fields.argtypes = [P, P]
@@ -309,6 +315,15 @@ def pamc_control_state(h) -> dict:
     return d
 
 
+def pamc_control_history(h):
+    """(history of M*, oldest first, as an int64 array; M* so far)."""
+    hist = np.zeros(64, dtype=np.int64)
+    ln = np.zeros(1, dtype=np.int32)
+    m = np.zeros(1, dtype=np.int64)
+    _check(_lib.pamc_control_history(h, _ptr(hist), _ptr(ln), _ptr(m)), h)
+    return hist[:int(ln[0])].copy(), int(m[0])
+
+
 def pamc_launch_count(h) -> int:
     return int(_lib.pamc_launch_count(h))
 
@@ -353,6 +368,10 @@ def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed,
     least R * n and int64 energies of at least R; the call runs with that
     device current."""
     L = load()
+    # sizes beyond the library's limits are refused by the library itself,
+    # before it reads any pointer; tensor sizes are checked only within them
+    in_limits = (1 <= int(n) <= NOALLOC_MAX_N and 0 <= int(nnz) <= NOALLOC_MAX_NNZ
+                 and 1 <= int(R) <= NOALLOC_MAX_R and 0 <= int(sweeps) <= NOALLOC_MAX_SWEEPS)
     want = {"row_ptr": (row_ptr, "int32", int(n) + 1), "col": (col, "int32", int(nnz)),
             "w": (w, "int32", int(nnz)), "spins_in": (spins_in, "int8", int(R) * int(n)),
             "spins_out": (spins_out, "int8", int(R) * int(n)), "E_out": (E_out, "int64", int(R))}
@@ -366,7 +385,7 @@ def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed,
             raise ValueError(f"{name} must be {dt}, got {x.dtype}")
         if not x.is_contiguous():
             raise ValueError(f"{name} must be contiguous")
-        if x.numel() < count:
+        if in_limits and x.numel() < count:
             raise ValueError(f"{name} holds {x.numel()} elements, the call reads or writes {count}")
         d = x.device.index or 0
         if dev is not None and d != dev:

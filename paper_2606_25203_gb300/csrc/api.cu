@@ -849,6 +849,19 @@ pamc_status pamc_control_state(pamc_handle h, int64_t *iv, double *dv) {
     return PAMC_OK;
 }
 
+pamc_status pamc_control_history(pamc_handle h, int64_t *hist, int32_t *hist_len, int64_t *mstar) {
+    if (!h || !hist_len) return fail(h, PAMC_ERR_ARG, "null argument");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_control_history before pamc_init");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    *hist_len = c.hist_len;
+    if (hist)
+        for (int32_t i = 0; i < c.hist_len && i < kHistMax; ++i) hist[i] = c.hist[i];
+    if (mstar) *mstar = c.mstar;
+    return PAMC_OK;
+}
+
 pamc_status pamc_hamming(pamc_handle h, int64_t *hist, int64_t *sum) {
     if (!h || !hist || !sum) return fail(h, PAMC_ERR_ARG, "null argument");
     if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_hamming before pamc_init");

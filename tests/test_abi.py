@@ -136,3 +136,11 @@ def test_binding_checks_sizes_against_the_handle():
             pg.pamc_set_population(h, np.ones((4, 9), dtype=np.int8))
     finally:
         pg._dims.pop(h.value, None)
+
+
+def test_binding_noalloc_limits_match_header():
+    src = open(os.path.join(ROOT, "include", "pamc.h")).read()
+    for name, val in (("N", pg.NOALLOC_MAX_N), ("NNZ", pg.NOALLOC_MAX_NNZ),
+                      ("SWEEPS", pg.NOALLOC_MAX_SWEEPS), ("R", pg.NOALLOC_MAX_R)):
+        m = re.search(rf"#define PAMC_NOALLOC_MAX_{name} (\d+)", src)
+        assert m and int(m.group(1)) == val, name

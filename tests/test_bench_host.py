@@ -74,3 +74,26 @@ def test_reference_arm_line(tmp_path):
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "attempts/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_timed_window_holds_the_most_control_events():
+    """The K-step window starts at or after step 40, ends within the
+    schedule, and holds as many cluster-move and reheat iterations of the
+    runs as any window can (earliest on ties)."""
+    ev = [{"ncm": [121, 160, 233], "reheat": [120, 159, 232], "restart": [399]},
+          {"ncm": [301], "reheat": [300], "restart": [399]}]
+    for K in (5, 20, 60):
+        a = bench.choose_window(ev, K)
+        assert 40 <= a <= bench.STEPS_SCHEDULE - K
+        marks = [t for e in ev for t in e["ncm"] + e["reheat"]]
+        got = sum(1 for t in marks if a <= t < a + K)
+        for b in range(40, bench.STEPS_SCHEDULE - K + 1):
+            assert sum(1 for t in marks if b <= t < b + K) <= got
+    assert bench.choose_window(ev, 20) == 102        # the earliest window holding steps 120 and 121
+    # no events at all: the window starts at step 40
+    assert bench.choose_window([{"ncm": [], "reheat": [], "restart": []}], 20) == 40
+    s = bench.window_summary(ev, 115, 20, [{"ncm_flipped": 5}, {"ncm_flipped": 0}],
+                             [{"ncm_flipped": 17}, {"ncm_flipped": 0}])
+    assert s["first"] == 115 and s["last"] == 134
+    assert s["ncm_steps"] == [[121], []] and s["reheat_steps"] == [[120], []]
+    assert s["ncm_spins_flipped"] == [12, 0]
