@@ -158,6 +158,15 @@ int64_t pamc_launch_count(pamc_handle h);
  * results.  PAMC_ERR_STATE before pamc_init or for dense runs. */
 pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_group, int *lanes_per_vertex);
 
+/* How the sparse Ising sweeps of an initialised run keep the local fields
+ * (Eq. 3): *mode = 0 pulled from the neighbours' spins at every visit over
+ * the CSR rows, 1 the same over position-indexed (ELL) rows, 2 kept in
+ * shared memory and updated on every flip (push; instances with
+ * max_i sum_j |w_ij| <= 63, ELL rows, one lane per vertex, at least one
+ * sweep).  Speed only, never results.  PAMC_ERR_STATE before pamc_init or
+ * for dense or Potts runs. */
+pamc_status pamc_sweep_mode(pamc_handle h, int *mode);
+
 /* W = sum_{i<j} w_ij of the instance (cut = (W - E)/2). */
 int64_t pamc_weight_sum(pamc_handle h);
 

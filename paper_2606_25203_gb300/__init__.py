@@ -26,7 +26,7 @@ __all__ = [
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
     "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_batch_set_lanes", "pamc_batch_get_lanes", "pamc_hamming", "pamc_lineage", "pamc_set_population", "pamc_fields",
-    "pamc_control_history",
+    "pamc_control_history", "pamc_sweep_mode",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -127,6 +127,8 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
                                       ctypes.c_size_t]
     L.pamc_dense_rows.argtypes = [P, P, P]
     L.pamc_control_history.argtypes = [P, P, P, P]
+    L.pamc_sweep_mode.argtypes = [P, P]
+    L.pamc_sweep_mode.restype = ctypes.c_int
     L.pamc_control_history.restype = ctypes.c_int
     L.pamc_set_population.argtypes = [P, P]
     L.pamc_set_population.restype = ctypes.c_int
@@ -340,6 +342,13 @@ def pamc_sweep_shape(h) -> tuple:
     v = np.zeros(3, dtype=np.int32)
     _check(_lib.pamc_sweep_shape(h, _ptr(v[0:1]), _ptr(v[1:2]), _ptr(v[2:3])), h)
     return int(v[0]), int(v[1]), int(v[2])
+
+
+def pamc_sweep_mode(h) -> int:
+    """0 pull over CSR rows, 1 pull over ELL rows, 2 push (fields kept and updated on flips)."""
+    v = ctypes.c_int(0)
+    _check(_lib.pamc_sweep_mode(h, ctypes.byref(v)), h)
+    return v.value
 
 
 def pamc_weight_sum(h) -> int:

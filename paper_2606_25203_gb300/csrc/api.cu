@@ -922,6 +922,15 @@ pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_
     return PAMC_OK;
 }
 
+pamc_status pamc_sweep_mode(pamc_handle h, int *mode) {
+    if (!h || !mode) return fail(h, PAMC_ERR_ARG, "null argument");
+    if (!h->initialized || h->dense || h->p.kind != 0)
+        return fail(h, PAMC_ERR_STATE, "no sparse Ising run initialised");
+    const bool ell = h->d_ell != nullptr;
+    *mode = sweep_push_ok(h->H, h->p.sweeps, ell, h->cfg.lanes_per_vertex) ? 2 : ell ? 1 : 0;
+    return PAMC_OK;
+}
+
 int64_t pamc_weight_sum(pamc_handle h) { return h ? h->W : 0; }
 
 pamc_status pamc_last_error(pamc_handle h, char *buf, size_t len) {
@@ -1069,10 +1078,11 @@ pamc_status rebuild(pamc_batch b) {
         d.W = h->ell_w; d.K = make_philox_keys(p.seed);
         d.sp[0] = h->d_spins[0]; d.sp[1] = h->d_spins[1]; d.en[0] = h->d_E[0]; d.en[1] = h->d_E[1];
         d.slots = kSchedSlots; d.t_end = t_end;
-        const int idx = (int)sw.size();
-        sw.push_back(d);
         const int cls = batch_class(h->n);
         const SweepCfg cfg = eff[cls];
+        d.push = sweep_push_ok(h->H, p.sweeps, h->d_ell != nullptr, cfg.lanes_per_vertex) ? 1 : 0;
+        const int idx = (int)sw.size();
+        sw.push_back(d);
         const int32_t ctas = ((p.R + 3) / 4 + cfg.groups_per_cta - 1) / cfg.groups_per_cta;
         // with sweeps = 0 the launch still copies the resampled population and its energies
         auto &items = swi[h->d_ell != nullptr][p.rule][cls];

@@ -69,6 +69,7 @@ struct SweepDesc {
     int8_t *sp[2];
     int64_t *en[2];
     int32_t slots, t_end;
+    int32_t push;   // push-model sweep (H <= 63, ELL, one lane per vertex, S >= 1)
 };
 
 struct SchedDesc {
@@ -154,6 +155,11 @@ void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t
                      int2 *pos = nullptr);
 
 size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
+// Push-model Ising sweeps (fields kept in shared memory, updated on flips):
+// used where H <= 63, on ELL schedules with one lane per vertex and S >= 1,
+// unless the environment variable PAMC_SWEEP_PUSH is "0".
+bool sweep_push_enabled();
+bool sweep_push_ok(int32_t H, int32_t S, bool ell, int lanes_per_vertex);
 void launch_schedule_batched(const SchedDesc *descs, const int2 *items, int32_t nitems, int32_t n_max,
                              cudaStream_t st);
 cudaError_t launch_population_batched(const PrepDesc *prep, const TabDesc *tabs, int32_t ninst,

@@ -16,6 +16,22 @@
 // Order.  Vertices of one level of the (t, sweep) schedule are pairwise
 // uncoupled; levels run in order with a named barrier per replica group, which
 // reproduces the sequential sweep exactly.
+//
+// Two ways of keeping the fields.  Pull (any H <= 127, any schedule, several
+// lanes per vertex): a visit sums its neighbours' spin words as above.  Push
+// (H <= 63, position-indexed ELL, one lane per vertex): byte q of a vertex's
+// word holds replica q's spin in bit 7 and its biased field
+// 64 + sum_j J_kj [s_j = +1] (in [1, 127]) in bits 0..6, computed once per
+// launch from the CSR.  A visit reads its own word only; a flip adds
+// (up - down) * J_jk to each neighbour's word -- the incrementally maintained
+// fields of Eq. 3.  The flips of a warp are gathered by ballot and their
+// neighbour updates spread over the warp's lanes, so a visit pays for the
+// updates only in proportion to the flips.  Two vertices of a level may share
+// a neighbour, so the updates are shared-memory atomics; 32-bit modular
+// addition is exact because every byte of every intermediate word is the
+// field byte of some configuration and stays in [1, 127].
+#include <cstdlib>
+
 #include "pamc_device.cuh"
 #include "pamc_internal.h"
 
@@ -67,6 +83,189 @@ __device__ __forceinline__ uint32_t ising_decide(uint32_t A, int32_t c0, const u
         }
     }
     return nw;
+}
+
+// The push model's decision: byte q of the vertex word F holds the spin of
+// replica q in bit 7 and the biased field 64 + sum_j J_kj [s_j = +1] in bits
+// 0..6; c0 = H - 128 - sum_j J_kj, so that 2 * field byte + c0 = h + H.
+template <int RULE>
+__device__ __forceinline__ uint32_t ising_decide_push(uint32_t F, int32_t c0, const u32x4 &u,
+                                                      const uint64_t *tab_s, int32_t H) {
+    const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+    uint32_t nw = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int32_t idx = 2 * (int32_t)((F >> (8 * q)) & 0x7Fu) + c0;   // h + H
+        if (RULE == 0) {
+            nw |= ((uint64_t)uw[q] < tab_s[idx] ? 1u : 0u) << (8 * q);
+        } else {
+            const uint32_t sq = (F >> (8 * q + 7)) & 1u;
+            const int32_t ix = sq ? idx : 2 * H - idx;             // s*h + H
+            nw |= (((uint64_t)uw[q] < tab_s[ix]) ? (sq ^ 1u) : sq) << (8 * q);
+        }
+    }
+    return nw;
+}
+
+// Push-model sweeps of one CTA's replica groups (H <= 63, position-indexed
+// ELL, one lane per vertex, S >= 1); same inputs, outputs and shared-memory
+// layout as the pull body below, and bit-identical results.
+template <int RULE, class KeyT>
+__device__ __forceinline__ void
+sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
+                      const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, const KeyT &draw,
+                      int32_t t, int32_t slot, const int32_t *__restrict__ slvl,
+                      const int32_t *__restrict__ snlev, const uint32_t *__restrict__ sell,
+                      const int2 *__restrict__ spos, int32_t W, const uint64_t *__restrict__ tab,
+                      const int8_t *__restrict__ src, const int32_t *__restrict__ parent,
+                      const int8_t *__restrict__ ncm_buf, const int32_t *__restrict__ ncm_idx,
+                      int8_t *__restrict__ dst, int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl,
+                      int gpc, int tpg, int32_t bid) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    if (ctl->done) return;
+    const int tabn = 2 * H + 1;
+    uint64_t *tab_s = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *spins_all = reinterpret_cast<uint32_t *>(smem + (((size_t)tabn * 8 + 15) & ~(size_t)15));
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(spins_all + (size_t)gpc * n_pad);
+    for (int i = threadIdx.x; i < tabn; i += blockDim.x) tab_s[i] = tab[i];
+    for (int i = threadIdx.x; i < gpc * 4; i += blockDim.x) red[i] = 0ull;
+
+    const int gl = threadIdx.x / tpg, li = threadIdx.x % tpg;
+    const int32_t g = bid * gpc + gl;
+    const int32_t r0 = g * 4;
+    const bool active = r0 < R;
+    uint32_t *sp = spins_all + (size_t)gl * n_pad;
+
+    if (active) {
+        // the replica copy of the population step (see the pull body), spins
+        // into bit 7 of each replica byte
+        const int8_t *rows[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int32_t r = r0 + q;
+            if (r < R) {
+                const int32_t m = ncm_idx[r];
+                rows[q] = m >= 0 ? ncm_buf + (size_t)m * n : src + (size_t)parent[r] * n;
+            } else {
+                rows[q] = nullptr;
+            }
+        }
+        for (int32_t k = li; k < n; k += tpg) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (rows[q] != nullptr) w |= (uint32_t)(rows[q][k] > 0) << (8 * q + 7);
+            sp[k] = w;
+        }
+    }
+    __syncthreads();
+
+    if (active) {
+        // the group's fields from the definition, once per launch, in chunks
+        // of one vertex per thread: every read of a chunk precedes its writes,
+        // and later chunks read only the spin bits, which the writes keep
+        for (int32_t k0 = 0; k0 < n; k0 += tpg) {
+            const int32_t k = k0 + li;
+            uint32_t A = 0x40404040u;
+            if (k < n)
+                for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+                    const uint32_t a = adj[e];
+                    A += ((sp[a & 0xFFFFFFu] >> 7) & 0x01010101u) * (uint32_t)((int32_t)a >> 24);
+                }
+            group_barrier(1 + gl, tpg, gpc);
+            if (k < n) sp[k] |= A;
+            group_barrier(1 + gl, tpg, gpc);
+        }
+
+        const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
+        const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)g;
+        const int lane = threadIdx.x & 31;
+        // a flip's couplings go to G lanes (G the power of two >= W, at most 32)
+        int lgG = 0;
+        while ((1 << lgG) < W && lgG < 5) ++lgG;
+        const int G = 1 << lgG, fpp = 32 >> lgG;       // flips per pass of the warp
+        const int sub = lane & (G - 1), fslot = lane >> lgG;
+        for (int32_t sw = 0; sw < S; ++sw) {
+            const size_t sb = (size_t)slot * S + sw;
+            const int32_t *lp = slvl + sb * (size_t)(n + 1);
+            const uint32_t *es = sell + sb * ell_stride;
+            const int2 *pos = spos + sb * (size_t)n;
+            const int32_t L = snlev[sb];
+            // the record of the next position is loaded one iteration ahead, for
+            // a level's first position before the previous level's barrier
+            int2 pr = make_int2(0, 0);
+            if (L > 0 && li < lp[1]) pr = pos[li];
+            for (int32_t lev = 0; lev < L; ++lev) {
+                const int32_t beg = lp[lev], end = lp[lev + 1];
+                for (int32_t b = beg; b < end; b += tpg) {     // uniform over the group
+                    const int32_t i = b + li;
+                    const bool act = i < end;
+                    int2 prn = make_int2(0, 0);
+                    if (i + tpg < end) prn = pos[i + tpg];
+                    // an idle lane decides on field byte 64 and sum 0 (table index
+                    // H, in range) and never writes
+                    const int32_t k = act ? (pr.x & 0xFFFFFF) : 0;
+                    const uint32_t F = act ? sp[k] : 0x40404040u;
+                    const u32x4 u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
+                    const uint32_t old = (F >> 7) & 0x01010101u;
+                    const uint32_t nw = ising_decide_push<RULE>(F, H - 128 - (act ? pr.y : 0), u, tab_s, H);
+                    const uint32_t fl = act ? (nw ^ old) : 0u;
+                    if (fl != 0u) sp[k] = F ^ (fl << 7);
+                    const uint32_t delta = (nw & fl) - (old & fl);   // per byte +1 up, -1 down (mod 2^32)
+                    const int32_t deg = (int32_t)((uint32_t)pr.x >> 24);
+                    // the warp's flips, fpp at a time, each on G lanes
+                    unsigned fm = __ballot_sync(0xffffffffu, fl != 0u);
+                    while (fm != 0u) {
+                        unsigned m = fm;
+                        for (int c = 0; c < fslot && m != 0u; ++c) m &= m - 1u;
+                        const int srcl = m != 0u ? __ffs(m) - 1 : 0;
+                        const int32_t ip = __shfl_sync(0xffffffffu, i, srcl);
+                        const uint32_t dl = __shfl_sync(0xffffffffu, delta, srcl);
+                        const int32_t dg = __shfl_sync(0xffffffffu, deg, srcl);
+                        if (m != 0u) {
+                            const uint32_t *ep = es + (size_t)(ip >> 5) * 32 * W + (ip & 31);
+                            for (int32_t sl = sub; sl < dg; sl += G) {
+                                const uint32_t e = ep[(size_t)sl * 32];
+                                atomicAdd(&sp[e & 0xFFFFFFu], dl * (uint32_t)((int32_t)e >> 24));
+                            }
+                        }
+                        for (int c = 0; c < fpp && fm != 0u; ++c) fm &= fm - 1u;
+                    }
+                    pr = prn;
+                }
+                if (lev + 1 < L && end + li < lp[lev + 2]) pr = pos[end + li];
+                group_barrier(1 + gl, tpg, gpc);
+            }
+        }
+
+        // energy E = -1/2 sum_k s_k h_k from the fields (by position over the
+        // last sweep's records, which carry sum_j J_kj), and the write-back
+        int32_t acc[4] = {0, 0, 0, 0};
+        const int2 *pos = spos + ((size_t)slot * S + (S - 1)) * (size_t)n;
+        for (int32_t i = li; i < n; i += tpg) {
+            const int2 p0 = pos[i];
+            const uint32_t F = sp[p0.x & 0xFFFFFF];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t h = 2 * ((int32_t)((F >> (8 * q)) & 0x7Fu) - 64) - p0.y;
+                acc[q] += ((F >> (8 * q + 7)) & 1u) ? h : -h;
+            }
+        }
+        for (int32_t k = li; k < n; k += tpg) {
+            const uint32_t w = sp[k];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (r0 + q < R) dst[(size_t)(r0 + q) * n + k] = ((w >> (8 * q + 7)) & 1u) ? 1 : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            long long v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&red[gl * 4 + q], (unsigned long long)v);
+        }
+    }
+    __syncthreads();
+    if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 4 + li] / 2);
 }
 
 // The sweep of one CTA's replica groups (groups bid*gpc .. bid*gpc+gpc-1 of
@@ -389,6 +588,13 @@ __global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int 
                                  d.ncm_idx, d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x);
 }
 
+template <int RULE>
+__global__ void __launch_bounds__(1024) k_sweep_ising_push(SweepDesc d, int gpc, int tpg) {
+    sweep_ising_push_body<RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t, d.slot, d.slvl,
+                                d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf, d.ncm_idx,
+                                d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x);
+}
+
 // Many instances in one launch: CTA b works on instance items[b].x, its
 // local block items[b].y.  Descriptors live in device memory and are read
 // field by field (no local copy of the descriptor).  LPV > 1: lanes per
@@ -402,12 +608,29 @@ k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restric
     const int32_t t = ctl->t;
     if (t >= d.t_end) return;
     const KeysSeed draw{d.K.k0[0], d.K.k1[0]};
+    if constexpr (ELLP && LPV == 1) {
+        if (d.push) {   // uniform over the CTA: one member per CTA
+            sweep_ising_push_body<RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.slvl,
+                                        d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.ncm_buf,
+                                        d.ncm_idx, d.sp[(t + 1) & 1], d.en[(t + 1) & 1], ctl, gpc, tpg, it.y);
+            return;
+        }
+    }
     sweep_ising_body<ELLP, RULE, LPV>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.sorder,
                                  d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.ncm_buf,
                                  d.ncm_idx, d.sp[(t + 1) & 1], d.en[(t + 1) & 1], ctl, gpc, tpg, it.y);
 }
 
 }  // namespace
+
+bool sweep_push_enabled() {
+    const char *env = getenv("PAMC_SWEEP_PUSH");   // "0": pull sweeps everywhere
+    return !(env && env[0] == '0');
+}
+
+bool sweep_push_ok(int32_t H, int32_t S, bool ell, int lanes_per_vertex) {
+    return ell && lanes_per_vertex == 1 && H <= 63 && S > 0 && sweep_push_enabled();
+}
 
 size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg) {
     const int32_t n_pad = (n + 3) & ~3;
@@ -450,6 +673,19 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
         }                                                                                         \
     } while (0)
     const int lpv = ell ? cfg.lanes_per_vertex : 1;
+    d.push = sweep_push_ok(H, p.sweeps, ell, lpv) ? 1 : 0;
+    if (d.push) {
+        if (rule == 0) {
+            err = allow_dynamic_smem(k_sweep_ising_push<0>, smem);
+            if (err != cudaSuccess) return err;
+            k_sweep_ising_push<0><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);
+        } else {
+            err = allow_dynamic_smem(k_sweep_ising_push<1>, smem);
+            if (err != cudaSuccess) return err;
+            k_sweep_ising_push<1><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);
+        }
+        return cudaGetLastError();
+    }
     if (ell) {
         if (rule == 0) PAMC_LAUNCH_LPV(0); else PAMC_LAUNCH_LPV(1);
     } else {

@@ -269,3 +269,46 @@ def test_potts_full_size_first_step(pg, rule):
     np.testing.assert_array_equal(spins, ref.spins())
     np.testing.assert_array_equal(E, ref.energy())
     s.close()
+
+
+def _hub_instance(n=300, seed=3):
+    """Vertex 0 coupled to 63 others with +-1 weights (sum |w| = 63, the
+    largest field range of the push-model sweep), weights +-1 and +-2 on a
+    random rest of average degree 19."""
+    rng = np.random.default_rng(seed)
+    ei, ej, w = [], [], []
+    for j in range(1, 64):
+        ei.append(0); ej.append(j); w.append(int(rng.choice([-1, 1])))
+    pairs = set()
+    while len(pairs) < 2200:     # dense enough that the schedules use the ELL rows
+        a, b = (int(x) for x in rng.integers(64, n, size=2))
+        if a != b:
+            pairs.add((min(a, b), max(a, b)))
+    for a, b in sorted(pairs):
+        ei.append(a); ej.append(b); w.append(int(rng.choice([-2, -1, 1, 2])))
+    inst = W.csr_from_edges(n, np.array(ei), np.array(ej), np.array(w), "hub63")
+    sums = [int(np.abs(inst.w[inst.row_ptr[i]:inst.row_ptr[i + 1]]).sum()) for i in range(n)]
+    assert max(sums) == 63
+    return inst
+
+
+@pytest.mark.parametrize("push", ["1", "0"])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_push_and_pull_sweeps(pg, monkeypatch, push, rule):
+    """The push-model sweep (fields kept in shared memory and updated on
+    flips: H <= 63, ELL schedules, one lane per vertex) and the pull sweep
+    both give the oracle's spins, energies and controller, step after step:
+    a torus, a ragged signed sparse graph, and a hub of field range 63 with
+    weights up to 3, under both rules and several group shapes."""
+    monkeypatch.setenv("PAMC_SWEEP_PUSH", push)
+    cases = ((W.torus(20, 20, signed=True, seed=1), 13, "1,4,1"),
+             (W.gnm(333, 900, signed=True, seed=2), 20, "3,2,1"),
+             (_hub_instance(), 9, "2,1,1"))
+    for inst, R, cfg in cases:
+        monkeypatch.setenv("PAMC_SWEEP_CFG", cfg)
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+        s.init(R=R, sweeps=3, steps=3, rule=rule, seed=4)
+        assert pg.pamc_sweep_mode(s.h) == (2 if push == "1" else 1), inst.name
+        s.close()
+        compare_run(pg, inst, 8, R=R, sweeps=3, beta0=0.2, beta1=3.0, rule=rule, stagnation=1, z_rst=6,
+                    cooldown_tau=1, seed=4)
