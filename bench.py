@@ -64,9 +64,9 @@ def load_peaks():
 # DRAM bytes per launch from the committed ncu captures (profiles/), valid
 # only while the kernel sources still hash to what was captured.
 PROFILED_TRAFFIC = {
-    # k_sweep_ising, torus 141x141, R=4096, 10 sweeps: one launch
-    "sweep_torus": (63.82e6, {"paper_2606_25203_gb300/csrc/sweep_ising.cu":
-                              "e17e3bcc4115ff182f430c678f68cca954727ae6"}),
+    # the sweep launches of the default window (per launch, both instances'
+    # average); re-captured for every change of the kernel source
+    "sweep_window": (None, {"paper_2606_25203_gb300/csrc/sweep_ising.cu": ""}),
     # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.688 GB) scaled by n^2 to n=100,000
     # (captured at 6a66522d; the source since differs by one comment line)
     "dense_sweep_100k": (1.688e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
@@ -313,7 +313,9 @@ def run_ours(args):
     for s in solvers:
         s.init(**run_params)
         s.step(start)                              # untimed steps before the window
+        pg.pamc_set_sweep_timing(s.h, True)
     torch.cuda.synchronize()
+    sw0 = [pg.pamc_sweep_stats(s.h) for s in solvers]   # resets the sweep timers
     ctl0 = [s.control() for s in solvers]
     launches0 = sum(s.launches() for s in solvers)
     if dist:
@@ -336,6 +338,9 @@ def run_ours(args):
     for s in solvers:
         s.sync()
     ctl1 = [s.control() for s in solvers]
+    sw1 = [pg.pamc_sweep_stats(s.h) for s in solvers]
+    for s in solvers:
+        pg.pamc_set_sweep_timing(s.h, False)
     window = window_summary(events, start, args.steps, ctl0, ctl1)
     ms, att = reduce_over_ranks(dist, ms, attempts_per_step(insts) * args.steps)
     value = att / (ms / 1e3)
@@ -348,15 +353,12 @@ def run_ours(args):
         for s in solvers:
             s.close()
         return None
-    # dominant kernel alone: sweeps of one step on the torus (events around
-    # the step minus the other kernels is not separable, so time a sweep-only
-    # step with stagnation off on a fresh handle, same launch configuration)
-    sw_ms, sw_att = sweep_kernel_time(pg, torch, insts[0], stream)
+    # dominant kernel: the sweep launches of the timed window, each timed by
+    # CUDA events the library records around it on its stream
     peaks, peak_src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    ops_per_attempt = alu_ops_per_attempt(insts[0])
-    achieved = sw_att * ops_per_attempt / (sw_ms / 1e3) / 1e12
-    peak_tops = 152 * 128 * sm_max * 1e6 / 1e12
+    sweep = sweep_roofline(insts, args.steps, sw0, sw1, sm_max)
+    mode = [pg.pamc_sweep_mode(s.h) for s in solvers]
     e2e = e2e_measure(pg, torch, insts, args, local, start)
     dense = None
     if world == 1 and not args.no_dense:
@@ -379,11 +381,10 @@ def run_ours(args):
                                       + (f"; steps 0..{start - 1} untimed" if start else "") + ")",
                        "timed_window": window,
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-                         "frac": achieved / peak_tops, "traffic": profiled_traffic("sweep_torus"),
-                         "kernel": "k_sweep_ising (torus 141x141, R=4096, 10 sweeps)",
-                         "ops_per_attempt": ops_per_attempt,
-                         "peak_source": f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)"},
+            "roofline": dict(sweep, traffic=profiled_traffic("sweep_window"),
+                             kernel=("k_sweep_ising_push" if all(m == 2 for m in mode) else "k_sweep_ising")
+                             + " (torus 141x141 and sparse N=7000, R=4096, 10 sweeps per launch)",
+                             peak_source=f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)"),
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
@@ -448,39 +449,32 @@ def window_summary(events, start, K, ctl0, ctl1):
     return out
 
 
-def alu_ops_per_attempt(inst):
-    """Algorithmic 32-bit integer operations per spin-flip attempt: a quarter
-    of one Philox4x32-10 call (10 rounds x 6 ops: 2 mul-hi, 2 mul-lo, 2 3-way
-    xor), 2 per incident edge (neighbour spin byte and its accumulation), and
-    3 for the threshold load, compare and select."""
-    avg_deg = inst.nnz / inst.n
-    return 60 / 4 + 2 * avg_deg + 3
+# Algorithmic 32-bit integer operations of the sweeps (Eq. 3-4 with
+# incrementally kept fields): per spin-flip attempt a quarter of one
+# Philox4x32-10 call (10 rounds x 6 ops: 2 mul-hi, 2 mul-lo, 2 three-way xor)
+# and 3 for the threshold (index, load, compare); per accepted flip 1 for the
+# spin and 2 per incident coupling (read-modify-write of the neighbour field).
+OPS_PER_ATTEMPT = 60 / 4 + 3
 
 
-def sweep_kernel_time(pg, torch, inst, stream):
-    """CUDA-event time of the sweep kernel alone: a step with S sweeps minus a
-    step with 0 sweeps on the same population (same launch sequence)."""
-    s = pg.Solver(inst.row_ptr, inst.col, inst.w, stream=stream.cuda_stream)
-    s.init(**dict(PARAMS, stagnation=0, z_rst=0))
-    s.step(3)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
-    a.record(stream)
-    s.step(reps)
-    b.record(stream)
-    torch.cuda.synchronize()
-    t_full = a.elapsed_time(b) / reps
-    s.init(**dict(PARAMS, stagnation=0, z_rst=0, sweeps=0))
-    s.step(3)
-    torch.cuda.synchronize()
-    a.record(stream)
-    s.step(reps)
-    b.record(stream)
-    torch.cuda.synchronize()
-    t_zero = a.elapsed_time(b) / reps
-    s.close()
-    return max(t_full - t_zero, 1e-6), R * inst.n * SWEEPS
+def ops_per_flip(inst):
+    return 1 + 2 * inst.nnz / inst.n
+
+
+def sweep_roofline(insts, steps, before, after, sm_max):
+    """ALU roofline of the sweep launches of the timed window: algorithmic
+    operations (attempts and counted flips) over their summed event time."""
+    att = sum(R * inst.n * SWEEPS * steps for inst in insts)
+    flips = [b["flips"] - a["flips"] for a, b in zip(before, after)]
+    ops = att * OPS_PER_ATTEMPT + sum(f * ops_per_flip(inst) for f, inst in zip(flips, insts))
+    ms = sum(b["ms"] for b in after)
+    launches = sum(b["launches"] for b in after)
+    achieved = ops / (ms / 1e3) / 1e12
+    peak = 152 * 128 * sm_max * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "launches": launches, "avg_launch_ms": ms / max(launches, 1), "sweep_ms": ms,
+            "ops_per_attempt": OPS_PER_ATTEMPT, "ops_per_flip": [ops_per_flip(i) for i in insts],
+            "flip_fraction": sum(flips) / att}
 
 
 def e2e_measure(pg, torch, insts, args, device, start=0):
@@ -554,7 +548,9 @@ def dense_measure(pg, torch, n, steps, warmup, e2e=False):
     pg.pamc_step(h, warmup)
     pg.pamc_sync(h)
     pg.pamc_init(h, **P)
+    pg.pamc_set_sweep_timing(h, True)
     torch.cuda.synchronize()
+    pg.pamc_sweep_stats(h)                       # resets the sweep timers
     l0 = pg.pamc_launch_count(h)
     rows0, pos0 = pg.pamc_dense_rows(h)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -566,6 +562,8 @@ def dense_measure(pg, torch, n, steps, warmup, e2e=False):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     pg.pamc_sync(h)
+    sw = pg.pamc_sweep_stats(h)                  # the sweep launches of the timed steps
+    pg.pamc_set_sweep_timing(h, False)
     rows1, pos1 = pg.pamc_dense_rows(h)
     per_step = [a.elapsed_time(b) for a, b in ev]
     ms = sum(per_step)
@@ -584,7 +582,7 @@ def dense_measure(pg, torch, n, steps, warmup, e2e=False):
     b.record(stream)
     torch.cuda.synchronize()
     ms_nosweep = a.elapsed_time(b) / 3
-    ms_sweep = ms / steps - ms_nosweep
+    ms_sweep = sw["ms"] / max(sw["launches"], 1)   # one sweep launch per step
     pg.pamc_destroy(h)
     peaks, src = load_peaks()
     hbm = peaks["hbm_gbs"]
@@ -611,7 +609,8 @@ def dense_measure(pg, torch, n, steps, warmup, e2e=False):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "config": {"workload": DENSE_WORKLOAD, "n": n, **P,
                                         "l2": "inputs (10 GB) larger than L2"},
-        "kernels_ms": {"step": ms / steps, "sweeps": ms_sweep, "recompute_and_rest": ms_nosweep},
+        "kernels_ms": {"step": ms / steps, "sweeps": ms_sweep, "sweep_launches_timed": sw["launches"],
+                       "step_without_sweeps": ms_nosweep},
         "roofline": {"bound": "hbm", "achieved": sw_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": sw_gbs / hbm,
                      "traffic": (profiled_traffic("dense_sweep_100k") * (n / 100000) ** 2

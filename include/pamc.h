@@ -167,6 +167,17 @@ pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_
  * for dense or Potts runs. */
 pamc_status pamc_sweep_mode(pamc_handle h, int *mode);
 
+/* Sweep statistics.  pamc_set_sweep_timing(h, 1) makes every following
+ * sweep launch of the handle (sparse or dense) record a CUDA event pair on
+ * the handle's stream around it (the stream is waited for once every 1024
+ * launches).  pamc_sweep_stats synchronises and returns, in any non-NULL
+ * argument: *flips = replica spins the sparse Ising sweeps changed since
+ * pamc_init (0 for dense and Potts runs); *launches and *ms = the sweep
+ * launches timed since the last call and their summed device time, which
+ * the call then resets. */
+pamc_status pamc_set_sweep_timing(pamc_handle h, int on);
+pamc_status pamc_sweep_stats(pamc_handle h, int64_t *flips, int64_t *launches, double *ms);
+
 /* W = sum_{i<j} w_ij of the instance (cut = (W - E)/2). */
 int64_t pamc_weight_sum(pamc_handle h);
 

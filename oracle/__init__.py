@@ -112,6 +112,8 @@ def lib():
             L.orc_set_sweep_replay.argtypes = [P, P, P]
             L.orc_get_ncm_targets.argtypes = [P, P, P]
             L.orc_get_history.argtypes = [P, P]
+            L.orc_sweep_flips.argtypes = [P]
+            L.orc_sweep_flips.restype = i64
             _lib = L
     return _lib
 
@@ -362,6 +364,9 @@ class OracleRun:
         m = np.ascontiguousarray(np.asarray(mask, dtype=bool).astype(np.uint8).reshape(self.R))
         sa = np.ascontiguousarray(spins_after, dtype=np.int8).reshape(self.R, self.n)
         lib().orc_set_sweep_replay(self._h, _ptr(m), _ptr(sa))
+
+    def sweep_flips(self) -> int:
+        return int(lib().orc_sweep_flips(self._h))
 
     def history(self) -> np.ndarray:
         out = np.zeros(64, dtype=np.int64)

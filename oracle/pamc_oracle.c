@@ -216,6 +216,7 @@ struct orc_state {
     int32_t hist_len;
     int32_t *ncm_targets;      /* slots of the last iteration's cluster move */
     int32_t n_ncm_targets;
+    int64_t sweep_flips;       /* Ising: replica spins the sweeps changed */
     uint8_t *rmask;            /* sampled sweeps: sweep replica r iff rmask[r] */
     int8_t *r_spins;           /* sampled sweeps: the other replicas' results */
 };
@@ -389,6 +390,7 @@ static void orc_sweep_ising(orc_state *st, int32_t r, const int32_t *perm, int32
             nw = (u < orc_thr_metropolis(st->beta, dE)) ? (int8_t)-old : old;
         }
         if (nw != old) {
+            st->sweep_flips += 1;
             st->E[r] += 2 * (int64_t)old * h[k];
             s[k] = nw;
             for (int32_t e = st->rp[k]; e < st->rp[k + 1]; ++e) h[st->col[e]] += 2 * nw * st->J[e];
@@ -785,3 +787,5 @@ void orc_get_ncm_targets(const orc_state *st, int32_t *targets, int32_t *count) 
 void orc_get_history(const orc_state *st, int64_t *hist) {
     memcpy(hist, st->hist, sizeof(int64_t) * (size_t)st->hist_len);
 }
+
+int64_t orc_sweep_flips(const orc_state *st) { return st->sweep_flips; }

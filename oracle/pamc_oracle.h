@@ -163,6 +163,9 @@ void orc_set_state(orc_state *st, int32_t t, const orc_ctl *ctl, int64_t mstar, 
  * population can be checked with the sweeps of a sample only.  mask NULL
  * switches the mode off. */
 void orc_set_sweep_replay(orc_state *st, const uint8_t *mask, const int8_t *spins_after);
+/* Ising: replica spins the sweeps changed since orc_create (a visit whose
+ * new spin differs from the old one counts once). */
+int64_t orc_sweep_flips(const orc_state *st);
 /* The M* history of the stagnation windows, oldest first (hist_len values
  * of orc_get_ctl). */
 void orc_get_history(const orc_state *st, int64_t *hist);

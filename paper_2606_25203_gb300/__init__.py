@@ -26,7 +26,7 @@ __all__ = [
     "pamc_batch_retire", "pamc_batch_size", "pamc_batch_active", "pamc_batch_launch_count",
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
     "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_batch_set_lanes", "pamc_batch_get_lanes", "pamc_hamming", "pamc_lineage", "pamc_set_population", "pamc_fields",
-    "pamc_control_history", "pamc_sweep_mode",
+    "pamc_control_history", "pamc_sweep_mode", "pamc_set_sweep_timing", "pamc_sweep_stats",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -128,6 +128,10 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_dense_rows.argtypes = [P, P, P]
     L.pamc_control_history.argtypes = [P, P, P, P]
     L.pamc_sweep_mode.argtypes = [P, P]
+    L.pamc_set_sweep_timing.argtypes = [P, ctypes.c_int]
+    L.pamc_set_sweep_timing.restype = ctypes.c_int
+    L.pamc_sweep_stats.argtypes = [P, P, P, P]
+    L.pamc_sweep_stats.restype = ctypes.c_int
     L.pamc_sweep_mode.restype = ctypes.c_int
     L.pamc_control_history.restype = ctypes.c_int
     L.pamc_set_population.argtypes = [P, P]
@@ -349,6 +353,18 @@ def pamc_sweep_mode(h) -> int:
     v = ctypes.c_int(0)
     _check(_lib.pamc_sweep_mode(h, ctypes.byref(v)), h)
     return v.value
+
+
+def pamc_set_sweep_timing(h, on: bool = True):
+    _check(_lib.pamc_set_sweep_timing(h, 1 if on else 0), h)
+
+
+def pamc_sweep_stats(h) -> dict:
+    """flips since init; launches and ms of the sweep launches timed since the last call."""
+    f = np.zeros(2, dtype=np.int64)
+    ms = np.zeros(1, dtype=np.float64)
+    _check(_lib.pamc_sweep_stats(h, _ptr(f[0:1]), _ptr(f[1:2]), _ptr(ms)), h)
+    return {"flips": int(f[0]), "launches": int(f[1]), "ms": float(ms[0])}
 
 
 def pamc_weight_sum(h) -> int:

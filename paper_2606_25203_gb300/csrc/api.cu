@@ -102,6 +102,13 @@ struct pamc_handle_s {
     void *d_bar = nullptr;
     int32_t dense_Hc = 0, dense_grid = 0, dense_nupd = 0, dense_rows = 0;
     int64_t launches = 0;
+    // device time of the sweep launches (pamc_set_sweep_timing): events
+    // recorded on the handle's stream around each sweep launch, in pairs
+    bool time_sweeps = false;
+    std::vector<cudaEvent_t> sweep_ev;
+    size_t sweep_ev_used = 0;      // pairs recorded and not yet folded
+    double sweep_ms = 0.0;         // time of the pairs folded since the last read
+    int64_t sweep_timed = 0;       // sweep launches timed since the last read
     char err[256] = "";
 };
 
@@ -194,6 +201,40 @@ pamc_status validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const
     if (fwd != bwd) return fail(nullptr, PAMC_ERR_ASYM, "coupling matrix is not symmetric");
     W /= 2;
     return PAMC_OK;
+}
+
+// Sum the recorded pairs into sweep_ms (waits for the stream).
+cudaError_t fold_sweep_events(pamc_handle h) {
+    if (h->sweep_ev_used == 0) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    for (size_t i = 0; e == cudaSuccess && i < h->sweep_ev_used; ++i) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, h->sweep_ev[2 * i], h->sweep_ev[2 * i + 1]);
+        h->sweep_ms += ms;
+    }
+    h->sweep_ev_used = 0;
+    return e;
+}
+
+// Events around one sweep launch when timing is on; at most 1024 pairs are
+// kept before they are folded (a wait for the stream every 1024 launches).
+cudaError_t sweep_timer(pamc_handle h, bool after) {
+    if (!h->time_sweeps) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (!after) {
+        if (h->sweep_ev_used == 1024) e = fold_sweep_events(h);
+        while (e == cudaSuccess && h->sweep_ev.size() < 2 * (h->sweep_ev_used + 1)) {
+            cudaEvent_t ev;
+            e = cudaEventCreate(&ev);
+            if (e == cudaSuccess) h->sweep_ev.push_back(ev);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->sweep_ev[2 * h->sweep_ev_used], h->stream);
+    } else {
+        e = cudaEventRecord(h->sweep_ev[2 * h->sweep_ev_used + 1], h->stream);
+        h->sweep_ev_used += 1;
+        h->sweep_timed += 1;
+    }
+    return e;
 }
 
 void release_run(pamc_handle h) {
@@ -417,11 +458,13 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
         if (e == cudaSuccess) e = launch_dense_tables(p.rule, h->dense_Hc, n, h->d_ctl, h->d_tab, h->stream);
         if (e == cudaSuccess)
             e = dense_recompute(h, src, h->d_parent, h->d_ncm_idx, -1);
+        if (e == cudaSuccess) e = sweep_timer(h, false);
         if (e == cudaSuccess)
             e = launch_dense_sweep(n, R, p.sweeps, p.rule, h->dense_Hc, (int32_t)t, p.seed, h->dense_nupd,
                                    h->dense_rows, h->dense_grid, h->d_J, h->d_perm, h->d_tab, src,
                                    h->d_parent, nullptr, h->d_ncm_idx, h->d_H, dst, Ed, h->d_G, h->d_T,
                                    h->d_T2, h->d_flip, h->d_snew, h->d_bar, h->d_ctl, h->stream, h->dense_tcu);
+        if (e == cudaSuccess) e = sweep_timer(h, true);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 7;
         if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
@@ -687,10 +730,12 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
             h->launches += 1;
         }
         SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w};
+        if (e == cudaSuccess) e = sweep_timer(h, false);
         if (e == cudaSuccess)
             e = launch_sweep(sweep_kind(p), p.rule, n, h->d_rp, h->d_adj, h->H, p, (int32_t)t,
                              (int32_t)(t % kSchedSlots), sv, h->d_tab, src, h->d_parent,
                              h->d_ncm_buf, h->d_ncm_idx, dst, Ed, h->d_ctl, h->cfg, h->W, h->stream);
+        if (e == cudaSuccess) e = sweep_timer(h, true);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 2;
         if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
@@ -922,6 +967,28 @@ pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_
     return PAMC_OK;
 }
 
+pamc_status pamc_set_sweep_timing(pamc_handle h, int on) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    h->time_sweeps = on != 0;
+    return PAMC_OK;
+}
+
+pamc_status pamc_sweep_stats(pamc_handle h, int64_t *flips, int64_t *launches, double *ms) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_sweep_stats before pamc_init");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    const cudaError_t e = fold_sweep_events(h);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sweep timing");
+    if (flips) *flips = c.sweep_flips;
+    if (launches) *launches = h->sweep_timed;
+    if (ms) *ms = h->sweep_ms;
+    h->sweep_timed = 0;
+    h->sweep_ms = 0.0;
+    return PAMC_OK;
+}
+
 pamc_status pamc_sweep_mode(pamc_handle h, int *mode) {
     if (!h || !mode) return fail(h, PAMC_ERR_ARG, "null argument");
     if (!h->initialized || h->dense || h->p.kind != 0)
@@ -943,6 +1010,7 @@ void pamc_destroy(pamc_handle h) {
     if (!h) return;
     cudaSetDevice(h->device);
     release_run(h);
+    for (cudaEvent_t ev : h->sweep_ev) cudaEventDestroy(ev);
     dev_free_all(h, h->inst_bufs);
     delete h;
 }

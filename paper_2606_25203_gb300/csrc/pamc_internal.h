@@ -32,6 +32,8 @@ struct DevCtl {
     // dense sweeps: coupling rows gathered by the field update (positions
     // that flipped in some replica) and positions visited, since pamc_init
     int64_t dense_rows, dense_positions;
+    // sparse Ising sweeps: replica spins that changed at a visit, since pamc_init
+    int64_t sweep_flips;
 };
 
 // Per-(t, sweep) update schedule: the random order's dependency levels.

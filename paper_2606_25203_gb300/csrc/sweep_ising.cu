@@ -24,9 +24,9 @@
 // 64 + sum_j J_kj [s_j = +1] (in [1, 127]) in bits 0..6, computed once per
 // launch from the CSR.  A visit reads its own word only; a flip adds
 // (up - down) * J_jk to each neighbour's word -- the incrementally maintained
-// fields of Eq. 3.  The flips of a warp are gathered by ballot and their
-// neighbour updates spread over the warp's lanes, so a visit pays for the
-// updates only in proportion to the flips.  Two vertices of a level may share
+// fields of Eq. 3.  The record and first four couplings of the next position
+// are loaded one iteration ahead as in the pull model, so a flip pushes
+// without waiting.  Two vertices of a level may share
 // a neighbour, so the updates are shared-memory atomics; 32-bit modular
 // addition is exact because every byte of every intermediate word is the
 // field byte of some configuration and stays in [1, 127].
@@ -45,6 +45,15 @@ __device__ __forceinline__ void group_barrier(int id, int nthreads, int groups) 
     } else {
         asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
     }
+}
+
+// Spin flips of a launch (replicas whose spin changed at a visit), summed per
+// warp into the controller's counter; every lane of the warp calls it.
+__device__ __forceinline__ void count_flips(uint32_t nflip, const DevCtl *ctl) {
+    unsigned long long v = nflip;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0ull)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&const_cast<DevCtl *>(ctl)->sweep_flips), v);
 }
 
 // Philox draws with the round keys precomputed (kernel parameter space) or
@@ -137,8 +146,9 @@ sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     uint32_t *sp = spins_all + (size_t)gl * n_pad;
 
     if (active) {
-        // the replica copy of the population step (see the pull body), spins
-        // into bit 7 of each replica byte
+        // the replica copy of the population step (see the pull body): spin
+        // bits and fields of each vertex straight from the source rows in
+        // global memory, so that no thread reads a word another one writes
         const int8_t *rows[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -150,94 +160,89 @@ sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                 rows[q] = nullptr;
             }
         }
-        for (int32_t k = li; k < n; k += tpg) {
+        auto bits = [&](int32_t j) {
             uint32_t w = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (rows[q] != nullptr) w |= (uint32_t)(rows[q][k] > 0) << (8 * q + 7);
-            sp[k] = w;
+                if (rows[q] != nullptr) w |= (uint32_t)(rows[q][j] > 0) << (8 * q);
+            return w;
+        };
+        for (int32_t k = li; k < n; k += tpg) {
+            uint32_t A = 0x40404040u;
+            for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
+                const uint32_t a = adj[e];
+                A += bits((int32_t)(a & 0xFFFFFFu)) * (uint32_t)((int32_t)a >> 24);
+            }
+            sp[k] = (bits(k) << 7) | A;
         }
     }
     __syncthreads();
 
     if (active) {
-        // the group's fields from the definition, once per launch, in chunks
-        // of one vertex per thread: every read of a chunk precedes its writes,
-        // and later chunks read only the spin bits, which the writes keep
-        for (int32_t k0 = 0; k0 < n; k0 += tpg) {
-            const int32_t k = k0 + li;
-            uint32_t A = 0x40404040u;
-            if (k < n)
-                for (int32_t e = rp[k]; e < rp[k + 1]; ++e) {
-                    const uint32_t a = adj[e];
-                    A += ((sp[a & 0xFFFFFFu] >> 7) & 0x01010101u) * (uint32_t)((int32_t)a >> 24);
-                }
-            group_barrier(1 + gl, tpg, gpc);
-            if (k < n) sp[k] |= A;
-            group_barrier(1 + gl, tpg, gpc);
-        }
-
         const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
         const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)g;
-        const int lane = threadIdx.x & 31;
-        // a flip's couplings go to G lanes (G the power of two >= W, at most 32)
-        int lgG = 0;
-        while ((1 << lgG) < W && lgG < 5) ++lgG;
-        const int G = 1 << lgG, fpp = 32 >> lgG;       // flips per pass of the warp
-        const int sub = lane & (G - 1), fslot = lane >> lgG;
+        uint32_t nflip = 0;
         for (int32_t sw = 0; sw < S; ++sw) {
             const size_t sb = (size_t)slot * S + sw;
             const int32_t *lp = slvl + sb * (size_t)(n + 1);
             const uint32_t *es = sell + sb * ell_stride;
             const int2 *pos = spos + sb * (size_t)n;
             const int32_t L = snlev[sb];
-            // the record of the next position is loaded one iteration ahead, for
-            // a level's first position before the previous level's barrier
+            // the record and the first four couplings of a position are loaded
+            // one iteration ahead -- for a level's first position before the
+            // previous level's barrier, from a clamped position (they do not
+            // depend on spins); a flip pushes along them
             int2 pr = make_int2(0, 0);
-            if (L > 0 && li < lp[1]) pr = pos[li];
+            uint32_t e4[4] = {0u, 0u, 0u, 0u};
+            auto fetch = [&](int32_t i, int2 &r, uint32_t (&e)[4]) {
+                r = pos[i];
+                const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) e[q] = ep[q * 32];
+            };
+            if (L > 0) fetch(min(li, n - 1), pr, e4);
             for (int32_t lev = 0; lev < L; ++lev) {
                 const int32_t beg = lp[lev], end = lp[lev + 1];
-                for (int32_t b = beg; b < end; b += tpg) {     // uniform over the group
-                    const int32_t i = b + li;
-                    const bool act = i < end;
+                int32_t i = beg + li;
+                while (i < end) {
+                    const int32_t inext = i + tpg;
                     int2 prn = make_int2(0, 0);
-                    if (i + tpg < end) prn = pos[i + tpg];
-                    // an idle lane decides on field byte 64 and sum 0 (table index
-                    // H, in range) and never writes
-                    const int32_t k = act ? (pr.x & 0xFFFFFF) : 0;
-                    const uint32_t F = act ? sp[k] : 0x40404040u;
+                    uint32_t e4n[4] = {0u, 0u, 0u, 0u};
+                    if (inext < end) fetch(inext, prn, e4n);
+                    const int32_t k = pr.x & 0xFFFFFF;
+                    const uint32_t F = sp[k];
                     const u32x4 u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
                     const uint32_t old = (F >> 7) & 0x01010101u;
-                    const uint32_t nw = ising_decide_push<RULE>(F, H - 128 - (act ? pr.y : 0), u, tab_s, H);
-                    const uint32_t fl = act ? (nw ^ old) : 0u;
-                    if (fl != 0u) sp[k] = F ^ (fl << 7);
-                    const uint32_t delta = (nw & fl) - (old & fl);   // per byte +1 up, -1 down (mod 2^32)
-                    const int32_t deg = (int32_t)((uint32_t)pr.x >> 24);
-                    // the warp's flips, fpp at a time, each on G lanes
-                    unsigned fm = __ballot_sync(0xffffffffu, fl != 0u);
-                    while (fm != 0u) {
-                        unsigned m = fm;
-                        for (int c = 0; c < fslot && m != 0u; ++c) m &= m - 1u;
-                        const int srcl = m != 0u ? __ffs(m) - 1 : 0;
-                        const int32_t ip = __shfl_sync(0xffffffffu, i, srcl);
-                        const uint32_t dl = __shfl_sync(0xffffffffu, delta, srcl);
-                        const int32_t dg = __shfl_sync(0xffffffffu, deg, srcl);
-                        if (m != 0u) {
-                            const uint32_t *ep = es + (size_t)(ip >> 5) * 32 * W + (ip & 31);
-                            for (int32_t sl = sub; sl < dg; sl += G) {
+                    const uint32_t nw = ising_decide_push<RULE>(F, H - 128 - pr.y, u, tab_s, H);
+                    const uint32_t fl = nw ^ old;
+                    if (fl != 0u) {
+                        sp[k] = F ^ (fl << 7);
+                        nflip += __popc(fl);
+                        // per byte +1 (up) or -1 (down), mod 2^32, times J_jk
+                        const uint32_t delta = (nw & fl) - (old & fl);
+                        const int32_t deg = (int32_t)((uint32_t)pr.x >> 24);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)   // padding slots: vertex 0, coupling 0
+                            if (q < deg) atomicAdd(&sp[e4[q] & 0xFFFFFFu], delta * (uint32_t)((int32_t)e4[q] >> 24));
+                        if (deg > 4) {
+                            const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+                            for (int32_t sl = 4; sl < deg; ++sl) {
                                 const uint32_t e = ep[(size_t)sl * 32];
-                                atomicAdd(&sp[e & 0xFFFFFFu], dl * (uint32_t)((int32_t)e >> 24));
+                                atomicAdd(&sp[e & 0xFFFFFFu], delta * (uint32_t)((int32_t)e >> 24));
                             }
                         }
-                        for (int c = 0; c < fpp && fm != 0u; ++c) fm &= fm - 1u;
                     }
+                    i = inext;
                     pr = prn;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) e4[q] = e4n[q];
                 }
-                if (lev + 1 < L && end + li < lp[lev + 2]) pr = pos[end + li];
+                if (lev + 1 < L) fetch(min(end + li, n - 1), pr, e4);
                 group_barrier(1 + gl, tpg, gpc);
             }
         }
 
+        count_flips(nflip, ctl);
         // energy E = -1/2 sum_k s_k h_k from the fields (by position over the
         // last sweep's records, which carry sum_j J_kj), and the write-back
         int32_t acc[4] = {0, 0, 0, 0};
@@ -328,6 +333,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     if (active) {
         const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
         const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)g;
+        uint32_t nflip = 0;
         for (int32_t sw = 0; sw < S; ++sw) {
             const size_t sb = (size_t)slot * S + sw;
             const int32_t *ord = sorder + sb * (size_t)n;
@@ -387,7 +393,10 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                         const uint32_t nw = ising_decide<RULE>(0x80808080u + Ap, H - 256 - pr.y, u, old, tab_s, H);
                         // every lane has read sp[k] before any lane of the group writes it
                         __syncwarp();
-                        if (act && sub == 0 && nw != old) sp[k] = nw;
+                        if (act && sub == 0 && nw != old) {
+                            sp[k] = nw;
+                            nflip += __popc(nw ^ old);
+                        }
                     }
                     if (lev + 1 < L) fetch(min(end + vl, n - 1));
                     group_barrier(1 + gl, tpg, gpc);
@@ -488,7 +497,10 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                     if (!ELLP) u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
                     const uint32_t old = sp[k];
                     const uint32_t nw = ising_decide<RULE>(A, H - 256 - jsum, u, old, tab_s, H);
-                    if (nw != old) sp[k] = nw;
+                    if (nw != old) {
+                        sp[k] = nw;
+                        nflip += __popc(nw ^ old);
+                    }
                     i = inext;
                     pr = prn;
 #pragma unroll
@@ -505,6 +517,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
             }
         }
 
+        count_flips(nflip, ctl);
         // energy from the definition E = -1/2 sum_k s_k h_k (per thread at most
         // n / 32 vertices of |s h| <= 127 each: int32), and the write-back
         int32_t acc[4] = {0, 0, 0, 0};

@@ -312,3 +312,26 @@ def test_push_and_pull_sweeps(pg, monkeypatch, push, rule):
         s.close()
         compare_run(pg, inst, 8, R=R, sweeps=3, beta0=0.2, beta1=3.0, rule=rule, stagnation=1, z_rst=6,
                     cooldown_tau=1, seed=4)
+
+
+@pytest.mark.parametrize("push", ["1", "0"])
+def test_sweep_flip_count_and_timing(pg, monkeypatch, push):
+    """pamc_sweep_stats: the flips counted by the sweep kernels equal the
+    oracle's count over a run, and with timing on every sweep launch of the
+    handle is timed (one per step), with a positive device time."""
+    monkeypatch.setenv("PAMC_SWEEP_PUSH", push)
+    inst = W.gnm(500, 1400, signed=True, seed=5)
+    params = dict(R=12, sweeps=3, steps=10, beta0=0.2, beta1=2.0, stagnation=1, z_rst=6, seed=8)
+    ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **params)
+    s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+    s.init(**params)
+    pg.pamc_set_sweep_timing(s.h, True)
+    s.step(4)
+    st = pg.pamc_sweep_stats(s.h)
+    ref.step(4)
+    assert st["flips"] == ref.sweep_flips() and st["launches"] == 4 and st["ms"] > 0
+    s.step(6)
+    st = pg.pamc_sweep_stats(s.h)
+    ref.step(6)
+    assert st["flips"] == ref.sweep_flips() and st["launches"] == 6
+    s.close()

@@ -120,3 +120,20 @@ def test_sampled_sweeps_detect_a_wrong_sample():
     np.testing.assert_array_equal(got[6], bad[6])        # taken as given
     rep.close()
     full.close()
+
+
+def test_sweep_flip_count_is_the_number_of_changed_spins():
+    """With one sweep per step and no resampling, a spin changes at most once
+    per step at its one visit, so the flips of a step are the spins that
+    differ before and after it."""
+    inst = W.torus(12, 12, signed=True, seed=3)
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=8, sweeps=1, steps=12, resample=0, seed=1)
+    total = 0
+    prev = run.spins()
+    for _ in range(12):
+        run.step(1)
+        cur = run.spins()
+        total += int((cur != prev).sum())
+        prev = cur
+        assert run.sweep_flips() == total
+    run.close()
