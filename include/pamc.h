@@ -161,9 +161,10 @@ pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_
 /* How the sparse Ising sweeps of an initialised run keep the local fields
  * (Eq. 3): *mode = 0 pulled from the neighbours' spins at every visit over
  * the CSR rows, 1 the same over position-indexed (ELL) rows, 2 kept in
- * shared memory and updated on every flip (push; instances with
- * max_i sum_j |w_ij| <= 63, ELL rows, one lane per vertex, at least one
- * sweep).  Speed only, never results.  PAMC_ERR_STATE before pamc_init or
+ * shared memory and updated on every flip (push; chosen by the environment
+ * variable PAMC_SWEEP_PUSH=1 for instances with max_i sum_j |w_ij| <= 63,
+ * ELL rows, one lane per vertex, at least one sweep).  Speed only, never
+ * results.  PAMC_ERR_STATE before pamc_init or
  * for dense or Potts runs. */
 pamc_status pamc_sweep_mode(pamc_handle h, int *mode);
 

@@ -159,7 +159,7 @@ void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t
 size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
 // Push-model Ising sweeps (fields kept in shared memory, updated on flips):
 // used where H <= 63, on ELL schedules with one lane per vertex and S >= 1,
-// unless the environment variable PAMC_SWEEP_PUSH is "0".
+// when the environment variable PAMC_SWEEP_PUSH is "1".
 bool sweep_push_enabled();
 bool sweep_push_ok(int32_t H, int32_t S, bool ell, int lanes_per_vertex);
 void launch_schedule_batched(const SchedDesc *descs, const int2 *items, int32_t nitems, int32_t n_max,

@@ -11,6 +11,8 @@
 //   k_control  M* / best configuration, the recent-progress history, the
 //              adaptive temperature rule (Sec. III.C) and the restart.
 // All state lives on the device so that an iteration never waits for the host.
+#include <cstdlib>
+
 #include "pamc_device.cuh"
 #include "pamc_internal.h"
 
@@ -315,9 +317,13 @@ __device__ __forceinline__ bool nbefore(uint32_t ka, int32_t a, uint32_t kb, int
 // every coupled candidate earlier in the trial's random order is rejected,
 // and rejected (2) once one of them is taken -- the same set the sequential
 // greedy scan in that order builds.  Returns the size of the set.
+// The rounds are bounded by lim (n + 1 always suffices: every round decides
+// at least the earliest undecided candidate); a trial still undecided after
+// lim rounds sets PAMC_ERR_TIMEOUT and keeps the set taken so far, which is
+// independent, so the move still preserves the energy.
 __device__ int32_t mis_trial(int32_t n, const int32_t *rp, const uint32_t *adj, uint8_t *stat,
                              uint32_t *key, int32_t a, int32_t t, int32_t m, uint32_t key0,
-                             uint32_t key1, DevCtl *ctl, int *s_flag, int *s_red) {
+                             uint32_t key1, DevCtl *ctl, int *s_flag, int *s_red, int32_t lim) {
     for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
         if (stat[k] != 3) {
             stat[k] = 0;
@@ -325,7 +331,7 @@ __device__ int32_t mis_trial(int32_t n, const int32_t *rp, const uint32_t *adj, 
         }
     }
     __syncthreads();
-    for (int32_t round = 0; round <= n + 1; ++round) {
+    for (int32_t round = 0; round <= lim; ++round) {
         if (threadIdx.x == 0) *s_flag = 0;
         __syncthreads();
         for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
@@ -349,7 +355,7 @@ __device__ int32_t mis_trial(int32_t n, const int32_t *rp, const uint32_t *adj, 
         const int more = *s_flag;
         __syncthreads();
         if (!more) break;
-        if (round == n + 1 && threadIdx.x == 0) atomicExch(&ctl->err, (int)PAMC_ERR_TIMEOUT);
+        if (round == lim && threadIdx.x == 0) atomicExch(&ctl->err, (int)PAMC_ERR_TIMEOUT);
     }
     int32_t c = 0;
     for (int32_t k = threadIdx.x; k < n; k += blockDim.x) c += stat[k] == 1 ? 1 : 0;
@@ -371,7 +377,7 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
       int32_t kind, int32_t n_top, int32_t trials, uint32_t key0, uint32_t key1,
       const int8_t *__restrict__ src, const int64_t *__restrict__ E_src,
       const int32_t *__restrict__ parent, const int32_t *__restrict__ targets,
-      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, int32_t key_smem,
+      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, int32_t key_smem, int32_t max_rounds,
       DevCtl *__restrict__ ctl) {
     // the per-site decision state of the MIS rounds lives in shared memory
     // (n bytes), and the trial's order keys too (4n bytes) when key_smem:
@@ -400,14 +406,15 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
         stat[k] = h == 0 ? 0 : 3;
     }
     __syncthreads();
+    const int32_t lim = max_rounds >= 0 && max_rounds < n + 1 ? max_rounds : n + 1;
     int32_t best = -1, besta = 0;
     for (int32_t a = 0; a < trials; ++a) {
-        const int32_t sz = mis_trial(n, rp, adj, stat, key, a, t, m, key0, key1, ctl, &s_flag, &s_red);
+        const int32_t sz = mis_trial(n, rp, adj, stat, key, a, t, m, key0, key1, ctl, &s_flag, &s_red, lim);
         if (sz > best) { best = sz; besta = a; }   // ties keep the earliest trial
     }
     if (trials <= 0) best = 0;
     if (best > 0) {
-        mis_trial(n, rp, adj, stat, key, besta, t, m, key0, key1, ctl, &s_flag, &s_red);
+        mis_trial(n, rp, adj, stat, key, besta, t, m, key0, key1, ctl, &s_flag, &s_red, lim);
         for (int32_t k = threadIdx.x; k < n; k += blockDim.x)
             if (stat[k] == 1) sp[k] = (int8_t)-sp[k];
     }
@@ -612,9 +619,13 @@ cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const 
     const size_t smem = key_smem ? with_keys : ncm_stat_bytes(n);
     cudaError_t err = allow_dynamic_smem(k_ncm, smem);
     if (err != cudaSuccess) return err;
+    // PAMC_NCM_MAX_ROUNDS: a smaller bound on the MIS rounds than n + 1, for
+    // tests that make the bounded wait run out (PAMC_ERR_TIMEOUT, pamc_sync)
+    int32_t max_rounds = -1;
+    if (const char *env = getenv("PAMC_NCM_MAX_ROUNDS")) max_rounds = atoi(env);
     k_ncm<<<ntop, kNcmThreads, smem, st>>>(n, rp, adj, p.R, p.kind, p.n_top, p.mis_trials,
                                            (uint32_t)p.seed, (uint32_t)(p.seed >> 32), src, E_src,
-                                           parent, targets, ncm_buf, nkey, key_smem, ctl);
+                                           parent, targets, ncm_buf, nkey, key_smem, max_rounds, ctl);
     return cudaGetLastError();
 }
 

@@ -59,7 +59,11 @@ def alone(pg, inst, p):
     return s
 
 
-def test_batch_members_equal_alone(pg):
+@pytest.mark.parametrize("push", ["0", "1"])
+def test_batch_members_equal_alone(pg, monkeypatch, push):
+    """Also with the push-model sweep for the members it applies to (field
+    range <= 63, ELL schedules, one lane per vertex), in and out of the batch."""
+    monkeypatch.setenv("PAMC_SWEEP_PUSH", push)
     cases = mix()
     ref = [alone(pg, inst, p) for inst, p in cases]
     b = pg.pamc_batch_create(0)
