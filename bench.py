@@ -302,7 +302,7 @@ def run_ours(args):
     run_params = dict(PARAMS, seed=rank_seed(PARAMS["seed"], rank))
     # the work of a step depends on where it is in the schedule (control,
     # cluster moves, restart): place the timed window
-    if args.steps >= STEPS_SCHEDULE:
+    if args.steps >= STEPS_SCHEDULE or args.lean:      # profiling runs time steps 0..K-1
         for _ in range(args.warmup):
             for s in solvers:
                 s.step(1)
@@ -641,8 +641,8 @@ def run_dense(args):
 
 
 SERVE_PARAMS = dict(R=512, sweeps=10, steps=200, beta0=0.1, beta1=3.0, seed=0)
-SERVE_WORKLOAD = ("serving stream: Max-Cut requests, N ~ U[800, 20000], ER unit / ER +-1 (avg deg 20) / "
-                  "torus +-1, R=512, 200 steps x 10 sweeps each")
+SERVE_WORKLOAD = ("serving stream: Max-Cut and Max-3-Cut requests, N ~ U[800, 20000], ER unit / ER +-1 "
+                  "(avg deg 20) / torus +-1, R=512, 200 steps x 10 sweeps each")
 
 
 def run_serving(args):
@@ -660,7 +660,7 @@ def run_serving(args):
     P = dict(SERVE_PARAMS)
     nreq = args.serve_requests
     t0 = time.perf_counter()
-    burst = W.serving_stream(nreq, rate=0.0, seed=1)
+    burst = W.serving_stream(nreq, rate=0.0, seed=1, max3cut_frac=args.serve_max3cut)
     gen_s = time.perf_counter() - t0
     warm = W.serving_stream(max(3, args.warmup), rate=0.0, seed=2, n_lo=800, n_hi=2000)
     wp = dict(P, steps=4)
@@ -684,7 +684,7 @@ def run_serving(args):
     cuts = {r.rid: r.cut for r in seq.results}
     identical = all(cuts[r.rid] == r.cut for r in st.results) and len(st.results) == nreq
     cap = st.solves_per_s
-    poisson = W.serving_stream(nreq, rate=0.5 * cap, seed=1)
+    poisson = W.serving_stream(nreq, rate=0.5 * cap, seed=1, max3cut_frac=args.serve_max3cut)
     lt = srv.serve(poisson, P)
     srv.close()
     peaks, src = load_peaks()
@@ -697,7 +697,8 @@ def run_serving(args):
         "steps": nreq, "warmup": len(warm), "ms_per_step": st.makespan / nreq * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": SERVE_WORKLOAD, "requests": nreq, **P, "max_active": args.serve_max_active,
+        "config": {"workload": SERVE_WORKLOAD, "requests": nreq, "max3cut_requests": sum(r.kind for r in burst),
+                   **P, "max_active": args.serve_max_active,
                    "timing": "host wall clock over the whole stream (upload, init, steps, best-cut readback)",
                    "l2": "populations and schedule rings of the resident requests exceed L2"},
         "p50_s": lt.latency_pct(50), "p99_s": lt.latency_pct(99),
@@ -977,6 +978,8 @@ def main():
     ap.add_argument("--batch-n-lo", type=int, default=800)
     ap.add_argument("--batch-n-hi", type=int, default=20000)
     ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-max3cut", type=float, default=0.25,
+                    help="fraction of the serving requests that ask for Max-3-Cut")
     ap.add_argument("--serve-max-active", type=int, default=64)
     ap.add_argument("--dense-n", type=int, default=DENSE_N)
     ap.add_argument("--dense-e2e", action="store_true", help="dense100k: add the end-to-end figure")

@@ -232,7 +232,8 @@ void pamc_destroy(pamc_handle h);
  * pamc_step computes for it alone (same random streams, orders, tables and
  * controller): its spins, energies, parents, counts and best cut are
  * identical in and out of the batch.
- * Members: initialised sparse Max-Cut (kind 0) handles with stagnation = 0
+ * Members: initialised sparse handles of Max-Cut (kind 0, either rule) or
+ * Max-3-Cut with the cascaded sampler (kind 1, rule 0), with stagnation = 0
  * and no restart re-initialisation (z_rst = 0 or restart_reinit = 0);
  * others are refused with PAMC_ERR_ARG.  A member must stay alive and must
  * not be stepped or re-initialised on its own while it is in the batch.  The batch runs on its

@@ -1108,16 +1108,24 @@ pamc_status rebuild(pamc_batch b) {
     std::vector<TabDesc> tabs;
     std::vector<CtlDesc> ctls;
     std::vector<SweepDesc> sw;
-    std::vector<int2> swi[2][2][kClasses];   // [ell][rule][class]
-    int32_t nmax[kClasses] = {0, 0, 0}, Rmax = 1;
+    std::vector<int2> swi[2][2][kClasses];   // Ising [ell][rule][class]
+    std::vector<int2> pswi[2][kClasses];     // Potts (cascaded sampler) [ell][class]
+    int32_t nmax[kClasses] = {0, 0, 0}, pnmax[kClasses] = {0, 0, 0}, Rmax = 1;
     for (pamc_handle h : b->members)
-        if (h->host_t < h->p.steps) nmax[batch_class(h->n)] = std::max(nmax[batch_class(h->n)], h->n);
-    // the shape of each class, with fewer groups per CTA where the largest member's spins need it
-    SweepCfg eff[kClasses];
+        if (h->host_t < h->p.steps) {
+            int32_t &m = (h->p.kind == 0 ? nmax : pnmax)[batch_class(h->n)];
+            m = std::max(m, h->n);
+        }
+    // the shape of each class, with fewer groups per CTA where the largest
+    // member's spins (Ising: 4n bytes a group, Potts: 8n) need it
+    SweepCfg eff[kClasses], peff[kClasses];
     for (int c = 0; c < kClasses; ++c) {
         eff[c] = b->shape[c];
         while (eff[c].groups_per_cta > 1 && sweep_ising_smem_bytes(nmax[c], 127, eff[c]) > kSmemMax)
             eff[c].groups_per_cta -= 1;
+        peff[c] = SweepCfg{b->shape[c].groups_per_cta, b->shape[c].warps_per_group, 1};
+        while (peff[c].groups_per_cta > 1 && sweep_potts_smem_bytes(pnmax[c], 127, peff[c]) > kSmemMax)
+            peff[c].groups_per_cta -= 1;
     }
     for (pamc_handle h : b->members) {
         const pamc_params &p = h->p;
@@ -1136,7 +1144,7 @@ pamc_status rebuild(pamc_batch b) {
                     p.kind, p.resample, p.n_top, p.cooldown_tau, k0, k1, {h->d_E[0], h->d_E[1]}, t_end,
                     h->d_fam, 0};
         prep.push_back(pd);
-        tabs.push_back(TabDesc{h->d_ctl, h->d_tab, p.rule, h->H, t_end});
+        tabs.push_back(TabDesc{h->d_ctl, h->d_tab, p.rule, h->H, t_end, p.kind});
         SweepDesc d;
         memset(&d, 0, sizeof(d));
         d.rp = h->d_rp; d.adj = h->d_adj; d.sorder = h->d_order; d.slvl = h->d_lvl; d.snlev = h->d_nlev;
@@ -1145,15 +1153,15 @@ pamc_status rebuild(pamc_batch b) {
         d.n = h->n; d.n_pad = (h->n + 3) & ~3; d.H = h->H; d.R = p.R; d.S = p.sweeps;
         d.W = h->ell_w; d.K = make_philox_keys(p.seed);
         d.sp[0] = h->d_spins[0]; d.sp[1] = h->d_spins[1]; d.en[0] = h->d_E[0]; d.en[1] = h->d_E[1];
-        d.slots = kSchedSlots; d.t_end = t_end;
+        d.slots = kSchedSlots; d.t_end = t_end; d.Wsum = h->W;
         const int cls = batch_class(h->n);
-        const SweepCfg cfg = eff[cls];
-        d.push = sweep_push_ok(h->H, p.sweeps, h->d_ell != nullptr, cfg.lanes_per_vertex) ? 1 : 0;
+        const SweepCfg cfg = p.kind == 0 ? eff[cls] : peff[cls];
+        d.push = p.kind == 0 && sweep_push_ok(h->H, p.sweeps, h->d_ell != nullptr, cfg.lanes_per_vertex) ? 1 : 0;
         const int idx = (int)sw.size();
         sw.push_back(d);
         const int32_t ctas = ((p.R + 3) / 4 + cfg.groups_per_cta - 1) / cfg.groups_per_cta;
         // with sweeps = 0 the launch still copies the resampled population and its energies
-        auto &items = swi[h->d_ell != nullptr][p.rule][cls];
+        auto &items = p.kind == 0 ? swi[h->d_ell != nullptr][p.rule][cls] : pswi[h->d_ell != nullptr][cls];
         for (int32_t x = 0; x < ctas; ++x) items.push_back(make_int2(idx, x));
         Rmax = std::max(Rmax, p.R);
         CtlDesc c{nullptr, nullptr, h->d_best, h->d_ctl, h->W, p.target_cut, p.reheat_factor, p.beta0,
@@ -1165,6 +1173,8 @@ pamc_status rebuild(pamc_batch b) {
     for (auto &a : swi)
         for (auto &c : a)
             for (auto &v : c) all_items.insert(all_items.end(), v.begin(), v.end());
+    for (auto &a : pswi)
+        for (auto &v : a) all_items.insert(all_items.end(), v.begin(), v.end());
     const bool ok = upload(b, b->sd, sd) && upload(b, b->sdi, sdi) && upload(b, b->prep, prep) &&
                     upload(b, b->tabs, tabs) && upload(b, b->sw, sw) && upload(b, b->ctl, ctls) &&
                     upload(b, b->swi, all_items);
@@ -1190,6 +1200,15 @@ pamc_status rebuild(pamc_batch b) {
                 off += items.size();
                 nl += 1;
             }
+    for (int el = 0; el < 2 && e == cudaSuccess; ++el)
+        for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+            const auto &items = pswi[el][c];
+            if (items.empty()) continue;
+            e = launch_sweep_potts_batched(el != 0, (const SweepDesc *)b->sw.p, (const int2 *)b->swi.p + off,
+                                           (int32_t)items.size(), pnmax[c], peff[c], b->stream);
+            off += items.size();
+            nl += 1;
+        }
     if (e == cudaSuccess) e = launch_control_batched((const CtlDesc *)b->ctl.p, (int32_t)ctls.size(), b->stream);
     nl += 1;
     if (e == cudaSuccess && !sdi.empty()) {
@@ -1258,7 +1277,9 @@ pamc_status pamc_batch_create(int cuda_device, void *stream, pamc_batch *out) {
 pamc_status pamc_batch_add(pamc_batch b, pamc_handle h) {
     if (!b || !h) return bfail(b, PAMC_ERR_ARG, "null batch or handle");
     if (!h->initialized) return bfail(b, PAMC_ERR_STATE, "handle not initialised (pamc_init)");
-    if (h->dense || h->p.kind != 0) return bfail(b, PAMC_ERR_ARG, "batches hold sparse Max-Cut (Ising) instances");
+    if (h->dense) return bfail(b, PAMC_ERR_ARG, "batches hold sparse instances");
+    if (h->p.kind == 1 && h->p.rule != 0)
+        return bfail(b, PAMC_ERR_ARG, "batched Max-3-Cut members use the cascaded sampler (rule 0)");
     if (h->p.stagnation || (h->p.z_rst > 0 && h->p.restart_reinit))
         return bfail(b, PAMC_ERR_ARG, "batched members run without NCM and without restart re-initialisation");
     if (h->device != b->device) return bfail(b, PAMC_ERR_ARG, "handle on another device");

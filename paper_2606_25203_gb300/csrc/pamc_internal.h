@@ -72,6 +72,7 @@ struct SweepDesc {
     int64_t *en[2];
     int32_t slots, t_end;
     int32_t push;   // push-model sweep (H <= 63, ELL, one lane per vertex, S >= 1)
+    int64_t Wsum;   // Potts: sum_{i<j} w_ij (E = -sum_k syn_sigma_k(k) - W)
 };
 
 struct SchedDesc {
@@ -104,6 +105,7 @@ struct TabDesc {
     const DevCtl *ctl;
     uint64_t *tab;
     int32_t rule, H, t_end;
+    int32_t kind;   // 0 Ising (2H+1 thresholds), 1 Potts cascaded (T1 over (4H+1)^2, then T2)
 };
 
 struct CtlDesc {
@@ -170,6 +172,9 @@ cudaError_t launch_control_batched(const CtlDesc *descs, int32_t ninst, cudaStre
 size_t prep_smem_bytes(int32_t R);
 cudaError_t launch_sweep_ising_batched(int rule, bool ell, const SweepDesc *descs, const int2 *items,
                                        int32_t nitems, int32_t n_max, SweepCfg cfg, cudaStream_t st);
+// Batched three-state Potts sweeps (cascaded sampler), one launch per (ELL, size class).
+cudaError_t launch_sweep_potts_batched(bool ell, const SweepDesc *descs, const int2 *items, int32_t nitems,
+                                       int32_t n_max, SweepCfg cfg, cudaStream_t st);
 cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uint32_t *adj,
                                int32_t H, const pamc_params &p, int32_t t, int32_t slot,
                                SchedView sv, const uint64_t *tab, const int8_t *src,

@@ -32,10 +32,34 @@ __device__ __forceinline__ void tables_ising_body(int rule, int32_t H, const Dev
     }
 }
 
+// Batched tables: kTabBlocks CTAs per member.  Ising: the 2H+1 thresholds;
+// Potts (cascaded sampler): T1 over (a, b) in [-2H, 2H]^2, then T2 over c, the
+// same values as the single-instance kernel below.
+constexpr int kTabBlocks = 8;
+
 __global__ void k_tables_batched(const TabDesc *__restrict__ descs) {
-    const TabDesc d = descs[blockIdx.x];
-    if (d.ctl->t >= d.t_end) return;
-    tables_ising_body(d.rule, d.H, d.ctl, d.tab, 0, 1);
+    __shared__ double e_s[4 * 127 + 1];
+    const TabDesc d = descs[blockIdx.x / kTabBlocks];
+    const int part = blockIdx.x % kTabBlocks;
+    if (d.ctl->t >= d.t_end || d.ctl->done) return;
+    if (d.kind == 0) {
+        tables_ising_body(d.rule, d.H, d.ctl, d.tab, part, kTabBlocks);
+        return;
+    }
+    const double beta = d.ctl->beta;
+    const int32_t H = d.H, W1 = 4 * H + 1;
+    for (int32_t i = threadIdx.x; i < W1; i += blockDim.x)
+        e_s[i] = det_exp(__dmul_rn(beta, (double)(i - 2 * H)));
+    __syncthreads();
+    const int32_t total = W1 * W1 + W1;
+    for (int32_t i = part * blockDim.x + threadIdx.x; i < total; i += kTabBlocks * blockDim.x) {
+        if (i < W1 * W1) {
+            d.tab[i] = thr_potts_b1_from(e_s[i / W1], e_s[i % W1]);
+        } else {
+            const int32_t c = i - W1 * W1;
+            d.tab[i] = thr_potts_b2(beta, (int64_t)(c - 2 * H));
+        }
+    }
 }
 
 // Softmax Potts: e(d) = (float) exp(-beta d) for d = max_m syn_m - syn_c in [0, 2H].
@@ -644,7 +668,7 @@ cudaError_t launch_population_batched(const PrepDesc *prep, const TabDesc *tabs,
     cudaError_t err = allow_dynamic_smem(k_prep_batched, smem);
     if (err != cudaSuccess) return err;
     k_prep_batched<<<ninst, kPrepThreads, smem, st>>>(prep);
-    k_tables_batched<<<ninst, 256, 0, st>>>(tabs);
+    k_tables_batched<<<ninst * kTabBlocks, 256, 0, st>>>(tabs);
     return cudaGetLastError();
 }
 

@@ -32,15 +32,18 @@ __device__ __forceinline__ uint2 onehot(uint32_t labels) {
     return make_uint2(__vcmpeq4(labels, 0u) & 0x01010101u, __vcmpeq4(labels, 0x01010101u) & 0x01010101u);
 }
 
+// The sweeps of one CTA's replica groups (groups bid*gpc .. bid*gpc+gpc-1 of
+// the instance), shared by the single-instance and the batched kernels.
 template <bool ELLP>
-__global__ void __launch_bounds__(1024)
-k_sweep_potts(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
-              int32_t H, int32_t R, int32_t S, uint32_t key0, uint32_t key1, int32_t t, int32_t slot,
-              const int32_t *__restrict__ sorder, const int32_t *__restrict__ slvl,
-              const int32_t *__restrict__ snlev, const uint32_t *__restrict__ sell,
-              const int2 *__restrict__ spos, int32_t W, const uint64_t *__restrict__ tab,
-              const int8_t *__restrict__ src, const int32_t *__restrict__ parent, int8_t *__restrict__ dst,
-              int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg) {
+__device__ __forceinline__ void
+potts_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
+           int32_t H, int32_t R, int32_t S, uint32_t key0, uint32_t key1, int32_t t, int32_t slot,
+           const int32_t *__restrict__ sorder, const int32_t *__restrict__ slvl,
+           const int32_t *__restrict__ snlev, const uint32_t *__restrict__ sell,
+           const int2 *__restrict__ spos, int32_t W, const uint64_t *__restrict__ tab,
+           const int8_t *__restrict__ src, const int32_t *__restrict__ parent, int8_t *__restrict__ dst,
+           int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg,
+           int32_t bid) {
     extern __shared__ __align__(16) uint8_t smem[];
     if (ctl->done) return;
     const int32_t W1 = 4 * H + 1;
@@ -52,7 +55,7 @@ k_sweep_potts(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const ui
     for (int i = threadIdx.x; i < gpc * 4; i += blockDim.x) red[i] = 0ull;
 
     const int gl = threadIdx.x / tpg, li = threadIdx.x % tpg;
-    const int32_t g = blockIdx.x * gpc + gl;
+    const int32_t g = bid * gpc + gl;
     const int32_t r0 = g * 4;
     const bool active = r0 < R;
     uint2 *oh = oh_all + (size_t)gl * n_pad;
@@ -195,6 +198,36 @@ k_sweep_potts(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const ui
     if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -(long long)red[gl * 4 + li] - Wsum;
 }
 
+template <bool ELLP>
+__global__ void __launch_bounds__(1024)
+k_sweep_potts(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
+              int32_t H, int32_t R, int32_t S, uint32_t key0, uint32_t key1, int32_t t, int32_t slot,
+              const int32_t *__restrict__ sorder, const int32_t *__restrict__ slvl,
+              const int32_t *__restrict__ snlev, const uint32_t *__restrict__ sell,
+              const int2 *__restrict__ spos, int32_t W, const uint64_t *__restrict__ tab,
+              const int8_t *__restrict__ src, const int32_t *__restrict__ parent, int8_t *__restrict__ dst,
+              int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg) {
+    potts_body<ELLP>(n, n_pad, rp, adj, H, R, S, key0, key1, t, slot, sorder, slvl, snlev, sell, spos, W, tab, src,
+                     parent, dst, E_dst, ctl, Wsum, gpc, tpg, blockIdx.x);
+}
+
+// Many Max-3-Cut instances in one launch: CTA b works on instance items[b].x,
+// its local block items[b].y; the member's step index comes from its device
+// controller (ctl->t), which picks the double-buffered labels and energies
+// and the schedule slot; steps at or past t_end do nothing.
+template <bool ELLP>
+__global__ void __launch_bounds__(1024)
+k_sweep_potts_batched(const SweepDesc *__restrict__ descs, const int2 *__restrict__ items, int gpc, int tpg) {
+    const int2 it = items[blockIdx.x];
+    const SweepDesc &d = descs[it.x];
+    const DevCtl *ctl = d.ctl;
+    const int32_t t = ctl->t;
+    if (t >= d.t_end) return;
+    potts_body<ELLP>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, d.K.k0[0], d.K.k1[0], t, t % d.slots, d.sorder,
+                     d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.sp[(t + 1) & 1],
+                     d.en[(t + 1) & 1], ctl, d.Wsum, gpc, tpg, it.y);
+}
+
 }  // namespace
 
 size_t sweep_potts_smem_bytes(int32_t n, int32_t H, SweepCfg cfg) {
@@ -226,6 +259,28 @@ cudaError_t launch_sweep_potts(int32_t n, const int32_t *rp, const uint32_t *adj
     if (ell) PAMC_POTTS(true);
     else PAMC_POTTS(false);
 #undef PAMC_POTTS
+    return cudaGetLastError();
+}
+
+}  // namespace pamc
+
+namespace pamc {
+
+cudaError_t launch_sweep_potts_batched(bool ell, const SweepDesc *descs, const int2 *items, int32_t nitems,
+                                       int32_t n_max, SweepCfg cfg, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
+    const size_t smem = sweep_potts_smem_bytes(n_max, 127, cfg);
+    cudaError_t err;
+    if (ell) {
+        err = allow_dynamic_smem(k_sweep_potts_batched<true>, smem);
+        if (err != cudaSuccess) return err;
+        k_sweep_potts_batched<true><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg);
+    } else {
+        err = allow_dynamic_smem(k_sweep_potts_batched<false>, smem);
+        if (err != cudaSuccess) return err;
+        k_sweep_potts_batched<false><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg);
+    }
     return cudaGetLastError();
 }
 

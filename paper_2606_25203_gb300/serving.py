@@ -1,6 +1,7 @@
 """Continuous-batching request loop over the batch entry points of libpamc.
 
-Requests (a Max-Cut CSR instance, run parameters and an arrival time) are
+Requests (a CSR instance, the problem -- Max-Cut, or Max-3-Cut with the
+cascaded three-state sampler -- and an arrival time; run parameters shared) are
 admitted while their device footprint (``pamc_footprint``: the instance, the
 two spin buffers, energies, parents, counts and the schedule ring) fits the
 HBM budget and a slot is free.  Every admitted population stays resident on
@@ -26,6 +27,12 @@ from . import (pamc_batch_active, pamc_batch_add, pamc_batch_create, pamc_batch_
                pamc_batch_graph_builds, pamc_batch_launch_count, pamc_batch_retire, pamc_batch_step,
                pamc_best, pamc_create_csr, pamc_destroy, pamc_footprint, pamc_init, pamc_launch_count,
                pamc_run)
+
+
+def request_params(params: dict, req) -> dict:
+    """The run parameters of one request: the shared ones and its problem kind
+    (0 Max-Cut, 1 Max-3-Cut; requests without a kind are Max-Cut)."""
+    return dict(params, kind=int(getattr(req, "kind", 0)))
 
 
 @dataclass
@@ -125,11 +132,11 @@ class Server:
                     req = pending.popleft()
                     h = pamc_create_csr(req.inst.n, req.inst.row_ptr, req.inst.col, req.inst.w,
                                         self.device, self.admit_stream.cuda_stream)
-                    staged = (req, h, pamc_footprint(h, **params))
+                    staged = (req, h, pamc_footprint(h, **request_params(params, req)))
                 req, h, fp = staged
                 if active and used + fp > self.hbm_budget:
                     break          # wait for a retirement
-                pamc_init(h, **params)
+                pamc_init(h, **request_params(params, req))
                 pamc_batch_add(self.batch, h)
                 active[h.value] = (req, h, fp, clock() - t0)
                 used += fp
@@ -182,7 +189,7 @@ def serve_sequential(requests, params: dict, device: int = 0, keep_spins: bool =
         h = pamc_create_csr(req.inst.n, req.inst.row_ptr, req.inst.col, req.inst.w, device,
                             stream.cuda_stream)
         try:
-            pamc_run(h, **params)
+            pamc_run(h, **request_params(params, req))
             cut, spins = pamc_best(h, req.inst.n)
             stats.launches += pamc_launch_count(h)
         finally:

@@ -187,6 +187,46 @@ def test_finished_member_is_frozen_and_target_stop(pg):
         pg.pamc_batch_destroy(b)
 
 
+def test_batch_max_cut_and_max3cut_members(pg):
+    """Max-3-Cut members (three-state Potts, cascaded sampler) share batches
+    with Max-Cut members: every member of every size class, ELL or CSR
+    schedules, ragged R, equals its run alone after every few steps, and a
+    Potts member equals the oracle."""
+    cases = [
+        (W.gnm(700, 4200, signed=False, seed=21), dict(kind=1, R=24, sweeps=2, steps=15, seed=31)),
+        (W.torus(40, 40, signed=True, seed=22), dict(kind=0, R=32, sweeps=2, steps=12, seed=32)),
+        (W.er_avg_degree(3000, 12, signed=True, seed=23), dict(kind=1, R=18, sweeps=1, steps=14, seed=33,
+                                                               z_rst=6, restart_reinit=0)),
+        (W.er_avg_degree(9500, 8, signed=False, seed=24), dict(kind=1, R=12, sweeps=2, steps=9, seed=34)),
+        (W.gnm(400, 700, signed=True, seed=25), dict(kind=0, R=20, sweeps=3, steps=16, rule=1, seed=35)),
+    ]
+    ref = [alone(pg, inst, p) for inst, p in cases]
+    inst0, p0 = cases[0]
+    orc = oracle.OracleRun(inst0.row_ptr, inst0.col, inst0.w, **p0)
+    orc.step(p0["steps"])
+    b = pg.pamc_batch_create(0)
+    hs = []
+    try:
+        for inst, p in cases:
+            h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+            pg.pamc_init(h, **p)
+            pg.pamc_batch_add(b, h)
+            hs.append(h)
+        while pg.pamc_batch_active(b) > 0:
+            pg.pamc_batch_step(b, 4)
+        pg.pamc_batch_sync(b)
+        for (inst, p), h, r in zip(cases, hs, ref):
+            assert_same(snapshot(pg, h, inst.n, p["R"]), r, inst.name)
+        spins, E, _, _ = pg.pamc_state(hs[0], p0["R"], inst0.n)
+        np.testing.assert_array_equal(spins, orc.spins())
+        np.testing.assert_array_equal(E, orc.energy())
+        assert pg.pamc_best(hs[0], inst0.n)[0] == orc.best()[0]
+    finally:
+        pg.pamc_batch_destroy(b)
+        for h in hs:
+            pg.pamc_destroy(h)
+
+
 def test_batch_refusals(pg):
     inst = W.torus(8, 8, signed=True, seed=1)
     b = pg.pamc_batch_create(0)
@@ -200,9 +240,9 @@ def test_batch_refusals(pg):
         pg.pamc_init(h, R=16, steps=5, z_rst=3, restart_reinit=1)
         with pytest.raises(pg.PamcError):
             pg.pamc_batch_add(b, h)                       # restart re-initialisation refused
-        pg.pamc_init(h, R=16, steps=5, kind=1)
+        pg.pamc_init(h, R=16, steps=5, kind=1, rule=2, K=4)
         with pytest.raises(pg.PamcError):
-            pg.pamc_batch_add(b, h)                       # Potts members are refused
+            pg.pamc_batch_add(b, h)                       # softmax Potts members are refused
         pg.pamc_init(h, R=16, steps=5)
         pg.pamc_batch_add(b, h)
         with pytest.raises(pg.PamcError):
@@ -215,7 +255,8 @@ def test_batch_refusals(pg):
 
 def test_server_equals_sequential(pg):
     from paper_2606_25203_gb300.serving import Server, serve_sequential
-    reqs = W.serving_stream(10, rate=400.0, seed=3, n_lo=300, n_hi=5000, er_degree=10.0)
+    reqs = W.serving_stream(12, rate=400.0, seed=3, n_lo=300, n_hi=5000, er_degree=10.0, max3cut_frac=0.4)
+    assert 0 < sum(r.kind for r in reqs) < len(reqs)      # Max-Cut and Max-3-Cut requests
     params = dict(R=64, sweeps=2, steps=24, beta0=0.1, beta1=3.0, seed=17)
     seq = serve_sequential(reqs, params, keep_spins=True)
     # a small budget forces admission to wait for retirements

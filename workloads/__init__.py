@@ -223,19 +223,24 @@ def er_avg_degree(n: int, avg_deg: float, signed: bool = False, seed: int = 0) -
 
 @dataclass
 class Request:
-    """One solve request of a serving stream: an instance and its arrival time (s)."""
+    """One solve request of a serving stream: an instance, its arrival time (s)
+    and the problem asked: 0 Max-Cut, 1 Max-3-Cut."""
     rid: int
     inst: Instance
     arrival: float
+    kind: int = 0
 
 
 def serving_stream(count: int, rate: float, seed: int = 0, n_lo: int = 800, n_hi: int = 20000,
-                   er_degree: float = 20.0) -> list:
-    """Max-Cut requests with Poisson arrivals (exponential gaps, mean 1/rate s),
-    N uniform in [n_lo, n_hi], the graph type cycling through Erdos-Renyi with
-    unit weights, Erdos-Renyi with +-1 weights and a +-1 torus (side
-    round(sqrt(N)), so N becomes side^2).  Erdos-Renyi requests have average
-    degree er_degree (the G22-G31 / G43-G47 density class)."""
+                   er_degree: float = 20.0, max3cut_frac: float = 0.0) -> list:
+    """Solve requests with Poisson arrivals (exponential gaps, mean 1/rate s),
+    N uniform in [n_lo, n_hi], the graph type drawn from Erdos-Renyi with unit
+    weights, Erdos-Renyi with +-1 weights and a +-1 torus (side round(sqrt(N)),
+    so N becomes side^2).  Erdos-Renyi requests have average degree er_degree
+    (the G22-G31 / G43-G47 density class).  A fraction max3cut_frac of the
+    requests (drawn from a stream of its own, so the instances do not depend
+    on it) asks for Max-3-Cut, the others for Max-Cut."""
+    kinds3 = np.random.default_rng([seed, 6, count]).random(count) < max3cut_frac
     rng = np.random.default_rng([seed, 5, count])
     gaps = rng.exponential(1.0 / rate, size=count) if rate > 0 else np.zeros(count)
     arrivals = np.cumsum(gaps) - gaps[0]
@@ -252,5 +257,5 @@ def serving_stream(count: int, rate: float, seed: int = 0, n_lo: int = 800, n_hi
         else:
             side = max(3, int(round(np.sqrt(n))))
             inst = torus(side, side, signed=True, seed=s)
-        out.append(Request(i, inst, float(arrivals[i])))
+        out.append(Request(i, inst, float(arrivals[i]), 1 if kinds3[i] else 0))
     return out
