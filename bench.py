@@ -719,8 +719,8 @@ def run_serving(args):
         "clocks": clk.summary(), "gpu_launches": st.launches, "graph_builds": st.graph_builds,
         "peak_active": st.peak_active, "peak_resident_bytes": st.peak_bytes,
         "batch_shapes": {str(c): {"groups_per_cta": g, "warps_per_group": w, "lanes_per_vertex": lv,
-                                  "ms_per_step": ms}
-                         for c, (g, w, lv, ms) in shapes.items()},
+                                  "spins_in_device_memory": bool(gm), "ms_per_step": ms}
+                         for c, (g, w, lv, ms, gm) in shapes.items()},
         "autotune_s": tune_s,
         "request_generation_s": gen_s,
     }

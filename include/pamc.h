@@ -95,7 +95,10 @@ pamc_status pamc_set_allocator(pamc_alloc_fn alloc, pamc_free_fn free_fn, void *
  * HOST (row_ptr[n+1], col[nnz], w[nnz]; Algorithm 1's coupling-matrix input).
  * The arrays are validated and copied; the caller keeps ownership.
  * Limits: 1 <= n < 2^24, |w| <= 127, max_i sum_j |w_ij| <= 127 (the field
- * range held by the sweep kernels), else PAMC_ERR_RANGE.  Asymmetric input
+ * range held by the sweep kernels), else PAMC_ERR_RANGE.  Max-Cut runs keep
+ * a replica group's spin words in shared memory while they fit (4n bytes)
+ * and in device memory beyond; Max-3-Cut runs need 8n bytes of shared memory
+ * per group (pamc_init returns PAMC_ERR_RANGE beyond).  Asymmetric input
  * gives PAMC_ERR_ASYM, a self loop PAMC_ERR_DIAG.  stream is a cudaStream_t
  * (NULL = legacy default stream) on device cuda_device. */
 pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *col,
@@ -160,7 +163,9 @@ pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_
 
 /* How the sparse Ising sweeps of an initialised run keep the local fields
  * (Eq. 3): *mode = 0 pulled from the neighbours' spins at every visit over
- * the CSR rows, 1 the same over position-indexed (ELL) rows, 2 kept in
+ * the CSR rows, 1 the same over position-indexed (ELL) rows, plus 4 when the
+ * replica groups' spin words are in device memory rather than shared memory
+ * (groups too large for shared memory, or PAMC_SWEEP_GLOBAL=1), 2 kept in
  * shared memory and updated on every flip (push; chosen by the environment
  * variable PAMC_SWEEP_PUSH=1 for instances with max_i sum_j |w_ij| <= 63,
  * ELL rows, one lane per vertex, at least one sweep).  Speed only, never
@@ -274,6 +279,14 @@ pamc_status pamc_batch_get_shape(pamc_batch b, int size_class, int *groups_per_c
  * never results.  PAMC_ERR_ARG for another value or class. */
 pamc_status pamc_batch_set_lanes(pamc_batch b, int size_class, int lanes_per_vertex);
 pamc_status pamc_batch_get_lanes(pamc_batch b, int size_class, int *lanes_per_vertex);
+/* Where the batched Ising sweep of a size class keeps each replica group's
+ * spin words: 0 shared memory (default), 1 device memory (a buffer of the
+ * member's, allocated at the next pamc_batch_step; then one lane per vertex
+ * and no shared-memory limit on n or on groups per SM).  Members whose groups
+ * do not fit shared memory use device memory in any class.  Speed only,
+ * never results.  PAMC_ERR_ARG for a bad class. */
+pamc_status pamc_batch_set_placement(pamc_batch b, int size_class, int global_spins);
+pamc_status pamc_batch_get_placement(pamc_batch b, int size_class, int *global_spins);
 int32_t pamc_batch_size(pamc_batch b);      /* members, finished or not */
 int32_t pamc_batch_active(pamc_batch b);    /* members with steps left */
 int64_t pamc_batch_launch_count(pamc_batch b);  /* kernel launches enqueued */

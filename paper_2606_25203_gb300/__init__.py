@@ -27,6 +27,7 @@ __all__ = [
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
     "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_batch_set_lanes", "pamc_batch_get_lanes", "pamc_hamming", "pamc_lineage", "pamc_set_population", "pamc_fields",
     "pamc_control_history", "pamc_sweep_mode", "pamc_set_sweep_timing", "pamc_sweep_stats",
+    "pamc_batch_set_placement", "pamc_batch_get_placement",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -165,6 +166,10 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_batch_set_lanes.restype = ctypes.c_int
     L.pamc_batch_get_lanes.argtypes = [P, ctypes.c_int, P]
     L.pamc_batch_get_lanes.restype = ctypes.c_int
+    L.pamc_batch_set_placement.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    L.pamc_batch_set_placement.restype = ctypes.c_int
+    L.pamc_batch_get_placement.argtypes = [P, ctypes.c_int, P]
+    L.pamc_batch_get_placement.restype = ctypes.c_int
     L.pamc_batch_sync.argtypes = [P]
     L.pamc_batch_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     L.pamc_batch_destroy.argtypes = [P]
@@ -531,6 +536,17 @@ def pamc_batch_get_lanes(b, size_class: int) -> int:
     v = ctypes.c_int(0)
     _bcheck(_lib.pamc_batch_get_lanes(b, int(size_class), ctypes.byref(v)), b)
     return v.value
+
+
+def pamc_batch_set_placement(b, size_class: int, global_spins: bool):
+    """Spin words of the class's Ising groups in device memory (True) or shared memory (False)."""
+    _bcheck(_lib.pamc_batch_set_placement(b, int(size_class), 1 if global_spins else 0), b)
+
+
+def pamc_batch_get_placement(b, size_class: int) -> bool:
+    v = ctypes.c_int(0)
+    _bcheck(_lib.pamc_batch_get_placement(b, int(size_class), ctypes.byref(v)), b)
+    return bool(v.value)
 
 
 def pamc_batch_size(b) -> int:

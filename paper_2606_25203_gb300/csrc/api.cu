@@ -84,6 +84,8 @@ struct pamc_handle_s {
     uint32_t *d_skey = nullptr;
     uint32_t *d_ell = nullptr;
     int2 *d_pos = nullptr;
+    uint32_t *d_gsp = nullptr;   // Ising: replica groups' spin words in device memory
+    bool gsp = false;            // the single-run sweeps use d_gsp (groups that do not fit on chip)
     DevCtl *d_ctl = nullptr;
     int8_t *d_best = nullptr;
     // dense instances
@@ -241,7 +243,12 @@ void release_run(pamc_handle h) {
     dev_free_all(h, h->bufs);
     h->initialized = 0;
     h->d_spins[0] = h->d_spins[1] = nullptr;
+    h->d_gsp = nullptr;
+    h->gsp = false;
 }
+
+// Words of the replica groups' spins in device memory (n_pad per group).
+size_t gsp_words(int32_t n, int32_t R) { return (size_t)((R + 3) / 4) * (size_t)((n + 3) & ~3); }
 
 // Launch shape of the sweep kernel: groups per CTA, warps per group and
 // lanes per vertex.  Ising runs on ELL schedules give each group a CTA of its
@@ -690,9 +697,22 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     h->cfg = choose_cfg(sweep_kind(p), n, R, h->H, avg_level, (double)h->nnz / std::max(n, 1), sms, h->ell_w);
-    if (sweep_smem_bytes(sweep_kind(p), n, h->H, h->cfg) > kSmemMax) {
+    // Ising groups whose spin words do not fit shared memory (or all of them
+    // with PAMC_SWEEP_GLOBAL=1) keep the words in device memory: one lane per
+    // vertex, one group per CTA
+    const char *genv = getenv("PAMC_SWEEP_GLOBAL");
+    if (p.kind == 0 && ((genv && genv[0] == '1') || sweep_smem_bytes(0, n, h->H, h->cfg) > kSmemMax)) {
+        if (!getenv("PAMC_SWEEP_CFG")) h->cfg = SweepCfg{1, 16, 1};
+        h->cfg.lanes_per_vertex = 1;
+        if (!alloc_n(h, h->d_gsp, gsp_words(n, R), h->bufs)) {
+            release_run(h);
+            return fail(h, PAMC_ERR_OOM, "device allocation of the group spin words failed");
+        }
+        h->gsp = true;
+    }
+    if (!h->gsp && sweep_smem_bytes(sweep_kind(p), n, h->H, h->cfg) > kSmemMax) {
         release_run(h);
-        return fail(h, PAMC_ERR_RANGE, "n = %d: one replica group's spins exceed shared memory", n);
+        return fail(h, PAMC_ERR_RANGE, "n = %d: one replica group's labels exceed shared memory", n);
     }
     h->host_t = 0;
     h->initialized = 1;
@@ -734,7 +754,8 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
         if (e == cudaSuccess)
             e = launch_sweep(sweep_kind(p), p.rule, n, h->d_rp, h->d_adj, h->H, p, (int32_t)t,
                              (int32_t)(t % kSchedSlots), sv, h->d_tab, src, h->d_parent,
-                             h->d_ncm_buf, h->d_ncm_idx, dst, Ed, h->d_ctl, h->cfg, h->W, h->stream);
+                             h->d_ncm_buf, h->d_ncm_idx, dst, Ed, h->d_ctl, h->cfg, h->W, h->stream,
+                             h->gsp ? h->d_gsp : nullptr);
         if (e == cudaSuccess) e = sweep_timer(h, true);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 2;
@@ -994,7 +1015,8 @@ pamc_status pamc_sweep_mode(pamc_handle h, int *mode) {
     if (!h->initialized || h->dense || h->p.kind != 0)
         return fail(h, PAMC_ERR_STATE, "no sparse Ising run initialised");
     const bool ell = h->d_ell != nullptr;
-    *mode = sweep_push_ok(h->H, h->p.sweeps, ell, h->cfg.lanes_per_vertex) ? 2 : ell ? 1 : 0;
+    if (h->gsp) *mode = (ell ? 1 : 0) | 4;
+    else *mode = sweep_push_ok(h->H, h->p.sweeps, ell, h->cfg.lanes_per_vertex) ? 2 : ell ? 1 : 0;
     return PAMC_OK;
 }
 
@@ -1036,6 +1058,7 @@ struct pamc_batch_s {
     int64_t launches = 0;
     int64_t rebuilds = 0;
     SweepCfg shape[3];            // batched sweep launch shape per size class
+    bool global[3] = {false, false, false};   // Ising members' spin words in device memory
     char err[256] = "";
 };
 
@@ -1108,18 +1131,21 @@ pamc_status rebuild(pamc_batch b) {
     std::vector<TabDesc> tabs;
     std::vector<CtlDesc> ctls;
     std::vector<SweepDesc> sw;
-    std::vector<int2> swi[2][2][kClasses];   // Ising [ell][rule][class]
+    std::vector<int2> swi[2][2][kClasses];   // Ising, spin words on chip [ell][rule][class]
+    std::vector<int2> gswi[2][2][kClasses];  // Ising, spin words in device memory
     std::vector<int2> pswi[2][kClasses];     // Potts (cascaded sampler) [ell][class]
-    int32_t nmax[kClasses] = {0, 0, 0}, pnmax[kClasses] = {0, 0, 0}, Rmax = 1;
+    int32_t nmax[kClasses] = {0, 0, 0}, pnmax[kClasses] = {0, 0, 0}, gnmax[kClasses] = {0, 0, 0}, Rmax = 1;
+    auto member_global = [&](pamc_handle h) { return h->p.kind == 0 && (h->gsp || b->global[batch_class(h->n)]); };
     for (pamc_handle h : b->members)
         if (h->host_t < h->p.steps) {
-            int32_t &m = (h->p.kind == 0 ? nmax : pnmax)[batch_class(h->n)];
+            int32_t &m = (h->p.kind != 0 ? pnmax : member_global(h) ? gnmax : nmax)[batch_class(h->n)];
             m = std::max(m, h->n);
         }
     // the shape of each class, with fewer groups per CTA where the largest
     // member's spins (Ising: 4n bytes a group, Potts: 8n) need it
-    SweepCfg eff[kClasses], peff[kClasses];
+    SweepCfg eff[kClasses], peff[kClasses], geff[kClasses];
     for (int c = 0; c < kClasses; ++c) {
+        geff[c] = SweepCfg{b->shape[c].groups_per_cta, b->shape[c].warps_per_group, 1};
         eff[c] = b->shape[c];
         while (eff[c].groups_per_cta > 1 && sweep_ising_smem_bytes(nmax[c], 127, eff[c]) > kSmemMax)
             eff[c].groups_per_cta -= 1;
@@ -1155,13 +1181,18 @@ pamc_status rebuild(pamc_batch b) {
         d.sp[0] = h->d_spins[0]; d.sp[1] = h->d_spins[1]; d.en[0] = h->d_E[0]; d.en[1] = h->d_E[1];
         d.slots = kSchedSlots; d.t_end = t_end; d.Wsum = h->W;
         const int cls = batch_class(h->n);
-        const SweepCfg cfg = p.kind == 0 ? eff[cls] : peff[cls];
-        d.push = p.kind == 0 && sweep_push_ok(h->H, p.sweeps, h->d_ell != nullptr, cfg.lanes_per_vertex) ? 1 : 0;
+        const bool gl = member_global(h);
+        if (gl && !h->d_gsp && !alloc_n(h, h->d_gsp, gsp_words(h->n, p.R), h->bufs))
+            return bfail(b, PAMC_ERR_OOM, "device allocation of a member's group spin words failed");
+        d.gsp = gl ? h->d_gsp : nullptr;
+        const SweepCfg cfg = p.kind != 0 ? peff[cls] : gl ? geff[cls] : eff[cls];
+        d.push = p.kind == 0 && !gl && sweep_push_ok(h->H, p.sweeps, h->d_ell != nullptr, cfg.lanes_per_vertex) ? 1 : 0;
         const int idx = (int)sw.size();
         sw.push_back(d);
         const int32_t ctas = ((p.R + 3) / 4 + cfg.groups_per_cta - 1) / cfg.groups_per_cta;
         // with sweeps = 0 the launch still copies the resampled population and its energies
-        auto &items = p.kind == 0 ? swi[h->d_ell != nullptr][p.rule][cls] : pswi[h->d_ell != nullptr][cls];
+        auto &items = p.kind != 0 ? pswi[h->d_ell != nullptr][cls]
+                                  : (gl ? gswi : swi)[h->d_ell != nullptr][p.rule][cls];
         for (int32_t x = 0; x < ctas; ++x) items.push_back(make_int2(idx, x));
         Rmax = std::max(Rmax, p.R);
         CtlDesc c{nullptr, nullptr, h->d_best, h->d_ctl, h->W, p.target_cut, p.reheat_factor, p.beta0,
@@ -1171,6 +1202,9 @@ pamc_status rebuild(pamc_batch b) {
     }
     std::vector<int2> all_items;
     for (auto &a : swi)
+        for (auto &c : a)
+            for (auto &v : c) all_items.insert(all_items.end(), v.begin(), v.end());
+    for (auto &a : gswi)
         for (auto &c : a)
             for (auto &v : c) all_items.insert(all_items.end(), v.begin(), v.end());
     for (auto &a : pswi)
@@ -1197,6 +1231,16 @@ pamc_status rebuild(pamc_batch b) {
                 if (items.empty()) continue;
                 e = launch_sweep_ising_batched(ru, el != 0, (const SweepDesc *)b->sw.p, (const int2 *)b->swi.p + off,
                                                (int32_t)items.size(), nmax[c], eff[c], b->stream);
+                off += items.size();
+                nl += 1;
+            }
+    for (int el = 0; el < 2 && e == cudaSuccess; ++el)
+        for (int ru = 0; ru < 2 && e == cudaSuccess; ++ru)
+            for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+                const auto &items = gswi[el][ru][c];
+                if (items.empty()) continue;
+                e = launch_sweep_ising_batched(ru, el != 0, (const SweepDesc *)b->sw.p, (const int2 *)b->swi.p + off,
+                                               (int32_t)items.size(), gnmax[c], geff[c], b->stream, true);
                 off += items.size();
                 nl += 1;
             }
@@ -1251,6 +1295,8 @@ size_t pamc_footprint(pamc_handle h, const pamc_params *p) {
     b += (size_t)(p->kind == 0 ? 2 * h->H + 1 : (4 * h->H + 1) * (4 * h->H + 1) + 4 * h->H + 1) * 8;
     if (p->stagnation && p->kind == 0) b += 5 * (size_t)std::min(p->n_top > 0 ? p->n_top : std::max(1, p->R / 16), p->R) * n;
     b += ((size_t)h->n + 1) * 4 + (size_t)std::max(h->nnz, 1) * 4;   // the instance itself
+    // Ising groups whose spin words do not fit shared memory keep them in device memory
+    if (p->kind == 0 && sweep_ising_smem_bytes(n, 127, SweepCfg{1, 1, 1}) > kSmemMax) b += gsp_words(n, p->R) * 4;
     return b + sizeof(DevCtl);
 }
 
@@ -1370,6 +1416,20 @@ pamc_status pamc_batch_set_lanes(pamc_batch b, int size_class, int lanes_per_ver
     if (!batch_lanes_ok(lanes_per_vertex)) return bfail(b, PAMC_ERR_ARG, "lanes per vertex must be 1, 2 or 4");
     b->shape[size_class].lanes_per_vertex = lanes_per_vertex;
     b->dirty = true;
+    return PAMC_OK;
+}
+
+pamc_status pamc_batch_set_placement(pamc_batch b, int size_class, int global_spins) {
+    if (!b || size_class < 0 || size_class >= kClasses) return bfail(b, PAMC_ERR_ARG, "bad batch or size class");
+    b->global[size_class] = global_spins != 0;
+    b->dirty = true;
+    return PAMC_OK;
+}
+
+pamc_status pamc_batch_get_placement(pamc_batch b, int size_class, int *global_spins) {
+    if (!b || !global_spins || size_class < 0 || size_class >= kClasses)
+        return bfail(b, PAMC_ERR_ARG, "bad batch, size class or null argument");
+    *global_spins = b->global[size_class] ? 1 : 0;
     return PAMC_OK;
 }
 

@@ -73,6 +73,7 @@ struct SweepDesc {
     int32_t slots, t_end;
     int32_t push;   // push-model sweep (H <= 63, ELL, one lane per vertex, S >= 1)
     int64_t Wsum;   // Potts: sum_{i<j} w_ij (E = -sum_k syn_sigma_k(k) - W)
+    uint32_t *gsp;  // Ising: the groups' spin words in device memory (n_pad words a group), or nullptr
 };
 
 struct SchedDesc {
@@ -158,7 +159,9 @@ void launch_schedule(int32_t n, const int32_t *rp, const uint32_t *adj, uint64_t
                      cudaStream_t st, uint32_t *ell = nullptr, int32_t W = 0,
                      int2 *pos = nullptr);
 
-size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
+// Dynamic shared memory of the Ising sweep; with global_spins the groups'
+// spin words live in device memory instead (see SweepDesc::gsp).
+size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg, bool global_spins = false);
 // Push-model Ising sweeps (fields kept in shared memory, updated on flips):
 // used where H <= 63, on ELL schedules with one lane per vertex and S >= 1,
 // when the environment variable PAMC_SWEEP_PUSH is "1".
@@ -171,7 +174,8 @@ cudaError_t launch_population_batched(const PrepDesc *prep, const TabDesc *tabs,
 cudaError_t launch_control_batched(const CtlDesc *descs, int32_t ninst, cudaStream_t st);
 size_t prep_smem_bytes(int32_t R);
 cudaError_t launch_sweep_ising_batched(int rule, bool ell, const SweepDesc *descs, const int2 *items,
-                                       int32_t nitems, int32_t n_max, SweepCfg cfg, cudaStream_t st);
+                                       int32_t nitems, int32_t n_max, SweepCfg cfg, cudaStream_t st,
+                                       bool global_spins = false);
 // Batched three-state Potts sweeps (cascaded sampler), one launch per (ELL, size class).
 cudaError_t launch_sweep_potts_batched(bool ell, const SweepDesc *descs, const int2 *items, int32_t nitems,
                                        int32_t n_max, SweepCfg cfg, cudaStream_t st);
@@ -180,7 +184,7 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
                                SchedView sv, const uint64_t *tab, const int8_t *src,
                                const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
-                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st);
+                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp = nullptr);
 
 // Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax;
 // every kind keeps groups of four replicas.
@@ -202,7 +206,7 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
                          const uint64_t *tab, const int8_t *src, const int32_t *parent,
                          const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst,
                          int64_t *E_dst, const DevCtl *ctl, SweepCfg cfg, int64_t Wsum,
-                         cudaStream_t st);
+                         cudaStream_t st, uint32_t *gsp = nullptr);
 
 // Random (re)initialisation of the population with key t, and its energies;
 // when only_if_restart is set the kernels do nothing unless the controller

@@ -279,7 +279,7 @@ sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
 // the coupling slots sub, sub + LPV, ...; the byte-lane partial sums add up
 // exactly under XOR shuffles (plain 32-bit addition), and every lane of the
 // group runs the same iterations so that the shuffles always converge.
-template <bool ELLP, int RULE, int LPV, class KeyT>
+template <bool ELLP, int RULE, int LPV, class KeyT, bool GSP = false>
 __device__ __forceinline__ void
 sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                  const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, const KeyT &draw,
@@ -290,13 +290,16 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                  const int32_t *__restrict__ parent, const int8_t *__restrict__ ncm_buf,
                  const int32_t *__restrict__ ncm_idx, int8_t *__restrict__ dst,
                  int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int gpc, int tpg,
-                 int32_t bid) {
+                 int32_t bid, uint32_t *__restrict__ gspins = nullptr) {
     extern __shared__ __align__(16) uint8_t smem[];
     if (ctl->done) return;
     const int tabn = 2 * H + 1;
     uint64_t *tab_s = reinterpret_cast<uint64_t *>(smem);
+    // the groups' spin words: shared memory, or (GSP) the caller's device
+    // buffer of n_pad words per group, for groups that do not fit on chip or
+    // where more groups per SM pay; the level barriers order both alike
     uint32_t *spins_all = reinterpret_cast<uint32_t *>(smem + (((size_t)tabn * 8 + 15) & ~(size_t)15));
-    unsigned long long *red = reinterpret_cast<unsigned long long *>(spins_all + (size_t)gpc * n_pad);
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(spins_all + (GSP ? 0 : (size_t)gpc * n_pad));
     for (int i = threadIdx.x; i < tabn; i += blockDim.x) tab_s[i] = tab[i];
     for (int i = threadIdx.x; i < gpc * 4; i += blockDim.x) red[i] = 0ull;
 
@@ -304,7 +307,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     const int32_t g = bid * gpc + gl;
     const int32_t r0 = g * 4;
     const bool active = r0 < R;
-    uint32_t *sp = spins_all + (size_t)gl * n_pad;
+    uint32_t *sp = GSP ? gspins + (size_t)g * n_pad : spins_all + (size_t)gl * n_pad;
 
     if (active) {
         // slot r reads the NCM output if the cluster move rewrote it, else
@@ -594,11 +597,12 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 4 + li] / 2);
 }
 
-template <bool ELLP, int RULE, int LPV>
+template <bool ELLP, int RULE, int LPV, bool GSP = false>
 __global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int tpg) {
-    sweep_ising_body<ELLP, RULE, LPV>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t, d.slot, d.sorder,
-                                 d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf,
-                                 d.ncm_idx, d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x);
+    sweep_ising_body<ELLP, RULE, LPV, KeysPre, GSP>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t,
+                                                    d.slot, d.sorder, d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab,
+                                                    d.src, d.parent, d.ncm_buf, d.ncm_idx, d.dst, d.E_dst, d.ctl, gpc,
+                                                    tpg, blockIdx.x, d.gsp);
 }
 
 template <int RULE>
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_push(SweepDesc d, int gpc,
 // local block items[b].y.  Descriptors live in device memory and are read
 // field by field (no local copy of the descriptor).  LPV > 1: lanes per
 // vertex, as for one instance (ELL schedules only).
-template <bool ELLP, int RULE, int LPV>
+template <bool ELLP, int RULE, int LPV, bool GSP = false>
 __global__ void __launch_bounds__(1024)
 k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restrict__ items, int gpc, int tpg) {
     const int2 it = items[blockIdx.x];
@@ -621,7 +625,7 @@ k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restric
     const int32_t t = ctl->t;
     if (t >= d.t_end) return;
     const KeysSeed draw{d.K.k0[0], d.K.k1[0]};
-    if constexpr (ELLP && LPV == 1) {
+    if constexpr (ELLP && LPV == 1 && !GSP) {
         if (d.push) {   // uniform over the CTA: one member per CTA
             sweep_ising_push_body<RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.slvl,
                                         d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.ncm_buf,
@@ -629,9 +633,10 @@ k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restric
             return;
         }
     }
-    sweep_ising_body<ELLP, RULE, LPV>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.sorder,
-                                 d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.ncm_buf,
-                                 d.ncm_idx, d.sp[(t + 1) & 1], d.en[(t + 1) & 1], ctl, gpc, tpg, it.y);
+    sweep_ising_body<ELLP, RULE, LPV, KeysSeed, GSP>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots,
+                                                     d.sorder, d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab,
+                                                     d.sp[t & 1], d.parent, d.ncm_buf, d.ncm_idx, d.sp[(t + 1) & 1],
+                                                     d.en[(t + 1) & 1], ctl, gpc, tpg, it.y, d.gsp);
 }
 
 }  // namespace
@@ -648,10 +653,10 @@ bool sweep_push_ok(int32_t H, int32_t S, bool ell, int lanes_per_vertex) {
     return ell && lanes_per_vertex == 1 && H <= 63 && S > 0 && sweep_push_enabled();
 }
 
-size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg) {
+size_t sweep_ising_smem_bytes(int32_t n, int32_t H, SweepCfg cfg, bool global_spins) {
     const int32_t n_pad = (n + 3) & ~3;
-    return (((size_t)(2 * H + 1) * 8 + 15) & ~(size_t)15) + (size_t)cfg.groups_per_cta * n_pad * 4 +
-           (size_t)cfg.groups_per_cta * 4 * 8;
+    return (((size_t)(2 * H + 1) * 8 + 15) & ~(size_t)15) +
+           (global_spins ? 0 : (size_t)cfg.groups_per_cta * n_pad * 4) + (size_t)cfg.groups_per_cta * 4 * 8;
 }
 
 cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uint32_t *adj,
@@ -659,7 +664,7 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
                                SchedView sv, const uint64_t *tab, const int8_t *src,
                                const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
-                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st) {
+                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp) {
     const int32_t groups = (p.R + 3) / 4;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
     SweepDesc d;
@@ -667,7 +672,8 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
     d.spos = sv.pos; d.tab = tab; d.src = src; d.parent = parent; d.ncm_buf = ncm_buf; d.ncm_idx = ncm_idx;
     d.dst = dst; d.E_dst = E_dst; d.ctl = ctl; d.n = n; d.n_pad = (n + 3) & ~3; d.H = H; d.R = p.R;
     d.S = p.sweeps; d.t = t; d.slot = slot; d.W = sv.W; d.K = make_philox_keys(p.seed);
-    const size_t smem = sweep_ising_smem_bytes(n, H, cfg);
+    d.gsp = gsp;
+    const size_t smem = sweep_ising_smem_bytes(n, H, cfg, gsp != nullptr);
     const int grid = (groups + gpc - 1) / gpc;
     const bool ell = sv.ell != nullptr;
     cudaError_t err = cudaSuccess;
@@ -676,6 +682,12 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
         err = allow_dynamic_smem(k_sweep_ising<EL, RU, LV>, smem);                                \
         if (err != cudaSuccess) return err;                                                       \
         k_sweep_ising<EL, RU, LV><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);                    \
+    } while (0)
+#define PAMC_LAUNCH_G(EL, RU)                                                                     \
+    do {                                                                                          \
+        err = allow_dynamic_smem(k_sweep_ising<EL, RU, 1, true>, smem);                           \
+        if (err != cudaSuccess) return err;                                                       \
+        k_sweep_ising<EL, RU, 1, true><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);               \
     } while (0)
 #define PAMC_LAUNCH_LPV(RU)                                                                       \
     do {                                                                                          \
@@ -689,6 +701,14 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
         }                                                                                         \
     } while (0)
     const int lpv = ell ? cfg.lanes_per_vertex : 1;
+    if (gsp) {   // spin words in device memory: one lane per vertex
+        if (ell) {
+            if (rule == 0) PAMC_LAUNCH_G(true, 0); else PAMC_LAUNCH_G(true, 1);
+        } else {
+            if (rule == 0) PAMC_LAUNCH_G(false, 0); else PAMC_LAUNCH_G(false, 1);
+        }
+        return cudaGetLastError();
+    }
     d.push = sweep_push_ok(H, p.sweeps, ell, lpv) ? 1 : 0;
     if (d.push) {
         if (rule == 0) {
@@ -708,16 +728,33 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
         if (rule == 0) PAMC_LAUNCH(false, 0, 1); else PAMC_LAUNCH(false, 1, 1);
     }
 #undef PAMC_LAUNCH_LPV
+#undef PAMC_LAUNCH_G
 #undef PAMC_LAUNCH
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_ising_batched(int rule, bool ell, const SweepDesc *descs, const int2 *items,
-                                       int32_t nitems, int32_t n_max, SweepCfg cfg, cudaStream_t st) {
+                                       int32_t nitems, int32_t n_max, SweepCfg cfg, cudaStream_t st,
+                                       bool global_spins) {
     if (nitems <= 0) return cudaSuccess;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
-    const size_t smem = sweep_ising_smem_bytes(n_max, 127, cfg);
+    const size_t smem = sweep_ising_smem_bytes(n_max, 127, cfg, global_spins);
     cudaError_t err = cudaSuccess;
+    if (global_spins) {   // one lane per vertex
+#define PAMC_LAUNCH_BG(EL, RU)                                                                        \
+    do {                                                                                              \
+        err = allow_dynamic_smem(k_sweep_ising_batched<EL, RU, 1, true>, smem);                       \
+        if (err != cudaSuccess) return err;                                                           \
+        k_sweep_ising_batched<EL, RU, 1, true><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg); \
+    } while (0)
+        if (ell) {
+            if (rule == 0) PAMC_LAUNCH_BG(true, 0); else PAMC_LAUNCH_BG(true, 1);
+        } else {
+            if (rule == 0) PAMC_LAUNCH_BG(false, 0); else PAMC_LAUNCH_BG(false, 1);
+        }
+#undef PAMC_LAUNCH_BG
+        return cudaGetLastError();
+    }
 #define PAMC_LAUNCH(EL, RU, LV)                                                                   \
     do {                                                                                          \
         err = allow_dynamic_smem(k_sweep_ising_batched<EL, RU, LV>, smem);                        \

@@ -3,30 +3,35 @@
 For every size class (``pamc_size_class``: n <= 2048, <= 8192, larger) that the
 sample instances cover, the samples of that class are loaded into a throwaway
 batch and each candidate shape -- replica groups (of four replicas) per CTA,
-warps per group and lanes per vertex -- is timed with CUDA events over a few
-batch steps; the fastest one is set on the caller's batch.  A shape changes
-speed only, never results, so tuning on copies of representative instances is
-safe.
+warps per group, lanes per vertex, and where the groups' spin words live
+(shared memory, or device memory with no shared-memory limit on groups per
+SM) -- is timed with CUDA events over a few batch steps; the fastest one is
+set on the caller's batch.  A shape changes speed only, never results, so
+tuning on copies of representative instances is safe.
 """
 from __future__ import annotations
 
 from . import (pamc_batch_add, pamc_batch_create, pamc_batch_destroy, pamc_batch_set_lanes,
-               pamc_batch_set_shape, pamc_batch_step, pamc_create_csr, pamc_destroy, pamc_init,
-               pamc_size_class)
+               pamc_batch_set_placement, pamc_batch_set_shape, pamc_batch_step, pamc_create_csr, pamc_destroy,
+               pamc_init, pamc_size_class)
 
-# (groups per CTA, warps per group, lanes per vertex); several lanes per vertex
-# only pay off with wide groups
-CANDIDATES = (tuple((g, w, 1) for g in (1, 2, 4, 8) for w in (1, 2, 4, 8, 16) if g * w <= 32) +
-              tuple((g, w, l) for g in (1, 2) for w in (4, 8, 16, 32) for l in (2, 4) if g * w <= 32))
+# (groups per CTA, warps per group, lanes per vertex, spin words in device
+# memory); several lanes per vertex only pay off with wide groups, and device
+# memory only with one lane per vertex
+CANDIDATES = (tuple((g, w, 1, 0) for g in (1, 2, 4, 8) for w in (1, 2, 4, 8, 16) if g * w <= 32) +
+              tuple((g, w, l, 0) for g in (1, 2) for w in (4, 8, 16, 32) for l in (2, 4) if g * w <= 32) +
+              tuple((g, w, 1, 1) for g in (1, 2, 4) for w in (4, 8, 16) if g * w <= 32))
 
 
 def tune_batch_shapes(batch, samples, params: dict, steps: int = 3, rounds: int = 2, device: int = 0,
                       candidates=CANDIDATES) -> dict:
     """samples: instances with ``n``, ``row_ptr``, ``col``, ``w`` (numpy CSR).
     params: run parameters of the served requests (R, sweeps, rule, ...).
-    candidates: (groups, warps) or (groups, warps, lanes) tuples.
-    Returns {size_class: (groups_per_cta, warps_per_group, lanes_per_vertex, ms_per_step)}."""
-    candidates = tuple(tuple(c) + (1,) * (3 - len(c)) for c in candidates)
+    candidates: (groups, warps), (groups, warps, lanes) or (groups, warps,
+    lanes, device-memory spin words) tuples.
+    Returns {size_class: (groups_per_cta, warps_per_group, lanes_per_vertex,
+    ms_per_step, device_memory_spins)}."""
+    candidates = tuple(tuple(c) + (1, 0)[len(c) - 2:] if len(c) < 4 else tuple(c) for c in candidates)
     import torch
     by_class = {}
     for inst in samples:
@@ -47,9 +52,10 @@ def tune_batch_shapes(batch, samples, params: dict, steps: int = 3, rounds: int 
                 pamc_batch_add(tmp, h)
             best = {}
             for _ in range(rounds):          # candidates interleaved, best of the rounds
-                for g, w, lv in candidates:
+                for g, w, lv, gm in candidates:
                     pamc_batch_set_shape(tmp, cls, g, w)
                     pamc_batch_set_lanes(tmp, cls, lv)
+                    pamc_batch_set_placement(tmp, cls, bool(gm))
                     pamc_batch_step(tmp, 1)  # capture and warm up
                     a = torch.cuda.Event(enable_timing=True)
                     b = torch.cuda.Event(enable_timing=True)
@@ -58,11 +64,12 @@ def tune_batch_shapes(batch, samples, params: dict, steps: int = 3, rounds: int 
                     b.record(stream)
                     b.synchronize()
                     ms = a.elapsed_time(b) / steps
-                    best[(g, w, lv)] = min(ms, best.get((g, w, lv), float("inf")))
-            (g, w, lv), ms = min(best.items(), key=lambda kv: kv[1])
+                    best[(g, w, lv, gm)] = min(ms, best.get((g, w, lv, gm), float("inf")))
+            (g, w, lv, gm), ms = min(best.items(), key=lambda kv: kv[1])
             pamc_batch_set_shape(batch, cls, g, w)
             pamc_batch_set_lanes(batch, cls, lv)
-            chosen[cls] = (g, w, lv, ms)
+            pamc_batch_set_placement(batch, cls, bool(gm))
+            chosen[cls] = (g, w, lv, ms, gm)
         finally:
             pamc_batch_destroy(tmp)
             for h in hs:

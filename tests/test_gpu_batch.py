@@ -187,6 +187,37 @@ def test_finished_member_is_frozen_and_target_stop(pg):
         pg.pamc_batch_destroy(b)
 
 
+def test_batch_device_memory_placement(pg):
+    """Size classes whose Ising groups keep their spin words in device memory
+    give every member what it computes alone (placement changes speed only),
+    next to classes on chip and Potts members."""
+    cases = mix()[:5] + [(W.gnm(700, 4200, signed=False, seed=21), dict(kind=1, R=24, sweeps=2, steps=15,
+                                                                       seed=31))]
+    ref = [alone(pg, inst, p) for inst, p in cases]
+    b = pg.pamc_batch_create(0)
+    hs = []
+    try:
+        pg.pamc_batch_set_placement(b, 0, True)
+        pg.pamc_batch_set_placement(b, 2, True)
+        assert pg.pamc_batch_get_placement(b, 0) and not pg.pamc_batch_get_placement(b, 1)
+        for inst, p in cases:
+            h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+            pg.pamc_init(h, **p)
+            pg.pamc_batch_add(b, h)
+            hs.append(h)
+        pg.pamc_batch_step(b, 3)
+        pg.pamc_batch_set_placement(b, 1, True)          # a change between steps takes effect at the next
+        while pg.pamc_batch_active(b) > 0:
+            pg.pamc_batch_step(b, 4)
+        pg.pamc_batch_sync(b)
+        for (inst, p), h, r in zip(cases, hs, ref):
+            assert_same(snapshot(pg, h, inst.n, p["R"]), r, inst.name)
+    finally:
+        pg.pamc_batch_destroy(b)
+        for h in hs:
+            pg.pamc_destroy(h)
+
+
 def test_batch_max_cut_and_max3cut_members(pg):
     """Max-3-Cut members (three-state Potts, cascaded sampler) share batches
     with Max-Cut members: every member of every size class, ELL or CSR

@@ -335,3 +335,22 @@ def test_sweep_flip_count_and_timing(pg, monkeypatch, push):
     ref.step(6)
     assert st["flips"] == ref.sweep_flips() and st["launches"] == 6
     s.close()
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_group_spins_in_device_memory(pg, monkeypatch, rule):
+    """The Ising sweep with the replica groups' spin words in device memory
+    (PAMC_SWEEP_GLOBAL=1; chosen by itself when a group does not fit shared
+    memory) gives the oracle's results step after step: ELL and CSR
+    schedules, a ragged population, cluster moves and restarts."""
+    monkeypatch.setenv("PAMC_SWEEP_GLOBAL", "1")
+    cases = ((W.torus(20, 20, signed=True, seed=1), 13),
+             (W.erdos_renyi(300, 0.2, signed=True, seed=4), 10),      # ELL padding too wide: CSR rows
+             (W.gnm(500, 1400, signed=True, seed=2), 22))
+    for inst, R in cases:
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+        s.init(R=R, sweeps=2, steps=3, rule=rule, seed=4)
+        assert pg.pamc_sweep_mode(s.h) & 4, inst.name
+        s.close()
+        compare_run(pg, inst, 10, R=R, sweeps=2, beta0=0.2, beta1=3.0, rule=rule, stagnation=1, z_rst=7,
+                    cooldown_tau=1, seed=4)

@@ -258,3 +258,24 @@ def test_dense100k_whole_late_step_replay(pg):
     np.testing.assert_array_equal(S1[slots], s.astype(np.int8))
     np.testing.assert_array_equal(E1[slots], E)
     assert len(rows) > 0                                      # flips happened in the replayed step
+
+
+def test_sparse80000_device_memory_spins_replay(pg):
+    """n = 80,000 (average degree 5.7, +-1): a replica group's spin words
+    (320 KB) no longer fit shared memory, so they live in device memory.
+    Augmented PAMC at R = 64: iterations 10 -> 11 and 30 -> 31 replayed."""
+    inst = W.gnm(80000, 228000, signed=True, seed=6)
+    params = dict(R=64, sweeps=2, steps=100, beta0=0.1, beta1=4.0, stagnation=1, z_rst=0, seed=5)
+    rng = np.random.default_rng(6)
+    s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+    s.init(**params)
+    assert pg.pamc_sweep_mode(s.h) & 4
+    ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **params)
+    try:
+        s.step(10)
+        _replay_one(pg, s, ref, rng, n_random=12)
+        s.step(19)
+        _replay_one(pg, s, ref, rng, n_random=12)
+    finally:
+        s.close()
+        ref.close()

@@ -23,6 +23,7 @@ class Model:
         self.cost = cost              # (cls, g, w, lv, round) -> ms
         self.shape = {}               # (batch, cls) -> (g, w)
         self.lanes = {}               # (batch, cls) -> lv
+        self.place = {}               # (batch, cls) -> spin words in device memory
         self.members = {}             # batch -> [classes]
         self.created, self.destroyed = [], []
         self.batches = []
@@ -57,6 +58,9 @@ class Model:
     def set_lanes(self, b, cls, lv):
         self.lanes[(b, cls)] = lv
 
+    def set_placement(self, b, cls, gm):
+        self.place[(b, cls)] = bool(gm)
+
     def step(self, b, k):
         self.last = (b, k)
 
@@ -68,10 +72,11 @@ class Model:
 
 
 def test_tuner_sets_the_fastest_shape_per_class(monkeypatch):
-    # class 0 is fastest at (2, 4, 2); class 2 at (1, 16, 1); round 1 adds noise
-    def cost(cls, g, w, lv, rnd):
-        best = {0: (2, 4, 2), 2: (1, 16, 1)}[cls]
-        d = abs(g - best[0]) + abs(w - best[1]) / 4 + abs(lv - best[2])
+    # class 0 is fastest at (2, 4, 2) with spin words on chip; class 2 at
+    # (1, 16, 1) with spin words in device memory; round 1 adds noise
+    def cost(cls, g, w, lv, gm, rnd):
+        best = {0: (2, 4, 2, 0), 2: (1, 16, 1, 1)}[cls]
+        d = abs(g - best[0]) + abs(w - best[1]) / 4 + abs(lv - best[2]) + 0.3 * abs(gm - best[3])
         return 1.0 + d + (0.5 if rnd == 1 else 0.0)
 
     m = Model(cost)
@@ -93,15 +98,17 @@ def test_tuner_sets_the_fastest_shape_per_class(monkeypatch):
             cls = next(c for (bb, c) in m.shape if bb is b)
             g, w = m.shape[(b, cls)]
             lv = m.lanes[(b, cls)]
+            gm = int(m.place[(b, cls)])
             rnd = state["count"] // ncand
             state["count"] += 1
-            return cost(cls, g, w, lv, rnd % 2) * 3
+            return cost(cls, g, w, lv, gm, rnd % 2) * 3
 
     monkeypatch.setattr(torch.cuda, "Stream", lambda device=0: types.SimpleNamespace(cuda_stream=None))
     monkeypatch.setattr(torch.cuda, "Event", Event)
     for name, fn in (("pamc_size_class", m.size_class), ("pamc_batch_create", m.batch_create),
                      ("pamc_create_csr", m.create), ("pamc_init", m.init), ("pamc_batch_add", m.add),
                      ("pamc_batch_set_shape", m.set_shape), ("pamc_batch_set_lanes", m.set_lanes),
+                     ("pamc_batch_set_placement", m.set_placement),
                      ("pamc_batch_step", m.step), ("pamc_batch_destroy", m.batch_destroy),
                      ("pamc_destroy", m.destroy)):
         monkeypatch.setattr(tune, name, fn)
@@ -112,7 +119,8 @@ def test_tuner_sets_the_fastest_shape_per_class(monkeypatch):
     assert set(chosen) == {0, 2}
     assert chosen[0][:3] == (2, 4, 2) and chosen[2][:3] == (1, 16, 1)
     assert chosen[0][3] == pytest.approx(1.0) and chosen[2][3] == pytest.approx(1.0)   # best round
-    assert m.shape[(caller, 0)] == (2, 4) and m.lanes[(caller, 0)] == 2
-    assert m.shape[(caller, 2)] == (1, 16) and m.lanes[(caller, 2)] == 1
+    assert chosen[0][4] == 0 and chosen[2][4] == 1
+    assert m.shape[(caller, 0)] == (2, 4) and m.lanes[(caller, 0)] == 2 and not m.place[(caller, 0)]
+    assert m.shape[(caller, 2)] == (1, 16) and m.lanes[(caller, 2)] == 1 and m.place[(caller, 2)]
     assert (caller, 1) not in m.shape                       # no sample of class 1: untouched
     assert sorted(m.destroyed) == sorted(h for h, _ in m.created)
