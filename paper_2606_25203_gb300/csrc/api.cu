@@ -192,9 +192,9 @@ pamc_status validate_csr(int32_t n, const int32_t *rp, const int32_t *col, const
             const int32_t J = -w[e];
             adj[e] = (uint32_t)j | ((uint32_t)(uint8_t)(int8_t)J << 24);
         }
-        if (habs > 127)
-            return fail(nullptr, PAMC_ERR_RANGE, "sum_j |w_ij| = %lld > 127 at vertex %d",
-                        (long long)habs, i);
+        if (habs > kWideLaneMaxH)
+            return fail(nullptr, PAMC_ERR_RANGE, "sum_j |w_ij| = %lld > %d at vertex %d",
+                        (long long)habs, kWideLaneMaxH, i);
         H = std::max<int32_t>(H, (int32_t)habs);
         maxdeg = std::max(maxdeg, deg);
     }
@@ -522,8 +522,9 @@ pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *co
     h->H = H;
     h->maxdeg = maxdeg;
     // position-indexed ELL when its padding stays within 4x the couplings
+    // (the schedule's position record holds the degree in 8 bits)
     const int64_t ell_entries = (int64_t)((n + 31) / 32) * 32 * ((maxdeg + 3) & ~3);
-    h->ell_w = (maxdeg > 0 && ell_entries <= 4 * (int64_t)h->nnz + 4096) ? ((maxdeg + 3) & ~3) : 0;
+    h->ell_w = (maxdeg > 0 && maxdeg < 256 && ell_entries <= 4 * (int64_t)h->nnz + 4096) ? ((maxdeg + 3) & ~3) : 0;
     if (!alloc_n(h, h->d_rp, (size_t)n + 1, h->inst_bufs) ||
         !alloc_n(h, h->d_adj, (size_t)std::max(h->nnz, 1), h->inst_bufs)) {
         dev_free_all(h, h->inst_bufs);
@@ -616,6 +617,9 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
     if (h->dense) return init_dense(h, p);
+    if (p.kind == 1 && h->H > kByteLaneMaxH)
+        return fail(h, PAMC_ERR_RANGE, "Max-3-Cut runs need sum_j |w_ij| <= %d (this instance: %d)", kByteLaneMaxH,
+                    h->H);
     release_run(h);
     h->p = p;
     const int32_t n = h->n, R = p.R, S = std::max(p.sweeps, 1);
@@ -701,10 +705,12 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     // with PAMC_SWEEP_GLOBAL=1) keep the words in device memory: one lane per
     // vertex, one group per CTA
     const char *genv = getenv("PAMC_SWEEP_GLOBAL");
+    const bool wide = p.kind == 0 && h->H > kByteLaneMaxH;   // 16-bit field lanes, one lane per vertex
+    if (wide) h->cfg.lanes_per_vertex = 1;
     if (p.kind == 0 && ((genv && genv[0] == '1') || sweep_smem_bytes(0, n, h->H, h->cfg) > kSmemMax)) {
         if (!getenv("PAMC_SWEEP_CFG")) h->cfg = SweepCfg{1, 16, 1};
         h->cfg.lanes_per_vertex = 1;
-        if (!alloc_n(h, h->d_gsp, gsp_words(n, R), h->bufs)) {
+        if (!alloc_n(h, h->d_gsp, gsp_words(n, R) * (wide ? 2 : 1), h->bufs)) {
             release_run(h);
             return fail(h, PAMC_ERR_OOM, "device allocation of the group spin words failed");
         }
@@ -1017,6 +1023,7 @@ pamc_status pamc_sweep_mode(pamc_handle h, int *mode) {
     const bool ell = h->d_ell != nullptr;
     if (h->gsp) *mode = (ell ? 1 : 0) | 4;
     else *mode = sweep_push_ok(h->H, h->p.sweeps, ell, h->cfg.lanes_per_vertex) ? 2 : ell ? 1 : 0;
+    if (h->H > kByteLaneMaxH) *mode |= 8;
     return PAMC_OK;
 }
 
@@ -1296,7 +1303,8 @@ size_t pamc_footprint(pamc_handle h, const pamc_params *p) {
     if (p->stagnation && p->kind == 0) b += 5 * (size_t)std::min(p->n_top > 0 ? p->n_top : std::max(1, p->R / 16), p->R) * n;
     b += ((size_t)h->n + 1) * 4 + (size_t)std::max(h->nnz, 1) * 4;   // the instance itself
     // Ising groups whose spin words do not fit shared memory keep them in device memory
-    if (p->kind == 0 && sweep_ising_smem_bytes(n, 127, SweepCfg{1, 1, 1}) > kSmemMax) b += gsp_words(n, p->R) * 4;
+    if (p->kind == 0 && sweep_smem_bytes(0, (int32_t)n, h->H, SweepCfg{1, 1, 1}) > kSmemMax)
+        b += gsp_words((int32_t)n, p->R) * 4 * (h->H > kByteLaneMaxH ? 2 : 1);
     return b + sizeof(DevCtl);
 }
 
@@ -1324,6 +1332,8 @@ pamc_status pamc_batch_add(pamc_batch b, pamc_handle h) {
     if (!b || !h) return bfail(b, PAMC_ERR_ARG, "null batch or handle");
     if (!h->initialized) return bfail(b, PAMC_ERR_STATE, "handle not initialised (pamc_init)");
     if (h->dense) return bfail(b, PAMC_ERR_ARG, "batches hold sparse instances");
+    if (h->H > kByteLaneMaxH)
+        return bfail(b, PAMC_ERR_ARG, "batched members need sum_j |w_ij| <= %d", kByteLaneMaxH);
     if (h->p.kind == 1 && h->p.rule != 0)
         return bfail(b, PAMC_ERR_ARG, "batched Max-3-Cut members use the cascaded sampler (rule 0)");
     if (h->p.stagnation || (h->p.z_rst > 0 && h->p.restart_reinit))

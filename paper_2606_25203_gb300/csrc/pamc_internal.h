@@ -186,6 +186,18 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
                                const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
                                const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp = nullptr);
 
+// Ising sweeps with 16-bit field lanes (sweep_wide.cu): instances with
+// 127 < H <= 32767; two words per vertex and replica group (8n bytes), in
+// shared memory or, with gsp, in device memory (2 * n_pad words a group).
+constexpr int32_t kByteLaneMaxH = 127;
+constexpr int32_t kWideLaneMaxH = 32767;
+size_t sweep_wide_smem_bytes(int32_t n, SweepCfg cfg, bool global_spins);
+cudaError_t launch_sweep_ising_wide(int rule, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t H,
+                                    const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
+                                    const uint64_t *tab, const int8_t *src, const int32_t *parent,
+                                    const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
+                                    const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp);
+
 // Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax;
 // every kind keeps groups of four replicas.
 size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg);

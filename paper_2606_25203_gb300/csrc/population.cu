@@ -598,7 +598,9 @@ cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint
     if (kind == 1 && rule == 2) {
         k_tables_softmax<<<1, 256, 0, st>>>(H, ctl, reinterpret_cast<float *>(tab));
     } else if (kind == 0) {
-        k_tables<<<1, 256, 0, st>>>(kind, rule, H, ctl, tab);
+        int grid = (2 * H + 1 + 255) / 256;   // wide field ranges: many entries
+        if (grid > 304) grid = 304;
+        k_tables<<<grid, 256, 0, st>>>(kind, rule, H, ctl, tab);
     } else {
         const int32_t W1 = 4 * H + 1;
         int grid = (W1 * W1 + W1 + 255) / 256;

@@ -76,7 +76,7 @@ __global__ void k_energy(int kind, int32_t n, const int32_t *__restrict__ rp,
 }  // namespace
 
 size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg) {
-    if (kind == 0) return sweep_ising_smem_bytes(n, H, cfg);
+    if (kind == 0) return H > kByteLaneMaxH ? sweep_wide_smem_bytes(n, cfg, false) : sweep_ising_smem_bytes(n, H, cfg);
     if (kind == 2) return sweep_softmax_smem_bytes(n, H, cfg);
     return sweep_potts_smem_bytes(n, H, cfg);
 }
@@ -87,6 +87,9 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
                          const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst,
                          int64_t *E_dst, const DevCtl *ctl, SweepCfg cfg, int64_t Wsum,
                          cudaStream_t st, uint32_t *gsp) {
+    if (kind == 0 && H > kByteLaneMaxH)
+        return launch_sweep_ising_wide(rule, n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_buf, ncm_idx,
+                                       dst, E_dst, ctl, cfg, st, gsp);
     if (kind == 0)
         return launch_sweep_ising(rule, n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_buf,
                                   ncm_idx, dst, E_dst, ctl, cfg, st, gsp);

@@ -354,3 +354,81 @@ def test_group_spins_in_device_memory(pg, monkeypatch, rule):
         s.close()
         compare_run(pg, inst, 10, R=R, sweeps=2, beta0=0.2, beta1=3.0, rule=rule, stagnation=1, z_rst=7,
                     cooldown_tau=1, seed=4)
+
+
+def _weighted_hub(n=600, hub_deg=300, wmax=2, m_rest=1500, wrest=100, seed=5):
+    """A hub coupled to hub_deg vertices (weights up to wmax, degree above the
+    255 an ELL record holds), and a random rest with weights up to wrest in
+    magnitude: field ranges well above a byte lane."""
+    rng = np.random.default_rng(seed)
+    ei, ej, w = [], [], []
+    for j in range(1, hub_deg + 1):
+        ei.append(0); ej.append(j); w.append(int(rng.integers(1, wmax + 1)) * int(rng.choice([-1, 1])))
+    pairs = set()
+    while len(pairs) < m_rest:
+        a, b = (int(x) for x in rng.integers(1, n, size=2))
+        if a != b:
+            pairs.add((min(a, b), max(a, b)))
+    for a, b in sorted(pairs):
+        ei.append(a); ej.append(b); w.append(int(rng.integers(-wrest, wrest + 1)) or 1)
+    return W.csr_from_edges(n, np.array(ei), np.array(ej), np.array(w), f"hub{hub_deg}_w{wrest}")
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_wide_field_range_instances(pg, monkeypatch, rule):
+    """Field ranges above 127 (Eq. 3 for any integer couplings up to |w| = 127
+    each, sum |w| per vertex up to 32,767) run the 16-bit-lane sweep: a
+    weighted hub of degree 300 (CSR rows), a random graph with weights up to
+    100 (ELL rows), each against the oracle step after step with cluster
+    moves and restarts; the same with the spin words in device memory."""
+    insts = (_weighted_hub(), W.gnm(700, 2800, signed=True, seed=9))
+    rng = np.random.default_rng(1)
+    g2 = insts[1]
+    g2 = W.Instance(g2.name + "_w100", g2.n, g2.row_ptr, g2.col, None)
+    # symmetric weights in [-100, 100] \ {0}: draw per undirected edge
+    rp, col = g2.row_ptr, g2.col
+    wmap = {}
+    w = np.zeros(col.shape[0], dtype=np.int32)
+    for i in range(g2.n):
+        for e in range(rp[i], rp[i + 1]):
+            j = int(col[e])
+            key = (min(i, j), max(i, j))
+            if key not in wmap:
+                wmap[key] = int(rng.integers(1, 101)) * int(rng.choice([-1, 1]))
+            w[e] = wmap[key]
+    g2.w = w
+    for inst in (insts[0], g2):
+        H = max(int(np.abs(inst.w[inst.row_ptr[i]:inst.row_ptr[i + 1]]).sum()) for i in range(inst.n))
+        assert 127 < H <= 32767, (inst.name, H)
+        for glob in ("0", "1"):
+            monkeypatch.setenv("PAMC_SWEEP_GLOBAL", glob)
+            s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+            s.init(R=10, sweeps=2, steps=3, rule=rule, seed=2)
+            mode = pg.pamc_sweep_mode(s.h)
+            assert mode & 8 and bool(mode & 4) == (glob == "1"), (inst.name, mode)
+            s.close()
+            compare_run(pg, inst, 9, R=10, sweeps=2, beta0=0.01, beta1=0.3, rule=rule, stagnation=1, z_rst=6,
+                        cooldown_tau=1, seed=2)
+
+
+def test_wide_field_range_refusals(pg):
+    """Max-3-Cut keeps the byte-lane bound; batches refuse wide members; more
+    than 32,767 per vertex is refused at creation."""
+    inst = _weighted_hub()
+    h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+    b = pg.pamc_batch_create(0)
+    try:
+        with pytest.raises(pg.PamcError) as e:
+            pg.pamc_init(h, kind=1, R=8, steps=2)
+        assert e.value.status == 4
+        pg.pamc_init(h, R=8, steps=2)
+        with pytest.raises(pg.PamcError):
+            pg.pamc_batch_add(b, h)
+    finally:
+        pg.pamc_batch_destroy(b)
+        pg.pamc_destroy(h)
+    n = 300                                   # a vertex with 299 couplings of 127: 37,973 > 32,767
+    big = W.csr_from_edges(n, np.zeros(n - 1, dtype=np.int64), np.arange(1, n), np.full(n - 1, 127), "star127")
+    with pytest.raises(pg.PamcError) as e:
+        pg.pamc_create_csr(big.n, big.row_ptr, big.col, big.w)
+    assert e.value.status == 4
