@@ -56,12 +56,13 @@ def test_host_validation_errors(lib):
     assert _create(lib, [0, 1], [0], [1])[0] == 3
     # weight out of range
     assert _create(lib, [0, 1, 2], [1, 0], [200, 200])[0] == 4
-    # field range: a vertex with 130 unit edges
-    n = 131
-    ei = np.zeros(130, dtype=np.int64)
-    ej = np.arange(1, 131)
+    # field range beyond the widest lanes
+    # (a vertex with 299 couplings of 127: 37,973 > 32,767, the widest lanes)
+    n = 300
+    ei = np.zeros(n - 1, dtype=np.int64)
+    ej = np.arange(1, n)
     import workloads as W
-    star = W.csr_from_edges(n, ei, ej, np.ones(130, dtype=np.int64), "star")
+    star = W.csr_from_edges(n, ei, ej, np.full(n - 1, 127, dtype=np.int64), "star")
     assert _create(lib, star.row_ptr, star.col, star.w)[0] == 4
     # bad row_ptr
     assert _create(lib, [1, 1], [], [])[0] == 1
