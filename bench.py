@@ -64,9 +64,9 @@ def load_peaks():
 # DRAM bytes per launch from the committed ncu captures (profiles/), valid
 # only while the kernel sources still hash to what was captured.
 PROFILED_TRAFFIC = {
-    # the sweep launches of the default window (per launch, both instances'
-    # average); re-captured for every change of the kernel source
-    "sweep_window": (None, {"paper_2606_25203_gb300/csrc/sweep_ising.cu": ""}),
+    # k_sweep_ising, torus 141x141, R=4096, 10 sweeps: one launch (filled in
+    # from the capture of the current source)
+    "sweep_torus": (None, {"paper_2606_25203_gb300/csrc/sweep_ising.cu": ""}),
     # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.688 GB) scaled by n^2 to n=100,000
     # (captured at 6a66522d; the source since differs by one comment line)
     "dense_sweep_100k": (1.688e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
@@ -357,8 +357,9 @@ def run_ours(args):
     # CUDA events the library records around it on its stream
     peaks, peak_src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    sweep = sweep_roofline(insts, args.steps, sw0, sw1, sm_max)
+    sweep = [sweep_roofline(inst, args.steps, a, b, sm_max) for inst, a, b in zip(insts, sw0, sw1)]
     mode = [pg.pamc_sweep_mode(s.h) for s in solvers]
+    kname = ["k_sweep_ising_push" if m == 2 else "k_sweep_ising" for m in mode]
     e2e = e2e_measure(pg, torch, insts, args, local, start)
     dense = None
     if world == 1 and not args.no_dense:
@@ -381,10 +382,11 @@ def run_ours(args):
                                       + (f"; steps 0..{start - 1} untimed" if start else "") + ")",
                        "timed_window": window,
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
-            "roofline": dict(sweep, traffic=profiled_traffic("sweep_window"),
-                             kernel=("k_sweep_ising_push" if all(m == 2 for m in mode) else "k_sweep_ising")
-                             + " (torus 141x141 and sparse N=7000, R=4096, 10 sweeps per launch)",
+            "roofline": dict(sweep[0], traffic=profiled_traffic("sweep_torus") if ONLY != "sparse" else None,
+                             kernel=kname[0] + f" ({insts[0].name}, R=4096, 10 sweeps per launch)",
                              peak_source=f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)"),
+            "roofline_other_instance": (dict(sweep[1], kernel=kname[1] + f" ({insts[1].name})")
+                                        if len(insts) > 1 else None),
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
@@ -461,20 +463,20 @@ def ops_per_flip(inst):
     return 1 + 2 * inst.nnz / inst.n
 
 
-def sweep_roofline(insts, steps, before, after, sm_max):
-    """ALU roofline of the sweep launches of the timed window: algorithmic
-    operations (attempts and counted flips) over their summed event time."""
-    att = sum(R * inst.n * SWEEPS * steps for inst in insts)
-    flips = [b["flips"] - a["flips"] for a, b in zip(before, after)]
-    ops = att * OPS_PER_ATTEMPT + sum(f * ops_per_flip(inst) for f, inst in zip(flips, insts))
-    ms = sum(b["ms"] for b in after)
-    launches = sum(b["launches"] for b in after)
+def sweep_roofline(inst, steps, before, after, sm_max):
+    """ALU roofline of one instance's sweep launches in the timed window:
+    algorithmic operations (attempts and counted flips) over their summed
+    event time (each launch timed by the library on its stream)."""
+    att = R * inst.n * SWEEPS * steps
+    flips = after["flips"] - before["flips"]
+    ops = att * OPS_PER_ATTEMPT + flips * ops_per_flip(inst)
+    ms, launches = after["ms"], after["launches"]
     achieved = ops / (ms / 1e3) / 1e12
     peak = 152 * 128 * sm_max * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
             "launches": launches, "avg_launch_ms": ms / max(launches, 1), "sweep_ms": ms,
-            "ops_per_attempt": OPS_PER_ATTEMPT, "ops_per_flip": [ops_per_flip(i) for i in insts],
-            "flip_fraction": sum(flips) / att}
+            "ops_per_attempt": OPS_PER_ATTEMPT, "ops_per_flip": ops_per_flip(inst),
+            "flip_fraction": flips / att, "attempts_per_s": att / (ms / 1e3)}
 
 
 def e2e_measure(pg, torch, insts, args, device, start=0):
@@ -537,7 +539,11 @@ def dense_measure(pg, torch, n, steps, warmup, e2e=False):
     w = dense_weights_device(torch, n)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
-    w_host = w.cpu().numpy() if e2e else None
+    w_host = None
+    if e2e:   # the weights in pinned host memory, as a caller streaming instances would hold them
+        w_pin = torch.empty((n, n), dtype=torch.int8, pin_memory=True)
+        w_pin.copy_(w)
+        w_host = w_pin.numpy()
     h = pg.pamc_create_dense(n, w, stream=stream.cuda_stream)
     del w
     torch.cuda.empty_cache()
@@ -601,8 +607,10 @@ def dense_measure(pg, torch, n, steps, warmup, e2e=False):
         pg.pamc_destroy(h)
         e2e_obj = {"value": att / dt, "unit": "attempts/s", "h2d_bytes_per_step": n * n / steps,
                    "d2h_bytes_per_step": 8 + n, "steps": steps,
-                   "includes": "upload of the n x n weights from pageable host memory, validation, init"}
+                   "includes": "upload of the n x n weights from pinned host memory, validation, init"}
     del w_host
+    if e2e:
+        del w_pin
     return {
         "metric": METRIC, "value": att / (ms / 1e3), "unit": "attempts/s", "n_gpus": 1,
         "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
