@@ -345,11 +345,12 @@ def test_shapes_change_speed_not_results(pg):
         with pytest.raises(pg.PamcError):
             pg.pamc_batch_set_lanes(b, 0, 3)         # 1, 2 or 4
         got = tune_batch_shapes(b, [c[0] for c in cases], dict(R=32, sweeps=1), steps=1, rounds=1,
-                                candidates=((1, 4), (2, 2), (1, 8, 2)))
+                                candidates=((1, 4), (2, 2), (1, 8, 2), (1, 8, 1, 1)))
         assert sorted(got) == [0, 1, 2]
-        for c, (g, w, lv, ms) in got.items():
-            assert (g, w, lv) in ((1, 4, 1), (2, 2, 1), (1, 8, 2)) and ms > 0
+        for c, (g, w, lv, ms, gm) in got.items():
+            assert (g, w, lv, gm) in ((1, 4, 1, 0), (2, 2, 1, 0), (1, 8, 2, 0), (1, 8, 1, 1)) and ms > 0
             assert pg.pamc_batch_get_shape(b, c) == (g, w)
             assert pg.pamc_batch_get_lanes(b, c) == lv
+            assert pg.pamc_batch_get_placement(b, c) == bool(gm)
     finally:
         pg.pamc_batch_destroy(b)
