@@ -273,13 +273,20 @@ sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 4 + li] / 2);
 }
 
+// Row i of a position-indexed ELL block of width W: lanes of a warp read
+// consecutive words (slot s of position i at (i & ~31) * W + 32 s + (i & 31)),
+// with 32-bit offset arithmetic (n W < 2^32: n < 2^24, W < 256).
+__device__ __forceinline__ const uint32_t *ell_row(const uint32_t *es, int32_t i, int32_t W) {
+    return es + ((uint32_t)(i & ~31) * (uint32_t)W + (uint32_t)(i & 31));
+}
+
 // The sweep of one CTA's replica groups (groups bid*gpc .. bid*gpc+gpc-1 of
 // the instance), shared by the single-instance and the batched kernels.  With
 // LPV > 1 (position-indexed ELL only; LPV a power of two up to 32) LPV lanes share a vertex: lane sub takes
 // the coupling slots sub, sub + LPV, ...; the byte-lane partial sums add up
 // exactly under XOR shuffles (plain 32-bit addition), and every lane of the
 // group runs the same iterations so that the shuffles always converge.
-template <bool ELLP, int RULE, int LPV, class KeyT, bool GSP = false>
+template <bool ELLP, int RULE, int LPV, class KeyT, bool GSP = false, bool W4 = false>
 __device__ __forceinline__ void
 sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                  const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, const KeyT &draw,
@@ -291,6 +298,8 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                  const int32_t *__restrict__ ncm_idx, int8_t *__restrict__ dst,
                  int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int gpc, int tpg,
                  int32_t bid, uint32_t *__restrict__ gspins = nullptr) {
+    // W4: the ELL width is 4 (every row in the first four slots), known at compile time
+    if constexpr (W4) W = 4;
     extern __shared__ __align__(16) uint8_t smem[];
     if (ctl->done) return;
     const int tabn = 2 * H + 1;
@@ -354,7 +363,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                 uint32_t e8[8];
                 auto fetch = [&](int32_t i) {
                     pr = pos[i];
-                    const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+                    const uint32_t *ep = ell_row(es, i, W);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int32_t sl = sub + q * LPV;   // slots >= deg hold coupling 0
@@ -377,7 +386,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
 #pragma unroll
                         for (int q = 0; q < 8; ++q) Ap += sp[e8[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e8[q] >> 24);
                         if (8 * LPV < deg) {
-                            const uint32_t *ep = es + (size_t)(ic >> 5) * 32 * W + (ic & 31);
+                            const uint32_t *ep = ell_row(es, ic, W);
                             for (int32_t s0 = sub + 8 * LPV; s0 < deg; s0 += 8 * LPV) {
                                 uint32_t ev[8];
 #pragma unroll
@@ -418,7 +427,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                 // decided once the level's bounds are known
                 const int32_t i0 = min(li, n - 1);
                 pr = pos[i0];
-                const uint32_t *ep = es + (size_t)(i0 >> 5) * 32 * W + (i0 & 31);
+                const uint32_t *ep = ell_row(es, i0, W);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) e4[q] = ep[q * 32];
             }
@@ -432,7 +441,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                     uint32_t e4n[4] = {0u, 0u, 0u, 0u};
                     if (ELLP && inext < end) {
                         prn = pos[inext];
-                        const uint32_t *epn = es + (size_t)(inext >> 5) * 32 * W + (inext & 31);
+                        const uint32_t *epn = ell_row(es, inext, W);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) e4n[q] = epn[q * 32];
                     }
@@ -447,13 +456,13 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                         jsum = pr.y;
                         // the next neighbour words are requested before the draw is
                         // computed, so that the Philox rounds overlap their latency
-                        if (W <= 4) {   // every neighbour word is already in registers
+                        if (W4 || W <= 4) {   // every neighbour word is already in registers
 #pragma unroll
                             for (int q = 0; q < 4; ++q)   // padding slots: coupling 0
                                 A += sp[e4[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e4[q] >> 24);
                             u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
                         } else {
-                        const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31) + 4 * 32;
+                        const uint32_t *ep = ell_row(es, i, W) + 4 * 32;
                         // up to sixteen more neighbour words in flight before the draw
                         uint32_t ev[8], ew[8];
                         if (deg > 4) {
@@ -512,7 +521,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                 if (ELLP && lev + 1 < L) {   // the next level's first position (clamped, see above)
                     const int32_t i2 = min(end + li, n - 1);
                     pr = pos[i2];
-                    const uint32_t *ep = es + (size_t)(i2 >> 5) * 32 * W + (i2 & 31);
+                    const uint32_t *ep = ell_row(es, i2, W);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) e4[q] = ep[q * 32];
                 }
@@ -534,7 +543,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
             uint32_t e4[4] = {0u, 0u, 0u, 0u};
             auto fetch = [&](int32_t i) {
                 pr = pos[i];
-                const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+                const uint32_t *ep = ell_row(es, i, W);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) e4[q] = q < W ? ep[q * 32] : 0u;
             };
@@ -547,7 +556,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                 if (i + tpg < n) fetch(i + tpg);
                 const int32_t deg = (int32_t)((uint32_t)p0.x >> 24);
                 if (deg > 4) {
-                    const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+                    const uint32_t *ep = ell_row(es, i, W);
                     for (int32_t sl = 4; sl < deg; ++sl) {
                         const uint32_t e = ep[(size_t)sl * 32];
                         A += sp[e & 0xFFFFFFu] * (uint32_t)((int32_t)e >> 24);
@@ -597,9 +606,9 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 4 + li] / 2);
 }
 
-template <bool ELLP, int RULE, int LPV, bool GSP = false>
+template <bool ELLP, int RULE, int LPV, bool GSP = false, bool W4 = false>
 __global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int tpg) {
-    sweep_ising_body<ELLP, RULE, LPV, KeysPre, GSP>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t,
+    sweep_ising_body<ELLP, RULE, LPV, KeysPre, GSP, W4>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t,
                                                     d.slot, d.sorder, d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab,
                                                     d.src, d.parent, d.ncm_buf, d.ncm_idx, d.dst, d.E_dst, d.ctl, gpc,
                                                     tpg, blockIdx.x, d.gsp);
@@ -683,6 +692,12 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
         if (err != cudaSuccess) return err;                                                       \
         k_sweep_ising<EL, RU, LV><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);                    \
     } while (0)
+#define PAMC_LAUNCH_W4(RU)                                                                        \
+    do {                                                                                          \
+        err = allow_dynamic_smem(k_sweep_ising<true, RU, 1, false, true>, smem);                  \
+        if (err != cudaSuccess) return err;                                                       \
+        k_sweep_ising<true, RU, 1, false, true><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);      \
+    } while (0)
 #define PAMC_LAUNCH_G(EL, RU)                                                                     \
     do {                                                                                          \
         err = allow_dynamic_smem(k_sweep_ising<EL, RU, 1, true>, smem);                           \
@@ -697,7 +712,9 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
         case 8: PAMC_LAUNCH(true, RU, 8); break;                                                  \
         case 4: PAMC_LAUNCH(true, RU, 4); break;                                                  \
         case 2: PAMC_LAUNCH(true, RU, 2); break;                                                  \
-        default: PAMC_LAUNCH(true, RU, 1); break;                                                 \
+        default:                                                                                  \
+            if (sv.W == 4) PAMC_LAUNCH_W4(RU); else PAMC_LAUNCH(true, RU, 1);                    \
+            break;                                                                                \
         }                                                                                         \
     } while (0)
     const int lpv = ell ? cfg.lanes_per_vertex : 1;
@@ -729,6 +746,7 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
     }
 #undef PAMC_LAUNCH_LPV
 #undef PAMC_LAUNCH_G
+#undef PAMC_LAUNCH_W4
 #undef PAMC_LAUNCH
     return cudaGetLastError();
 }
