@@ -286,7 +286,7 @@ __device__ __forceinline__ const uint32_t *ell_row(const uint32_t *es, int32_t i
 // the coupling slots sub, sub + LPV, ...; the byte-lane partial sums add up
 // exactly under XOR shuffles (plain 32-bit addition), and every lane of the
 // group runs the same iterations so that the shuffles always converge.
-template <bool ELLP, int RULE, int LPV, class KeyT, bool GSP = false, bool W4 = false>
+template <bool ELLP, int RULE, int LPV, class KeyT, bool GSP = false, int WC = 0>
 __device__ __forceinline__ void
 sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                  const uint32_t *__restrict__ adj, int32_t H, int32_t R, int32_t S, const KeyT &draw,
@@ -298,8 +298,9 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                  const int32_t *__restrict__ ncm_idx, int8_t *__restrict__ dst,
                  int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int gpc, int tpg,
                  int32_t bid, uint32_t *__restrict__ gspins = nullptr) {
-    // W4: the ELL width is 4 (every row in the first four slots), known at compile time
-    if constexpr (W4) W = 4;
+    // WC > 0: the ELL width, known at compile time (4: every row in the first
+    // four slots, the torus; 8, 12, 16: sparse graphs of low degree)
+    if constexpr (WC > 0) W = WC;
     extern __shared__ __align__(16) uint8_t smem[];
     if (ctl->done) return;
     const int tabn = 2 * H + 1;
@@ -456,7 +457,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                         jsum = pr.y;
                         // the next neighbour words are requested before the draw is
                         // computed, so that the Philox rounds overlap their latency
-                        if (W4 || W <= 4) {   // every neighbour word is already in registers
+                        if (W <= 4) {   // every neighbour word is already in registers
 #pragma unroll
                             for (int q = 0; q < 4; ++q)   // padding slots: coupling 0
                                 A += sp[e4[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e4[q] >> 24);
@@ -606,9 +607,9 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 4 + li] / 2);
 }
 
-template <bool ELLP, int RULE, int LPV, bool GSP = false, bool W4 = false>
+template <bool ELLP, int RULE, int LPV, bool GSP = false, int WC = 0>
 __global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int tpg) {
-    sweep_ising_body<ELLP, RULE, LPV, KeysPre, GSP, W4>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t,
+    sweep_ising_body<ELLP, RULE, LPV, KeysPre, GSP, WC>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t,
                                                     d.slot, d.sorder, d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab,
                                                     d.src, d.parent, d.ncm_buf, d.ncm_idx, d.dst, d.E_dst, d.ctl, gpc,
                                                     tpg, blockIdx.x, d.gsp);
@@ -692,11 +693,11 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
         if (err != cudaSuccess) return err;                                                       \
         k_sweep_ising<EL, RU, LV><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);                    \
     } while (0)
-#define PAMC_LAUNCH_W4(RU)                                                                        \
+#define PAMC_LAUNCH_WC(RU, WV)                                                                    \
     do {                                                                                          \
-        err = allow_dynamic_smem(k_sweep_ising<true, RU, 1, false, true>, smem);                  \
+        err = allow_dynamic_smem(k_sweep_ising<true, RU, 1, false, WV>, smem);                    \
         if (err != cudaSuccess) return err;                                                       \
-        k_sweep_ising<true, RU, 1, false, true><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);      \
+        k_sweep_ising<true, RU, 1, false, WV><<<grid, gpc * tpg, smem, st>>>(d, gpc, tpg);        \
     } while (0)
 #define PAMC_LAUNCH_G(EL, RU)                                                                     \
     do {                                                                                          \
@@ -713,7 +714,13 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
         case 4: PAMC_LAUNCH(true, RU, 4); break;                                                  \
         case 2: PAMC_LAUNCH(true, RU, 2); break;                                                  \
         default:                                                                                  \
-            if (sv.W == 4) PAMC_LAUNCH_W4(RU); else PAMC_LAUNCH(true, RU, 1);                    \
+            switch (sv.W) {                                                                       \
+            case 4: PAMC_LAUNCH_WC(RU, 4); break;                                                 \
+            case 8: PAMC_LAUNCH_WC(RU, 8); break;                                                 \
+            case 12: PAMC_LAUNCH_WC(RU, 12); break;                                               \
+            case 16: PAMC_LAUNCH_WC(RU, 16); break;                                               \
+            default: PAMC_LAUNCH(true, RU, 1); break;                                             \
+            }                                                                                     \
             break;                                                                                \
         }                                                                                         \
     } while (0)
@@ -746,7 +753,7 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
     }
 #undef PAMC_LAUNCH_LPV
 #undef PAMC_LAUNCH_G
-#undef PAMC_LAUNCH_W4
+#undef PAMC_LAUNCH_WC
 #undef PAMC_LAUNCH
     return cudaGetLastError();
 }
