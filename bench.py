@@ -292,9 +292,12 @@ def run_ours(args):
     pg.load()
     insts = instances()
     stream = torch.cuda.current_stream()
+    # the two instances are independent: each steps on a stream of its own
+    # (unless --one-stream), so one's kernels fill the other's last wave
+    sstreams = [stream if args.one_stream else torch.cuda.Stream() for _ in insts]
     solvers = []
-    for inst in insts:
-        s = pg.Solver(inst.row_ptr, inst.col, inst.w, device=local, stream=stream.cuda_stream)
+    for inst, st in zip(insts, sstreams):
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w, device=local, stream=st.cuda_stream)
         s.init(**dict(PARAMS, seed=rank_seed(PARAMS["seed"], rank)))
         solvers.append(s)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
@@ -323,12 +326,17 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    done = [torch.cuda.Event() for _ in solvers]
     with clk:
         for k in range(args.steps):
             flush.add_(1)
             ev[k][0].record(stream)
-            for s in solvers:
+            for s, st, d in zip(solvers, sstreams, done):
+                st.wait_event(ev[k][0])          # the step starts after the flush
                 s.step(1)
+                d.record(st)
+            for d in done:
+                stream.wait_event(d)             # and ends when both instances' iterations have
             ev[k][1].record(stream)
         torch.cuda.synchronize()
     if dist:
@@ -490,15 +498,18 @@ def e2e_measure(pg, torch, insts, args, device, start=0):
     h2d = 0
     d2h = 0
     solvers = []
-    for inst in insts:
-        s = pg.Solver(inst.row_ptr, inst.col, inst.w, device=device)
+    streams = [None if args.one_stream else torch.cuda.Stream() for _ in insts]
+    for inst, st in zip(insts, streams):
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w, device=device,
+                      stream=None if st is None else st.cuda_stream)
         h2d += inst.row_ptr.nbytes + inst.col.nbytes + inst.w.nbytes
         s.init(**PARAMS)
         solvers.append(s)
     nsteps = start + args.steps
     for _ in range(nsteps):
-        for s in solvers:
+        for s in solvers:          # both instances' iterations enqueued, then both read back
             s.step(1)
+        for s in solvers:
             s.best()
             d2h += 8 + s.n
     torch.cuda.synchronize()
@@ -991,6 +1002,8 @@ def main():
     ap.add_argument("--serve-max-active", type=int, default=64)
     ap.add_argument("--dense-n", type=int, default=DENSE_N)
     ap.add_argument("--dense-e2e", action="store_true", help="dense100k: add the end-to-end figure")
+    ap.add_argument("--one-stream", action="store_true",
+                    help="sparse workload: step the two instances one after the other on one stream")
     ap.add_argument("--no-dense", action="store_true",
                     help="sparse workload: leave out the dense100k object (profiling)")
     args = ap.parse_args()
