@@ -82,7 +82,8 @@ __device__ __forceinline__ uint32_t ising_decide(uint32_t A, int32_t c0, const u
     uint32_t nw = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int32_t idx = 2 * (int32_t)((A >> (8 * q)) & 0xFFu) + c0;   // h + H
+        // byte q of A, zero-extended (one byte permute)
+        const int32_t idx = 2 * (int32_t)__byte_perm(A, 0u, 0x4440u + q) + c0;   // h + H
         if (RULE == 0) {
             nw |= ((uint64_t)uw[q] < tab_s[idx] ? 1u : 0u) << (8 * q);
         } else {
