@@ -572,3 +572,54 @@ def test_dense_sk_anneal_reaches_parisi_neighbourhood():
     m, _ = hot.best()
     assert (hot.weight_sum() - 2 * m) / n ** 1.5 > -0.5
     hot.close()
+
+
+def _weighted(n, p, wmax, seed):
+    rng = np.random.default_rng(seed)
+    ei, ej, w = [], [], []
+    for i in range(n):
+        for j in range(i + 1, n):
+            if rng.random() < p:
+                ei.append(i); ej.append(j); w.append(int(rng.integers(1, wmax + 1)) * int(rng.choice([-1, 1])))
+    return W.csr_from_edges(n, np.array(ei), np.array(ej), np.array(w), f"weighted{wmax}_s{seed}")
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pamc_finds_brute_force_maxcut_large_weights(seed):
+    """Weights up to 100 in magnitude (field ranges far beyond a byte, the
+    regime of the 16-bit-lane sweep): the annealer over a temperature range
+    scaled to the weights reaches the exhaustive optimum, and the best
+    configuration's cut is what it reports."""
+    inst = _weighted(16, 0.5, 100, seed)
+    H = max(int(np.abs(inst.w[inst.row_ptr[i]:inst.row_ptr[i + 1]]).sum()) for i in range(inst.n))
+    assert H > 127
+    opt = _brute_maxcut(inst)
+    run = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=64, sweeps=2, steps=60, beta0=0.001,
+                           beta1=0.05, seed=seed)
+    run.step(60)
+    m, best = run.best()
+    assert m == opt
+    cut = sum(inst.w[e] for i in range(inst.n) for e in range(inst.row_ptr[i], inst.row_ptr[i + 1])
+              if i < inst.col[e] and best[i] != best[inst.col[e]])
+    assert cut == m
+
+
+def test_thresholds_saturate_exactly_at_large_fields():
+    """Large |h| (up to 32,767): the heat-bath threshold is exactly 2^32 or 0
+    once the Eq. 4 probability is within half a unit of 2^-32 of 1 or 0, and
+    Metropolis accepts every downhill move and no move whose e^{-beta dE}
+    rounds to 0; both stay within one unit of the closed forms everywhere."""
+    for beta in (0.001, 0.05, 1.0):
+        for h in (-32767, -5000, -300, -128, 128, 300, 5000, 32767):
+            T = oracle.thr_heatbath(beta, h)
+            exact = TWO32 * (1.0 + math.tanh(beta * h)) / 2.0
+            assert abs(T - exact) <= 1.0 + 1e-6 * exact and 0 <= T <= TWO32
+            if beta * h > 12:
+                assert T == TWO32
+            if beta * h < -12:
+                assert T == 0
+            M = oracle.thr_metropolis(beta, 2 * h)
+            if h <= 0:
+                assert M == TWO32
+            else:
+                assert abs(M - TWO32 * math.exp(-2 * beta * h)) <= 1.0
