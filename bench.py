@@ -687,10 +687,10 @@ def run_serving(args):
     srv = Server(max_active=args.serve_max_active, steps_per_tick=2)
     # launch shape per size class, tuned on copies of requests from another stream
     t1 = time.perf_counter()
-    tune_reqs = W.serving_stream(24, rate=0.0, seed=3)
+    tune_reqs = W.serving_stream(24, rate=0.0, seed=3, max3cut_frac=args.serve_max3cut)
     samples = []
     for lo, hi in ((800, 2048), (2049, 8192), (8193, 20000)):
-        samples += [r.inst for r in tune_reqs if lo <= r.inst.n <= hi][:6]
+        samples += [(r.inst, r.kind) for r in tune_reqs if lo <= r.inst.n <= hi][:6]
     shapes = srv.autotune(samples, P)
     tune_s = time.perf_counter() - t1
     srv.serve(warm, wp)

@@ -25,7 +25,9 @@ CANDIDATES = (tuple((g, w, 1, 0) for g in (1, 2, 4, 8) for w in (1, 2, 4, 8, 16)
 
 def tune_batch_shapes(batch, samples, params: dict, steps: int = 3, rounds: int = 2, device: int = 0,
                       candidates=CANDIDATES) -> dict:
-    """samples: instances with ``n``, ``row_ptr``, ``col``, ``w`` (numpy CSR).
+    """samples: instances with ``n``, ``row_ptr``, ``col``, ``w`` (numpy CSR),
+    or (instance, kind) pairs -- kind 0 Max-Cut, 1 Max-3-Cut -- so that a
+    class's shape is timed on the mix of problems it will serve.
     params: run parameters of the served requests (R, sweeps, rule, ...).
     candidates: (groups, warps), (groups, warps, lanes) or (groups, warps,
     lanes, device-memory spin words) tuples.
@@ -34,8 +36,9 @@ def tune_batch_shapes(batch, samples, params: dict, steps: int = 3, rounds: int 
     candidates = tuple(tuple(c) + (1, 0)[len(c) - 2:] if len(c) < 4 else tuple(c) for c in candidates)
     import torch
     by_class = {}
-    for inst in samples:
-        by_class.setdefault(pamc_size_class(inst.n), []).append(inst)
+    for smp in samples:
+        inst, kind = smp if isinstance(smp, tuple) else (smp, 0)
+        by_class.setdefault(pamc_size_class(inst.n), []).append((inst, kind))
     p = dict(params)
     p["steps"] = 1 << 20          # the throwaway runs never finish
     p.pop("target_cut", None)
@@ -45,10 +48,10 @@ def tune_batch_shapes(batch, samples, params: dict, steps: int = 3, rounds: int 
         hs = []
         tmp = pamc_batch_create(device, stream.cuda_stream)
         try:
-            for inst in insts:
+            for inst, kind in insts:
                 h = pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w, device, stream.cuda_stream)
                 hs.append(h)
-                pamc_init(h, **p)
+                pamc_init(h, **dict(p, kind=kind))
                 pamc_batch_add(tmp, h)
             best = {}
             for _ in range(rounds):          # candidates interleaved, best of the rounds

@@ -47,6 +47,7 @@ class Model:
 
     def init(self, h, **p):
         assert p["steps"] >= 1 << 20 and "target_cut" not in p
+        self.kinds = getattr(self, "kinds", []) + [(dict(self.created)[h.value], p.get("kind", 0))]
 
     def add(self, b, h):
         n = dict(self.created)[h.value]
@@ -115,6 +116,7 @@ def test_tuner_sets_the_fastest_shape_per_class(monkeypatch):
 
     caller = object()
     samples = [types.SimpleNamespace(n=n, row_ptr=None, col=None, w=None) for n in (900, 1500, 12000)]
+    samples[1] = (samples[1], 1)                    # a Max-3-Cut sample, given as (instance, kind)
     chosen = tune.tune_batch_shapes(caller, samples, dict(R=64, sweeps=2, steps=10, target_cut=5))
     assert set(chosen) == {0, 2}
     assert chosen[0][:3] == (2, 4, 2) and chosen[2][:3] == (1, 16, 1)
@@ -124,3 +126,4 @@ def test_tuner_sets_the_fastest_shape_per_class(monkeypatch):
     assert m.shape[(caller, 2)] == (1, 16) and m.lanes[(caller, 2)] == 1 and m.place[(caller, 2)]
     assert (caller, 1) not in m.shape                       # no sample of class 1: untouched
     assert sorted(m.destroyed) == sorted(h for h, _ in m.created)
+    assert sorted(m.kinds) == [(900, 0), (1500, 1), (12000, 0)]     # each sample run as its problem
