@@ -432,3 +432,29 @@ def test_wide_field_range_refusals(pg):
     with pytest.raises(pg.PamcError) as e:
         pg.pamc_create_csr(big.n, big.row_ptr, big.col, big.w)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_maximum_population(pg, rule):
+    """R = 16,384, the largest population pamc_init takes (4,096 replica
+    groups, 1,024 cluster-move targets), against the oracle step by step."""
+    inst = W.torus(12, 12, signed=True, seed=7)
+    ref, _ = compare_run(pg, inst, 6, R=16384, sweeps=2, beta0=0.3, beta1=3.0, rule=rule, stagnation=1, z_rst=0,
+                         cooldown_tau=1, win_short=2, win_long=3, seed=5)
+    assert ref.ctl()["ncm_flipped"] > 0
+
+
+def test_degenerate_sizes_other_placements(pg, monkeypatch):
+    """One vertex, one replica, zero sweeps, with the spin words in device
+    memory and with 16-bit field lanes."""
+    one = W.csr_from_edges(1, np.zeros(0), np.zeros(0), np.zeros(0), "one")
+    monkeypatch.setenv("PAMC_SWEEP_GLOBAL", "1")
+    compare_run(pg, one, 3, R=3, sweeps=2)
+    inst = W.gnm(50, 80, signed=True, seed=3)
+    compare_run(pg, inst, 4, R=1, sweeps=1)
+    compare_run(pg, inst, 3, R=8, sweeps=0)
+    monkeypatch.delenv("PAMC_SWEEP_GLOBAL")
+    pair = W.csr_from_edges(2, np.array([0]), np.array([1]), np.array([127]), "pair127")
+    star = W.csr_from_edges(3, np.array([0, 0]), np.array([1, 2]), np.array([127, -100]), "star227")
+    for g in (pair, star):
+        compare_run(pg, g, 4, R=5, sweeps=2, beta0=0.001, beta1=0.05)
