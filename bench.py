@@ -394,8 +394,6 @@ def run_ours(args):
             "roofline": dict(sweep[0], traffic=profiled_traffic("sweep_torus") if ONLY != "sparse" else None,
                              kernel=kname[0] + f" ({insts[0].name}, R=4096, 10 sweeps per launch)",
                              peak_source=f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)"),
-            "roofline_other_instance": (dict(sweep[1], kernel=kname[1] + f" ({insts[1].name})")
-                                        if len(insts) > 1 else None),
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
