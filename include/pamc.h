@@ -295,6 +295,85 @@ pamc_status pamc_batch_sync(pamc_batch b);
 pamc_status pamc_batch_last_error(pamc_batch b, char *buf, size_t len);
 void pamc_batch_destroy(pamc_batch b);
 
+/* ---- One population split over several processes (one GPU each) ----
+ * The population step of Algorithm 1 (Eq. 1-2) is global over the R
+ * replicas, so a population split over nranks processes exchanges once per
+ * iteration: every process gathers all R energies, computes the same
+ * parent map and controller decisions from them, and receives the parent
+ * replicas of its slots that live elsewhere.  Process `rank` owns slots
+ * [rank R/nranks, (rank + 1) R/nranks); R must be a multiple of 4 nranks.
+ * The random draws are keyed by each replica's index in the whole
+ * population, so the split run equals pamc_step on one handle with the same
+ * parameters, bit for bit (spins, energies, parents, counts, controller, M*).
+ * The library makes no collective call: the caller moves the data
+ * (all-gather of energies, all-to-all of replica rows), in the order below,
+ * on the handle's stream or synchronised with it.  One iteration:
+ *   pamc_shard_energies -> all-gather E_own into E_all (slot order)
+ *   pamc_shard_resample(E_all) -> parent map -> pamc_shard_plan
+ *   pamc_shard_pack -> all-to-all of rows (send_counts / recv_counts)
+ *   pamc_shard_sweep -> all-gather E_own into E_all
+ *   pamc_shard_control(E_all)
+ * (the first all-gather may reuse the last one when no restart redraws the
+ * population: p->z_rst == 0 or p->restart_reinit == 0).  Sparse (CSR)
+ * instances only.  pamc_step, pamc_set_population, pamc_hamming and batches
+ * refuse a split handle; pamc_state returns its own slots; the NCM counters
+ * of pamc_control_state count its own slots. */
+
+/* Own slots of process `rank`: *base = rank * R / nranks, *count = R /
+ * nranks.  PAMC_ERR_ARG unless 0 <= rank < nranks and R % (4 nranks) == 0.
+ * Host only. */
+pamc_status pamc_shard_range(int32_t R, int32_t nranks, int32_t rank, int32_t *base, int32_t *count);
+
+/* pamc_init for this process's share (same parameters on every process,
+ * p->R the whole population).  Draws the own slots of the initial
+ * population. */
+pamc_status pamc_shard_init(pamc_handle h, const pamc_params *p, int32_t rank, int32_t nranks);
+
+/* Copy the own slots' current energies (count int64) to E_own (DEVICE). */
+pamc_status pamc_shard_energies(pamc_handle h, int64_t *E_own);
+
+/* The population step (reweighting by Delta beta, systematic resampling,
+ * NCM target choice; Eq. 1-2 and Algorithm 1) on E_all (DEVICE, R int64:
+ * every process's energies in slot order).  parent (HOST, R int32)
+ * receives the parent map: slot m copies old replica parent[m].
+ * Synchronises the stream. */
+pamc_status pamc_shard_resample(pamc_handle h, const int64_t *E_all, int32_t *parent);
+
+/* Host only: the exchange that parent implies for process `rank`.
+ * send_counts[nranks]: own replicas to send to each process (0 to itself);
+ * send_rows (capacity R - R/nranks): their own-row indices (0 .. count-1),
+ * process by process in rank order, ascending within a process.
+ * recv_counts[nranks]: replicas received from each process, arriving in rank
+ * order, ascending within a process.  local_parent[count]: the source row
+ * of each own slot's parent: an own row (< count), or count + its position
+ * among the received rows.  PAMC_ERR_RANGE on a parent outside [0, R). */
+pamc_status pamc_shard_plan(int32_t R, int32_t nranks, int32_t rank, const int32_t *parent,
+                            int32_t *send_counts, int32_t *send_rows, int32_t *recv_counts,
+                            int32_t *local_parent);
+
+/* Gather the nrows own replicas rows[] (HOST, own-row indices) into sendbuf
+ * (DEVICE, nrows * n int8, caller-owned) for the all-to-all.  Asynchronous. */
+pamc_status pamc_shard_pack(pamc_handle h, const int32_t *rows, int32_t nrows, int8_t *sendbuf);
+
+/* Copy the own slots' parents (local_parent: HOST, from pamc_shard_plan;
+ * imports: DEVICE, nimports received rows of n int8), apply the cluster
+ * moves of the own NCM targets, and run the S sweeps of the own slots
+ * (Algorithm 1).  E_all must still hold the energies given to
+ * pamc_shard_resample.  E_own (DEVICE, count int64, may be NULL) receives
+ * the own energies after the sweeps.  Asynchronous. */
+pamc_status pamc_shard_sweep(pamc_handle h, const int64_t *E_all, const int32_t *local_parent,
+                             const int8_t *imports, int32_t nimports, int64_t *E_own);
+
+/* M* and the controller (Algorithm 1) on E_all (DEVICE, R int64: the
+ * energies after the sweeps, all processes); a restart that re-initialises
+ * redraws the own slots, and E_own (DEVICE, may be NULL) receives their
+ * energies (unchanged without a restart).  Asynchronous. */
+pamc_status pamc_shard_control(pamc_handle h, const int64_t *E_all, int64_t *E_own);
+
+/* M* (the same on every process) and, when this process holds it (*owned =
+ * 1), its configuration (HOST n int8, as pamc_best).  Synchronises. */
+pamc_status pamc_shard_best(pamc_handle h, int64_t *cut, int8_t *spins, int32_t *owned);
+
 /* Size limits of pamc_sweeps_noalloc and the bytes of device memory its
  * file-scope scratch array takes on every GPU that loads the library. */
 #define PAMC_NOALLOC_MAX_N 32768

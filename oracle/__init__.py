@@ -114,6 +114,14 @@ def lib():
             L.orc_get_history.argtypes = [P, P]
             L.orc_sweep_flips.argtypes = [P]
             L.orc_sweep_flips.restype = i64
+            for nm in ("orc_iter_population", "orc_iter_sweeps", "orc_iter_control"):
+                getattr(L, nm).argtypes = [P]
+                getattr(L, nm).restype = None
+            L.orc_set_own.argtypes = [P, i32, i32]
+            L.orc_set_energies.argtypes = [P, P]
+            L.orc_set_rows.argtypes = [P, i32, i32, P]
+            L.orc_best_owned.argtypes = [P]
+            L.orc_best_owned.restype = i32
             _lib = L
     return _lib
 
@@ -372,6 +380,31 @@ class OracleRun:
         out = np.zeros(64, dtype=np.int64)
         lib().orc_get_history(self._h, _ptr(out))
         return out[:self.ctl()["hist_len"]]
+
+    # one population split over several processes (orc_set_own and the
+    # three parts of an iteration; see pamc_oracle.h)
+    def iter_population(self):
+        lib().orc_iter_population(self._h)
+
+    def iter_sweeps(self):
+        lib().orc_iter_sweeps(self._h)
+
+    def iter_control(self):
+        lib().orc_iter_control(self._h)
+
+    def set_own(self, lo: int, hi: int):
+        lib().orc_set_own(self._h, int(lo), int(hi))
+
+    def set_energies(self, E):
+        e = np.ascontiguousarray(E, dtype=np.int64).reshape(self.R)
+        lib().orc_set_energies(self._h, _ptr(e))
+
+    def set_rows(self, r0: int, rows):
+        rw = np.ascontiguousarray(rows, dtype=np.int8).reshape(-1, self.n)
+        lib().orc_set_rows(self._h, int(r0), int(rw.shape[0]), _ptr(rw))
+
+    def best_owned(self) -> bool:
+        return bool(lib().orc_best_owned(self._h))
 
     def ncm_targets(self) -> np.ndarray:
         out = np.zeros(self.R, dtype=np.int32)

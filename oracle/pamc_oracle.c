@@ -219,6 +219,8 @@ struct orc_state {
     int64_t sweep_flips;       /* Ising: replica spins the sweeps changed */
     uint8_t *rmask;            /* sampled sweeps: sweep replica r iff rmask[r] */
     int8_t *r_spins;           /* sampled sweeps: the other replicas' results */
+    int32_t own_lo, own_hi;    /* slots this state moves (NCM, sweeps); all R unless split */
+    int32_t best_owned;        /* the last M* improvement came from an own slot */
 };
 
 static int32_t nf(const orc_state *st) { return st->p.kind == 1 ? st->p.K : 1; }
@@ -347,6 +349,9 @@ orc_state *orc_create(int32_t n, const int32_t *rp, const int32_t *col, const in
     st->n_ncm_targets = 0;
     st->rmask = NULL;
     st->r_spins = NULL;
+    st->own_lo = 0;
+    st->own_hi = R;
+    st->best_owned = 1;
     st->dbeta = p->steps > 1 ? (p->beta1 - p->beta0) / (double)(p->steps - 1) : 0.0;
     st->t = 0; st->z = 1; st->cycle = 0; st->cooldown = 0; st->enable_cm = 0; st->done = 0;
     st->beta = p->beta0; st->delta = st->dbeta;
@@ -609,7 +614,10 @@ int orc_control(orc_ctl *c, const orc_params *p, double dbeta, int64_t mstar) {
 /* ------------------------------------------------------------------ */
 /* One iteration of Algorithm 1                                        */
 /* ------------------------------------------------------------------ */
-static void orc_iteration(orc_state *st) {
+/* Algorithm 1, one iteration, in its three parts: the population step
+ * (resampling at the new beta, then the cluster moves), the S sweeps, and
+ * M* with the controller. */
+void orc_iter_population(orc_state *st) {
     int32_t n = st->n, R = st->p.R, F = nf(st);
     /* Reading: the Potts update follows Eq. 8 literally (P ~ e^{beta syn_k}),
      * which samples e^{-(beta/2) E} with E of Eq. 6, so the reweighting uses
@@ -642,6 +650,7 @@ static void orc_iteration(orc_state *st) {
                 for (int32_t q = 0; q < ntop; ++q) {
                     int32_t r = idx[q];
                     st->ncm_targets[st->n_ncm_targets++] = r;
+                    if (r < st->own_lo || r >= st->own_hi) continue;   /* another process's slot */
                     int64_t before = st->E[r];
                     st->ncm_flipped += orc_ncm_replica(n, st->rp, st->col, st->J,
                                                        st->s + (size_t)r * n, st->h + (size_t)r * n,
@@ -659,11 +668,15 @@ static void orc_iteration(orc_state *st) {
             st->cooldown = st->p.cooldown_tau;
         }
     }
+}
+
+void orc_iter_sweeps(orc_state *st) {
+    int32_t n = st->n, R = st->p.R;
     /* S sweeps at the current beta */
     int32_t *perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     for (int32_t sw = 0; sw < st->p.sweeps; ++sw) {
         orc_permutation(n, st->p.seed, st->t, sw, perm);
-        for (int32_t r = 0; r < R; ++r) {
+        for (int32_t r = st->own_lo; r < st->own_hi; ++r) {
             if (st->rmask && !st->rmask[r]) continue;
             if (st->p.kind == 0) orc_sweep_ising(st, r, perm, sw);
             else if (st->p.rule == 2) orc_sweep_potts_softmax(st, r, perm, sw);
@@ -678,6 +691,10 @@ static void orc_iteration(orc_state *st) {
                 memcpy(st->s + (size_t)r * n, st->r_spins + (size_t)r * n, (size_t)n);
                 orc_refresh_replica(st, r);
             }
+}
+
+void orc_iter_control(orc_state *st) {
+    int32_t n = st->n, R = st->p.R;
     /* M* <- max(M*, max Cut(P)); cut = (W - E)/2 */
     int32_t rbest = 0;
     for (int32_t r = 1; r < R; ++r)
@@ -685,7 +702,8 @@ static void orc_iteration(orc_state *st) {
     int64_t cut = (st->W - st->E[rbest]) / 2;
     if (cut > st->mstar) {
         st->mstar = cut;
-        memcpy(st->best, st->s + (size_t)rbest * n, (size_t)n);
+        st->best_owned = rbest >= st->own_lo && rbest < st->own_hi;
+        if (st->best_owned) memcpy(st->best, st->s + (size_t)rbest * n, (size_t)n);
     }
     orc_ctl c;
     c.z = st->z; c.cycle = st->cycle; c.cooldown = st->cooldown; c.enable_cm = st->enable_cm;
@@ -698,6 +716,12 @@ static void orc_iteration(orc_state *st) {
     if (restart && st->p.restart_reinit) orc_init_population(st, st->t + 1);
     st->t += 1;
     if (st->p.target_cut >= 0 && st->mstar >= st->p.target_cut) st->done = 1;
+}
+
+static void orc_iteration(orc_state *st) {
+    orc_iter_population(st);
+    orc_iter_sweeps(st);
+    orc_iter_control(st);
 }
 
 int32_t orc_step(orc_state *st, int32_t nsteps) {
@@ -789,3 +813,22 @@ void orc_get_history(const orc_state *st, int64_t *hist) {
 }
 
 int64_t orc_sweep_flips(const orc_state *st) { return st->sweep_flips; }
+
+void orc_set_own(orc_state *st, int32_t lo, int32_t hi) {
+    if (lo < 0) lo = 0;
+    if (hi > st->p.R) hi = st->p.R;
+    st->own_lo = lo;
+    st->own_hi = hi < lo ? lo : hi;
+}
+void orc_set_energies(orc_state *st, const int64_t *E) {
+    memcpy(st->E, E, sizeof(int64_t) * (size_t)st->p.R);
+}
+void orc_set_rows(orc_state *st, int32_t r0, int32_t count, const int8_t *rows) {
+    for (int32_t i = 0; i < count; ++i) {
+        int32_t r = r0 + i;
+        if (r < 0 || r >= st->p.R) continue;
+        memcpy(st->s + (size_t)r * st->n, rows + (size_t)i * st->n, (size_t)st->n);
+        orc_refresh_replica(st, r);
+    }
+}
+int32_t orc_best_owned(const orc_state *st) { return st->best_owned; }

@@ -173,6 +173,26 @@ void orc_get_history(const orc_state *st, int64_t *hist);
  * chosen (lowest (energy, slot) first); *count = 0 when none did. */
 void orc_get_ncm_targets(const orc_state *st, int32_t *targets, int32_t *count);
 
+/* ---- One population split over several processes ----
+ * orc_step runs orc_iter_population (resampling at the new beta, then the
+ * cluster moves), orc_iter_sweeps (the S sweeps) and orc_iter_control (M*,
+ * the controller, a restart's re-draw) in turn.  A process that holds slots
+ * [lo, hi) of the population calls orc_set_own(lo, hi): the cluster moves
+ * and sweeps then touch those slots only (the NCM target list still covers
+ * the whole population), and the best configuration is copied only when
+ * the replica holding the new M* is an own slot (orc_best_owned).  Between
+ * the parts it loads the energies of every process (orc_set_energies, R
+ * values: resampling, the choice of NCM targets and M* read them) and the
+ * replicas it received (orc_set_rows: spins, with fields and energies
+ * recomputed from the definition). */
+void orc_iter_population(orc_state *st);
+void orc_iter_sweeps(orc_state *st);
+void orc_iter_control(orc_state *st);
+void orc_set_own(orc_state *st, int32_t lo, int32_t hi);
+void orc_set_energies(orc_state *st, const int64_t *E);
+void orc_set_rows(orc_state *st, int32_t r0, int32_t count, const int8_t *rows);
+int32_t orc_best_owned(const orc_state *st);
+
 /* Energy from the definition (i<j pairs), used by the pins. */
 int64_t orc_energy_ising(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *J,
                          const int8_t *s);

@@ -27,7 +27,9 @@ __all__ = [
     "pamc_batch_graph_builds", "pamc_batch_sync", "pamc_batch_destroy", "pamc_size_class",
     "pamc_batch_set_shape", "pamc_batch_get_shape", "pamc_batch_set_lanes", "pamc_batch_get_lanes", "pamc_hamming", "pamc_lineage", "pamc_set_population", "pamc_fields",
     "pamc_control_history", "pamc_sweep_mode", "pamc_set_sweep_timing", "pamc_sweep_stats",
-    "pamc_batch_set_placement", "pamc_batch_get_placement",
+    "pamc_batch_set_placement", "pamc_batch_get_placement", "pamc_shard_range", "pamc_shard_init",
+    "pamc_shard_energies", "pamc_shard_resample", "pamc_shard_plan", "pamc_shard_pack", "pamc_shard_sweep",
+    "pamc_shard_control", "pamc_shard_best",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -174,6 +176,18 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_batch_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     L.pamc_batch_destroy.argtypes = [P]
     L.pamc_batch_destroy.restype = None
+    L.pamc_shard_range.argtypes = [i32, i32, i32, P, P]
+    L.pamc_shard_init.argtypes = [P, ctypes.POINTER(Params), i32, i32]
+    L.pamc_shard_energies.argtypes = [P, P]
+    L.pamc_shard_resample.argtypes = [P, P, P]
+    L.pamc_shard_plan.argtypes = [i32, i32, i32, P, P, P, P, P]
+    L.pamc_shard_pack.argtypes = [P, P, i32, P]
+    L.pamc_shard_sweep.argtypes = [P, P, P, P, i32, P]
+    L.pamc_shard_control.argtypes = [P, P, P]
+    L.pamc_shard_best.argtypes = [P, P, P, P]
+    for nm in ("pamc_shard_range", "pamc_shard_init", "pamc_shard_energies", "pamc_shard_resample",
+               "pamc_shard_plan", "pamc_shard_pack", "pamc_shard_sweep", "pamc_shard_control", "pamc_shard_best"):
+        getattr(L, nm).restype = ctypes.c_int
     for nm in ("pamc_batch_create", "pamc_batch_add", "pamc_batch_step", "pamc_batch_sync",
                "pamc_batch_last_error"):
         getattr(L, nm).restype = ctypes.c_int
@@ -270,7 +284,7 @@ def pamc_create_dense(n, w, device: int = 0, stream=None):
 def _set_R(h, R):
     d = _dims.get(getattr(h, "value", None))
     if d is not None:
-        d[1] = int(R)
+        _dims[h.value] = [d[0], int(R)]
 
 
 def pamc_init(h, **params):
@@ -443,6 +457,119 @@ def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed,
     import torch
     with torch.cuda.device(dev):
         call()
+
+
+# ---------------------------------------------------------------- split population
+def _dev_arg(x, name, dtype, count, allow_none=False):
+    """A contiguous CUDA tensor of dtype holding at least count elements ->
+    its device address."""
+    if x is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not getattr(x, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(x.dtype) != "torch." + dtype:
+        raise ValueError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if x.numel() < count:
+        raise ValueError(f"{name} holds {x.numel()} elements, the call uses {count}")
+    return ctypes.c_void_p(int(x.data_ptr()))
+
+
+def _shard_dims(h):
+    d = _dims.get(getattr(h, "value", None))
+    if d is None or len(d) < 4:
+        raise ValueError("not a split-population handle made by pamc_shard_init")
+    return d   # [n, own count, R, nranks]
+
+
+def pamc_shard_range(R: int, nranks: int, rank: int):
+    """(base, count): the own slots of process rank (host only)."""
+    L = load(torch_allocator=False)
+    b = np.zeros(1, dtype=np.int32)
+    c = np.zeros(1, dtype=np.int32)
+    rc = L.pamc_shard_range(int(R), int(nranks), int(rank), _ptr(b), _ptr(c))
+    if rc != 0:
+        raise PamcError(rc, "R must be a multiple of 4 nranks and 0 <= rank < nranks")
+    return int(b[0]), int(c[0])
+
+
+def pamc_shard_init(h, rank: int, nranks: int, **params):
+    p = make_params(**params)
+    _check(_lib.pamc_shard_init(h, ctypes.byref(p), int(rank), int(nranks)), h)
+    d = _dims.get(getattr(h, "value", None))
+    if d is not None:
+        _, count = pamc_shard_range(p.R, nranks, rank)
+        _dims[h.value] = [d[0], count, int(p.R), int(nranks)]
+    return p
+
+
+def pamc_shard_energies(h, E_own):
+    _, c, _, _ = _shard_dims(h)
+    _check(_lib.pamc_shard_energies(h, _dev_arg(E_own, "E_own", "int64", c)), h)
+
+
+def pamc_shard_resample(h, E_all) -> np.ndarray:
+    _, _, R, _ = _shard_dims(h)
+    parent = np.zeros(R, dtype=np.int32)
+    _check(_lib.pamc_shard_resample(h, _dev_arg(E_all, "E_all", "int64", R), _ptr(parent)), h)
+    return parent
+
+
+def pamc_shard_plan(R: int, nranks: int, rank: int, parent):
+    """(send_counts, send_rows, recv_counts, local_parent) for process rank
+    (host only; see include/pamc.h)."""
+    L = load(torch_allocator=False)
+    par = np.ascontiguousarray(parent, dtype=np.int32).reshape(-1)
+    if par.shape[0] != int(R):
+        raise ValueError(f"parent must hold R = {int(R)} entries, got {par.shape[0]}")
+    _, c = pamc_shard_range(R, nranks, rank)
+    sc = np.zeros(int(nranks), dtype=np.int32)
+    rc_ = np.zeros(int(nranks), dtype=np.int32)
+    rows = np.zeros(max(int(R) - c, 1), dtype=np.int32)
+    lp = np.zeros(c, dtype=np.int32)
+    rc = L.pamc_shard_plan(int(R), int(nranks), int(rank), _ptr(par), _ptr(sc), _ptr(rows), _ptr(rc_), _ptr(lp))
+    if rc != 0:
+        raise PamcError(rc, "pamc_shard_plan: parent entries must lie in [0, R)")
+    return sc, rows[:int(sc.sum())].copy(), rc_, lp
+
+
+def pamc_shard_pack(h, rows, sendbuf):
+    n, c, R, _ = _shard_dims(h)
+    r = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1)
+    k = int(r.shape[0])
+    buf = _dev_arg(sendbuf, "sendbuf", "int8", k * n) if k > 0 else None
+    _check(_lib.pamc_shard_pack(h, _ptr(r) if k > 0 else None, k, buf), h)
+
+
+def pamc_shard_sweep(h, E_all, local_parent, imports, nimports: int, E_own=None):
+    n, c, R, _ = _shard_dims(h)
+    lp = np.ascontiguousarray(local_parent, dtype=np.int32).reshape(-1)
+    if lp.shape[0] != c:
+        raise ValueError(f"local_parent must hold the {c} own slots, got {lp.shape[0]}")
+    k = int(nimports)
+    imp = _dev_arg(imports, "imports", "int8", k * n) if k > 0 else None
+    _check(_lib.pamc_shard_sweep(h, _dev_arg(E_all, "E_all", "int64", R), _ptr(lp), imp, k,
+                                 _dev_arg(E_own, "E_own", "int64", c, allow_none=True)), h)
+
+
+def pamc_shard_control(h, E_all, E_own=None):
+    _, c, R, _ = _shard_dims(h)
+    _check(_lib.pamc_shard_control(h, _dev_arg(E_all, "E_all", "int64", R),
+                                   _dev_arg(E_own, "E_own", "int64", c, allow_none=True)), h)
+
+
+def pamc_shard_best(h):
+    """(cut, spins or None, owned): M* and, on the process holding it, its
+    configuration."""
+    n = _shard_dims(h)[0]
+    cut = np.zeros(1, dtype=np.int64)
+    owned = np.zeros(1, dtype=np.int32)
+    spins = np.zeros(n, dtype=np.int8)
+    _check(_lib.pamc_shard_best(h, _ptr(cut), _ptr(spins), _ptr(owned)), h)
+    return int(cut[0]), (spins if owned[0] else None), bool(owned[0])
 
 
 def pamc_set_population(h, spins):

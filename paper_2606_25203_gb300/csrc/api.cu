@@ -30,9 +30,11 @@ cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl,
 cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
                        const int8_t *src, const int64_t *E_src, const int32_t *parent,
                        const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey,
-                       DevCtl *ctl, cudaStream_t st);
+                       DevCtl *ctl, cudaStream_t st, int32_t base = 0, int32_t count = -1,
+                       const int32_t *prow = nullptr);
 cudaError_t launch_control(int32_t n, int64_t W, const pamc_params &p, const int64_t *E,
-                           const int8_t *spins, int8_t *best, DevCtl *ctl, cudaStream_t st);
+                           const int8_t *spins, int8_t *best, DevCtl *ctl, cudaStream_t st,
+                           int32_t base = 0, int32_t count = -1);
 size_t prep_smem_bytes(int32_t R);
 }  // namespace pamc
 
@@ -111,6 +113,15 @@ struct pamc_handle_s {
     size_t sweep_ev_used = 0;      // pairs recorded and not yet folded
     double sweep_ms = 0.0;         // time of the pairs folded since the last read
     int64_t sweep_timed = 0;       // sweep launches timed since the last read
+    // a population split over processes (pamc_shard_init): this handle owns
+    // slots [sh_base, sh_base + sh_count) of the p.R replicas; the energies,
+    // parent map, counts and controller cover all p.R, the spins only its own
+    // slots and, during a step, the foreign parents it received
+    bool sharded = false;
+    int32_t sh_rank = 0, sh_nranks = 1, sh_base = 0, sh_count = 0;
+    int sh_phase = 0;              // next call: 0 resample, 1 sweep, 2 control
+    int32_t *d_plocal = nullptr;   // [sh_count] source row of each own slot's parent
+    int32_t *d_rows = nullptr;     // [p.R] own rows to send
     char err[256] = "";
 };
 
@@ -245,6 +256,9 @@ void release_run(pamc_handle h) {
     h->d_spins[0] = h->d_spins[1] = nullptr;
     h->d_gsp = nullptr;
     h->gsp = false;
+    h->sharded = false;
+    h->sh_rank = 0; h->sh_nranks = 1; h->sh_base = 0; h->sh_count = 0; h->sh_phase = 0;
+    h->d_plocal = h->d_rows = nullptr;
 }
 
 // Words of the replica groups' spins in device memory (n_pad per group).
@@ -596,7 +610,9 @@ pamc_status pamc_create_dense(int32_t n, const int8_t *w, int w_on_device, int c
     return PAMC_OK;
 }
 
-pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
+// nranks = 0: the whole population on this handle (pamc_init); else this
+// handle's share of a population split over nranks processes.
+static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, int32_t nranks) {
     if (!h || !pp) return fail(h, PAMC_ERR_ARG, "null handle or params");
     pamc_params p = *pp;
     if (p.K == 0) p.K = 3;
@@ -616,6 +632,11 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     if (!(p.beta0 == p.beta0) || !(p.beta1 == p.beta1)) return fail(h, PAMC_ERR_ARG, "beta is NaN");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (nranks > 0 && h->dense)
+        return fail(h, PAMC_ERR_ARG, "a split population needs a sparse (CSR) instance");
+    int32_t base = 0, own = p.R;   // own slots [base, base + own)
+    if (nranks > 0 && pamc_shard_range(p.R, nranks, rank, &base, &own) != PAMC_OK)
+        return fail(h, PAMC_ERR_ARG, "split population: need 0 <= rank < nranks and R a multiple of 4 nranks");
     if (h->dense) return init_dense(h, p);
     if (p.kind == 1 && h->H > kByteLaneMaxH)
         return fail(h, PAMC_ERR_RANGE, "Max-3-Cut runs need sum_j |w_ij| <= %d (this instance: %d)", kByteLaneMaxH,
@@ -626,9 +647,11 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     const int32_t ntop = std::min(p.n_top, R);
     const size_t tabn = p.kind == 0 ? (size_t)(2 * h->H + 1)
                                     : (size_t)(4 * h->H + 1) * (4 * h->H + 1) + (4 * h->H + 1);
-    bool ok = alloc_n(h, h->d_spins[0], (size_t)R * n, h->bufs) &&
-              alloc_n(h, h->d_spins[1], (size_t)R * n, h->bufs) &&
-              alloc_n(h, h->d_E[0], R, h->bufs) && alloc_n(h, h->d_E[1], R, h->bufs) &&
+    // spin rows: the own slots, and as many again for received parents
+    const size_t rows = nranks > 0 ? 2 * (size_t)own : (size_t)R;
+    bool ok = alloc_n(h, h->d_spins[0], rows * n, h->bufs) &&
+              alloc_n(h, h->d_spins[1], rows * n, h->bufs) &&
+              alloc_n(h, h->d_E[0], own, h->bufs) && alloc_n(h, h->d_E[1], own, h->bufs) &&
               alloc_n(h, h->d_q, R, h->bufs) &&
               alloc_n(h, h->d_parent, R, h->bufs) && alloc_n(h, h->d_count, R, h->bufs) &&
               alloc_n(h, h->d_fam, 2 * (size_t)R, h->bufs) &&
@@ -650,6 +673,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     if (ok && p.stagnation && p.kind == 0)
         ok = alloc_n(h, h->d_ncm_buf, (size_t)ntop * n, h->bufs) &&
              alloc_n(h, h->d_nkey, (size_t)ntop * n, h->bufs);
+    if (ok && nranks > 0) ok = alloc_n(h, h->d_plocal, own, h->bufs) && alloc_n(h, h->d_rows, R, h->bufs);
     if (!ok) {
         release_run(h);
         return fail(h, PAMC_ERR_OOM, "device allocation of the population failed");
@@ -676,8 +700,8 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
         e = cudaMemcpyAsync(h->d_ncm_idx, minus.data(), sizeof(int32_t) * R, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_best, 0, n, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "initial state upload");
-    e = launch_init(p.kind, p.K, n, h->d_rp, h->d_adj, R, p.seed, 0, 0, h->d_ctl, h->W, h->d_spins[0],
-                    h->d_E[0], h->stream);
+    e = launch_init(p.kind, p.K, n, h->d_rp, h->d_adj, own, p.seed, 0, 0, h->d_ctl, h->W, h->d_spins[0],
+                    h->d_E[0], h->stream, base);
     if (e != cudaSuccess) return cuda_fail(h, e, "initial population");
     h->launches += 2;
     // host copies of the host-side vectors must stay alive until the copies ran
@@ -700,7 +724,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    h->cfg = choose_cfg(sweep_kind(p), n, R, h->H, avg_level, (double)h->nnz / std::max(n, 1), sms, h->ell_w);
+    h->cfg = choose_cfg(sweep_kind(p), n, own, h->H, avg_level, (double)h->nnz / std::max(n, 1), sms, h->ell_w);
     // Ising groups whose spin words do not fit shared memory (or all of them
     // with PAMC_SWEEP_GLOBAL=1) keep the words in device memory: one lane per
     // vertex, one group per CTA
@@ -710,7 +734,7 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
     if (p.kind == 0 && ((genv && genv[0] == '1') || sweep_smem_bytes(0, n, h->H, h->cfg) > kSmemMax)) {
         if (!getenv("PAMC_SWEEP_CFG")) h->cfg = SweepCfg{1, 16, 1};
         h->cfg.lanes_per_vertex = 1;
-        if (!alloc_n(h, h->d_gsp, gsp_words(n, R) * (wide ? 2 : 1), h->bufs)) {
+        if (!alloc_n(h, h->d_gsp, gsp_words(n, own) * (wide ? 2 : 1), h->bufs)) {
             release_run(h);
             return fail(h, PAMC_ERR_OOM, "device allocation of the group spin words failed");
         }
@@ -721,13 +745,29 @@ pamc_status pamc_init(pamc_handle h, const pamc_params *pp) {
         return fail(h, PAMC_ERR_RANGE, "n = %d: one replica group's labels exceed shared memory", n);
     }
     h->host_t = 0;
+    if (nranks > 0) {
+        h->sharded = true;
+        h->sh_rank = rank;
+        h->sh_nranks = nranks;
+        h->sh_base = base;
+        h->sh_count = own;
+        h->sh_phase = 0;
+    }
     h->initialized = 1;
     return PAMC_OK;
+}
+
+pamc_status pamc_init(pamc_handle h, const pamc_params *pp) { return init_run(h, pp, 0, 0); }
+
+pamc_status pamc_shard_init(pamc_handle h, const pamc_params *p, int32_t rank, int32_t nranks) {
+    if (nranks < 1) return fail(h, PAMC_ERR_ARG, "nranks must be >= 1");
+    return init_run(h, p, rank, nranks);
 }
 
 pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
     if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
     if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_step before pamc_init");
+    if (h->sharded) return fail(h, PAMC_ERR_STATE, "a split population steps through the pamc_shard_* calls");
     if (nsteps < 0) return fail(h, PAMC_ERR_ARG, "nsteps < 0");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
@@ -791,6 +831,157 @@ pamc_status pamc_sync(pamc_handle h) {
     return PAMC_OK;
 }
 
+// ---------------------------------------------------------------- split population
+// One iteration of Algorithm 1 in three calls, with the caller's exchange
+// between them (the calls of pamc_step, in the same order and with the same
+// random streams; every process runs the population step and the controller
+// on all R energies and so takes the same decisions).
+
+static pamc_status read_ctl(pamc_handle h, DevCtl &c);
+
+static pamc_status shard_check(pamc_handle h, int phase, const char *what) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    if (!h->initialized || !h->sharded) return fail(h, PAMC_ERR_STATE, "%s: no split population initialised", what);
+    if (h->sh_phase != phase)
+        return fail(h, PAMC_ERR_STATE, "%s out of order (expected %s next)", what,
+                    h->sh_phase == 0 ? "pamc_shard_resample" : h->sh_phase == 1 ? "pamc_shard_sweep"
+                                                                                : "pamc_shard_control");
+    const cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    return PAMC_OK;
+}
+
+pamc_status pamc_shard_energies(pamc_handle h, int64_t *E_own) {
+    pamc_status s = shard_check(h, 0, "pamc_shard_energies");
+    if (s != PAMC_OK) return s;
+    if (!E_own) return fail(h, PAMC_ERR_ARG, "null E_own");
+    const cudaError_t e = cudaMemcpyAsync(E_own, h->d_E[h->host_t & 1], sizeof(int64_t) * (size_t)h->sh_count,
+                                          cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pamc_shard_energies");
+    return PAMC_OK;
+}
+
+pamc_status pamc_shard_resample(pamc_handle h, const int64_t *E_all, int32_t *parent) {
+    pamc_status s = shard_check(h, 0, "pamc_shard_resample");
+    if (s != PAMC_OK) return s;
+    if (!E_all || !parent) return fail(h, PAMC_ERR_ARG, "null E_all or parent");
+    const pamc_params &p = h->p;
+    const int64_t t = h->host_t;
+    if (t > INT32_MAX - 2) return fail(h, PAMC_ERR_RANGE, "step counter overflow");
+    if (p.sweeps > 0 && t >= h->sched_end) {
+        launch_schedule(h->n, h->d_rp, h->d_adj, p.seed, (int32_t)t, kSchedSlots, p.sweeps, 0, kSchedSlots,
+                        h->d_order, h->d_lvl, h->d_nlev, h->d_skey, h->d_scnt, h->stream, h->d_ell, h->ell_w,
+                        h->d_pos);
+        h->sched_end = t + kSchedSlots;
+        h->launches += 1;
+    }
+    cudaError_t e = launch_prep(p, E_all, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
+                                h->d_q, h->stream);
+    if (e == cudaSuccess) e = launch_tables(p.kind, p.rule, h->H, h->d_ctl, h->d_tab, h->stream);
+    h->launches += 3;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(parent, h->d_parent, sizeof(int32_t) * (size_t)p.R, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pamc_shard_resample");
+    h->sh_phase = 1;
+    return PAMC_OK;
+}
+
+pamc_status pamc_shard_pack(pamc_handle h, const int32_t *rows, int32_t nrows, int8_t *sendbuf) {
+    pamc_status s = shard_check(h, 1, "pamc_shard_pack");
+    if (s != PAMC_OK) return s;
+    const int32_t c = h->sh_count;
+    if (nrows < 0 || nrows > h->p.R - c) return fail(h, PAMC_ERR_ARG, "nrows must be in [0, R - own slots]");
+    if (nrows == 0) return PAMC_OK;
+    if (!rows || !sendbuf) return fail(h, PAMC_ERR_ARG, "null rows or sendbuf");
+    for (int32_t i = 0; i < nrows; ++i)
+        if (rows[i] < 0 || rows[i] >= c) return fail(h, PAMC_ERR_RANGE, "row %d out of range", rows[i]);
+    cudaError_t e = cudaMemcpyAsync(h->d_rows, rows, sizeof(int32_t) * (size_t)nrows, cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess) e = launch_gather_rows(h->n, h->d_rows, nrows, h->d_spins[h->host_t & 1], sendbuf, h->stream);
+    h->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(h, e, "pamc_shard_pack");
+    return PAMC_OK;
+}
+
+pamc_status pamc_shard_sweep(pamc_handle h, const int64_t *E_all, const int32_t *local_parent,
+                             const int8_t *imports, int32_t nimports, int64_t *E_own) {
+    pamc_status s = shard_check(h, 1, "pamc_shard_sweep");
+    if (s != PAMC_OK) return s;
+    const int32_t c = h->sh_count, n = h->n;
+    if (!E_all || !local_parent) return fail(h, PAMC_ERR_ARG, "null E_all or local_parent");
+    if (nimports < 0 || nimports > c) return fail(h, PAMC_ERR_ARG, "nimports must be in [0, own slots]");
+    if (nimports > 0 && !imports) return fail(h, PAMC_ERR_ARG, "null imports");
+    for (int32_t m = 0; m < c; ++m)
+        if (local_parent[m] < 0 || local_parent[m] >= c + nimports)
+            return fail(h, PAMC_ERR_RANGE, "local_parent[%d] = %d out of range", m, local_parent[m]);
+    const pamc_params &p = h->p;
+    const int64_t t = h->host_t;
+    int8_t *src = h->d_spins[t & 1], *dst = h->d_spins[(t + 1) & 1];
+    int64_t *Ed = h->d_E[(t + 1) & 1];
+    cudaError_t e = cudaMemcpyAsync(h->d_plocal, local_parent, sizeof(int32_t) * (size_t)c, cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess && nimports > 0)
+        e = cudaMemcpyAsync(src + (size_t)c * n, imports, (size_t)nimports * n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess && p.stagnation && p.kind == 0) {
+        e = launch_ncm(n, h->d_rp, h->d_adj, p, src, E_all, h->d_parent, h->d_targets, h->d_ncm_buf, h->d_nkey,
+                       h->d_ctl, h->stream, h->sh_base, c, h->d_plocal);
+        h->launches += 1;
+    }
+    pamc_params pl = p;   // the sweep sees the own slots only
+    pl.R = c;
+    SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w};
+    if (e == cudaSuccess) e = sweep_timer(h, false);
+    if (e == cudaSuccess)
+        e = launch_sweep(sweep_kind(p), p.rule, n, h->d_rp, h->d_adj, h->H, pl, (int32_t)t,
+                         (int32_t)(t % kSchedSlots), sv, h->d_tab, src, h->d_plocal, h->d_ncm_buf,
+                         h->d_ncm_idx + h->sh_base, dst, Ed, h->d_ctl, h->cfg, h->W, h->stream,
+                         h->gsp ? h->d_gsp : nullptr, h->sh_base);
+    if (e == cudaSuccess) e = sweep_timer(h, true);
+    h->launches += 1;
+    if (e == cudaSuccess && E_own)
+        e = cudaMemcpyAsync(E_own, Ed, sizeof(int64_t) * (size_t)c, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pamc_shard_sweep");
+    h->sh_phase = 2;
+    return PAMC_OK;
+}
+
+pamc_status pamc_shard_control(pamc_handle h, const int64_t *E_all, int64_t *E_own) {
+    pamc_status s = shard_check(h, 2, "pamc_shard_control");
+    if (s != PAMC_OK) return s;
+    if (!E_all) return fail(h, PAMC_ERR_ARG, "null E_all");
+    const pamc_params &p = h->p;
+    const int32_t c = h->sh_count, n = h->n;
+    const int64_t t = h->host_t;
+    int8_t *dst = h->d_spins[(t + 1) & 1];
+    int64_t *Ed = h->d_E[(t + 1) & 1];
+    cudaError_t e = launch_control(n, h->W, p, E_all, dst, h->d_best, h->d_ctl, h->stream, h->sh_base, c);
+    h->launches += 1;
+    if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
+        e = launch_init(p.kind, p.K, n, h->d_rp, h->d_adj, c, p.seed, (int32_t)(t + 1), 1, h->d_ctl, h->W, dst, Ed,
+                        h->stream, h->sh_base);
+        h->launches += 2;
+    }
+    if (e == cudaSuccess && E_own)
+        e = cudaMemcpyAsync(E_own, Ed, sizeof(int64_t) * (size_t)c, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pamc_shard_control");
+    h->host_t = t + 1;
+    h->sh_phase = 0;
+    return PAMC_OK;
+}
+
+pamc_status pamc_shard_best(pamc_handle h, int64_t *cut, int8_t *spins, int32_t *owned) {
+    if (!h) return fail(h, PAMC_ERR_ARG, "null handle");
+    if (!h->initialized || !h->sharded) return fail(h, PAMC_ERR_STATE, "pamc_shard_best: no split population");
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    if (owned) *owned = c.best_owned;
+    if (cut) *cut = c.mstar;
+    if (spins && c.best_owned) return pamc_best(h, nullptr, spins);
+    return PAMC_OK;
+}
+
 pamc_status pamc_run(pamc_handle h, const pamc_params *p) {
     pamc_status s = pamc_init(h, p);
     if (s != PAMC_OK) return s;
@@ -814,6 +1005,8 @@ pamc_status pamc_best(pamc_handle h, int64_t *cut, int8_t *spins) {
     pamc_status s = read_ctl(h, c);
     if (s != PAMC_OK) return s;
     if (cut) *cut = c.mstar;
+    if (spins && h->sharded && !c.best_owned)
+        return fail(h, PAMC_ERR_STATE, "the best configuration is held by another process (pamc_shard_best)");
     if (spins) {
         std::vector<int8_t> b(h->n);
         cudaError_t e = cudaMemcpy(b.data(), h->d_best, h->n, cudaMemcpyDeviceToHost);
@@ -839,15 +1032,19 @@ pamc_status pamc_state(pamc_handle h, int8_t *spins, int64_t *E, int32_t *parent
     DevCtl c;
     pamc_status s = read_ctl(h, c);
     if (s != PAMC_OK) return s;
+    if (h->sharded && h->sh_phase != 0)
+        return fail(h, PAMC_ERR_STATE, "pamc_state in the middle of a split-population step");
     const int cur = c.t & 1;
-    const size_t R = (size_t)h->p.R;
+    // a split population: the own slots (their parents as indices into all R)
+    const size_t R = (size_t)(h->sharded ? h->sh_count : h->p.R);
+    const size_t off = h->sharded ? (size_t)h->sh_base : 0;
     cudaError_t e = cudaSuccess;
     if (spins) e = cudaMemcpy(spins, h->d_spins[cur], R * h->n, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && E) e = cudaMemcpy(E, h->d_E[cur], R * sizeof(int64_t), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && parents)
-        e = cudaMemcpy(parents, h->d_parent, R * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(parents, h->d_parent + off, R * sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && counts)
-        e = cudaMemcpy(counts, h->d_count, R * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(counts, h->d_count + off, R * sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "state readback");
     return PAMC_OK;
 }
@@ -855,6 +1052,7 @@ pamc_status pamc_state(pamc_handle h, int8_t *spins, int64_t *E, int32_t *parent
 pamc_status pamc_set_population(pamc_handle h, const int8_t *spins) {
     if (!h || !spins) return fail(h, PAMC_ERR_ARG, "null argument");
     if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_set_population before pamc_init");
+    if (h->sharded) return fail(h, PAMC_ERR_STATE, "pamc_set_population: the population is split over processes");
     DevCtl c;
     pamc_status s = read_ctl(h, c);
     if (s != PAMC_OK) return s;
@@ -937,6 +1135,7 @@ pamc_status pamc_control_history(pamc_handle h, int64_t *hist, int32_t *hist_len
 pamc_status pamc_hamming(pamc_handle h, int64_t *hist, int64_t *sum) {
     if (!h || !hist || !sum) return fail(h, PAMC_ERR_ARG, "null argument");
     if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_hamming before pamc_init");
+    if (h->sharded) return fail(h, PAMC_ERR_STATE, "pamc_hamming: the population is split over processes");
     if (h->p.kind != 0) return fail(h, PAMC_ERR_ARG, "Hamming distances are defined for Ising (Max-Cut) runs");
     DevCtl c;
     pamc_status s = read_ctl(h, c);
@@ -1332,6 +1531,7 @@ pamc_status pamc_batch_add(pamc_batch b, pamc_handle h) {
     if (!b || !h) return bfail(b, PAMC_ERR_ARG, "null batch or handle");
     if (!h->initialized) return bfail(b, PAMC_ERR_STATE, "handle not initialised (pamc_init)");
     if (h->dense) return bfail(b, PAMC_ERR_ARG, "batches hold sparse instances");
+    if (h->sharded) return bfail(b, PAMC_ERR_ARG, "a split population cannot join a batch");
     if (h->H > kByteLaneMaxH)
         return bfail(b, PAMC_ERR_ARG, "batched members need sum_j |w_ij| <= %d", kByteLaneMaxH);
     if (h->p.kind == 1 && h->p.rule != 0)

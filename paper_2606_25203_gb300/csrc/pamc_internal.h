@@ -24,7 +24,8 @@ struct DevCtl {
     int32_t restart;      // the last iteration restarted (reinit pending)
     int32_t err;          // device-side error code (pamc_status), 0 = none
     int32_t best_replica; // replica holding M* when it was last improved
-    int32_t pad_;
+    int32_t best_owned;   // the replica holding M* is one of this handle's own (always, unless the
+                          // population is split over processes)
     double beta, delta, dbeta;
     int64_t mstar;        // best cut so far (INT64_MIN = none yet)
     int64_t ncm_flipped, ncm_dE_max;
@@ -74,6 +75,7 @@ struct SweepDesc {
     int32_t push;   // push-model sweep (H <= 63, ELL, one lane per vertex, S >= 1)
     int64_t Wsum;   // Potts: sum_{i<j} w_ij (E = -sum_k syn_sigma_k(k) - W)
     uint32_t *gsp;  // Ising: the groups' spin words in device memory (n_pad words a group), or nullptr
+    int32_t gbase;  // group index of the first local group in the whole population (keys the draws)
 };
 
 struct SchedDesc {
@@ -184,7 +186,8 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
                                SchedView sv, const uint64_t *tab, const int8_t *src,
                                const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
-                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp = nullptr);
+                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp = nullptr,
+                               int32_t rbase = 0);
 
 // Ising sweeps with 16-bit field lanes (sweep_wide.cu): instances with
 // 127 < H <= 32767; two words per vertex and replica group (8n bytes), in
@@ -196,7 +199,8 @@ cudaError_t launch_sweep_ising_wide(int rule, int32_t n, const int32_t *rp, cons
                                     const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
                                     const uint64_t *tab, const int8_t *src, const int32_t *parent,
                                     const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
-                                    const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp);
+                                    const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp,
+                                    int32_t rbase = 0);
 
 // Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax;
 // every kind keeps groups of four replicas.
@@ -206,30 +210,37 @@ size_t sweep_potts_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
 cudaError_t launch_sweep_potts(int32_t n, const int32_t *rp, const uint32_t *adj, int32_t H, const pamc_params &p,
                                int32_t t, int32_t slot, SchedView sv, const uint64_t *tab, const int8_t *src,
                                const int32_t *parent, int8_t *dst, int64_t *E_dst, const DevCtl *ctl,
-                               SweepCfg cfg, int64_t Wsum, cudaStream_t st);
+                               SweepCfg cfg, int64_t Wsum, cudaStream_t st, int32_t rbase = 0);
 cudaError_t launch_sweep_softmax(int32_t n, const int32_t *rp, const uint32_t *adj, int32_t H,
                                  const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
                                  const uint64_t *tab, const int8_t *src, const int32_t *parent,
                                  const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst, const DevCtl *ctl,
-                                 SweepCfg cfg, int64_t Wsum, cudaStream_t st);
+                                 SweepCfg cfg, int64_t Wsum, cudaStream_t st, int32_t rbase = 0);
 
+// rbase: index of the first local replica in the whole population (a
+// multiple of 4; nonzero when the population is split over processes): the
+// random draws are keyed by the replica's index in the whole population.
 cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const uint32_t *adj,
                          int32_t H, const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
                          const uint64_t *tab, const int8_t *src, const int32_t *parent,
                          const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst,
                          int64_t *E_dst, const DevCtl *ctl, SweepCfg cfg, int64_t Wsum,
-                         cudaStream_t st, uint32_t *gsp = nullptr);
+                         cudaStream_t st, uint32_t *gsp = nullptr, int32_t rbase = 0);
 
 // Random (re)initialisation of the population with key t, and its energies;
 // when only_if_restart is set the kernels do nothing unless the controller
 // has just restarted the schedule.
 cudaError_t launch_init(int kind, int32_t K, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
                         uint64_t seed, int32_t t, int only_if_restart, const DevCtl *ctl,
-                        int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st);
+                        int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st, int32_t rbase = 0);
 
 // Energies of a given population from the definition (one CTA per replica).
 cudaError_t launch_energy(int kind, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
                           const DevCtl *ctl, int64_t Wsum, const int8_t *spins, int64_t *E, cudaStream_t st);
+
+// ---- a population split over processes (shard.cu): rows[i] of src -> row i of dst
+cudaError_t launch_gather_rows(int32_t n, const int32_t *rows, int32_t nrows, const int8_t *src, int8_t *dst,
+                               cudaStream_t st);
 
 // ---- diagnostics (diag.cu)
 // Pairwise corrected Hamming distances of a +-1 population (R rows of n int8):

@@ -402,7 +402,7 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
       const int8_t *__restrict__ src, const int64_t *__restrict__ E_src,
       const int32_t *__restrict__ parent, const int32_t *__restrict__ targets,
       int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, int32_t key_smem, int32_t max_rounds,
-      DevCtl *__restrict__ ctl) {
+      DevCtl *__restrict__ ctl, int32_t base, int32_t count, const int32_t *__restrict__ prow) {
     // the per-site decision state of the MIS rounds lives in shared memory
     // (n bytes), and the trial's order keys too (4n bytes) when key_smem:
     // every round reads the state and key of every neighbour
@@ -414,7 +414,11 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
     if (q >= min(n_top, R)) return;
     const int32_t t = ctl->t;
     const int32_t m = targets[q];
-    const int8_t *row = src + (size_t)parent[m] * n;
+    // a population split over processes: this handle moves only its own
+    // slots [base, base + count), whose parents sit at rows prow[m - base]
+    // of its source buffer (own replicas and the ones it received)
+    if (m < base || m - base >= count) return;
+    const int8_t *row = src + (size_t)(prow ? prow[m - base] : parent[m]) * n;
     int8_t *sp = ncm_buf + (size_t)q * n;
     uint32_t *key = key_smem ? reinterpret_cast<uint32_t *>(sm + ncm_stat_bytes(n)) : nkey + (size_t)q * n;
     uint8_t *stat = sm;
@@ -480,7 +484,9 @@ __device__ __forceinline__ void
 control_body(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst, int32_t win_short,
              int32_t win_long, int32_t max_ds, int32_t max_dl, double reheat, double beta0,
              int64_t target, const int64_t *__restrict__ E, const int8_t *__restrict__ spins,
-             int8_t *__restrict__ best, DevCtl *__restrict__ ctl) {
+             int8_t *__restrict__ best, DevCtl *__restrict__ ctl, int32_t base, int32_t count) {
+    // E holds all R energies; spins only rows [base, base + count) of the
+    // population (all of it unless the population is split over processes)
     __shared__ long long s_e[32];
     __shared__ int s_i[32];
     __shared__ int s_improved, s_rb;
@@ -507,11 +513,15 @@ control_body(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst,
         const long long cut = (W - be) / 2;
         s_improved = cut > ctl->mstar;
         s_rb = bi;
-        if (s_improved) { ctl->mstar = cut; ctl->best_replica = bi; }
+        if (s_improved) {
+            ctl->mstar = cut;
+            ctl->best_replica = bi;
+            ctl->best_owned = bi >= base && bi - base < count ? 1 : 0;
+        }
     }
     __syncthreads();
-    if (s_improved) {
-        const int8_t *row = spins + (size_t)s_rb * n;
+    if (s_improved && s_rb >= base && s_rb - base < count) {
+        const int8_t *row = spins + (size_t)(s_rb - base) * n;
         for (int32_t k = threadIdx.x; k < n; k += blockDim.x) best[k] = row[k];
     }
     DevCtl &c = *ctl;
@@ -577,9 +587,9 @@ __global__ void __launch_bounds__(kCtlThreads)
 k_control(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst, int32_t win_short,
           int32_t win_long, int32_t max_ds, int32_t max_dl, double reheat, double beta0,
           int64_t target, const int64_t *__restrict__ E, const int8_t *__restrict__ spins,
-          int8_t *__restrict__ best, DevCtl *__restrict__ ctl) {
+          int8_t *__restrict__ best, DevCtl *__restrict__ ctl, int32_t base, int32_t count) {
     control_body(n, W, R, stagnation, z_rst, win_short, win_long, max_ds, max_dl, reheat, beta0, target, E,
-                 spins, best, ctl);
+                 spins, best, ctl, base, count);
 }
 
 __global__ void __launch_bounds__(kCtlThreads) k_control_batched(const CtlDesc *__restrict__ descs) {
@@ -588,7 +598,7 @@ __global__ void __launch_bounds__(kCtlThreads) k_control_batched(const CtlDesc *
     const int32_t t = d.ctl->t;
     if (t >= d.t_end) return;
     control_body(d.n, d.W, d.R, d.stagnation, d.z_rst, d.win_short, d.win_long, d.max_ds, d.max_dl,
-                 d.reheat, d.beta0, d.target, d.en[(t + 1) & 1], d.sp[(t + 1) & 1], d.best, d.ctl);
+                 d.reheat, d.beta0, d.target, d.en[(t + 1) & 1], d.sp[(t + 1) & 1], d.best, d.ctl, 0, d.R);
 }
 
 }  // namespace
@@ -637,7 +647,7 @@ cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl,
 cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
                        const int8_t *src, const int64_t *E_src, const int32_t *parent,
                        const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey, DevCtl *ctl,
-                       cudaStream_t st) {
+                       cudaStream_t st, int32_t base, int32_t count, const int32_t *prow) {
     const int32_t ntop = p.n_top < p.R ? p.n_top : p.R;
     if (ntop <= 0 || p.kind != 0 || !p.stagnation) return cudaSuccess;
     const size_t with_keys = ncm_stat_bytes(n) + (size_t)n * 4;
@@ -651,15 +661,18 @@ cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const 
     if (const char *env = getenv("PAMC_NCM_MAX_ROUNDS")) max_rounds = atoi(env);
     k_ncm<<<ntop, kNcmThreads, smem, st>>>(n, rp, adj, p.R, p.kind, p.n_top, p.mis_trials,
                                            (uint32_t)p.seed, (uint32_t)(p.seed >> 32), src, E_src,
-                                           parent, targets, ncm_buf, nkey, key_smem, max_rounds, ctl);
+                                           parent, targets, ncm_buf, nkey, key_smem, max_rounds, ctl, base,
+                                           count < 0 ? p.R : count, prow);
     return cudaGetLastError();
 }
 
 cudaError_t launch_control(int32_t n, int64_t W, const pamc_params &p, const int64_t *E,
-                           const int8_t *spins, int8_t *best, DevCtl *ctl, cudaStream_t st) {
+                           const int8_t *spins, int8_t *best, DevCtl *ctl, cudaStream_t st, int32_t base,
+                           int32_t count) {
     k_control<<<1, kCtlThreads, 0, st>>>(n, W, p.R, p.stagnation, p.z_rst, p.win_short, p.win_long,
                                          p.max_distinct_short, p.max_distinct_long, p.reheat_factor,
-                                         p.beta0, p.target_cut, E, spins, best, ctl);
+                                         p.beta0, p.target_cut, E, spins, best, ctl, base,
+                                         count < 0 ? p.R : count);
     return cudaGetLastError();
 }
 

@@ -6,7 +6,8 @@
 // sweep_softmax.cu (K-state Potts, softmax noisy argmax of Sec. III.F, Eq. 8-9).
 //
 // Initial values: replica r's value at vertex i comes from word r mod 4 of
-// Philox(i, 0, t, INIT<<24 | r/4): s = +1 iff the top bit is set (Ising), or
+// Philox(i, 0, t, INIT<<24 | r/4), r the replica's index in the whole
+// population: s = +1 iff the top bit is set (Ising), or
 // label floor(K u / 2^32) (Potts).  Energies: E = -1/2 sum_k s_k h_k (Ising),
 // E = -sum_k syn_{sigma_k}(k) - W (Potts).
 #include "pamc_device.cuh"
@@ -18,7 +19,7 @@ namespace {
 
 __global__ void k_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint32_t key0, uint32_t key1,
                              int32_t t, int only_if_restart, const DevCtl *__restrict__ ctl,
-                             int8_t *__restrict__ spins) {
+                             int8_t *__restrict__ spins, int32_t gbase) {
     // a restart re-draws the population in the iteration that restarted
     // (the controller has then advanced t to the key t)
     if (only_if_restart && !(ctl->restart && ctl->t == t)) return;
@@ -27,7 +28,7 @@ __global__ void k_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint32_t
     for (size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x; x < total;
          x += (size_t)gridDim.x * blockDim.x) {
         const int32_t g = (int32_t)(x / n), i = (int32_t)(x % n);
-        const u32x4 u = philox((uint32_t)i, 0u, (uint32_t)t, (kTagInit << 24) | (uint32_t)g, key0, key1);
+        const u32x4 u = philox((uint32_t)i, 0u, (uint32_t)t, (kTagInit << 24) | (uint32_t)(g + gbase), key0, key1);
         const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -86,28 +87,29 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
                          const uint64_t *tab, const int8_t *src, const int32_t *parent,
                          const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst,
                          int64_t *E_dst, const DevCtl *ctl, SweepCfg cfg, int64_t Wsum,
-                         cudaStream_t st, uint32_t *gsp) {
+                         cudaStream_t st, uint32_t *gsp, int32_t rbase) {
     if (kind == 0 && H > kByteLaneMaxH)
         return launch_sweep_ising_wide(rule, n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_buf, ncm_idx,
-                                       dst, E_dst, ctl, cfg, st, gsp);
+                                       dst, E_dst, ctl, cfg, st, gsp, rbase);
     if (kind == 0)
         return launch_sweep_ising(rule, n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_buf,
-                                  ncm_idx, dst, E_dst, ctl, cfg, st, gsp);
+                                  ncm_idx, dst, E_dst, ctl, cfg, st, gsp, rbase);
     if (kind == 2)
         return launch_sweep_softmax(n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_idx, dst, E_dst, ctl,
-                                    cfg, Wsum, st);
-    return launch_sweep_potts(n, rp, adj, H, p, t, slot, sv, tab, src, parent, dst, E_dst, ctl, cfg, Wsum, st);
+                                    cfg, Wsum, st, rbase);
+    return launch_sweep_potts(n, rp, adj, H, p, t, slot, sv, tab, src, parent, dst, E_dst, ctl, cfg, Wsum, st,
+                              rbase);
 }
 
 cudaError_t launch_init(int kind, int32_t K, int32_t n, const int32_t *rp, const uint32_t *adj, int32_t R,
                         uint64_t seed, int32_t t, int only_if_restart, const DevCtl *ctl,
-                        int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st) {
+                        int64_t Wsum, int8_t *spins, int64_t *E, cudaStream_t st, int32_t rbase) {
     const size_t total = (size_t)((R + 3) / 4) * n;
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
     k_init_spins<<<grid, 256, 0, st>>>(kind, K, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
-                                        only_if_restart, ctl, spins);
+                                        only_if_restart, ctl, spins, rbase / 4);
     k_energy<<<R, 256, 0, st>>>(kind, n, rp, adj, R, only_if_restart, ctl, Wsum, t, spins, E);
     return cudaGetLastError();
 }
@@ -125,7 +127,7 @@ cudaError_t launch_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint64_
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
     k_init_spins<<<grid, 256, 0, st>>>(kind, K, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
-                                        only_if_restart, ctl, spins);
+                                        only_if_restart, ctl, spins, 0);
     return cudaGetLastError();
 }
 

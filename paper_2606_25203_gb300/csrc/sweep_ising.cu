@@ -130,7 +130,7 @@ sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                       const int8_t *__restrict__ src, const int32_t *__restrict__ parent,
                       const int8_t *__restrict__ ncm_buf, const int32_t *__restrict__ ncm_idx,
                       int8_t *__restrict__ dst, int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl,
-                      int gpc, int tpg, int32_t bid) {
+                      int gpc, int tpg, int32_t bid, int32_t gbase = 0) {
     extern __shared__ __align__(16) uint8_t smem[];
     if (ctl->done) return;
     const int tabn = 2 * H + 1;
@@ -181,7 +181,7 @@ sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
 
     if (active) {
         const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
-        const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)g;
+        const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)(g + gbase);
         uint32_t nflip = 0;
         for (int32_t sw = 0; sw < S; ++sw) {
             const size_t sb = (size_t)slot * S + sw;
@@ -298,7 +298,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                  const int32_t *__restrict__ parent, const int8_t *__restrict__ ncm_buf,
                  const int32_t *__restrict__ ncm_idx, int8_t *__restrict__ dst,
                  int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int gpc, int tpg,
-                 int32_t bid, uint32_t *__restrict__ gspins = nullptr) {
+                 int32_t bid, uint32_t *__restrict__ gspins = nullptr, int32_t gbase = 0) {
     // WC > 0: the ELL width, known at compile time (4: every row in the first
     // four slots, the torus; 8, 12, 16: sparse graphs of low degree)
     if constexpr (WC > 0) W = WC;
@@ -346,7 +346,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
 
     if (active) {
         const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
-        const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)g;
+        const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)(g + gbase);
         uint32_t nflip = 0;
         for (int32_t sw = 0; sw < S; ++sw) {
             const size_t sb = (size_t)slot * S + sw;
@@ -613,14 +613,14 @@ __global__ void __launch_bounds__(1024) k_sweep_ising(SweepDesc d, int gpc, int 
     sweep_ising_body<ELLP, RULE, LPV, KeysPre, GSP, WC>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t,
                                                     d.slot, d.sorder, d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab,
                                                     d.src, d.parent, d.ncm_buf, d.ncm_idx, d.dst, d.E_dst, d.ctl, gpc,
-                                                    tpg, blockIdx.x, d.gsp);
+                                                    tpg, blockIdx.x, d.gsp, d.gbase);
 }
 
 template <int RULE>
 __global__ void __launch_bounds__(1024) k_sweep_ising_push(SweepDesc d, int gpc, int tpg) {
     sweep_ising_push_body<RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, KeysPre{d.K}, d.t, d.slot, d.slvl,
                                 d.snlev, d.sell, d.spos, d.W, d.tab, d.src, d.parent, d.ncm_buf, d.ncm_idx,
-                                d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x);
+                                d.dst, d.E_dst, d.ctl, gpc, tpg, blockIdx.x, d.gbase);
 }
 
 // Many instances in one launch: CTA b works on instance items[b].x, its
@@ -640,14 +640,14 @@ k_sweep_ising_batched(const SweepDesc *__restrict__ descs, const int2 *__restric
         if (d.push) {   // uniform over the CTA: one member per CTA
             sweep_ising_push_body<RULE>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots, d.slvl,
                                         d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.ncm_buf,
-                                        d.ncm_idx, d.sp[(t + 1) & 1], d.en[(t + 1) & 1], ctl, gpc, tpg, it.y);
+                                        d.ncm_idx, d.sp[(t + 1) & 1], d.en[(t + 1) & 1], ctl, gpc, tpg, it.y, d.gbase);
             return;
         }
     }
     sweep_ising_body<ELLP, RULE, LPV, KeysSeed, GSP>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, draw, t, t % d.slots,
                                                      d.sorder, d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab,
                                                      d.sp[t & 1], d.parent, d.ncm_buf, d.ncm_idx, d.sp[(t + 1) & 1],
-                                                     d.en[(t + 1) & 1], ctl, gpc, tpg, it.y, d.gsp);
+                                                     d.en[(t + 1) & 1], ctl, gpc, tpg, it.y, d.gsp, d.gbase);
 }
 
 }  // namespace
@@ -675,7 +675,8 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
                                SchedView sv, const uint64_t *tab, const int8_t *src,
                                const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
-                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp) {
+                               const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp,
+                               int32_t rbase) {
     const int32_t groups = (p.R + 3) / 4;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
     SweepDesc d;
@@ -684,6 +685,7 @@ cudaError_t launch_sweep_ising(int rule, int32_t n, const int32_t *rp, const uin
     d.dst = dst; d.E_dst = E_dst; d.ctl = ctl; d.n = n; d.n_pad = (n + 3) & ~3; d.H = H; d.R = p.R;
     d.S = p.sweeps; d.t = t; d.slot = slot; d.W = sv.W; d.K = make_philox_keys(p.seed);
     d.gsp = gsp;
+    d.gbase = rbase / 4;
     const size_t smem = sweep_ising_smem_bytes(n, H, cfg, gsp != nullptr);
     const int grid = (groups + gpc - 1) / gpc;
     const bool ell = sv.ell != nullptr;

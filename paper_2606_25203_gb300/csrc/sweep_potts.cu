@@ -43,7 +43,7 @@ potts_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint3
            const int2 *__restrict__ spos, int32_t W, const uint64_t *__restrict__ tab,
            const int8_t *__restrict__ src, const int32_t *__restrict__ parent, int8_t *__restrict__ dst,
            int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg,
-           int32_t bid) {
+           int32_t bid, int32_t gbase) {
     extern __shared__ __align__(16) uint8_t smem[];
     if (ctl->done) return;
     const int32_t W1 = 4 * H + 1;
@@ -56,6 +56,7 @@ potts_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint3
 
     const int gl = threadIdx.x / tpg, li = threadIdx.x % tpg;
     const int32_t g = bid * gpc + gl;
+    const int32_t gk = g + gbase;   // the group's index in the whole population keys its draws
     const int32_t r0 = g * 4;
     const bool active = r0 < R;
     uint2 *oh = oh_all + (size_t)gl * n_pad;
@@ -101,9 +102,9 @@ potts_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint3
                         k = pr.x & 0xFFFFFF;
                         const int32_t deg = (int32_t)((uint32_t)pr.x >> 24);
                         jsum = pr.y;
-                        ua = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, (kTagFlip << 24) | (uint32_t)(2 * g),
+                        ua = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, (kTagFlip << 24) | (uint32_t)(2 * gk),
                                     key0, key1);
-                        ub = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, (kTagFlip << 24) | (uint32_t)(2 * g + 1),
+                        ub = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, (kTagFlip << 24) | (uint32_t)(2 * gk + 1),
                                     key0, key1);
 #pragma unroll
                         for (int q = 0; q < 16; ++q) {
@@ -135,9 +136,9 @@ potts_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint3
                             A1 += o.y * (uint32_t)J;
                             jsum += J;
                         }
-                        ua = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, (kTagFlip << 24) | (uint32_t)(2 * g),
+                        ua = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, (kTagFlip << 24) | (uint32_t)(2 * gk),
                                     key0, key1);
-                        ub = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, (kTagFlip << 24) | (uint32_t)(2 * g + 1),
+                        ub = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t, (kTagFlip << 24) | (uint32_t)(2 * gk + 1),
                                     key0, key1);
                     }
                     const uint32_t u0[4] = {ua.x, ua.z, ub.x, ub.z};
@@ -206,9 +207,10 @@ k_sweep_potts(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const ui
               const int32_t *__restrict__ snlev, const uint32_t *__restrict__ sell,
               const int2 *__restrict__ spos, int32_t W, const uint64_t *__restrict__ tab,
               const int8_t *__restrict__ src, const int32_t *__restrict__ parent, int8_t *__restrict__ dst,
-              int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg) {
+              int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg,
+              int32_t gbase) {
     potts_body<ELLP>(n, n_pad, rp, adj, H, R, S, key0, key1, t, slot, sorder, slvl, snlev, sell, spos, W, tab, src,
-                     parent, dst, E_dst, ctl, Wsum, gpc, tpg, blockIdx.x);
+                     parent, dst, E_dst, ctl, Wsum, gpc, tpg, blockIdx.x, gbase);
 }
 
 // Many Max-3-Cut instances in one launch: CTA b works on instance items[b].x,
@@ -225,7 +227,7 @@ k_sweep_potts_batched(const SweepDesc *__restrict__ descs, const int2 *__restric
     if (t >= d.t_end) return;
     potts_body<ELLP>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, d.K.k0[0], d.K.k1[0], t, t % d.slots, d.sorder,
                      d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.sp[(t + 1) & 1],
-                     d.en[(t + 1) & 1], ctl, d.Wsum, gpc, tpg, it.y);
+                     d.en[(t + 1) & 1], ctl, d.Wsum, gpc, tpg, it.y, d.gbase);
 }
 
 }  // namespace
@@ -239,7 +241,7 @@ size_t sweep_potts_smem_bytes(int32_t n, int32_t H, SweepCfg cfg) {
 cudaError_t launch_sweep_potts(int32_t n, const int32_t *rp, const uint32_t *adj, int32_t H, const pamc_params &p,
                                int32_t t, int32_t slot, SchedView sv, const uint64_t *tab, const int8_t *src,
                                const int32_t *parent, int8_t *dst, int64_t *E_dst, const DevCtl *ctl,
-                               SweepCfg cfg, int64_t Wsum, cudaStream_t st) {
+                               SweepCfg cfg, int64_t Wsum, cudaStream_t st, int32_t rbase) {
     const int32_t groups = (p.R + 3) / 4;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
     const size_t smem = sweep_potts_smem_bytes(n, H, cfg);
@@ -254,7 +256,7 @@ cudaError_t launch_sweep_potts(int32_t n, const int32_t *rp, const uint32_t *adj
         k_sweep_potts<EL><<<grid, gpc * tpg, smem, st>>>(                                                         \
             n, (n + 3) & ~3, rp, adj, H, p.R, p.sweeps, k0, k1, t, slot, sv.order, sv.lvl_ptr, sv.nlev,           \
             EL ? sv.ell : nullptr, EL ? sv.pos : nullptr, EL ? sv.W : 0, tab, src, parent, dst, E_dst, ctl, Wsum, \
-            gpc, tpg);                                                                                            \
+            gpc, tpg, rbase / 4);                                                                                 \
     } while (0)
     if (ell) PAMC_POTTS(true);
     else PAMC_POTTS(false);

@@ -40,7 +40,7 @@ k_sweep_softmax(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const 
                 const int32_t *__restrict__ snlev, const float *__restrict__ tab,
                 const int8_t *__restrict__ src, const int32_t *__restrict__ parent,
                 const int32_t *__restrict__ ncm_idx, int8_t *__restrict__ dst, int64_t *__restrict__ E_dst,
-                const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg) {
+                const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg, int32_t rbase) {
     extern __shared__ __align__(16) uint8_t smem[];
     if (ctl->done) return;
     const int tabn = 2 * H + 1;
@@ -122,7 +122,7 @@ k_sweep_softmax(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const 
                         for (int b = 0; b < kMaxK / 4; ++b) {
                             if (b < nb) {
                                 const u32x4 x = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t,
-                                                       (kTagFlip << 24) | (uint32_t)(r * nb + b), key0, key1);
+                                                       (kTagFlip << 24) | (uint32_t)((r + rbase) * nb + b), key0, key1);
                                 u[4 * b] = x.x; u[4 * b + 1] = x.y; u[4 * b + 2] = x.z; u[4 * b + 3] = x.w;
                             } else {
                                 u[4 * b] = u[4 * b + 1] = u[4 * b + 2] = u[4 * b + 3] = 0u;
@@ -186,7 +186,7 @@ cudaError_t launch_sweep_softmax(int32_t n, const int32_t *rp, const uint32_t *a
                                  const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
                                  const uint64_t *tab, const int8_t *src, const int32_t *parent,
                                  const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst, const DevCtl *ctl,
-                                 SweepCfg cfg, int64_t Wsum, cudaStream_t st) {
+                                 SweepCfg cfg, int64_t Wsum, cudaStream_t st, int32_t rbase) {
     const int32_t groups = (p.R + 3) / 4;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
     const size_t smem = sweep_softmax_smem_bytes(n, H, cfg);
@@ -196,7 +196,7 @@ cudaError_t launch_sweep_softmax(int32_t n, const int32_t *rp, const uint32_t *a
     k_sweep_softmax<<<grid, gpc * tpg, smem, st>>>(
         n, (n + 3) & ~3, rp, adj, H, p.K, (float)p.gamma, p.R, p.sweeps, (uint32_t)p.seed,
         (uint32_t)(p.seed >> 32), t, slot, sv.order, sv.lvl_ptr, sv.nlev, reinterpret_cast<const float *>(tab),
-        src, parent, ncm_idx, dst, E_dst, ctl, Wsum, gpc, tpg);
+        src, parent, ncm_idx, dst, E_dst, ctl, Wsum, gpc, tpg, rbase);
     return cudaGetLastError();
 }
 

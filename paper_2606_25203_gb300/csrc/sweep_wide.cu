@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_wide(SweepDesc d, int gpc,
 
     if (active) {
         const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
-        const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)g;
+        const uint32_t ctr3 = (kTagFlip << 24) | (uint32_t)(g + d.gbase);
         const KeysPreW draw{d.K};
         uint32_t nflip = 0;
         for (int32_t sw = 0; sw < S; ++sw) {
@@ -205,7 +205,8 @@ cudaError_t launch_sweep_ising_wide(int rule, int32_t n, const int32_t *rp, cons
                                     const pamc_params &p, int32_t t, int32_t slot, SchedView sv,
                                     const uint64_t *tab, const int8_t *src, const int32_t *parent,
                                     const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
-                                    const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp) {
+                                    const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp,
+                                    int32_t rbase) {
     const int32_t groups = (p.R + 3) / 4;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
     SweepDesc d;
@@ -214,6 +215,7 @@ cudaError_t launch_sweep_ising_wide(int rule, int32_t n, const int32_t *rp, cons
     d.spos = sv.pos; d.tab = tab; d.src = src; d.parent = parent; d.ncm_buf = ncm_buf; d.ncm_idx = ncm_idx;
     d.dst = dst; d.E_dst = E_dst; d.ctl = ctl; d.n = n; d.n_pad = (n + 3) & ~3; d.H = H; d.R = p.R;
     d.S = p.sweeps; d.t = t; d.slot = slot; d.W = sv.W; d.K = make_philox_keys(p.seed); d.gsp = gsp;
+    d.gbase = rbase / 4;
     const bool g = gsp != nullptr, ell = sv.ell != nullptr;
     const size_t smem = sweep_wide_smem_bytes(n, cfg, g);
     const int grid = (groups + gpc - 1) / gpc;
