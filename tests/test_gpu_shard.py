@@ -83,7 +83,7 @@ class ThreadComm:
         self.torch.cuda.synchronize()
 
 
-def run_split(pg, inst, G, steps, **params):
+def run_split(pg, inst, G, nsteps, params):
     from paper_2606_25203_gb300 import shard as S
     group = _Group(G)
     out, errs = [None] * G, []
@@ -92,7 +92,7 @@ def run_split(pg, inst, G, steps, **params):
         try:
             sh = S.LibShard(inst.row_ptr, inst.col, inst.w, rank, G, **params)
             comm = ThreadComm(group, rank)
-            for _ in range(steps):
+            for _ in range(nsteps):
                 S.run_step(sh, comm)
             cut, best = S.best(sh, comm)
             spins, E, par, cnt = pg.pamc_state(sh.h, sh.count, inst.n)
@@ -114,10 +114,10 @@ def run_split(pg, inst, G, steps, **params):
     return out
 
 
-def run_single(pg, inst, steps, **params):
+def run_single(pg, inst, nsteps, params):
     h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
-    p = pg.pamc_init(h, steps=steps, **params)
-    pg.pamc_step(h, steps)
+    p = pg.pamc_init(h, **params)
+    pg.pamc_step(h, nsteps)
     spins, E, par, cnt = pg.pamc_state(h, p.R, inst.n)
     res = dict(spins=spins, E=E, par=par, cnt=cnt, ctl=pg.pamc_control_state(h), hist=pg.pamc_control_history(h),
                best=pg.pamc_best(h, inst.n), mode=pg.pamc_sweep_mode(h))
@@ -152,8 +152,9 @@ def test_split_equals_single_and_oracle_small(pg, G):
     single-handle run and the oracle agree."""
     inst = W.torus(14, 14, signed=True, seed=2)
     steps = 150
-    parts = run_split(pg, inst, G, steps, R=32, steps=steps, **AUG)
-    ref = run_single(pg, inst, steps, R=32, **AUG)
+    params = dict(R=32, steps=steps, **AUG)
+    parts = run_split(pg, inst, G, steps, params)
+    ref = run_single(pg, inst, steps, params)
     assert_split_equals(parts, ref, f"G={G}")
     orc = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, R=32, steps=steps, **AUG)
     orc.step(steps)
@@ -186,8 +187,8 @@ def test_split_equals_single_handle(pg, monkeypatch, case):
         monkeypatch.setenv("PAMC_SWEEP_GLOBAL", "1")
         inst = W.torus(40, 40, signed=True, seed=1)
         params = dict(R=128, steps=40, sweeps=2, beta0=0.2, beta1=3.0, stagnation=1, z_rst=30, seed=9)
-    parts = run_split(pg, inst, G, params["steps"], **params)
-    ref = run_single(pg, inst, params["steps"], **{k: v for k, v in params.items() if k != "steps"})
+    parts = run_split(pg, inst, G, params["steps"], params)
+    ref = run_single(pg, inst, params["steps"], params)
     assert_split_equals(parts, ref, case)
     assert all(p["mode"] == ref["mode"] for p in parts)
     if case == "wide_lanes":
