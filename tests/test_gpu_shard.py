@@ -98,7 +98,7 @@ def run_split(pg, inst, G, nsteps, params):
             spins, E, par, cnt = pg.pamc_state(sh.h, sh.count, inst.n)
             out[rank] = dict(spins=spins, E=E, par=par, cnt=cnt, ctl=pg.pamc_control_state(sh.h),
                              hist=pg.pamc_control_history(sh.h), cut=cut, best=best, moved=sh.moved,
-                             mode=pg.pamc_sweep_mode(sh.h))
+                             mode=pg.pamc_sweep_mode(sh.h) if params.get("kind", 0) == 0 else None)
             sh.close()
         except BaseException as e:   # noqa: BLE001 -- re-raised below
             errs.append(e)
@@ -120,7 +120,7 @@ def run_single(pg, inst, nsteps, params):
     pg.pamc_step(h, nsteps)
     spins, E, par, cnt = pg.pamc_state(h, p.R, inst.n)
     res = dict(spins=spins, E=E, par=par, cnt=cnt, ctl=pg.pamc_control_state(h), hist=pg.pamc_control_history(h),
-               best=pg.pamc_best(h, inst.n), mode=pg.pamc_sweep_mode(h))
+               best=pg.pamc_best(h, inst.n), mode=pg.pamc_sweep_mode(h) if params.get("kind", 0) == 0 else None)
     pg.pamc_destroy(h)
     return res
 
