@@ -17,6 +17,14 @@ The line also carries a "dense100k" object: the whole 200-step anneal of the
 fully connected N=100,000 instance, device-timed, with its HBM roofline and
 an end-to-end figure from host buffers.
 
+Several GPUs (torchrun, one process per GPU): ONE population of R = 4,096 x
+GPUs replicas per instance, split in equal blocks over the GPUs, with the
+energies gathered and the migrating parent replicas exchanged by NCCL once
+per iteration (weak scaling: 4,096 replicas per GPU and instance, as on one
+GPU; the result equals the one-GPU run of the same R bit for bit).
+--replicas runs independent populations instead; --split runs the split
+path on one GPU (a group of one).
+
 Timing: device time with CUDA events on the library's stream, one event pair
 per step; between timed steps a 512 MB buffer is written to flush L2 (the
 populations are smaller than L2).  The dominant kernel (the sweep) is also
@@ -287,10 +295,16 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None
-    if world > 1:
+    if world > 1 or args.split:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if world == 1 and "MASTER_ADDR" not in os.environ:
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", "29541")
+            os.environ.setdefault("RANK", "0")
+        dist.init_process_group("nccl", world_size=world, rank=rank)
     pg.load()
+    if (world > 1 and not args.replicas) or args.split:
+        return run_split(args, pg, torch, dist, rank, world, local)
     insts = instances()
     stream = torch.cuda.current_stream()
     # the two instances are independent: each steps on a stream of its own
@@ -406,6 +420,163 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return result
+
+
+def run_split(args, pg, torch, dist, rank, world, local):
+    """Several GPUs: ONE population of R = 4,096 x GPUs replicas per instance,
+    split in equal blocks over the GPUs (weak scaling: every GPU sweeps
+    4,096 replicas of each instance, as on one GPU).  Every iteration
+    gathers the R energies (NCCL all-gather), runs the same population step
+    and controller on every GPU, and moves the parent replicas that live on
+    another GPU (NCCL all-to-all); the result equals the one-GPU run of the
+    same R bit for bit.  The timed steps are the iterations the one-GPU line
+    times (its pre-pass on one GPU's population picks them)."""
+    from paper_2606_25203_gb300 import shard as S
+    insts = instances()
+    Rg = R * world
+    params = dict(PARAMS, R=Rg)
+    comm = S.TorchComm()
+    streams = [torch.cuda.Stream() for _ in insts]
+    start, events = 0, None
+    if args.steps < STEPS_SCHEDULE and not args.lean:
+        probe = [pg.Solver(inst.row_ptr, inst.col, inst.w, device=local) for inst in insts]
+        for s in probe:
+            s.init(**PARAMS)
+        events = schedule_events(probe)
+        start = choose_window(events, args.steps)
+        for s in probe:
+            s.close()
+
+    def make():
+        out = []
+        for inst, st in zip(insts, streams):
+            with torch.cuda.stream(st):
+                out.append(S.LibShard(inst.row_ptr, inst.col, inst.w, rank, world, device=local, **params))
+        return out
+
+    def step_all(shards):
+        for sh, st in zip(shards, streams):
+            with torch.cuda.stream(st):
+                S.run_step(sh, comm)
+
+    if start < args.warmup:              # warm-up on a population of its own
+        warm = make()
+        for _ in range(args.warmup):
+            step_all(warm)
+        for sh in warm:
+            sh.close()
+    shards = make()
+    for _ in range(start):               # untimed iterations before the window
+        step_all(shards)
+    for sh in shards:
+        pg.pamc_set_sweep_timing(sh.h, True)
+    torch.cuda.synchronize()
+    sw0 = [pg.pamc_sweep_stats(sh.h) for sh in shards]
+    ctl0 = [pg.pamc_control_state(sh.h) for sh in shards]
+    launches0 = sum(pg.pamc_launch_count(sh.h) for sh in shards)
+    moved0 = sum(sh.moved for sh in shards)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    clk = ClockSampler(local).start()
+    cur = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    with clk:
+        for k in range(args.steps):
+            flush.add_(1)
+            ev[k][0].record(cur)
+            for st in streams:
+                st.wait_stream(cur)
+            step_all(shards)
+            for st in streams:
+                cur.wait_stream(st)
+            ev[k][1].record(cur)
+        torch.cuda.synchronize()
+    dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    launches = sum(pg.pamc_launch_count(sh.h) for sh in shards) - launches0
+    moved = sum(sh.moved for sh in shards) - moved0
+    ctl1 = [pg.pamc_control_state(sh.h) for sh in shards]
+    sw1 = [pg.pamc_sweep_stats(sh.h) for sh in shards]
+    own_attempts = sum(sh.count * inst.n * SWEEPS for sh, inst in zip(shards, insts)) * args.steps
+    ms, att = reduce_over_ranks(dist, ms, own_attempts)
+    value = att / (ms / 1e3)
+    for sh in shards:
+        pg.pamc_set_sweep_timing(sh.h, False)
+        sh.close()
+    if args.lean:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
+                              "ms_per_step": ms / args.steps, "gpu_launches": launches, "clocks": clk.summary(),
+                              "config": {"only": ONLY, "R_total": Rg, "split": True}}))
+        dist.destroy_process_group()
+        return None
+    peaks, peak_src = load_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sweep = sweep_roofline(insts[0], args.steps, sw0[0], sw1[0], sm_max)
+    e2e = split_e2e(args, pg, torch, S, comm, insts, params, rank, world, local, start, dist)
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("R=4096", f"one population of R={Rg} per instance"),
+                       "R": Rg, "R_per_gpu": R, "sweeps_per_step": SWEEPS,
+                       "attempts_per_step": attempts_per_step(insts) * world,
+                       "l2": "flushed between steps (512 MB write)",
+                       "timed_steps": f"steps {start}..{start + args.steps - 1} of a fresh run",
+                       "timed_window": window_summary(events, start, args.steps, ctl0, ctl1),
+                       "parallelism": f"one population split over {world} GPU(s): replica blocks, NCCL all-gather "
+                                      f"of the energies and all-to-all of the migrating replicas per iteration",
+                       "replicas_moved_per_step": moved / args.steps},
+            "roofline": dict(sweep, traffic=None,
+                             kernel=f"k_sweep_ising ({insts[0].name}, 4096 replicas per GPU, 10 sweeps per launch)",
+                             peak_source=f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)"),
+            "clocks": clk.summary(),
+            "gpu_launches": launches,
+            "e2e": e2e,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(result))
+    dist.destroy_process_group()
+    return result
+
+
+def split_e2e(args, pg, torch, S, comm, insts, params, rank, world, local, start, dist):
+    """End to end through the public API with host buffers, for the split
+    population: each process uploads the instance (host CSR) and draws its
+    block, runs the iterations up to the end of the window, and after every
+    iteration the best cut and its configuration reach every process's host
+    (the holder broadcasts it); all of it timed, max over processes."""
+    streams = [torch.cuda.Stream() for _ in insts]
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    shards = []
+    for inst, st in zip(insts, streams):
+        with torch.cuda.stream(st):
+            shards.append(S.LibShard(inst.row_ptr, inst.col, inst.w, rank, world, device=local, **params))
+        h2d += inst.row_ptr.nbytes + inst.col.nbytes + inst.w.nbytes
+    nsteps = start + args.steps
+    for _ in range(nsteps):
+        for sh, st in zip(shards, streams):
+            with torch.cuda.stream(st):
+                S.run_step(sh, comm)
+        for sh, st in zip(shards, streams):
+            with torch.cuda.stream(st):
+                S.best(sh, comm)
+            d2h += 8 + sh.n
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for sh in shards:
+        sh.close()
+    own = sum(sh.count * inst.n * SWEEPS for sh, inst in zip(shards, insts)) * nsteps
+    ms, att = reduce_over_ranks(dist, dt * 1e3, own)
+    return {"value": att / (ms / 1e3), "unit": "attempts/s", "h2d_bytes_per_step": h2d / nsteps,
+            "d2h_bytes_per_step": d2h / nsteps, "steps": nsteps}
 
 
 def schedule_events(solvers):
@@ -1005,6 +1176,10 @@ def main():
                     help="sparse workload: step the two instances one after the other on one stream")
     ap.add_argument("--no-dense", action="store_true",
                     help="sparse workload: leave out the dense100k object (profiling)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="several GPUs: independent populations (own seed each) instead of one split population")
+    ap.add_argument("--split", action="store_true",
+                    help="one GPU: run the split-population path (the exchange over a group of one)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = STEPS_SCHEDULE if (args.workload == "sparse" and args.impl == "ours") else 20
