@@ -295,6 +295,21 @@ pamc_status pamc_batch_sync(pamc_batch b);
 pamc_status pamc_batch_last_error(pamc_batch b, char *buf, size_t len);
 void pamc_batch_destroy(pamc_batch b);
 
+/* ---- Checkpoints ----
+ * pamc_save writes the whole state of a run at the start of its next
+ * iteration -- the parameters, the controller of Algorithm 1 (beta, Delta,
+ * z, cycle, cooldown, flags, the M* history, M*, counters), the population
+ * and its energies, the last iteration's parents and copy counts, the
+ * lineage and the best configuration -- into a HOST buffer of *size bytes
+ * (buf = NULL: only *size is set; capacity too small: PAMC_ERR_RANGE).
+ * pamc_load re-initialises a handle of the SAME instance (checked against
+ * n, the couplings and W; PAMC_ERR_ARG otherwise) from such a buffer; the
+ * run then continues exactly as the uninterrupted one, since every random
+ * draw is keyed by the step index.  Both synchronise; the caller owns the
+ * buffer.  Split populations (pamc_shard_*) are refused (PAMC_ERR_STATE). */
+pamc_status pamc_save(pamc_handle h, void *buf, size_t capacity, size_t *size);
+pamc_status pamc_load(pamc_handle h, const void *buf, size_t size);
+
 /* ---- One population split over several processes (one GPU each) ----
  * The population step of Algorithm 1 (Eq. 1-2) is global over the R
  * replicas, so a population split over nranks processes exchanges once per

@@ -29,7 +29,7 @@ __all__ = [
     "pamc_control_history", "pamc_sweep_mode", "pamc_set_sweep_timing", "pamc_sweep_stats",
     "pamc_batch_set_placement", "pamc_batch_get_placement", "pamc_shard_range", "pamc_shard_init",
     "pamc_shard_energies", "pamc_shard_resample", "pamc_shard_plan", "pamc_shard_pack", "pamc_shard_sweep",
-    "pamc_shard_control", "pamc_shard_best",
+    "pamc_shard_control", "pamc_shard_best", "pamc_save", "pamc_load",
 ]
 
 STATUS = {0: "PAMC_OK", 1: "PAMC_ERR_ARG", 2: "PAMC_ERR_ASYM", 3: "PAMC_ERR_DIAG",
@@ -176,6 +176,10 @@ def load(build_if_missing: bool = True, torch_allocator: bool = True):
     L.pamc_batch_last_error.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t]
     L.pamc_batch_destroy.argtypes = [P]
     L.pamc_batch_destroy.restype = None
+    L.pamc_save.argtypes = [P, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
+    L.pamc_load.argtypes = [P, P, ctypes.c_size_t]
+    L.pamc_save.restype = ctypes.c_int
+    L.pamc_load.restype = ctypes.c_int
     L.pamc_shard_range.argtypes = [i32, i32, i32, P, P]
     L.pamc_shard_init.argtypes = [P, ctypes.POINTER(Params), i32, i32]
     L.pamc_shard_energies.argtypes = [P, P]
@@ -459,6 +463,27 @@ def pamc_sweeps_noalloc(n, nnz, row_ptr, col, w, H, rule, R, sweeps, beta, seed,
         call()
 
 
+# ---------------------------------------------------------------- checkpoints
+def pamc_save(h) -> bytes:
+    """The run's whole state at the start of its next iteration (see
+    include/pamc.h)."""
+    size = ctypes.c_size_t(0)
+    _check(_lib.pamc_save(h, None, 0, ctypes.byref(size)), h)
+    buf = ctypes.create_string_buffer(size.value)
+    _check(_lib.pamc_save(h, buf, size.value, ctypes.byref(size)), h)
+    return buf.raw[:size.value]
+
+
+def pamc_load(h, data: bytes):
+    """Continue a run from pamc_save's bytes on a handle of the same instance."""
+    raw = bytes(data)
+    buf = ctypes.create_string_buffer(raw, len(raw))
+    _check(_lib.pamc_load(h, buf, len(raw)), h)
+    d = _dims.get(getattr(h, "value", None))
+    if d is not None:
+        _dims[h.value] = [d[0], None]   # R comes from the checkpoint
+
+
 # ---------------------------------------------------------------- split population
 def _dev_arg(x, name, dtype, count, allow_none=False):
     """A contiguous CUDA tensor of dtype holding at least count elements ->
@@ -736,6 +761,17 @@ class Solver:
 
     def launches(self) -> int:
         return pamc_launch_count(self.h)
+
+    def save(self) -> bytes:
+        """Checkpoint of the run (pamc_save)."""
+        return pamc_save(self.h)
+
+    def load(self, data: bytes, R: int):
+        """Continue from a checkpoint of this instance (pamc_load); R is the
+        checkpointed run's population size."""
+        pamc_load(self.h, data)
+        self.R = int(R)
+        _set_R(self.h, R)
 
     def close(self):
         pamc_destroy(self.h)

@@ -17,7 +17,24 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pamc_internal.h"
+
+// NVTX ranges around the host-side phases (a profiler shows the kernels each
+// phase enqueued under its name; without a tool attached a range is a
+// pointer check)
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+#define PAMC_CAT2(a, b) a##b
+#define PAMC_CAT(a, b) PAMC_CAT2(a, b)
+#define PAMC_RANGE(name) NvtxRange PAMC_CAT(pamc_range_, __LINE__)(name)
 
 using namespace pamc;
 
@@ -122,6 +139,7 @@ struct pamc_handle_s {
     int sh_phase = 0;              // next call: 0 resample, 1 sweep, 2 control
     int32_t *d_plocal = nullptr;   // [sh_count] source row of each own slot's parent
     int32_t *d_rows = nullptr;     // [p.R] own rows to send
+    uint64_t inst_hash = 0;        // FNV-1a of the packed CSR (0 for dense instances)
     char err[256] = "";
 };
 
@@ -462,6 +480,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
 }
 
 pamc_status step_dense(pamc_handle h, int32_t nsteps) {
+    PAMC_RANGE("pamc_step (dense)");
     const pamc_params &p = h->p;
     const int32_t n = h->n, R = p.R;
     pamc_params pp = p;
@@ -535,6 +554,15 @@ pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *co
     h->W = W;
     h->H = H;
     h->maxdeg = maxdeg;
+    {   // identifies the instance in checkpoints (pamc_save / pamc_load)
+        uint64_t x = 1469598103934665603ull;
+        auto mix = [&x](uint32_t v) {
+            for (int b = 0; b < 4; ++b) { x ^= (v >> (8 * b)) & 0xFFu; x *= 1099511628211ull; }
+        };
+        for (int32_t i = 0; i <= n; ++i) mix((uint32_t)row_ptr[i]);
+        for (uint32_t a : adj) mix(a);
+        h->inst_hash = x;
+    }
     // position-indexed ELL when its padding stays within 4x the couplings
     // (the schedule's position record holds the degree in 8 bits)
     const int64_t ell_entries = (int64_t)((n + 31) / 32) * 32 * ((maxdeg + 3) & ~3);
@@ -614,6 +642,7 @@ pamc_status pamc_create_dense(int32_t n, const int8_t *w, int w_on_device, int c
 // handle's share of a population split over nranks processes.
 static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, int32_t nranks) {
     if (!h || !pp) return fail(h, PAMC_ERR_ARG, "null handle or params");
+    PAMC_RANGE("pamc_init");
     pamc_params p = *pp;
     if (p.K == 0) p.K = 3;
     if (p.kind != 0 && p.kind != 1) return fail(h, PAMC_ERR_ARG, "kind must be 0 or 1");
@@ -772,9 +801,11 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
     if (h->dense) return step_dense(h, nsteps);
+    PAMC_RANGE("pamc_step");
     const pamc_params &p = h->p;
     const int32_t n = h->n;
     for (int32_t i = 0; i < nsteps; ++i) {
+        PAMC_RANGE("iteration");
         const int64_t t = h->host_t;
         if (t > INT32_MAX - 2) return fail(h, PAMC_ERR_RANGE, "step counter overflow");
         if (p.sweeps > 0 && t >= h->sched_end) {
@@ -862,6 +893,7 @@ pamc_status pamc_shard_energies(pamc_handle h, int64_t *E_own) {
 }
 
 pamc_status pamc_shard_resample(pamc_handle h, const int64_t *E_all, int32_t *parent) {
+    PAMC_RANGE("pamc_shard_resample");
     pamc_status s = shard_check(h, 0, "pamc_shard_resample");
     if (s != PAMC_OK) return s;
     if (!E_all || !parent) return fail(h, PAMC_ERR_ARG, "null E_all or parent");
@@ -906,6 +938,7 @@ pamc_status pamc_shard_pack(pamc_handle h, const int32_t *rows, int32_t nrows, i
 
 pamc_status pamc_shard_sweep(pamc_handle h, const int64_t *E_all, const int32_t *local_parent,
                              const int8_t *imports, int32_t nimports, int64_t *E_own) {
+    PAMC_RANGE("pamc_shard_sweep");
     pamc_status s = shard_check(h, 1, "pamc_shard_sweep");
     if (s != PAMC_OK) return s;
     const int32_t c = h->sh_count, n = h->n;
@@ -947,6 +980,7 @@ pamc_status pamc_shard_sweep(pamc_handle h, const int64_t *E_all, const int32_t 
 }
 
 pamc_status pamc_shard_control(pamc_handle h, const int64_t *E_all, int64_t *E_own) {
+    PAMC_RANGE("pamc_shard_control");
     pamc_status s = shard_check(h, 2, "pamc_shard_control");
     if (s != PAMC_OK) return s;
     if (!E_all) return fail(h, PAMC_ERR_ARG, "null E_all");
@@ -1046,6 +1080,125 @@ pamc_status pamc_state(pamc_handle h, int8_t *spins, int64_t *E, int32_t *parent
     if (e == cudaSuccess && counts)
         e = cudaMemcpy(counts, h->d_count + off, R * sizeof(int32_t), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "state readback");
+    return PAMC_OK;
+}
+
+// ---------------------------------------------------------------- checkpoints
+namespace {
+
+// The whole state of Algorithm 1 at the start of iteration t: the
+// parameters, the controller (beta, Delta, z, cycle, cooldown, flags, M*
+// history, M*, counters), the population and its energies, the last
+// iteration's parents and copy counts, the lineage and the best
+// configuration.  Every random draw is keyed by (seed, t, ...), so a run
+// continued from it is the uninterrupted run.
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, ctl_bytes;
+    int32_t dense, n, nnz, H;
+    int64_t W;
+    uint64_t inst_hash;
+    pamc_params p;
+};
+constexpr uint32_t kCkptVersion = 1;
+
+size_t ckpt_bytes(int32_t n, int32_t R) {
+    return sizeof(CkptHeader) + sizeof(DevCtl) + (size_t)R * n + (size_t)R * 8 + (size_t)R * 4 * 4 + (size_t)n;
+}
+
+}  // namespace
+
+pamc_status pamc_save(pamc_handle h, void *buf, size_t capacity, size_t *size) {
+    PAMC_RANGE("pamc_save");
+    if (!h || !size) return fail(h, PAMC_ERR_ARG, "null handle or size");
+    if (!h->initialized) return fail(h, PAMC_ERR_STATE, "pamc_save before pamc_init");
+    if (h->sharded) return fail(h, PAMC_ERR_STATE, "pamc_save: the population is split over processes");
+    const int32_t n = h->n, R = h->p.R;
+    *size = ckpt_bytes(n, R);
+    if (!buf) return PAMC_OK;
+    if (capacity < *size) return fail(h, PAMC_ERR_RANGE, "checkpoint needs %zu bytes", *size);
+    DevCtl c;
+    pamc_status s = read_ctl(h, c);
+    if (s != PAMC_OK) return s;
+    const int cur = c.t & 1;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "PAMCCKPT", 8);
+    hd.version = kCkptVersion;
+    hd.ctl_bytes = (uint32_t)sizeof(DevCtl);
+    hd.dense = h->dense;
+    hd.n = n; hd.nnz = h->nnz; hd.H = h->H; hd.W = h->W;
+    hd.inst_hash = h->inst_hash;
+    hd.p = h->p;
+    char *o = static_cast<char *>(buf);
+    memcpy(o, &hd, sizeof(hd));
+    o += sizeof(hd);
+    memcpy(o, &c, sizeof(c));
+    o += sizeof(c);
+    cudaError_t e = cudaMemcpy(o, h->d_spins[cur], (size_t)R * n, cudaMemcpyDeviceToHost);
+    o += (size_t)R * n;
+    if (e == cudaSuccess) e = cudaMemcpy(o, h->d_E[cur], (size_t)R * 8, cudaMemcpyDeviceToHost);
+    o += (size_t)R * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(o, h->d_parent, (size_t)R * 4, cudaMemcpyDeviceToHost);
+    o += (size_t)R * 4;
+    if (e == cudaSuccess) e = cudaMemcpy(o, h->d_count, (size_t)R * 4, cudaMemcpyDeviceToHost);
+    o += (size_t)R * 4;
+    if (e == cudaSuccess) e = cudaMemcpy(o, h->d_fam, (size_t)R * 8, cudaMemcpyDeviceToHost);
+    o += (size_t)R * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(o, h->d_best, (size_t)n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pamc_save readback");
+    return PAMC_OK;
+}
+
+pamc_status pamc_load(pamc_handle h, const void *buf, size_t size) {
+    PAMC_RANGE("pamc_load");
+    if (!h || !buf) return fail(h, PAMC_ERR_ARG, "null handle or buffer");
+    if (size < sizeof(CkptHeader)) return fail(h, PAMC_ERR_ARG, "not a checkpoint (too short)");
+    CkptHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    if (memcmp(hd.magic, "PAMCCKPT", 8) != 0 || hd.version != kCkptVersion || hd.ctl_bytes != sizeof(DevCtl))
+        return fail(h, PAMC_ERR_ARG, "not a checkpoint of this library version");
+    if (hd.dense != h->dense || hd.n != h->n || hd.nnz != h->nnz || hd.H != h->H || hd.W != h->W ||
+        hd.inst_hash != h->inst_hash)
+        return fail(h, PAMC_ERR_ARG, "the checkpoint belongs to another instance");
+    const int32_t n = h->n, R = hd.p.R;
+    if (R < 1 || R > 16384 || size != ckpt_bytes(n, R)) return fail(h, PAMC_ERR_ARG, "checkpoint size mismatch");
+    DevCtl c;
+    const char *in = static_cast<const char *>(buf) + sizeof(hd);
+    memcpy(&c, in, sizeof(c));
+    in += sizeof(c);
+    if (c.t < 0 || c.t > INT32_MAX - 2) return fail(h, PAMC_ERR_RANGE, "checkpoint step index out of range");
+    const int8_t *spins = reinterpret_cast<const int8_t *>(in);
+    for (size_t x = 0; x < (size_t)R * n; ++x) {
+        const int8_t v = spins[x];
+        const bool ok = hd.p.kind == 0 ? (v == 1 || v == -1) : (v >= 0 && v < (hd.p.K ? hd.p.K : 3));
+        if (!ok) return fail(h, PAMC_ERR_RANGE, "checkpoint spin %zu out of range", x);
+    }
+    const int32_t *ints = reinterpret_cast<const int32_t *>(in + (size_t)R * n + (size_t)R * 8);
+    for (size_t x = 0; x < (size_t)R * 4; ++x)      // parents, counts, two lineage rows
+        if (ints[x] < 0 || ints[x] > R) return fail(h, PAMC_ERR_RANGE, "checkpoint index out of range");
+    pamc_status s = init_run(h, &hd.p, 0, 0);
+    if (s != PAMC_OK) return s;
+    const int cur = c.t & 1;
+    cudaError_t e = cudaMemcpyAsync(h->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_spins[cur], in, (size_t)R * n, cudaMemcpyHostToDevice, h->stream);
+    in += (size_t)R * n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_E[cur], in, (size_t)R * 8, cudaMemcpyHostToDevice, h->stream);
+    in += (size_t)R * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_parent, in, (size_t)R * 4, cudaMemcpyHostToDevice, h->stream);
+    in += (size_t)R * 4;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_count, in, (size_t)R * 4, cudaMemcpyHostToDevice, h->stream);
+    in += (size_t)R * 4;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_fam, in, (size_t)R * 8, cudaMemcpyHostToDevice, h->stream);
+    in += (size_t)R * 8;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_best, in, (size_t)n, cudaMemcpyHostToDevice, h->stream);
+    // dense runs keep the fields of the population: recompute them exactly
+    if (e == cudaSuccess && h->dense) e = dense_recompute(h, h->d_spins[cur], h->d_ident, h->d_nonc, -1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // the host buffer may go after return
+    if (e != cudaSuccess) return cuda_fail(h, e, "pamc_load upload");
+    h->host_t = c.t;
+    h->sched_end = c.t;   // the next step builds the schedules from step t on
+    h->launches += h->dense ? 1 : 0;
     return PAMC_OK;
 }
 
@@ -1562,6 +1715,7 @@ pamc_status pamc_batch_add(pamc_batch b, pamc_handle h) {
 }
 
 pamc_status pamc_batch_step(pamc_batch b, int32_t nsteps) {
+    PAMC_RANGE("pamc_batch_step");
     if (!b || nsteps < 0) return bfail(b, PAMC_ERR_ARG, "null batch or nsteps < 0");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "cudaSetDevice failed");
     for (int32_t it = 0; it < nsteps; ++it) {
