@@ -382,7 +382,7 @@ def run_ours(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sweep = [sweep_roofline(inst, args.steps, a, b, sm_max) for inst, a, b in zip(insts, sw0, sw1)]
     mode = [pg.pamc_sweep_mode(s.h) for s in solvers]
-    kname = ["k_sweep_ising_push" if m == 2 else "k_sweep_ising" for m in mode]
+    kname = ["k_sweep_ising_nib" if m & 16 else "k_sweep_ising_push" if m == 2 else "k_sweep_ising" for m in mode]
     e2e = e2e_measure(pg, torch, insts, args, local, start)
     dense = None
     if world == 1 and not args.no_dense:

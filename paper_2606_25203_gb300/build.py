@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpamc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "schedule.cu", "sweep.cu", "sweep_ising.cu", "population.cu", "noalloc.cu", "dense.cu", "diag.cu", "sweep_softmax.cu", "dense_tc.cu", "sweep_potts.cu", "sweep_wide.cu", "shard.cu"]
+SOURCES = ["api.cu", "schedule.cu", "sweep.cu", "sweep_ising.cu", "population.cu", "noalloc.cu", "dense.cu", "diag.cu", "sweep_softmax.cu", "dense_tc.cu", "sweep_potts.cu", "sweep_wide.cu", "shard.cu", "sweep_nibble.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

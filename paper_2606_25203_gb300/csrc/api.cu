@@ -105,6 +105,7 @@ struct pamc_handle_s {
     int2 *d_pos = nullptr;
     uint32_t *d_gsp = nullptr;   // Ising: replica groups' spin words in device memory
     bool gsp = false;            // the single-run sweeps use d_gsp (groups that do not fit on chip)
+    bool nib = false;            // the single-run sweeps use 4-bit lanes, eight replicas a word
     DevCtl *d_ctl = nullptr;
     int8_t *d_best = nullptr;
     // dense instances
@@ -274,6 +275,7 @@ void release_run(pamc_handle h) {
     h->d_spins[0] = h->d_spins[1] = nullptr;
     h->d_gsp = nullptr;
     h->gsp = false;
+    h->nib = false;
     h->sharded = false;
     h->sh_rank = 0; h->sh_nranks = 1; h->sh_base = 0; h->sh_count = 0; h->sh_phase = 0;
     h->d_plocal = h->d_rows = nullptr;
@@ -769,6 +771,17 @@ static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, 
         }
         h->gsp = true;
     }
+    // field ranges of at most 7 on ELL schedules: eight replicas a word
+    // (groups of eight, shaped like a population of half the size)
+    if (p.kind == 0 && !h->gsp && sweep_nibble_ok(h->H, p.sweeps, h->ell_w, 1, false)) {
+        SweepCfg c = choose_cfg(0, n, 4 * ((own + 7) / 8), h->H, avg_level, (double)h->nnz / std::max(n, 1), sms,
+                                h->ell_w);
+        c.lanes_per_vertex = 1;
+        if (sweep_nibble_smem_bytes(n, h->H, c) <= kSmemMax) {
+            h->cfg = c;
+            h->nib = true;
+        }
+    }
     if (!h->gsp && sweep_smem_bytes(sweep_kind(p), n, h->H, h->cfg) > kSmemMax) {
         release_run(h);
         return fail(h, PAMC_ERR_RANGE, "n = %d: one replica group's labels exceed shared memory", n);
@@ -832,7 +845,7 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
             e = launch_sweep(sweep_kind(p), p.rule, n, h->d_rp, h->d_adj, h->H, p, (int32_t)t,
                              (int32_t)(t % kSchedSlots), sv, h->d_tab, src, h->d_parent,
                              h->d_ncm_buf, h->d_ncm_idx, dst, Ed, h->d_ctl, h->cfg, h->W, h->stream,
-                             h->gsp ? h->d_gsp : nullptr);
+                             h->gsp ? h->d_gsp : nullptr, 0, h->nib);
         if (e == cudaSuccess) e = sweep_timer(h, true);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 2;
@@ -969,7 +982,7 @@ pamc_status pamc_shard_sweep(pamc_handle h, const int64_t *E_all, const int32_t 
         e = launch_sweep(sweep_kind(p), p.rule, n, h->d_rp, h->d_adj, h->H, pl, (int32_t)t,
                          (int32_t)(t % kSchedSlots), sv, h->d_tab, src, h->d_plocal, h->d_ncm_buf,
                          h->d_ncm_idx + h->sh_base, dst, Ed, h->d_ctl, h->cfg, h->W, h->stream,
-                         h->gsp ? h->d_gsp : nullptr, h->sh_base);
+                         h->gsp ? h->d_gsp : nullptr, h->sh_base, h->nib);
     if (e == cudaSuccess) e = sweep_timer(h, true);
     h->launches += 1;
     if (e == cudaSuccess && E_own)
@@ -1374,6 +1387,7 @@ pamc_status pamc_sweep_mode(pamc_handle h, int *mode) {
         return fail(h, PAMC_ERR_STATE, "no sparse Ising run initialised");
     const bool ell = h->d_ell != nullptr;
     if (h->gsp) *mode = (ell ? 1 : 0) | 4;
+    else if (h->nib) *mode = 1 | 16;
     else *mode = sweep_push_ok(h->H, h->p.sweeps, ell, h->cfg.lanes_per_vertex) ? 2 : ell ? 1 : 0;
     if (h->H > kByteLaneMaxH) *mode |= 8;
     return PAMC_OK;

@@ -202,6 +202,19 @@ cudaError_t launch_sweep_ising_wide(int rule, int32_t n, const int32_t *rp, cons
                                     const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, uint32_t *gsp,
                                     int32_t rbase = 0);
 
+// Ising sweeps with 4-bit field lanes, eight replicas per word
+// (sweep_nibble.cu): instances with H <= 7 on ELL schedules of width 4 or 8,
+// S >= 1, one lane per vertex, words in shared memory; off with
+// PAMC_SWEEP_NIBBLE=0.  Groups of eight replicas (ceil(R / 8) of them).
+constexpr int32_t kNibbleMaxH = 7;
+bool sweep_nibble_enabled();
+bool sweep_nibble_ok(int32_t H, int32_t S, int32_t ell_w, int lanes_per_vertex, bool global_spins);
+size_t sweep_nibble_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
+cudaError_t launch_sweep_ising_nib(int rule, int32_t n, int32_t H, const pamc_params &p, int32_t t, int32_t slot,
+                                   SchedView sv, const uint64_t *tab, const int8_t *src, const int32_t *parent,
+                                   const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
+                                   const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, int32_t rbase);
+
 // Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax;
 // every kind keeps groups of four replicas.
 size_t sweep_smem_bytes(int kind, int32_t n, int32_t H, SweepCfg cfg);
@@ -225,7 +238,7 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
                          const uint64_t *tab, const int8_t *src, const int32_t *parent,
                          const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst,
                          int64_t *E_dst, const DevCtl *ctl, SweepCfg cfg, int64_t Wsum,
-                         cudaStream_t st, uint32_t *gsp = nullptr, int32_t rbase = 0);
+                         cudaStream_t st, uint32_t *gsp = nullptr, int32_t rbase = 0, bool nib = false);
 
 // Random (re)initialisation of the population with key t, and its energies;
 // when only_if_restart is set the kernels do nothing unless the controller

@@ -87,7 +87,10 @@ cudaError_t launch_sweep(int kind, int rule, int32_t n, const int32_t *rp, const
                          const uint64_t *tab, const int8_t *src, const int32_t *parent,
                          const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst,
                          int64_t *E_dst, const DevCtl *ctl, SweepCfg cfg, int64_t Wsum,
-                         cudaStream_t st, uint32_t *gsp, int32_t rbase) {
+                         cudaStream_t st, uint32_t *gsp, int32_t rbase, bool nib) {
+    if (kind == 0 && nib)
+        return launch_sweep_ising_nib(rule, n, H, p, t, slot, sv, tab, src, parent, ncm_buf, ncm_idx, dst, E_dst,
+                                      ctl, cfg, st, rbase);
     if (kind == 0 && H > kByteLaneMaxH)
         return launch_sweep_ising_wide(rule, n, rp, adj, H, p, t, slot, sv, tab, src, parent, ncm_buf, ncm_idx,
                                        dst, E_dst, ctl, cfg, st, gsp, rbase);

@@ -301,6 +301,7 @@ def test_push_and_pull_sweeps(pg, monkeypatch, push, rule):
     a torus, a ragged signed sparse graph, and a hub of field range 63 with
     weights up to 3, under both rules and several group shapes."""
     monkeypatch.setenv("PAMC_SWEEP_PUSH", push)
+    monkeypatch.setenv("PAMC_SWEEP_NIBBLE", "0")     # the torus would take the 4-bit lanes
     cases = ((W.torus(20, 20, signed=True, seed=1), 13, "1,4,1"),
              (W.gnm(333, 900, signed=True, seed=2), 20, "3,2,1"),
              (_hub_instance(), 9, "2,1,1"))
@@ -432,6 +433,48 @@ def test_wide_field_range_refusals(pg):
     with pytest.raises(pg.PamcError) as e:
         pg.pamc_create_csr(big.n, big.row_ptr, big.col, big.w)
     assert e.value.status == 4
+
+
+def _max_degree_graph(n, m, dmax, seed):
+    """A random graph with +-1 weights and every degree <= dmax, some = dmax."""
+    rng = np.random.default_rng(seed)
+    deg = np.zeros(n, dtype=np.int64)
+    pairs = set()
+    while len(pairs) < m:
+        a, b = (int(x) for x in rng.integers(0, n, size=2))
+        if a == b or (min(a, b), max(a, b)) in pairs or deg[a] >= dmax or deg[b] >= dmax:
+            continue
+        pairs.add((min(a, b), max(a, b)))
+        deg[a] += 1
+        deg[b] += 1
+    ei, ej = np.array(sorted(pairs)).T
+    w = rng.choice([-1, 1], size=len(ei))
+    inst = W.csr_from_edges(n, ei, ej, w, f"maxdeg{dmax}")
+    assert deg.max() == dmax
+    return inst
+
+
+@pytest.mark.parametrize("nib", ["1", "0"])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_nibble_lanes(pg, monkeypatch, nib, rule):
+    """Field ranges up to 7 run eight replicas per word (4-bit lanes) on ELL
+    rows of width 4 (torus) and 8 (degree 7): the oracle's results step after
+    step with a ragged population (R not a multiple of 8), cluster moves and
+    restarts, and with the lanes switched off; range 8 keeps the byte lanes."""
+    monkeypatch.setenv("PAMC_SWEEP_NIBBLE", nib)
+    for inst, R in ((W.torus(18, 18, signed=True, seed=3), 13), (_max_degree_graph(400, 1100, 7, 4), 21),
+                    (_max_degree_graph(300, 700, 6, 5), 8)):
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+        s.init(R=R, sweeps=3, steps=3, rule=rule, seed=4)
+        assert pg.pamc_sweep_mode(s.h) == (17 if nib == "1" else 1), inst.name
+        s.close()
+        compare_run(pg, inst, 10, R=R, sweeps=3, beta0=0.2, beta1=3.0, rule=rule, stagnation=1, z_rst=7,
+                    cooldown_tau=1, win_short=2, win_long=3, seed=4)
+    eight = _max_degree_graph(300, 900, 8, 6)
+    s = pg.Solver(eight.row_ptr, eight.col, eight.w)
+    s.init(R=16, sweeps=2, steps=3, seed=1)
+    assert pg.pamc_sweep_mode(s.h) == 1
+    s.close()
 
 
 @pytest.mark.parametrize("rule", [0, 1])
