@@ -422,20 +422,35 @@ def run_ours(args):
     return result
 
 
+R_MAX = 16384   # the largest population one population step takes (pamc_init)
+
+
+def split_groups(world: int) -> int:
+    """GPUs per population: the largest divisor of world whose population of
+    4,096 replicas per GPU the population step takes (R <= 16,384)."""
+    return max(d for d in range(1, world + 1) if world % d == 0 and d * R <= R_MAX)
+
+
 def run_split(args, pg, torch, dist, rank, world, local):
-    """Several GPUs: ONE population of R = 4,096 x GPUs replicas per instance,
-    split in equal blocks over the GPUs (weak scaling: every GPU sweeps
-    4,096 replicas of each instance, as on one GPU).  Every iteration
-    gathers the R energies (NCCL all-gather), runs the same population step
-    and controller on every GPU, and moves the parent replicas that live on
-    another GPU (NCCL all-to-all); the result equals the one-GPU run of the
-    same R bit for bit.  The timed steps are the iterations the one-GPU line
-    times (its pre-pass on one GPU's population picks them)."""
+    """Several GPUs: populations of R = 4,096 x G replicas per instance, each
+    split in equal blocks over G GPUs (G = the GPUs up to R = 16,384, so one
+    population on up to four GPUs, two of 16,384 on eight; weak scaling:
+    every GPU sweeps 4,096 replicas of each instance, as on one GPU).  Every
+    iteration gathers the R energies of a population (NCCL all-gather), runs
+    the same population step and controller on each of its GPUs, and moves
+    the parent replicas that live on another GPU (NCCL all-to-all); the
+    result equals the one-GPU run of the same R bit for bit.  The timed
+    steps are the iterations the one-GPU line times (its pre-pass on one
+    GPU's population picks them)."""
     from paper_2606_25203_gb300 import shard as S
     insts = instances()
-    Rg = R * world
-    params = dict(PARAMS, R=Rg)
-    comm = S.TorchComm()
+    G = split_groups(world)
+    npop = world // G
+    pop, prank = rank // G, rank % G
+    groups = [dist.new_group(list(range(q * G, (q + 1) * G))) for q in range(npop)] if npop > 1 else [None]
+    Rg = R * G
+    params = dict(PARAMS, R=Rg, seed=PARAMS["seed"] + pop)
+    comm = S.TorchComm(groups[pop])
     streams = [torch.cuda.Stream() for _ in insts]
     start, events = 0, None
     if args.steps < STEPS_SCHEDULE and not args.lean:
@@ -451,7 +466,7 @@ def run_split(args, pg, torch, dist, rank, world, local):
         out = []
         for inst, st in zip(insts, streams):
             with torch.cuda.stream(st):
-                out.append(S.LibShard(inst.row_ptr, inst.col, inst.w, rank, world, device=local, **params))
+                out.append(S.LibShard(inst.row_ptr, inst.col, inst.w, prank, G, device=local, **params))
         return out
 
     def step_all(shards):
@@ -509,27 +524,29 @@ def run_split(args, pg, torch, dist, rank, world, local):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
                               "ms_per_step": ms / args.steps, "gpu_launches": launches, "clocks": clk.summary(),
-                              "config": {"only": ONLY, "R_total": Rg, "split": True}}))
+                              "config": {"only": ONLY, "R_total": Rg, "populations": npop, "split": True}}))
         dist.destroy_process_group()
         return None
     peaks, peak_src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sweep = sweep_roofline(insts[0], args.steps, sw0[0], sw1[0], sm_max)
-    e2e = split_e2e(args, pg, torch, S, comm, insts, params, rank, world, local, start, dist)
+    e2e = split_e2e(args, pg, torch, S, comm, insts, params, prank, G, local, start, dist)
     result = None
     if rank == 0:
         result = {
             "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("R=4096", f"one population of R={Rg} per instance"),
-                       "R": Rg, "R_per_gpu": R, "sweeps_per_step": SWEEPS,
+            "config": {"workload": WORKLOAD.replace("R=4096", f"{npop} population(s) of R={Rg} per instance"),
+                       "R": Rg, "populations": npop, "gpus_per_population": G, "R_per_gpu": R,
+                       "sweeps_per_step": SWEEPS,
                        "attempts_per_step": attempts_per_step(insts) * world,
                        "l2": "flushed between steps (512 MB write)",
                        "timed_steps": f"steps {start}..{start + args.steps - 1} of a fresh run",
                        "timed_window": window_summary(events, start, args.steps, ctl0, ctl1),
-                       "parallelism": f"one population split over {world} GPU(s): replica blocks, NCCL all-gather "
-                                      f"of the energies and all-to-all of the migrating replicas per iteration",
+                       "parallelism": f"{npop} population(s), each split over {G} GPU(s): replica blocks, NCCL "
+                                      f"all-gather of the energies and all-to-all of the migrating replicas per "
+                                      f"iteration",
                        "replicas_moved_per_step": moved / args.steps},
             "roofline": dict(sweep, traffic=None,
                              kernel=f"k_sweep_ising ({insts[0].name}, 4096 replicas per GPU, 10 sweeps per launch)",

@@ -50,7 +50,9 @@ class TorchComm:
                                     input_split_sizes=list(send_splits), group=self.group)
 
     def broadcast(self, t, src: int):
-        self.dist.broadcast(t, src, group=self.group)
+        """src: the rank within the group."""
+        g = src if self.group is None else self.dist.get_global_rank(self.group, src)
+        self.dist.broadcast(t, g, group=self.group)
 
 
 def run_step(shard, comm) -> None:

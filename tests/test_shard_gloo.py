@@ -146,6 +146,57 @@ def _rank_main(rank, world, port, case, out):
     out.put(res)
 
 
+def _groups_main(rank, world, port, out):
+    """Two populations of R = 16 over two ranks each (subgroups of a world of
+    four), with their own seeds, as the benchmark runs several populations
+    when one would exceed the population step's size."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2606_25203_gb300 import shard as S
+        groups = [dist.new_group([0, 1]), dist.new_group([2, 3])]
+        pop, prank = rank // 2, rank % 2
+        params = dict(CASES["ising_ncm"], R=16, steps=40, z_rst=30, seed=10 + pop)
+        shard = OracleShard(_instance(), prank, 2, params)
+        comm = S.TorchComm(groups[pop])
+        assert (comm.rank, comm.size) == (prank, 2)
+        for _ in range(params["steps"]):
+            S.run_step(shard, comm)
+        cut, best = S.best(shard, comm)
+        res = dict(rank=rank, pop=pop, spins=shard.run.spins()[shard.lo:shard.hi], cut=cut, best=best)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+    out.put(res)
+
+
+def test_two_populations_on_subgroups():
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_groups_main, args=(r, 4, port, q)) for r in range(4)]
+    for pr in procs:
+        pr.start()
+    res = sorted([q.get(timeout=300) for _ in range(4)], key=lambda d: d["rank"])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    inst = _instance()
+    for pop in (0, 1):
+        params = dict(CASES["ising_ncm"], R=16, steps=40, z_rst=30, seed=10 + pop)
+        ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **params)
+        ref.step(params["steps"])
+        part = [r for r in res if r["pop"] == pop]
+        np.testing.assert_array_equal(np.concatenate([r["spins"] for r in part]), ref.spins())
+        mstar, best = ref.best()
+        for r in part:
+            assert r["cut"] == mstar
+            np.testing.assert_array_equal(r["best"], best)
+        ref.close()
+
+
 def _run_split(case, world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
