@@ -424,9 +424,9 @@ pamc_status pamc_shard_best(pamc_handle h, int64_t *cut, int8_t *spins, int32_t 
  * fresh).  Calls whose device work overlaps on one GPU (different streams or
  * threads) race on it: serialise them.  The first call on each device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current and keeps it for the process; make that first call before any
- * stream capture.  A cudaDeviceReset while the library is loaded is not
- * supported (the kept address would be stale).  Each call waits for its
+ * current and keeps it for the process.  A cudaDeviceReset while the
+ * library is loaded is not supported (the kept address would be stale).
+ * Each call waits for its
  * stream twice: after validating the instance and before returning. */
 pamc_status pamc_sweeps_noalloc(int32_t n, int32_t nnz, const int32_t *row_ptr, const int32_t *col,
                                 const int32_t *w, int32_t H, int32_t rule, int32_t R,
