@@ -112,7 +112,12 @@ pamc_status pamc_create_dense(int32_t n, const int8_t *w, int w_on_device, int c
                               void *stream, pamc_handle *out);
 
 /* Set the run parameters, allocate the population and draw the random
- * initial population (Algorithm 1, Initialization).  Asynchronous. */
+ * initial population (Algorithm 1, Initialization).  1 <= R <= 1,048,576:
+ * up to 16,384 replicas the population step runs in one CTA, above in
+ * several kernels with the prefix sums in device memory (the same results),
+ * where a Max-Cut run with cluster moves takes at most 16,384 targets
+ * (n_top; PAMC_ERR_RANGE beyond).  Batches take members of up to 16,384.
+ * Asynchronous. */
 pamc_status pamc_init(pamc_handle h, const pamc_params *p);
 
 /* Enqueue nsteps iterations of Algorithm 1 (asynchronous; iterations after

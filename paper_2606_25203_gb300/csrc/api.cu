@@ -43,7 +43,7 @@ cudaError_t launch_tables(int kind, int rule, int32_t H, const DevCtl *ctl, uint
                           cudaStream_t st);
 cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
                         int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, uint64_t *qbuf,
-                        cudaStream_t st);
+                        cudaStream_t st, long long *mm = nullptr);
 cudaError_t launch_ncm(int32_t n, const int32_t *rp, const uint32_t *adj, const pamc_params &p,
                        const int8_t *src, const int64_t *E_src, const int32_t *parent,
                        const int32_t *targets, int8_t *ncm_buf, uint32_t *nkey,
@@ -95,6 +95,7 @@ struct pamc_handle_s {
     int64_t *d_E[2] = {nullptr, nullptr};
     int32_t *d_parent = nullptr, *d_count = nullptr, *d_ncm_idx = nullptr, *d_targets = nullptr;
     uint64_t *d_q = nullptr;   // resampling weights (sparse handles)
+    long long *d_mm = nullptr; // E_min / E_max of a large population (R > kPrepOneCtaMaxR)
     int32_t *d_fam = nullptr;   // [2][R] lineage (family of each slot)
     int8_t *d_ncm_buf = nullptr;
     uint32_t *d_nkey = nullptr;
@@ -279,6 +280,7 @@ void release_run(pamc_handle h) {
     h->sharded = false;
     h->sh_rank = 0; h->sh_nranks = 1; h->sh_base = 0; h->sh_count = 0; h->sh_phase = 0;
     h->d_plocal = h->d_rows = nullptr;
+    h->d_mm = nullptr;
 }
 
 // Words of the replica groups' spins in device memory (n_pad per group).
@@ -654,11 +656,14 @@ static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, 
         return fail(h, PAMC_ERR_ARG, "Potts: rule 0 (cascaded) needs K = 3, rule 2 (softmax) 2 <= K <= 8");
     if (p.kind == 1 && p.rule == 2 && !(p.gamma >= 0.0 && p.gamma < 1e30))
         return fail(h, PAMC_ERR_ARG, "softmax noise amplitude gamma must be finite and >= 0");
-    if (p.R < 1 || p.R > 16384) return fail(h, PAMC_ERR_RANGE, "R must be in [1, 16384]");
+    if (p.R < 1 || p.R > kMaxPopulation) return fail(h, PAMC_ERR_RANGE, "R must be in [1, %d]", kMaxPopulation);
     if (p.sweeps < 0 || p.steps < 1) return fail(h, PAMC_ERR_ARG, "sweeps >= 0 and steps >= 1 required");
     if (p.win_short < 0 || p.win_long < 0 || p.win_short > kHistMax || p.win_long > kHistMax)
         return fail(h, PAMC_ERR_RANGE, "stagnation windows must be in [0, %d]", kHistMax);
     if (p.n_top <= 0) p.n_top = std::max(1, p.R / 16);
+    if (p.R > kPrepOneCtaMaxR && p.stagnation && p.kind == 0 && std::min(p.n_top, p.R) > kNcmSelectMaxTop)
+        return fail(h, PAMC_ERR_RANGE, "populations above %d take at most %d NCM targets (n_top)", kPrepOneCtaMaxR,
+                    kNcmSelectMaxTop);
     if (p.mis_trials < 0) return fail(h, PAMC_ERR_ARG, "mis_trials must be >= 0");
     if (!(p.beta0 == p.beta0) || !(p.beta1 == p.beta1)) return fail(h, PAMC_ERR_ARG, "beta is NaN");
     cudaError_t e = cudaSetDevice(h->device);
@@ -705,6 +710,7 @@ static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, 
         ok = alloc_n(h, h->d_ncm_buf, (size_t)ntop * n, h->bufs) &&
              alloc_n(h, h->d_nkey, (size_t)ntop * n, h->bufs);
     if (ok && nranks > 0) ok = alloc_n(h, h->d_plocal, own, h->bufs) && alloc_n(h, h->d_rows, R, h->bufs);
+    if (ok && R > kPrepOneCtaMaxR) ok = alloc_n(h, h->d_mm, 2, h->bufs);
     if (!ok) {
         release_run(h);
         return fail(h, PAMC_ERR_OOM, "device allocation of the population failed");
@@ -831,7 +837,7 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
         int8_t *src = h->d_spins[t & 1], *dst = h->d_spins[(t + 1) & 1];
         int64_t *Es = h->d_E[t & 1], *Ed = h->d_E[(t + 1) & 1];
         e = launch_prep(p, Es, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
-                        h->d_q, h->stream);
+                        h->d_q, h->stream, h->d_mm);
         if (e == cudaSuccess) e = launch_tables(p.kind, p.rule, h->H, h->d_ctl, h->d_tab, h->stream);
         h->launches += 3;
         if (e == cudaSuccess && p.stagnation && p.kind == 0) {
@@ -921,7 +927,7 @@ pamc_status pamc_shard_resample(pamc_handle h, const int64_t *E_all, int32_t *pa
         h->launches += 1;
     }
     cudaError_t e = launch_prep(p, E_all, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
-                                h->d_q, h->stream);
+                                h->d_q, h->stream, h->d_mm);
     if (e == cudaSuccess) e = launch_tables(p.kind, p.rule, h->H, h->d_ctl, h->d_tab, h->stream);
     h->launches += 3;
     if (e == cudaSuccess)
@@ -1175,7 +1181,8 @@ pamc_status pamc_load(pamc_handle h, const void *buf, size_t size) {
         hd.inst_hash != h->inst_hash)
         return fail(h, PAMC_ERR_ARG, "the checkpoint belongs to another instance");
     const int32_t n = h->n, R = hd.p.R;
-    if (R < 1 || R > 16384 || size != ckpt_bytes(n, R)) return fail(h, PAMC_ERR_ARG, "checkpoint size mismatch");
+    if (R < 1 || R > kMaxPopulation || size != ckpt_bytes(n, R))
+        return fail(h, PAMC_ERR_ARG, "checkpoint size mismatch");
     DevCtl c;
     const char *in = static_cast<const char *>(buf) + sizeof(hd);
     memcpy(&c, in, sizeof(c));
@@ -1699,6 +1706,8 @@ pamc_status pamc_batch_add(pamc_batch b, pamc_handle h) {
     if (!h->initialized) return bfail(b, PAMC_ERR_STATE, "handle not initialised (pamc_init)");
     if (h->dense) return bfail(b, PAMC_ERR_ARG, "batches hold sparse instances");
     if (h->sharded) return bfail(b, PAMC_ERR_ARG, "a split population cannot join a batch");
+    if (h->p.R > kPrepOneCtaMaxR)
+        return bfail(b, PAMC_ERR_ARG, "batched members have at most %d replicas", kPrepOneCtaMaxR);
     if (h->H > kByteLaneMaxH)
         return bfail(b, PAMC_ERR_ARG, "batched members need sum_j |w_ij| <= %d", kByteLaneMaxH);
     if (h->p.kind == 1 && h->p.rule != 0)

@@ -11,6 +11,12 @@
 namespace pamc {
 
 constexpr int kHistMax = 64;   // longest stagnation window supported
+// Populations up to this size run the population step in one CTA (prefix
+// sums and the NCM target sort in shared memory); larger ones (up to
+// kMaxPopulation) in several kernels with the prefix sums in device memory.
+constexpr int32_t kPrepOneCtaMaxR = 16384;
+constexpr int32_t kMaxPopulation = 1 << 20;
+constexpr int32_t kNcmSelectMaxTop = 16384;   // NCM targets sorted in one CTA's shared memory
 
 // Algorithm 1's controller state, resident in device memory so that a whole
 // iteration (resample, NCM, sweeps, M*, control) runs without the host.

@@ -131,17 +131,23 @@ constexpr int kWeightThreads = 256;
 // when the step does not resample.
 __global__ void __launch_bounds__(kWeightThreads)
 k_weights(int32_t R, int32_t kind, int32_t do_resample, const int64_t *__restrict__ E_src,
-          const DevCtl *__restrict__ ctl, uint64_t *__restrict__ q) {
+          const DevCtl *__restrict__ ctl, uint64_t *__restrict__ q, const long long *__restrict__ mm) {
     __shared__ long long red_ll[32];
     if (ctl->done || !(ctl->z > 1 && do_resample)) return;
     const double delta = ctl->delta;
-    long long lmin = LLONG_MAX, lmax = LLONG_MIN;
-    for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
-        lmin = min(lmin, (long long)E_src[r]);
-        lmax = max(lmax, (long long)E_src[r]);
+    long long emin, emax;
+    if (mm) {   // large populations: reduced once by k_minmax
+        emin = mm[0];
+        emax = mm[1];
+    } else {
+        long long lmin = LLONG_MAX, lmax = LLONG_MIN;
+        for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
+            lmin = min(lmin, (long long)E_src[r]);
+            lmax = max(lmax, (long long)E_src[r]);
+        }
+        emin = block_reduce(lmin, [](long long a, long long b) { return a < b ? a : b; }, red_ll);
+        emax = block_reduce(lmax, [](long long a, long long b) { return a > b ? a : b; }, red_ll);
     }
-    const long long emin = block_reduce(lmin, [](long long a, long long b) { return a < b ? a : b; }, red_ll);
-    const long long emax = block_reduce(lmax, [](long long a, long long b) { return a > b ? a : b; }, red_ll);
     const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     int lg = 0;
@@ -327,6 +333,227 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_batched(const PrepDesc *_
     if (t >= d.t_end) return;
     prep_body(d.R, d.kind, d.do_resample, d.n_top, d.tau, d.key0, d.key1, d.en[t & 1], d.ctl, d.parent, d.count,
               d.ncm_idx, d.targets, d.fam, d.fam_reset, nullptr);
+}
+
+// ---------------------------------------------------------------- large populations
+// R > kPrepOneCtaMaxR: the prefix sums live in device memory and the steps
+// of prep_body run as separate kernels -- the same definitions (Eq. 1-2,
+// systematic resampling by binary search over the integer prefix sums, the
+// n_top lowest (energy, slot) NCM targets), so every result is the one a
+// single CTA would give.
+constexpr int kBigThreads = 1024;
+
+__global__ void __launch_bounds__(kBigThreads)
+k_minmax(int32_t R, int32_t do_resample, const int64_t *__restrict__ E, const DevCtl *__restrict__ ctl,
+         long long *__restrict__ mm) {
+    __shared__ long long red_ll[32];
+    if (ctl->done || !(ctl->z > 1 && do_resample)) return;
+    long long lmin = LLONG_MAX, lmax = LLONG_MIN;
+    for (int32_t r = threadIdx.x; r < R; r += blockDim.x) {
+        lmin = min(lmin, (long long)E[r]);
+        lmax = max(lmax, (long long)E[r]);
+    }
+    const long long emin = block_reduce(lmin, [](long long a, long long b) { return a < b ? a : b; }, red_ll);
+    const long long emax = block_reduce(lmax, [](long long a, long long b) { return a > b ? a : b; }, red_ll);
+    if (threadIdx.x == 0) { mm[0] = emin; mm[1] = emax; }
+}
+
+// Inclusive prefix sums of the weights, in place: a contiguous chunk per
+// thread, the chunk totals scanned across the block (one CTA).
+__global__ void __launch_bounds__(kBigThreads)
+k_scan_big(int32_t R, int32_t do_resample, uint64_t *__restrict__ q, const DevCtl *__restrict__ ctl) {
+    __shared__ unsigned long long red_u[32];
+    if (ctl->done || !(ctl->z > 1 && do_resample)) return;
+    const int32_t per = (R + blockDim.x - 1) / blockDim.x;
+    const int32_t lo = min(R, (int32_t)threadIdx.x * per), hi = min(R, lo + per);
+    unsigned long long local = 0;
+    for (int32_t r = lo; r < hi; ++r) {
+        local += q[r];
+        q[r] = local;
+    }
+    unsigned long long x = local;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) red_u[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long v = lane < (int)(blockDim.x >> 5) ? red_u[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        red_u[lane] = v;
+    }
+    __syncthreads();
+    const unsigned long long excl = (x - local) + (wid > 0 ? red_u[wid - 1] : 0ull);
+    for (int32_t r = lo; r < hi; ++r) q[r] += excl;
+}
+
+// Parent of every slot (binary search over the prefix sums C), copy counts
+// (count zeroed beforehand), lineage and the NCM index reset: one thread per slot.
+__global__ void __launch_bounds__(256)
+k_parent_big(int32_t R, int32_t do_resample, uint32_t key0, uint32_t key1, const uint64_t *__restrict__ C,
+             const DevCtl *__restrict__ ctl, int32_t *__restrict__ parent, int32_t *__restrict__ count,
+             int32_t *__restrict__ ncm_idx, int32_t *__restrict__ fam, int32_t fam_reset) {
+    if (ctl->done) return;
+    const int32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= R) return;
+    const int32_t t = ctl->t;
+    const bool resampled = ctl->z > 1 && do_resample;
+    ncm_idx[m] = -1;
+    int32_t pm = m;
+    if (resampled) {
+        const uint64_t T = C[R - 1];
+        const u32x4 u = philox(0u, 0u, (uint32_t)t, kTagResample << 24, key0, key1);
+        const uint64_t v = ((uint64_t)u.y << 32) | (uint64_t)u.x;
+        const uint64_t U = __umul64hi(v, T);
+        const unsigned __int128 pos = (unsigned __int128)m * T + U;
+        int32_t lo2 = 0, hi2 = R - 1;   // smallest j with R*C_j > pos
+        while (lo2 < hi2) {
+            const int32_t mid = (lo2 + hi2) >> 1;
+            if ((unsigned __int128)R * C[mid] > pos) hi2 = mid;
+            else lo2 = mid + 1;
+        }
+        pm = lo2;
+        atomicAdd(&count[pm], 1);
+    } else {
+        count[m] = 1;
+    }
+    parent[m] = pm;
+    if (fam) {
+        const int32_t *fs = fam + (size_t)(t & 1) * R;
+        int32_t *fd = fam + (size_t)((t + 1) & 1) * R;
+        fd[m] = (fam_reset && ctl->restart != 0) ? m : fs[pm];
+    }
+}
+
+// NCM targets of a large population (one CTA): the n_top slots of lowest
+// (energy, slot).  The n_top-th smallest energy is found by a radix select
+// over E - E_min (eight passes of eight bits); the slots below it and the
+// lowest-index slots at it are gathered and sorted by (energy, slot) in
+// shared memory.  Then the controller flags of the population step.
+__global__ void __launch_bounds__(kBigThreads)
+k_ncm_select_big(int32_t R, int32_t kind, int32_t do_resample, int32_t n_top, int32_t tau,
+                 const int64_t *__restrict__ E_src, const int32_t *__restrict__ parent, DevCtl *__restrict__ ctl,
+                 int32_t *__restrict__ targets, int32_t *__restrict__ ncm_idx) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ long long red_ll[32];
+    __shared__ unsigned int hist[256];
+    __shared__ unsigned int s_base[kBigThreads / 32];
+    __shared__ unsigned long long s_prefix;
+    __shared__ unsigned int s_k;
+    if (ctl->done) return;
+    const int32_t z = ctl->z;
+    const bool resampled = z > 1 && do_resample;
+    const bool ncm = z > 1 && ctl->enable_cm && ctl->cooldown == 0;
+    __syncthreads();
+    if (ncm && kind == 0) {
+        const int32_t ntop = min(n_top, R);
+        long long lmin = LLONG_MAX;
+        for (int32_t m = threadIdx.x; m < R; m += blockDim.x) lmin = min(lmin, (long long)E_src[parent[m]]);
+        const long long emin = block_reduce(lmin, [](long long a, long long b) { return a < b ? a : b; }, red_ll);
+        auto key = [&](int32_t m) { return (unsigned long long)((long long)E_src[parent[m]] - emin); };
+        // radix select of the ntop-th smallest key (1-based rank k)
+        if (threadIdx.x == 0) { s_prefix = 0ull; s_k = (unsigned)ntop; }
+        unsigned long long mask = 0ull;
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0u;
+            __syncthreads();
+            const unsigned long long pre = s_prefix;
+            for (int32_t m = threadIdx.x; m < R; m += blockDim.x) {
+                const unsigned long long kk = key(m);
+                if ((kk & mask) == pre) atomicAdd(&hist[(kk >> shift) & 0xFFu], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned int k = s_k, b = 0;
+                while (hist[b] < k) { k -= hist[b]; ++b; }
+                s_k = k;
+                s_prefix = pre | ((unsigned long long)b << shift);
+            }
+            mask |= 0xFFull << shift;
+            __syncthreads();
+        }
+        const unsigned long long kv = s_prefix;   // the ntop-th smallest key
+        const unsigned int take_eq = s_k;         // slots at kv to take, lowest indices first
+        // gather: keys below kv, and the first take_eq slots (by index) at kv;
+        // a contiguous range of slots per thread keeps the index order
+        unsigned long long *Ek = reinterpret_cast<unsigned long long *>(sm);
+        int32_t P2 = 1;
+        while (P2 < ntop) P2 <<= 1;
+        int32_t *Mi = reinterpret_cast<int32_t *>(sm + (size_t)P2 * 8);
+        const int32_t per = (R + blockDim.x - 1) / blockDim.x;
+        const int32_t lo = min(R, (int32_t)threadIdx.x * per), hi = min(R, lo + per);
+        unsigned int n_eq = 0, n_lt = 0;
+        for (int32_t m = lo; m < hi; ++m) {
+            const unsigned long long kk = key(m);
+            n_eq += kk == kv ? 1u : 0u;
+            n_lt += kk < kv ? 1u : 0u;
+        }
+        // exclusive prefix over threads of n_eq (for the equal-key quota) and
+        // of the number each thread writes
+        auto block_excl = [&](unsigned int v) {
+            unsigned int x = v;
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            __syncthreads();
+            if (lane == 31) s_base[wid] = x;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned int acc = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { const unsigned int c = s_base[w]; s_base[w] = acc; acc += c; }
+            }
+            __syncthreads();
+            return x - v + s_base[wid];
+        };
+        const unsigned int eq_before = block_excl(n_eq);
+        const unsigned int eq_mine = eq_before >= take_eq ? 0u : min(n_eq, take_eq - eq_before);
+        const unsigned int out_before = block_excl(n_lt + eq_mine);
+        unsigned int o = out_before, eq_taken = 0;
+        for (int32_t m = lo; m < hi; ++m) {
+            const unsigned long long kk = key(m);
+            bool take = kk < kv;
+            if (kk == kv && eq_taken < eq_mine) { take = true; ++eq_taken; }
+            if (take) { Ek[o] = kk; Mi[o] = m; ++o; }
+        }
+        for (int32_t x = ntop + threadIdx.x; x < P2; x += blockDim.x) { Ek[x] = ~0ull; Mi[x] = INT32_MAX; }
+        __syncthreads();
+        for (int32_t k = 2; k <= P2; k <<= 1) {
+            for (int32_t j = k >> 1; j > 0; j >>= 1) {
+                for (int32_t i = threadIdx.x; i < P2; i += blockDim.x) {
+                    const int32_t l = i ^ j;
+                    if (l > i) {
+                        const unsigned long long ei = Ek[i], el = Ek[l];
+                        const int32_t mi = Mi[i], ml = Mi[l];
+                        const bool gt = ei > el || (ei == el && mi > ml);
+                        if (gt == ((i & k) == 0)) {
+                            Ek[i] = el; Ek[l] = ei;
+                            Mi[i] = ml; Mi[l] = mi;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int32_t q = threadIdx.x; q < ntop; q += blockDim.x) {
+            const int32_t m = Mi[q];
+            targets[q] = m;
+            ncm_idx[m] = q;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->resampled = resampled ? 1 : 0;
+        ctl->ncm_active = ncm ? 1 : 0;
+        ctl->ncm_last = ncm ? 1 : 0;
+        if (ncm) { ctl->enable_cm = 0; ctl->cooldown = tau; }
+    }
 }
 
 // ---------------------------------------------------------------- NCM
@@ -628,15 +855,40 @@ size_t prep_smem_bytes(int32_t R) {
     return P2 * 8 + P2 * 4;
 }
 
+size_t ncm_select_smem_bytes(int32_t n_top) {
+    size_t P2 = 1;
+    while (P2 < (size_t)(n_top > 1 ? n_top : 1)) P2 <<= 1;
+    return P2 * 8 + P2 * 4;
+}
+
 cudaError_t launch_prep(const pamc_params &p, const int64_t *E_src, DevCtl *ctl, int32_t *parent,
                         int32_t *count, int32_t *ncm_idx, int32_t *targets, int32_t *fam, uint64_t *qbuf,
-                        cudaStream_t st) {
+                        cudaStream_t st, long long *mm) {
+    if (p.R > kPrepOneCtaMaxR) {
+        if (!qbuf || !mm) return cudaErrorInvalidValue;
+        const int fam_reset = p.z_rst > 0 && p.restart_reinit ? 1 : 0;
+        const int32_t ntop = p.n_top < p.R ? p.n_top : p.R;
+        const size_t sel_smem = ncm_select_smem_bytes(ntop);
+        cudaError_t err = allow_dynamic_smem(k_ncm_select_big, sel_smem);
+        if (err != cudaSuccess) return err;
+        k_minmax<<<1, kBigThreads, 0, st>>>(p.R, p.resample, E_src, ctl, mm);
+        k_weights<<<(p.R + kWeightThreads - 1) / kWeightThreads, kWeightThreads, 0, st>>>(p.R, p.kind, p.resample,
+                                                                                          E_src, ctl, qbuf, mm);
+        k_scan_big<<<1, kBigThreads, 0, st>>>(p.R, p.resample, qbuf, ctl);
+        err = cudaMemsetAsync(count, 0, sizeof(int32_t) * (size_t)p.R, st);
+        if (err != cudaSuccess) return err;
+        k_parent_big<<<(p.R + 255) / 256, 256, 0, st>>>(p.R, p.resample, (uint32_t)p.seed, (uint32_t)(p.seed >> 32),
+                                                        qbuf, ctl, parent, count, ncm_idx, fam, fam_reset);
+        k_ncm_select_big<<<1, kBigThreads, sel_smem, st>>>(p.R, p.kind, p.resample, p.n_top, p.cooldown_tau, E_src,
+                                                           parent, ctl, targets, ncm_idx);
+        return cudaGetLastError();
+    }
     const size_t smem = prep_smem_bytes(p.R);
     cudaError_t err = allow_dynamic_smem(k_prep, smem);
     if (err != cudaSuccess) return err;
     if (qbuf)
         k_weights<<<(p.R + kWeightThreads - 1) / kWeightThreads, kWeightThreads, 0, st>>>(p.R, p.kind, p.resample,
-                                                                                          E_src, ctl, qbuf);
+                                                                                          E_src, ctl, qbuf, nullptr);
     k_prep<<<1, kPrepThreads, smem, st>>>(p.R, p.kind, p.resample, p.n_top, p.cooldown_tau,
                                           (uint32_t)p.seed, (uint32_t)(p.seed >> 32), E_src, ctl,
                                           parent, count, ncm_idx, targets, fam,

@@ -487,6 +487,36 @@ def test_maximum_population(pg, rule):
     assert ref.ctl()["ncm_flipped"] > 0
 
 
+@pytest.mark.parametrize("R,extra", [(16385, dict(stagnation=1, n_top=3000)),
+                                     (32768, dict(stagnation=1, rule=1)),
+                                     (20001, dict(stagnation=1, n_top=16384, z_rst=5)),
+                                     (65536, dict())])
+def test_large_populations(pg, R, extra):
+    """Populations above 16,384 (the population step in several kernels,
+    prefix sums in device memory, NCM targets by radix select) against the
+    oracle step by step: just above the threshold, ragged sizes, the largest
+    NCM target count, both rules, a restart."""
+    inst = W.torus(8, 8, signed=True, seed=11)
+    params = dict(sweeps=2, beta0=0.3, beta1=3.0, win_short=2, win_long=3, cooldown_tau=1, seed=13)
+    params.update(extra)
+    ref, _ = compare_run(pg, inst, 7, R=R, **params)
+    if params.get("stagnation"):
+        assert ref.ctl()["ncm_flipped"] > 0
+
+
+def test_large_population_limits(pg):
+    inst = W.torus(8, 8, signed=True, seed=11)
+    h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+    with pytest.raises(pg.PamcError) as e:       # too many NCM targets for the one-CTA sort
+        pg.pamc_init(h, R=40000, steps=3, stagnation=1, n_top=16385)
+    assert e.value.status == pg.STATUS_CODES["PAMC_ERR_RANGE"]
+    with pytest.raises(pg.PamcError) as e:
+        pg.pamc_init(h, R=(1 << 20) + 1, steps=3)
+    assert e.value.status == pg.STATUS_CODES["PAMC_ERR_RANGE"]
+    pg.pamc_init(h, R=40000, steps=3, stagnation=0, n_top=16385)   # no cluster moves: no limit on n_top
+    pg.pamc_destroy(h)
+
+
 def test_degenerate_sizes_other_placements(pg, monkeypatch):
     """One vertex, one replica, zero sweeps, with the spin words in device
     memory and with 16-bit field lanes."""

@@ -166,7 +166,8 @@ def test_split_equals_single_and_oracle_small(pg, G):
     orc.close()
 
 
-@pytest.mark.parametrize("case", ["sparse_ncm", "potts_cascaded", "potts_softmax", "wide_lanes", "global_words"])
+@pytest.mark.parametrize("case", ["sparse_ncm", "potts_cascaded", "potts_softmax", "wide_lanes", "global_words",
+                                  "large_population"])
 def test_split_equals_single_handle(pg, monkeypatch, case):
     G = 4
     if case == "sparse_ncm":
@@ -183,6 +184,10 @@ def test_split_equals_single_handle(pg, monkeypatch, case):
         from test_gpu_parity import _weighted_hub
         inst = _weighted_hub()
         params = dict(R=64, steps=40, sweeps=2, beta0=0.01, beta1=0.5, stagnation=1, z_rst=30, seed=8)
+    elif case == "large_population":   # 32,768 replicas: the population step in several kernels
+        inst = W.torus(10, 10, signed=True, seed=2)
+        params = dict(R=32768, steps=12, sweeps=2, beta0=0.3, beta1=3.0, stagnation=1, win_short=2, win_long=3,
+                      cooldown_tau=1, z_rst=9, seed=12)
     else:
         monkeypatch.setenv("PAMC_SWEEP_GLOBAL", "1")
         inst = W.torus(40, 40, signed=True, seed=1)
