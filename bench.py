@@ -422,20 +422,21 @@ def run_ours(args):
     return result
 
 
-R_MAX = 16384   # the largest population one population step takes (pamc_init)
+R_MAX = 1 << 20   # the largest population pamc_init takes
 
 
 def split_groups(world: int) -> int:
     """GPUs per population: the largest divisor of world whose population of
-    4,096 replicas per GPU the population step takes (R <= 16,384)."""
+    4,096 replicas per GPU pamc_init takes (R <= 1,048,576): all of them up
+    to 256 GPUs."""
     return max(d for d in range(1, world + 1) if world % d == 0 and d * R <= R_MAX)
 
 
 def run_split(args, pg, torch, dist, rank, world, local):
-    """Several GPUs: populations of R = 4,096 x G replicas per instance, each
-    split in equal blocks over G GPUs (G = the GPUs up to R = 16,384, so one
-    population on up to four GPUs, two of 16,384 on eight; weak scaling:
-    every GPU sweeps 4,096 replicas of each instance, as on one GPU).  Every
+    """Several GPUs: ONE population of R = 4,096 x GPUs replicas per instance
+    (several of at most 1,048,576 beyond 256 GPUs), split in equal blocks over
+    the GPUs (weak scaling: every GPU sweeps 4,096 replicas of each instance,
+    as on one GPU).  Every
     iteration gathers the R energies of a population (NCCL all-gather), runs
     the same population step and controller on each of its GPUs, and moves
     the parent replicas that live on another GPU (NCCL all-to-all); the
