@@ -779,7 +779,7 @@ static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, 
     }
     // field ranges of at most 7 on ELL schedules: eight replicas a word
     // (groups of eight, shaped like a population of half the size)
-    if (p.kind == 0 && !h->gsp && sweep_nibble_ok(h->H, p.sweeps, h->ell_w, 1, false)) {
+    if (p.kind == 0 && !h->gsp && sweep_nibble_ok(h->H, p.sweeps, h->ell_w, 1, false) && !sweep_push_enabled()) {
         SweepCfg c = choose_cfg(0, n, 4 * ((own + 7) / 8), h->H, avg_level, (double)h->nnz / std::max(n, 1), sms,
                                 h->ell_w);
         c.lanes_per_vertex = 1;
@@ -1514,17 +1514,28 @@ pamc_status rebuild(pamc_batch b) {
     std::vector<int2> swi[2][2][kClasses];   // Ising, spin words on chip [ell][rule][class]
     std::vector<int2> gswi[2][2][kClasses];  // Ising, spin words in device memory
     std::vector<int2> pswi[2][kClasses];     // Potts (cascaded sampler) [ell][class]
-    int32_t nmax[kClasses] = {0, 0, 0}, pnmax[kClasses] = {0, 0, 0}, gnmax[kClasses] = {0, 0, 0}, Rmax = 1;
+    std::vector<int2> nswi[2][kClasses];     // Ising, 4-bit lanes (ELL rows) [rule][class]
+    int32_t nmax[kClasses] = {0, 0, 0}, pnmax[kClasses] = {0, 0, 0}, gnmax[kClasses] = {0, 0, 0},
+            nnmax[kClasses] = {0, 0, 0}, Rmax = 1;
     auto member_global = [&](pamc_handle h) { return h->p.kind == 0 && (h->gsp || b->global[batch_class(h->n)]); };
+    // field ranges up to 7 on ELL rows take eight replicas a word, as alone
+    auto member_nib = [&](pamc_handle h) {
+        return h->p.kind == 0 && !member_global(h) && sweep_nibble_ok(h->H, h->p.sweeps, h->ell_w, 1, false) &&
+               !sweep_push_enabled();
+    };
     for (pamc_handle h : b->members)
         if (h->host_t < h->p.steps) {
-            int32_t &m = (h->p.kind != 0 ? pnmax : member_global(h) ? gnmax : nmax)[batch_class(h->n)];
+            int32_t &m = (h->p.kind != 0 ? pnmax : member_global(h) ? gnmax : member_nib(h) ? nnmax
+                                                                                            : nmax)[batch_class(h->n)];
             m = std::max(m, h->n);
         }
     // the shape of each class, with fewer groups per CTA where the largest
     // member's spins (Ising: 4n bytes a group, Potts: 8n) need it
-    SweepCfg eff[kClasses], peff[kClasses], geff[kClasses];
+    SweepCfg eff[kClasses], peff[kClasses], geff[kClasses], neff[kClasses];
     for (int c = 0; c < kClasses; ++c) {
+        neff[c] = SweepCfg{b->shape[c].groups_per_cta, b->shape[c].warps_per_group, 1};
+        while (neff[c].groups_per_cta > 1 && sweep_nibble_smem_bytes(nnmax[c], kNibbleMaxH, neff[c]) > kSmemMax)
+            neff[c].groups_per_cta -= 1;
         geff[c] = SweepCfg{b->shape[c].groups_per_cta, b->shape[c].warps_per_group, 1};
         eff[c] = b->shape[c];
         while (eff[c].groups_per_cta > 1 && sweep_ising_smem_bytes(nmax[c], 127, eff[c]) > kSmemMax)
@@ -1565,14 +1576,17 @@ pamc_status rebuild(pamc_batch b) {
         if (gl && !h->d_gsp && !alloc_n(h, h->d_gsp, gsp_words(h->n, p.R), h->bufs))
             return bfail(b, PAMC_ERR_OOM, "device allocation of a member's group spin words failed");
         d.gsp = gl ? h->d_gsp : nullptr;
-        const SweepCfg cfg = p.kind != 0 ? peff[cls] : gl ? geff[cls] : eff[cls];
-        d.push = p.kind == 0 && !gl && sweep_push_ok(h->H, p.sweeps, h->d_ell != nullptr, cfg.lanes_per_vertex) ? 1 : 0;
+        const bool nb = member_nib(h);
+        const SweepCfg cfg = p.kind != 0 ? peff[cls] : gl ? geff[cls] : nb ? neff[cls] : eff[cls];
+        d.push = p.kind == 0 && !gl && !nb && sweep_push_ok(h->H, p.sweeps, h->d_ell != nullptr, cfg.lanes_per_vertex)
+                     ? 1 : 0;
         const int idx = (int)sw.size();
         sw.push_back(d);
-        const int32_t ctas = ((p.R + 3) / 4 + cfg.groups_per_cta - 1) / cfg.groups_per_cta;
+        const int32_t groups = nb ? (p.R + 7) / 8 : (p.R + 3) / 4;
+        const int32_t ctas = (groups + cfg.groups_per_cta - 1) / cfg.groups_per_cta;
         // with sweeps = 0 the launch still copies the resampled population and its energies
         auto &items = p.kind != 0 ? pswi[h->d_ell != nullptr][cls]
-                                  : (gl ? gswi : swi)[h->d_ell != nullptr][p.rule][cls];
+                                  : nb ? nswi[p.rule][cls] : (gl ? gswi : swi)[h->d_ell != nullptr][p.rule][cls];
         for (int32_t x = 0; x < ctas; ++x) items.push_back(make_int2(idx, x));
         Rmax = std::max(Rmax, p.R);
         CtlDesc c{nullptr, nullptr, h->d_best, h->d_ctl, h->W, p.target_cut, p.reheat_factor, p.beta0,
@@ -1588,6 +1602,8 @@ pamc_status rebuild(pamc_batch b) {
         for (auto &c : a)
             for (auto &v : c) all_items.insert(all_items.end(), v.begin(), v.end());
     for (auto &a : pswi)
+        for (auto &v : a) all_items.insert(all_items.end(), v.begin(), v.end());
+    for (auto &a : nswi)
         for (auto &v : a) all_items.insert(all_items.end(), v.begin(), v.end());
     const bool ok = upload(b, b->sd, sd) && upload(b, b->sdi, sdi) && upload(b, b->prep, prep) &&
                     upload(b, b->tabs, tabs) && upload(b, b->sw, sw) && upload(b, b->ctl, ctls) &&
@@ -1630,6 +1646,15 @@ pamc_status rebuild(pamc_batch b) {
             if (items.empty()) continue;
             e = launch_sweep_potts_batched(el != 0, (const SweepDesc *)b->sw.p, (const int2 *)b->swi.p + off,
                                            (int32_t)items.size(), pnmax[c], peff[c], b->stream);
+            off += items.size();
+            nl += 1;
+        }
+    for (int ru = 0; ru < 2 && e == cudaSuccess; ++ru)
+        for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+            const auto &items = nswi[ru][c];
+            if (items.empty()) continue;
+            e = launch_sweep_ising_nib_batched(ru, (const SweepDesc *)b->sw.p, (const int2 *)b->swi.p + off,
+                                               (int32_t)items.size(), nnmax[c], neff[c], b->stream);
             off += items.size();
             nl += 1;
         }

@@ -220,6 +220,10 @@ cudaError_t launch_sweep_ising_nib(int rule, int32_t n, int32_t H, const pamc_pa
                                    SchedView sv, const uint64_t *tab, const int8_t *src, const int32_t *parent,
                                    const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
                                    const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, int32_t rbase);
+// Batched 4-bit-lane sweeps (members with H <= 7, ELL width 4 or 8, S >= 1,
+// words on chip); items (member, block of groups of eight).
+cudaError_t launch_sweep_ising_nib_batched(int rule, const SweepDesc *descs, const int2 *items, int32_t nitems,
+                                           int32_t n_max, SweepCfg cfg, cudaStream_t st);
 
 // Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax;
 // every kind keeps groups of four replicas.

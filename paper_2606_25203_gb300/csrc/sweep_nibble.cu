@@ -29,11 +29,18 @@ namespace pamc {
 
 namespace {
 
-// Philox draws with the round keys of the seed in kernel parameter space.
+// Philox draws with the round keys of the seed in kernel parameter space, or
+// advanced from the seed (batched launches: the key differs per member).
 struct NibKeys {
     const PhiloxKeys &K;
     __device__ __forceinline__ u32x4 operator()(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) const {
         return philox_rk(c0, c1, c2, c3, K);
+    }
+};
+struct NibKeysSeed {
+    uint32_t k0, k1;
+    __device__ __forceinline__ u32x4 operator()(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3) const {
+        return philox(c0, c1, c2, c3, k0, k1);
     }
 };
 
@@ -70,13 +77,18 @@ __device__ __forceinline__ uint32_t ising_decide8(uint32_t A, int32_t c0, const 
     return nw;
 }
 
-template <int RULE, int WC>
-__global__ void __launch_bounds__(1024) k_sweep_ising_nib(SweepDesc d, int gpc, int tpg) {
+// The sweeps of one CTA's groups of eight (groups bid*gpc .. bid*gpc+gpc-1
+// of the instance), shared by the single-instance and the batched kernels;
+// WC = 0: the ELL width (4 or 8) read at run time.
+template <int RULE, int WC, class KeyT>
+__device__ __forceinline__ void
+nib_body(const SweepDesc &d, const KeyT &draw, int32_t t, int32_t slot, const int8_t *__restrict__ src,
+         int8_t *__restrict__ dst, int64_t *__restrict__ E_dst, int gpc, int tpg, int32_t bid) {
     extern __shared__ __align__(16) uint8_t smem[];
     const DevCtl *ctl = d.ctl;
     if (ctl->done) return;
-    const int32_t n = d.n, n_pad = d.n_pad, H = d.H, R = d.R, S = d.S, t = d.t, slot = d.slot;
-    constexpr int32_t W = WC;
+    const int32_t n = d.n, n_pad = d.n_pad, H = d.H, R = d.R, S = d.S;
+    const int32_t W = WC > 0 ? WC : d.W;
     const int tabn = 2 * H + 1;
     uint64_t *tab_s = reinterpret_cast<uint64_t *>(smem);
     uint32_t *spins_all = reinterpret_cast<uint32_t *>(smem + (((size_t)tabn * 8 + 15) & ~(size_t)15));
@@ -85,7 +97,7 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_nib(SweepDesc d, int gpc, 
     for (int i = threadIdx.x; i < gpc * 8; i += blockDim.x) red[i] = 0ull;
 
     const int gl = threadIdx.x / tpg, li = threadIdx.x % tpg;
-    const int32_t g = blockIdx.x * gpc + gl;   // group of eight replicas
+    const int32_t g = bid * gpc + gl;   // group of eight replicas
     const int32_t r0 = g * 8;
     const bool active = r0 < R;
     uint32_t *sp = spins_all + (size_t)gl * n_pad;
@@ -99,7 +111,7 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_nib(SweepDesc d, int gpc, 
             const int32_t r = r0 + q;
             if (r < R) {
                 const int32_t m = d.ncm_idx[r];
-                rows[q] = m >= 0 ? d.ncm_buf + (size_t)m * n : d.src + (size_t)d.parent[r] * n;
+                rows[q] = m >= 0 ? d.ncm_buf + (size_t)m * n : src + (size_t)d.parent[r] * n;
             } else {
                 rows[q] = nullptr;
             }
@@ -115,7 +127,6 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_nib(SweepDesc d, int gpc, 
     __syncthreads();
 
     if (active) {
-        const NibKeys draw{d.K};
         const size_t ell_stride = (size_t)(((n + 31) >> 5) << 5) * W;
         const uint32_t ctrA = (kTagFlip << 24) | (uint32_t)(2 * g + d.gbase);
         const uint32_t ctrB = ctrA + 1u;
@@ -223,7 +234,7 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_nib(SweepDesc d, int gpc, 
             const uint32_t w = sp[k];
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                if (r0 + q < R) d.dst[(size_t)(r0 + q) * n + k] = ((w >> (4 * q)) & 1u) ? 1 : -1;
+                if (r0 + q < R) dst[(size_t)(r0 + q) * n + k] = ((w >> (4 * q)) & 1u) ? 1 : -1;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -233,7 +244,25 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_nib(SweepDesc d, int gpc, 
         }
     }
     __syncthreads();
-    if (active && li < 8 && r0 + li < R) d.E_dst[r0 + li] = -((long long)red[gl * 8 + li] / 2);
+    if (active && li < 8 && r0 + li < R) E_dst[r0 + li] = -((long long)red[gl * 8 + li] / 2);
+}
+
+template <int RULE, int WC>
+__global__ void __launch_bounds__(1024) k_sweep_ising_nib(SweepDesc d, int gpc, int tpg) {
+    nib_body<RULE, WC>(d, NibKeys{d.K}, d.t, d.slot, d.src, d.dst, d.E_dst, gpc, tpg, blockIdx.x);
+}
+
+// Many instances in one launch: CTA b works on member items[b].x, its block
+// of groups items[b].y; the step index comes from the member's controller.
+template <int RULE>
+__global__ void __launch_bounds__(1024)
+k_sweep_ising_nib_batched(const SweepDesc *__restrict__ descs, const int2 *__restrict__ items, int gpc, int tpg) {
+    const int2 it = items[blockIdx.x];
+    const SweepDesc &d = descs[it.x];
+    const int32_t t = d.ctl->t;
+    if (t >= d.t_end) return;
+    nib_body<RULE, 0>(d, NibKeysSeed{d.K.k0[0], d.K.k1[0]}, t, t % d.slots, d.sp[t & 1], d.sp[(t + 1) & 1],
+                      d.en[(t + 1) & 1], gpc, tpg, it.y);
 }
 
 }  // namespace
@@ -286,6 +315,24 @@ cudaError_t launch_sweep_ising_nib(int rule, int32_t n, int32_t H, const pamc_pa
         else PAMC_NIB(1, 8);
     }
 #undef PAMC_NIB
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_ising_nib_batched(int rule, const SweepDesc *descs, const int2 *items, int32_t nitems,
+                                           int32_t n_max, SweepCfg cfg, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
+    const size_t smem = sweep_nibble_smem_bytes(n_max, kNibbleMaxH, cfg);
+    cudaError_t err;
+    if (rule == 0) {
+        err = allow_dynamic_smem(k_sweep_ising_nib_batched<0>, smem);
+        if (err != cudaSuccess) return err;
+        k_sweep_ising_nib_batched<0><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg);
+    } else {
+        err = allow_dynamic_smem(k_sweep_ising_nib_batched<1>, smem);
+        if (err != cudaSuccess) return err;
+        k_sweep_ising_nib_batched<1><<<nitems, gpc * tpg, smem, st>>>(descs, items, gpc, tpg);
+    }
     return cudaGetLastError();
 }
 
