@@ -463,12 +463,13 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                             for (int q = 0; q < 4; ++q)   // padding slots: coupling 0
                                 A += sp[e4[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e4[q] >> 24);
                             u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
-                        } else {
+                        } else if constexpr (WC > 0 && WC <= 16) {
                         const uint32_t *ep = ell_row(es, i, W) + 4 * 32;
-                        // up to twelve more neighbour words in flight before the
-                        // draw, in blocks of four slots (a level's positions are
-                        // grouped by degree, so a warp's lanes mostly agree on
-                        // how many blocks they need)
+                        // rows of at most sixteen slots (compile-time width):
+                        // the words beyond the first four in blocks of four,
+                        // all in flight before the draw (a level's positions
+                        // are grouped by degree, so a warp's lanes mostly
+                        // agree on how many blocks they need)
                         uint32_t ev[4], ew[4], ex[4];
                         if (deg > 4) {
 #pragma unroll
@@ -501,14 +502,39 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                             for (int q = 0; q < 4; ++q)
                                 A += sp[ex[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ex[q] >> 24);
                         }
-                        for (int32_t b0 = 16; b0 < deg; b0 += 8) {
-                            const uint32_t *eq = ep + (size_t)(b0 - 4) * 32;
-                            uint32_t ey[8];
+                        } else {
+                        const uint32_t *ep = ell_row(es, i, W) + 4 * 32;
+                        // up to sixteen more neighbour words in flight before the draw
+                        uint32_t ev[8], ew[8];
+                        if (deg > 4) {
 #pragma unroll
-                            for (int q = 0; q < 8; ++q) ey[q] = (b0 + q < W) ? eq[q * 32] : 0u;
+                            for (int q = 0; q < 8; ++q) ev[q] = (4 + q < W) ? ep[q * 32] : 0u;
+                        }
+                        if (deg > 12) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) ew[q] = (12 + q < W) ? ep[(8 + q) * 32] : 0u;
+                        }
+                        u = draw((uint32_t)k, (uint32_t)sw, (uint32_t)t, ctr3);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)   // padding slots: coupling 0
+                            A += sp[e4[q] & 0xFFFFFFu] * (uint32_t)((int32_t)e4[q] >> 24);
+                        if (deg > 4) {
 #pragma unroll
                             for (int q = 0; q < 8; ++q)
-                                A += sp[ey[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ey[q] >> 24);
+                                A += sp[ev[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ev[q] >> 24);
+                        }
+                        if (deg > 12) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                A += sp[ew[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ew[q] >> 24);
+                        }
+                        for (int32_t b0 = 20; b0 < deg; b0 += 8) {
+                            ep += (b0 == 20 ? 16 : 8) * 32;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) ev[q] = (b0 + q < W) ? ep[q * 32] : 0u;
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                A += sp[ev[q] & 0xFFFFFFu] * (uint32_t)((int32_t)ev[q] >> 24);
                         }
                         }
                     } else {
