@@ -334,8 +334,9 @@ pamc_status pamc_load(pamc_handle h, const void *buf, size_t size);
  *   pamc_shard_sweep -> all-gather E_own into E_all
  *   pamc_shard_control(E_all)
  * (the first all-gather may reuse the last one when no restart redraws the
- * population: p->z_rst == 0 or p->restart_reinit == 0).  Sparse (CSR)
- * instances only.  pamc_step, pamc_set_population, pamc_hamming and batches
+ * population: p->z_rst == 0 or p->restart_reinit == 0).  Sparse and dense
+ * instances (dense: at most 64 replicas per process).  pamc_step,
+ * pamc_set_population, pamc_hamming and batches
  * refuse a split handle; pamc_state returns its own slots; the NCM counters
  * of pamc_control_state count its own slots. */
 

@@ -124,6 +124,7 @@ struct pamc_handle_s {
     unsigned long long *d_flip = nullptr, *d_snew = nullptr;
     void *d_bar = nullptr;
     int32_t dense_Hc = 0, dense_grid = 0, dense_nupd = 0, dense_rows = 0;
+    int32_t dense_R = 0;                 // replicas this handle sweeps (p.R unless split over processes)
     int64_t launches = 0;
     // device time of the sweep launches (pamc_set_sweep_timing): events
     // recorded on the handle's stream around each sweep launch, in pairs
@@ -384,15 +385,19 @@ SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level,
 cudaError_t dense_recompute(pamc_handle h, const int8_t *src, const int32_t *parent, const int32_t *ncm_idx,
                             int restart_t) {
     if (h->dense_tc)
-        return launch_dense_recompute_tc(h->n, h->p.R, h->tm_J, h->tm_S, src, parent, nullptr, ncm_idx, h->d_Sb,
+        return launch_dense_recompute_tc(h->n, h->dense_R, h->tm_J, h->tm_S, src, parent, nullptr, ncm_idx, h->d_Sb,
                                          h->d_H, h->d_ctl, h->stream, restart_t);
-    return launch_dense_recompute(h->n, h->p.R, h->d_J, src, parent, nullptr, ncm_idx, h->d_H, h->d_ctl,
+    return launch_dense_recompute(h->n, h->dense_R, h->d_J, src, parent, nullptr, ncm_idx, h->d_H, h->d_ctl,
                                   h->stream, restart_t);
 }
 
-pamc_status init_dense(pamc_handle h, pamc_params p) {
+// own: the replicas this handle sweeps (base: the first one's index in the
+// whole population of p.R); own = p.R unless the population is split.
+pamc_status init_dense(pamc_handle h, pamc_params p, int32_t base, int32_t own, bool split) {
     if (p.kind != 0) return fail(h, PAMC_ERR_ARG, "dense instances run the Ising (Max-Cut) kind only");
-    if (p.R > 64) return fail(h, PAMC_ERR_RANGE, "dense instances support R <= 64");
+    if (own > 64) return fail(h, PAMC_ERR_RANGE, "dense instances support at most 64 replicas per handle");
+    if (p.R > kPrepOneCtaMaxR) return fail(h, PAMC_ERR_RANGE, "dense populations hold at most %d replicas",
+                                            kPrepOneCtaMaxR);
     if (p.stagnation && (h->n & 1))
         return fail(h, PAMC_ERR_ARG, "cluster moves on dense instances need even n (no iso-sites then)");
     if (p.sweeps > 64) return fail(h, PAMC_ERR_RANGE, "dense instances support at most 64 sweeps per step");
@@ -400,7 +405,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     if (!coop) return fail(h, PAMC_ERR_CUDA, "device lacks cooperative launch");
-    const int32_t n = h->n, R = p.R, S = std::max(p.sweeps, 1);
+    const int32_t n = h->n, R = own, Rg = p.R, S = std::max(p.sweeps, 1);
     const int chain = (R + 3) / 4;
     const int grid = sms;
     const int nupd = grid - chain;
@@ -420,14 +425,17 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
     h->dense_rows = rows;
     h->dense_tcu = tcu;
     h->dense_Hc = std::min<int32_t>(n, 32767);
+    h->dense_R = R;
     const int B = dense_block_positions();
     const size_t tabn = (size_t)2 * h->dense_Hc + 1;
-    bool ok = alloc_n(h, h->d_spins[0], (size_t)R * n, h->bufs) &&
-              alloc_n(h, h->d_spins[1], (size_t)R * n, h->bufs) &&
+    // spin rows: the own replicas, and as many again for received parents
+    const size_t rows_sp = split ? 2 * (size_t)R : (size_t)R;
+    bool ok = alloc_n(h, h->d_spins[0], rows_sp * n, h->bufs) &&
+              alloc_n(h, h->d_spins[1], rows_sp * n, h->bufs) &&
               alloc_n(h, h->d_E[0], 64, h->bufs) && alloc_n(h, h->d_E[1], 64, h->bufs) &&
-              alloc_n(h, h->d_parent, R, h->bufs) && alloc_n(h, h->d_count, R, h->bufs) &&
-              alloc_n(h, h->d_fam, 2 * (size_t)R, h->bufs) &&
-              alloc_n(h, h->d_ncm_idx, R, h->bufs) && alloc_n(h, h->d_targets, R, h->bufs) &&
+              alloc_n(h, h->d_parent, Rg, h->bufs) && alloc_n(h, h->d_count, Rg, h->bufs) &&
+              alloc_n(h, h->d_fam, 2 * (size_t)Rg, h->bufs) &&
+              alloc_n(h, h->d_ncm_idx, Rg, h->bufs) && alloc_n(h, h->d_targets, Rg, h->bufs) &&
               alloc_n(h, h->d_tab, tabn, h->bufs) && alloc_n(h, h->d_ctl, 1, h->bufs) &&
               alloc_n(h, h->d_best, n, h->bufs) && alloc_n(h, h->d_H, (size_t)R * n, h->bufs) &&
               alloc_n(h, h->d_perm, (size_t)S * n, h->bufs) && alloc_n(h, h->d_pkey, (size_t)S * n, h->bufs) &&
@@ -437,6 +445,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
               (h->d_bar = dev_alloc(h, 64, h->bufs)) != nullptr &&
               alloc_n(h, h->d_ident, R, h->bufs) && alloc_n(h, h->d_nonc, R, h->bufs) &&
               alloc_n(h, h->d_boff, dense_perm_offsets(S), h->bufs);
+    if (ok && split) ok = alloc_n(h, h->d_plocal, R, h->bufs) && alloc_n(h, h->d_rows, Rg, h->bufs);
     const char *rc_env = getenv("PAMC_DENSE_RECOMPUTE");   // "mma": the mma.sync kernel
     h->dense_tc = dense_tc_supported(n) && !(rc_env && strcmp(rc_env, "mma") == 0);
     if (ok && h->dense_tc) {
@@ -457,20 +466,21 @@ pamc_status init_dense(pamc_handle h, pamc_params p) {
     c.delta = c.dbeta;
     c.mstar = INT64_MIN;
     c.best_replica = -1;
-    std::vector<int32_t> ident(R), ones(R, 1), minus(R, -1);
-    for (int32_t r = 0; r < R; ++r) ident[r] = r;
+    std::vector<int32_t> ident(Rg), ones(Rg, 1), minus(Rg, -1);
+    for (int32_t r = 0; r < Rg; ++r) ident[r] = r;
     cudaError_t e = cudaMemcpyAsync(h->d_ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_parent, ident.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_fam, ident.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_parent, ident.data(), 4 * Rg, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_fam, ident.data(), 4 * Rg, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ident, ident.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_count, ones.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ncm_idx, minus.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_count, ones.data(), 4 * Rg, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ncm_idx, minus.data(), 4 * Rg, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_nonc, minus.data(), 4 * R, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_best, 0, n, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_E[0], 0, 64 * 8, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_E[1], 0, 64 * 8, h->stream);
     // initial population, its fields (tensor-core recompute) and energies
-    if (e == cudaSuccess) e = launch_init_spins(0, 0, n, R, p.seed, 0, 0, h->d_ctl, h->d_spins[0], h->stream);
+    if (e == cudaSuccess)
+        e = launch_init_spins(0, 0, n, R, p.seed, 0, 0, h->d_ctl, h->d_spins[0], h->stream, base);
     if (e == cudaSuccess)
         e = dense_recompute(h, h->d_spins[0], h->d_ident, h->d_nonc, -1);
     if (e == cudaSuccess)
@@ -668,12 +678,21 @@ static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, 
     if (!(p.beta0 == p.beta0) || !(p.beta1 == p.beta1)) return fail(h, PAMC_ERR_ARG, "beta is NaN");
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
-    if (nranks > 0 && h->dense)
-        return fail(h, PAMC_ERR_ARG, "a split population needs a sparse (CSR) instance");
     int32_t base = 0, own = p.R;   // own slots [base, base + own)
     if (nranks > 0 && pamc_shard_range(p.R, nranks, rank, &base, &own) != PAMC_OK)
         return fail(h, PAMC_ERR_ARG, "split population: need 0 <= rank < nranks and R a multiple of 4 nranks");
-    if (h->dense) return init_dense(h, p);
+    if (h->dense) {
+        const pamc_status s = init_dense(h, p, base, own, nranks > 0);
+        if (s == PAMC_OK && nranks > 0) {
+            h->sharded = true;
+            h->sh_rank = rank;
+            h->sh_nranks = nranks;
+            h->sh_base = base;
+            h->sh_count = own;
+            h->sh_phase = 0;
+        }
+        return s;
+    }
     if (p.kind == 1 && h->H > kByteLaneMaxH)
         return fail(h, PAMC_ERR_RANGE, "Max-3-Cut runs need sum_j |w_ij| <= %d (this instance: %d)", kByteLaneMaxH,
                     h->H);
@@ -919,6 +938,24 @@ pamc_status pamc_shard_resample(pamc_handle h, const int64_t *E_all, int32_t *pa
     const pamc_params &p = h->p;
     const int64_t t = h->host_t;
     if (t > INT32_MAX - 2) return fail(h, PAMC_ERR_RANGE, "step counter overflow");
+    if (h->dense) {   // the step's order, the population step (no cluster moves) and the tables
+        pamc_params pp = p;
+        pp.n_top = 0;
+        cudaError_t e = launch_dense_perm(h->n, p.seed, (int32_t)t, p.sweeps, h->d_perm, h->d_pkey, h->d_sidx,
+                                          h->d_boff, h->d_ctl, h->stream);
+        if (e == cudaSuccess)
+            e = launch_prep(pp, E_all, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, h->d_fam,
+                            nullptr, h->stream);
+        if (e == cudaSuccess) e = launch_dense_tables(p.rule, h->dense_Hc, h->n, h->d_ctl, h->d_tab, h->stream);
+        h->launches += 4;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(parent, h->d_parent, sizeof(int32_t) * (size_t)p.R, cudaMemcpyDeviceToHost,
+                                h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "pamc_shard_resample");
+        h->sh_phase = 1;
+        return PAMC_OK;
+    }
     if (p.sweeps > 0 && t >= h->sched_end) {
         launch_schedule(h->n, h->d_rp, h->d_adj, p.seed, (int32_t)t, kSchedSlots, p.sweeps, 0, kSchedSlots,
                         h->d_order, h->d_lvl, h->d_nlev, h->d_skey, h->d_scnt, h->stream, h->d_ell, h->ell_w,
@@ -975,6 +1012,22 @@ pamc_status pamc_shard_sweep(pamc_handle h, const int64_t *E_all, const int32_t 
                                     h->stream);
     if (e == cudaSuccess && nimports > 0)
         e = cudaMemcpyAsync(src + (size_t)c * n, imports, (size_t)nimports * n, cudaMemcpyDeviceToDevice, h->stream);
+    if (h->dense) {   // the fields of the own slots' parents, then the sweeps
+        if (e == cudaSuccess) e = dense_recompute(h, src, h->d_plocal, h->d_ncm_idx + h->sh_base, -1);
+        if (e == cudaSuccess) e = sweep_timer(h, false);
+        if (e == cudaSuccess)
+            e = launch_dense_sweep(n, c, p.sweeps, p.rule, h->dense_Hc, (int32_t)t, p.seed, h->dense_nupd,
+                                   h->dense_rows, h->dense_grid, h->d_J, h->d_perm, h->d_tab, src, h->d_plocal,
+                                   nullptr, h->d_ncm_idx + h->sh_base, h->d_H, dst, Ed, h->d_G, h->d_T, h->d_T2,
+                                   h->d_flip, h->d_snew, h->d_bar, h->d_ctl, h->stream, h->dense_tcu, h->sh_base);
+        if (e == cudaSuccess) e = sweep_timer(h, true);
+        h->launches += 4;
+        if (e == cudaSuccess && E_own)
+            e = cudaMemcpyAsync(E_own, Ed, sizeof(int64_t) * (size_t)c, cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "pamc_shard_sweep");
+        h->sh_phase = 2;
+        return PAMC_OK;
+    }
     if (e == cudaSuccess && p.stagnation && p.kind == 0) {
         e = launch_ncm(n, h->d_rp, h->d_adj, p, src, E_all, h->d_parent, h->d_targets, h->d_ncm_buf, h->d_nkey,
                        h->d_ctl, h->stream, h->sh_base, c, h->d_plocal);
@@ -1011,9 +1064,17 @@ pamc_status pamc_shard_control(pamc_handle h, const int64_t *E_all, int64_t *E_o
     cudaError_t e = launch_control(n, h->W, p, E_all, dst, h->d_best, h->d_ctl, h->stream, h->sh_base, c);
     h->launches += 1;
     if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
-        e = launch_init(p.kind, p.K, n, h->d_rp, h->d_adj, c, p.seed, (int32_t)(t + 1), 1, h->d_ctl, h->W, dst, Ed,
-                        h->stream, h->sh_base);
-        h->launches += 2;
+        if (h->dense) {
+            const int32_t tk = (int32_t)(t + 1);
+            e = launch_init_spins(0, 0, n, c, p.seed, tk, 1, h->d_ctl, dst, h->stream, h->sh_base);
+            if (e == cudaSuccess) e = dense_recompute(h, dst, h->d_ident, h->d_nonc, tk);
+            if (e == cudaSuccess) e = launch_dense_energy(n, c, h->d_H, dst, Ed, h->d_ctl, h->stream, tk);
+            h->launches += 3;
+        } else {
+            e = launch_init(p.kind, p.K, n, h->d_rp, h->d_adj, c, p.seed, (int32_t)(t + 1), 1, h->d_ctl, h->W, dst,
+                            Ed, h->stream, h->sh_base);
+            h->launches += 2;
+        }
     }
     if (e == cudaSuccess && E_own)
         e = cudaMemcpyAsync(E_own, Ed, sizeof(int64_t) * (size_t)c, cudaMemcpyDeviceToDevice, h->stream);

@@ -470,6 +470,7 @@ struct DenseSweepArgs {
     unsigned long long *snew; // [3][kB] replica bit masks of the new spin (+1)
     GridBar *bar;
     DevCtl *ctl;
+    int32_t gbase;            // group index of the first local replica group in the whole population
 };
 
 __device__ __forceinline__ const int8_t *pop_row(const DenseSweepArgs &a, int r) {
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_dense_sweep(DenseSweepArgs a)
         const int32_t t = (int32_t)threadIdx.x - tid0;
         int32_t *thr = thr_all + (size_t)(qb & 1) * 4 * kB;
         for (int32_t m = t; m < cnt; m += nthr) {
-            const u32x4 u = philox_rk((uint32_t)P[m], (uint32_t)sw, (uint32_t)a.t, (kTagFlip << 24) | (uint32_t)cg, a.K);
+            const u32x4 u = philox_rk((uint32_t)P[m], (uint32_t)sw, (uint32_t)a.t, (kTagFlip << 24) | (uint32_t)(cg + a.gbase), a.K);
             udraw[m] = u.x;
             udraw[kB + m] = u.y;
             udraw[2 * kB + m] = u.z;
@@ -1504,7 +1505,8 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
                                const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int32_t *H, int8_t *dst, int64_t *E,
                                int32_t *G, uint32_t *T, uint32_t *T2, unsigned long long *flip,
-                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st, bool tcu) {
+                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st, bool tcu,
+                               int32_t rbase) {
     DenseSweepArgs a;
     a.n = n; a.R = R; a.S = S; a.rule = rule; a.Hc = Hc; a.n_upd = n_upd; a.rows_per = rows_per;
     a.ntiles = (rows_per + 127) / 128;
@@ -1512,6 +1514,7 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
     a.tab = tab; a.src = src; a.parent = parent; a.ncm_buf = ncm_buf; a.ncm_idx = ncm_idx; a.H = H;
     a.dst = dst; a.E = E; a.G = G; a.T = T; a.T2 = T2; a.flip = flip; a.snew = snew;
     a.bar = reinterpret_cast<GridBar *>(bar); a.ctl = ctl;
+    a.gbase = rbase / 4;
     if (tcu && (a.ntiles > kTuMaxTiles || n % 16 != 0 || rows_per % 32 != 0)) return cudaErrorInvalidValue;
     const size_t smem = dense_sweep_smem(n, R, rows_per, tcu);
     const void *fn = tcu ? (const void *)k_dense_sweep<true> : (const void *)k_dense_sweep<false>;

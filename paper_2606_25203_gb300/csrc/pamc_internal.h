@@ -288,7 +288,8 @@ cudaError_t launch_dense_recompute(int32_t n, int32_t R, const int8_t *J, const 
 cudaError_t launch_dense_energy(int32_t n, int32_t R, const int32_t *H, const int8_t *spins, int64_t *E,
                                 const DevCtl *ctl, cudaStream_t st, int restart_t);
 cudaError_t launch_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint64_t seed, int32_t t,
-                              int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st);
+                              int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st,
+                              int32_t rbase = 0);
 int dense_block_positions();
 int dense_sweep_threads();
 size_t dense_sweep_smem(int32_t n, int32_t R, int32_t rows_per, bool tcu);
@@ -298,7 +299,8 @@ cudaError_t launch_dense_sweep(int32_t n, int32_t R, int32_t S, int32_t rule, in
                                const int8_t *src, const int32_t *parent, const int8_t *ncm_buf,
                                const int32_t *ncm_idx, int32_t *H, int8_t *dst, int64_t *E,
                                int32_t *G, uint32_t *T, uint32_t *T2, unsigned long long *flip,
-                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st, bool tcu);
+                               unsigned long long *snew, void *bar, DevCtl *ctl, cudaStream_t st, bool tcu,
+                               int32_t rbase = 0);
 cudaError_t launch_dense_to_e4m3(size_t total, int8_t *J, cudaStream_t st);
 
 // ---- dense recompute on tcgen05 (dense_tc.cu), n a multiple of 16

@@ -124,13 +124,14 @@ cudaError_t launch_energy(int kind, int32_t n, const int32_t *rp, const uint32_t
 }
 
 cudaError_t launch_init_spins(int kind, int32_t K, int32_t n, int32_t R, uint64_t seed, int32_t t,
-                              int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st) {
+                              int only_if_restart, const DevCtl *ctl, int8_t *spins, cudaStream_t st,
+                              int32_t rbase) {
     const size_t total = (size_t)((R + 3) / 4) * n;
     int grid = (int)((total + 255) / 256);
     if (grid > 152 * 16) grid = 152 * 16;
     if (grid < 1) grid = 1;
     k_init_spins<<<grid, 256, 0, st>>>(kind, K, n, R, (uint32_t)seed, (uint32_t)(seed >> 32), t,
-                                        only_if_restart, ctl, spins, 0);
+                                        only_if_restart, ctl, spins, rbase / 4);
     return cudaGetLastError();
 }
 

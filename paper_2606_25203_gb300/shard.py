@@ -27,7 +27,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (load, pamc_create_csr, pamc_destroy, pamc_shard_best, pamc_shard_control, pamc_shard_energies,
+from . import (load, pamc_create_csr, pamc_create_dense, pamc_destroy, pamc_shard_best, pamc_shard_control,
+               pamc_shard_energies,
                pamc_shard_init, pamc_shard_pack, pamc_shard_plan, pamc_shard_range, pamc_shard_resample,
                pamc_shard_sweep)
 
@@ -105,14 +106,20 @@ class LibShard:
     The handle runs on the current torch stream of its device, so the
     collectives torch issues afterwards are ordered behind its kernels."""
 
-    def __init__(self, row_ptr, col, w, rank: int, nranks: int, device: int = 0, **params):
+    def __init__(self, row_ptr, col, w, rank: int, nranks: int, device: int = 0, dense_w=None, **params):
+        """A CSR instance (row_ptr, col, w), or a dense one (dense_w: n x n
+        int8 weights, host array or CUDA tensor; row_ptr, col, w None)."""
         import torch
         load()
         self.torch = torch
         self.dev = torch.device("cuda", device)
-        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
-        self.n = len(rp) - 1
-        self.h = pamc_create_csr(self.n, rp, col, w, device=device)
+        if dense_w is not None:
+            self.n = int(dense_w.shape[0])
+            self.h = pamc_create_dense(self.n, dense_w, device=device)
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            self.n = len(rp) - 1
+            self.h = pamc_create_csr(self.n, rp, col, w, device=device)
         self.p = pamc_shard_init(self.h, rank, nranks, **params)
         self.R, self.rank, self.nranks = int(self.p.R), int(rank), int(nranks)
         self.base, self.count = pamc_shard_range(self.R, nranks, rank)

@@ -203,6 +203,58 @@ def test_split_equals_single_handle(pg, monkeypatch, case):
     assert sum(p["moved"] for p in parts) > 0
 
 
+def _run_split_dense(pg, w, G, nsteps, params):
+    from paper_2606_25203_gb300 import shard as S
+    group = _Group(G)
+    out, errs = [None] * G, []
+
+    def work(rank):
+        try:
+            sh = S.LibShard(None, None, None, rank, G, dense_w=w, **params)
+            comm = ThreadComm(group, rank)
+            for _ in range(nsteps):
+                S.run_step(sh, comm)
+            cut, best = S.best(sh, comm)
+            spins, E, par, cnt = pg.pamc_state(sh.h, sh.count, sh.n)
+            out[rank] = dict(spins=spins, E=E, par=par, cnt=cnt, ctl=pg.pamc_control_state(sh.h),
+                             hist=pg.pamc_control_history(sh.h), cut=cut, best=best, moved=sh.moved)
+            sh.close()
+        except BaseException as e:   # noqa: BLE001 -- re-raised below
+            errs.append(e)
+            group.barrier.abort()
+
+    threads = [threading.Thread(target=work, args=(r,)) for r in range(G)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errs:
+        raise errs[0]
+    return out
+
+
+@pytest.mark.parametrize("G", [2, 4])
+def test_split_dense_equals_single_handle(pg, G):
+    """A dense +-1 instance (n = 2,048) with R = 64 split over two and four
+    handles (the dense sweep's chains and tensor-core field updates on each
+    handle's replicas, draws keyed by the global replica index) equals the
+    single-handle run, through a restart that re-draws the population."""
+    n = 2048
+    w = W.dense_rows_np(n, np.arange(n), seed=4)
+    params = dict(R=64, steps=30, sweeps=2, beta0=0.05, beta1=1.5, z_rst=17, seed=21)
+    parts = _run_split_dense(pg, w, G, params["steps"], params)
+    h = pg.pamc_create_dense(n, w)
+    p = pg.pamc_init(h, **params)
+    pg.pamc_step(h, params["steps"])
+    spins, E, par, cnt = pg.pamc_state(h, p.R, n)
+    ref = dict(spins=spins, E=E, par=par, cnt=cnt, ctl=pg.pamc_control_state(h), hist=pg.pamc_control_history(h),
+               best=pg.pamc_best(h, n))
+    pg.pamc_destroy(h)
+    assert_split_equals(parts, ref, f"dense G={G}")
+    assert ref["ctl"]["cycle"] >= 1
+    assert sum(p["moved"] for p in parts) > 0
+
+
 def test_split_phase_order_and_refusals(pg):
     """Calls out of order and the single-population calls on a split handle
     are refused on the host; a bad plan argument is refused before any
