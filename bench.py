@@ -843,8 +843,74 @@ def dense_measure(pg, torch, n, steps, warmup, e2e=False):
 def run_dense(args):
     import torch
     import paper_2606_25203_gb300 as pg
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 or args.split:
+        return run_dense_split(args, pg, torch, world)
     pg.load()
     print(json.dumps(dense_measure(pg, torch, args.dense_n, args.steps, args.warmup, e2e=args.dense_e2e)))
+
+
+def run_dense_split(args, pg, torch, world):
+    """Configuration 4 on several GPUs: one population of R = 64 x GPUs,
+    64 replicas per GPU (weak scaling), J on every GPU; every iteration
+    gathers the energies, runs the same population step everywhere and moves
+    the parent replicas (n int8 each) that live on another GPU (NCCL).
+    Steps 0..K-1 of a fresh anneal (after K warm-up steps of another run),
+    device-timed, max over GPUs."""
+    import torch.distributed as dist
+    from paper_2606_25203_gb300 import shard as S
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world == 1 and "MASTER_ADDR" not in os.environ:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29543")
+    dist.init_process_group("nccl", world_size=world, rank=rank)
+    pg.load()
+    n = args.dense_n
+    w = dense_weights_device(torch, n)
+    params = dict(DENSE_PARAMS, R=64 * world)
+    comm = S.TorchComm()
+    cur = torch.cuda.current_stream()
+
+    def make():
+        return S.LibShard(None, None, None, rank, world, device=local, dense_w=w, **params)
+
+    warm = make()
+    for _ in range(args.warmup):
+        S.run_step(warm, comm)
+    warm.close()
+    sh = make()
+    del w
+    torch.cuda.empty_cache()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(cur)
+            S.run_step(sh, comm)
+            ev[k][1].record(cur)
+        torch.cuda.synchronize()
+    dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    own = sh.count * n * params["sweeps"] * args.steps
+    ms, att = reduce_over_ranks(dist, ms, own)
+    cut, _ = S.best(sh, comm)
+    moved = sh.moved
+    sh.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": att / (ms / 1e3), "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": DENSE_WORKLOAD.replace("R=64", f"one population of R={64 * world}"),
+                       "n": n, "R": 64 * world, "R_per_gpu": 64,
+                       "parallelism": f"one population split over {world} GPU(s), NCCL exchange per iteration",
+                       "replicas_moved_per_step": moved / args.steps,
+                       "timed_steps": f"steps 0..{args.steps - 1} of a fresh run"},
+            "best_cut": int(cut), "clocks": clk.summary()}))
+    dist.destroy_process_group()
 
 
 SERVE_PARAMS = dict(R=512, sweeps=10, steps=200, beta0=0.1, beta1=3.0, seed=0)
