@@ -1378,12 +1378,18 @@ pamc_status pamc_hamming(pamc_handle h, int64_t *hist, int64_t *sum) {
     const size_t nb = (size_t)n / 2 + 1, nw = ((size_t)n + 31) / 32;
     std::vector<DevBuf> tmp;
     uint32_t *bits = nullptr;
+    uint8_t *sb = nullptr;
     unsigned long long *dh = nullptr;
-    if (!alloc_n(h, bits, std::max<size_t>((size_t)R * nw, 1), tmp) || !alloc_n(h, dh, nb + 1, tmp)) {
+    const bool tc = hamming_tc_enabled(n, R);   // overlaps on the tensor cores, else XOR-popcount
+    const bool ok = tc ? alloc_n(h, sb, hamming_tc_scratch(n, R), tmp)
+                       : alloc_n(h, bits, std::max<size_t>((size_t)R * nw, 1), tmp);
+    if (!ok || !alloc_n(h, dh, nb + 1, tmp)) {
         dev_free_all(h, tmp);
         return fail(h, PAMC_ERR_OOM, "device allocation for the Hamming distances failed");
     }
-    cudaError_t e = launch_hamming(n, R, h->d_spins[c.t & 1], bits, dh, dh + nb, h->stream);
+    int *err = reinterpret_cast<int *>(reinterpret_cast<char *>(h->d_ctl) + offsetof(DevCtl, err));
+    cudaError_t e = tc ? launch_hamming_tc(n, R, h->d_spins[c.t & 1], sb, dh, dh + nb, err, h->stream)
+                       : launch_hamming(n, R, h->d_spins[c.t & 1], bits, dh, dh + nb, h->stream);
     std::vector<unsigned long long> out(nb + 1);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out.data(), dh, sizeof(unsigned long long) * (nb + 1), cudaMemcpyDeviceToHost,
@@ -1391,6 +1397,8 @@ pamc_status pamc_hamming(pamc_handle h, int64_t *hist, int64_t *sum) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     dev_free_all(h, tmp);
     if (e != cudaSuccess) return cuda_fail(h, e, "Hamming distances");
+    s = pamc_sync(h);   // a bounded wait of the tensor-core kernel that gave up is reported here
+    if (s != PAMC_OK) return s;
     for (size_t k = 0; k < nb; ++k) hist[k] = (int64_t)out[k];
     *sum = (int64_t)out[nb];
     return PAMC_OK;

@@ -271,6 +271,13 @@ cudaError_t launch_gather_rows(int32_t n, const int32_t *rows, int32_t nrows, co
 // bits: scratch of R * ceil(n / 32) words.  hist and sum are zeroed first.
 cudaError_t launch_hamming(int32_t n, int32_t R, const int8_t *spins, uint32_t *bits,
                            unsigned long long *hist, unsigned long long *sum, cudaStream_t st);
+// The same on the tensor cores: the e4m3 population (scratch of
+// hamming_tc_scratch bytes) and its overlaps S S^T by tcgen05 (err: the
+// device status word, PAMC_ERR_TIMEOUT if a bounded wait gives up).
+bool hamming_tc_enabled(int32_t n, int32_t R);
+size_t hamming_tc_scratch(int32_t n, int32_t R);
+cudaError_t launch_hamming_tc(int32_t n, int32_t R, const int8_t *spins, uint8_t *Sb, unsigned long long *hist,
+                              unsigned long long *sum, int *err, cudaStream_t st);
 
 // ---- dense instances (dense.cu)
 cudaError_t launch_dense_validate(int32_t n, const int8_t *J, int *err, cudaStream_t st);

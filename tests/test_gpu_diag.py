@@ -20,8 +20,14 @@ def pg():
     return pg
 
 
-@pytest.mark.parametrize("n,R,steps", [(300, 64, 6), (31, 33, 3), (1000, 70, 4), (40, 1, 2), (97, 5, 0)])
-def test_hamming_matches_definition(pg, n, R, steps):
+@pytest.mark.parametrize("path", ["tensor", "cuda"])
+@pytest.mark.parametrize("n,R,steps", [(300, 64, 6), (31, 33, 3), (1000, 70, 4), (40, 1, 2), (97, 5, 0),
+                                       (2000, 300, 2)])
+def test_hamming_matches_definition(pg, monkeypatch, path, n, R, steps):
+    """Both paths: overlaps on the tensor cores (ragged n and R: padded K and
+    rows, several 256 x 64 blocks) and XOR-popcount on the CUDA cores."""
+    if path == "cuda":
+        monkeypatch.setenv("PAMC_HAMMING", "cuda")
     inst = W.erdos_renyi(n, min(0.5, 8.0 / n), signed=True, seed=n)
     p = dict(R=R, sweeps=2, steps=max(steps, 1), seed=3, beta0=0.2, beta1=2.0)
     ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **p)
