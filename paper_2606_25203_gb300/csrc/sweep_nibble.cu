@@ -63,11 +63,16 @@ __device__ __forceinline__ uint32_t ising_decide8(uint32_t A, int32_t c0, const 
                                                   uint32_t old, const uint64_t *tab_s, int32_t H) {
     const uint32_t uw[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
     uint32_t nw = 0;
+    // heat-bath: entry h + H = 2 nibble + c0 sits 16 * nibble bytes past
+    // tab_s + c0, and 16 * nibble is nibble q of A moved to bits 4..7
+    const char *tp = reinterpret_cast<const char *>(tab_s + c0);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int32_t idx = 2 * (int32_t)((A >> (4 * q)) & 0xFu) + c0;   // h + H
         if (RULE == 0) {
-            nw |= ((uint64_t)uw[q] < tab_s[idx] ? 1u : 0u) << (4 * q);
+            const uint32_t off = q == 0 ? (A << 4) & 0xF0u : (A >> (4 * q - 4)) & 0xF0u;
+            const uint64_t T = *reinterpret_cast<const uint64_t *>(tp + off);
+            nw |= ((uint64_t)uw[q] < T ? 1u : 0u) << (4 * q);
         } else {
             const uint32_t s = (old >> (4 * q)) & 1u;
             const int32_t ix = s ? idx : 2 * H - idx;              // s*h + H
