@@ -87,6 +87,11 @@ struct pamc_handle_s {
     pamc_params p{};
     int initialized = 0;
     int64_t host_t = 0;
+    // Algorithm 1's iteration counter z as the controller will hold it at
+    // the start of step host_t (1 after init, z + 1 each step, back to 1
+    // after the restart at z = z_rst): the host launches a restart's re-draw
+    // only in the step that restarts
+    int32_t host_z = 1;
     int64_t sched_end = 0;     // schedules exist for steps < sched_end
     SweepCfg cfg{1, 1};
     std::vector<DevBuf> bufs;  // every device allocation of the run
@@ -283,6 +288,13 @@ void release_run(pamc_handle h) {
     h->d_plocal = h->d_rows = nullptr;
     h->d_mm = nullptr;
 }
+
+// The controller restarts at the end of a step that begins with z >= z_rst;
+// advance the host's copy of z past one step.
+bool restart_due(const pamc_handle_s *h) {
+    return h->p.z_rst > 0 && h->p.restart_reinit && h->host_z >= h->p.z_rst;
+}
+void advance_z(pamc_handle_s *h) { h->host_z = (h->p.z_rst > 0 && h->host_z >= h->p.z_rst) ? 1 : h->host_z + 1; }
 
 // Words of the replica groups' spins in device memory (n_pad per group).
 size_t gsp_words(int32_t n, int32_t R) { return (size_t)((R + 3) / 4) * (size_t)((n + 3) & ~3); }
@@ -489,6 +501,7 @@ pamc_status init_dense(pamc_handle h, pamc_params p, int32_t base, int32_t own, 
     if (e != cudaSuccess) return cuda_fail(h, e, "dense init");
     h->launches += 3;
     h->host_t = 0;
+    h->host_z = 1;
     h->initialized = 1;
     return PAMC_OK;
 }
@@ -521,7 +534,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
         if (e == cudaSuccess) e = sweep_timer(h, true);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 7;
-        if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
+        if (e == cudaSuccess && restart_due(h)) {
             const int32_t tk = (int32_t)(t + 1);
             e = launch_init_spins(0, 0, n, R, p.seed, tk, 1, h->d_ctl, dst, h->stream);
             if (e == cudaSuccess)
@@ -531,6 +544,7 @@ pamc_status step_dense(pamc_handle h, int32_t nsteps) {
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "dense kernel launch");
         h->host_t = t + 1;
+        advance_z(h);
     }
     return PAMC_OK;
 }
@@ -812,6 +826,7 @@ static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, 
         return fail(h, PAMC_ERR_RANGE, "n = %d: one replica group's labels exceed shared memory", n);
     }
     h->host_t = 0;
+    h->host_z = 1;
     if (nranks > 0) {
         h->sharded = true;
         h->sh_rank = rank;
@@ -874,13 +889,14 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
         if (e == cudaSuccess) e = sweep_timer(h, true);
         if (e == cudaSuccess) e = launch_control(n, h->W, p, Ed, dst, h->d_best, h->d_ctl, h->stream);
         h->launches += 2;
-        if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
+        if (e == cudaSuccess && restart_due(h)) {
             e = launch_init(p.kind, p.K, n, h->d_rp, h->d_adj, p.R, p.seed, (int32_t)(t + 1), 1, h->d_ctl,
                             h->W, dst, Ed, h->stream);
             h->launches += 2;
         }
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
         h->host_t = t + 1;
+        advance_z(h);
     }
     return PAMC_OK;
 }
@@ -1063,7 +1079,7 @@ pamc_status pamc_shard_control(pamc_handle h, const int64_t *E_all, int64_t *E_o
     int64_t *Ed = h->d_E[(t + 1) & 1];
     cudaError_t e = launch_control(n, h->W, p, E_all, dst, h->d_best, h->d_ctl, h->stream, h->sh_base, c);
     h->launches += 1;
-    if (e == cudaSuccess && p.z_rst > 0 && p.restart_reinit) {
+    if (e == cudaSuccess && restart_due(h)) {
         if (h->dense) {
             const int32_t tk = (int32_t)(t + 1);
             e = launch_init_spins(0, 0, n, c, p.seed, tk, 1, h->d_ctl, dst, h->stream, h->sh_base);
@@ -1080,6 +1096,7 @@ pamc_status pamc_shard_control(pamc_handle h, const int64_t *E_all, int64_t *E_o
         e = cudaMemcpyAsync(E_own, Ed, sizeof(int64_t) * (size_t)c, cudaMemcpyDeviceToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "pamc_shard_control");
     h->host_t = t + 1;
+    advance_z(h);
     h->sh_phase = 0;
     return PAMC_OK;
 }
@@ -1278,6 +1295,7 @@ pamc_status pamc_load(pamc_handle h, const void *buf, size_t size) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // the host buffer may go after return
     if (e != cudaSuccess) return cuda_fail(h, e, "pamc_load upload");
     h->host_t = c.t;
+    h->host_z = c.z;
     h->sched_end = c.t;   // the next step builds the schedules from step t on
     h->launches += h->dense ? 1 : 0;
     return PAMC_OK;
