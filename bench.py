@@ -381,6 +381,16 @@ def run_ours(args):
     peaks, peak_src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sweep = [sweep_roofline(inst, args.steps, a, b, sm_max) for inst, a, b in zip(insts, sw0, sw1)]
+    # the same kernel without the other instance's launches beside it: the K
+    # steps after the window, the first instance alone on its stream
+    pg.pamc_set_sweep_timing(solvers[0].h, True)
+    torch.cuda.synchronize()
+    iso0 = pg.pamc_sweep_stats(solvers[0].h)
+    for _ in range(args.steps):
+        solvers[0].step(1)
+    solvers[0].sync()
+    iso = sweep_roofline(insts[0], args.steps, iso0, pg.pamc_sweep_stats(solvers[0].h), sm_max)
+    pg.pamc_set_sweep_timing(solvers[0].h, False)
     mode = [pg.pamc_sweep_mode(s.h) for s in solvers]
     kname = ["k_sweep_ising_nib" if m & 16 else "k_sweep_ising_push" if m == 2 else "k_sweep_ising" for m in mode]
     e2e = e2e_measure(pg, torch, insts, args, local, start)
@@ -407,7 +417,12 @@ def run_ours(args):
                        "parallelism": "replicas only" if world > 1 else "single GPU"},
             "roofline": dict(sweep[0], traffic=profiled_traffic("sweep_torus") if ONLY != "sparse" else None,
                              kernel=kname[0] + f" ({insts[0].name}, R=4096, 10 sweeps per launch)",
-                             peak_source=f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)"),
+                             peak_source=f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)",
+                             note="launches of the timed window, beside the other instance's on their own stream "
+                                  "(the SMs are shared, so each launch is stretched)",
+                             alone={k: iso[k] for k in ("achieved", "frac", "avg_launch_ms", "launches")}
+                                   | {"window": f"steps {start + args.steps}..{start + 2 * args.steps - 1}, "
+                                                f"this instance alone"}),
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "e2e": e2e,
