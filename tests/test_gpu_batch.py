@@ -22,6 +22,11 @@ def pg():
     return pg
 
 
+def _max_degree_graph(n, m, dmax, seed):
+    from test_gpu_parity import _max_degree_graph as g
+    return g(n, m, dmax, seed)
+
+
 def mix():
     """Instances of every size class (n <= 2048, <= 8192, larger), both weight
     kinds, CSR and ELL sweeps, ragged R, both update rules."""
@@ -33,6 +38,10 @@ def mix():
         (W.er_avg_degree(9000, 12, signed=True, seed=4), dict(R=36, sweeps=1, steps=18, rule=0, seed=14)),
         (W.er_avg_degree(2100, 20, signed=False, seed=5), dict(R=128, sweeps=2, steps=40, rule=1, seed=15,
                                                             z_rst=13, restart_reinit=0)),
+        # field ranges up to 7: 4-bit lanes in the batch as alone (ELL widths 4
+        # and 8, ragged groups of eight, both rules)
+        (W.torus(80, 80, signed=True, seed=8), dict(R=28, sweeps=2, steps=15, rule=1, seed=17)),
+        (_max_degree_graph(1200, 3500, 7, 9), dict(R=20, sweeps=2, steps=12, rule=0, seed=18)),
     ]
 
 
