@@ -1519,6 +1519,7 @@ struct pamc_batch_s {
     std::vector<pamc_handle> members;
     bool dirty = true;
     DevBuf sw, swi, sd, sdi, prep, tabs, ctl;
+    DevBuf ncm, ncmi, rd, rdi;   // cluster moves and restart re-draws of the members that have them
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int32_t graph_launches = 0;   // kernel launches in one replay
@@ -1602,6 +1603,11 @@ pamc_status rebuild(pamc_batch b) {
     std::vector<int2> gswi[2][2][kClasses];  // Ising, spin words in device memory
     std::vector<int2> pswi[2][kClasses];     // Potts (cascaded sampler) [ell][class]
     std::vector<int2> nswi[2][kClasses];     // Ising, 4-bit lanes (ELL rows) [rule][class]
+    std::vector<NcmDesc> ncm;
+    std::vector<int2> ncmi;
+    std::vector<RedrawDesc> rds;
+    std::vector<int2> rdsi, rdei;             // re-draw items: (member, chunk of draws), (member, replica)
+    int32_t ncm_nmax = 1;
     int32_t nmax[kClasses] = {0, 0, 0}, pnmax[kClasses] = {0, 0, 0}, gnmax[kClasses] = {0, 0, 0},
             nnmax[kClasses] = {0, 0, 0}, Rmax = 1;
     auto member_global = [&](pamc_handle h) { return h->p.kind == 0 && (h->gsp || b->global[batch_class(h->n)]); };
@@ -1646,14 +1652,32 @@ pamc_status rebuild(pamc_batch b) {
         }
         PrepDesc pd{nullptr, h->d_ctl, h->d_parent, h->d_count, h->d_ncm_idx, h->d_targets, p.R,
                     p.kind, p.resample, p.n_top, p.cooldown_tau, k0, k1, {h->d_E[0], h->d_E[1]}, t_end,
-                    h->d_fam, 0};
+                    h->d_fam, p.z_rst > 0 && p.restart_reinit ? 1 : 0};
         prep.push_back(pd);
+        if (p.stagnation && p.kind == 0) {   // the cluster moves of the member's targets
+            NcmDesc nd{h->d_rp, h->d_adj, h->d_parent, h->d_targets, h->d_ncm_buf, h->d_nkey, h->d_ctl,
+                       {h->d_spins[0], h->d_spins[1]}, {h->d_E[0], h->d_E[1]}, h->n, p.R, p.n_top,
+                       p.mis_trials, t_end, k0, k1};
+            const int nidx = (int)ncm.size();
+            ncm.push_back(nd);
+            for (int32_t q = 0; q < std::min(p.n_top, p.R); ++q) ncmi.push_back(make_int2(nidx, q));
+            ncm_nmax = std::max(ncm_nmax, h->n);
+        }
+        if (p.z_rst > 0 && p.restart_reinit) {   // a restart's re-draw
+            RedrawDesc rdd{h->d_rp, h->d_adj, h->d_ctl, {h->d_spins[0], h->d_spins[1]}, {h->d_E[0], h->d_E[1]},
+                           h->W, h->n, p.R, p.kind, p.K, k0, k1};
+            const int ridx = (int)rds.size();
+            rds.push_back(rdd);
+            const size_t total = (size_t)((p.R + 3) / 4) * h->n, chunk = (size_t)256 * kRedrawPerThread;
+            for (size_t c = 0; c * chunk < total; ++c) rdsi.push_back(make_int2(ridx, (int)c));
+            for (int32_t r = 0; r < p.R; ++r) rdei.push_back(make_int2(ridx, r));
+        }
         tabs.push_back(TabDesc{h->d_ctl, h->d_tab, p.rule, h->H, t_end, p.kind});
         SweepDesc d;
         memset(&d, 0, sizeof(d));
         d.rp = h->d_rp; d.adj = h->d_adj; d.sorder = h->d_order; d.slvl = h->d_lvl; d.snlev = h->d_nlev;
         d.sell = h->d_ell; d.spos = h->d_pos; d.tab = h->d_tab; d.parent = h->d_parent;
-        d.ncm_buf = nullptr; d.ncm_idx = h->d_ncm_idx; d.ctl = h->d_ctl;
+        d.ncm_buf = h->d_ncm_buf; d.ncm_idx = h->d_ncm_idx; d.ctl = h->d_ctl;
         d.n = h->n; d.n_pad = (h->n + 3) & ~3; d.H = h->H; d.R = p.R; d.S = p.sweeps;
         d.W = h->ell_w; d.K = make_philox_keys(p.seed);
         d.sp[0] = h->d_spins[0]; d.sp[1] = h->d_spins[1]; d.en[0] = h->d_E[0]; d.en[1] = h->d_E[1];
@@ -1692,9 +1716,12 @@ pamc_status rebuild(pamc_batch b) {
         for (auto &v : a) all_items.insert(all_items.end(), v.begin(), v.end());
     for (auto &a : nswi)
         for (auto &v : a) all_items.insert(all_items.end(), v.begin(), v.end());
+    const size_t n_rdsi = rdsi.size();
+    rdsi.insert(rdsi.end(), rdei.begin(), rdei.end());   // one upload: spin items, then energy items
     const bool ok = upload(b, b->sd, sd) && upload(b, b->sdi, sdi) && upload(b, b->prep, prep) &&
                     upload(b, b->tabs, tabs) && upload(b, b->sw, sw) && upload(b, b->ctl, ctls) &&
-                    upload(b, b->swi, all_items);
+                    upload(b, b->swi, all_items) && upload(b, b->ncm, ncm) && upload(b, b->ncmi, ncmi) &&
+                    upload(b, b->rd, rds) && upload(b, b->rdi, rdsi);
     if (!ok) return bfail(b, PAMC_ERR_CUDA, "descriptor upload failed");
     b->dirty = false;
     b->graph_launches = 0;
@@ -1706,6 +1733,11 @@ pamc_status rebuild(pamc_batch b) {
     e = launch_population_batched((const PrepDesc *)b->prep.p, (const TabDesc *)b->tabs.p, (int32_t)prep.size(),
                                   Rmax, b->stream);
     nl += 2;
+    if (e == cudaSuccess && !ncmi.empty()) {
+        e = launch_ncm_batched((const NcmDesc *)b->ncm.p, (const int2 *)b->ncmi.p, (int32_t)ncmi.size(), ncm_nmax,
+                               b->stream);
+        nl += 1;
+    }
     size_t off = 0;
     for (int el = 0; el < 2 && e == cudaSuccess; ++el)
         for (int ru = 0; ru < 2 && e == cudaSuccess; ++ru)
@@ -1747,6 +1779,11 @@ pamc_status rebuild(pamc_batch b) {
         }
     if (e == cudaSuccess) e = launch_control_batched((const CtlDesc *)b->ctl.p, (int32_t)ctls.size(), b->stream);
     nl += 1;
+    if (e == cudaSuccess && !rds.empty()) {
+        e = launch_redraw_batched((const RedrawDesc *)b->rd.p, (int32_t)rds.size(), (const int2 *)b->rdi.p,
+                                  (int32_t)n_rdsi, (const int2 *)b->rdi.p + n_rdsi, (int32_t)rdei.size(), b->stream);
+        nl += 3;
+    }
     if (e == cudaSuccess && !sdi.empty()) {
         int32_t sched_nmax = 1;
         for (const SchedDesc &d : sd) sched_nmax = std::max(sched_nmax, d.n);
@@ -1824,8 +1861,6 @@ pamc_status pamc_batch_add(pamc_batch b, pamc_handle h) {
         return bfail(b, PAMC_ERR_ARG, "batched members need sum_j |w_ij| <= %d", kByteLaneMaxH);
     if (h->p.kind == 1 && h->p.rule != 0)
         return bfail(b, PAMC_ERR_ARG, "batched Max-3-Cut members use the cascaded sampler (rule 0)");
-    if (h->p.stagnation || (h->p.z_rst > 0 && h->p.restart_reinit))
-        return bfail(b, PAMC_ERR_ARG, "batched members run without NCM and without restart re-initialisation");
     if (h->device != b->device) return bfail(b, PAMC_ERR_ARG, "handle on another device");
     for (pamc_handle m : b->members)
         if (m == h) return bfail(b, PAMC_ERR_ARG, "handle already in the batch");
@@ -1842,7 +1877,11 @@ pamc_status pamc_batch_add(pamc_batch b, pamc_handle h) {
         h->launches += 1;
         h->sched_end = want;
     }
-    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    // no re-draw is pending when the member joins (a single run re-draws by
+    // step index and leaves the batch's flag as its last restart set it)
+    cudaError_t e = cudaMemsetAsync(reinterpret_cast<char *>(h->d_ctl) + offsetof(DevCtl, redraw), 0, sizeof(int32_t),
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return bfail(b, PAMC_ERR_CUDA, "member sync: %s", cudaGetErrorString(e));
     b->members.push_back(h);
     b->dirty = true;
@@ -1979,7 +2018,8 @@ void pamc_batch_destroy(pamc_batch b) {
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     drop_graph(b);
-    for (DevBuf *d : {&b->sw, &b->swi, &b->sd, &b->sdi, &b->prep, &b->tabs, &b->ctl})
+    for (DevBuf *d : {&b->sw, &b->swi, &b->sd, &b->sdi, &b->prep, &b->tabs, &b->ctl, &b->ncm, &b->ncmi, &b->rd,
+                      &b->rdi})
         if (d->p) cudaFree(d->p);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;

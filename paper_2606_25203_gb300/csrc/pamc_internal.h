@@ -32,6 +32,8 @@ struct DevCtl {
     int32_t best_replica; // replica holding M* when it was last improved
     int32_t best_owned;   // the replica holding M* is one of this handle's own (always, unless the
                           // population is split over processes)
+    int32_t redraw;       // a restart re-draw pending for a batch member (raised by the controller)
+    int32_t pad_;
     double beta, delta, dbeta;
     int64_t mstar;        // best cut so far (INT64_MIN = none yet)
     int64_t ncm_flipped, ncm_dE_max;
@@ -129,6 +131,38 @@ struct CtlDesc {
     const int8_t *sp[2];
     int32_t t_end;
 };
+
+// Batched cluster moves (members with stagnation control, Max-Cut): items
+// (member, target q).
+struct NcmDesc {
+    const int32_t *rp;
+    const uint32_t *adj;
+    const int32_t *parent, *targets;
+    int8_t *ncm_buf;
+    uint32_t *nkey;
+    DevCtl *ctl;
+    const int8_t *sp[2];
+    const int64_t *en[2];
+    int32_t n, R, n_top, trials, t_end;
+    uint32_t key0, key1;
+};
+
+// Batched restart re-draws (members with restart_reinit).
+constexpr int kRedrawPerThread = 16;   // spin-draw elements (group, vertex) per thread of a re-draw item
+struct RedrawDesc {
+    const int32_t *rp;
+    const uint32_t *adj;
+    DevCtl *ctl;
+    int8_t *sp[2];
+    int64_t *en[2];
+    int64_t Wsum;
+    int32_t n, R, kind, K;
+    uint32_t key0, key1;
+};
+cudaError_t launch_ncm_batched(const NcmDesc *descs, const int2 *items, int32_t nitems, int32_t n_max,
+                               cudaStream_t st);
+cudaError_t launch_redraw_batched(const RedrawDesc *descs, int32_t nmem, const int2 *spin_items, int32_t nspin,
+                                  const int2 *energy_items, int32_t nenergy, cudaStream_t st);
 
 // Allows every launch of `func` with up to `bytes` of dynamic shared memory
 // by raising the kernel's limit to the device's opt-in maximum (minus its

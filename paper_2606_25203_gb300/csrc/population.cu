@@ -623,13 +623,15 @@ __device__ int32_t mis_trial(int32_t n, const int32_t *rp, const uint32_t *adj, 
 __host__ __device__ constexpr size_t ncm_stat_bytes(int32_t n) { return ((size_t)n + 15) & ~(size_t)15; }
 constexpr size_t kNcmKeySmemMax = 160 * 1024;   // keys join the states in shared memory up to this total
 
-__global__ void __launch_bounds__(kNcmThreads)
-k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj, int32_t R,
-      int32_t kind, int32_t n_top, int32_t trials, uint32_t key0, uint32_t key1,
-      const int8_t *__restrict__ src, const int64_t *__restrict__ E_src,
-      const int32_t *__restrict__ parent, const int32_t *__restrict__ targets,
-      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, int32_t key_smem, int32_t max_rounds,
-      DevCtl *__restrict__ ctl, int32_t base, int32_t count, const int32_t *__restrict__ prow) {
+// The cluster move of target q (one CTA), shared by the single-instance and
+// the batched kernels.
+__device__ __forceinline__ void
+ncm_body(int32_t q, int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj, int32_t R,
+         int32_t kind, int32_t n_top, int32_t trials, uint32_t key0, uint32_t key1,
+         const int8_t *__restrict__ src, const int64_t *__restrict__ E_src,
+         const int32_t *__restrict__ parent, const int32_t *__restrict__ targets,
+         int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, int32_t key_smem, int32_t max_rounds,
+         DevCtl *__restrict__ ctl, int32_t base, int32_t count, const int32_t *__restrict__ prow) {
     // the per-site decision state of the MIS rounds lives in shared memory
     // (n bytes), and the trial's order keys too (4n bytes) when key_smem:
     // every round reads the state and key of every neighbour
@@ -637,7 +639,6 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
     __shared__ int s_flag, s_red;
     __shared__ long long s_e[32];
     if (ctl->done || !ctl->ncm_active || kind != 0) return;
-    const int32_t q = blockIdx.x;
     if (q >= min(n_top, R)) return;
     const int32_t t = ctl->t;
     const int32_t m = targets[q];
@@ -691,6 +692,93 @@ k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ ad
         atomicMax((unsigned long long *)&ctl->ncm_dE_max, (unsigned long long)d);
         atomicAdd((unsigned long long *)&ctl->ncm_flipped, (unsigned long long)(best > 0 ? best : 0));
     }
+}
+
+__global__ void __launch_bounds__(kNcmThreads)
+k_ncm(int32_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj, int32_t R,
+      int32_t kind, int32_t n_top, int32_t trials, uint32_t key0, uint32_t key1,
+      const int8_t *__restrict__ src, const int64_t *__restrict__ E_src,
+      const int32_t *__restrict__ parent, const int32_t *__restrict__ targets,
+      int8_t *__restrict__ ncm_buf, uint32_t *__restrict__ nkey, int32_t key_smem, int32_t max_rounds,
+      DevCtl *__restrict__ ctl, int32_t base, int32_t count, const int32_t *__restrict__ prow) {
+    ncm_body(blockIdx.x, n, rp, adj, R, kind, n_top, trials, key0, key1, src, E_src, parent, targets, ncm_buf, nkey,
+             key_smem, max_rounds, ctl, base, count, prow);
+}
+
+// Cluster moves of many instances in one launch: CTA b moves target
+// items[b].y of member items[b].x, reading the member's step from its
+// controller (the population of step t is sp[t & 1]).
+__global__ void __launch_bounds__(kNcmThreads)
+k_ncm_batched(const NcmDesc *__restrict__ descs, const int2 *__restrict__ items, int32_t key_smem,
+              int32_t max_rounds) {
+    const int2 it = items[blockIdx.x];
+    const NcmDesc &d = descs[it.x];
+    const int32_t t = d.ctl->t;
+    if (t >= d.t_end) return;
+    ncm_body(it.y, d.n, d.rp, d.adj, d.R, 0, d.n_top, d.trials, d.key0, d.key1, d.sp[t & 1], d.en[t & 1], d.parent,
+             d.targets, d.ncm_buf, d.nkey, key_smem, max_rounds, d.ctl, 0, d.R, nullptr);
+}
+
+// A restart's re-draw in a batch (after the controller, which advanced t and
+// raised redraw): the initial-population draw of step ctl->t for every group
+// of four replicas (items (member, chunk of groups)), the energies from the
+// definition (items (member, replica)), then the flag is lowered.
+__global__ void __launch_bounds__(256)
+k_redraw_spins_batched(const RedrawDesc *__restrict__ descs, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.x];
+    const RedrawDesc &d = descs[it.x];
+    const DevCtl *ctl = d.ctl;
+    if (!ctl->redraw) return;
+    const int32_t t = ctl->t, n = d.n, R = d.R;
+    int8_t *spins = d.sp[t & 1];
+    const int32_t groups = (R + 3) / 4;
+    const size_t total = (size_t)groups * n;
+    const size_t chunk = (size_t)256 * kRedrawPerThread;
+    const size_t lo = (size_t)it.y * chunk, hi = lo + chunk < total ? lo + chunk : total;
+    for (size_t x = lo + threadIdx.x; x < hi; x += blockDim.x) {
+        const int32_t g = (int32_t)(x / n), i = (int32_t)(x % n);
+        const u32x4 u = philox((uint32_t)i, 0u, (uint32_t)t, (kTagInit << 24) | (uint32_t)g, d.key0, d.key1);
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int32_t r = 4 * g + q;
+            if (r >= R) break;
+            int8_t v;
+            if (d.kind == 0) v = (w[q] >> 31) ? 1 : -1;
+            else v = (int8_t)(((uint64_t)w[q] * (uint64_t)d.K) >> 32);
+            spins[(size_t)r * n + i] = v;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_redraw_energy_batched(const RedrawDesc *__restrict__ descs, const int2 *__restrict__ items) {
+    __shared__ long long red[32];
+    const int2 it = items[blockIdx.x];
+    const RedrawDesc &d = descs[it.x];
+    const DevCtl *ctl = d.ctl;
+    if (!ctl->redraw) return;
+    const int32_t t = ctl->t, n = d.n, r = it.y;
+    const int8_t *s = d.sp[t & 1] + (size_t)r * n;
+    long long acc = 0;
+    for (int32_t k = threadIdx.x; k < n; k += blockDim.x) {
+        long long h = 0;
+        const int8_t sk = s[k];
+        for (int32_t e = d.rp[k]; e < d.rp[k + 1]; ++e) {
+            const uint32_t a = d.adj[e];
+            const int32_t J = (int32_t)a >> 24;
+            if (d.kind == 0) h += (long long)J * s[a & 0xFFFFFFu];
+            else h += (s[a & 0xFFFFFFu] == sk) ? J : 0;
+        }
+        acc += d.kind == 0 ? (long long)sk * h : h;
+    }
+    const long long tot = block_reduce(acc, [](long long x, long long y) { return x + y; }, red);
+    if (threadIdx.x == 0) d.en[t & 1][r] = d.kind == 0 ? -(tot / 2) : (-tot - d.Wsum);
+}
+
+__global__ void k_redraw_done_batched(const RedrawDesc *__restrict__ descs, int32_t nmem) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nmem) descs[i].ctl->redraw = 0;
 }
 
 // ---------------------------------------------------------------- controller
@@ -801,6 +889,7 @@ control_body(int32_t n, int64_t W, int32_t R, int32_t stagnation, int32_t z_rst,
         c.cooldown = 0;
         c.hist_len = 0;
         c.restart = 1;
+        c.redraw = 1;   // consumed by a batch's re-draw (a single run re-draws by step index)
     } else {
         c.z += 1;
         c.beta = __dadd_rn(c.beta, c.delta);
@@ -936,6 +1025,29 @@ cudaError_t launch_population_batched(const PrepDesc *prep, const TabDesc *tabs,
     if (err != cudaSuccess) return err;
     k_prep_batched<<<ninst, kPrepThreads, smem, st>>>(prep);
     k_tables_batched<<<ninst * kTabBlocks, 256, 0, st>>>(tabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ncm_batched(const NcmDesc *descs, const int2 *items, int32_t nitems, int32_t n_max,
+                               cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const size_t with_keys = ncm_stat_bytes(n_max) + (size_t)n_max * 4;
+    const int key_smem = with_keys <= kNcmKeySmemMax ? 1 : 0;
+    const size_t smem = key_smem ? with_keys : ncm_stat_bytes(n_max);
+    cudaError_t err = allow_dynamic_smem(k_ncm_batched, smem);
+    if (err != cudaSuccess) return err;
+    int32_t max_rounds = -1;
+    if (const char *env = getenv("PAMC_NCM_MAX_ROUNDS")) max_rounds = atoi(env);
+    k_ncm_batched<<<nitems, kNcmThreads, smem, st>>>(descs, items, key_smem, max_rounds);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_redraw_batched(const RedrawDesc *descs, int32_t nmem, const int2 *spin_items, int32_t nspin,
+                                  const int2 *energy_items, int32_t nenergy, cudaStream_t st) {
+    if (nmem <= 0) return cudaSuccess;
+    if (nspin > 0) k_redraw_spins_batched<<<nspin, 256, 0, st>>>(descs, spin_items);
+    if (nenergy > 0) k_redraw_energy_batched<<<nenergy, 256, 0, st>>>(descs, energy_items);
+    k_redraw_done_batched<<<(nmem + 127) / 128, 128, 0, st>>>(descs, nmem);
     return cudaGetLastError();
 }
 

@@ -267,6 +267,55 @@ def test_batch_max_cut_and_max3cut_members(pg):
             pg.pamc_destroy(h)
 
 
+def test_batch_augmented_members_equal_alone(pg):
+    """Members with the stagnation controller (reheats and cluster moves,
+    run per member in the batch) and with restarts that re-draw the
+    population (in the batch, after the controller) end exactly as they do
+    alone -- Max-Cut on byte and 4-bit lanes, both rules, and Max-3-Cut --
+    joining at different steps, beside plain members."""
+    aug = dict(stagnation=1, win_short=2, win_long=3, cooldown_tau=1)
+    cases = [
+        (W.torus(40, 40, signed=True, seed=31), dict(R=64, sweeps=2, steps=40, rule=0, z_rst=17, seed=41, **aug)),
+        (W.gnm(1500, 4300, signed=True, seed=32), dict(R=44, sweeps=2, steps=36, rule=1, z_rst=13, seed=42, **aug)),
+        (W.gnm(900, 3600, signed=False, seed=33), dict(kind=1, R=24, sweeps=2, steps=30, z_rst=11, seed=43)),
+        (W.er_avg_degree(9000, 12, signed=True, seed=34), dict(R=20, sweeps=1, steps=25, z_rst=8, seed=44, **aug)),
+        (W.erdos_renyi(300, 0.05, signed=False, seed=35), dict(R=32, sweeps=2, steps=20, seed=45)),
+    ]
+    ref = [alone(pg, inst, p) for inst, p in cases]
+    b = pg.pamc_batch_create(0)
+    hs = []
+    try:
+        for inst, p in cases:
+            h = pg.pamc_create_csr(inst.n, inst.row_ptr, inst.col, inst.w)
+            pg.pamc_init(h, **p)
+            hs.append(h)
+        pg.pamc_step(hs[1], 14)      # steps alone past its first restart, then joins
+        pg.pamc_batch_add(b, hs[0])
+        pg.pamc_batch_add(b, hs[1])
+        pg.pamc_batch_add(b, hs[2])
+        pg.pamc_batch_step(b, 6)
+        for h in hs[3:]:
+            pg.pamc_batch_add(b, h)
+        got = {}
+        while pg.pamc_batch_size(b) > 0:
+            pg.pamc_batch_step(b, 4)
+            for h in pg.pamc_batch_retire(b):
+                i = [x.value for x in hs].index(h.value)
+                inst, p = cases[i]
+                got[i] = snapshot(pg, h, inst.n, p["R"])
+        assert sorted(got) == list(range(len(cases)))
+        for i in range(len(cases)):
+            assert_same(got[i], ref[i], f"member {i} ({cases[i][0].name})")
+            if cases[i][1].get("stagnation"):
+                assert got[i]["ctl"]["ncm_flipped"] > 0, i
+            if cases[i][1].get("z_rst"):
+                assert got[i]["ctl"]["cycle"] >= 1, i
+    finally:
+        for h in hs:
+            pg.pamc_destroy(h)
+        pg.pamc_batch_destroy(b)
+
+
 def test_batch_refusals(pg):
     inst = W.torus(8, 8, signed=True, seed=1)
     b = pg.pamc_batch_create(0)
@@ -274,12 +323,6 @@ def test_batch_refusals(pg):
     try:
         with pytest.raises(pg.PamcError):
             pg.pamc_batch_add(b, h)                       # not initialised
-        pg.pamc_init(h, R=16, steps=5, stagnation=1)
-        with pytest.raises(pg.PamcError):
-            pg.pamc_batch_add(b, h)                       # NCM members are refused
-        pg.pamc_init(h, R=16, steps=5, z_rst=3, restart_reinit=1)
-        with pytest.raises(pg.PamcError):
-            pg.pamc_batch_add(b, h)                       # restart re-initialisation refused
         pg.pamc_init(h, R=16, steps=5, kind=1, rule=2, K=4)
         with pytest.raises(pg.PamcError):
             pg.pamc_batch_add(b, h)                       # softmax Potts members are refused
