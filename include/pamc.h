@@ -233,8 +233,9 @@ void pamc_destroy(pamc_handle h);
 
 /* ---- Batches: many independent instances advanced together ----
  * Not in the paper: a serving extension.  A batch advances every member by
- * one iteration of Algorithm 1 per step (resampling, tables, sweeps,
- * controller) with one launch per kernel type, the sweep launched once per
+ * one iteration of Algorithm 1 per step (resampling, tables, cluster
+ * moves, sweeps, controller, a restart's re-draw) with one launch per kernel
+ * type, the sweep launched once per
  * size class of n with its own shape, so uneven instances share the GPU.
  * Each launch reads the member's step index from the member's device-side
  * controller, so one step's launches are captured into a CUDA graph once per
@@ -242,9 +243,10 @@ void pamc_destroy(pamc_handle h);
  * pamc_step computes for it alone (same random streams, orders, tables and
  * controller): its spins, energies, parents, counts and best cut are
  * identical in and out of the batch.
- * Members: initialised sparse handles of Max-Cut (kind 0, either rule) or
- * Max-3-Cut with the cascaded sampler (kind 1, rule 0), with stagnation = 0
- * and no restart re-initialisation (z_rst = 0 or restart_reinit = 0);
+ * Members: initialised sparse handles of Max-Cut (kind 0, either rule,
+ * with or without the stagnation controller and its cluster moves) or
+ * Max-3-Cut with the cascaded sampler (kind 1, rule 0), restarts with or
+ * without re-draws, field ranges up to 127 and populations up to 16,384;
  * others are refused with PAMC_ERR_ARG.  A member must stay alive and must
  * not be stepped or re-initialised on its own while it is in the batch.  The batch runs on its
  * own stream (the one given, or one it creates when stream is NULL); read a
