@@ -173,9 +173,14 @@ pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_
  * (groups too large for shared memory, or PAMC_SWEEP_GLOBAL=1), 2 kept in
  * shared memory and updated on every flip (push; chosen by the environment
  * variable PAMC_SWEEP_PUSH=1 for instances with max_i sum_j |w_ij| <= 63,
- * ELL rows, one lane per vertex, at least one sweep).  Speed only, never
- * results.  PAMC_ERR_STATE before pamc_init or
- * for dense or Potts runs. */
+ * ELL rows, one lane per vertex, at least one sweep).  Plus 8 when the
+ * fields take 16-bit lanes (max_i sum_j |w_ij| > 127), plus 16 when a word
+ * holds eight replicas on 4-bit lanes (ELL rows, one lane per vertex, spin
+ * words in shared memory, at least one sweep, and either sum_j |w_ij| <= 7
+ * per vertex on rows of width 4 or 8, or at most 15 over each vertex's first
+ * eight nonzero couplings in CSR order and over the rest, on rows up to 16
+ * wide; off with PAMC_SWEEP_NIBBLE=0).  Speed only, never results.
+ * PAMC_ERR_STATE before pamc_init or for dense or Potts runs. */
 pamc_status pamc_sweep_mode(pamc_handle h, int *mode);
 
 /* Sweep statistics.  pamc_set_sweep_timing(h, 1) makes every following

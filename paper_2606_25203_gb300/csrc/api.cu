@@ -83,6 +83,7 @@ struct pamc_handle_s {
     // instance
     int32_t *d_rp = nullptr;
     uint32_t *d_adj = nullptr;
+    int4 *d_nibc = nullptr;      // per-vertex constants of the biased 4-bit lanes, or nullptr
     // run
     pamc_params p{};
     int initialized = 0;
@@ -595,8 +596,14 @@ pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *co
     // (the schedule's position record holds the degree in 8 bits)
     const int64_t ell_entries = (int64_t)((n + 31) / 32) * 32 * ((maxdeg + 3) & ~3);
     h->ell_w = (maxdeg > 0 && maxdeg < 256 && ell_entries <= 4 * (int64_t)h->nnz + 4096) ? ((maxdeg + 3) & ~3) : 0;
+    // field ranges beyond the fixed 4-bit bias (7) but within 15 a half-row:
+    // the biased 4-bit lanes' per-vertex constants
+    std::vector<int4> nibc;
+    const bool biased = h->ell_w > 0 && !(H <= kNibbleMaxH && (h->ell_w == 4 || h->ell_w == 8)) &&
+                        nibble_biased_constants(n, row_ptr, adj.data(), H, h->ell_w, nibc);
     if (!alloc_n(h, h->d_rp, (size_t)n + 1, h->inst_bufs) ||
-        !alloc_n(h, h->d_adj, (size_t)std::max(h->nnz, 1), h->inst_bufs)) {
+        !alloc_n(h, h->d_adj, (size_t)std::max(h->nnz, 1), h->inst_bufs) ||
+        (biased && !alloc_n(h, h->d_nibc, (size_t)n, h->inst_bufs))) {
         dev_free_all(h, h->inst_bufs);
         delete h;
         return fail(nullptr, PAMC_ERR_OOM, "device allocation of the instance failed");
@@ -605,6 +612,8 @@ pamc_status pamc_create_csr(int32_t n, const int32_t *row_ptr, const int32_t *co
     if (e == cudaSuccess && h->nnz > 0)
         e = cudaMemcpyAsync(h->d_adj, adj.data(), sizeof(uint32_t) * h->nnz, cudaMemcpyHostToDevice,
                             h->stream);
+    if (e == cudaSuccess && biased)
+        e = cudaMemcpyAsync(h->d_nibc, nibc.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         dev_free_all(h, h->inst_bufs);
@@ -810,12 +819,20 @@ static pamc_status init_run(pamc_handle h, const pamc_params *pp, int32_t rank, 
         }
         h->gsp = true;
     }
-    // field ranges of at most 7 on ELL schedules: eight replicas a word
-    // (groups of eight, shaped like a population of half the size)
-    if (p.kind == 0 && !h->gsp && sweep_nibble_ok(h->H, p.sweeps, h->ell_w, 1, false) && !sweep_push_enabled()) {
+    // field ranges of at most 7 on ELL rows of width 4 or 8, or of 15 a
+    // half-row on rows up to 16 wide: eight replicas a word (groups of eight,
+    // shaped like a population of half the size)
+    if (p.kind == 0 && !h->gsp && sweep_nibble_ok(h->H, p.sweeps, h->ell_w, 1, false, h->d_nibc != nullptr) &&
+        !sweep_push_enabled()) {
         SweepCfg c = choose_cfg(0, n, 4 * ((own + 7) / 8), h->H, avg_level, (double)h->nnz / std::max(n, 1), sms,
                                 h->ell_w);
         c.lanes_per_vertex = 1;
+        // a one-group CTA keeps at least one pass of its warps busy per
+        // average level (down to 8 warps): with less, a lane has no next
+        // position whose loads could overlap the current one
+        if (!getenv("PAMC_SWEEP_CFG"))
+            while (c.groups_per_cta == 1 && c.warps_per_group > 8 && avg_level < 32.0 * c.warps_per_group)
+                c.warps_per_group >>= 1;
         if (sweep_nibble_smem_bytes(n, h->H, c) <= kSmemMax) {
             h->cfg = c;
             h->nib = true;
@@ -879,7 +896,7 @@ pamc_status pamc_step(pamc_handle h, int32_t nsteps) {
                            h->d_nkey, h->d_ctl, h->stream);
             h->launches += 1;
         }
-        SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w};
+        SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w, h->d_nibc};
         if (e == cudaSuccess) e = sweep_timer(h, false);
         if (e == cudaSuccess)
             e = launch_sweep(sweep_kind(p), p.rule, n, h->d_rp, h->d_adj, h->H, p, (int32_t)t,
@@ -1051,7 +1068,7 @@ pamc_status pamc_shard_sweep(pamc_handle h, const int64_t *E_all, const int32_t 
     }
     pamc_params pl = p;   // the sweep sees the own slots only
     pl.R = c;
-    SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w};
+    SchedView sv{h->d_order, h->d_lvl, h->d_nlev, h->d_ell, h->d_pos, h->ell_w, h->d_nibc};
     if (e == cudaSuccess) e = sweep_timer(h, false);
     if (e == cudaSuccess)
         e = launch_sweep(sweep_kind(p), p.rule, n, h->d_rp, h->d_adj, h->H, pl, (int32_t)t,
@@ -1602,7 +1619,7 @@ pamc_status rebuild(pamc_batch b) {
     std::vector<int2> swi[2][2][kClasses];   // Ising, spin words on chip [ell][rule][class]
     std::vector<int2> gswi[2][2][kClasses];  // Ising, spin words in device memory
     std::vector<int2> pswi[2][kClasses];     // Potts (cascaded sampler) [ell][class]
-    std::vector<int2> nswi[2][kClasses];     // Ising, 4-bit lanes (ELL rows) [rule][class]
+    std::vector<int2> nswi[2][2][kClasses];  // Ising, 4-bit lanes (ELL rows) [biased][rule][class]
     std::vector<NcmDesc> ncm;
     std::vector<int2> ncmi;
     std::vector<RedrawDesc> rds;
@@ -1611,10 +1628,10 @@ pamc_status rebuild(pamc_batch b) {
     int32_t nmax[kClasses] = {0, 0, 0}, pnmax[kClasses] = {0, 0, 0}, gnmax[kClasses] = {0, 0, 0},
             nnmax[kClasses] = {0, 0, 0}, Rmax = 1;
     auto member_global = [&](pamc_handle h) { return h->p.kind == 0 && (h->gsp || b->global[batch_class(h->n)]); };
-    // field ranges up to 7 on ELL rows take eight replicas a word, as alone
+    // members whose field ranges fit 4-bit lanes take eight replicas a word, as alone
     auto member_nib = [&](pamc_handle h) {
-        return h->p.kind == 0 && !member_global(h) && sweep_nibble_ok(h->H, h->p.sweeps, h->ell_w, 1, false) &&
-               !sweep_push_enabled();
+        return h->p.kind == 0 && !member_global(h) &&
+               sweep_nibble_ok(h->H, h->p.sweeps, h->ell_w, 1, false, h->d_nibc != nullptr) && !sweep_push_enabled();
     };
     for (pamc_handle h : b->members)
         if (h->host_t < h->p.steps) {
@@ -1627,7 +1644,7 @@ pamc_status rebuild(pamc_batch b) {
     SweepCfg eff[kClasses], peff[kClasses], geff[kClasses], neff[kClasses];
     for (int c = 0; c < kClasses; ++c) {
         neff[c] = SweepCfg{b->shape[c].groups_per_cta, b->shape[c].warps_per_group, 1};
-        while (neff[c].groups_per_cta > 1 && sweep_nibble_smem_bytes(nnmax[c], kNibbleMaxH, neff[c]) > kSmemMax)
+        while (neff[c].groups_per_cta > 1 && sweep_nibble_smem_bytes(nnmax[c], kNibbleBiasedMaxH, neff[c]) > kSmemMax)
             neff[c].groups_per_cta -= 1;
         geff[c] = SweepCfg{b->shape[c].groups_per_cta, b->shape[c].warps_per_group, 1};
         eff[c] = b->shape[c];
@@ -1688,6 +1705,7 @@ pamc_status rebuild(pamc_batch b) {
             return bfail(b, PAMC_ERR_OOM, "device allocation of a member's group spin words failed");
         d.gsp = gl ? h->d_gsp : nullptr;
         const bool nb = member_nib(h);
+        d.nibc = nb ? h->d_nibc : nullptr;
         const SweepCfg cfg = p.kind != 0 ? peff[cls] : gl ? geff[cls] : nb ? neff[cls] : eff[cls];
         d.push = p.kind == 0 && !gl && !nb && sweep_push_ok(h->H, p.sweeps, h->d_ell != nullptr, cfg.lanes_per_vertex)
                      ? 1 : 0;
@@ -1697,7 +1715,8 @@ pamc_status rebuild(pamc_batch b) {
         const int32_t ctas = (groups + cfg.groups_per_cta - 1) / cfg.groups_per_cta;
         // with sweeps = 0 the launch still copies the resampled population and its energies
         auto &items = p.kind != 0 ? pswi[h->d_ell != nullptr][cls]
-                                  : nb ? nswi[p.rule][cls] : (gl ? gswi : swi)[h->d_ell != nullptr][p.rule][cls];
+                                  : nb ? nswi[h->d_nibc != nullptr][p.rule][cls]
+                                       : (gl ? gswi : swi)[h->d_ell != nullptr][p.rule][cls];
         for (int32_t x = 0; x < ctas; ++x) items.push_back(make_int2(idx, x));
         Rmax = std::max(Rmax, p.R);
         CtlDesc c{nullptr, nullptr, h->d_best, h->d_ctl, h->W, p.target_cut, p.reheat_factor, p.beta0,
@@ -1715,7 +1734,8 @@ pamc_status rebuild(pamc_batch b) {
     for (auto &a : pswi)
         for (auto &v : a) all_items.insert(all_items.end(), v.begin(), v.end());
     for (auto &a : nswi)
-        for (auto &v : a) all_items.insert(all_items.end(), v.begin(), v.end());
+        for (auto &c : a)
+            for (auto &v : c) all_items.insert(all_items.end(), v.begin(), v.end());
     const size_t n_rdsi = rdsi.size();
     rdsi.insert(rdsi.end(), rdei.begin(), rdei.end());   // one upload: spin items, then energy items
     const bool ok = upload(b, b->sd, sd) && upload(b, b->sdi, sdi) && upload(b, b->prep, prep) &&
@@ -1768,15 +1788,17 @@ pamc_status rebuild(pamc_batch b) {
             off += items.size();
             nl += 1;
         }
-    for (int ru = 0; ru < 2 && e == cudaSuccess; ++ru)
-        for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
-            const auto &items = nswi[ru][c];
-            if (items.empty()) continue;
-            e = launch_sweep_ising_nib_batched(ru, (const SweepDesc *)b->sw.p, (const int2 *)b->swi.p + off,
-                                               (int32_t)items.size(), nnmax[c], neff[c], b->stream);
-            off += items.size();
-            nl += 1;
-        }
+    for (int bi = 0; bi < 2 && e == cudaSuccess; ++bi)
+        for (int ru = 0; ru < 2 && e == cudaSuccess; ++ru)
+            for (int c = 0; c < kClasses && e == cudaSuccess; ++c) {
+                const auto &items = nswi[bi][ru][c];
+                if (items.empty()) continue;
+                e = launch_sweep_ising_nib_batched(ru, bi != 0, (const SweepDesc *)b->sw.p,
+                                                   (const int2 *)b->swi.p + off, (int32_t)items.size(), nnmax[c],
+                                                   neff[c], b->stream);
+                off += items.size();
+                nl += 1;
+            }
     if (e == cudaSuccess) e = launch_control_batched((const CtlDesc *)b->ctl.p, (int32_t)ctls.size(), b->stream);
     nl += 1;
     if (e == cudaSuccess && !rds.empty()) {

@@ -4,6 +4,7 @@
 
 #include <climits>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/pamc.h"
 #include "pamc_device.cuh"
@@ -56,6 +57,10 @@ struct SchedView {
     const uint32_t *ell;     // [slots][S][ceil(n/32)*32*W] or nullptr (CSR reads)
     const int2 *pos;         // [slots][S][n]: {k | deg << 24, sum_j J_kj} (with ell)
     int32_t W;               // ELL width (a multiple of 4, zero-padded)
+    // per vertex {M1 * 0x11111111, M2 * 0x11111111, H - sum_j |J_kj|, 0}
+    // (M1, M2: the weight of the negative couplings in ELL slots 0..7 and
+    // 8..15): the biased 4-bit lanes of sweep_nibble.cu, or nullptr
+    const int4 *nibc = nullptr;
 };
 
 // Everything the Ising sweep of one instance needs (single or batched launch).
@@ -84,6 +89,7 @@ struct SweepDesc {
     int64_t Wsum;   // Potts: sum_{i<j} w_ij (E = -sum_k syn_sigma_k(k) - W)
     uint32_t *gsp;  // Ising: the groups' spin words in device memory (n_pad words a group), or nullptr
     int32_t gbase;  // group index of the first local group in the whole population (keys the draws)
+    const int4 *nibc;   // biased 4-bit lanes: the per-vertex constants (SchedView::nibc), or nullptr
 };
 
 struct SchedDesc {
@@ -243,21 +249,32 @@ cudaError_t launch_sweep_ising_wide(int rule, int32_t n, const int32_t *rp, cons
                                     int32_t rbase = 0);
 
 // Ising sweeps with 4-bit field lanes, eight replicas per word
-// (sweep_nibble.cu): instances with H <= 7 on ELL schedules of width 4 or 8,
-// S >= 1, one lane per vertex, words in shared memory; off with
-// PAMC_SWEEP_NIBBLE=0.  Groups of eight replicas (ceil(R / 8) of them).
+// (sweep_nibble.cu), S >= 1, one lane per vertex, words in shared memory; off
+// with PAMC_SWEEP_NIBBLE=0.  Groups of eight replicas (ceil(R / 8) of them).
+// Fixed bias: H <= 7 on ELL rows of width 4 or 8.  Biased lanes (per-vertex
+// constants, two accumulators): ELL width 4 to 16 with sum |J| <= 15 over
+// the slots 0..7 and over the slots 8..15 of every vertex.
 constexpr int32_t kNibbleMaxH = 7;
+constexpr int32_t kNibbleHalfMaxH = 15;
+constexpr int32_t kNibbleBiasedMaxH = 2 * kNibbleHalfMaxH;
 bool sweep_nibble_enabled();
-bool sweep_nibble_ok(int32_t H, int32_t S, int32_t ell_w, int lanes_per_vertex, bool global_spins);
+bool sweep_nibble_ok(int32_t H, int32_t S, int32_t ell_w, int lanes_per_vertex, bool global_spins,
+                     bool biased_ok);
+// The biased lanes' per-vertex constants from the packed CSR (J in the top
+// byte, the ELL slot order: the nonzero couplings in CSR order); false when
+// some vertex exceeds kNibbleHalfMaxH in a half or the width exceeds 16.
+bool nibble_biased_constants(int32_t n, const int32_t *rp, const uint32_t *adj, int32_t H, int32_t ell_w,
+                             std::vector<int4> &out);
 size_t sweep_nibble_smem_bytes(int32_t n, int32_t H, SweepCfg cfg);
 cudaError_t launch_sweep_ising_nib(int rule, int32_t n, int32_t H, const pamc_params &p, int32_t t, int32_t slot,
                                    SchedView sv, const uint64_t *tab, const int8_t *src, const int32_t *parent,
                                    const int8_t *ncm_buf, const int32_t *ncm_idx, int8_t *dst, int64_t *E_dst,
                                    const DevCtl *ctl, SweepCfg cfg, cudaStream_t st, int32_t rbase);
-// Batched 4-bit-lane sweeps (members with H <= 7, ELL width 4 or 8, S >= 1,
-// words on chip); items (member, block of groups of eight).
-cudaError_t launch_sweep_ising_nib_batched(int rule, const SweepDesc *descs, const int2 *items, int32_t nitems,
-                                           int32_t n_max, SweepCfg cfg, cudaStream_t st);
+// Batched 4-bit-lane sweeps (members as for the single launch, fixed or
+// biased lanes per member, words on chip); items (member, block of groups of
+// eight).
+cudaError_t launch_sweep_ising_nib_batched(int rule, bool biased, const SweepDesc *descs, const int2 *items,
+                                           int32_t nitems, int32_t n_max, SweepCfg cfg, cudaStream_t st);
 
 // Sweep kinds: 0 Ising, 1 Potts K=3 cascaded sampler, 2 Potts softmax noisy argmax;
 // every kind keeps groups of four replicas.

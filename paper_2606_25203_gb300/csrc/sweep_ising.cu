@@ -49,6 +49,13 @@ __device__ __forceinline__ void group_barrier(int id, int nthreads, int groups) 
 
 // Spin flips of a launch (replicas whose spin changed at a visit), summed per
 // warp into the controller's counter; every lane of the warp calls it.
+// The spin bits (bit 8q of a word) of the replicas r0 + q < R: the lanes of
+// a ragged last group that hold no replica are left out of the flip count.
+__device__ __forceinline__ uint32_t live_byte_lanes(int32_t r0, int32_t R) {
+    const int32_t v = R - r0;
+    return v >= 4 ? 0x01010101u : v <= 0 ? 0u : 0x01010101u & ((1u << (8 * v)) - 1u);
+}
+
 __device__ __forceinline__ void count_flips(uint32_t nflip, const DevCtl *ctl) {
     unsigned long long v = nflip;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -144,6 +151,7 @@ sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     const int32_t g = bid * gpc + gl;
     const int32_t r0 = g * 4;
     const bool active = r0 < R;
+    const uint32_t live = live_byte_lanes(r0, R);
     uint32_t *sp = spins_all + (size_t)gl * n_pad;
 
     if (active) {
@@ -218,7 +226,7 @@ sweep_ising_push_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                     const uint32_t fl = nw ^ old;
                     if (fl != 0u) {
                         sp[k] = F ^ (fl << 7);
-                        nflip += __popc(fl);
+                        nflip += __popc(fl & live);
                         // per byte +1 (up) or -1 (down), mod 2^32, times J_jk
                         const uint32_t delta = (nw & fl) - (old & fl);
                         const int32_t deg = (int32_t)((uint32_t)pr.x >> 24);
@@ -318,6 +326,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
     const int32_t g = bid * gpc + gl;
     const int32_t r0 = g * 4;
     const bool active = r0 < R;
+    const uint32_t live = live_byte_lanes(r0, R);
     uint32_t *sp = GSP ? gspins + (size_t)g * n_pad : spins_all + (size_t)gl * n_pad;
 
     if (active) {
@@ -409,7 +418,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                         __syncwarp();
                         if (act && sub == 0 && nw != old) {
                             sp[k] = nw;
-                            nflip += __popc(nw ^ old);
+                            nflip += __popc((nw ^ old) & live);
                         }
                     }
                     if (lev + 1 < L) fetch(min(end + vl, n - 1));
@@ -552,7 +561,7 @@ sweep_ising_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp,
                     const uint32_t nw = ising_decide<RULE>(A, H - 256 - jsum, u, old, tab_s, H);
                     if (nw != old) {
                         sp[k] = nw;
-                        nflip += __popc(nw ^ old);
+                        nflip += __popc((nw ^ old) & live);
                     }
                     i = inext;
                     pr = prn;

@@ -75,6 +75,11 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_wide(SweepDesc d, int gpc,
     const int32_t g = blockIdx.x * gpc + gl;
     const int32_t r0 = g * 4;
     const bool active = r0 < R;
+    // flips of replicas 0..3 counted at bits 0, 16, 1, 17 (below): those of
+    // the replicas r0 + q < R
+    const int32_t nlive = R - r0;
+    const uint32_t live = nlive >= 4 ? 0x00030003u : nlive == 3 ? 0x00010003u : nlive == 2 ? 0x00010001u
+                          : nlive == 1 ? 0x1u : 0u;
     uint2 *sp = GSP ? reinterpret_cast<uint2 *>(d.gsp) + (size_t)g * n_pad : words_all + (size_t)gl * n_pad;
 
     if (active) {
@@ -147,7 +152,7 @@ __global__ void __launch_bounds__(1024) k_sweep_ising_wide(SweepDesc d, int gpc,
                     const uint2 nw = wide_decide<RULE>(A, H - 65536 - jsum, u, old, d.tab, H);
                     if (nw.x != old.x || nw.y != old.y) {
                         sp[k] = nw;
-                        nflip += __popc((nw.x ^ old.x) | ((nw.y ^ old.y) << 1));
+                        nflip += __popc(((nw.x ^ old.x) | ((nw.y ^ old.y) << 1)) & live);
                     }
                 }
                 wide_barrier(1 + gl, tpg, gpc);

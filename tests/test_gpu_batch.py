@@ -22,9 +22,9 @@ def pg():
     return pg
 
 
-def _max_degree_graph(n, m, dmax, seed):
+def _max_degree_graph(n, m, dmax, seed, **kw):
     from test_gpu_parity import _max_degree_graph as g
-    return g(n, m, dmax, seed)
+    return g(n, m, dmax, seed, **kw)
 
 
 def mix():
@@ -38,10 +38,15 @@ def mix():
         (W.er_avg_degree(9000, 12, signed=True, seed=4), dict(R=36, sweeps=1, steps=18, rule=0, seed=14)),
         (W.er_avg_degree(2100, 20, signed=False, seed=5), dict(R=128, sweeps=2, steps=40, rule=1, seed=15,
                                                             z_rst=13, restart_reinit=0)),
-        # field ranges up to 7: 4-bit lanes in the batch as alone (ELL widths 4
-        # and 8, ragged groups of eight, both rules)
+        # field ranges that fit 4-bit lanes: eight replicas a word in the
+        # batch as alone -- the fixed bias (ELL widths 4 and 8) and the biased
+        # lanes (half-row ranges <= 15 on widths 12 and 16, weighted too; the
+        # signed gnm member above as well), ragged groups of eight, both rules
         (W.torus(80, 80, signed=True, seed=8), dict(R=28, sweeps=2, steps=15, rule=1, seed=17)),
         (_max_degree_graph(1200, 3500, 7, 9), dict(R=20, sweeps=2, steps=12, rule=0, seed=18)),
+        (_max_degree_graph(2500, 13000, 16, 10, weights=(-2, -1, 1, 1)), dict(R=44, sweeps=2, steps=14, rule=1,
+                                                                           seed=19)),
+        (_max_degree_graph(900, 4000, 12, 11), dict(R=12, sweeps=1, steps=10, rule=0, seed=20)),
     ]
 
 

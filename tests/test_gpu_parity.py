@@ -139,6 +139,7 @@ def test_lanes_per_vertex_shapes(pg, monkeypatch, cfg, rule):
     give the sequential result: dense ER rows longer than the lanes' share,
     sparse rows shorter than it, a ragged population, both update rules."""
     monkeypatch.setenv("PAMC_SWEEP_CFG", cfg)
+    monkeypatch.setenv("PAMC_SWEEP_NIBBLE", "0")    # the gnm rows would take the 4-bit lanes (one lane a vertex)
     lpv = int(cfg.split(",")[2])
     for inst, R in ((W.erdos_renyi(300, 0.2, signed=True, seed=4), 13),
                     (W.gnm(333, 900, signed=True, seed=2), 20)):
@@ -315,17 +316,25 @@ def test_push_and_pull_sweeps(pg, monkeypatch, push, rule):
                     cooldown_tau=1, seed=4)
 
 
-@pytest.mark.parametrize("push", ["1", "0"])
-def test_sweep_flip_count_and_timing(pg, monkeypatch, push):
+@pytest.mark.parametrize("case", ["push", "byte", "fixed4", "biased4", "wide16"])
+def test_sweep_flip_count_and_timing(pg, monkeypatch, case):
     """pamc_sweep_stats: the flips counted by the sweep kernels equal the
-    oracle's count over a run, and with timing on every sweep launch of the
-    handle is timed (one per step), with a positive device time."""
-    monkeypatch.setenv("PAMC_SWEEP_PUSH", push)
-    inst = W.gnm(500, 1400, signed=True, seed=5)
-    params = dict(R=12, sweeps=3, steps=10, beta0=0.2, beta1=2.0, stagnation=1, z_rst=6, seed=8)
+    oracle's count over a run -- on every field-lane layout, with a ragged
+    last replica group whose empty lanes must not count -- and with timing
+    on every sweep launch of the handle is timed (one per step), with a
+    positive device time."""
+    monkeypatch.setenv("PAMC_SWEEP_PUSH", "1" if case == "push" else "0")
+    monkeypatch.setenv("PAMC_SWEEP_NIBBLE", "0" if case == "byte" else "1")
+    inst = {"fixed4": W.torus(16, 16, signed=True, seed=2), "wide16": _weighted_hub()}.get(
+        case, W.gnm(500, 1400, signed=True, seed=5))
+    want = {"push": 2, "byte": 1, "fixed4": 17, "biased4": 17, "wide16": 8}[case]
+    params = dict(R=13, sweeps=3, steps=10, beta0=0.2, beta1=2.0, stagnation=1, z_rst=6, seed=8)
+    if case == "wide16":
+        params.update(beta0=0.01, beta1=0.3)
     ref = oracle.OracleRun(inst.row_ptr, inst.col, inst.w, **params)
     s = pg.Solver(inst.row_ptr, inst.col, inst.w)
     s.init(**params)
+    assert pg.pamc_sweep_mode(s.h) == want, case
     pg.pamc_set_sweep_timing(s.h, True)
     s.step(4)
     st = pg.pamc_sweep_stats(s.h)
@@ -435,8 +444,9 @@ def test_wide_field_range_refusals(pg):
     assert e.value.status == 4
 
 
-def _max_degree_graph(n, m, dmax, seed):
-    """A random graph with +-1 weights and every degree <= dmax, some = dmax."""
+def _max_degree_graph(n, m, dmax, seed, weights=(-1, 1)):
+    """A random graph with every degree <= dmax, some = dmax, weights drawn
+    from the given values."""
     rng = np.random.default_rng(seed)
     deg = np.zeros(n, dtype=np.int64)
     pairs = set()
@@ -448,30 +458,65 @@ def _max_degree_graph(n, m, dmax, seed):
         deg[a] += 1
         deg[b] += 1
     ei, ej = np.array(sorted(pairs)).T
-    w = rng.choice([-1, 1], size=len(ei))
+    w = rng.choice(np.asarray(weights), size=len(ei))
     inst = W.csr_from_edges(n, ei, ej, w, f"maxdeg{dmax}")
     assert deg.max() == dmax
     return inst
 
 
+def _half_row_ranges(inst):
+    """Per vertex, sum |w| over its first eight nonzero couplings (CSR order:
+    the ELL slots 0..7) and over the rest."""
+    out = []
+    for k in range(inst.n):
+        w = inst.w[inst.row_ptr[k]:inst.row_ptr[k + 1]]
+        w = np.abs(w[w != 0])
+        out.append((int(w[:8].sum()), int(w[8:].sum())))
+    return np.array(out)
+
+
 @pytest.mark.parametrize("nib", ["1", "0"])
 @pytest.mark.parametrize("rule", [0, 1])
 def test_nibble_lanes(pg, monkeypatch, nib, rule):
-    """Field ranges up to 7 run eight replicas per word (4-bit lanes) on ELL
-    rows of width 4 (torus) and 8 (degree 7): the oracle's results step after
-    step with a ragged population (R not a multiple of 8), cluster moves and
-    restarts, and with the lanes switched off; range 8 keeps the byte lanes."""
+    """Field ranges that fit 4-bit lanes run eight replicas per word: the
+    fixed bias (range <= 7) on ELL rows of width 4 (torus) and 8 (degree 7),
+    and the biased lanes with two half-row accumulators (each half-row's
+    range <= 15) on widths 8, 12 and 16, +-1 and weighted couplings.  The
+    oracle's results step after step with ragged populations (R not a
+    multiple of 8), cluster moves and restarts, and with the lanes switched
+    off."""
     monkeypatch.setenv("PAMC_SWEEP_NIBBLE", nib)
-    for inst, R in ((W.torus(18, 18, signed=True, seed=3), 13), (_max_degree_graph(400, 1100, 7, 4), 21),
-                    (_max_degree_graph(300, 700, 6, 5), 8)):
+    cases = ((W.torus(18, 18, signed=True, seed=3), 13), (_max_degree_graph(400, 1100, 7, 4), 21),
+             (_max_degree_graph(300, 700, 6, 5), 8), (_max_degree_graph(300, 900, 8, 6), 16),
+             (_max_degree_graph(500, 2400, 12, 7), 19), (_max_degree_graph(600, 3600, 16, 8), 27),
+             (_max_degree_graph(400, 1000, 7, 9, weights=(-2, -1, 1, 2)), 11),
+             (_max_degree_graph(500, 2000, 16, 10, weights=(-2, -1, -1, 1, 1, 2)), 24))
+    for inst, R in cases:
+        half = _half_row_ranges(inst)
+        assert half.max() <= 15, inst.name           # every case fits the biased lanes
         s = pg.Solver(inst.row_ptr, inst.col, inst.w)
         s.init(R=R, sweeps=3, steps=3, rule=rule, seed=4)
         assert pg.pamc_sweep_mode(s.h) == (17 if nib == "1" else 1), inst.name
         s.close()
         compare_run(pg, inst, 10, R=R, sweeps=3, beta0=0.2, beta1=3.0, rule=rule, stagnation=1, z_rst=7,
                     cooldown_tau=1, win_short=2, win_long=3, seed=4)
-    eight = _max_degree_graph(300, 900, 8, 6)
-    s = pg.Solver(eight.row_ptr, eight.col, eight.w)
+
+
+def test_nibble_lanes_limits(pg):
+    """A half-row range of 16 (or a row wider than 16) keeps the byte lanes;
+    15 takes the biased 4-bit lanes."""
+    n = 40
+    for wv, mode in ((2, 1), ((2, 2, 2, 2, 2, 2, 2, 1), 17)):
+        ws = np.resize(np.asarray(wv), 8)
+        inst = W.csr_from_edges(n, np.zeros(8, dtype=np.int64), np.arange(1, 9), ws, "star8")
+        assert _half_row_ranges(inst).max() == int(ws.sum())
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+        s.init(R=16, sweeps=2, steps=3, seed=1)
+        assert pg.pamc_sweep_mode(s.h) == mode, ws
+        s.close()
+        compare_run(pg, inst, 4, R=16, sweeps=2, beta0=0.2, beta1=2.0, seed=3)
+    hub = W.csr_from_edges(n, np.zeros(17, dtype=np.int64), np.arange(1, 18), np.ones(17), "star17")
+    s = pg.Solver(hub.row_ptr, hub.col, hub.w)
     s.init(R=16, sweeps=2, steps=3, seed=1)
     assert pg.pamc_sweep_mode(s.h) == 1
     s.close()
