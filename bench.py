@@ -73,9 +73,9 @@ def load_peaks():
 # only while the kernel sources still hash to what was captured.
 PROFILED_TRAFFIC = {
     # k_sweep_ising_nib<heat-bath, width 4> (eight replicas a word), torus
-    # 141x141, R=4096, 10 sweeps: one launch (42.49 MB read + 23.08 MB written)
-    "sweep_torus": (65.57e6, {"paper_2606_25203_gb300/csrc/sweep_nibble.cu":
-                              "cdeb9e0493057b5e4c84cff43c6fcf92200976b5"}),
+    # 141x141, R=4096, 10 sweeps: one launch (42.11 MB read + 21.99 MB written)
+    "sweep_torus": (64.10e6, {"paper_2606_25203_gb300/csrc/sweep_nibble.cu":
+                              "69b21e268255bc135dd9ddeb4be65725178d0691"}),
     # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.688 GB) scaled by n^2 to n=100,000
     # (captured at 6a66522d; the source since differs by one comment line)
     "dense_sweep_100k": (1.688e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
