@@ -76,10 +76,10 @@ PROFILED_TRAFFIC = {
     # 141x141, R=4096, 10 sweeps: one launch (42.11 MB read + 21.99 MB written)
     "sweep_torus": (64.10e6, {"paper_2606_25203_gb300/csrc/sweep_nibble.cu":
                               "69b21e268255bc135dd9ddeb4be65725178d0691"}),
-    # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.688 GB) scaled by n^2 to n=100,000
-    # (captured at 6a66522d; the source since differs by one comment line)
-    "dense_sweep_100k": (1.688e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
-                                                           "6f3fe9f84c0c5abf5a9ed8b7440af1d08f591712"}),
+    # k_dense_sweep<TCU>, 2 sweeps: the n=30,000 capture (1.6856 GB read + 3.3 MB written, the
+    # third step of a fresh run) scaled by n^2 to n=100,000
+    "dense_sweep_100k": (1.6889e9 * (100000 / 30000) ** 2, {"paper_2606_25203_gb300/csrc/dense.cu":
+                                                            "855fcc6f9ccbc2654a4c49491e4e39a2ac464c6a"}),
 }
 
 
