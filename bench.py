@@ -420,7 +420,8 @@ def run_ours(args):
                              peak_source=f"152 SMs x 128 int32 lanes x {sm_max:.0f} MHz ({peak_src} clock)",
                              note="launches of the timed window, beside the other instance's on their own stream "
                                   "(the SMs are shared, so each launch is stretched)",
-                             alone={k: iso[k] for k in ("achieved", "frac", "avg_launch_ms", "launches")}
+                             alone={k: iso[k] for k in ("achieved", "frac", "avg_launch_ms", "launches",
+                                                        "pull_count")}
                                    | {"window": f"steps {start + args.steps}..{start + 2 * args.steps - 1}, "
                                                 f"this instance alone"}),
             "clocks": clk.summary(),
@@ -684,10 +685,16 @@ def sweep_roofline(inst, steps, before, after, sm_max):
     ms, launches = after["ms"], after["launches"]
     achieved = ops / (ms / 1e3) / 1e12
     peak = 152 * 128 * sm_max * 1e6 / 1e12
+    # the same launches on the pull sweep's own count (every attempt reads its
+    # neighbours: 2 ops per incident coupling, no flip term), the count of
+    # earlier figures, for comparison
+    pull_ops = OPS_PER_ATTEMPT + 2.0 * inst.nnz / inst.n
+    pull_frac = att * pull_ops / (ms / 1e3) / 1e12 / peak
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
             "launches": launches, "avg_launch_ms": ms / max(launches, 1), "sweep_ms": ms,
             "ops_per_attempt": OPS_PER_ATTEMPT, "ops_per_flip": ops_per_flip(inst),
-            "flip_fraction": flips / att, "attempts_per_s": att / (ms / 1e3)}
+            "flip_fraction": flips / att, "attempts_per_s": att / (ms / 1e3),
+            "pull_count": {"ops_per_attempt": pull_ops, "frac": pull_frac}}
 
 
 def e2e_measure(pg, torch, insts, args, device, start=0):
@@ -850,6 +857,9 @@ def dense_measure(pg, torch, n, steps, warmup, e2e=False):
         "clocks": clk.summary(), "gpu_launches": launches,
         "timed_steps": f"steps 0..{steps - 1} of a fresh run (beta {P['beta0']} -> {P['beta1']} over {P['steps']})",
         "ms_step_first_last": [per_step[0], per_step[-1]],
+        # where the anneal's time goes: mean step time over windows of 10 steps
+        "ms_step_windows": {"size": 10, "mean_ms": [round(sum(per_step[i:i + 10]) / len(per_step[i:i + 10]), 3)
+                                                     for i in range(0, len(per_step), 10)]},
         "best_cut": m, "best_energy_density": e_best / n ** 1.5,
         "instance_generation_s": gen_s,
     }
