@@ -74,7 +74,7 @@ class Model:
 
 def test_tuner_sets_the_fastest_shape_per_class(monkeypatch):
     # class 0 is fastest at (2, 4, 2) with spin words on chip; class 2 at
-    # (1, 16, 1) with spin words in device memory; round 1 adds noise
+    # (1, 16, 1) with spin words in device memory; the second timing pass adds noise
     def cost(cls, g, w, lv, gm, rnd):
         best = {0: (2, 4, 2, 0), 2: (1, 16, 1, 1)}[cls]
         d = abs(g - best[0]) + abs(w - best[1]) / 4 + abs(lv - best[2]) + 0.3 * abs(gm - best[3])
