@@ -12,6 +12,12 @@
 // Philox(k, sweep, t, FLIP<<24 | r/2): two calls per group.  Levels of the
 // (t, sweep) schedule give the exact sequential order.  The couplings come
 // from the position-indexed ELL of the schedule when it exists, else from CSR.
+//
+// Lane pairs (PAIR, ELL rows): two lanes share a position.  Lane s runs the
+// Philox call of replicas 2s and 2s + 1 and sums the coupling slots of its
+// parity; one shuffle adds the two partial byte-lane sums (one of them
+// carries the bias) and one more ORs the two halves of the new label word.
+// The draws and decisions are those of the one-lane body.
 #include "pamc_device.cuh"
 #include "pamc_internal.h"
 
@@ -34,7 +40,7 @@ __device__ __forceinline__ uint2 onehot(uint32_t labels) {
 
 // The sweeps of one CTA's replica groups (groups bid*gpc .. bid*gpc+gpc-1 of
 // the instance), shared by the single-instance and the batched kernels.
-template <bool ELLP>
+template <bool ELLP, bool PAIR>
 __device__ __forceinline__ void
 potts_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
            int32_t H, int32_t R, int32_t S, uint32_t key0, uint32_t key1, int32_t t, int32_t slot,
@@ -87,6 +93,67 @@ potts_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint3
             const int32_t L = snlev[sb];
             for (int32_t lev = 0; lev < L; ++lev) {
                 const int32_t beg = lp[lev], end = lp[lev + 1];
+                if constexpr (PAIR && ELLP) {
+                    // every lane of the group runs the same passes (the
+                    // shuffles need whole warps); a pair past the level's end
+                    // works on its last position and writes nothing
+                    const int sl = li & 1;
+                    const int32_t half = tpg >> 1;
+                    for (int32_t b = beg; b < end; b += half) {
+                        const int32_t iv = b + (li >> 1);
+                        const bool valid = iv < end;
+                        const int32_t i = valid ? iv : end - 1;
+                        const int2 pr = pos[i];
+                        const uint32_t *ep = es + (size_t)(i >> 5) * 32 * W + (i & 31);
+                        uint32_t ev[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) ev[q] = 2 * q + sl < W ? ep[(2 * q + sl) * 32] : 0u;
+                        const int32_t k = pr.x & 0xFFFFFF;
+                        const int32_t deg = (int32_t)((uint32_t)pr.x >> 24);
+                        const int32_t jsum = pr.y;
+                        const u32x4 u = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t,
+                                               (kTagFlip << 24) | (uint32_t)(2 * gk + sl), key0, key1);
+                        uint32_t A0 = sl ? 0u : 0x80808080u, A1 = sl ? 0u : 0x80808080u;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const uint2 o = oh[ev[q] & 0xFFFFFFu];
+                            const uint32_t J = (uint32_t)((int32_t)ev[q] >> 24);
+                            A0 += o.x * J;
+                            A1 += o.y * J;
+                        }
+                        for (int32_t b0 = 16; b0 < deg; b0 += 4) {   // W >= deg rounded up to 4
+                            const uint32_t ew0 = ep[(b0 + sl) * 32], ew1 = ep[(b0 + 2 + sl) * 32];
+                            const uint2 o0 = oh[ew0 & 0xFFFFFFu], o1 = oh[ew1 & 0xFFFFFFu];
+                            const uint32_t J0 = (uint32_t)((int32_t)ew0 >> 24), J1 = (uint32_t)((int32_t)ew1 >> 24);
+                            A0 += o0.x * J0 + o1.x * J1;
+                            A1 += o0.y * J0 + o1.y * J1;
+                        }
+                        A0 += __shfl_xor_sync(0xffffffffu, A0, 1);
+                        A1 += __shfl_xor_sync(0xffffffffu, A1, 1);
+                        uint32_t lab = 0u;
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int q = 2 * sl + j;
+                            uint32_t c = 3u;   // padding replicas: no label
+                            if (r0 + q < R) {
+                                const int32_t s0 = (int32_t)((A0 >> (8 * q)) & 0xFFu) - 128;
+                                const int32_t s1 = (int32_t)((A1 >> (8 * q)) & 0xFFu) - 128;
+                                const int32_t s2 = jsum - s0 - s1;
+                                const uint64_t t1 = __ldg(&T1[(size_t)(s1 - s0 + 2 * H) * W1 + (s2 - s0 + 2 * H)]);
+                                const uint32_t w0 = j ? u.z : u.x, w1 = j ? u.w : u.y;
+                                if ((uint64_t)w0 < t1) c = 0u;
+                                else if ((uint64_t)w1 < T2s[s2 - s1 + 2 * H]) c = 1u;
+                                else c = 2u;
+                            }
+                            lab |= c << (8 * q);
+                        }
+                        lab |= __shfl_xor_sync(0xffffffffu, lab, 1);
+                        const uint2 nw = onehot(lab), old = oh[k];
+                        if (valid && sl == 0 && (nw.x != old.x || nw.y != old.y)) oh[k] = nw;
+                    }
+                    potts_barrier(1 + gl, tpg, gpc);
+                    continue;
+                }
                 for (int32_t i = beg + li; i < end; i += tpg) {
                     uint32_t A0 = 0x80808080u, A1 = 0x80808080u;
                     int32_t k, jsum;
@@ -199,7 +266,7 @@ potts_body(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint3
     if (active && li < 4 && r0 + li < R) E_dst[r0 + li] = -(long long)red[gl * 4 + li] - Wsum;
 }
 
-template <bool ELLP>
+template <bool ELLP, bool PAIR>
 __global__ void __launch_bounds__(1024)
 k_sweep_potts(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
               int32_t H, int32_t R, int32_t S, uint32_t key0, uint32_t key1, int32_t t, int32_t slot,
@@ -209,8 +276,8 @@ k_sweep_potts(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const ui
               const int8_t *__restrict__ src, const int32_t *__restrict__ parent, int8_t *__restrict__ dst,
               int64_t *__restrict__ E_dst, const DevCtl *__restrict__ ctl, int64_t Wsum, int gpc, int tpg,
               int32_t gbase) {
-    potts_body<ELLP>(n, n_pad, rp, adj, H, R, S, key0, key1, t, slot, sorder, slvl, snlev, sell, spos, W, tab, src,
-                     parent, dst, E_dst, ctl, Wsum, gpc, tpg, blockIdx.x, gbase);
+    potts_body<ELLP, PAIR>(n, n_pad, rp, adj, H, R, S, key0, key1, t, slot, sorder, slvl, snlev, sell, spos, W,
+                           tab, src, parent, dst, E_dst, ctl, Wsum, gpc, tpg, blockIdx.x, gbase);
 }
 
 // Many Max-3-Cut instances in one launch: CTA b works on instance items[b].x,
@@ -225,7 +292,7 @@ k_sweep_potts_batched(const SweepDesc *__restrict__ descs, const int2 *__restric
     const DevCtl *ctl = d.ctl;
     const int32_t t = ctl->t;
     if (t >= d.t_end) return;
-    potts_body<ELLP>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, d.K.k0[0], d.K.k1[0], t, t % d.slots, d.sorder,
+    potts_body<ELLP, false>(d.n, d.n_pad, d.rp, d.adj, d.H, d.R, d.S, d.K.k0[0], d.K.k1[0], t, t % d.slots, d.sorder,
                      d.slvl, d.snlev, d.sell, d.spos, d.W, d.tab, d.sp[t & 1], d.parent, d.sp[(t + 1) & 1],
                      d.en[(t + 1) & 1], ctl, d.Wsum, gpc, tpg, it.y, d.gbase);
 }
@@ -248,18 +315,20 @@ cudaError_t launch_sweep_potts(int32_t n, const int32_t *rp, const uint32_t *adj
     const int grid = (groups + gpc - 1) / gpc;
     const uint32_t k0 = (uint32_t)p.seed, k1 = (uint32_t)(p.seed >> 32);
     const bool ell = sv.ell != nullptr;
+    const bool pair = ell && cfg.lanes_per_vertex == 2;   // lane pairs: ELL rows only
     cudaError_t err;
-#define PAMC_POTTS(EL)                                                                                            \
+#define PAMC_POTTS(EL, PA)                                                                                        \
     do {                                                                                                          \
-        err = allow_dynamic_smem(k_sweep_potts<EL>, smem);                                                        \
+        err = allow_dynamic_smem(k_sweep_potts<EL, PA>, smem);                                                    \
         if (err != cudaSuccess) return err;                                                                       \
-        k_sweep_potts<EL><<<grid, gpc * tpg, smem, st>>>(                                                         \
+        k_sweep_potts<EL, PA><<<grid, gpc * tpg, smem, st>>>(                                                     \
             n, (n + 3) & ~3, rp, adj, H, p.R, p.sweeps, k0, k1, t, slot, sv.order, sv.lvl_ptr, sv.nlev,           \
             EL ? sv.ell : nullptr, EL ? sv.pos : nullptr, EL ? sv.W : 0, tab, src, parent, dst, E_dst, ctl, Wsum, \
             gpc, tpg, rbase / 4);                                                                                 \
     } while (0)
-    if (ell) PAMC_POTTS(true);
-    else PAMC_POTTS(false);
+    if (pair) PAMC_POTTS(true, true);
+    else if (ell) PAMC_POTTS(true, false);
+    else PAMC_POTTS(false, false);
 #undef PAMC_POTTS
     return cudaGetLastError();
 }

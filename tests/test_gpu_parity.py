@@ -154,13 +154,21 @@ def test_lanes_per_vertex_shapes(pg, monkeypatch, cfg, rule):
 @pytest.mark.parametrize("rule", [0, 2])
 def test_potts_launch_shapes_same_results(pg, monkeypatch, rule):
     """Potts sweeps under several forced launch shapes (groups per CTA,
-    warps per group) give the oracle's labels and energies."""
+    warps per group, and for the cascaded sampler lane pairs: two lanes a
+    position, rows longer than 16 slots, levels that leave pairs idle) give
+    the oracle's labels and energies."""
     inst = W.gnm(700, 4200, signed=False, seed=12)
-    params = dict(kind=1, rule=rule, R=24, sweeps=2, beta0=0.2, beta1=2.5, seed=6)
+    assert int(np.diff(inst.row_ptr).max()) > 16
+    params = dict(kind=1, rule=rule, R=26, sweeps=2, beta0=0.2, beta1=2.5, seed=6)
     if rule == 2:
         params.update(K=3, gamma=1.0)
-    for cfg in ("1,1", "1,4", "3,2", "2,8"):
+    for cfg in ("1,1", "1,4", "3,2", "2,8", "1,1,2", "1,8,2", "3,2,2"):
         monkeypatch.setenv("PAMC_SWEEP_CFG", cfg)
+        if cfg.count(",") == 2 and cfg.endswith(",2") and rule == 0:
+            s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+            s.init(steps=4, **params)
+            assert pg.pamc_sweep_shape(s.h)[2] == 2, cfg
+            s.close()
         compare_run(pg, inst, 4, **params)
 
 
