@@ -323,8 +323,8 @@ SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level,
         if (got >= 2 && a >= 1 && a <= 15 && b >= 1 && a * b * 32 <= 1024 &&
             v >= 1 && v <= 32 && (v & (v - 1)) == 0) {
             // Ising: lanes per vertex on ELL rows; the cascaded Potts sweep:
-            // lane pairs (2) on ELL rows
-            const int lpv = lpv_ok ? v : (kind == 1 && ell_w > 0 && v == 2) ? 2 : 1;
+            // lane pairs (2) on ELL rows; the softmax Potts sweep: quads (4)
+            const int lpv = lpv_ok ? v : (kind == 1 && ell_w > 0 && v == 2) ? 2 : (kind == 2 && v == 4) ? 4 : 1;
             SweepCfg c{a, b, lpv};
             if (sweep_smem_bytes(kind, n, H, c) <= 227 * 1024) return c;
         }
@@ -361,13 +361,15 @@ SweepCfg choose_cfg(int kind, int32_t n, int32_t R, int32_t H, double avg_level,
         SweepCfg c{1, 1, 1};
         while (c.warps_per_group < 32 && 32.0 * c.warps_per_group < std::max(avg_level, 1.0)) c.warps_per_group *= 2;
         if (32 * c.warps_per_group <= lanes && sweep_smem_bytes(kind, n, H, c) <= 227 * 1024) {
-            // the cascaded sampler on ELL rows: lane pairs, twice the warps
-            // (a pass covers the same positions) where that still fits the
-            // group's share of the SM, two groups to a CTA where the SMs hold
-            // two or more (configuration 3: 0.720 against 0.773 ms per step
-            // for one group of four warps a CTA, one lane a position)
-            if (kind == 1 && ell_w > 0 && c.warps_per_group <= 16 && 64 * c.warps_per_group <= lanes) {
-                SweepCfg p2{1, 2 * c.warps_per_group, 2};
+            // several lanes a position -- the cascaded sampler on ELL rows:
+            // pairs; the softmax sampler: quads -- with twice the warps where
+            // that still fits the group's share of the SM, two groups to a
+            // CTA where the SMs hold two or more (configuration 3: cascaded
+            // 0.720 against 0.773 ms per step, softmax 1.65 against 2.08, for
+            // one group of four warps a CTA, one lane a position)
+            if (((kind == 1 && ell_w > 0) || kind == 2) && c.warps_per_group <= 16 &&
+                64 * c.warps_per_group <= lanes) {
+                SweepCfg p2{1, 2 * c.warps_per_group, kind == 2 ? 4 : 2};
                 if (groups >= 2 * (int64_t)sms && 2 * 32 * p2.warps_per_group <= 1024) p2.groups_per_cta = 2;
                 if (sweep_smem_bytes(kind, n, H, p2) <= 227 * 1024) return p2;
             }

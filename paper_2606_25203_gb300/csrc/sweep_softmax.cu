@@ -16,6 +16,11 @@
 // words c mod 4 of Philox(k, sweep, t, FLIP<<24 | (r * ceil(K/4) + c/4)).
 // Levels of the (t, sweep) schedule give the exact sequential order, as for
 // the Ising sweep.
+//
+// Quads (QUAD): four lanes share a position, lane q deciding replica q.  Each
+// lane sums every fourth coupling of the row (one of them carries the bias);
+// two shuffles per label add the partial byte-lane sums, two more OR the new
+// label bytes.  The draws and decisions are those of the one-lane body.
 #include "pamc_device.cuh"
 #include "pamc_internal.h"
 
@@ -33,6 +38,7 @@ __device__ __forceinline__ void softmax_barrier(int id, int nthreads, int groups
     }
 }
 
+template <bool QUAD>
 __global__ void __launch_bounds__(1024)
 k_sweep_softmax(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const uint32_t *__restrict__ adj,
                 int32_t H, int32_t K, float gamma, int32_t R, int32_t S, uint32_t key0, uint32_t key1,
@@ -84,6 +90,82 @@ k_sweep_softmax(int32_t n, int32_t n_pad, const int32_t *__restrict__ rp, const 
             const int32_t L = snlev[sb];
             for (int32_t lev = 0; lev < L; ++lev) {
                 const int32_t beg = lp[lev], end = lp[lev + 1];
+                if constexpr (QUAD) {
+                    // every lane of the group runs the same passes (the
+                    // shuffles need whole warps); a quad past the level's end
+                    // works on its last position and writes nothing
+                    const int qq = li & 3;
+                    const int32_t quarter = tpg >> 2;
+                    for (int32_t b0 = beg; b0 < end; b0 += quarter) {
+                        const int32_t iv = b0 + (li >> 2);
+                        const bool valid = iv < end;
+                        const int32_t k = ord[valid ? iv : end - 1] & 0xFFFFFF;
+                        uint32_t A[kMaxK];
+#pragma unroll
+                        for (int c = 0; c < kMaxK; ++c) A[c] = qq == 0 ? 0x80808080u : 0u;
+                        for (int32_t e = rp[k] + qq; e < rp[k + 1]; e += 4) {
+                            const uint32_t a = adj[e];
+                            const uint32_t J = (uint32_t)((int32_t)a >> 24);
+                            const uint32_t w = sp[a & 0xFFFFFFu];
+#pragma unroll
+                            for (int c = 0; c < kMaxK; ++c)
+                                if (c < K) A[c] += (__vcmpeq4(w, 0x01010101u * (uint32_t)c) & 0x01010101u) * J;
+                        }
+#pragma unroll
+                        for (int c = 0; c < kMaxK; ++c)
+                            if (c < K) {   // K is the same for every lane
+                                A[c] += __shfl_xor_sync(0xffffffffu, A[c], 1);
+                                A[c] += __shfl_xor_sync(0xffffffffu, A[c], 2);
+                            }
+                        uint32_t lab = 0u;
+                        const int32_t r = r0 + qq;
+                        if (r < R) {
+                            int32_t syn[kMaxK];
+                            int32_t smax = -1000;
+#pragma unroll
+                            for (int c = 0; c < kMaxK; ++c) {
+                                syn[c] = (int32_t)((A[c] >> (8 * qq)) & 0xFFu) - 128;
+                                if (c < K) smax = max(smax, syn[c]);
+                            }
+                            float ev[kMaxK];
+                            float Ssum = 0.0f;
+#pragma unroll
+                            for (int c = 0; c < kMaxK; ++c) {
+                                ev[c] = c < K ? tab_s[smax - syn[c]] : 0.0f;
+                                if (c < K) Ssum = __fadd_rn(Ssum, ev[c]);
+                            }
+                            uint32_t u[kMaxK];
+#pragma unroll
+                            for (int b = 0; b < kMaxK / 4; ++b) {
+                                if (b < nb) {
+                                    const u32x4 x = philox((uint32_t)k, (uint32_t)sw, (uint32_t)t,
+                                                           (kTagFlip << 24) | (uint32_t)((r + rbase) * nb + b), key0,
+                                                           key1);
+                                    u[4 * b] = x.x; u[4 * b + 1] = x.y; u[4 * b + 2] = x.z; u[4 * b + 3] = x.w;
+                                } else {
+                                    u[4 * b] = u[4 * b + 1] = u[4 * b + 2] = u[4 * b + 3] = 0u;
+                                }
+                            }
+                            int32_t best = 0;
+                            float vbest = 0.0f;
+#pragma unroll
+                            for (int c = 0; c < kMaxK; ++c) {
+                                if (c < K) {
+                                    const float P = __fdiv_rn(ev[c], Ssum);
+                                    const float U = __fmul_rn(__uint2float_rn(u[c]), 0x1p-32f);
+                                    const float v = __fsub_rn(P, __fmul_rn(gamma, U));
+                                    if (c == 0 || v > vbest) { vbest = v; best = c; }
+                                }
+                            }
+                            lab = (uint32_t)best << (8 * qq);
+                        }
+                        lab |= __shfl_xor_sync(0xffffffffu, lab, 1);
+                        lab |= __shfl_xor_sync(0xffffffffu, lab, 2);
+                        if (valid && qq == 0 && lab != sp[k]) sp[k] = lab;
+                    }
+                    softmax_barrier(1 + gl, tpg, gpc);
+                    continue;
+                }
                 for (int32_t i = beg + li; i < end; i += tpg) {
                     const int32_t k = ord[i] & 0xFFFFFF;
                     uint32_t A[kMaxK];
@@ -190,13 +272,20 @@ cudaError_t launch_sweep_softmax(int32_t n, const int32_t *rp, const uint32_t *a
     const int32_t groups = (p.R + 3) / 4;
     const int gpc = cfg.groups_per_cta, tpg = cfg.warps_per_group * 32;
     const size_t smem = sweep_softmax_smem_bytes(n, H, cfg);
-    cudaError_t err = allow_dynamic_smem(k_sweep_softmax, smem);
-    if (err != cudaSuccess) return err;
     const int grid = (groups + gpc - 1) / gpc;
-    k_sweep_softmax<<<grid, gpc * tpg, smem, st>>>(
-        n, (n + 3) & ~3, rp, adj, H, p.K, (float)p.gamma, p.R, p.sweeps, (uint32_t)p.seed,
-        (uint32_t)(p.seed >> 32), t, slot, sv.order, sv.lvl_ptr, sv.nlev, reinterpret_cast<const float *>(tab),
-        src, parent, ncm_idx, dst, E_dst, ctl, Wsum, gpc, tpg, rbase);
+    cudaError_t err;
+#define PAMC_SOFTMAX(QU)                                                                                          \
+    do {                                                                                                          \
+        err = allow_dynamic_smem(k_sweep_softmax<QU>, smem);                                                      \
+        if (err != cudaSuccess) return err;                                                                       \
+        k_sweep_softmax<QU><<<grid, gpc * tpg, smem, st>>>(                                                       \
+            n, (n + 3) & ~3, rp, adj, H, p.K, (float)p.gamma, p.R, p.sweeps, (uint32_t)p.seed,                    \
+            (uint32_t)(p.seed >> 32), t, slot, sv.order, sv.lvl_ptr, sv.nlev, reinterpret_cast<const float *>(tab), \
+            src, parent, ncm_idx, dst, E_dst, ctl, Wsum, gpc, tpg, rbase);                                        \
+    } while (0)
+    if (cfg.lanes_per_vertex == 4) PAMC_SOFTMAX(true);   // quads: four lanes a position
+    else PAMC_SOFTMAX(false);
+#undef PAMC_SOFTMAX
     return cudaGetLastError();
 }
 

@@ -154,21 +154,23 @@ def test_lanes_per_vertex_shapes(pg, monkeypatch, cfg, rule):
 @pytest.mark.parametrize("rule", [0, 2])
 def test_potts_launch_shapes_same_results(pg, monkeypatch, rule):
     """Potts sweeps under several forced launch shapes (groups per CTA,
-    warps per group, and for the cascaded sampler lane pairs: two lanes a
-    position, rows longer than 16 slots, levels that leave pairs idle) give
+    warps per group; lane pairs for the cascaded sampler and quads of lanes
+    for the softmax one -- several lanes a position, rows longer than 16
+    slots, levels that leave pairs or quads idle, a ragged population) give
     the oracle's labels and energies."""
     inst = W.gnm(700, 4200, signed=False, seed=12)
     assert int(np.diff(inst.row_ptr).max()) > 16
     params = dict(kind=1, rule=rule, R=26, sweeps=2, beta0=0.2, beta1=2.5, seed=6)
     if rule == 2:
         params.update(K=3, gamma=1.0)
-    for cfg in ("1,1", "1,4", "3,2", "2,8", "1,1,2", "1,8,2", "3,2,2"):
+    for cfg in ("1,1", "1,4", "3,2", "2,8", "1,1,2", "1,8,2", "3,2,2", "1,1,4", "1,8,4", "2,4,4"):
         monkeypatch.setenv("PAMC_SWEEP_CFG", cfg)
-        if cfg.count(",") == 2 and cfg.endswith(",2") and rule == 0:
-            s = pg.Solver(inst.row_ptr, inst.col, inst.w)
-            s.init(steps=4, **params)
-            assert pg.pamc_sweep_shape(s.h)[2] == 2, cfg
-            s.close()
+        lanes = int(cfg.split(",")[2]) if cfg.count(",") == 2 else 1
+        want = lanes if (rule, lanes) in ((0, 2), (2, 4)) else 1
+        s = pg.Solver(inst.row_ptr, inst.col, inst.w)
+        s.init(steps=4, **params)
+        assert pg.pamc_sweep_shape(s.h)[2] == want, cfg
+        s.close()
         compare_run(pg, inst, 4, **params)
 
 
