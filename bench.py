@@ -48,6 +48,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# stdout carries the one JSON line: NCCL's own log (its version banner when
+# NCCL_DEBUG asks for it) goes to stderr unless the caller chose a file
+os.environ.setdefault("NCCL_DEBUG_FILE", "/dev/stderr")
 
 import workloads as W  # noqa: E402
 
