@@ -48,9 +48,16 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# stdout carries the one JSON line: NCCL's own log (its version banner when
-# NCCL_DEBUG asks for it) goes to stderr unless the caller chose a file
-os.environ.setdefault("NCCL_DEBUG_FILE", "/dev/stderr")
+# The JSON lines go to JSON_OUT.  Run as a script, that is the process's
+# original stdout and file descriptor 1 is pointed at stderr, so nothing else
+# (NCCL's version banner, library messages) reaches stdout.
+JSON_OUT = sys.stdout
+
+
+def emit(obj) -> None:
+    JSON_OUT.write(json.dumps(obj) + "\n")
+    JSON_OUT.flush()
+
 
 import workloads as W  # noqa: E402
 
@@ -249,7 +256,7 @@ def run_reference(args):
                          "sample": f"first iteration of both instances with R={Rs} (same seeds)"},
         "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
+    emit(line)
 
 
 def cpu_baseline_sample():
@@ -373,9 +380,9 @@ def run_ours(args):
 
     if args.lean:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": "attempts/s",
+            emit({"metric": METRIC, "value": value, "unit": "attempts/s",
                               "ms_per_step": ms / args.steps, "gpu_launches": launches,
-                              "clocks": clk.summary(), "config": {"only": ONLY}}))
+                              "clocks": clk.summary(), "config": {"only": ONLY}})
         for s in solvers:
             s.close()
         return None
@@ -433,7 +440,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "dense100k": dense,
         }
-        print(json.dumps(result))
+        emit(result)
     for s in solvers:
         s.close()
     if dist:
@@ -542,9 +549,9 @@ def run_split(args, pg, torch, dist, rank, world, local):
         sh.close()
     if args.lean:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
+            emit({"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
                               "ms_per_step": ms / args.steps, "gpu_launches": launches, "clocks": clk.summary(),
-                              "config": {"only": ONLY, "R_total": Rg, "populations": npop, "split": True}}))
+                              "config": {"only": ONLY, "R_total": Rg, "populations": npop, "split": True}})
         dist.destroy_process_group()
         return None
     peaks, peak_src = load_peaks()
@@ -576,7 +583,7 @@ def run_split(args, pg, torch, dist, rank, world, local):
             "e2e": e2e,
             "cpu_baseline": None,
         }
-        print(json.dumps(result))
+        emit(result)
     dist.destroy_process_group()
     return result
 
@@ -875,7 +882,7 @@ def run_dense(args):
     if world > 1 or args.split:
         return run_dense_split(args, pg, torch, world)
     pg.load()
-    print(json.dumps(dense_measure(pg, torch, args.dense_n, args.steps, args.warmup, e2e=args.dense_e2e)))
+    emit(dense_measure(pg, torch, args.dense_n, args.steps, args.warmup, e2e=args.dense_e2e))
 
 
 def run_dense_split(args, pg, torch, world):
@@ -928,7 +935,7 @@ def run_dense_split(args, pg, torch, world):
     moved = sh.moved
     sh.close()
     if rank == 0:
-        print(json.dumps({
+        emit({
             "metric": METRIC, "value": att / (ms / 1e3), "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -937,7 +944,7 @@ def run_dense_split(args, pg, torch, world):
                        "parallelism": f"one population split over {world} GPU(s), NCCL exchange per iteration",
                        "replicas_moved_per_step": moved / args.steps,
                        "timed_steps": f"steps 0..{args.steps - 1} of a fresh run"},
-            "best_cut": int(cut), "clocks": clk.summary()}))
+            "best_cut": int(cut), "clocks": clk.summary()})
     dist.destroy_process_group()
 
 
@@ -1025,7 +1032,7 @@ def run_serving(args):
         "autotune_s": tune_s,
         "request_generation_s": gen_s,
     }
-    print(json.dumps(line))
+    emit(line)
 
 
 def run_batch(args):
@@ -1072,7 +1079,7 @@ def run_batch(args):
                      "traffic": None, "kernel": "whole batched step (all kernels)"},
         "clocks": clk.summary(), "gpu_launches": pg.pamc_batch_launch_count(b) - l0,
     }
-    print(json.dumps(line))
+    emit(line)
     pg.pamc_batch_destroy(b)
     for h in hs:
         pg.pamc_destroy(h)
@@ -1139,7 +1146,7 @@ def run_potts(args):
                     "gamma": 1.0},
         "clocks": c["clocks"], "gpu_launches": c["launches"],
     }
-    print(json.dumps(line))
+    emit(line)
 
 
 # time-to-target runs: the paper's method (stagnation control and NCM on) on the Erdos-Renyi N=800 instance
@@ -1214,7 +1221,7 @@ def run_tts(args):
         "reached": sum(1 for r in reach if r is not None), "runs_wall_s": wall,
         "gpu_launches": launches, "clocks": clk.summary(),
     }
-    print(json.dumps(line))
+    emit(line)
 
 
 def run_diag(args):
@@ -1268,7 +1275,7 @@ def run_diag(args):
         "mean_normalised_distance": total / (pairs * inst.n), "lineage_ms": t_lin * 1e3,
         "families_alive": nf, "clocks": clk.summary(), "gpu_launches": 2 * args.steps,
     }
-    print(json.dumps(line))
+    emit(line)
     pg.pamc_destroy(h)
 
 
@@ -1336,4 +1343,7 @@ def main():
 
 
 if __name__ == "__main__":
+    sys.stdout.flush()
+    JSON_OUT = os.fdopen(os.dup(1), "w")
+    os.dup2(2, 1)
     main()
