@@ -362,6 +362,33 @@ def test_server_equals_sequential(pg):
         assert r.finished >= r.admitted >= r.arrival - 1e-9
 
 
+def test_served_stream_requests_match_oracle(pg):
+    """Requests drawn by the configuration-5 generator at its own settings (N
+    in [800, 20000], Erdos-Renyi unit and +-1 weights of degree 20 and +-1
+    tori, a quarter Max-3-Cut): the six smallest of forty, served through the
+    batching server with a small budget, each end with the oracle's best cut
+    and configuration (fewer replicas and steps than the stream's, so that
+    the oracle finishes in seconds)."""
+    from paper_2606_25203_gb300.serving import Server
+    stream = W.serving_stream(40, rate=400.0, seed=11, max3cut_frac=0.25)
+    reqs = sorted(stream, key=lambda r: r.inst.n)[:6]
+    assert {r.kind for r in reqs} == {0, 1}, [(r.inst.name, r.kind) for r in reqs]
+    params = dict(R=32, sweeps=2, steps=12, beta0=0.1, beta1=3.0, seed=23)
+    srv = Server(hbm_budget=64 << 20, max_active=3, steps_per_tick=4, keep_spins=True)
+    try:
+        st = srv.serve(reqs, params)
+    finally:
+        srv.close()
+    got = {r.rid: r for r in st.results}
+    assert len(got) == len(reqs)
+    for req in reqs:
+        ref = oracle.OracleRun(req.inst.row_ptr, req.inst.col, req.inst.w, kind=req.kind, **params)
+        ref.step(params["steps"])
+        cut, spins = ref.best()
+        assert got[req.rid].cut == cut, f"request {req.rid} ({req.inst.name}, kind {req.kind})"
+        np.testing.assert_array_equal(got[req.rid].spins, spins, err_msg=f"request {req.rid}")
+
+
 def test_shapes_change_speed_not_results(pg):
     """Every launch shape of every size class gives the same members' results,
     and the autotuner sets one of the candidates."""
