@@ -159,10 +159,14 @@ pamc_status pamc_control_history(pamc_handle h, int64_t *hist, int32_t *hist_len
 int64_t pamc_launch_count(pamc_handle h);
 
 /* Launch shape the sparse sweep of an initialised run uses: replica groups
- * (four replicas each) per CTA, warps per group, and lanes that share one
- * vertex's couplings (1 except for Ising runs on ELL schedules; set by
+ * per CTA (four replicas each; eight on 4-bit lanes, see pamc_sweep_mode),
+ * warps per group, and lanes that share one position: Ising runs on ELL
+ * schedules split a vertex's couplings over 1-32 lanes; Max-3-Cut runs take
+ * lane pairs with the cascaded sampler on ELL schedules (each lane one
+ * Philox call, half the couplings and two replicas' decisions) and quads
+ * with the softmax sampler (one replica each); 1 otherwise.  Set by
  * pamc_init from the schedule's level widths, or by the environment variable
- * PAMC_SWEEP_CFG="gpc,wpg[,lpv]").  The shape changes speed only, never
+ * PAMC_SWEEP_CFG="gpc,wpg[,lpv]".  The shape changes speed only, never
  * results.  PAMC_ERR_STATE before pamc_init or for dense runs. */
 pamc_status pamc_sweep_shape(pamc_handle h, int *groups_per_cta, int *warps_per_group, int *lanes_per_vertex);
 
