@@ -64,8 +64,8 @@ def test_reference_arm_line(tmp_path):
                           "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600,
                          cwd=str(tmp_path))
     assert out.returncode == 0, out.stderr
-    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
-    assert len(lines) == 1
+    lines = out.stdout.splitlines()
+    assert len(lines) == 1 and lines[0].startswith("{"), out.stdout   # stdout holds the JSON line only
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "attempts/s"
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 1 and d["higher_is_better"] is True
@@ -97,3 +97,23 @@ def test_timed_window_holds_the_most_control_events():
     assert s["first"] == 115 and s["last"] == 134
     assert s["ncm_steps"] == [[121], []] and s["reheat_steps"] == [[120], []]
     assert s["ncm_spins_flipped"] == [12, 0]
+
+
+def test_sweep_roofline_counts():
+    """The ALU roofline of a sweep window: the method's count (18 operations
+    per attempt, 1 + 2 x degree per counted flip) and the pull sweep's count
+    (18 + 2 x degree per attempt, no flip term) over the summed launch time,
+    against 152 SMs x 128 lanes x the clock."""
+    import workloads as W
+    inst = W.torus(10, 10, signed=True, seed=1)        # degree 4
+    att = bench.R * inst.n * bench.SWEEPS * 3
+    flips = att // 20
+    r = bench.sweep_roofline(inst, 3, {"flips": 0}, {"flips": flips, "ms": 2.0, "launches": 3}, 2000.0)
+    peak = 152 * 128 * 2000e6 / 1e12
+    assert abs(r["peak"] - peak) < 1e-9
+    assert abs(r["achieved"] - (att * 18 + flips * 9) / 2e-3 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / peak) < 1e-12
+    assert r["pull_count"]["ops_per_attempt"] == 26.0
+    assert abs(r["pull_count"]["frac"] - att * 26 / 2e-3 / 1e12 / peak) < 1e-12
+    assert r["launches"] == 3 and abs(r["avg_launch_ms"] - 2.0 / 3) < 1e-12
+    assert abs(r["flip_fraction"] - flips / att) < 1e-12
